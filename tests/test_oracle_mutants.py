@@ -1,0 +1,150 @@
+"""The pins must catch plausible mistakes in the oracle.
+
+Each case copies the oracle's C source, plants one mistake (a flipped sign,
+a dropped term, a wrong or transposed index, a disabled protection step),
+compiles the copy into a temporary library and runs a fast detector suite
+built only from independent checks (hand-derived golden vectors, the
+residual definition, an overflow case, arbitrary-precision brute force).
+The unmodified oracle must pass the suite; every mutant must fail it.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from evec_checks import (U, canonical_norms, column_groups, generalized_residuals,
+                         mp_canonical, mp_eigvec, standard_residuals)
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "hand_examples.json")
+
+MUTANTS = [
+    ("update_sign", "yr[r] -= Sc[r] * zr;", "yr[r] += Sc[r] * zr;"),
+    ("imag_update_dropped",
+     "for (int64_t r = 0; r < q; r++) yi[r] -= Sc[r] * zi;", ";"),
+    ("own_block_wrong_entry", "o[3] = w / b;", "o[3] = w / c;"),
+    ("protect_update_disabled",
+     "if (tau > (OMEGA - nu) / mu) return -1 - ((int64_t)ilogb(mu) + 1);",
+     "if (tau > (OMEGA - nu) / mu) return 0;"),
+    ("small_system_transposed",
+     "double sv = AT(P->S, P->lds, i0 + a, i0 + b);",
+     "double sv = AT(P->S, P->lds, i0 + b, i0 + a);"),
+    ("canonical_exponent_sign", "    e -= tcan;\n            if (Q) {",
+     "    e += tcan;\n            if (Q) {"),
+    ("backtransform_transposed", "x[r] += Qc[r] * v;", "x[r] += AT(Q, ldq, j, r) * v;"),
+    ("division_scale_not_applied",
+     "zr[i] = ldexp(hr[i], (int)(kr + s));", "zr[i] = ldexp(hr[i], (int)(kr));"),
+    ("generalized_alpha_sign",
+     "yr[r] -= sv * zr - tr * (ar * zr - ai * zi);",
+     "yr[r] -= sv * zr + tr * (ar * zr - ai * zi);"),
+    ("generalized_cross_term",
+     "if (cplx) yi[r] -= sv * zi - tr * (ar * zi + ai * zr);",
+     "if (cplx) yi[r] -= sv * zi - tr * (ar * zi - ai * zr);"),
+    ("pivot_permutation_not_undone",
+     "hr[colp[0]] = w1r; hi[colp[0]] = w1i;\n        hr[colp[1]] = w2r; hi[colp[1]] = w2i;",
+     "hr[0] = w1r; hi[0] = w1i;\n        hr[1] = w2r; hi[1] = w2i;"),
+    ("eigenvalue_imag_sign", "lre[k] = a; lim[k] = w;", "lre[k] = a; lim[k] = -w;"),
+]
+
+
+def detector_failures(orc):
+    """Run the independent checks against one oracle build; return the names
+    of the checks that fail."""
+    fails = []
+
+    def check(name, fn):
+        try:
+            with np.errstate(all="ignore"):
+                ok = fn()
+        except Exception:  # a crash or a rejected input counts as a failure
+            ok = False
+        if not ok:
+            fails.append(name)
+
+    def golden():
+        for case in json.load(open(GOLDEN))["cases"]:
+            S = np.array(case["S"], dtype=np.float64)
+            X, e, lr, li = orc.standard(S)
+            for (j, pair), ref in zip(column_groups(li), case["eigen"]):
+                y_ref = np.array([complex(a, b) for a, b in ref["y"]])
+                y = np.ldexp(X[:, j], -int(e[j])).astype(complex)
+                if pair:
+                    y = y + 1j * np.ldexp(X[:, j + 1], -int(e[j]))
+                if not np.allclose(y, y_ref, rtol=0, atol=8 * U * np.abs(y_ref).max()):
+                    return False
+                lam = complex(*ref["lambda"])
+                if abs(complex(lr[j], li[j]) - lam) > 8 * U * abs(lam):
+                    return False
+        return True
+
+    T0, _ = workloads.config0_schur(96, seed=5)
+    Q0 = workloads.householder_orthogonal(96, seed=6)
+
+    def residual_std():
+        X, e, lr, li = orc.standard(T0)
+        if not np.isfinite(X).all():
+            return False
+        nr = canonical_norms(X, li)
+        return standard_residuals(T0, X, lr, li).max() <= 10 * 96 and nr.min() >= 1 and nr.max() < 2
+
+    def residual_backtransformed():
+        X, e, lr, li = orc.standard(T0, Q=Q0)
+        A = Q0 @ T0 @ Q0.T
+        return np.isfinite(X).all() and standard_residuals(A, X, lr, li).max() <= 10 * 96
+
+    def adversarial():
+        T, _ = workloads.adversarial_schur(128, seed=8)
+        X, e, lr, li = orc.standard(T)
+        return np.isfinite(X).all() and standard_residuals(T, X, lr, li).max() <= 10 * 128
+
+    def brute_force():
+        T, blocks = workloads.config0_schur(20, seed=9)
+        X, e, lr, li = orc.standard(T)
+        col = 0
+        for (p, sz) in blocks:
+            y, _ = mp_eigvec(T, p, sz)
+            xr, xi, emp = mp_canonical(y, sz == 2)
+            de = int(e[col]) - emp
+            if abs(de) > 1:
+                return False
+            err = np.abs(np.ldexp(X[:, col], -de) - xr)
+            if sz == 2:
+                err = err + np.abs(np.ldexp(X[:, col + 1], -de) - xi)
+            if err.max() > 1e-12 * np.max(np.abs(xr) + np.abs(xi)):
+                return False
+            col += sz
+        return True
+
+    def generalized():
+        S, T, _ = workloads.generalized_pair(80, seed=10)
+        Z = workloads.householder_orthogonal(80, seed=11)
+        X, e, ar, ai, be = orc.generalized(S, T, Z=Z)
+        # residual of the original pencil (Z S Z^T, Z T Z^T) for X = Z Y
+        A = Z @ S @ Z.T
+        B = Z @ T @ Z.T
+        return np.isfinite(X).all() and generalized_residuals(A, B, X, ar, ai, be).max() <= 10 * 80
+
+    check("golden", golden)
+    check("residual_std", residual_std)
+    check("residual_backtransformed", residual_backtransformed)
+    check("adversarial", adversarial)
+    check("brute_force", brute_force)
+    check("generalized", generalized)
+    return fails
+
+
+def test_unmodified_oracle_passes_detectors():
+    assert detector_failures(oracle.default()) == []
+
+
+@pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_mutant_is_caught(tmp_path, name, old, new):
+    src = open(oracle.source_path()).read()
+    assert src.count(old) == 1, f"mutation site for {name} not found exactly once"
+    mutated = tmp_path / f"mut_{name}.c"
+    mutated.write_text(src.replace(old, new))
+    lib = oracle.compile_library(str(mutated), str(tmp_path / f"libmut_{name}.so"))
+    fails = detector_failures(oracle.Oracle(lib))
+    assert fails, f"mutant {name} passed every pin"
