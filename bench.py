@@ -1,0 +1,372 @@
+#!/usr/bin/env python
+"""Benchmark of the robust eigenvector path on one B300 (replicas across GPUs).
+
+Workload (one step = the whole path once): all eigenvectors of an n = 4096
+real Schur form drawn from the config-0 distribution (75% real 1x1 blocks,
+25% standardized 2x2 blocks, strictly upper part N(0, 1)), back-transformed
+by an orthogonal Q (product of 64 Householder reflectors), FP64 throughout.
+Inputs are seeded and synthetic; T, Q and X are 128 MiB each, larger than L2.
+
+Metric: eigenvector columns per second (and achieved FP64 TFLOPS with the
+algorithmic count F = sum_j [k_j^2 + 2 n (k_j + b_j)], k_j rows above the
+column's block, b_j its size).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (the plain column-by-column robust
+substitution) on the machine's host cores, each step a bounded random sample of
+the same workload's columns.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP64 DFMA rate per SM and clock measured on this B300 (fp64 probe):
+# 1.126 TFLOP/s at 1935 MHz over 148 SMs = 3.93 flop/clk/SM, i.e. 2 DFMA/clk/SM.
+FP64_FLOP_PER_CLK_PER_SM = 4.0
+N_SMS = 148
+
+REASON_BITS = {
+    0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap",
+    0x8: "hw_slowdown", 0x10: "sync_boost", 0x20: "sw_thermal_slowdown",
+    0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown",
+    0x100: "display_clock_setting",
+}
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=4096)
+    ap.add_argument("--tile", type=int, default=0)
+    ap.add_argument("--cpu-sample", type=int, default=1024,
+                    help="columns of the CPU-oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(n):
+    T, blocks = workloads.config0_schur(n, seed=workloads.SEED_BASE + 1)
+    Q = workloads.householder_orthogonal(n, seed=workloads.SEED_BASE + 101)
+    return T, blocks, Q
+
+
+def flop_counts(n, blocks, tile_start, with_q=True):
+    """Algorithmic FP64 flops: total per the method's definition, and the
+    parts done by the tile-update GEMMs and by the back-transformation."""
+    tile_start = np.asarray(tile_start)
+    total = 0.0
+    upd = 0.0
+    bt = 0.0
+    for p, sz in blocks:
+        k = p
+        for _ in range(sz):
+            total += k * k + (2.0 * n * (k + sz) if with_q else 0.0)
+            bt += 2.0 * n * (k + sz) if with_q else 0.0
+            # rows above the column's own tile are updated by the GEMMs
+            c = int(np.searchsorted(tile_start, p, side="right") - 1)
+            t0c = tile_start[c]
+            upd += 2.0 * t0c * (p + sz - t0c)
+            for s in range(1, c):
+                upd += 2.0 * tile_start[s] * (tile_start[s + 1] - tile_start[s])
+    return total, upd, bt
+
+
+def measured_peaks():
+    try:
+        return json.load(open(MEASURED))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id=None):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", "200"]
+        if gpu_id:
+            cmd += ["-i", gpu_id]
+        try:
+            self.p = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                      text=True)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except Exception:
+            self.p.kill()
+            out = ""
+        sm, smax, reasons = [], [], set()
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                act = int(f[4], 16)
+            except ValueError:
+                continue
+            for bit, name in REASON_BITS.items():
+                if act & bit and name != "gpu_idle":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(T, blocks, Q, sample_cols, seed=5):
+    """The oracle, as it stands, on a seeded random sample of the workload's
+    columns, on all host cores."""
+    import oracle
+    n = T.shape[0]
+    rng = np.random.default_rng(seed)
+    order = rng.permutation(len(blocks))
+    sel = np.zeros(n, np.uint8)
+    cols = 0
+    for b in order:
+        if cols >= sample_cols:
+            break
+        p, sz = blocks[b]
+        sel[p:p + sz] = 1
+        cols += sz
+    oracle.build()
+    t = time.perf_counter()
+    X, e, lr, li = oracle.standard(T, Q=Q, select=sel)
+    dt = time.perf_counter() - t
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    threads = int(os.environ.get("OMP_NUM_THREADS", cores))
+    return {"value": X.shape[1] / dt, "unit": "columns/s", "cores": threads, "kind": "oracle",
+            "columns": X.shape[1], "seconds": dt,
+            "sample": f"{X.shape[1]} randomly chosen columns (seed {seed}) of the n={n} "
+                      f"workload incl. back-transformation, {dt:.2f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    T, blocks, Q = workload(args.n)
+    per_step = max(16, args.cpu_sample // 4)
+    times, cols = [], []
+    for i in range(args.warmup + args.steps):
+        r = cpu_baseline(T, blocks, Q, per_step, seed=1000 + i)
+        if i >= args.warmup:
+            cols.append(r["columns"])
+            times.append(r["seconds"])
+    value = sum(cols) / sum(times)
+    cores = r["cores"]
+    line = {
+        "impl": "reference",
+        "metric": "eigvec columns/s (robust FP64 eigenvectors incl. back-transformation)",
+        "value": value, "unit": "columns/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"config-0 Schur form n={args.n} + Q, all columns (oracle samples)"},
+        "cpu_baseline": {"value": value, "unit": "columns/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{per_step} random columns per step of the n={args.n} "
+                                   "workload, on the host cores"},
+        "e2e": {"value": value, "unit": "columns/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import ctypes
+
+    import torch
+
+    import paper_2002_05024_b300 as ev
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    n = args.n
+    T, blocks, Q = workload(n)
+    m = sum(sz for _, sz in blocks)
+    d = np.ascontiguousarray(np.diagonal(T))
+    _, tile_start = ev.plan_query(d, np.ascontiguousarray(np.diagonal(T, -1)),
+                                  np.ascontiguousarray(np.diagonal(T, 1)), None, args.tile or 64)
+    F, F_upd, F_bt = flop_counts(n, blocks, tile_start)
+
+    dT = torch.from_numpy(T).to(dev)
+    dQ = torch.from_numpy(Q).to(dev)
+    X = torch.empty((m, n), dtype=torch.float64, device=dev).t()
+    e = torch.empty(m, dtype=torch.int32, device=dev)
+    lr = torch.empty(m, dtype=torch.float64, device=dev)
+    li = torch.empty(m, dtype=torch.float64, device=dev)
+    out = (X, e, lr, li)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        ev.standard(dT, dQ, tile=args.tile, out=out)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    ev.sync(local_rank)
+    h = ev.handle(local_rank)
+    h.profile(True)
+    h.profile_read()
+
+    gpu_id = None
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    sampler = ClockSampler(gpu_id) if rank == 0 else None
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        step()
+    t1.record(stream)
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    elapsed_ms = t0.elapsed_time(t1)
+    clocks = sampler.stop() if sampler else None
+    prof = h.profile_read()
+    h.profile(False)
+    ev.sync(local_rank)
+    if dist:
+        tt = torch.tensor([elapsed_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(tt.item())
+
+    ms_per_step = elapsed_ms / args.steps
+    value = world * m * args.steps / (elapsed_ms / 1e3)
+    tflops = world * F * args.steps / (elapsed_ms / 1e3) / 1e12
+
+    # roofline of the dominant kernel (largest share of event-timed time)
+    kernel, (kms, kn) = max(prof.items(), key=lambda kv: kv[1][0])
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2032.0))
+    fp64_peak = N_SMS * FP64_FLOP_PER_CLK_PER_SM * sm_max * 1e6 / 1e12
+    alg = {"backtransform": F_bt, "tile_update": F_upd}.get(kernel)
+    roofline = None
+    if alg is not None and kn:
+        per_launch = alg / (kn / args.steps)
+        achieved = per_launch / (kms / kn / 1e3) / 1e12
+        roofline = {"kernel": kernel, "bound": "alu", "achieved": achieved, "peak": fp64_peak,
+                    "unit": "TFLOP/s", "frac": achieved / fp64_peak, "traffic": None,
+                    "peak_source": "FP64 DFMA: 4 flop/clk/SM (measured) x 148 SMs x max SM clock"}
+    gpu_launches = sum(c for _, c in prof.values())
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    e2e = None
+    if not os.environ.get("EVEC_BENCH_NO_E2E"):
+        pin = lambda shape, dt: torch.empty(shape, dtype=dt, pin_memory=True).numpy()  # noqa: E731
+        hT = pin((n, n), torch.float64)
+        hT[...] = T.T          # row-major view of the column-major bytes
+        hQ = pin((n, n), torch.float64)
+        hQ[...] = Q.T
+        hX = pin((m, n), torch.float64)
+        hE = pin((m,), torch.int32)
+        hLr = pin((m,), torch.float64)
+        hLi = pin((m,), torch.float64)
+        opts = ev._opts(args.tile, False)
+        hh = ev.handle(local_rank)
+        P = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+
+        def host_step():
+            st = ev.lib().evec_standard_host(hh.ptr, n, P(hT), P(hQ), None, P(hX), P(hE),
+                                             P(hLr), P(hLi), ctypes.byref(opts))
+            if st:
+                raise ev.EvecError(st, "evec_standard_host")
+
+        for _ in range(args.warmup):
+            host_step()
+        if dist:
+            dist.barrier()
+        w0 = time.perf_counter()
+        for _ in range(args.steps):
+            host_step()
+        w = time.perf_counter() - w0
+        if dist:
+            tt = torch.tensor([w], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            w = float(tt.item())
+        e2e = {"value": world * m * args.steps / w, "unit": "columns/s",
+               "h2d_bytes_per_step": 2 * n * n * 8,
+               "d2h_bytes_per_step": n * m * 8 + m * 4 + 2 * m * 8}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(T, blocks, Q, args.cpu_sample)
+        cpu.pop("columns")
+        cpu.pop("seconds")
+    line = {
+        "metric": "eigvec columns/s (robust FP64 eigenvectors incl. back-transformation)",
+        "value": value, "unit": "columns/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"config-0 Schur form n={n} + Q (64 Householder reflectors), "
+                               f"all {m} columns, FP64",
+                   "n": n, "columns": m, "tile": args.tile or 64, "parallelism": "replicas",
+                   "l2": "inputs larger than L2 (T, Q, X 128 MiB each)"},
+        "tflops_fp64": tflops,
+        "flops_per_step": F,
+        "roofline": roofline,
+        "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+        "gpu_launches": gpu_launches,
+        "clocks": clocks,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,184 @@
+/*
+ * evec.h -- robust eigenvectors of real Schur forms on one GPU.
+ *
+ * The operation (Sec. 2, Eq. evec_solve and Eq. evec_backtransform of
+ * "Task-based, GPU-accelerated and Robust Library for Solving Dense
+ * Nonsymmetric Eigenvalue Problems"): given a real upper quasi-triangular
+ * Schur form T (1x1 diagonal blocks for real eigenvalues, 2x2 blocks for
+ * complex-conjugate pairs) and optionally its orthogonal factor Q, solve
+ * (T - lambda_i I) y_i = 0 by backsubstitution for every selected eigenvalue
+ * and return x_i = Q y_i.  The solve is robust (Sec. 3.4): no intermediate
+ * or final value overflows, because every tile segment of every column
+ * carries an integer power-of-two scale factor (the augmented tile
+ * <alpha, X> represents y_j = x_j / alpha_j) and every tile update
+ * Y <- Y - T X is preceded by a scaling that bounds its result.
+ *
+ * Conventions shared by all entry points
+ * --------------------------------------
+ * - Matrices are FP64, column-major, with a leading dimension (ld >= n).
+ *   Matrix arguments are DEVICE pointers unless the name ends in _host.
+ *   Entries of T below the first subdiagonal are never read.
+ * - A 2x2 diagonal block must be standardized: equal diagonal entries a and
+ *   off-diagonal entries b, c of opposite sign; its eigenvalues are
+ *   a +- i w, w = sqrt(|b|) sqrt(|c|).  Two consecutive nonzero
+ *   subdiagonal entries, or a non-standardized 2x2 block, is EVEC_ENOTSCHUR.
+ * - Every referenced entry must be finite (else EVEC_ENONFINITE) and of
+ *   magnitude <= 2^1000 (else EVEC_EINVAL).  2^1020 is the overflow
+ *   threshold of every intermediate bound.
+ * - select_host: HOST array of n bytes; eigenvalue i is selected when
+ *   select_host[i] != 0.  A 2x2 block is selected when either of its two
+ *   eigenvalues is.  NULL selects all eigenvalues.
+ * - Output columns follow the order of the diagonal blocks.  A real
+ *   eigenvalue gives one column; a selected 2x2 block gives two columns
+ *   (Re, Im) of the eigenvector for lambda = a + i w with w > 0 (the
+ *   conjugate eigenvalue has the conjugate vector).  m, the number of
+ *   output columns, is returned by evec_count.
+ * - Scaling: on return the true eigenvector is  X[:, j] * 2^(-scale_exp[j])
+ *   and X is canonical: max_i |X[i, j]| lies in [1, 2) (for a pair,
+ *   max_i |X[i, p]| + |X[i, p+1]| lies in [1, 2) and both columns share one
+ *   exponent).  scale_exp is int32 (the paper's 32-bit scale exponents).
+ *   Entries far below the column maximum may underflow to subnormal or zero
+ *   when the final consolidation (Sec. 3.4, post-processing) brings every
+ *   segment of a column to one common exponent.
+ * - The block part of each eigenvector is fixed: y_p = 1 for a 1x1 block at
+ *   p; for a pair, (y_p, y_p+1) = (1, i w / b) when |b| >= |c|, otherwise
+ *   (-w / c, i).  Rows below the block are zero before back-transformation.
+ * - Calls are asynchronous on the handle's stream.  Argument errors
+ *   (EVEC_EINVAL, EVEC_ENOTSCHUR found while planning) are returned
+ *   synchronously and nothing is launched.  Errors found on the device
+ *   (EVEC_ENONFINITE, EVEC_EINVAL for an entry above 2^1000) are reported
+ *   by evec_sync, which also returns the offending index.  There is no CPU
+ *   fallback: without a usable CUDA device every call returns EVEC_ECUDA.
+ * - Ownership: the caller owns every matrix and output buffer.  The handle
+ *   owns its workspace (working copy of Y when Q is given, per-segment
+ *   exponents and norms, the plan), grows it on demand and frees it in
+ *   evec_destroy.  One handle must not be used by two host threads at once.
+ */
+#ifndef EVEC_H
+#define EVEC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct evec_ctx *evec_handle;
+
+typedef enum {
+    EVEC_OK = 0,
+    EVEC_EINVAL = 1,     /* bad argument, or an entry above 2^1000 */
+    EVEC_ENOTSCHUR = 2,  /* not a (standardized) quasi-triangular Schur form */
+    EVEC_ENONFINITE = 3, /* NaN or Inf in a referenced entry */
+    EVEC_ENOMEM = 4,     /* device or host allocation failed */
+    EVEC_ECUDA = 5,      /* CUDA runtime error */
+    EVEC_ETIMEOUT = 6,   /* a bounded device-side wait gave up */
+    EVEC_ERESIDUAL = 7   /* reserved: residual gate failed */
+} evec_status;
+
+typedef enum {
+    EVEC_FP64 = 0 /* every operation in FP64 on the GPU */
+} evec_mode;
+
+typedef struct {
+    int mode;   /* evec_mode */
+    int tile;   /* tile size nb of the tiled solve, 16..128; 0 = default */
+    int check;  /* nonzero: synchronise at the end of the call and return
+                   the device status directly */
+} evec_opts;
+
+/* Create a handle on CUDA device `device` that launches on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).
+ * Errors: EVEC_EINVAL (h NULL or bad device), EVEC_ECUDA, EVEC_ENOMEM. */
+evec_status evec_create(evec_handle *h, int device, void *cuda_stream);
+
+/* Release the handle and its workspace (after synchronising its stream). */
+evec_status evec_destroy(evec_handle h);
+
+/* Change the stream later calls launch on. */
+evec_status evec_set_stream(evec_handle h, void *cuda_stream);
+
+/* Number of output columns m of a selection (2 per selected pair).  Reads
+ * the diagonal and the first sub- and super-diagonal of the device matrix T
+ * (synchronises the handle's stream).
+ * Errors: EVEC_EINVAL, EVEC_ENOTSCHUR, EVEC_ECUDA. */
+evec_status evec_count(evec_handle h, int64_t n, const double *T, int64_t ldt,
+                       const uint8_t *select_host, int64_t *m);
+
+/*
+ * Right eigenvectors of the quasi-triangular T (Eq. evec_solve), optionally
+ * back-transformed by the orthogonal Q (Eq. evec_backtransform; Q == NULL
+ * returns Y itself).  Device arrays:
+ *   T [ldt x n], Q [ldq x n] or NULL, X [ldx x m] output,
+ *   scale_exp [m] int32 output, lam_re / lam_im [m] FP64 outputs or NULL
+ *   (lam_im[j] = w, lam_im[j+1] = -w for a pair).
+ * X must not overlap T or Q.  opt may be NULL (defaults).
+ * Errors (synchronous): EVEC_EINVAL, EVEC_ENOTSCHUR, EVEC_ENOMEM,
+ * EVEC_ECUDA; (at evec_sync) EVEC_ENONFINITE, EVEC_EINVAL.
+ */
+evec_status evec_standard(evec_handle h, int64_t n, const double *T, int64_t ldt,
+                          const double *Q, int64_t ldq, const uint8_t *select_host,
+                          double *X, int64_t ldx, int32_t *scale_exp,
+                          double *lam_re, double *lam_im, const evec_opts *opt);
+
+/*
+ * The same computation with HOST buffers (column-major, ld = n): copies
+ * T (and Q) to the device, computes, copies X [n x m], scale_exp [m],
+ * lam_re [m] and lam_im [m] back (each output may be NULL) and
+ * synchronises.  Page-locked host memory gives the fastest copies.  Device
+ * errors are returned directly.
+ */
+evec_status evec_standard_host(evec_handle h, int64_t n, const double *T_host,
+                               const double *Q_host, const uint8_t *select_host,
+                               double *X_host, int32_t *scale_exp_host,
+                               double *lam_re_host, double *lam_im_host,
+                               const evec_opts *opt);
+
+/* Host-only planning query (no GPU needed).  From the diagonal, the first
+ * subdiagonal and the first superdiagonal of T (host arrays of n, n-1 and
+ * n-1 values) compute the number of output columns m of a selection and
+ * the tile boundaries used for tile size nb (16..128): tiles of nb rows,
+ * one row shorter where a boundary would split a 2x2 block.  tile_start
+ * (may be NULL) receives ntiles + 1 entries and must hold n / (nb - 1) + 2.
+ * Errors: EVEC_EINVAL (bad argument or an entry above 2^1000),
+ * EVEC_ENOTSCHUR, EVEC_ENONFINITE (*bad_index: linear index with ld = n). */
+evec_status evec_plan_query(int64_t n, const double *diag, const double *sub,
+                            const double *sup, const uint8_t *select_host, int nb,
+                            int64_t *m, int32_t *ntiles, int32_t *tile_start,
+                            int64_t *bad_index);
+
+/* Wait for the handle's stream; return the first device-detected error of
+ * the calls since the previous evec_sync (and its linear index i + j*ld into
+ * the offending matrix when bad_index is non-NULL), then clear it. */
+evec_status evec_sync(evec_handle h, int64_t *bad_index);
+
+/* Kernel classes reported by evec_profile_read (array index). */
+enum {
+    EVEC_K_GATHER = 0,       /* diagonal gather for the plan */
+    EVEC_K_NORMS = 1,        /* tile norms + input validation */
+    EVEC_K_DIAG_SOLVE = 2,   /* robust diagonal-tile solves + decisions */
+    EVEC_K_TILE_UPDATE = 3,  /* FP64 off-diagonal tile updates */
+    EVEC_K_FINALIZE = 4,     /* consolidation + canonical form */
+    EVEC_K_BACKTRANSFORM = 5,/* X = Q Y */
+    EVEC_K_CANONICALIZE = 6, /* canonical form after Q */
+    EVEC_K_COUNT = 7
+};
+
+/* Enable (1) or disable (0) per-kernel timing: while enabled, every kernel
+ * launch of the handle is bracketed by CUDA events on the handle's stream. */
+evec_status evec_profile(evec_handle h, int enable);
+
+/* Synchronise the handle's stream and return, per kernel class, the summed
+ * event-timed milliseconds and the number of launches since the previous
+ * read (arrays of nk entries, nk <= EVEC_K_COUNT; either may be NULL); then
+ * reset the counters. */
+evec_status evec_profile_read(evec_handle h, double *ms, int64_t *launches, int nk);
+
+/* Static, human-readable name of a status code. */
+const char *evec_strerror(evec_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EVEC_H */

@@ -1,0 +1,289 @@
+"""Robust eigenvectors of real Schur forms on one B300 GPU.
+
+A thin ctypes binding over the C ABI in ``include/evec.h`` (library
+``_lib/libevec.so``, built by ``paper_2002_05024_b300.build``).  Every step of
+the computation runs in the library's CUDA kernels; this module only
+marshals arguments.  PyTorch supplies device memory and the current stream.
+
+Matrices are float64 CUDA tensors in column-major layout: shape (n, n) with
+strides (1, ld), ld >= n -- e.g. ``torch.from_numpy(np.asfortranarray(A)).cuda()``
+or ``colmajor(t)``.  Results follow the library's conventions: the true
+eigenvector j is ``X[:, j] * 2**(-scale_exp[j])`` with max |X[:, j]| in
+[1, 2) (a complex pair occupies two columns (Re, Im) and shares one
+exponent; its norm is max |re| + |im|).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libevec.so")
+
+STATUS = {0: "EVEC_OK", 1: "EVEC_EINVAL", 2: "EVEC_ENOTSCHUR", 3: "EVEC_ENONFINITE",
+          4: "EVEC_ENOMEM", 5: "EVEC_ECUDA", 6: "EVEC_ETIMEOUT", 7: "EVEC_ERESIDUAL"}
+EVEC_OK, EVEC_EINVAL, EVEC_ENOTSCHUR, EVEC_ENONFINITE = 0, 1, 2, 3
+EVEC_ENOMEM, EVEC_ECUDA, EVEC_ETIMEOUT, EVEC_ERESIDUAL = 4, 5, 6, 7
+KERNELS = ("gather", "tile_norms", "diag_solve", "tile_update", "finalize",
+           "backtransform", "canonicalize")
+
+
+class EvecError(RuntimeError):
+    def __init__(self, status: int, where: str, bad: int = -1):
+        msg = f"{where}: {STATUS.get(status, status)}"
+        if bad >= 0:
+            msg += f" (index {bad})"
+        super().__init__(msg)
+        self.status = status
+        self.bad = bad
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int), ("tile", ctypes.c_int), ("check", ctypes.c_int)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded C library; raises if it has not been built (there is no
+    fallback implementation)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library missing: {LIB_PATH}; run "
+                               "`python -m paper_2002_05024_b300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        i64, p, i32 = ctypes.c_int64, ctypes.c_void_p, ctypes.c_int32
+        L.evec_create.argtypes = [ctypes.POINTER(p), ctypes.c_int, p]
+        L.evec_destroy.argtypes = [p]
+        L.evec_set_stream.argtypes = [p, p]
+        L.evec_count.argtypes = [p, i64, p, i64, p, ctypes.POINTER(i64)]
+        L.evec_standard.argtypes = [p, i64, p, i64, p, i64, p, p, i64, p, p, p,
+                                    ctypes.POINTER(_Opts)]
+        L.evec_standard_host.argtypes = [p, i64, p, p, p, p, p, p, p, ctypes.POINTER(_Opts)]
+        L.evec_sync.argtypes = [p, ctypes.POINTER(i64)]
+        L.evec_plan_query.argtypes = [i64, p, p, p, p, ctypes.c_int, ctypes.POINTER(i64),
+                                      ctypes.POINTER(i32), p, ctypes.POINTER(i64)]
+        L.evec_profile.argtypes = [p, ctypes.c_int]
+        L.evec_profile_read.argtypes = [p, p, p, ctypes.c_int]
+        L.evec_strerror.argtypes = [ctypes.c_int]
+        L.evec_strerror.restype = ctypes.c_char_p
+        for f in ("evec_create", "evec_destroy", "evec_set_stream", "evec_count",
+                  "evec_standard", "evec_standard_host", "evec_sync", "evec_plan_query",
+                  "evec_profile", "evec_profile_read"):
+            getattr(L, f).restype = ctypes.c_int
+        _lib = L
+        return L
+
+
+def strerror(status: int) -> str:
+    return lib().evec_strerror(int(status)).decode()
+
+
+def _check(status: int, where: str, bad: int = -1):
+    if status != EVEC_OK:
+        raise EvecError(status, where, bad)
+
+
+def _np_ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _mask(select, n):
+    if select is None:
+        return None
+    if hasattr(select, "detach"):
+        select = select.detach().cpu().numpy()
+    s = np.ascontiguousarray(select, dtype=np.uint8)
+    if s.shape != (n,):
+        raise ValueError("selection mask must have n entries")
+    return s
+
+
+def _opts(tile, check):
+    return _Opts(0, int(tile), 1 if check else 0)
+
+
+# ---------------------------------------------------------------------------
+# handles: one per device, bound to the caller's current stream at each call
+# ---------------------------------------------------------------------------
+class Handle:
+    def __init__(self, device: int = 0, stream=None):
+        self._h = ctypes.c_void_p()
+        _check(lib().evec_create(ctypes.byref(self._h), int(device),
+                                 ctypes.c_void_p(stream or 0)), "evec_create")
+        self.device = int(device)
+
+    @property
+    def ptr(self):
+        return self._h
+
+    def set_stream(self, stream):
+        _check(lib().evec_set_stream(self._h, ctypes.c_void_p(stream or 0)), "evec_set_stream")
+
+    def sync(self):
+        bad = ctypes.c_int64(-1)
+        st = lib().evec_sync(self._h, ctypes.byref(bad))
+        _check(st, "evec_sync", bad.value)
+
+    def profile(self, enable: bool):
+        _check(lib().evec_profile(self._h, 1 if enable else 0), "evec_profile")
+
+    def profile_read(self):
+        """{kernel class: (milliseconds, launches)} since the last read."""
+        ms = np.zeros(len(KERNELS))
+        cnt = np.zeros(len(KERNELS), dtype=np.int64)
+        _check(lib().evec_profile_read(self._h, _np_ptr(ms), _np_ptr(cnt), len(KERNELS)),
+               "evec_profile_read")
+        return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(KERNELS)}
+
+    def close(self):
+        if self._h:
+            lib().evec_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_handles: dict = {}
+
+
+def handle(device=None) -> Handle:
+    import torch
+    dev = torch.cuda.current_device() if device is None else int(device)
+    h = _handles.get(dev)
+    if h is None:
+        h = Handle(dev)
+        _handles[dev] = h
+    h.set_stream(torch.cuda.current_stream(dev).cuda_stream)
+    return h
+
+
+def colmajor(t):
+    """Column-major copy (strides (1, n)) of a 2-D tensor."""
+    return t.t().contiguous().t()
+
+
+def _check_colmajor(t, name, n=None):
+    import torch
+    if t.dtype != torch.float64 or not t.is_cuda or t.dim() != 2:
+        raise ValueError(f"{name} must be a float64 CUDA matrix")
+    rows, cols = t.shape
+    if n is not None and (rows != n or cols != n):
+        raise ValueError(f"{name} must be {n} x {n}")
+    if rows > 1 and t.stride(0) != 1:
+        raise ValueError(f"{name} must be column-major (stride(0) == 1); use colmajor()")
+    ld = t.stride(1) if cols > 1 else max(rows, 1)
+    if ld < rows:
+        raise ValueError(f"{name}: leading dimension below the row count")
+    return ld
+
+
+# ---------------------------------------------------------------------------
+# public functions
+# ---------------------------------------------------------------------------
+def plan_query(diag, sub, sup, select=None, tile: int = 64):
+    """Host-only: number of output columns and tile boundaries for T's
+    diagonal / subdiagonal / superdiagonal (numpy arrays)."""
+    d = np.ascontiguousarray(diag, dtype=np.float64)
+    n = d.shape[0]
+    s = np.ascontiguousarray(sub, dtype=np.float64)
+    u = np.ascontiguousarray(sup, dtype=np.float64)
+    sel = _mask(select, n)
+    m = ctypes.c_int64(0)
+    nt = ctypes.c_int32(0)
+    starts = np.zeros(n // max(tile - 1, 1) + 3, dtype=np.int32)
+    bad = ctypes.c_int64(-1)
+    st = lib().evec_plan_query(n, _np_ptr(d), _np_ptr(s), _np_ptr(u), _np_ptr(sel), int(tile),
+                               ctypes.byref(m), ctypes.byref(nt), _np_ptr(starts),
+                               ctypes.byref(bad))
+    _check(st, "evec_plan_query", bad.value)
+    return int(m.value), starts[: nt.value + 1].copy()
+
+
+def count(T, select=None) -> int:
+    ldt = _check_colmajor(T, "T")
+    n = T.shape[0]
+    sel = _mask(select, n)
+    m = ctypes.c_int64(0)
+    h = handle(T.device.index)
+    _check(lib().evec_count(h.ptr, n, T.data_ptr(), ldt, _np_ptr(sel), ctypes.byref(m)),
+           "evec_count")
+    return int(m.value)
+
+
+def standard(T, Q=None, select=None, tile: int = 0, check: bool = False, out=None):
+    """Eigenvectors of the quasi-triangular T (optionally X = Q Y).
+
+    Returns (X, scale_exp, lam_re, lam_im) as CUDA tensors; X is (n, m)
+    column-major.  The call is asynchronous on the current stream; device
+    detected input errors surface at ``sync()`` (or immediately with
+    check=True)."""
+    import torch
+    n = T.shape[0]
+    ldt = _check_colmajor(T, "T", n)
+    ldq = _check_colmajor(Q, "Q", n) if Q is not None else max(n, 1)
+    sel = _mask(select, n)
+    dev = T.device
+    h = handle(dev.index)
+    m = count(T, sel) if n else 0
+    if out is not None:
+        X, e, lr, li = out
+    else:
+        X = torch.empty((m, n), dtype=torch.float64, device=dev).t()
+        e = torch.empty(m, dtype=torch.int32, device=dev)
+        lr = torch.empty(m, dtype=torch.float64, device=dev)
+        li = torch.empty(m, dtype=torch.float64, device=dev)
+    ldx = X.stride(1) if m > 1 else max(n, 1)
+    if m == 0:
+        return X, e, lr, li
+    opts = _opts(tile, False)
+    st = lib().evec_standard(h.ptr, n, T.data_ptr(), ldt, Q.data_ptr() if Q is not None else None,
+                             ldq, _np_ptr(sel), X.data_ptr(), ldx, e.data_ptr(), lr.data_ptr(),
+                             li.data_ptr(), ctypes.byref(opts))
+    _check(st, "evec_standard")
+    if check:
+        h.sync()
+    return X, e, lr, li
+
+
+def standard_host(T, Q=None, select=None, tile: int = 0, device: int = 0):
+    """The same computation from host numpy arrays (column-major float64);
+    copies in, computes, copies out.  Returns numpy arrays."""
+    Tf = np.asfortranarray(T, dtype=np.float64)
+    n = Tf.shape[0]
+    Qf = None if Q is None else np.asfortranarray(Q, dtype=np.float64)
+    sel = _mask(select, n)
+    d = np.ascontiguousarray(np.diagonal(Tf))
+    sub = np.ascontiguousarray(np.diagonal(Tf, -1))
+    sup = np.ascontiguousarray(np.diagonal(Tf, 1))
+    m, _ = plan_query(d, sub, sup, sel, tile or 64) if n else (0, None)
+    X = np.zeros((n, m), dtype=np.float64, order="F")
+    e = np.zeros(m, dtype=np.int32)
+    lr = np.zeros(m)
+    li = np.zeros(m)
+    import torch
+    h = handle(device)
+    h.set_stream(torch.cuda.current_stream(device).cuda_stream)
+    opts = _opts(tile, False)
+    st = lib().evec_standard_host(h.ptr, n, _np_ptr(Tf), _np_ptr(Qf), _np_ptr(sel), _np_ptr(X),
+                                  _np_ptr(e), _np_ptr(lr), _np_ptr(li), ctypes.byref(opts))
+    _check(st, "evec_standard_host")
+    return X, e, lr, li
+
+
+def sync(device=None):
+    handle(device).sync()

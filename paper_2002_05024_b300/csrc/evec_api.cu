@@ -1,0 +1,622 @@
+// evec_api.cu -- the C ABI of include/evec.h: planning on the host, workspace
+// ownership, and the launch sequence of the tiled robust solve.
+//
+// Launch sequence of evec_standard (all on the handle's stream):
+//   gather diagonals -> (host) plan -> tile norms + input validation
+//   for s = N-1 .. 0:  diag_solve(s)  [+ decisions for tiles r < s]
+//                      tile_update(s) [Y_r -= T_rs X_s for all r < s]
+//   finalize (consolidate segments, canonical form, zeros below the block)
+//   [Q given]  back-transform X = Q Y, re-canonicalise
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "../../include/evec.h"
+#include "evec_internal.cuh"
+
+namespace evec {
+
+// launchers defined in the kernel files
+void launch_gather_diagonals(const double *T, int64_t ldt, int64_t n, double *out,
+                             cudaStream_t st);
+void launch_tile_norms(const double *T, int64_t ldt, const Plan &p, double *tau,
+                       double *blk_tau, DevStatus *status, cudaStream_t st);
+void launch_diag_solve(int s, const double *T, int64_t ldt, const Plan &p,
+                       const int32_t *tile_start_h, const int32_t *tile_unit_h,
+                       const double *tau, const double *blk_tau, double *Y, int64_t ldy,
+                       int32_t *seg_e, double *seg_nu, int32_t *seg_dx, int32_t *seg_dy,
+                       cudaStream_t st);
+void launch_tile_update(int s, const double *T, int64_t ldt, const Plan &p, int max_tile,
+                        const int32_t *tile_col_h, double *Y, int64_t ldy,
+                        const int32_t *seg_dx, const int32_t *seg_dy, double *seg_nu,
+                        cudaStream_t st);
+void launch_finalize(const Plan &p, double *Y, int64_t ldy, const int32_t *seg_e,
+                     int32_t *scale_exp, cudaStream_t st);
+void launch_backtransform(const double *Q, int64_t ldq, const Plan &p, const double *Y,
+                          int64_t ldy, double *X, int64_t ldx, cudaStream_t st);
+void launch_canonicalize(const Plan &p, double *X, int64_t ldx, int32_t *scale_exp,
+                         cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// host plan
+// ---------------------------------------------------------------------------
+struct HostPlan {
+    int64_t n = 0, m = 0;
+    int nb = 0, max_tile = 0;
+    std::vector<int32_t> tile_start, tile_blk, tile_unit, tile_col;
+    std::vector<int32_t> blk_start, unit_col, unit_blk, unit_tile, col_unit;
+    std::vector<int8_t> blk_size;
+    std::vector<double> unit_lam, unit_own, col_lam_re, col_lam_im;
+};
+
+static evec_status check_value(double v, int64_t idx, int64_t *bad) {
+    if (!isfinite(v)) { if (bad) *bad = idx; return EVEC_ENONFINITE; }
+    if (fabs(v) > kInputMax) { if (bad) *bad = idx; return EVEC_EINVAL; }
+    return EVEC_OK;
+}
+
+// Block scan (Sec. 2: 1x1 and 2x2 diagonal blocks), eigenvalues, tiles whose
+// boundaries never split a 2x2 block, and the unit / column maps of the
+// selection.  diag[n], sub[n-1] (T[i+1, i]), sup[n-1] (T[i, i+1]).
+// Linear indices in *bad refer to a column-major matrix with ld = ld_report.
+static evec_status build_plan(int64_t n, const double *diag, const double *sub,
+                              const double *sup, const uint8_t *select, int nb,
+                              int64_t ld_report, HostPlan &P, int64_t *bad) {
+    P = HostPlan();
+    P.n = n;
+    P.nb = nb;
+    for (int64_t i = 0; i < n; i++) {
+        evec_status st = check_value(diag[i], i + i * ld_report, bad);
+        if (st) return st;
+        if (i + 1 < n) {
+            st = check_value(sub[i], (i + 1) + i * ld_report, bad);
+            if (st) return st;
+            st = check_value(sup[i], i + (i + 1) * ld_report, bad);
+            if (st) return st;
+        }
+    }
+    // blocks
+    std::vector<int8_t> in_pair_second(n, 0);
+    for (int64_t i = 0; i < n;) {
+        if (i + 1 < n && sub[i] != 0.0) {
+            if (i + 2 < n && sub[i + 1] != 0.0) { if (bad) *bad = i + 1; return EVEC_ENOTSCHUR; }
+            const double b = sup[i], c = sub[i];
+            if (diag[i] != diag[i + 1] || !((b > 0.0 && c < 0.0) || (b < 0.0 && c > 0.0))) {
+                if (bad) *bad = i;
+                return EVEC_ENOTSCHUR;
+            }
+            P.blk_start.push_back((int32_t)i);
+            P.blk_size.push_back(2);
+            in_pair_second[i + 1] = 1;
+            i += 2;
+        } else {
+            P.blk_start.push_back((int32_t)i);
+            P.blk_size.push_back(1);
+            i += 1;
+        }
+    }
+    const int64_t nblk = (int64_t)P.blk_start.size();
+    // tiles: greedy, nb rows, one row shorter where the boundary would split a pair
+    P.tile_start.push_back(0);
+    while (P.tile_start.back() < n) {
+        int64_t b = P.tile_start.back() + nb;
+        if (b >= n) b = n;
+        else if (in_pair_second[b]) b -= 1;
+        P.tile_start.push_back((int32_t)b);
+    }
+    const int N = (int)P.tile_start.size() - 1;
+    P.max_tile = 0;
+    for (int t = 0; t < N; t++)
+        P.max_tile = std::max(P.max_tile, P.tile_start[t + 1] - P.tile_start[t]);
+    // blocks per tile (blocks are in row order and never straddle a boundary)
+    P.tile_blk.assign(N + 1, 0);
+    {
+        int t = 0;
+        for (int64_t k = 0; k < nblk; k++) {
+            while (P.blk_start[k] >= P.tile_start[t + 1]) { t++; P.tile_blk[t] = (int32_t)k; }
+        }
+        for (int tt = t + 1; tt <= N; tt++) P.tile_blk[tt] = (int32_t)nblk;
+        // tiles with no block cannot occur (every row belongs to a block)
+    }
+    // units in block order
+    P.tile_unit.assign(N + 1, 0);
+    P.tile_col.assign(N + 1, 0);
+    int64_t col = 0;
+    int t = 0;
+    for (int64_t k = 0; k < nblk; k++) {
+        while (P.blk_start[k] >= P.tile_start[t + 1]) {
+            t++;
+            P.tile_unit[t] = (int32_t)P.unit_col.size();
+            P.tile_col[t] = (int32_t)col;
+        }
+        const int64_t p = P.blk_start[k];
+        const int bs = P.blk_size[k];
+        const bool sel = select == nullptr || select[p] || (bs == 2 && select[p + 1]);
+        if (!sel) continue;
+        const int32_t u = (int32_t)P.unit_col.size();
+        P.unit_col.push_back((int32_t)col);
+        P.unit_blk.push_back((int32_t)k);
+        P.unit_tile.push_back(t);
+        if (bs == 1) {
+            P.unit_lam.push_back(diag[p]);
+            P.unit_lam.push_back(0.0);
+            P.unit_own.insert(P.unit_own.end(), {1.0, 0.0, 0.0, 0.0});
+            P.col_unit.push_back(u);
+            P.col_lam_re.push_back(diag[p]);
+            P.col_lam_im.push_back(0.0);
+        } else {
+            const double a = diag[p], b = sup[p], c = sub[p];
+            const double w = sqrt(fabs(b)) * sqrt(fabs(c));
+            P.unit_lam.push_back(a);
+            P.unit_lam.push_back(w);
+            // null vector of [[-i w, b], [c, -i w]]: (1, i w / b) or (-w / c, i)
+            if (fabs(b) >= fabs(c)) P.unit_own.insert(P.unit_own.end(), {1.0, 0.0, 0.0, w / b});
+            else P.unit_own.insert(P.unit_own.end(), {-w / c, 0.0, 0.0, 1.0});
+            P.col_unit.push_back(u);
+            P.col_unit.push_back(u);
+            P.col_lam_re.push_back(a);
+            P.col_lam_re.push_back(a);
+            P.col_lam_im.push_back(w);
+            P.col_lam_im.push_back(-w);
+        }
+        col += bs;
+    }
+    for (int tt = t + 1; tt <= N; tt++) {
+        P.tile_unit[tt] = (int32_t)P.unit_col.size();
+        P.tile_col[tt] = (int32_t)col;
+    }
+    P.m = col;
+    return EVEC_OK;
+}
+
+}  // namespace evec
+
+using namespace evec;
+
+// ---------------------------------------------------------------------------
+// handle
+// ---------------------------------------------------------------------------
+struct evec_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    // device workspace
+    double *diag_d = nullptr; size_t diag_cap = 0;
+    unsigned char *plan_d = nullptr; size_t plan_cap = 0;
+    double *Y = nullptr; size_t Y_cap = 0;
+    int32_t *seg_e = nullptr, *seg_dx = nullptr, *seg_dy = nullptr; size_t segi_cap[3] = {0, 0, 0};
+    double *seg_nu = nullptr; size_t segn_cap = 0;
+    double *tau = nullptr; size_t tau_cap = 0;
+    double *blk_tau = nullptr; size_t blk_tau_cap = 0;
+    DevStatus *status_d = nullptr;
+    // host-buffer entry point
+    double *hT = nullptr, *hQ = nullptr, *hX = nullptr; size_t hT_cap = 0, hQ_cap = 0, hX_cap = 0;
+    int32_t *hE = nullptr; size_t hE_cap = 0;
+    double *hL = nullptr; size_t hL_cap = 0;
+    // pinned host buffers
+    double *diag_h = nullptr; size_t diag_h_cap = 0;
+    unsigned char *plan_h = nullptr; size_t plan_h_cap = 0;
+    DevStatus *status_h = nullptr;
+    HostPlan plan;
+    // per-kernel event timing
+    struct Timed {
+        int kind;
+        cudaEvent_t a, b;
+    };
+    bool profiling = false;
+    std::vector<Timed> live;
+    std::vector<cudaEvent_t> spare;
+    double prof_ms[EVEC_K_COUNT] = {0};
+    int64_t prof_n[EVEC_K_COUNT] = {0};
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) { cudaGetLastError(); prev = -1; }
+        ok = cudaSetDevice(dev) == cudaSuccess;
+        if (!ok) cudaGetLastError();
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+template <class T>
+evec_status grow_device(T **p, size_t *cap, size_t count) {
+    if (count <= *cap && *p) return EVEC_OK;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    if (count == 0) count = 1;
+    if (cudaMalloc((void **)p, count * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return EVEC_ENOMEM;
+    }
+    *cap = count;
+    return EVEC_OK;
+}
+
+template <class T>
+evec_status grow_host(T **p, size_t *cap, size_t count) {
+    if (count <= *cap && *p) return EVEC_OK;
+    if (*p) cudaFreeHost(*p);
+    *p = nullptr;
+    *cap = 0;
+    if (count == 0) count = 1;
+    if (cudaMallocHost((void **)p, count * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return EVEC_ENOMEM;
+    }
+    *cap = count;
+    return EVEC_OK;
+}
+
+evec_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return EVEC_OK;
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? EVEC_ENOMEM : EVEC_ECUDA;
+}
+
+#define EVEC_TRY(x)                          \
+    do {                                     \
+        evec_status _s = (x);                \
+        if (_s != EVEC_OK) return _s;        \
+    } while (0)
+#define EVEC_CUDA(x) EVEC_TRY(cuda_status(x))
+
+int resolve_tile(const evec_opts *opt) {
+    int nb = (opt && opt->tile) ? opt->tile : 64;
+    return nb;
+}
+
+cudaEvent_t take_event(evec_handle h) {
+    if (!h->spare.empty()) {
+        cudaEvent_t e = h->spare.back();
+        h->spare.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+    return e;
+}
+
+// Run one launch, bracketed by events when the handle is profiling.
+template <class F>
+void timed(evec_handle h, int kind, F &&launch) {
+    if (!h->profiling) { launch(); return; }
+    cudaEvent_t a = take_event(h), b = take_event(h);
+    if (!a || !b) { launch(); return; }
+    cudaEventRecord(a, h->stream);
+    launch();
+    cudaEventRecord(b, h->stream);
+    h->live.push_back({kind, a, b});
+}
+
+// Read T's three central diagonals and build the host plan.
+evec_status plan_device_matrix(evec_handle h, int64_t n, const double *T, int64_t ldt,
+                               const uint8_t *select, int nb, int64_t *bad) {
+    const size_t cnt = (size_t)(3 * n > 2 ? 3 * n - 2 : 1);
+    EVEC_TRY(grow_device(&h->diag_d, &h->diag_cap, cnt));
+    EVEC_TRY(grow_host(&h->diag_h, &h->diag_h_cap, cnt));
+    timed(h, EVEC_K_GATHER, [&] { launch_gather_diagonals(T, ldt, n, h->diag_d, h->stream); });
+    EVEC_CUDA(cudaGetLastError());
+    EVEC_CUDA(cudaMemcpyAsync(h->diag_h, h->diag_d, cnt * sizeof(double),
+                              cudaMemcpyDeviceToHost, h->stream));
+    EVEC_CUDA(cudaStreamSynchronize(h->stream));
+    const double *d = h->diag_h;
+    return build_plan(n, d, d + n, d + 2 * n - 1, select, nb, ldt, h->plan, bad);
+}
+
+// Pack the host plan into one pinned buffer, copy it to the device, and fill
+// the device-pointer view.
+evec_status upload_plan(evec_handle h, Plan &dp) {
+    const HostPlan &P = h->plan;
+    const size_t N1 = P.tile_start.size();
+    const size_t nd = P.unit_lam.size() + P.unit_own.size() + P.col_lam_re.size() + P.col_lam_im.size();
+    const size_t ni = 4 * N1 + P.blk_start.size() + P.unit_col.size() + P.unit_blk.size() +
+                      P.unit_tile.size() + P.col_unit.size();
+    const size_t bytes = nd * 8 + ni * 4 + P.blk_size.size() + 64;
+    EVEC_TRY(grow_host(&h->plan_h, &h->plan_h_cap, bytes));
+    EVEC_TRY(grow_device(&h->plan_d, &h->plan_cap, bytes));
+    size_t off = 0;
+    auto put = [&](const void *src, size_t nbytes, size_t align) -> const void * {
+        off = (off + align - 1) / align * align;
+        if (nbytes) memcpy(h->plan_h + off, src, nbytes);
+        const void *dev = h->plan_d + off;
+        off += nbytes;
+        return dev;
+    };
+    dp.n = P.n;
+    dp.m = P.m;
+    dp.ntiles = (int32_t)(N1 - 1);
+    dp.nblk = (int32_t)P.blk_start.size();
+    dp.nunits = (int32_t)P.unit_col.size();
+    dp.nb = P.nb;
+    dp.unit_lam = (const double *)put(P.unit_lam.data(), P.unit_lam.size() * 8, 8);
+    dp.unit_own = (const double *)put(P.unit_own.data(), P.unit_own.size() * 8, 8);
+    put(P.col_lam_re.data(), P.col_lam_re.size() * 8, 8);
+    put(P.col_lam_im.data(), P.col_lam_im.size() * 8, 8);
+    dp.tile_start = (const int32_t *)put(P.tile_start.data(), N1 * 4, 4);
+    dp.tile_blk = (const int32_t *)put(P.tile_blk.data(), N1 * 4, 4);
+    dp.tile_unit = (const int32_t *)put(P.tile_unit.data(), N1 * 4, 4);
+    dp.tile_col = (const int32_t *)put(P.tile_col.data(), N1 * 4, 4);
+    dp.blk_start = (const int32_t *)put(P.blk_start.data(), P.blk_start.size() * 4, 4);
+    dp.unit_col = (const int32_t *)put(P.unit_col.data(), P.unit_col.size() * 4, 4);
+    dp.unit_blk = (const int32_t *)put(P.unit_blk.data(), P.unit_blk.size() * 4, 4);
+    dp.unit_tile = (const int32_t *)put(P.unit_tile.data(), P.unit_tile.size() * 4, 4);
+    dp.col_unit = (const int32_t *)put(P.col_unit.data(), P.col_unit.size() * 4, 4);
+    dp.blk_size = (const int8_t *)put(P.blk_size.data(), P.blk_size.size(), 1);
+    EVEC_CUDA(cudaMemcpyAsync(h->plan_d, h->plan_h, off, cudaMemcpyHostToDevice, h->stream));
+    return EVEC_OK;
+}
+
+bool ld_ok(int64_t ld, int64_t n) { return ld >= (n > 0 ? n : 1); }
+
+
+
+}  // namespace
+
+extern "C" {
+
+const char *evec_strerror(evec_status s) {
+    switch (s) {
+        case EVEC_OK: return "EVEC_OK: success";
+        case EVEC_EINVAL: return "EVEC_EINVAL: invalid argument or entry above 2^1000";
+        case EVEC_ENOTSCHUR: return "EVEC_ENOTSCHUR: not a standardized quasi-triangular Schur form";
+        case EVEC_ENONFINITE: return "EVEC_ENONFINITE: NaN or Inf in the input";
+        case EVEC_ENOMEM: return "EVEC_ENOMEM: allocation failed";
+        case EVEC_ECUDA: return "EVEC_ECUDA: CUDA runtime error";
+        case EVEC_ETIMEOUT: return "EVEC_ETIMEOUT: bounded device wait gave up";
+        case EVEC_ERESIDUAL: return "EVEC_ERESIDUAL: residual gate failed";
+    }
+    return "unknown evec_status";
+}
+
+evec_status evec_plan_query(int64_t n, const double *diag, const double *sub, const double *sup,
+                            const uint8_t *select_host, int nb, int64_t *m, int32_t *ntiles,
+                            int32_t *tile_start, int64_t *bad_index) {
+    if (n < 0 || (n > 0 && (!diag || (n > 1 && (!sub || !sup)))) || nb < 16 || nb > kMaxTile)
+        return EVEC_EINVAL;
+    HostPlan P;
+    if (n == 0) {
+        if (m) *m = 0;
+        if (ntiles) *ntiles = 0;
+        if (tile_start) tile_start[0] = 0;
+        return EVEC_OK;
+    }
+    evec_status st = build_plan(n, diag, sub, sup, select_host, nb, n, P, bad_index);
+    if (st) return st;
+    if (m) *m = P.m;
+    if (ntiles) *ntiles = (int32_t)P.tile_start.size() - 1;
+    if (tile_start) memcpy(tile_start, P.tile_start.data(), P.tile_start.size() * 4);
+    return EVEC_OK;
+}
+
+evec_status evec_create(evec_handle *h, int device, void *cuda_stream) {
+    if (!h) return EVEC_EINVAL;
+    *h = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess) { cudaGetLastError(); return EVEC_ECUDA; }
+    if (device < 0 || device >= count) return EVEC_EINVAL;
+    DeviceGuard g(device);
+    if (!g.ok) return EVEC_ECUDA;
+    evec_ctx *c = new (std::nothrow) evec_ctx();
+    if (!c) return EVEC_ENOMEM;
+    c->device = device;
+    c->stream = (cudaStream_t)cuda_stream;
+    if (cudaMalloc((void **)&c->status_d, sizeof(DevStatus)) != cudaSuccess ||
+        cudaMallocHost((void **)&c->status_h, sizeof(DevStatus)) != cudaSuccess) {
+        cudaGetLastError();
+        if (c->status_d) cudaFree(c->status_d);
+        delete c;
+        return EVEC_ENOMEM;
+    }
+    if (cudaMemset(c->status_d, 0, sizeof(DevStatus)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(c->status_d);
+        cudaFreeHost(c->status_h);
+        delete c;
+        return EVEC_ECUDA;
+    }
+    *h = c;
+    return EVEC_OK;
+}
+
+evec_status evec_destroy(evec_handle h) {
+    if (!h) return EVEC_EINVAL;
+    DeviceGuard g(h->device);
+    cudaStreamSynchronize(h->stream);
+    cudaGetLastError();
+    void *dev[] = {h->diag_d, h->plan_d, h->Y, h->seg_e, h->seg_dx, h->seg_dy, h->seg_nu,
+                   h->tau, h->blk_tau, h->status_d, h->hT, h->hQ, h->hX, h->hE, h->hL};
+    for (void *p : dev)
+        if (p) cudaFree(p);
+    for (auto &t : h->live) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
+    for (cudaEvent_t e : h->spare) cudaEventDestroy(e);
+    void *host[] = {h->diag_h, h->plan_h, h->status_h};
+    for (void *p : host)
+        if (p) cudaFreeHost(p);
+    cudaGetLastError();
+    delete h;
+    return EVEC_OK;
+}
+
+evec_status evec_profile(evec_handle h, int enable) {
+    if (!h) return EVEC_EINVAL;
+    h->profiling = enable != 0;
+    return EVEC_OK;
+}
+
+evec_status evec_profile_read(evec_handle h, double *ms, int64_t *launches, int nk) {
+    if (!h || nk < 0 || nk > EVEC_K_COUNT) return EVEC_EINVAL;
+    DeviceGuard g(h->device);
+    if (!g.ok) return EVEC_ECUDA;
+    EVEC_CUDA(cudaStreamSynchronize(h->stream));
+    for (auto &t : h->live) {
+        float e = 0.0f;
+        if (cudaEventElapsedTime(&e, t.a, t.b) == cudaSuccess) h->prof_ms[t.kind] += e;
+        else cudaGetLastError();
+        h->prof_n[t.kind] += 1;
+        h->spare.push_back(t.a);
+        h->spare.push_back(t.b);
+    }
+    h->live.clear();
+    for (int k = 0; k < nk; k++) {
+        if (ms) ms[k] = h->prof_ms[k];
+        if (launches) launches[k] = h->prof_n[k];
+    }
+    for (int k = 0; k < EVEC_K_COUNT; k++) { h->prof_ms[k] = 0.0; h->prof_n[k] = 0; }
+    return EVEC_OK;
+}
+
+evec_status evec_set_stream(evec_handle h, void *cuda_stream) {
+    if (!h) return EVEC_EINVAL;
+    h->stream = (cudaStream_t)cuda_stream;
+    return EVEC_OK;
+}
+
+evec_status evec_count(evec_handle h, int64_t n, const double *T, int64_t ldt,
+                       const uint8_t *select_host, int64_t *m) {
+    if (!h || !m || n < 0 || !ld_ok(ldt, n) || (n > 0 && !T)) return EVEC_EINVAL;
+    if (n == 0) { *m = 0; return EVEC_OK; }
+    DeviceGuard g(h->device);
+    if (!g.ok) return EVEC_ECUDA;
+    EVEC_TRY(plan_device_matrix(h, n, T, ldt, select_host, 64, nullptr));
+    *m = h->plan.m;
+    return EVEC_OK;
+}
+
+evec_status evec_sync(evec_handle h, int64_t *bad_index) {
+    if (!h) return EVEC_EINVAL;
+    DeviceGuard g(h->device);
+    if (!g.ok) return EVEC_ECUDA;
+    EVEC_CUDA(cudaMemcpyAsync(h->status_h, h->status_d, sizeof(DevStatus),
+                              cudaMemcpyDeviceToHost, h->stream));
+    EVEC_CUDA(cudaStreamSynchronize(h->stream));
+    const DevStatus s = *h->status_h;
+    if (s.code != 0) {
+        EVEC_CUDA(cudaMemsetAsync(h->status_d, 0, sizeof(DevStatus), h->stream));
+        EVEC_CUDA(cudaStreamSynchronize(h->stream));
+    }
+    if (bad_index) *bad_index = s.code ? (int64_t)s.index : -1;
+    return (evec_status)s.code;
+}
+
+evec_status evec_standard(evec_handle h, int64_t n, const double *T, int64_t ldt,
+                          const double *Q, int64_t ldq, const uint8_t *select_host,
+                          double *X, int64_t ldx, int32_t *scale_exp, double *lam_re,
+                          double *lam_im, const evec_opts *opt) {
+    if (!h || n < 0 || !ld_ok(ldt, n) || !ld_ok(ldx, n) || (Q && !ld_ok(ldq, n)))
+        return EVEC_EINVAL;
+    if (opt && opt->mode != EVEC_FP64) return EVEC_EINVAL;
+    const int nb = resolve_tile(opt);
+    if (nb < 16 || nb > kMaxTile) return EVEC_EINVAL;
+    if (n == 0) return EVEC_OK;
+    if (!T || !X || !scale_exp) return EVEC_EINVAL;
+    DeviceGuard g(h->device);
+    if (!g.ok) return EVEC_ECUDA;
+
+    int64_t bad = -1;
+    EVEC_TRY(plan_device_matrix(h, n, T, ldt, select_host, nb, &bad));
+    const HostPlan &HP = h->plan;
+    const int64_t m = HP.m;
+    if (m == 0) return EVEC_OK;
+    const int N = (int)HP.tile_start.size() - 1;
+
+    Plan dp;
+    EVEC_TRY(upload_plan(h, dp));
+    double *Y = X;
+    int64_t ldy = ldx;
+    if (Q) {
+        EVEC_TRY(grow_device(&h->Y, &h->Y_cap, (size_t)n * (size_t)m));
+        Y = h->Y;
+        ldy = n;
+    }
+    const size_t segs = (size_t)N * (size_t)m;
+    EVEC_TRY(grow_device(&h->seg_e, &h->segi_cap[0], segs));
+    EVEC_TRY(grow_device(&h->seg_dx, &h->segi_cap[1], segs));
+    EVEC_TRY(grow_device(&h->seg_dy, &h->segi_cap[2], segs));
+    EVEC_TRY(grow_device(&h->seg_nu, &h->segn_cap, segs));
+    EVEC_TRY(grow_device(&h->tau, &h->tau_cap, (size_t)N * (size_t)N));
+    EVEC_TRY(grow_device(&h->blk_tau, &h->blk_tau_cap, HP.blk_start.size()));
+
+    cudaStream_t st = h->stream;
+    timed(h, EVEC_K_NORMS,
+          [&] { launch_tile_norms(T, ldt, dp, h->tau, h->blk_tau, h->status_d, st); });
+    for (int s = N - 1; s >= 0; s--) {
+        timed(h, EVEC_K_DIAG_SOLVE, [&] {
+            launch_diag_solve(s, T, ldt, dp, HP.tile_start.data(), HP.tile_unit.data(), h->tau,
+                              h->blk_tau, Y, ldy, h->seg_e, h->seg_nu, h->seg_dx, h->seg_dy, st);
+        });
+        if (s > 0 && HP.tile_col[s] < m)
+            timed(h, EVEC_K_TILE_UPDATE, [&] {
+                launch_tile_update(s, T, ldt, dp, HP.max_tile, HP.tile_col.data(), Y, ldy,
+                                   h->seg_dx, h->seg_dy, h->seg_nu, st);
+            });
+    }
+    timed(h, EVEC_K_FINALIZE, [&] { launch_finalize(dp, Y, ldy, h->seg_e, scale_exp, st); });
+    if (Q) {
+        timed(h, EVEC_K_BACKTRANSFORM,
+              [&] { launch_backtransform(Q, ldq, dp, Y, ldy, X, ldx, st); });
+        timed(h, EVEC_K_CANONICALIZE, [&] { launch_canonicalize(dp, X, ldx, scale_exp, st); });
+    }
+    EVEC_CUDA(cudaGetLastError());
+    // eigenvalues per column, from the pinned plan buffer
+    const size_t lam_off = (HP.unit_lam.size() + HP.unit_own.size()) * 8;
+    if (lam_re)
+        EVEC_CUDA(cudaMemcpyAsync(lam_re, h->plan_h + lam_off, m * 8, cudaMemcpyHostToDevice, st));
+    if (lam_im)
+        EVEC_CUDA(cudaMemcpyAsync(lam_im, h->plan_h + lam_off + m * 8, m * 8,
+                                  cudaMemcpyHostToDevice, st));
+    if (opt && opt->check) return evec_sync(h, nullptr);
+    return EVEC_OK;
+}
+
+evec_status evec_standard_host(evec_handle h, int64_t n, const double *T_host,
+                               const double *Q_host, const uint8_t *select_host,
+                               double *X_host, int32_t *scale_exp_host, double *lam_re_host,
+                               double *lam_im_host, const evec_opts *opt) {
+    if (!h || n < 0 || (n > 0 && !T_host)) return EVEC_EINVAL;
+    if (n == 0) return EVEC_OK;
+    DeviceGuard g(h->device);
+    if (!g.ok) return EVEC_ECUDA;
+    const size_t nn = (size_t)n * (size_t)n;
+    EVEC_TRY(grow_device(&h->hT, &h->hT_cap, nn));
+    cudaStream_t st = h->stream;
+    EVEC_CUDA(cudaMemcpyAsync(h->hT, T_host, nn * 8, cudaMemcpyHostToDevice, st));
+    if (Q_host) {
+        EVEC_TRY(grow_device(&h->hQ, &h->hQ_cap, nn));
+        EVEC_CUDA(cudaMemcpyAsync(h->hQ, Q_host, nn * 8, cudaMemcpyHostToDevice, st));
+    }
+    // the output size needs the plan; evec_standard plans again (cheap, host)
+    int64_t bad = -1;
+    EVEC_TRY(plan_device_matrix(h, n, h->hT, n, select_host, resolve_tile(opt), &bad));
+    const int64_t m = h->plan.m;
+    if (m == 0) return EVEC_OK;
+    EVEC_TRY(grow_device(&h->hX, &h->hX_cap, (size_t)n * (size_t)m));
+    EVEC_TRY(grow_device(&h->hE, &h->hE_cap, (size_t)m));
+    EVEC_TRY(grow_device(&h->hL, &h->hL_cap, 2 * (size_t)m));
+    EVEC_TRY(evec_standard(h, n, h->hT, n, Q_host ? h->hQ : nullptr, n, select_host, h->hX, n,
+                           h->hE, h->hL, h->hL + m, opt));
+    if (X_host)
+        EVEC_CUDA(cudaMemcpyAsync(X_host, h->hX, (size_t)n * m * 8, cudaMemcpyDeviceToHost, st));
+    if (scale_exp_host)
+        EVEC_CUDA(cudaMemcpyAsync(scale_exp_host, h->hE, m * 4, cudaMemcpyDeviceToHost, st));
+    if (lam_re_host)
+        EVEC_CUDA(cudaMemcpyAsync(lam_re_host, h->hL, m * 8, cudaMemcpyDeviceToHost, st));
+    if (lam_im_host)
+        EVEC_CUDA(cudaMemcpyAsync(lam_im_host, h->hL + m, m * 8, cudaMemcpyDeviceToHost, st));
+    return evec_sync(h, nullptr);
+}
+
+}  // extern "C"

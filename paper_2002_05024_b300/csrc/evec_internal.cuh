@@ -1,0 +1,113 @@
+// evec_internal.cuh -- shared declarations of the CUDA path (not installed).
+//
+// Data layout in device memory (all FP64 matrices column-major):
+//   T [ldt x n]           caller's quasi-triangular Schur form
+//   Y [ldy x m]           working eigenvector matrix; X itself when no Q
+//   seg_* [N x m]         one entry per (tile row r, output column j), row
+//                         major: index r * m + j.  Segment (r, j) is the part
+//                         of column j in the rows of tile r; it holds
+//                         y_true = Y * 2^(-seg_e) (the augmented tile
+//                         <alpha, X> of Sec. 3.4 with alpha = 2^seg_e).
+//   tau [N x N]           tau[r * N + s] = |T_rs|_inf for r < s
+//   blk_tau [nblk]        |T[tile start : q, block q]|_inf inside the tile
+// Units: one unit per selected real eigenvalue (one column) or selected
+// complex pair (two columns, Re then Im), in block order.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace evec {
+
+// Overflow threshold of every bound; 2^4 of headroom below DBL_MAX covers
+// the rounding of the bound arithmetic itself.
+constexpr double kOmega = 0x1p1020;
+constexpr double kInputMax = 0x1p1000;
+constexpr double kUlp = 0x1p-52;
+constexpr double kSafeMin = 0x1p-1022;
+constexpr int kOmegaExp = 1020;
+// dy sentinel: the segment has never been written; treat it as zero.
+constexpr int32_t kFresh = INT32_MIN;
+constexpr int kMaxTile = 128;
+
+struct DevStatus {
+    int code;          // evec_status of the first device-detected error
+    int pad;
+    long long index;   // linear index of the offending entry
+};
+
+// The plan: everything the kernels need about blocks, tiles and units.
+// All arrays live in one device buffer; pointers are set by the host.
+struct Plan {
+    int64_t n, m;
+    int32_t ntiles, nblk, nunits;
+    int32_t nb;                 // target tile size
+    const int32_t *tile_start;  // [ntiles + 1]
+    const int32_t *tile_blk;    // [ntiles + 1] first block of each tile
+    const int32_t *tile_unit;   // [ntiles + 1] first unit whose block is in the tile
+    const int32_t *tile_col;    // [ntiles + 1] first output column of the tile's units
+    const int32_t *blk_start;   // [nblk]
+    const int8_t *blk_size;     // [nblk]
+    const int32_t *unit_col;    // [nunits] first output column
+    const int32_t *unit_blk;    // [nunits] block index
+    const int32_t *unit_tile;   // [nunits]
+    const double *unit_lam;     // [2 * nunits] (re, im), im > 0 for a pair
+    const double *unit_own;     // [4 * nunits] block part: re0, re1, im0, im1
+    const int32_t *col_unit;    // [m] unit of each column
+};
+
+// ---------------------------------------------------------------------------
+// exact power-of-two scaling, from the IEEE-754 binary64 encoding
+// ---------------------------------------------------------------------------
+
+// 2^k for -1022 <= k <= 1023 (a normal number).
+__device__ __forceinline__ double pow2_normal(int k) {
+    return __longlong_as_double((long long)(k + 1023) << 52);
+}
+
+// x * 2^k for any integer k, by at most three exact multiplications; only a
+// result in the subnormal range is rounded (once per step).
+__device__ __forceinline__ double scale2(double x, int k) {
+    if (k >= -1022 && k <= 1023) return x * pow2_normal(k);
+    if (k < -1022) {
+        if (k < -2200) return x * 0.0;
+        x *= pow2_normal(-1022);
+        k += 1022;
+        if (k < -1022) { x *= pow2_normal(-1022); k += 1022; if (k < -1022) k = -1022; }
+        return x * pow2_normal(k);
+    }
+    if (k > 2200) k = 2200;
+    x *= pow2_normal(1023);
+    k -= 1023;
+    if (k > 1023) { x *= pow2_normal(1023); k -= 1023; }
+    return x * pow2_normal(k);
+}
+
+// floor(log2 |x|) for finite nonzero x, from the exponent field (subnormals
+// handled through one exact rescaling).
+__device__ __forceinline__ int ilog2_abs(double x) {
+    long long b = __double_as_longlong(x) & 0x7fffffffffffffffLL;
+    int ex = (int)(b >> 52);
+    if (ex == 0) {  // subnormal
+        double y = __longlong_as_double(b) * 0x1p64;
+        long long c = __double_as_longlong(y);
+        return (int)(c >> 52) - 1023 - 64;
+    }
+    return ex - 1023;
+}
+
+// Update protection (Sec. 3.4: before Z <- Y - T X, scale so the result
+// cannot exceed the threshold).  nu = |y|, tau = |T|, mu = |x|, with
+// nu <= Omega and tau <= Omega.  Returns q <= 0 such that
+// 2^q nu + tau 2^q mu <= Omega.
+__device__ __forceinline__ int protect_update(double nu, double tau, double mu) {
+    if (mu <= 1.0) {
+        return (tau * mu > kOmega - nu) ? -1 : 0;
+    }
+    return (tau > (kOmega - nu) / mu) ? -2 - ilog2_abs(mu) : 0;
+}
+
+__device__ __forceinline__ void report(DevStatus *st, int code, long long index) {
+    if (atomicCAS(&st->code, 0, code) == 0) st->index = index;
+}
+
+}  // namespace evec

@@ -1,0 +1,256 @@
+// k_gemm.cu -- the dense contractions of the method, in FP64 on the DFMA pipe.
+//
+// tile update (Sec. 3.4, the single level-3 operation of Z <- Y - T X):
+//   for every tile r < s and every active column j (its block in tile >= s)
+//     Y_r[:, j] <- 2^dy[r, j] Y_r[:, j] - T_rs (2^dx[r, j] X_s[:, j])
+//   with dy / dx from the diagonal-tile kernel (dy = fresh: Y_r[:, j] has not
+//   been written yet and counts as zero), and the new column maxima
+//   |Y_r[:, j]|_inf written to seg_nu for the next decisions.
+// back-transformation (Eq. evec_backtransform): X = Q Y, where Y is block
+//   upper triangular: column j is zero below its own diagonal block, so each
+//   column block only runs K up to the end of its last column's block.
+//
+// On B300 the FP64 tensor path (mma.sync .f64) was measured below the plain
+// DFMA rate, so both kernels are register-tiled DFMA GEMMs: a CTA of 256
+// threads computes a BM x 64 tile, each thread (BM/16) x 4 outputs, with
+// operands staged through double-buffered shared memory (K step 16, the next
+// chunk prefetched into registers while the current one is consumed).
+#include "evec_internal.cuh"
+
+namespace evec {
+
+constexpr int kBN = 64;
+constexpr int kBK = 16;
+constexpr int kThreads = 256;
+constexpr int kBPad = kBN + 1;   // B rows padded: conflict-free column-wise stores
+
+template <int BM>
+struct GemmSmem {
+    double A[2][kBK][BM];
+    double B[2][kBK][kBPad];
+    int bexp[kBN];
+};
+
+// acc[i][jj] += sum_k A[row i][k] * B[k][col jj] over k in [0, K).
+//   A(i, k) = A[i + k * lda], rows i < a_rows (rows beyond read as 0)
+//   B(k, j) = B[k + j * ldb], columns j < ncols
+//   scale_b: B column j is multiplied by 2^sm.bexp[j] while staged (exact)
+template <int BM>
+__device__ __forceinline__ void dfma_mainloop(const double *__restrict__ A, int64_t lda, int a_rows,
+                                              const double *__restrict__ B, int64_t ldb, int K,
+                                              int ncols, GemmSmem<BM> &sm, bool scale_b,
+                                              double (&acc)[BM / 16][4]) {
+    constexpr int MI = BM / 16;
+    constexpr int A_PER = BM * kBK / kThreads;   // A elements per thread per chunk
+    constexpr int B_PER = kBK * kBN / kThreads;  // = 4
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    double ra[A_PER], rb[B_PER];
+
+    auto load = [&](int kb) {
+#pragma unroll
+        for (int t = 0; t < A_PER; t++) {
+            const int e = tid + kThreads * t;
+            const int i = e % BM, k = e / BM;
+            ra[t] = (i < a_rows && kb + k < K) ? A[i + (int64_t)(kb + k) * lda] : 0.0;
+        }
+#pragma unroll
+        for (int t = 0; t < B_PER; t++) {
+            const int e = tid + kThreads * t;
+            const int k = e % kBK, j = e / kBK;
+            rb[t] = (j < ncols && kb + k < K) ? B[(kb + k) + (int64_t)j * ldb] : 0.0;
+        }
+    };
+    auto store = [&](int buf) {
+#pragma unroll
+        for (int t = 0; t < A_PER; t++) {
+            const int e = tid + kThreads * t;
+            sm.A[buf][e / BM][e % BM] = ra[t];
+        }
+#pragma unroll
+        for (int t = 0; t < B_PER; t++) {
+            const int e = tid + kThreads * t;
+            const int k = e % kBK, j = e / kBK;
+            sm.B[buf][k][j] = scale_b ? scale2(rb[t], sm.bexp[j]) : rb[t];
+        }
+    };
+
+#pragma unroll
+    for (int i = 0; i < MI; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) acc[i][j] = 0.0;
+
+    if (K <= 0) return;
+    load(0);
+    store(0);
+    __syncthreads();
+    int buf = 0;
+    for (int kb = 0; kb < K; kb += kBK) {
+        const bool more = kb + kBK < K;
+        if (more) load(kb + kBK);
+#pragma unroll
+        for (int k = 0; k < kBK; k++) {
+            double a[MI], b[4];
+#pragma unroll
+            for (int i = 0; i < MI; i++) a[i] = sm.A[buf][k][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; j++) b[j] = sm.B[buf][k][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < MI; i++)
+#pragma unroll
+                for (int j = 0; j < 4; j++) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+        if (more) {
+            store(buf ^ 1);
+            __syncthreads();
+            buf ^= 1;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// tile update at step s: grid (column blocks, r = 0..s-1)
+// ---------------------------------------------------------------------------
+template <int BM>
+__global__ void __launch_bounds__(kThreads)
+    k_tile_update(int s, const double *__restrict__ T, int64_t ldt, Plan P,
+                  double *__restrict__ Y, int64_t ldy, const int32_t *__restrict__ seg_dx,
+                  const int32_t *__restrict__ seg_dy, double *__restrict__ seg_nu) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    GemmSmem<BM> &sm = *reinterpret_cast<GemmSmem<BM> *>(smraw);
+    __shared__ int sdy[kBN];
+    __shared__ double red[16][kBN + 1];
+    constexpr int MI = BM / 16;
+
+    const int r = blockIdx.y;
+    const int r0 = P.tile_start[r];
+    const int rows = P.tile_start[r + 1] - r0;
+    const int k0 = P.tile_start[s];
+    const int K = P.tile_start[s + 1] - k0;
+    const int64_t m = P.m;
+    const int64_t j0 = (int64_t)P.tile_col[s] + (int64_t)blockIdx.x * kBN;
+    const int ncols = (int)min((int64_t)kBN, m - j0);
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+
+    if (tid < kBN) {
+        int dx = 0, dy = kFresh;
+        if (tid < ncols) {
+            dx = seg_dx[(int64_t)r * m + j0 + tid];
+            dy = seg_dy[(int64_t)r * m + j0 + tid];
+        }
+        sm.bexp[tid] = dx;
+        sdy[tid] = dy;
+    }
+    __syncthreads();
+
+    double acc[MI][4];
+    dfma_mainloop<BM>(T + r0 + (int64_t)k0 * ldt, ldt, rows, Y + k0 + j0 * ldy, ldy, K, ncols,
+                      sm, true, acc);
+
+    double cmax[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int jj = 0; jj < 4; jj++) {
+        const int jl = tx + 16 * jj;
+        if (jl >= ncols) continue;
+        const int dy = sdy[jl];
+        double *c = Y + (j0 + jl) * ldy + r0;
+#pragma unroll
+        for (int i = 0; i < MI; i++) {
+            const int row = ty + 16 * i;
+            if (row < rows) {
+                const double old = (dy == kFresh) ? 0.0 : scale2(c[row], dy);
+                const double v = old - acc[i][jj];
+                c[row] = v;
+                cmax[jj] = fmax(cmax[jj], fabs(v));
+            }
+        }
+    }
+#pragma unroll
+    for (int jj = 0; jj < 4; jj++) red[ty][tx + 16 * jj] = cmax[jj];
+    __syncthreads();
+    if (tid < ncols) {
+        double mx = 0.0;
+#pragma unroll
+        for (int t = 0; t < 16; t++) mx = fmax(mx, red[t][tid]);
+        seg_nu[(int64_t)r * m + j0 + tid] = mx;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// back-transformation X = Q Y: grid (column blocks, heaviest first; row blocks)
+// ---------------------------------------------------------------------------
+template <int BM>
+__global__ void __launch_bounds__(kThreads)
+    k_backtransform(const double *__restrict__ Q, int64_t ldq, Plan P,
+                    const double *__restrict__ Y, int64_t ldy, double *__restrict__ X,
+                    int64_t ldx) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    GemmSmem<BM> &sm = *reinterpret_cast<GemmSmem<BM> *>(smraw);
+    constexpr int MI = BM / 16;
+    const int64_t m = P.m, n = P.n;
+    const int64_t nblk_cols = (m + kBN - 1) / kBN;
+    const int64_t cb = nblk_cols - 1 - blockIdx.x;          // heaviest blocks first
+    const int64_t j0 = cb * kBN;
+    const int ncols = (int)min((int64_t)kBN, m - j0);
+    const int64_t i0 = (int64_t)blockIdx.y * BM;
+    const int rows = (int)min((int64_t)BM, n - i0);
+    // rows of Y beyond the last column's diagonal block are zero
+    const int ul = P.col_unit[j0 + ncols - 1];
+    const int kb = P.unit_blk[ul];
+    const int K = P.blk_start[kb] + P.blk_size[kb];
+
+    double acc[MI][4];
+    dfma_mainloop<BM>(Q + i0, ldq, rows, Y + j0 * ldy, ldy, K, ncols, sm, false, acc);
+
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+#pragma unroll
+    for (int jj = 0; jj < 4; jj++) {
+        const int jl = tx + 16 * jj;
+        if (jl >= ncols) continue;
+        double *c = X + (j0 + jl) * ldx + i0;
+#pragma unroll
+        for (int i = 0; i < MI; i++) {
+            const int row = ty + 16 * i;
+            if (row < rows) c[row] = acc[i][jj];
+        }
+    }
+}
+
+template <int BM>
+static void set_smem_attr() {
+    cudaFuncSetAttribute(k_tile_update<BM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(GemmSmem<BM>));
+    cudaFuncSetAttribute(k_backtransform<BM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(GemmSmem<BM>));
+}
+
+void launch_tile_update(int s, const double *T, int64_t ldt, const Plan &p, int max_tile,
+                        const int32_t *tile_col_h, double *Y, int64_t ldy,
+                        const int32_t *seg_dx, const int32_t *seg_dy, double *seg_nu,
+                        cudaStream_t st) {
+    if (s <= 0) return;
+    const int64_t cols = p.m - tile_col_h[s];
+    if (cols <= 0) return;
+    dim3 grid((unsigned)((cols + kBN - 1) / kBN), (unsigned)s);
+    if (max_tile <= 64) {
+        set_smem_attr<64>();
+        k_tile_update<64><<<grid, kThreads, sizeof(GemmSmem<64>), st>>>(s, T, ldt, p, Y, ldy,
+                                                                        seg_dx, seg_dy, seg_nu);
+    } else {
+        set_smem_attr<128>();
+        k_tile_update<128><<<grid, kThreads, sizeof(GemmSmem<128>), st>>>(s, T, ldt, p, Y, ldy,
+                                                                          seg_dx, seg_dy, seg_nu);
+    }
+}
+
+void launch_backtransform(const double *Q, int64_t ldq, const Plan &p, const double *Y,
+                          int64_t ldy, double *X, int64_t ldx, cudaStream_t st) {
+    constexpr int BM = 128;
+    set_smem_attr<BM>();
+    dim3 grid((unsigned)((p.m + kBN - 1) / kBN), (unsigned)((p.n + BM - 1) / BM));
+    k_backtransform<BM><<<grid, kThreads, sizeof(GemmSmem<BM>), st>>>(Q, ldq, p, Y, ldy, X, ldx);
+}
+
+}  // namespace evec

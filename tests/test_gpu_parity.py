@@ -1,0 +1,205 @@
+"""GPU path vs the CPU oracle, through the C ABI (via the thin binding).
+
+Tolerances (the library's stated parity bar):
+  * scale exponents agree within +-1 (both sides take floor(log2 |y|) of the
+    same true vector; a value next to a power of two may round either way);
+  * well-conditioned inputs: every column agrees normwise within 1e-10
+    relative after bringing both to one exponent;
+  * every input: normalised residual ||T x - lambda x||_1 / (||T||_1 ||x||_1 u)
+    <= 10 n, all entries finite, canonical norm in [1, 2), exact zeros below
+    the diagonal block (before back-transformation).
+Clustered adversarial inputs (eigenvalues 1e-9 apart, upper part 1e3) have
+eigenvectors whose forward error is of order |T| / gap * u; there the columns
+are compared to a looser bound stated in the test.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2002_05024_b300 as ev
+import workloads
+from evec_checks import (canonical_norms, column_groups, compare_canonical,
+                         standard_residuals)
+
+pytestmark = pytest.mark.gpu
+
+REL_TOL = 1e-10
+
+
+def _gpu(T, Q=None, select=None, tile=0):
+    dT = torch.from_numpy(np.asfortranarray(T)).cuda()
+    dQ = None if Q is None else torch.from_numpy(np.asfortranarray(Q)).cuda()
+    X, e, lr, li = ev.standard(dT, dQ, select=select, tile=tile, check=True)
+    torch.cuda.synchronize()
+    return X.cpu().numpy(), e.cpu().numpy(), lr.cpu().numpy(), li.cpu().numpy()
+
+
+def _check_structure(T, blocks, X, li, select=None):
+    assert np.isfinite(X).all()
+    nr = canonical_norms(X, li)
+    assert nr.min() >= 1.0 and nr.max() < 2.0
+    col = 0
+    for p, sz in blocks:
+        if select is not None and not (select[p] or (sz == 2 and select[p + 1])):
+            continue
+        for k in range(sz):
+            assert np.all(X[p + sz:, col + k] == 0.0)
+        col += sz
+
+
+def _parity(T, Q, X, e, lr, li, select=None, rel_tol=REL_TOL):
+    Xo, eo, lro, lio = oracle.standard(T, Q=Q, select=select)
+    assert X.shape == Xo.shape
+    np.testing.assert_array_equal(lr, lro)
+    np.testing.assert_array_equal(li, lio)
+    de, rel = compare_canonical(Xo, eo, X, e, lio)
+    assert de <= 1, de
+    assert rel <= rel_tol, rel
+    A = T if Q is None else Q @ T @ Q.T
+    res = standard_residuals(A, X, lr, li)
+    assert res.max() <= 10 * T.shape[0], res.max()
+    return rel, res.max()
+
+
+@pytest.mark.parametrize("tile", [16, 32, 64, 128])
+def test_config0_all_tiles(tile):
+    T, blocks = workloads.config0_schur(256)
+    X, e, lr, li = _gpu(T, tile=tile)
+    _check_structure(T, blocks, X, li)
+    _parity(T, None, X, e, lr, li)
+
+
+@pytest.mark.parametrize("n,tile", [(517, 64), (1000, 128), (333, 16)])
+def test_ragged_with_backtransform(n, tile):
+    T, blocks = workloads.config0_schur(n, seed=n)
+    Q = workloads.householder_orthogonal(n, seed=n + 1)
+    X, e, lr, li = _gpu(T, Q, tile=tile)
+    nr = canonical_norms(X, li)
+    assert np.isfinite(X).all() and nr.min() >= 1.0 and nr.max() < 2.0
+    _parity(T, Q, X, e, lr, li)
+
+
+def test_selection_subset():
+    T, blocks = workloads.config0_schur(700, seed=5)
+    sel = workloads.random_eigen_selection(700, blocks, 0.35, seed=6)
+    X, e, lr, li = _gpu(T, select=sel, tile=64)
+    _check_structure(T, blocks, X, li, select=sel)
+    _parity(T, None, X, e, lr, li, select=sel)
+
+
+def test_adversarial_overflow_case():
+    n = 512
+    T, blocks = workloads.adversarial_schur(n, seed=77)
+    _, bad = oracle.naive_standard(T)
+    assert bad > 0                        # unscaled substitution overflows
+    X, e, lr, li = _gpu(T, tile=64)
+    _check_structure(T, blocks, X, li)
+    assert e.min() < -1074                # true vectors far outside the double range
+    # forward error of a 1e-9-cluster eigenvector ~ |T| / gap * u ~ 1e-3
+    _parity(T, None, X, e, lr, li, rel_tol=1e-3)
+
+
+def test_edge_sizes():
+    for S in (np.array([[0.5]]), np.array([[0.2, 1.0], [-0.5, 0.2]]),
+              np.array([[1.0, 2.0, 3.0], [0.0, 0.5, 1.0], [0.0, -2.0, 0.5]])):
+        X, e, lr, li = _gpu(S, tile=16)
+        _parity(S, None, X, e, lr, li)
+    T, blocks = workloads.config0_schur(40, seed=2)
+    X, e, lr, li = _gpu(T, select=np.zeros(40, np.uint8))
+    assert X.shape == (40, 0)
+    X, e, lr, li = _gpu(np.zeros((0, 0)))
+    assert X.shape == (0, 0)
+
+
+def test_errors_are_reported():
+    S = np.triu(np.ones((6, 6)))
+    S[1, 0] = -1.0
+    S[2, 1] = -1.0
+    with pytest.raises(ev.EvecError) as ei:
+        _gpu(S)
+    assert ei.value.status == ev.EVEC_ENOTSCHUR
+    T, _ = workloads.config0_schur(200, seed=9)
+    T[3, 150] = np.inf
+    with pytest.raises(ev.EvecError) as ei:
+        _gpu(T, tile=32)
+    assert ei.value.status == ev.EVEC_ENONFINITE and ei.value.bad == 3 + 150 * 200
+    T[3, 150] = 2.0 ** 1005
+    with pytest.raises(ev.EvecError) as ei:
+        _gpu(T, tile=32)
+    assert ei.value.status == ev.EVEC_EINVAL
+    # the handle stays usable after a reported error
+    T[3, 150] = 0.5
+    X, e, lr, li = _gpu(T, tile=32)
+    _parity(T, None, X, e, lr, li)
+
+
+def test_host_entry_point_matches_device():
+    n = 300
+    T, _ = workloads.config0_schur(n, seed=12)
+    Q = workloads.householder_orthogonal(n, seed=13)
+    X, e, lr, li = _gpu(T, Q, tile=64)
+    Xh, eh, lrh, lih = ev.standard_host(T, Q, tile=64)
+    np.testing.assert_array_equal(X, Xh)
+    np.testing.assert_array_equal(e, eh)
+    np.testing.assert_array_equal(lr, lrh)
+    np.testing.assert_array_equal(li, lih)
+
+
+def test_deterministic_and_power_of_two_invariant():
+    n = 640
+    T, _ = workloads.config0_schur(n, seed=21)
+    X1, e1, _, _ = _gpu(T, tile=64)
+    X2, e2, _, _ = _gpu(T, tile=64)
+    np.testing.assert_array_equal(X1, X2)
+    np.testing.assert_array_equal(e1, e2)
+    # T -> 2^6 T: same eigenvectors, every operation scaled exactly
+    X3, e3, _, _ = _gpu(np.ldexp(T, 6), tile=64)
+    np.testing.assert_array_equal(X1, X3)
+    np.testing.assert_array_equal(e1, e3)
+
+
+# ---------------------------------------------------------------------------
+# full size, in the benchmark's launch configuration (tile 64, with Q):
+# the GPU computes every column, the oracle a seeded sample of columns
+# ---------------------------------------------------------------------------
+def _sampled_parity(T, blocks, Q, k, seed, rel_tol):
+    n = T.shape[0]
+    X, e, lr, li = _gpu(T, Q, tile=0)
+    assert np.isfinite(X).all()
+    rng = np.random.default_rng(seed)
+    chosen = rng.choice(len(blocks), size=k, replace=False)
+    sel = np.zeros(n, np.uint8)
+    for b in chosen:
+        p, sz = blocks[b]
+        sel[p:p + sz] = 1
+    Xo, eo, lro, lio = oracle.standard(T, Q=Q, select=sel)
+    cols = []
+    col = 0
+    for p, sz in blocks:
+        if sel[p]:
+            cols.extend(range(col, col + sz))
+        col += sz
+    de, rel = compare_canonical(Xo, eo, X[:, cols], e[cols], lio)
+    assert de <= 1
+    assert rel <= rel_tol, rel
+    A = Q @ T @ Q.T
+    res = standard_residuals(A, X[:, cols], lr[cols], li[cols])
+    assert res.max() <= 10 * n
+    nr = canonical_norms(X, li)
+    assert nr.min() >= 1.0 and nr.max() < 2.0
+    return rel
+
+
+def test_full_size_config1a_sampled():
+    n = 4096
+    T, blocks = workloads.config0_schur(n, seed=workloads.SEED_BASE + 1)
+    Q = workloads.householder_orthogonal(n, seed=workloads.SEED_BASE + 101)
+    _sampled_parity(T, blocks, Q, k=48, seed=1, rel_tol=REL_TOL)
+
+
+def test_full_size_config1b_sampled():
+    n = 4096
+    T, blocks = workloads.adversarial_schur(n, seed=workloads.SEED_BASE + 11)
+    Q = workloads.householder_orthogonal(n, seed=workloads.SEED_BASE + 111)
+    _sampled_parity(T, blocks, Q, k=32, seed=2, rel_tol=1e-3)
