@@ -73,7 +73,8 @@ typedef enum {
     EVEC_ENOMEM = 4,     /* device or host allocation failed */
     EVEC_ECUDA = 5,      /* CUDA runtime error */
     EVEC_ETIMEOUT = 6,   /* a bounded device-side wait gave up */
-    EVEC_ERESIDUAL = 7   /* reserved: residual gate failed */
+    EVEC_ERESIDUAL = 7,  /* reserved: residual gate failed */
+    EVEC_ECAPACITY = 8   /* problem larger than evec_standard_noalloc's fixed scratch */
 } evec_status;
 
 typedef enum {
@@ -173,6 +174,43 @@ evec_status evec_profile(evec_handle h, int enable);
  * read (arrays of nk entries, nk <= EVEC_K_COUNT; either may be NULL); then
  * reset the counters. */
 evec_status evec_profile_read(evec_handle h, double *ms, int64_t *launches, int nk);
+
+/* Limits of evec_standard_noalloc. */
+#define EVEC_NOALLOC_MAX_N 512
+#define EVEC_NOALLOC_SCRATCH_BYTES (1 << 20)
+
+/*
+ * evec_standard_noalloc -- the paper has no counterpart to this entry point;
+ * it exists for callers that cannot allocate GPU memory while they run: a
+ * serving process whose own memory pool already owns the device, code where
+ * a cudaMalloc would synchronise the device or fail, a program with a fixed,
+ * pre-reserved memory budget.  It computes the same result as evec_standard
+ * with Q == NULL (X = Y, canonical columns, scale_exp) for n <= 512, and
+ * allocates nothing: no handle, no cudaMalloc / cudaFree, no pinned host
+ * memory.  All scratch lives in one fixed device array of
+ * EVEC_NOALLOC_SCRATCH_BYTES inside the library, which every GPU that loads
+ * the library holds until the process exits.
+ *   T [ldt x n], X [ldx x m] output, scale_exp [m]: device pointers on the
+ *   current device; select_host as for evec_standard (m from evec_count or
+ *   evec_plan_query); tile: 16..128, 0 = 64; cuda_stream: stream of the
+ *   current device (NULL = legacy default stream).
+ * The first call on a device looks up the array's device address (with
+ * that device current); make that first call before any stream capture.
+ * Every call shares the array and reuses whatever the previous call left in
+ * it (the status word is cleared at the start of each call; everything else
+ * is written before it is read).  Calls are serialised inside the library
+ * and each one synchronises its stream before returning, so calls through
+ * this entry point never overlap on the GPU; two processes or any other
+ * overlapping use would race on the array.
+ * Returns, synchronously: EVEC_ECAPACITY when n > EVEC_NOALLOC_MAX_N or the
+ * chosen tile needs more than the fixed scratch; EVEC_EINVAL,
+ * EVEC_ENOTSCHUR, EVEC_ENONFINITE (with *bad_index, linear index into T) as
+ * evec_standard and evec_sync would; EVEC_ECUDA on a runtime error.
+ */
+evec_status evec_standard_noalloc(int64_t n, const double *T, int64_t ldt,
+                                  const uint8_t *select_host, double *X, int64_t ldx,
+                                  int32_t *scale_exp, int tile, void *cuda_stream,
+                                  int64_t *bad_index);
 
 /* Static, human-readable name of a status code. */
 const char *evec_strerror(evec_status s);

@@ -24,9 +24,11 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libevec.so")
 
 STATUS = {0: "EVEC_OK", 1: "EVEC_EINVAL", 2: "EVEC_ENOTSCHUR", 3: "EVEC_ENONFINITE",
-          4: "EVEC_ENOMEM", 5: "EVEC_ECUDA", 6: "EVEC_ETIMEOUT", 7: "EVEC_ERESIDUAL"}
+          4: "EVEC_ENOMEM", 5: "EVEC_ECUDA", 6: "EVEC_ETIMEOUT", 7: "EVEC_ERESIDUAL",
+          8: "EVEC_ECAPACITY"}
 EVEC_OK, EVEC_EINVAL, EVEC_ENOTSCHUR, EVEC_ENONFINITE = 0, 1, 2, 3
 EVEC_ENOMEM, EVEC_ECUDA, EVEC_ETIMEOUT, EVEC_ERESIDUAL = 4, 5, 6, 7
+EVEC_ECAPACITY = 8
 KERNELS = ("gather", "tile_norms", "diag_solve", "tile_update", "finalize",
            "backtransform", "canonicalize")
 

@@ -378,6 +378,7 @@ const char *evec_strerror(evec_status s) {
         case EVEC_ECUDA: return "EVEC_ECUDA: CUDA runtime error";
         case EVEC_ETIMEOUT: return "EVEC_ETIMEOUT: bounded device wait gave up";
         case EVEC_ERESIDUAL: return "EVEC_ERESIDUAL: residual gate failed";
+        case EVEC_ECAPACITY: return "EVEC_ECAPACITY: larger than the fixed no-allocation scratch";
     }
     return "unknown evec_status";
 }
