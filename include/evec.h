@@ -212,6 +212,10 @@ evec_status evec_standard_noalloc(int64_t n, const double *T, int64_t ldt,
                                   int32_t *scale_exp, int tile, void *cuda_stream,
                                   int64_t *bad_index);
 
+/* Text of the most recent CUDA runtime error that made a call of this
+ * library on the calling host thread return EVEC_ECUDA or EVEC_ENOMEM. */
+const char *evec_last_cuda_error(void);
+
 /* Static, human-readable name of a status code. */
 const char *evec_strerror(evec_status s);
 

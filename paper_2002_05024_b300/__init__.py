@@ -38,6 +38,8 @@ class EvecError(RuntimeError):
         msg = f"{where}: {STATUS.get(status, status)}"
         if bad >= 0:
             msg += f" (index {bad})"
+        if status in (4, 5) and _lib is not None:
+            msg += f" [{_lib.evec_last_cuda_error().decode()}]"
         super().__init__(msg)
         self.status = status
         self.bad = bad
@@ -77,6 +79,8 @@ def lib() -> ctypes.CDLL:
                                       ctypes.POINTER(i32), p, ctypes.POINTER(i64)]
         L.evec_profile.argtypes = [p, ctypes.c_int]
         L.evec_profile_read.argtypes = [p, p, p, ctypes.c_int]
+        L.evec_last_cuda_error.argtypes = []
+        L.evec_last_cuda_error.restype = ctypes.c_char_p
         L.evec_strerror.argtypes = [ctypes.c_int]
         L.evec_strerror.restype = ctypes.c_char_p
         for f in ("evec_create", "evec_destroy", "evec_set_stream", "evec_count",

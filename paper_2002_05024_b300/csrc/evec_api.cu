@@ -27,7 +27,8 @@ void launch_gather_diagonals(const double *T, int64_t ldt, int64_t n, double *ou
 void launch_tile_norms(const double *T, int64_t ldt, const Plan &p, double *tau,
                        double *blk_tau, DevStatus *status, cudaStream_t st);
 void launch_diag_solve(int s, const double *T, int64_t ldt, const Plan &p,
-                       const int32_t *tile_start_h, const int32_t *tile_unit_h,
+                       const int32_t *tile_start_h, const int32_t *tile_real_h,
+                       const int32_t *tile_cplx_h,
                        const double *tau, const double *blk_tau, double *Y, int64_t ldy,
                        int32_t *seg_e, double *seg_nu, int32_t *seg_dx, int32_t *seg_dy,
                        cudaStream_t st);
@@ -50,6 +51,7 @@ struct HostPlan {
     int nb = 0, max_tile = 0;
     std::vector<int32_t> tile_start, tile_blk, tile_unit, tile_col;
     std::vector<int32_t> blk_start, unit_col, unit_blk, unit_tile, col_unit;
+    std::vector<int32_t> ord_real, ord_cplx, tile_real, tile_cplx;
     std::vector<int8_t> blk_size;
     std::vector<double> unit_lam, unit_own, col_lam_re, col_lam_im;
 };
@@ -171,6 +173,22 @@ static evec_status build_plan(int64_t n, const double *diag, const double *sub,
         P.tile_col[tt] = (int32_t)col;
     }
     P.m = col;
+    // solve order: real and complex units, each in unit (= tile) order
+    P.tile_real.assign(N + 1, 0);
+    P.tile_cplx.assign(N + 1, 0);
+    for (int32_t u = 0; u < (int32_t)P.unit_col.size(); u++) {
+        if (P.unit_lam[2 * u + 1] == 0.0) P.ord_real.push_back(u);
+        else P.ord_cplx.push_back(u);
+    }
+    {
+        size_t ir = 0, ic = 0;
+        for (int tt = 0; tt <= N; tt++) {
+            while (ir < P.ord_real.size() && P.unit_tile[P.ord_real[ir]] < tt) ir++;
+            while (ic < P.ord_cplx.size() && P.unit_tile[P.ord_cplx[ic]] < tt) ic++;
+            P.tile_real[tt] = (int32_t)ir;
+            P.tile_cplx[tt] = (int32_t)ic;
+        }
+    }
     return EVEC_OK;
 }
 
@@ -261,8 +279,12 @@ evec_status grow_host(T **p, size_t *cap, size_t count) {
     return EVEC_OK;
 }
 
+// most recent CUDA error seen by this library on the calling host thread
+thread_local cudaError_t g_last_cuda_error = cudaSuccess;
+
 evec_status cuda_status(cudaError_t e) {
     if (e == cudaSuccess) return EVEC_OK;
+    g_last_cuda_error = e;
     cudaGetLastError();
     return e == cudaErrorMemoryAllocation ? EVEC_ENOMEM : EVEC_ECUDA;
 }
@@ -323,8 +345,9 @@ evec_status upload_plan(evec_handle h, Plan &dp) {
     const HostPlan &P = h->plan;
     const size_t N1 = P.tile_start.size();
     const size_t nd = P.unit_lam.size() + P.unit_own.size() + P.col_lam_re.size() + P.col_lam_im.size();
-    const size_t ni = 4 * N1 + P.blk_start.size() + P.unit_col.size() + P.unit_blk.size() +
-                      P.unit_tile.size() + P.col_unit.size();
+    const size_t ni = 6 * N1 + P.blk_start.size() + P.unit_col.size() + P.unit_blk.size() +
+                      P.unit_tile.size() + P.col_unit.size() + P.ord_real.size() +
+                      P.ord_cplx.size();
     const size_t bytes = nd * 8 + ni * 4 + P.blk_size.size() + 64;
     EVEC_TRY(grow_host(&h->plan_h, &h->plan_h_cap, bytes));
     EVEC_TRY(grow_device(&h->plan_d, &h->plan_cap, bytes));
@@ -355,6 +378,12 @@ evec_status upload_plan(evec_handle h, Plan &dp) {
     dp.unit_blk = (const int32_t *)put(P.unit_blk.data(), P.unit_blk.size() * 4, 4);
     dp.unit_tile = (const int32_t *)put(P.unit_tile.data(), P.unit_tile.size() * 4, 4);
     dp.col_unit = (const int32_t *)put(P.col_unit.data(), P.col_unit.size() * 4, 4);
+    dp.nreal = (int32_t)P.ord_real.size();
+    dp.ncplx = (int32_t)P.ord_cplx.size();
+    dp.ord_real = (const int32_t *)put(P.ord_real.data(), P.ord_real.size() * 4, 4);
+    dp.ord_cplx = (const int32_t *)put(P.ord_cplx.data(), P.ord_cplx.size() * 4, 4);
+    dp.tile_real = (const int32_t *)put(P.tile_real.data(), N1 * 4, 4);
+    dp.tile_cplx = (const int32_t *)put(P.tile_cplx.data(), N1 * 4, 4);
     dp.blk_size = (const int8_t *)put(P.blk_size.data(), P.blk_size.size(), 1);
     EVEC_CUDA(cudaMemcpyAsync(h->plan_d, h->plan_h, off, cudaMemcpyHostToDevice, h->stream));
     return EVEC_OK;
@@ -381,6 +410,10 @@ const char *evec_strerror(evec_status s) {
         case EVEC_ECAPACITY: return "EVEC_ECAPACITY: larger than the fixed no-allocation scratch";
     }
     return "unknown evec_status";
+}
+
+const char *evec_last_cuda_error(void) {
+    return g_last_cuda_error == cudaSuccess ? "no CUDA error" : cudaGetErrorString(g_last_cuda_error);
 }
 
 evec_status evec_plan_query(int64_t n, const double *diag, const double *sub, const double *sup,
@@ -556,7 +589,8 @@ evec_status evec_standard(evec_handle h, int64_t n, const double *T, int64_t ldt
           [&] { launch_tile_norms(T, ldt, dp, h->tau, h->blk_tau, h->status_d, st); });
     for (int s = N - 1; s >= 0; s--) {
         timed(h, EVEC_K_DIAG_SOLVE, [&] {
-            launch_diag_solve(s, T, ldt, dp, HP.tile_start.data(), HP.tile_unit.data(), h->tau,
+            launch_diag_solve(s, T, ldt, dp, HP.tile_start.data(), HP.tile_real.data(),
+                              HP.tile_cplx.data(), h->tau,
                               h->blk_tau, Y, ldy, h->seg_e, h->seg_nu, h->seg_dx, h->seg_dy, st);
         });
         if (s > 0 && HP.tile_col[s] < m)

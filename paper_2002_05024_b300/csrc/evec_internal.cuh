@@ -53,6 +53,13 @@ struct Plan {
     const double *unit_lam;     // [2 * nunits] (re, im), im > 0 for a pair
     const double *unit_own;     // [4 * nunits] block part: re0, re1, im0, im1
     const int32_t *col_unit;    // [m] unit of each column
+    // solve order: real units and complex units, each in unit order, so the
+    // units active at step s (block in tile >= s) are a suffix of each list
+    int32_t nreal, ncplx;
+    const int32_t *ord_real;    // [nreal] unit indices
+    const int32_t *ord_cplx;    // [ncplx]
+    const int32_t *tile_real;   // [ntiles + 1] first position in ord_real with tile >= s
+    const int32_t *tile_cplx;   // [ntiles + 1]
 };
 
 // ---------------------------------------------------------------------------
@@ -99,11 +106,47 @@ __device__ __forceinline__ int ilog2_abs(double x) {
 // cannot exceed the threshold).  nu = |y|, tau = |T|, mu = |x|, with
 // nu <= Omega and tau <= Omega.  Returns q <= 0 such that
 // 2^q nu + tau 2^q mu <= Omega.
+// The test is tau * mu > Omega - nu: a product that overflows to +Inf
+// (tau, mu <= Omega) still compares as "too large", so no division is needed.
 __device__ __forceinline__ int protect_update(double nu, double tau, double mu) {
-    if (mu <= 1.0) {
-        return (tau * mu > kOmega - nu) ? -1 : 0;
+    if (!(tau * mu > kOmega - nu)) return 0;
+    return mu <= 1.0 ? -1 : -2 - ilog2_abs(mu);
+}
+
+// 1 / x for finite nonzero x without the IEEE division sequence: x = m 2^k
+// with m in [1, 2) (exponent field), a hardware approximation of 1/m
+// (rcp.approx.ftz.f64), two Newton-Raphson steps r <- r + r (1 - m r) in
+// FP64, then the exact rescaling by 2^-k.  Relative error within a few ulp.
+__device__ __forceinline__ double rcp_fast(double x) {
+    long long b = __double_as_longlong(x);
+    int ex = (int)((b >> 52) & 0x7ff);
+    int adj = 0;
+    if (ex == 0) {  // subnormal: rescale exactly first
+        x *= 0x1p64;
+        b = __double_as_longlong(x);
+        ex = (int)((b >> 52) & 0x7ff);
+        adj = 64;
     }
-    return (tau > (kOmega - nu) / mu) ? -2 - ilog2_abs(mu) : 0;
+    const double m = __longlong_as_double((b & 0x800fffffffffffffLL) | (1023LL << 52));
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(m));
+    double e = fma(-m, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-m, r, 1.0);
+    r = fma(r, e, r);
+    return scale2(r, 1023 - ex + adj);
+}
+
+// Biased exponent field of x (0 for zero and subnormals): |x| < 2^(field - 1022).
+// Integer arithmetic on fields replaces FP64 compares on latency chains.
+__device__ __forceinline__ int efield(double x) {
+    return (__double2hiint(x) >> 20) & 0x7ff;
+}
+
+// max of |a| over doubles through their bit patterns (integer pipe): the
+// order of non-negative IEEE doubles is the order of their encodings.
+__device__ __forceinline__ long long abs_bits(double x) {
+    return __double_as_longlong(x) & 0x7fffffffffffffffLL;
 }
 
 __device__ __forceinline__ void report(DevStatus *st, int code, long long index) {

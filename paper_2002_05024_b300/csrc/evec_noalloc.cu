@@ -38,7 +38,8 @@ void launch_gather_diagonals(const double *T, int64_t ldt, int64_t n, double *ou
 void launch_tile_norms(const double *T, int64_t ldt, const Plan &p, double *tau,
                        double *blk_tau, DevStatus *status, cudaStream_t st);
 void launch_diag_solve(int s, const double *T, int64_t ldt, const Plan &p,
-                       const int32_t *tile_start_h, const int32_t *tile_unit_h,
+                       const int32_t *tile_start_h, const int32_t *tile_real_h,
+                       const int32_t *tile_cplx_h,
                        const double *tau, const double *blk_tau, double *Y, int64_t ldy,
                        int32_t *seg_e, double *seg_nu, int32_t *seg_dx, int32_t *seg_dy,
                        cudaStream_t st);
@@ -70,6 +71,8 @@ struct SmallPlan {
     int32_t tile_unit[kMaxTiles + 1], tile_col[kMaxTiles + 1];
     int32_t blk_start[kMaxN], unit_col[kMaxN], unit_blk[kMaxN], unit_tile[kMaxN];
     int32_t col_unit[kMaxN];
+    int32_t ord_real[kMaxN], ord_cplx[kMaxN], tile_real[kMaxTiles + 1], tile_cplx[kMaxTiles + 1];
+    int nreal, ncplx;
     int8_t blk_size[kMaxN], second[kMaxN];
     double unit_lam[2 * kMaxN], unit_own[4 * kMaxN];
     double diag[3 * kMaxN];
@@ -153,6 +156,18 @@ evec_status plan_small(SmallPlan &P, int n, const uint8_t *sel, int nb, int64_t 
         P.tile_unit[tt] = P.nunits;
         P.tile_col[tt] = P.m;
     }
+    P.nreal = P.ncplx = 0;
+    for (int u = 0; u < P.nunits; u++) {
+        if (P.unit_lam[2 * u + 1] == 0.0) P.ord_real[P.nreal++] = u;
+        else P.ord_cplx[P.ncplx++] = u;
+    }
+    int ir = 0, ic = 0;
+    for (int tt = 0; tt <= P.ntiles; tt++) {
+        while (ir < P.nreal && P.unit_tile[P.ord_real[ir]] < tt) ir++;
+        while (ic < P.ncplx && P.unit_tile[P.ord_cplx[ic]] < tt) ic++;
+        P.tile_real[tt] = ir;
+        P.tile_cplx[tt] = ic;
+    }
     return EVEC_OK;
 }
 
@@ -171,7 +186,7 @@ Layout layout(int n, int ntiles, int nblk, int nunits, int m) {
     L.diag = o; o = align_up(o + sizeof(double) * (3 * (size_t)n), 256);
     L.plan = o;
     const size_t plan_bytes = sizeof(double) * (6 * (size_t)nunits) +
-                              sizeof(int32_t) * (4 * (size_t)(ntiles + 1) + nblk + 3 * (size_t)nunits + m) +
+                              sizeof(int32_t) * (6 * (size_t)(ntiles + 1) + nblk + 4 * (size_t)nunits + m) +
                               (size_t)nblk + 64;
     o = align_up(o + plan_bytes, 256);
     L.tau = o; o = align_up(o + sizeof(double) * (size_t)ntiles * ntiles, 256);
@@ -240,7 +255,7 @@ extern "C" evec_status evec_standard_noalloc(int64_t n, const double *T, int64_t
 
     // pack the plan on the stack, copy it into the scratch array
     alignas(8) unsigned char packed[sizeof(double) * 6 * kMaxN +
-                                    sizeof(int32_t) * (4 * (kMaxTiles + 1) + 5 * kMaxN) +
+                                    sizeof(int32_t) * (6 * (kMaxTiles + 1) + 6 * kMaxN) +
                                     kMaxN + 64];
     size_t off = 0;
     Plan dp;
@@ -268,6 +283,12 @@ extern "C" evec_status evec_standard_noalloc(int64_t n, const double *T, int64_t
     dp.unit_blk = (const int32_t *)put(P.unit_blk, 4 * (size_t)P.nunits, 4);
     dp.unit_tile = (const int32_t *)put(P.unit_tile, 4 * (size_t)P.nunits, 4);
     dp.col_unit = (const int32_t *)put(P.col_unit, 4 * (size_t)P.m, 4);
+    dp.nreal = P.nreal;
+    dp.ncplx = P.ncplx;
+    dp.ord_real = (const int32_t *)put(P.ord_real, 4 * (size_t)P.nreal, 4);
+    dp.ord_cplx = (const int32_t *)put(P.ord_cplx, 4 * (size_t)P.ncplx, 4);
+    dp.tile_real = (const int32_t *)put(P.tile_real, 4 * (size_t)(P.ntiles + 1), 4);
+    dp.tile_cplx = (const int32_t *)put(P.tile_cplx, 4 * (size_t)(P.ntiles + 1), 4);
     dp.blk_size = (const int8_t *)put(P.blk_size, (size_t)P.nblk, 1);
 
     DevStatus *status = (DevStatus *)(base + L.status);
@@ -286,7 +307,8 @@ extern "C" evec_status evec_standard_noalloc(int64_t n, const double *T, int64_t
     }
     launch_tile_norms(T, ldt, dp, tau, blk_tau, status, st);
     for (int s = P.ntiles - 1; s >= 0; s--) {
-        launch_diag_solve(s, T, ldt, dp, P.tile_start, P.tile_unit, tau, blk_tau, X, ldx, seg_e,
+        launch_diag_solve(s, T, ldt, dp, P.tile_start, P.tile_real, P.tile_cplx, tau, blk_tau, X,
+                          ldx, seg_e,
                           seg_nu, seg_dx, seg_dy, st);
         if (s > 0 && P.tile_col[s] < P.m)
             launch_tile_update(s, T, ldt, dp, P.max_tile, P.tile_col, X, ldx, seg_dx, seg_dy,

@@ -3,350 +3,562 @@
 // decisions for every tile above it (Sec. 3.4, the preprocessing step of the
 // update Z <- Y - T X).
 //
-// One warp per unit (a real eigenvalue, or a complex pair solved as one
-// complex column).  T_ss sits in shared memory and is shared by the CTA's
-// warps; the unit's tile segment lives in a per-warp shared buffer.  Every
-// unit runs its own chain of block steps from the bottom of the tile to the
-// top; within a step the rows above the block are updated by the 32 lanes.
+// Work split: G = 8 lanes per unit (a real eigenvalue, or a complex pair
+// solved as one complex column), 4 units per warp, CTAs of W = 4 warps
+// (W = 2 for tiles above 64 rows); real and complex units in separate CTAs
+// of one launch.  On B300 one SM sub-partition issues at most one FP64
+// warp-instruction per 64 cycles, so the FP64 instructions of a unit's
+// chain are spread thin: about one update row per lane per block step, and
+// the W warps of a CTA land on different sub-partitions.  Row i of a unit's segment
+// belongs to lane i mod G.  The block solves form a sequential chain per
+// unit, and a warp issues in order, so the chain is kept short: the
+// factors of every shifted 1x1/2x2 block system of the tile are computed
+// first (independent of the data, spread over the unit's lanes; pivot
+// reciprocals by rcp.approx + Newton steps, no IEEE division) and kept in
+// shared memory; each block step then only applies its factors without
+// normalisation (falling back to the normalised, protected solve when the
+// result is not finite or too large) and runs the update with every load
+// issued before its DFMAs.  Maxima and range checks use integer compares on
+// the IEEE bit patterns.
 //
 // Per block step (block at local row q, size 1 or 2):
-//   1. solve (T_qq - lambda I) z = rhs_q, 1x1 or 2x2, real or complex, with
-//      pivots perturbed up to smin and a power-of-two scale 2^sc <= 1 chosen
-//      so |z| <= Omega (the division protection);
-//   2. protect the update rows[0:q] -= T[0:q, q-block] z with the bound
-//      nu + tau mu <= Omega (tau = blk_tau, nu = running bound on the rows,
+//   1. z = (T_qq - lambda I)^-1 rhs_q with pivots perturbed up to smin and a
+//      power-of-two scale 2^sc <= 1 keeping |z| <= Omega (division
+//      protection);
+//   2. protect rows[0:q] -= T[0:q, q-block] z with nu + tau mu <= Omega
+//      (tau = in-tile block norm, nu = running bound on the rows above,
 //      recomputed exactly only when the bound asks for a scaling);
 //   3. apply the update.
-// All scalings are exact powers of two and accumulate in the segment's
-// exponent e (y_true = y * 2^-e).
+// All scalings are exact powers of two accumulated in the segment exponent
+// e (y_true = y * 2^-e).
 //
-// Afterwards, for every tile r < s of the unit's column, the decisions of
-// the update Y_r <- Y_r - T_rs X_s are taken here: common exponent
-// a = min(e_r, e_s), protection q of (nu_r 2^(a-e_r), tau_rs, mu_s 2^(a-e_s)),
-// new e_r = a + q, and the two scale exponents dy = a + q - e_r (for Y_r) and
-// dx = a + q - e_s (for X_s), consumed by the update kernel.
+// Afterwards, for every tile r < s of each unit's column, the decisions of
+// the update Y_r <- Y_r - T_rs X_s: a = min(e_r, e_s), protection q of
+// (nu_r 2^(a-e_r), tau_rs, mu_s 2^(a-e_s)), new e_r = a + q,
+// dy = a + q - e_r (scale of Y_r), dx = a + q - e_s (scale of X_s).
 #include "evec_internal.cuh"
 
 namespace evec {
 
 namespace {
 
+constexpr int kG = 8;                  // lanes per unit
+constexpr int kUnitsPerWarp = 32 / kG;
+
 struct Cx {
     double re, im;
 };
 
-__device__ __forceinline__ double abs1(Cx a) { return fabs(a.re) + fabs(a.im); }
-__device__ __forceinline__ double absmax(Cx a) { return fmax(fabs(a.re), fabs(a.im)); }
+template <bool C>
 __device__ __forceinline__ Cx cmul(Cx a, Cx b) {
-    return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+    if (!C) return {a.re * b.re, 0.0};
+    return {fma(a.re, b.re, -a.im * b.im), fma(a.re, b.im, a.im * b.re)};
 }
 __device__ __forceinline__ Cx csub(Cx a, Cx b) { return {a.re - b.re, a.im - b.im}; }
 __device__ __forceinline__ Cx cscale(Cx a, int k) { return {scale2(a.re, k), scale2(a.im, k)}; }
+__device__ __forceinline__ long long cbits(Cx a) { return max(abs_bits(a.re), abs_bits(a.im)); }
 
-// a / b by Smith's method (no intermediate above ~2 max|a| / max|b|).
-__device__ __forceinline__ Cx cdiv(Cx a, Cx b) {
-    if (fabs(b.re) >= fabs(b.im)) {
-        double t = b.im / b.re, d = b.re + b.im * t;
-        return {(a.re + a.im * t) / d, (a.im - a.re * t) / d};
-    }
-    double t = b.re / b.im, d = b.im + b.re * t;
-    return {(a.re * t + a.im) / d, (a.im * t - a.re) / d};
+// 1 / a, a != 0: (re - i im) / (re^2 + im^2) after an exact power-of-two
+// normalisation of a.
+__device__ __forceinline__ Cx crcp(Cx a) {
+    if (a.im == 0.0) return {rcp_fast(a.re), 0.0};
+    const int k = ilog2_abs(__longlong_as_double(cbits(a)));
+    const double ar = scale2(a.re, -k), ai = scale2(a.im, -k);
+    const double id = rcp_fast(fma(ar, ar, ai * ai));
+    return {scale2(ar * id, -k), scale2(-ai * id, -k)};
 }
 
-__device__ __forceinline__ double warp_max(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
+// Factors of the shifted block system M = T_qq - lambda I (complete
+// pivoting for 2x2, pivots below smin replaced by smin).
+struct Fac {
+    Cx ia, l, g, iu;
+    int pr, pc;
+};
+
+// |a|_max key for pivot choice: high word of the larger component (the order
+// of non-negative doubles restricted to their high words; ties arbitrary)
+__device__ __forceinline__ int pkey(Cx a) {
+    return max(__double2hiint(a.re) & 0x7fffffff, __double2hiint(a.im) & 0x7fffffff);
+}
+// "below smin" on exponent fields: |a|_max < 2^(field(smin) - 1023) <= smin
+__device__ __forceinline__ bool tiny(Cx a, int fsmin) {
+    return max(efield(a.re), efield(a.im)) < fsmin;
 }
 
-// Solve the bs x bs shifted system at local row q; returns sc <= 0 and
-// z with M z = 2^sc rhs, |z| <= Omega.  Ts: tile in shared memory, ld ts.
-__device__ int small_solve(int bs, const double *Ts, int ts, int q, double lr, double li,
-                           double smin, Cx r0, Cx r1, Cx &z0, Cx &z1) {
-    z1 = {0.0, 0.0};
-    if (bs == 1 && li == 0.0) {
-        // real 1x1: the common case, decided directly on the pivot
-        double piv = Ts[q + q * ts] - lr;
-        if (fabs(piv) < smin) piv = smin;
-        const double rn = fabs(r0.re);
-        if (rn == 0.0) { z0 = {0.0, 0.0}; return 0; }
-        int sc = 0;
-        double rr = r0.re;
-        if (fabs(piv) < 1.0 && rn > kOmega * fabs(piv)) {
-            sc = ilog2_abs(kOmega * piv) - ilog2_abs(rn) - 1;
-            rr = scale2(rr, sc);
-        }
-        z0 = {rr / piv, 0.0};
-        return sc;
-    }
-    // general case: normalise the right-hand side, solve with complete
-    // pivoting, then fit the scale to the computed solution
-    double rn = fmax(absmax(r0), bs == 2 ? absmax(r1) : 0.0);
-    if (rn == 0.0) { z0 = {0.0, 0.0}; return 0; }
-    const int kr = ilog2_abs(rn) + 1;
-    Cx c0 = cscale(r0, -kr), c1 = cscale(r1, -kr);
-    Cx h0, h1 = {0.0, 0.0};
+template <bool C>
+__device__ Fac factor(int bs, const double *Ts, int ts, int q, double lr, double li, double smin) {
+    Fac F;
+    F.pr = F.pc = 0;
+    F.l = F.g = F.iu = {0.0, 0.0};
+    const int fsmin = efield(smin);
     if (bs == 1) {
-        Cx piv = {Ts[q + q * ts] - lr, -li};
-        if (abs1(piv) < smin) piv = {smin, 0.0};
-        h0 = cdiv(c0, piv);
-    } else {
-        Cx M[2][2];
-#pragma unroll
-        for (int a = 0; a < 2; a++)
-#pragma unroll
-            for (int b = 0; b < 2; b++) {
-                double t = Ts[(q + a) + (q + b) * ts];
-                M[a][b] = (a == b) ? Cx{t - lr, -li} : Cx{t, 0.0};
-            }
-        int pr = 0, pc = 0;
-        double best = -1.0;
-#pragma unroll
-        for (int a = 0; a < 2; a++)
-#pragma unroll
-            for (int b = 0; b < 2; b++)
-                if (abs1(M[a][b]) > best) { best = abs1(M[a][b]); pr = a; pc = b; }
-        Cx a11 = M[pr][pc], a12 = M[pr][1 - pc];
-        Cx a21 = M[1 - pr][pc], a22 = M[1 - pr][1 - pc];
-        Cx d1 = pr == 0 ? c0 : c1, d2 = pr == 0 ? c1 : c0;
-        if (abs1(a11) < smin) a11 = {smin, 0.0};
-        Cx l = cdiv(a21, a11);
-        Cx u = csub(a22, cmul(l, a12));
-        if (abs1(u) < smin) u = {smin, 0.0};
-        Cx w2 = cdiv(csub(d2, cmul(l, d1)), u);
-        Cx w1 = csub(cdiv(d1, a11), cmul(cdiv(a12, a11), w2));
-        // w1 belongs to column pc, w2 to column 1 - pc
-        h0 = pc == 0 ? w1 : w2;
-        h1 = pc == 0 ? w2 : w1;
+        Cx p = {Ts[q + q * ts] - lr, C ? -li : 0.0};
+        if (tiny(p, fsmin)) p = {smin, 0.0};
+        F.ia = crcp(p);
+        return F;
     }
-    double hn = fmax(absmax(h0), absmax(h1));
-    if (hn == 0.0) { z0 = {0.0, 0.0}; z1 = {0.0, 0.0}; return 0; }
-    int sc = kOmegaExp - ilog2_abs(hn) - 1 - kr;
+    Cx M[2][2];
+#pragma unroll
+    for (int a = 0; a < 2; a++)
+#pragma unroll
+        for (int b = 0; b < 2; b++) {
+            const double t = Ts[(q + a) + (q + b) * ts];
+            M[a][b] = (a == b) ? Cx{t - lr, C ? -li : 0.0} : Cx{t, 0.0};
+        }
+    int best = -1;
+#pragma unroll
+    for (int a = 0; a < 2; a++)
+#pragma unroll
+        for (int b = 0; b < 2; b++) {
+            const int v = pkey(M[a][b]);
+            if (v > best) { best = v; F.pr = a; F.pc = b; }
+        }
+    Cx a11 = M[F.pr][F.pc];
+    const Cx a12 = M[F.pr][1 - F.pc], a21 = M[1 - F.pr][F.pc], a22 = M[1 - F.pr][1 - F.pc];
+    if (tiny(a11, fsmin)) a11 = {smin, 0.0};
+    F.ia = crcp(a11);
+    F.l = cmul<C>(a21, F.ia);
+    F.g = cmul<C>(a12, F.ia);
+    Cx u = csub(a22, cmul<C>(F.l, a12));
+    if (tiny(u, fsmin)) u = {smin, 0.0};
+    F.iu = crcp(u);
+    return F;
+}
+
+template <bool C>
+__device__ __forceinline__ void apply(const Fac &F, int bs, Cx r0, Cx r1, Cx &z0, Cx &z1) {
+    if (bs == 1) {
+        z0 = cmul<C>(r0, F.ia);
+        z1 = {0.0, 0.0};
+        return;
+    }
+    const Cx d1 = F.pr == 0 ? r0 : r1, d2 = F.pr == 0 ? r1 : r0;
+    const Cx w2 = cmul<C>(csub(d2, cmul<C>(F.l, d1)), F.iu);
+    const Cx w1 = csub(cmul<C>(d1, F.ia), cmul<C>(F.g, w2));
+    z0 = F.pc == 0 ? w1 : w2;
+    z1 = F.pc == 0 ? w2 : w1;
+}
+
+// Solve with the division protection: the unnormalised application is
+// exact up to rounding whenever its result is finite and <= Omega (an
+// intermediate overflow always leaves an Inf or NaN in the result);
+// otherwise normalise the right-hand side, apply again and fit sc <= 0.
+template <bool C>
+__device__ __forceinline__ int solve(const Fac &F, int bs, Cx r0, Cx r1, Cx &z0, Cx &z1) {
+    apply<C>(F, bs, r0, r1, z0, z1);
+    // |z| < 2^1020 (and finite) on the exponent fields alone
+    const int fz = max(max(efield(z0.re), efield(z0.im)), max(efield(z1.re), efield(z1.im)));
+    if (fz <= 2042) return 0;
+    const long long rb = max(cbits(r0), cbits(r1));
+    if (rb == 0) { z0 = {0.0, 0.0}; z1 = {0.0, 0.0}; return 0; }
+    const int kr = ilog2_abs(__longlong_as_double(rb)) + 1;
+    Cx h0, h1;
+    apply<C>(F, bs, cscale(r0, -kr), cscale(r1, -kr), h0, h1);
+    const long long hb = max(cbits(h0), cbits(h1));
+    if (hb == 0) { z0 = {0.0, 0.0}; z1 = {0.0, 0.0}; return 0; }
+    int sc = kOmegaExp - ilog2_abs(__longlong_as_double(hb)) - 1 - kr;
     if (sc > 0) sc = 0;
     z0 = cscale(h0, kr + sc);
     z1 = cscale(h1, kr + sc);
     return sc;
 }
 
-}  // namespace
+__device__ __forceinline__ long long group_max_bits(long long v) {
+#pragma unroll
+    for (int o = kG / 2; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
 
-template <int NWARP>
-__global__ void __launch_bounds__(NWARP * 32)
-    k_diag_solve(int s, const double *__restrict__ T, int64_t ldt, Plan P,
-                 const double *__restrict__ tau, const double *__restrict__ blk_tau,
-                 double *__restrict__ Y, int64_t ldy, int32_t *__restrict__ seg_e,
-                 double *__restrict__ seg_nu, int32_t *__restrict__ seg_dx,
-                 int32_t *__restrict__ seg_dy) {
-    extern __shared__ double smem[];
-    const int t0 = P.tile_start[s];
-    const int ts = P.tile_start[s + 1] - t0;
-    double *Ts = smem;                                   // ts x ts, ld ts
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    double *yr = smem + ts * ts + warp * 2 * kMaxTile;
-    double *yi = yr + kMaxTile;
+__device__ __forceinline__ void cp_async8(void *smem_dst, const void *gsrc) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gsrc));
+}
 
-    for (int idx = threadIdx.x; idx < ts * ts; idx += NWARP * 32) {
-        const int i = idx % ts, j = idx / ts;
-        Ts[idx] = (i <= j + 1) ? T[(t0 + i) + (int64_t)(t0 + j) * ldt] : 0.0;
-    }
-    __syncthreads();
+struct Shared {
+    double *Ts, *btau, *yr, *yi, *umu, *fac;
+    int *bq, *bsz, *btf, *ucol, *uown, *ue, *facp;
+    int ys;   // padded row stride of the segment buffers (units per CTA + 1)
+};
 
-    const int u = P.tile_unit[s] + blockIdx.x * NWARP + warp;
-    if (u >= P.nunits) return;
-
-    const int64_t m = P.m;
-    const int col = P.unit_col[u];
-    const int kown = P.unit_blk[u];
-    const bool own = P.unit_tile[u] == s;
-    const double lr = P.unit_lam[2 * u], li = P.unit_lam[2 * u + 1];
-    const bool cplx = li != 0.0;
-    double smin = kUlp * (fabs(lr) + fabs(li));
-    smin = fmax(smin, kSafeMin * ((double)P.n / kUlp));
-    const int kb0 = P.tile_blk[s], kb1 = P.tile_blk[s + 1];
-
-    int e = 0;
-    double nu = 0.0;      // running upper bound on |rows above the current block|
-    int kfirst;           // first block to solve, going up
-
-    // scale every row of the segment (and the caller's z) by 2^g
-    auto scale_all = [&](int g) {
-        for (int i = lane; i < ts; i += 32) {
-            yr[i] = scale2(yr[i], g);
-            yi[i] = scale2(yi[i], g);
+// rows [0, q) of one unit -= T[0:q, q-block] z; the lane's rows in chunks of
+// 8 with every load of a chunk issued before its DFMAs
+template <bool C, int BS>
+__device__ __forceinline__ void update_rows(double *myr, double *myi, const double *c0,
+                                            const double *c1, int q, int g, Cx z0, Cx z1,
+                                            const int kYS) {
+    for (int j0 = 0; g + kG * j0 < q; j0 += 8) {
+        double a[8], b[8], ta[8], tb[8];
+#pragma unroll
+        for (int jj = 0; jj < 8; jj++) {
+            const int i = g + kG * (j0 + jj);
+            const bool ok = i < q;
+            a[jj] = ok ? myr[i * kYS] : 0.0;
+            b[jj] = (C && ok) ? myi[i * kYS] : 0.0;
+            ta[jj] = ok ? c0[i] : 0.0;
+            tb[jj] = (BS == 2 && ok) ? c1[i] : 0.0;
         }
-    };
-
-    // protected update of rows [0, q) from block k whose solution is z
-    auto update_from = [&](int k, int q, int bs, Cx z0, Cx z1) {
-        double mu = fmax(absmax(z0), absmax(z1));
-        const double tq = blk_tau[k];
-        int g = protect_update(nu, tq, mu);
-        if (g != 0) {
-            // the bound asks for a scaling: recompute the rows' true maximum
-            double loc = 0.0;
-            for (int i = lane; i < q; i += 32) loc = fmax(loc, fmax(fabs(yr[i]), fabs(yi[i])));
-            nu = warp_max(loc);
-            g = protect_update(nu, tq, mu);
-            if (g != 0) {
-                __syncwarp();
-                scale_all(g);
-                z0 = cscale(z0, g);
-                z1 = cscale(z1, g);
-                mu = scale2(mu, g);
-                nu = scale2(nu, g);
-                e += g;
+#pragma unroll
+        for (int jj = 0; jj < 8; jj++) {
+            const int i = g + kG * (j0 + jj);
+            if (i < q) {
+                double v = fma(-ta[jj], z0.re, a[jj]);
+                if (BS == 2) v = fma(-tb[jj], z1.re, v);
+                myr[i * kYS] = v;
+                if (C) {
+                    double w = fma(-ta[jj], z0.im, b[jj]);
+                    if (BS == 2) w = fma(-tb[jj], z1.im, w);
+                    myi[i * kYS] = w;
+                }
             }
-        }
-        __syncwarp();
-        const double *c0 = Ts + q * ts;
-        const double *c1 = Ts + (q + 1) * ts;
-        if (bs == 1) {
-            for (int i = lane; i < q; i += 32) {
-                const double t = c0[i];
-                yr[i] = fma(-t, z0.re, yr[i]);
-                yi[i] = fma(-t, z0.im, yi[i]);
-            }
-        } else {
-            for (int i = lane; i < q; i += 32) {
-                const double ta = c0[i], tb = c1[i];
-                yr[i] = fma(-tb, z1.re, fma(-ta, z0.re, yr[i]));
-                yi[i] = fma(-tb, z1.im, fma(-ta, z0.im, yi[i]));
-            }
-        }
-        nu = nu + tq * mu;
-        __syncwarp();
-    };
-
-    if (own) {
-        for (int i = lane; i < ts; i += 32) { yr[i] = 0.0; yi[i] = 0.0; }
-        __syncwarp();
-        const int q = P.blk_start[kown] - t0;
-        const int bs = P.blk_size[kown];
-        const double *o = P.unit_own + 4 * u;
-        Cx z0 = {o[0], o[2]}, z1 = {o[1], o[3]};
-        if (lane == 0) {
-            yr[q] = z0.re; yi[q] = z0.im;
-            if (bs == 2) { yr[q + 1] = z1.re; yi[q + 1] = z1.im; }
-        }
-        __syncwarp();
-        if (bs == 1) z1 = {0.0, 0.0};
-        if (q > 0) update_from(kown, q, bs, z0, z1);
-        kfirst = kown - 1;
-    } else {
-        const double *gr = Y + (int64_t)col * ldy + t0;
-        const double *gi = Y + (int64_t)(col + 1) * ldy + t0;
-        double loc = 0.0;
-        for (int i = lane; i < ts; i += 32) {
-            const double a = gr[i];
-            const double b = cplx ? gi[i] : 0.0;
-            yr[i] = a;
-            yi[i] = b;
-            loc = fmax(loc, fmax(fabs(a), fabs(b)));
-        }
-        nu = warp_max(loc);
-        e = seg_e[(int64_t)s * m + col];
-        kfirst = kb1 - 1;
-        __syncwarp();
-    }
-
-    for (int k = kfirst; k >= kb0; k--) {
-        const int q = P.blk_start[k] - t0;
-        const int bs = P.blk_size[k];
-        Cx r0 = {yr[q], yi[q]};
-        Cx r1 = bs == 2 ? Cx{yr[q + 1], yi[q + 1]} : Cx{0.0, 0.0};
-        Cx z0, z1;
-        const int sc = small_solve(bs, Ts, ts, q, lr, li, smin, r0, r1, z0, z1);
-        __syncwarp();
-        if (sc != 0) {
-            scale_all(sc);
-            nu = scale2(nu, sc);
-            e += sc;
-            __syncwarp();
-        }
-        if (lane == 0) {
-            yr[q] = z0.re; yi[q] = z0.im;
-            if (bs == 2) { yr[q + 1] = z1.re; yi[q + 1] = z1.im; }
-        }
-        __syncwarp();
-        if (q > 0) update_from(k, q, bs, z0, z1);
-    }
-
-    // write the solved segment back, with its exponent and column maxima
-    double mr = 0.0, mi = 0.0;
-    {
-        double *gr = Y + (int64_t)col * ldy + t0;
-        double *gi = Y + (int64_t)(col + 1) * ldy + t0;
-        for (int i = lane; i < ts; i += 32) {
-            gr[i] = yr[i];
-            mr = fmax(mr, fabs(yr[i]));
-            if (cplx) {
-                gi[i] = yi[i];
-                mi = fmax(mi, fabs(yi[i]));
-            }
-        }
-    }
-    mr = warp_max(mr);
-    mi = warp_max(mi);
-    if (lane == 0) {
-        seg_e[(int64_t)s * m + col] = e;
-        seg_nu[(int64_t)s * m + col] = mr;
-        if (cplx) {
-            seg_e[(int64_t)s * m + col + 1] = e;
-            seg_nu[(int64_t)s * m + col + 1] = mi;
-        }
-    }
-    const double mu_s = fmax(mr, mi);
-
-    // consolidation + protection decisions for the tiles above (Sec. 3.4)
-    for (int r = lane; r < s; r += 32) {
-        const int64_t at = (int64_t)r * m + col;
-        int er;
-        double nur;
-        if (own) {
-            er = e;
-            nur = 0.0;
-        } else {
-            er = seg_e[at];
-            nur = seg_nu[at];
-            if (cplx) nur = fmax(nur, seg_nu[at + 1]);
-        }
-        const int a = min(er, e);
-        const double nup = scale2(nur, a - er);
-        const double mup = scale2(mu_s, a - e);
-        const int g = protect_update(nup, tau[(int64_t)r * P.ntiles + s], mup);
-        const int ne = a + g;
-        seg_e[at] = ne;
-        seg_dx[at] = ne - e;
-        seg_dy[at] = own ? kFresh : ne - er;
-        if (cplx) {
-            seg_e[at + 1] = ne;
-            seg_dx[at + 1] = ne - e;
-            seg_dy[at + 1] = own ? kFresh : ne - er;
         }
     }
 }
 
-constexpr int kSolveWarps = 16;
+// The sequential part: one unit's backsubstitution through the tile.
+// Chain-side tests use exponent fields: nu < 2^Enu is an integer bound on
+// the rows above the current block, raised by one binade per update and
+// recomputed exactly only when the fast test cannot show nu + tau mu <= Omega.
+template <bool C>
+__device__ void solve_tile(const Shared &S, const Plan &P, int s, int ts, int kb0, int kb1,
+                           int slot, int g, bool valid, int u, int32_t *__restrict__ seg_e,
+                           double *__restrict__ seg_nu) {
+    const int64_t m = P.m;
+    const int nbt = kb1 - kb0;
+    const int kYS = S.ys;
+    const int col = valid ? P.unit_col[u] : 0;
+    const int kown = valid ? P.unit_blk[u] : -1;
+    const bool own = valid && P.unit_tile[u] == s;
+    const double lr = valid ? P.unit_lam[2 * u] : 0.0;
+    const double li = (C && valid) ? P.unit_lam[2 * u + 1] : 0.0;
+    const double smin = fmax(kUlp * (fabs(lr) + fabs(li)), kSafeMin * ((double)P.n / kUlp));
+    double *myr = S.yr + slot;
+    double *myi = S.yi + slot;
+    const double *Ts = S.Ts;
+    double *fac = S.fac + (size_t)slot * ts * 8;
+    int *facp = S.facp + slot * ts;
+
+    // factors of every block this unit solves, spread over its lanes
+    if (valid) {
+#pragma unroll 2
+        for (int kk = g; kk < nbt; kk += kG) {
+            if (own && kb0 + kk >= kown) continue;
+            const Fac F = factor<C>(S.bsz[kk], Ts, ts, S.bq[kk], lr, li, smin);
+            double *f = fac + kk * 8;
+            f[0] = F.ia.re; f[1] = F.ia.im; f[2] = F.l.re; f[3] = F.l.im;
+            f[4] = F.g.re;  f[5] = F.g.im;  f[6] = F.iu.re; f[7] = F.iu.im;
+            facp[kk] = F.pr | (F.pc << 1);
+        }
+    }
+
+    int e = 0;
+    long long nb = 0;
+    if (valid && !own) {
+        e = seg_e[(int64_t)s * m + col];
+        for (int i = g; i < ts; i += kG) {
+            nb = max(nb, abs_bits(myr[i * kYS]));
+            if (C) nb = max(nb, abs_bits(myi[i * kYS]));
+        }
+    }
+    int Enu = efield(__longlong_as_double(group_max_bits(nb))) - 1022;   // nu < 2^Enu
+    __syncwarp();
+
+    auto scale_rows = [&](int k) {
+        for (int i = g; i < ts; i += kG) {
+            myr[i * kYS] = scale2(myr[i * kYS], k);
+            if (C) myi[i * kYS] = scale2(myi[i * kYS], k);
+        }
+    };
+
+    for (int k = kb1 - 1; k >= kb0; k--) {
+        const int kk = k - kb0;
+        const int q = S.bq[kk];
+        const int bs = S.bsz[kk];
+        const int ftq = S.btf[kk];
+        const bool act = valid && (!own || k <= kown);
+        const bool solving = act && !(own && k == kown);
+        Cx z0 = {0.0, 0.0}, z1 = {0.0, 0.0};
+        const Cx r0 = {myr[q * kYS], C ? myi[q * kYS] : 0.0};
+        const Cx r1 = bs == 2 ? Cx{myr[(q + 1) * kYS], C ? myi[(q + 1) * kYS] : 0.0} : Cx{0.0, 0.0};
+        Fac F;
+        {
+            const double *f = fac + kk * 8;
+            F.ia = {f[0], C ? f[1] : 0.0};
+            F.l = {f[2], C ? f[3] : 0.0};
+            F.g = {f[4], C ? f[5] : 0.0};
+            F.iu = {f[6], C ? f[7] : 0.0};
+            const int pp = facp[kk];
+            F.pr = pp & 1;
+            F.pc = pp >> 1;
+        }
+        __syncwarp();
+        if (act) {
+            int sc = 0;
+            if (!solving) {
+                const double *o = P.unit_own + 4 * u;
+                z0 = {o[0], C ? o[2] : 0.0};
+                z1 = {o[1], C ? o[3] : 0.0};
+            } else {
+                sc = solve<C>(F, bs, r0, r1, z0, z1);
+            }
+            if (sc != 0) {
+                scale_rows(sc);
+                Enu += sc;
+                e += sc;
+            }
+            if (g == q % kG) { myr[q * kYS] = z0.re; if (C) myi[q * kYS] = z0.im; }
+            if (bs == 2 && g == (q + 1) % kG) {
+                myr[(q + 1) * kYS] = z1.re;
+                if (C) myi[(q + 1) * kYS] = z1.im;
+            }
+        }
+        // protection of the update of rows [0, q): fast test on exponents,
+        // exact FP64 test only when it cannot decide
+        int fmu = max(max(efield(z0.re), efield(z0.im)), max(efield(z1.re), efield(z1.im)));
+        const bool trig = act && q > 0 && (Enu > 1019 || fmu + ftq > 3063);
+        if (__any_sync(0xffffffffu, trig)) {
+            long long b = 0;
+            if (trig)
+                for (int i = g; i < q; i += kG) {
+                    b = max(b, abs_bits(myr[i * kYS]));
+                    if (C) b = max(b, abs_bits(myi[i * kYS]));
+                }
+            b = group_max_bits(b);
+            if (trig) {
+                double nu = __longlong_as_double(b);
+                const double mu = __longlong_as_double(max(cbits(z0), cbits(z1)));
+                const int g2 = protect_update(nu, S.btau[kk], mu);
+                if (g2 != 0) {
+                    scale_rows(g2);
+                    z0 = cscale(z0, g2);
+                    z1 = cscale(z1, g2);
+                    nu = scale2(nu, g2);
+                    e += g2;
+                    fmu = max(max(efield(z0.re), efield(z0.im)), max(efield(z1.re), efield(z1.im)));
+                }
+                Enu = efield(nu) - 1022;
+            }
+        }
+        if (act && q > 0) {
+            const double *c0 = Ts + q * ts;
+            if (bs == 1) update_rows<C, 1>(myr, myi, c0, c0, q, g, z0, z1, kYS);
+            else update_rows<C, 2>(myr, myi, c0, c0 + ts, q, g, z0, z1, kYS);
+            Enu = max(Enu, fmu + ftq - 2044) + 1;
+        }
+        __syncwarp();
+    }
+    // segment maxima per column, exponent (for the decisions and the next steps)
+    long long br = 0, bi = 0;
+    for (int i = g; i < ts; i += kG) {
+        br = max(br, abs_bits(myr[i * kYS]));
+        if (C) bi = max(bi, abs_bits(myi[i * kYS]));
+    }
+    br = group_max_bits(br);
+    bi = group_max_bits(bi);
+    if (g == 0) {
+        S.ue[slot] = e;
+        S.umu[slot] = __longlong_as_double(max(br, bi));
+        if (valid) {
+            seg_e[(int64_t)s * m + col] = e;
+            seg_nu[(int64_t)s * m + col] = __longlong_as_double(br);
+            if (C) {
+                seg_e[(int64_t)s * m + col + 1] = e;
+                seg_nu[(int64_t)s * m + col + 1] = __longlong_as_double(bi);
+            }
+        }
+    }
+}
+
+}  // namespace
+
+template <int W>
+__global__ void __launch_bounds__(32 * W)
+    k_diag_solve(int s, int nreal_ctas, const double *__restrict__ T, int64_t ldt, Plan P,
+                 const double *__restrict__ tau, const double *__restrict__ blk_tau,
+                 double *__restrict__ Y, int64_t ldy, int32_t *__restrict__ seg_e,
+                 double *__restrict__ seg_nu, int32_t *__restrict__ seg_dx,
+                 int32_t *__restrict__ seg_dy) {
+    constexpr int kThreads = 32 * W;
+    constexpr int kUnits = kUnitsPerWarp * W;
+    constexpr int kYS = kUnits + 1;
+    extern __shared__ double smem[];
+    const int t0 = P.tile_start[s];
+    const int ts = P.tile_start[s + 1] - t0;
+    const int kb0 = P.tile_blk[s], kb1 = P.tile_blk[s + 1];
+    const int nbt = kb1 - kb0;
+    Shared S;
+    S.Ts = smem;                              // ts x ts, ld ts
+    S.btau = S.Ts + ts * ts;                  // [kMaxTile]
+    S.umu = S.btau + kMaxTile;                // [kUnits]
+    S.yr = S.umu + kUnits;                    // [ts][kYS]
+    S.yi = S.yr + ts * kYS;                   // [ts][kYS]
+    S.fac = S.yi + ts * kYS;                  // [kUnits][ts][8] block factors
+    S.bq = (int *)(S.fac + (size_t)kUnits * ts * 8);  // [kMaxTile]
+    S.bsz = S.bq + kMaxTile;                  // [kMaxTile]
+    S.btf = S.bsz + kMaxTile;                 // [kMaxTile] exponent fields of btau
+    S.ucol = S.btf + kMaxTile;                // [kUnits] column, -1 = none
+    S.uown = S.ucol + kUnits;                 // [kUnits]
+    S.ue = S.uown + kUnits;                   // [kUnits]
+    S.facp = S.ue + kUnits;                   // [kUnits][ts] pivot positions
+    S.ys = kYS;
+
+    const bool cplx = blockIdx.x >= nreal_ctas;
+    const int32_t *ord = cplx ? P.ord_cplx : P.ord_real;
+    const int list_end = cplx ? P.ncplx : P.nreal;
+    const int list_pos0 = (cplx ? P.tile_cplx[s] + (blockIdx.x - nreal_ctas) * kUnits
+                                : P.tile_real[s] + blockIdx.x * kUnits);
+    const int tid = threadIdx.x;
+
+    // diagonal tile (upper part and first subdiagonal only), asynchronously
+    for (int j = 0; j < ts; j++) {
+        const int iend = min(j + 2, ts);
+        const double *src = T + t0 + (int64_t)(t0 + j) * ldt;
+        for (int i = tid; i < ts; i += kThreads) {
+            if (i < iend) cp_async8(&S.Ts[i + j * ts], src + i);
+            else S.Ts[i + j * ts] = 0.0;
+        }
+    }
+    asm volatile("cp.async.commit_group;");
+    for (int k = tid; k < nbt; k += kThreads) {
+        S.bq[k] = P.blk_start[kb0 + k] - t0;
+        S.bsz[k] = P.blk_size[kb0 + k];
+        S.btau[k] = blk_tau[kb0 + k];
+        S.btf[k] = efield(blk_tau[kb0 + k]);
+    }
+    if (tid < kUnits) {
+        const int pos = list_pos0 + tid;
+        int c = -1, own = 0;
+        if (pos < list_end) {
+            const int u = ord[pos];
+            c = P.unit_col[u];
+            own = P.unit_tile[u] == s;
+        }
+        S.ucol[tid] = c;
+        S.uown[tid] = own;
+    }
+    __syncthreads();   // the unit map is read by every warp below
+    // the segments, column by column (coalesced); own units start at zero
+    for (int idx = tid; idx < kUnits * ts; idx += kThreads) {
+        const int uu = idx / ts, i = idx % ts;
+        const int c = S.ucol[uu];
+        if (c >= 0 && !S.uown[uu]) {
+            cp_async8(&S.yr[i * kYS + uu], &Y[(t0 + i) + (int64_t)c * ldy]);
+            if (cplx) cp_async8(&S.yi[i * kYS + uu], &Y[(t0 + i) + (int64_t)(c + 1) * ldy]);
+            else S.yi[i * kYS + uu] = 0.0;
+        } else {
+            S.yr[i * kYS + uu] = 0.0;
+            S.yi[i * kYS + uu] = 0.0;
+        }
+    }
+    asm volatile("cp.async.commit_group;");
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+
+    const int slot = tid / kG, g = tid % kG;
+    const int pos = list_pos0 + slot;
+    const bool valid = pos < list_end;
+    const int u = valid ? ord[pos] : 0;
+    if (cplx) solve_tile<true>(S, P, s, ts, kb0, kb1, slot, g, valid, u, seg_e, seg_nu);
+    else solve_tile<false>(S, P, s, ts, kb0, kb1, slot, g, valid, u, seg_e, seg_nu);
+    __syncthreads();
+
+    // write the solved segments back (coalesced) with exponents and maxima
+    for (int idx = tid; idx < kUnits * ts; idx += kThreads) {
+        const int uu = idx / ts, i = idx % ts;
+        const int c = S.ucol[uu];
+        if (c >= 0) {
+            Y[(t0 + i) + (int64_t)c * ldy] = S.yr[i * kYS + uu];
+            if (cplx) Y[(t0 + i) + (int64_t)(c + 1) * ldy] = S.yi[i * kYS + uu];
+        }
+    }
+    const int64_t m = P.m;
+    // consolidation + protection decisions for the tiles above (Sec. 3.4):
+    // thread -> (unit, tile row), consecutive threads on consecutive columns;
+    // four items per thread per round so their loads are in flight together
+    constexpr int kBatch = 4;
+    const int items = kUnits * s;
+    for (int base = tid; base < items; base += kBatch * kThreads) {
+        int er[kBatch];
+        double nur[kBatch];
+#pragma unroll
+        for (int j = 0; j < kBatch; j++) {
+            const int idx = base + j * kThreads;
+            er[j] = 0;
+            nur[j] = 0.0;
+            if (idx < items) {
+                const int uu = idx % kUnits, r = idx / kUnits;
+                const int c = S.ucol[uu];
+                if (c >= 0 && !S.uown[uu]) {
+                    const int64_t at = (int64_t)r * m + c;
+                    er[j] = seg_e[at];
+                    nur[j] = seg_nu[at];
+                    if (cplx) nur[j] = fmax(nur[j], seg_nu[at + 1]);
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kBatch; j++) {
+            const int idx = base + j * kThreads;
+            if (idx >= items) continue;
+            const int uu = idx % kUnits, r = idx / kUnits;
+            const int c = S.ucol[uu];
+            if (c < 0) continue;
+            const int64_t at = (int64_t)r * m + c;
+            const int es = S.ue[uu];
+            const bool own = S.uown[uu];
+            const int e_r = own ? es : er[j];
+            const int a = min(e_r, es);
+            const double nup = own ? 0.0 : scale2(nur[j], a - e_r);
+            const double mup = scale2(S.umu[uu], a - es);
+            const int g2 = protect_update(nup, tau[(int64_t)r * P.ntiles + s], mup);
+            const int ne = a + g2;
+            seg_e[at] = ne;
+            seg_dx[at] = ne - es;
+            seg_dy[at] = own ? kFresh : ne - e_r;
+            if (cplx) {
+                seg_e[at + 1] = ne;
+                seg_dx[at + 1] = ne - es;
+                seg_dy[at + 1] = own ? kFresh : ne - e_r;
+            }
+        }
+    }
+}
+
+template <int W>
+static size_t diag_smem_bytes(int t) {
+    constexpr int kUnits = kUnitsPerWarp * W;
+    return sizeof(double) * ((size_t)t * t + kMaxTile + kUnits + 2 * (size_t)t * (kUnits + 1) +
+                             (size_t)kUnits * t * 8) +
+           sizeof(int) * (3 * (size_t)kMaxTile + 3 * kUnits + (size_t)kUnits * t);
+}
+
+template <int W>
+static void launch_w(int s, int ts, int nr, int nc, const double *T, int64_t ldt, const Plan &p,
+                     const double *tau, const double *blk_tau, double *Y, int64_t ldy,
+                     int32_t *seg_e, double *seg_nu, int32_t *seg_dx, int32_t *seg_dy,
+                     cudaStream_t st) {
+    constexpr int kUnits = kUnitsPerWarp * W;
+    const int rct = (nr + kUnits - 1) / kUnits;
+    const int cct = (nc + kUnits - 1) / kUnits;
+    if (rct + cct == 0) return;
+    cudaFuncSetAttribute(k_diag_solve<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)diag_smem_bytes<W>(W == 4 ? 64 : kMaxTile));
+    k_diag_solve<W><<<rct + cct, 32 * W, diag_smem_bytes<W>(ts), st>>>(
+        s, rct, T, ldt, p, tau, blk_tau, Y, ldy, seg_e, seg_nu, seg_dx, seg_dy);
+}
 
 void launch_diag_solve(int s, const double *T, int64_t ldt, const Plan &p,
-                       const int32_t *tile_start_h, const int32_t *tile_unit_h,
-                       const double *tau, const double *blk_tau, double *Y, int64_t ldy,
-                       int32_t *seg_e, double *seg_nu, int32_t *seg_dx, int32_t *seg_dy,
-                       cudaStream_t st) {
+                       const int32_t *tile_start_h, const int32_t *tile_real_h,
+                       const int32_t *tile_cplx_h, const double *tau, const double *blk_tau,
+                       double *Y, int64_t ldy, int32_t *seg_e, double *seg_nu, int32_t *seg_dx,
+                       int32_t *seg_dy, cudaStream_t st) {
     const int ts = tile_start_h[s + 1] - tile_start_h[s];
-    const int units = p.nunits - tile_unit_h[s];
-    if (units <= 0) return;
-    const int blocks = (units + kSolveWarps - 1) / kSolveWarps;
-    const size_t shm = sizeof(double) * ((size_t)ts * ts + (size_t)kSolveWarps * 2 * kMaxTile);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(k_diag_solve<kSolveWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(sizeof(double) * ((size_t)kMaxTile * kMaxTile +
-                                                     (size_t)kSolveWarps * 2 * kMaxTile)));
-        attr_set = true;
-    }
-    k_diag_solve<kSolveWarps><<<blocks, kSolveWarps * 32, shm, st>>>(
-        s, T, ldt, p, tau, blk_tau, Y, ldy, seg_e, seg_nu, seg_dx, seg_dy);
+    const int nr = p.nreal - tile_real_h[s];
+    const int nc = p.ncplx - tile_cplx_h[s];
+    // four warps (16 units) share a tile of up to 64 rows; two for larger tiles
+    if (ts <= 64)
+        launch_w<4>(s, ts, nr, nc, T, ldt, p, tau, blk_tau, Y, ldy, seg_e, seg_nu, seg_dx, seg_dy, st);
+    else
+        launch_w<2>(s, ts, nr, nc, T, ldt, p, tau, blk_tau, Y, ldy, seg_e, seg_nu, seg_dx, seg_dy, st);
 }
 
 }  // namespace evec
