@@ -3,13 +3,15 @@
 // decisions for every tile above it (Sec. 3.4, the preprocessing step of the
 // update Z <- Y - T X).
 //
-// Work split: G = 8 lanes per unit (a real eigenvalue, or a complex pair
-// solved as one complex column), 4 units per warp, CTAs of W = 4 warps
+// Work split: G lanes per unit -- G = 8 for a real eigenvalue, G = 16 for a
+// complex pair solved as one complex column -- and CTAs of W = 4 warps
 // (W = 2 for tiles above 64 rows); real and complex units in separate CTAs
 // of one launch.  On B300 one SM sub-partition issues at most one FP64
-// warp-instruction per 64 cycles, so the FP64 instructions of a unit's
-// chain are spread thin: about one update row per lane per block step, and
-// the W warps of a CTA land on different sub-partitions.  Row i of a unit's segment
+// warp-instruction per 64 cycles, and an FP64 instruction costs that slot
+// whether its lanes are active, masked or predicated off, so the FP64
+// instructions of a unit's chain are spread thin (a few update rows per
+// lane per block step, loop trip counts uniform across the warp) and the W
+// warps of a CTA land on different sub-partitions.  Row i of a unit's segment
 // belongs to lane i mod G.  The block solves form a sequential chain per
 // unit, and a warp issues in order, so the chain is kept short: the
 // factors of every shifted 1x1/2x2 block system of the tile are computed
@@ -36,14 +38,19 @@
 // the update Y_r <- Y_r - T_rs X_s: a = min(e_r, e_s), protection q of
 // (nu_r 2^(a-e_r), tau_rs, mu_s 2^(a-e_s)), new e_r = a + q,
 // dy = a + q - e_r (scale of Y_r), dx = a + q - e_s (scale of X_s).
+#include <algorithm>
+
 #include "evec_internal.cuh"
 
 namespace evec {
 
 namespace {
 
-constexpr int kG = 8;                  // lanes per unit
-constexpr int kUnitsPerWarp = 32 / kG;
+template <bool C>
+struct Lanes {
+    static constexpr int G = C ? 16 : 8;     // lanes per unit
+    static constexpr int U = 32 / G;         // units per warp
+};
 
 struct Cx {
     double re, im;
@@ -133,8 +140,21 @@ __device__ __forceinline__ void apply(const Fac &F, int bs, Cx r0, Cx r1, Cx &z0
         return;
     }
     const Cx d1 = F.pr == 0 ? r0 : r1, d2 = F.pr == 0 ? r1 : r0;
-    const Cx w2 = cmul<C>(csub(d2, cmul<C>(F.l, d1)), F.iu);
-    const Cx w1 = csub(cmul<C>(d1, F.ia), cmul<C>(F.g, w2));
+    Cx t;   // d2 - l d1, fused
+    if (C) {
+        t.re = fma(-F.l.re, d1.re, fma(F.l.im, d1.im, d2.re));
+        t.im = fma(-F.l.re, d1.im, fma(-F.l.im, d1.re, d2.im));
+    } else {
+        t = {fma(-F.l.re, d1.re, d2.re), 0.0};
+    }
+    const Cx w2 = cmul<C>(t, F.iu);
+    Cx w1;  // d1 ia - g w2, fused
+    if (C) {
+        w1.re = fma(d1.re, F.ia.re, fma(-d1.im, F.ia.im, fma(-F.g.re, w2.re, F.g.im * w2.im)));
+        w1.im = fma(d1.re, F.ia.im, fma(d1.im, F.ia.re, fma(-F.g.re, w2.im, -F.g.im * w2.re)));
+    } else {
+        w1 = {fma(d1.re, F.ia.re, -F.g.re * w2.re), 0.0};
+    }
     z0 = F.pc == 0 ? w1 : w2;
     z1 = F.pc == 0 ? w2 : w1;
 }
@@ -163,9 +183,10 @@ __device__ __forceinline__ int solve(const Fac &F, int bs, Cx r0, Cx r1, Cx &z0,
     return sc;
 }
 
+template <int G>
 __device__ __forceinline__ long long group_max_bits(long long v) {
 #pragma unroll
-    for (int o = kG / 2; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    for (int o = G / 2; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
 }
 
@@ -174,119 +195,198 @@ __device__ __forceinline__ void cp_async8(void *smem_dst, const void *gsrc) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gsrc));
 }
 
-struct Shared {
-    double *Ts, *btau, *yr, *yi, *umu, *fac;
-    int *bq, *bsz, *btf, *ucol, *uown, *ue, *facp;
-    int ys;   // padded row stride of the segment buffers (units per CTA + 1)
-};
-
-// rows [0, q) of one unit -= T[0:q, q-block] z; the lane's rows in chunks of
-// 8 with every load of a chunk issued before its DFMAs
-template <bool C, int BS>
+// rows [0, q) of one unit -= T[0:q, q-block] z: the lane's rows g, g + G, ...
+// with a trip count uniform across the warp, two rows per step (loads first)
+template <bool C, int BS, int G>
 __device__ __forceinline__ void update_rows(double *myr, double *myi, const double *c0,
                                             const double *c1, int q, int g, Cx z0, Cx z1,
-                                            const int kYS) {
-    for (int j0 = 0; g + kG * j0 < q; j0 += 8) {
-        double a[8], b[8], ta[8], tb[8];
-#pragma unroll
-        for (int jj = 0; jj < 8; jj++) {
-            const int i = g + kG * (j0 + jj);
-            const bool ok = i < q;
-            a[jj] = ok ? myr[i * kYS] : 0.0;
-            b[jj] = (C && ok) ? myi[i * kYS] : 0.0;
-            ta[jj] = ok ? c0[i] : 0.0;
-            tb[jj] = (BS == 2 && ok) ? c1[i] : 0.0;
+                                            int ys) {
+    const int n = (q + G - 1) / G;
+    int j = 0;
+    for (; j + 2 <= n; j += 2) {
+        const int i0 = g + G * j, i1 = i0 + G;
+        const bool ok1 = i1 < q;            // only the last pair can be partial
+        const double a0 = myr[i0 * ys], a1 = ok1 ? myr[i1 * ys] : 0.0;
+        const double b0 = C ? myi[i0 * ys] : 0.0, b1 = (C && ok1) ? myi[i1 * ys] : 0.0;
+        const double t0 = c0[i0], t1 = ok1 ? c0[i1] : 0.0;
+        const double u0 = BS == 2 ? c1[i0] : 0.0, u1 = (BS == 2 && ok1) ? c1[i1] : 0.0;
+        double v0 = fma(-t0, z0.re, a0), v1 = fma(-t1, z0.re, a1);
+        if (BS == 2) { v0 = fma(-u0, z1.re, v0); v1 = fma(-u1, z1.re, v1); }
+        myr[i0 * ys] = v0;
+        if (ok1) myr[i1 * ys] = v1;
+        if (C) {
+            double w0 = fma(-t0, z0.im, b0), w1 = fma(-t1, z0.im, b1);
+            if (BS == 2) { w0 = fma(-u0, z1.im, w0); w1 = fma(-u1, z1.im, w1); }
+            myi[i0 * ys] = w0;
+            if (ok1) myi[i1 * ys] = w1;
         }
-#pragma unroll
-        for (int jj = 0; jj < 8; jj++) {
-            const int i = g + kG * (j0 + jj);
-            if (i < q) {
-                double v = fma(-ta[jj], z0.re, a[jj]);
-                if (BS == 2) v = fma(-tb[jj], z1.re, v);
-                myr[i * kYS] = v;
-                if (C) {
-                    double w = fma(-ta[jj], z0.im, b[jj]);
-                    if (BS == 2) w = fma(-tb[jj], z1.im, w);
-                    myi[i * kYS] = w;
-                }
+    }
+    if (j < n) {
+        const int i = g + G * j;
+        if (i < q) {
+            double v = fma(-c0[i], z0.re, myr[i * ys]);
+            if (BS == 2) v = fma(-c1[i], z1.re, v);
+            myr[i * ys] = v;
+            if (C) {
+                double w = fma(-c0[i], z0.im, myi[i * ys]);
+                if (BS == 2) w = fma(-c1[i], z1.im, w);
+                myi[i * ys] = w;
             }
         }
     }
 }
 
-// The sequential part: one unit's backsubstitution through the tile.
-// Chain-side tests use exponent fields: nu < 2^Enu is an integer bound on
-// the rows above the current block, raised by one binade per update and
-// recomputed exactly only when the fast test cannot show nu + tau mu <= Omega.
-template <bool C>
-__device__ void solve_tile(const Shared &S, const Plan &P, int s, int ts, int kb0, int kb1,
-                           int slot, int g, bool valid, int u, int32_t *__restrict__ seg_e,
-                           double *__restrict__ seg_nu) {
-    const int64_t m = P.m;
+// The whole kernel for one kind of unit (real or complex) and W warps.
+template <int W, bool C>
+__device__ void diag_tile(int s, int list_pos0, const double *__restrict__ T, int64_t ldt,
+                          const Plan &P, const double *__restrict__ tau,
+                          const double *__restrict__ blk_tau, double *__restrict__ Y, int64_t ldy,
+                          int32_t *__restrict__ seg_e, double *__restrict__ seg_nu,
+                          int32_t *__restrict__ seg_dx, int32_t *__restrict__ seg_dy,
+                          double *smem) {
+    constexpr int G = Lanes<C>::G;
+    constexpr int kThreads = 32 * W;
+    constexpr int kUnits = Lanes<C>::U * W;
+    constexpr int ys = kUnits + 1;
+    const int t0 = P.tile_start[s];
+    const int ts = P.tile_start[s + 1] - t0;
+    const int kb0 = P.tile_blk[s], kb1 = P.tile_blk[s + 1];
     const int nbt = kb1 - kb0;
-    const int kYS = S.ys;
+    const int32_t *ord = C ? P.ord_cplx : P.ord_real;
+    const int list_end = C ? P.ncplx : P.nreal;
+    const int64_t m = P.m;
+    const int tid = threadIdx.x;
+
+    // shared layout
+    double *Ts = smem;                                 // ts x ts, ld ts
+    double *btau = Ts + ts * ts;                       // [kMaxTile]
+    double *umu = btau + kMaxTile;                     // [kUnits]
+    double *yr = umu + kUnits;                         // [ts][ys]
+    double *yi = yr + ts * ys;                         // [ts][ys]
+    double *fac = yi + ts * ys;                        // [kUnits][ts][8]
+    int *bq = (int *)(fac + (size_t)kUnits * ts * 8);  // [kMaxTile]
+    int *bsz = bq + kMaxTile;                          // [kMaxTile]
+    int *btf = bsz + kMaxTile;                         // [kMaxTile] exponent field of btau
+    int *ford = btf + kMaxTile;                        // [kMaxTile] 1x1 blocks, then 2x2
+    int *ucol = ford + kMaxTile;                       // [kUnits] column, -1 = none
+    int *uown = ucol + kUnits;                         // [kUnits]
+    int *ue = uown + kUnits;                           // [kUnits]
+    int *facp = ue + kUnits;                           // [kUnits][ts] pivot positions
+
+    // diagonal tile (upper part and first subdiagonal only), asynchronously
+    for (int idx = tid; idx < ts * ts; idx += kThreads) {
+        const int i = idx % ts, j = idx / ts;
+        if (i <= j + 1) cp_async8(&Ts[idx], T + (t0 + i) + (int64_t)(t0 + j) * ldt);
+        else Ts[idx] = 0.0;
+    }
+    asm volatile("cp.async.commit_group;");
+    for (int k = tid; k < nbt; k += kThreads) {
+        bq[k] = P.blk_start[kb0 + k] - t0;
+        bsz[k] = P.blk_size[kb0 + k];
+        btau[k] = blk_tau[kb0 + k];
+        btf[k] = efield(blk_tau[kb0 + k]);
+    }
+    if (tid < kUnits) {
+        const int pos = list_pos0 + tid;
+        int c = -1, own = 0;
+        if (pos < list_end) {
+            const int u = ord[pos];
+            c = P.unit_col[u];
+            own = P.unit_tile[u] == s;
+        }
+        ucol[tid] = c;
+        uown[tid] = own;
+    }
+    __syncthreads();   // block list and unit map are read by every warp below
+    if (tid == 0) {    // factor order: all 1x1 blocks, then all 2x2 blocks
+        int f = 0;
+        for (int k = 0; k < nbt; k++) if (bsz[k] == 1) ford[f++] = k;
+        for (int k = 0; k < nbt; k++) if (bsz[k] == 2) ford[f++] = k;
+    }
+    // the segments, column by column (coalesced); own units start at zero
+    for (int idx = tid; idx < kUnits * ts; idx += kThreads) {
+        const int uu = idx / ts, i = idx % ts;
+        const int c = ucol[uu];
+        if (c >= 0 && !uown[uu]) {
+            cp_async8(&yr[i * ys + uu], &Y[(t0 + i) + (int64_t)c * ldy]);
+            if (C) cp_async8(&yi[i * ys + uu], &Y[(t0 + i) + (int64_t)(c + 1) * ldy]);
+            else yi[i * ys + uu] = 0.0;
+        } else {
+            yr[i * ys + uu] = 0.0;
+            yi[i * ys + uu] = 0.0;
+        }
+    }
+    asm volatile("cp.async.commit_group;");
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+
+    // ---- one unit per G lanes --------------------------------------------
+    const int slot = tid / G, g = tid % G;
+    const int pos = list_pos0 + slot;
+    const bool valid = pos < list_end;
+    const int u = valid ? ord[pos] : 0;
     const int col = valid ? P.unit_col[u] : 0;
     const int kown = valid ? P.unit_blk[u] : -1;
     const bool own = valid && P.unit_tile[u] == s;
     const double lr = valid ? P.unit_lam[2 * u] : 0.0;
     const double li = (C && valid) ? P.unit_lam[2 * u + 1] : 0.0;
     const double smin = fmax(kUlp * (fabs(lr) + fabs(li)), kSafeMin * ((double)P.n / kUlp));
-    double *myr = S.yr + slot;
-    double *myi = S.yi + slot;
-    const double *Ts = S.Ts;
-    double *fac = S.fac + (size_t)slot * ts * 8;
-    int *facp = S.facp + slot * ts;
+    double *myr = yr + slot;
+    double *myi = yi + slot;
+    double *myfac = fac + (size_t)slot * ts * 8;
+    int *myfacp = facp + slot * ts;
 
-    // factors of every block this unit solves, spread over its lanes
+    // factors of every block this unit solves, spread over its lanes in
+    // size order (lanes of a warp take the same branch)
     if (valid) {
-#pragma unroll 2
-        for (int kk = g; kk < nbt; kk += kG) {
+        for (int f = g; f < nbt; f += G) {
+            const int kk = ford[f];
             if (own && kb0 + kk >= kown) continue;
-            const Fac F = factor<C>(S.bsz[kk], Ts, ts, S.bq[kk], lr, li, smin);
-            double *f = fac + kk * 8;
-            f[0] = F.ia.re; f[1] = F.ia.im; f[2] = F.l.re; f[3] = F.l.im;
-            f[4] = F.g.re;  f[5] = F.g.im;  f[6] = F.iu.re; f[7] = F.iu.im;
-            facp[kk] = F.pr | (F.pc << 1);
+            const Fac F = factor<C>(bsz[kk], Ts, ts, bq[kk], lr, li, smin);
+            double *fp = myfac + kk * 8;
+            fp[0] = F.ia.re; fp[1] = F.ia.im; fp[2] = F.l.re; fp[3] = F.l.im;
+            fp[4] = F.g.re;  fp[5] = F.g.im;  fp[6] = F.iu.re; fp[7] = F.iu.im;
+            myfacp[kk] = F.pr | (F.pc << 1);
         }
     }
 
     int e = 0;
-    long long nb = 0;
+    long long nbits = 0;
     if (valid && !own) {
         e = seg_e[(int64_t)s * m + col];
-        for (int i = g; i < ts; i += kG) {
-            nb = max(nb, abs_bits(myr[i * kYS]));
-            if (C) nb = max(nb, abs_bits(myi[i * kYS]));
+        for (int i = g; i < ts; i += G) {
+            nbits = max(nbits, abs_bits(myr[i * ys]));
+            if (C) nbits = max(nbits, abs_bits(myi[i * ys]));
         }
     }
-    int Enu = efield(__longlong_as_double(group_max_bits(nb))) - 1022;   // nu < 2^Enu
+    int Enu = efield(__longlong_as_double(group_max_bits<G>(nbits))) - 1022;   // nu < 2^Enu
     __syncwarp();
 
     auto scale_rows = [&](int k) {
-        for (int i = g; i < ts; i += kG) {
-            myr[i * kYS] = scale2(myr[i * kYS], k);
-            if (C) myi[i * kYS] = scale2(myi[i * kYS], k);
+        for (int i = g; i < ts; i += G) {
+            myr[i * ys] = scale2(myr[i * ys], k);
+            if (C) myi[i * ys] = scale2(myi[i * ys], k);
         }
     };
 
     for (int k = kb1 - 1; k >= kb0; k--) {
         const int kk = k - kb0;
-        const int q = S.bq[kk];
-        const int bs = S.bsz[kk];
-        const int ftq = S.btf[kk];
+        const int q = bq[kk];
+        const int bs = bsz[kk];
+        const int ftq = btf[kk];
         const bool act = valid && (!own || k <= kown);
         const bool solving = act && !(own && k == kown);
         Cx z0 = {0.0, 0.0}, z1 = {0.0, 0.0};
-        const Cx r0 = {myr[q * kYS], C ? myi[q * kYS] : 0.0};
-        const Cx r1 = bs == 2 ? Cx{myr[(q + 1) * kYS], C ? myi[(q + 1) * kYS] : 0.0} : Cx{0.0, 0.0};
+        const Cx r0 = {myr[q * ys], C ? myi[q * ys] : 0.0};
+        const Cx r1 = bs == 2 ? Cx{myr[(q + 1) * ys], C ? myi[(q + 1) * ys] : 0.0} : Cx{0.0, 0.0};
         Fac F;
         {
-            const double *f = fac + kk * 8;
-            F.ia = {f[0], C ? f[1] : 0.0};
-            F.l = {f[2], C ? f[3] : 0.0};
-            F.g = {f[4], C ? f[5] : 0.0};
-            F.iu = {f[6], C ? f[7] : 0.0};
-            const int pp = facp[kk];
+            const double *fp = myfac + kk * 8;
+            F.ia = {fp[0], C ? fp[1] : 0.0};
+            F.l = {fp[2], C ? fp[3] : 0.0};
+            F.g = {fp[4], C ? fp[5] : 0.0};
+            F.iu = {fp[6], C ? fp[7] : 0.0};
+            const int pp = myfacp[kk];
             F.pr = pp & 1;
             F.pc = pp >> 1;
         }
@@ -305,10 +405,10 @@ __device__ void solve_tile(const Shared &S, const Plan &P, int s, int ts, int kb
                 Enu += sc;
                 e += sc;
             }
-            if (g == q % kG) { myr[q * kYS] = z0.re; if (C) myi[q * kYS] = z0.im; }
-            if (bs == 2 && g == (q + 1) % kG) {
-                myr[(q + 1) * kYS] = z1.re;
-                if (C) myi[(q + 1) * kYS] = z1.im;
+            if (g == q % G) { myr[q * ys] = z0.re; if (C) myi[q * ys] = z0.im; }
+            if (bs == 2 && g == (q + 1) % G) {
+                myr[(q + 1) * ys] = z1.re;
+                if (C) myi[(q + 1) * ys] = z1.im;
             }
         }
         // protection of the update of rows [0, q): fast test on exponents,
@@ -318,15 +418,15 @@ __device__ void solve_tile(const Shared &S, const Plan &P, int s, int ts, int kb
         if (__any_sync(0xffffffffu, trig)) {
             long long b = 0;
             if (trig)
-                for (int i = g; i < q; i += kG) {
-                    b = max(b, abs_bits(myr[i * kYS]));
-                    if (C) b = max(b, abs_bits(myi[i * kYS]));
+                for (int i = g; i < q; i += G) {
+                    b = max(b, abs_bits(myr[i * ys]));
+                    if (C) b = max(b, abs_bits(myi[i * ys]));
                 }
-            b = group_max_bits(b);
+            b = group_max_bits<G>(b);
             if (trig) {
                 double nu = __longlong_as_double(b);
                 const double mu = __longlong_as_double(max(cbits(z0), cbits(z1)));
-                const int g2 = protect_update(nu, S.btau[kk], mu);
+                const int g2 = protect_update(nu, btau[kk], mu);
                 if (g2 != 0) {
                     scale_rows(g2);
                     z0 = cscale(z0, g2);
@@ -340,29 +440,92 @@ __device__ void solve_tile(const Shared &S, const Plan &P, int s, int ts, int kb
         }
         if (act && q > 0) {
             const double *c0 = Ts + q * ts;
-            if (bs == 1) update_rows<C, 1>(myr, myi, c0, c0, q, g, z0, z1, kYS);
-            else update_rows<C, 2>(myr, myi, c0, c0 + ts, q, g, z0, z1, kYS);
+            if (bs == 1) update_rows<C, 1, G>(myr, myi, c0, c0, q, g, z0, z1, ys);
+            else update_rows<C, 2, G>(myr, myi, c0, c0 + ts, q, g, z0, z1, ys);
             Enu = max(Enu, fmu + ftq - 2044) + 1;
         }
         __syncwarp();
     }
-    // segment maxima per column, exponent (for the decisions and the next steps)
-    long long br = 0, bi = 0;
-    for (int i = g; i < ts; i += kG) {
-        br = max(br, abs_bits(myr[i * kYS]));
-        if (C) bi = max(bi, abs_bits(myi[i * kYS]));
+    // segment maxima per column, exponent
+    {
+        long long br = 0, bi = 0;
+        for (int i = g; i < ts; i += G) {
+            br = max(br, abs_bits(myr[i * ys]));
+            if (C) bi = max(bi, abs_bits(myi[i * ys]));
+        }
+        br = group_max_bits<G>(br);
+        bi = group_max_bits<G>(bi);
+        if (g == 0) {
+            ue[slot] = e;
+            umu[slot] = __longlong_as_double(max(br, bi));
+            if (valid) {
+                seg_e[(int64_t)s * m + col] = e;
+                seg_nu[(int64_t)s * m + col] = __longlong_as_double(br);
+                if (C) {
+                    seg_e[(int64_t)s * m + col + 1] = e;
+                    seg_nu[(int64_t)s * m + col + 1] = __longlong_as_double(bi);
+                }
+            }
+        }
     }
-    br = group_max_bits(br);
-    bi = group_max_bits(bi);
-    if (g == 0) {
-        S.ue[slot] = e;
-        S.umu[slot] = __longlong_as_double(max(br, bi));
-        if (valid) {
-            seg_e[(int64_t)s * m + col] = e;
-            seg_nu[(int64_t)s * m + col] = __longlong_as_double(br);
+    __syncthreads();
+
+    // ---- write-back and the decisions for the tiles above ------------------
+    for (int idx = tid; idx < kUnits * ts; idx += kThreads) {
+        const int uu = idx / ts, i = idx % ts;
+        const int c = ucol[uu];
+        if (c >= 0) {
+            Y[(t0 + i) + (int64_t)c * ldy] = yr[i * ys + uu];
+            if (C) Y[(t0 + i) + (int64_t)(c + 1) * ldy] = yi[i * ys + uu];
+        }
+    }
+    // consolidation + protection decisions (Sec. 3.4): thread -> (unit,
+    // tile row), consecutive threads on consecutive columns; four items per
+    // thread per round so their loads are in flight together
+    constexpr int kBatch = 4;
+    const int items = kUnits * s;
+    for (int base = tid; base < items; base += kBatch * kThreads) {
+        int er[kBatch];
+        double nur[kBatch];
+#pragma unroll
+        for (int j = 0; j < kBatch; j++) {
+            const int idx = base + j * kThreads;
+            er[j] = 0;
+            nur[j] = 0.0;
+            if (idx < items) {
+                const int uu = idx % kUnits, r = idx / kUnits;
+                const int c = ucol[uu];
+                if (c >= 0 && !uown[uu]) {
+                    const int64_t at = (int64_t)r * m + c;
+                    er[j] = seg_e[at];
+                    nur[j] = seg_nu[at];
+                    if (C) nur[j] = fmax(nur[j], seg_nu[at + 1]);
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kBatch; j++) {
+            const int idx = base + j * kThreads;
+            if (idx >= items) continue;
+            const int uu = idx % kUnits, r = idx / kUnits;
+            const int c = ucol[uu];
+            if (c < 0) continue;
+            const int64_t at = (int64_t)r * m + c;
+            const int es = ue[uu];
+            const bool ownu = uown[uu];
+            const int e_r = ownu ? es : er[j];
+            const int a = min(e_r, es);
+            const double nup = ownu ? 0.0 : scale2(nur[j], a - e_r);
+            const double mup = scale2(umu[uu], a - es);
+            const int g2 = protect_update(nup, tau[(int64_t)r * P.ntiles + s], mup);
+            const int ne = a + g2;
+            seg_e[at] = ne;
+            seg_dx[at] = ne - es;
+            seg_dy[at] = ownu ? kFresh : ne - e_r;
             if (C) {
-                seg_e[(int64_t)s * m + col + 1] = e;
-                seg_nu[(int64_t)s * m + col + 1] = __longlong_as_double(bi);
+                seg_e[at + 1] = ne;
+                seg_dx[at + 1] = ne - es;
+                seg_dy[at + 1] = ownu ? kFresh : ne - e_r;
             }
         }
     }
@@ -377,158 +540,26 @@ __global__ void __launch_bounds__(32 * W)
                  double *__restrict__ Y, int64_t ldy, int32_t *__restrict__ seg_e,
                  double *__restrict__ seg_nu, int32_t *__restrict__ seg_dx,
                  int32_t *__restrict__ seg_dy) {
-    constexpr int kThreads = 32 * W;
-    constexpr int kUnits = kUnitsPerWarp * W;
-    constexpr int kYS = kUnits + 1;
     extern __shared__ double smem[];
-    const int t0 = P.tile_start[s];
-    const int ts = P.tile_start[s + 1] - t0;
-    const int kb0 = P.tile_blk[s], kb1 = P.tile_blk[s + 1];
-    const int nbt = kb1 - kb0;
-    Shared S;
-    S.Ts = smem;                              // ts x ts, ld ts
-    S.btau = S.Ts + ts * ts;                  // [kMaxTile]
-    S.umu = S.btau + kMaxTile;                // [kUnits]
-    S.yr = S.umu + kUnits;                    // [ts][kYS]
-    S.yi = S.yr + ts * kYS;                   // [ts][kYS]
-    S.fac = S.yi + ts * kYS;                  // [kUnits][ts][8] block factors
-    S.bq = (int *)(S.fac + (size_t)kUnits * ts * 8);  // [kMaxTile]
-    S.bsz = S.bq + kMaxTile;                  // [kMaxTile]
-    S.btf = S.bsz + kMaxTile;                 // [kMaxTile] exponent fields of btau
-    S.ucol = S.btf + kMaxTile;                // [kUnits] column, -1 = none
-    S.uown = S.ucol + kUnits;                 // [kUnits]
-    S.ue = S.uown + kUnits;                   // [kUnits]
-    S.facp = S.ue + kUnits;                   // [kUnits][ts] pivot positions
-    S.ys = kYS;
+    if ((int)blockIdx.x < nreal_ctas)
+        diag_tile<W, false>(s, P.tile_real[s] + blockIdx.x * (Lanes<false>::U * W), T, ldt, P, tau,
+                            blk_tau, Y, ldy, seg_e, seg_nu, seg_dx, seg_dy, smem);
+    else
+        diag_tile<W, true>(s, P.tile_cplx[s] + (blockIdx.x - nreal_ctas) * (Lanes<true>::U * W), T,
+                           ldt, P, tau, blk_tau, Y, ldy, seg_e, seg_nu, seg_dx, seg_dy, smem);
+}
 
-    const bool cplx = blockIdx.x >= nreal_ctas;
-    const int32_t *ord = cplx ? P.ord_cplx : P.ord_real;
-    const int list_end = cplx ? P.ncplx : P.nreal;
-    const int list_pos0 = (cplx ? P.tile_cplx[s] + (blockIdx.x - nreal_ctas) * kUnits
-                                : P.tile_real[s] + blockIdx.x * kUnits);
-    const int tid = threadIdx.x;
-
-    // diagonal tile (upper part and first subdiagonal only), asynchronously
-    for (int j = 0; j < ts; j++) {
-        const int iend = min(j + 2, ts);
-        const double *src = T + t0 + (int64_t)(t0 + j) * ldt;
-        for (int i = tid; i < ts; i += kThreads) {
-            if (i < iend) cp_async8(&S.Ts[i + j * ts], src + i);
-            else S.Ts[i + j * ts] = 0.0;
-        }
-    }
-    asm volatile("cp.async.commit_group;");
-    for (int k = tid; k < nbt; k += kThreads) {
-        S.bq[k] = P.blk_start[kb0 + k] - t0;
-        S.bsz[k] = P.blk_size[kb0 + k];
-        S.btau[k] = blk_tau[kb0 + k];
-        S.btf[k] = efield(blk_tau[kb0 + k]);
-    }
-    if (tid < kUnits) {
-        const int pos = list_pos0 + tid;
-        int c = -1, own = 0;
-        if (pos < list_end) {
-            const int u = ord[pos];
-            c = P.unit_col[u];
-            own = P.unit_tile[u] == s;
-        }
-        S.ucol[tid] = c;
-        S.uown[tid] = own;
-    }
-    __syncthreads();   // the unit map is read by every warp below
-    // the segments, column by column (coalesced); own units start at zero
-    for (int idx = tid; idx < kUnits * ts; idx += kThreads) {
-        const int uu = idx / ts, i = idx % ts;
-        const int c = S.ucol[uu];
-        if (c >= 0 && !S.uown[uu]) {
-            cp_async8(&S.yr[i * kYS + uu], &Y[(t0 + i) + (int64_t)c * ldy]);
-            if (cplx) cp_async8(&S.yi[i * kYS + uu], &Y[(t0 + i) + (int64_t)(c + 1) * ldy]);
-            else S.yi[i * kYS + uu] = 0.0;
-        } else {
-            S.yr[i * kYS + uu] = 0.0;
-            S.yi[i * kYS + uu] = 0.0;
-        }
-    }
-    asm volatile("cp.async.commit_group;");
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
-    __syncthreads();
-
-    const int slot = tid / kG, g = tid % kG;
-    const int pos = list_pos0 + slot;
-    const bool valid = pos < list_end;
-    const int u = valid ? ord[pos] : 0;
-    if (cplx) solve_tile<true>(S, P, s, ts, kb0, kb1, slot, g, valid, u, seg_e, seg_nu);
-    else solve_tile<false>(S, P, s, ts, kb0, kb1, slot, g, valid, u, seg_e, seg_nu);
-    __syncthreads();
-
-    // write the solved segments back (coalesced) with exponents and maxima
-    for (int idx = tid; idx < kUnits * ts; idx += kThreads) {
-        const int uu = idx / ts, i = idx % ts;
-        const int c = S.ucol[uu];
-        if (c >= 0) {
-            Y[(t0 + i) + (int64_t)c * ldy] = S.yr[i * kYS + uu];
-            if (cplx) Y[(t0 + i) + (int64_t)(c + 1) * ldy] = S.yi[i * kYS + uu];
-        }
-    }
-    const int64_t m = P.m;
-    // consolidation + protection decisions for the tiles above (Sec. 3.4):
-    // thread -> (unit, tile row), consecutive threads on consecutive columns;
-    // four items per thread per round so their loads are in flight together
-    constexpr int kBatch = 4;
-    const int items = kUnits * s;
-    for (int base = tid; base < items; base += kBatch * kThreads) {
-        int er[kBatch];
-        double nur[kBatch];
-#pragma unroll
-        for (int j = 0; j < kBatch; j++) {
-            const int idx = base + j * kThreads;
-            er[j] = 0;
-            nur[j] = 0.0;
-            if (idx < items) {
-                const int uu = idx % kUnits, r = idx / kUnits;
-                const int c = S.ucol[uu];
-                if (c >= 0 && !S.uown[uu]) {
-                    const int64_t at = (int64_t)r * m + c;
-                    er[j] = seg_e[at];
-                    nur[j] = seg_nu[at];
-                    if (cplx) nur[j] = fmax(nur[j], seg_nu[at + 1]);
-                }
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < kBatch; j++) {
-            const int idx = base + j * kThreads;
-            if (idx >= items) continue;
-            const int uu = idx % kUnits, r = idx / kUnits;
-            const int c = S.ucol[uu];
-            if (c < 0) continue;
-            const int64_t at = (int64_t)r * m + c;
-            const int es = S.ue[uu];
-            const bool own = S.uown[uu];
-            const int e_r = own ? es : er[j];
-            const int a = min(e_r, es);
-            const double nup = own ? 0.0 : scale2(nur[j], a - e_r);
-            const double mup = scale2(S.umu[uu], a - es);
-            const int g2 = protect_update(nup, tau[(int64_t)r * P.ntiles + s], mup);
-            const int ne = a + g2;
-            seg_e[at] = ne;
-            seg_dx[at] = ne - es;
-            seg_dy[at] = own ? kFresh : ne - e_r;
-            if (cplx) {
-                seg_e[at + 1] = ne;
-                seg_dx[at + 1] = ne - es;
-                seg_dy[at + 1] = own ? kFresh : ne - e_r;
-            }
-        }
-    }
+template <int W, bool C>
+static size_t diag_smem_bytes(int t) {
+    constexpr int kUnits = Lanes<C>::U * W;
+    return sizeof(double) * ((size_t)t * t + kMaxTile + kUnits + 2 * (size_t)t * (kUnits + 1) +
+                             (size_t)kUnits * t * 8) +
+           sizeof(int) * (4 * (size_t)kMaxTile + 3 * kUnits + (size_t)kUnits * t);
 }
 
 template <int W>
-static size_t diag_smem_bytes(int t) {
-    constexpr int kUnits = kUnitsPerWarp * W;
-    return sizeof(double) * ((size_t)t * t + kMaxTile + kUnits + 2 * (size_t)t * (kUnits + 1) +
-                             (size_t)kUnits * t * 8) +
-           sizeof(int) * (3 * (size_t)kMaxTile + 3 * kUnits + (size_t)kUnits * t);
+static size_t diag_smem(int t) {
+    return std::max(diag_smem_bytes<W, false>(t), diag_smem_bytes<W, true>(t));
 }
 
 template <int W>
@@ -536,13 +567,13 @@ static void launch_w(int s, int ts, int nr, int nc, const double *T, int64_t ldt
                      const double *tau, const double *blk_tau, double *Y, int64_t ldy,
                      int32_t *seg_e, double *seg_nu, int32_t *seg_dx, int32_t *seg_dy,
                      cudaStream_t st) {
-    constexpr int kUnits = kUnitsPerWarp * W;
-    const int rct = (nr + kUnits - 1) / kUnits;
-    const int cct = (nc + kUnits - 1) / kUnits;
+    constexpr int ur = Lanes<false>::U * W, uc = Lanes<true>::U * W;
+    const int rct = (nr + ur - 1) / ur;
+    const int cct = (nc + uc - 1) / uc;
     if (rct + cct == 0) return;
     cudaFuncSetAttribute(k_diag_solve<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)diag_smem_bytes<W>(W == 4 ? 64 : kMaxTile));
-    k_diag_solve<W><<<rct + cct, 32 * W, diag_smem_bytes<W>(ts), st>>>(
+                         (int)diag_smem<W>(W == 4 ? 64 : kMaxTile));
+    k_diag_solve<W><<<rct + cct, 32 * W, diag_smem<W>(ts), st>>>(
         s, rct, T, ldt, p, tau, blk_tau, Y, ldy, seg_e, seg_nu, seg_dx, seg_dy);
 }
 
@@ -554,7 +585,7 @@ void launch_diag_solve(int s, const double *T, int64_t ldt, const Plan &p,
     const int ts = tile_start_h[s + 1] - tile_start_h[s];
     const int nr = p.nreal - tile_real_h[s];
     const int nc = p.ncplx - tile_cplx_h[s];
-    // four warps (16 units) share a tile of up to 64 rows; two for larger tiles
+    // four warps share a tile of up to 64 rows; two for larger tiles
     if (ts <= 64)
         launch_w<4>(s, ts, nr, nc, T, ldt, p, tau, blk_tau, Y, ldy, seg_e, seg_nu, seg_dx, seg_dy, st);
     else
