@@ -56,6 +56,8 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=4096)
     ap.add_argument("--tile", type=int, default=0)
+    ap.add_argument("--mode", choices=["fp64", "split"], default="split")
+    ap.add_argument("--slices", type=int, default=0)
     ap.add_argument("--cpu-sample", type=int, default=1024,
                     help="columns of the CPU-oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -230,7 +232,7 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.current_stream(dev)
 
     def step():
-        ev.standard(dT, dQ, tile=args.tile, out=out)
+        ev.standard(dT, dQ, tile=args.tile, out=out, mode=args.mode, slices=args.slices)
 
     for _ in range(args.warmup):
         step()
@@ -299,7 +301,7 @@ def run_ours(args, rank, world, local_rank):
         hE = pin((m,), torch.int32)
         hLr = pin((m,), torch.float64)
         hLi = pin((m,), torch.float64)
-        opts = ev._opts(args.tile, False)
+        opts = ev._opts(args.tile, False, args.mode, args.slices)
         hh = ev.handle(local_rank)
         P = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
 
@@ -341,7 +343,9 @@ def run_ours(args, rank, world, local_rank):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"config-0 Schur form n={n} + Q (64 Householder reflectors), "
                                f"all {m} columns, FP64",
-                   "n": n, "columns": m, "tile": args.tile or 64, "parallelism": "replicas",
+                   "n": n, "columns": m, "tile": args.tile or 64, "mode": args.mode,
+                   "slices": (args.slices or 7) if args.mode == "split" else None,
+                   "parallelism": "replicas",
                    "l2": "inputs larger than L2 (T, Q, X 128 MiB each)"},
         "tflops_fp64": tflops,
         "flops_per_step": F,

@@ -72,20 +72,26 @@ typedef enum {
     EVEC_ENONFINITE = 3, /* NaN or Inf in a referenced entry */
     EVEC_ENOMEM = 4,     /* device or host allocation failed */
     EVEC_ECUDA = 5,      /* CUDA runtime error */
-    EVEC_ETIMEOUT = 6,   /* a bounded device-side wait gave up */
+    EVEC_ETIMEOUT = 6,   /* a bounded device-side wait gave up (reported by evec_sync) */
     EVEC_ERESIDUAL = 7,  /* reserved: residual gate failed */
     EVEC_ECAPACITY = 8   /* problem larger than evec_standard_noalloc's fixed scratch */
 } evec_status;
 
 typedef enum {
-    EVEC_FP64 = 0 /* every operation in FP64 on the GPU */
+    EVEC_FP64 = 0,  /* every operation in FP64 on the GPU (DFMA) */
+    EVEC_SPLIT = 1  /* dense contractions as split-precision products on the
+                       BF16 tensor cores (FP64 operands cut into `slices`
+                       7-bit digit slices, exact FP32 accumulation per digit
+                       diagonal, FP64 recombination); everything else FP64 */
 } evec_mode;
 
 typedef struct {
-    int mode;   /* evec_mode */
-    int tile;   /* tile size nb of the tiled solve, 16..128; 0 = default */
-    int check;  /* nonzero: synchronise at the end of the call and return
-                   the device status directly */
+    int mode;    /* evec_mode */
+    int tile;    /* tile size nb of the tiled solve, 16..128; 0 = default */
+    int check;   /* nonzero: synchronise at the end of the call and return
+                    the device status directly */
+    int slices;  /* EVEC_SPLIT: digit slices per operand, 2..7; 0 = 7
+                    (relative error of a product ~2^(-7 slices)) */
 } evec_opts;
 
 /* Create a handle on CUDA device `device` that launches on `cuda_stream`

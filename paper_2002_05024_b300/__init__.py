@@ -46,7 +46,11 @@ class EvecError(RuntimeError):
 
 
 class _Opts(ctypes.Structure):
-    _fields_ = [("mode", ctypes.c_int), ("tile", ctypes.c_int), ("check", ctypes.c_int)]
+    _fields_ = [("mode", ctypes.c_int), ("tile", ctypes.c_int), ("check", ctypes.c_int),
+                ("slices", ctypes.c_int)]
+
+
+MODES = {"fp64": 0, "split": 1}
 
 
 _lib = None
@@ -115,8 +119,8 @@ def _mask(select, n):
     return s
 
 
-def _opts(tile, check):
-    return _Opts(0, int(tile), 1 if check else 0)
+def _opts(tile, check, mode="fp64", slices=0):
+    return _Opts(MODES[mode], int(tile), 1 if check else 0, int(slices))
 
 
 # ---------------------------------------------------------------------------
@@ -231,7 +235,8 @@ def count(T, select=None) -> int:
     return int(m.value)
 
 
-def standard(T, Q=None, select=None, tile: int = 0, check: bool = False, out=None):
+def standard(T, Q=None, select=None, tile: int = 0, check: bool = False, out=None,
+             mode: str = "fp64", slices: int = 0):
     """Eigenvectors of the quasi-triangular T (optionally X = Q Y).
 
     Returns (X, scale_exp, lam_re, lam_im) as CUDA tensors; X is (n, m)
@@ -256,7 +261,7 @@ def standard(T, Q=None, select=None, tile: int = 0, check: bool = False, out=Non
     ldx = X.stride(1) if m > 1 else max(n, 1)
     if m == 0:
         return X, e, lr, li
-    opts = _opts(tile, False)
+    opts = _opts(tile, False, mode, slices)
     st = lib().evec_standard(h.ptr, n, T.data_ptr(), ldt, Q.data_ptr() if Q is not None else None,
                              ldq, _np_ptr(sel), X.data_ptr(), ldx, e.data_ptr(), lr.data_ptr(),
                              li.data_ptr(), ctypes.byref(opts))
@@ -266,7 +271,8 @@ def standard(T, Q=None, select=None, tile: int = 0, check: bool = False, out=Non
     return X, e, lr, li
 
 
-def standard_host(T, Q=None, select=None, tile: int = 0, device: int = 0):
+def standard_host(T, Q=None, select=None, tile: int = 0, device: int = 0,
+                  mode: str = "fp64", slices: int = 0):
     """The same computation from host numpy arrays (column-major float64);
     copies in, computes, copies out.  Returns numpy arrays."""
     Tf = np.asfortranarray(T, dtype=np.float64)
@@ -284,7 +290,7 @@ def standard_host(T, Q=None, select=None, tile: int = 0, device: int = 0):
     import torch
     h = handle(device)
     h.set_stream(torch.cuda.current_stream(device).cuda_stream)
-    opts = _opts(tile, False)
+    opts = _opts(tile, False, mode, slices)
     st = lib().evec_standard_host(h.ptr, n, _np_ptr(Tf), _np_ptr(Qf), _np_ptr(sel), _np_ptr(X),
                                   _np_ptr(e), _np_ptr(lr), _np_ptr(li), ctypes.byref(opts))
     _check(st, "evec_standard_host")

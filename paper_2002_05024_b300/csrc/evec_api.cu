@@ -16,6 +16,8 @@
 #include <new>
 #include <vector>
 
+#include <cuda_bf16.h>
+
 #include "../../include/evec.h"
 #include "evec_internal.cuh"
 
@@ -42,6 +44,15 @@ void launch_backtransform(const double *Q, int64_t ldq, const Plan &p, const dou
                           int64_t ldy, double *X, int64_t ldx, cudaStream_t st);
 void launch_canonicalize(const Plan &p, double *X, int64_t ldx, int32_t *scale_exp,
                          cudaStream_t st);
+cudaError_t launch_split_gemm(const double *A, int64_t lda, const double *B, int64_t ldb, int M,
+                              int N, int K, int S, const int *kend, double *C, int64_t ldc,
+                              __nv_bfloat16 *sa, __nv_bfloat16 *sb, unsigned long long *rowmax,
+                              unsigned long long *colmax, int *ea, int *eb, int *err,
+                              cudaStream_t st);
+int split_pad_m(int M);
+int split_pad_n(int N);
+int split_pad_k(int K);
+constexpr int kSplitColTile = 64;
 
 // ---------------------------------------------------------------------------
 // host plan
@@ -52,6 +63,7 @@ struct HostPlan {
     std::vector<int32_t> tile_start, tile_blk, tile_unit, tile_col;
     std::vector<int32_t> blk_start, unit_col, unit_blk, unit_tile, col_unit;
     std::vector<int32_t> ord_real, ord_cplx, tile_real, tile_cplx;
+    std::vector<int32_t> bt_kend;   // per 64-column tile: K extent of the back-transform
     std::vector<int8_t> blk_size;
     std::vector<double> unit_lam, unit_own, col_lam_re, col_lam_im;
 };
@@ -173,6 +185,14 @@ static evec_status build_plan(int64_t n, const double *diag, const double *sub,
         P.tile_col[tt] = (int32_t)col;
     }
     P.m = col;
+    // K extent of each 64-column tile of X = Q Y: rows of Y up to the end of
+    // the last column's block, rounded up to the 32-row stage of the split GEMM
+    for (int64_t j0 = 0; j0 < P.m; j0 += kSplitColTile) {
+        const int64_t jl = std::min(P.m, j0 + (int64_t)kSplitColTile) - 1;
+        const int32_t k = P.unit_blk[P.col_unit[jl]];
+        const int64_t end = (int64_t)P.blk_start[k] + P.blk_size[k];
+        P.bt_kend.push_back((int32_t)((end + 31) / 32 * 32));
+    }
     // solve order: real and complex units, each in unit (= tile) order
     P.tile_real.assign(N + 1, 0);
     P.tile_cplx.assign(N + 1, 0);
@@ -211,6 +231,11 @@ struct evec_ctx {
     double *tau = nullptr; size_t tau_cap = 0;
     double *blk_tau = nullptr; size_t blk_tau_cap = 0;
     DevStatus *status_d = nullptr;
+    // split-precision workspace
+    __nv_bfloat16 *slA = nullptr, *slB = nullptr; size_t slA_cap = 0, slB_cap = 0;
+    unsigned long long *rmax = nullptr, *cmax = nullptr; size_t rmax_cap = 0, cmax_cap = 0;
+    int *ea = nullptr, *eb = nullptr; size_t ea_cap = 0, eb_cap = 0;
+    const int32_t *bt_kend_d = nullptr;
     // host-buffer entry point
     double *hT = nullptr, *hQ = nullptr, *hX = nullptr; size_t hT_cap = 0, hQ_cap = 0, hX_cap = 0;
     int32_t *hE = nullptr; size_t hE_cap = 0;
@@ -347,7 +372,7 @@ evec_status upload_plan(evec_handle h, Plan &dp) {
     const size_t nd = P.unit_lam.size() + P.unit_own.size() + P.col_lam_re.size() + P.col_lam_im.size();
     const size_t ni = 6 * N1 + P.blk_start.size() + P.unit_col.size() + P.unit_blk.size() +
                       P.unit_tile.size() + P.col_unit.size() + P.ord_real.size() +
-                      P.ord_cplx.size();
+                      P.ord_cplx.size() + P.bt_kend.size();
     const size_t bytes = nd * 8 + ni * 4 + P.blk_size.size() + 64;
     EVEC_TRY(grow_host(&h->plan_h, &h->plan_h_cap, bytes));
     EVEC_TRY(grow_device(&h->plan_d, &h->plan_cap, bytes));
@@ -384,6 +409,7 @@ evec_status upload_plan(evec_handle h, Plan &dp) {
     dp.ord_cplx = (const int32_t *)put(P.ord_cplx.data(), P.ord_cplx.size() * 4, 4);
     dp.tile_real = (const int32_t *)put(P.tile_real.data(), N1 * 4, 4);
     dp.tile_cplx = (const int32_t *)put(P.tile_cplx.data(), N1 * 4, 4);
+    h->bt_kend_d = (const int32_t *)put(P.bt_kend.data(), P.bt_kend.size() * 4, 4);
     dp.blk_size = (const int8_t *)put(P.blk_size.data(), P.blk_size.size(), 1);
     EVEC_CUDA(cudaMemcpyAsync(h->plan_d, h->plan_h, off, cudaMemcpyHostToDevice, h->stream));
     return EVEC_OK;
@@ -472,7 +498,8 @@ evec_status evec_destroy(evec_handle h) {
     cudaStreamSynchronize(h->stream);
     cudaGetLastError();
     void *dev[] = {h->diag_d, h->plan_d, h->Y, h->seg_e, h->seg_dx, h->seg_dy, h->seg_nu,
-                   h->tau, h->blk_tau, h->status_d, h->hT, h->hQ, h->hX, h->hE, h->hL};
+                   h->tau, h->blk_tau, h->status_d, h->hT, h->hQ, h->hX, h->hE, h->hL,
+                   h->slA, h->slB, h->rmax, h->cmax, h->ea, h->eb};
     for (void *p : dev)
         if (p) cudaFree(p);
     for (auto &t : h->live) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
@@ -538,11 +565,12 @@ evec_status evec_sync(evec_handle h, int64_t *bad_index) {
                               cudaMemcpyDeviceToHost, h->stream));
     EVEC_CUDA(cudaStreamSynchronize(h->stream));
     const DevStatus s = *h->status_h;
-    if (s.code != 0) {
+    if (s.code != 0 || s.timeout != 0) {
         EVEC_CUDA(cudaMemsetAsync(h->status_d, 0, sizeof(DevStatus), h->stream));
         EVEC_CUDA(cudaStreamSynchronize(h->stream));
     }
     if (bad_index) *bad_index = s.code ? (int64_t)s.index : -1;
+    if (s.code == 0 && s.timeout != 0) return EVEC_ETIMEOUT;
     return (evec_status)s.code;
 }
 
@@ -552,7 +580,10 @@ evec_status evec_standard(evec_handle h, int64_t n, const double *T, int64_t ldt
                           double *lam_im, const evec_opts *opt) {
     if (!h || n < 0 || !ld_ok(ldt, n) || !ld_ok(ldx, n) || (Q && !ld_ok(ldq, n)))
         return EVEC_EINVAL;
-    if (opt && opt->mode != EVEC_FP64) return EVEC_EINVAL;
+    const int mode = opt ? opt->mode : EVEC_FP64;
+    if (mode != EVEC_FP64 && mode != EVEC_SPLIT) return EVEC_EINVAL;
+    const int slices = (opt && opt->slices) ? opt->slices : 7;
+    if (slices < 2 || slices > 7) return EVEC_EINVAL;
     const int nb = resolve_tile(opt);
     if (nb < 16 || nb > kMaxTile) return EVEC_EINVAL;
     if (n == 0) return EVEC_OK;
@@ -600,7 +631,23 @@ evec_status evec_standard(evec_handle h, int64_t n, const double *T, int64_t ldt
             });
     }
     timed(h, EVEC_K_FINALIZE, [&] { launch_finalize(dp, Y, ldy, h->seg_e, scale_exp, st); });
-    if (Q) {
+    if (Q && mode == EVEC_SPLIT) {
+        const int Mp = split_pad_m((int)n), Np = split_pad_n((int)m), Kp = split_pad_k((int)n);
+        EVEC_TRY(grow_device(&h->slA, &h->slA_cap, (size_t)slices * Mp * Kp));
+        EVEC_TRY(grow_device(&h->slB, &h->slB_cap, (size_t)slices * Np * Kp));
+        EVEC_TRY(grow_device(&h->rmax, &h->rmax_cap, (size_t)Mp));
+        EVEC_TRY(grow_device(&h->cmax, &h->cmax_cap, (size_t)Np));
+        EVEC_TRY(grow_device(&h->ea, &h->ea_cap, (size_t)Mp));
+        EVEC_TRY(grow_device(&h->eb, &h->eb_cap, (size_t)Np));
+        cudaError_t ce = cudaSuccess;
+        timed(h, EVEC_K_BACKTRANSFORM, [&] {
+            ce = launch_split_gemm(Q, ldq, Y, ldy, (int)n, (int)m, (int)n, slices, h->bt_kend_d, X,
+                                   ldx, h->slA, h->slB, h->rmax, h->cmax, h->ea, h->eb,
+                                   &h->status_d->timeout, st);
+        });
+        EVEC_CUDA(ce);
+        timed(h, EVEC_K_CANONICALIZE, [&] { launch_canonicalize(dp, X, ldx, scale_exp, st); });
+    } else if (Q) {
         timed(h, EVEC_K_BACKTRANSFORM,
               [&] { launch_backtransform(Q, ldq, dp, Y, ldy, X, ldx, st); });
         timed(h, EVEC_K_CANONICALIZE, [&] { launch_canonicalize(dp, X, ldx, scale_exp, st); });

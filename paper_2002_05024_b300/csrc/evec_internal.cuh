@@ -31,7 +31,7 @@ constexpr int kMaxTile = 128;
 
 struct DevStatus {
     int code;          // evec_status of the first device-detected error
-    int pad;
+    int timeout;       // nonzero: a bounded device-side wait gave up
     long long index;   // linear index of the offending entry
 };
 

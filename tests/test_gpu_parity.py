@@ -27,10 +27,11 @@ pytestmark = pytest.mark.gpu
 REL_TOL = 1e-10
 
 
-def _gpu(T, Q=None, select=None, tile=0):
+def _gpu(T, Q=None, select=None, tile=0, mode="fp64", slices=0):
     dT = torch.from_numpy(np.asfortranarray(T)).cuda()
     dQ = None if Q is None else torch.from_numpy(np.asfortranarray(Q)).cuda()
-    X, e, lr, li = ev.standard(dT, dQ, select=select, tile=tile, check=True)
+    X, e, lr, li = ev.standard(dT, dQ, select=select, tile=tile, check=True, mode=mode,
+                               slices=slices)
     torch.cuda.synchronize()
     return X.cpu().numpy(), e.cpu().numpy(), lr.cpu().numpy(), li.cpu().numpy()
 
@@ -163,9 +164,9 @@ def test_deterministic_and_power_of_two_invariant():
 # full size, in the benchmark's launch configuration (tile 64, with Q):
 # the GPU computes every column, the oracle a seeded sample of columns
 # ---------------------------------------------------------------------------
-def _sampled_parity(T, blocks, Q, k, seed, rel_tol):
+def _sampled_parity(T, blocks, Q, k, seed, rel_tol, mode="fp64"):
     n = T.shape[0]
-    X, e, lr, li = _gpu(T, Q, tile=0)
+    X, e, lr, li = _gpu(T, Q, tile=0, mode=mode)
     assert np.isfinite(X).all()
     rng = np.random.default_rng(seed)
     chosen = rng.choice(len(blocks), size=k, replace=False)
@@ -203,3 +204,45 @@ def test_full_size_config1b_sampled():
     T, blocks = workloads.adversarial_schur(n, seed=workloads.SEED_BASE + 11)
     Q = workloads.householder_orthogonal(n, seed=workloads.SEED_BASE + 111)
     _sampled_parity(T, blocks, Q, k=32, seed=2, rel_tol=1e-3)
+
+
+# ---------------------------------------------------------------------------
+# split precision (BF16 slices on the tensor cores) -- same parity bar at 7
+# slices: a product's error is ~2^-48 of its row/column maxima
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n,tile", [(300, 64), (517, 32), (1000, 128)])
+def test_split_backtransform(n, tile):
+    T, blocks = workloads.config0_schur(n, seed=n + 5)
+    Q = workloads.householder_orthogonal(n, seed=n + 6)
+    X, e, lr, li = _gpu(T, Q, tile=tile, mode="split")
+    nr = canonical_norms(X, li)
+    assert np.isfinite(X).all() and nr.min() >= 1.0 and nr.max() < 2.0
+    _parity(T, Q, X, e, lr, li)
+
+
+def test_split_selection_and_determinism():
+    n = 700
+    T, blocks = workloads.config0_schur(n, seed=15)
+    Q = workloads.householder_orthogonal(n, seed=16)
+    sel = workloads.random_eigen_selection(n, blocks, 0.35, seed=17)
+    X1, e1, lr, li = _gpu(T, Q, select=sel, tile=64, mode="split")
+    X2, e2, _, _ = _gpu(T, Q, select=sel, tile=64, mode="split")
+    np.testing.assert_array_equal(X1, X2)
+    np.testing.assert_array_equal(e1, e2)
+    _parity(T, Q, X1, e1, lr, li, select=sel)
+
+
+def test_split_adversarial():
+    n = 512
+    T, blocks = workloads.adversarial_schur(n, seed=78)
+    Q = workloads.householder_orthogonal(n, seed=79)
+    X, e, lr, li = _gpu(T, Q, tile=64, mode="split")
+    assert np.isfinite(X).all()
+    _parity(T, Q, X, e, lr, li, rel_tol=1e-3)
+
+
+def test_split_full_size_config1a_sampled():
+    n = 4096
+    T, blocks = workloads.config0_schur(n, seed=workloads.SEED_BASE + 1)
+    Q = workloads.householder_orthogonal(n, seed=workloads.SEED_BASE + 101)
+    _sampled_parity(T, blocks, Q, k=48, seed=3, rel_tol=REL_TOL, mode="split")
