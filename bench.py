@@ -344,7 +344,7 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": f"config-0 Schur form n={n} + Q (64 Householder reflectors), "
                                f"all {m} columns, FP64",
                    "n": n, "columns": m, "tile": args.tile or 64, "mode": args.mode,
-                   "slices": (args.slices or 7) if args.mode == "split" else None,
+                   "slices": (args.slices or 8) if args.mode == "split" else None,
                    "parallelism": "replicas",
                    "l2": "inputs larger than L2 (T, Q, X 128 MiB each)"},
         "tflops_fp64": tflops,

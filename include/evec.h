@@ -90,7 +90,7 @@ typedef struct {
     int tile;    /* tile size nb of the tiled solve, 16..128; 0 = default */
     int check;   /* nonzero: synchronise at the end of the call and return
                     the device status directly */
-    int slices;  /* EVEC_SPLIT: digit slices per operand, 2..7; 0 = 7
+    int slices;  /* EVEC_SPLIT: digit slices per operand, 2..8; 0 = 8
                     (relative error of a product ~2^(-7 slices)) */
 } evec_opts;
 

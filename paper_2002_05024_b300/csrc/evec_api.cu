@@ -16,10 +16,11 @@
 #include <new>
 #include <vector>
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include "../../include/evec.h"
-#include "evec_internal.cuh"
+#include "split_common.cuh"
 
 namespace evec {
 
@@ -53,6 +54,22 @@ int split_pad_m(int M);
 int split_pad_n(int N);
 int split_pad_k(int K);
 constexpr int kSplitColTile = 64;
+cudaError_t split_update_prepare(const double *T, int64_t ldt, int n, int ntiles, int maxtile,
+                                 const int32_t *tstart_d, const int32_t *prow0_d,
+                                 const int32_t *pea_d, int total_rows, int S, int m,
+                                 __nv_bfloat16 *panels, int *ea_panels, __nv_bfloat16 *sb,
+                                 SplitUpdateCtx *ctx, cudaStream_t st);
+cudaError_t split_update_step_resident(const SplitUpdateCtx &ctx, int t0, int ts, int prow0,
+                                       int pea, int col0, int m, double *Y, int64_t ldy,
+                                       const int *ea_panels, __nv_bfloat16 *sb, int *eb,
+                                       const int32_t *row_tile, const int32_t *dx,
+                                       const int32_t *dy, double *seg_nu, int *err, int nsm,
+                                       cudaStream_t st);
+cudaError_t split_update_step(const SplitUpdateCtx &ctx, int t0, int ts, int prow0, int pea,
+                              int col0, int m, double *Y, int64_t ldy, const int *ea_panels,
+                              __nv_bfloat16 *sb, unsigned long long *colmax, int *eb,
+                              const int32_t *row_tile, const int32_t *dx, const int32_t *dy,
+                              double *seg_nu, int *err, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // host plan
@@ -64,6 +81,11 @@ struct HostPlan {
     std::vector<int32_t> blk_start, unit_col, unit_blk, unit_tile, col_unit;
     std::vector<int32_t> ord_real, ord_cplx, tile_real, tile_cplx;
     std::vector<int32_t> bt_kend;   // per 64-column tile: K extent of the back-transform
+    std::vector<int32_t> row_tile;  // tile of each row
+    // split tile updates: panel s (rows above tile s) starts at row prow0[s]
+    // of the panel-slice buffer; its row exponents at pea[s] (set per call)
+    std::vector<int32_t> prow0, pea;
+    int panel_rows = 0;
     std::vector<int8_t> blk_size;
     std::vector<double> unit_lam, unit_own, col_lam_re, col_lam_im;
 };
@@ -185,6 +207,9 @@ static evec_status build_plan(int64_t n, const double *diag, const double *sub,
         P.tile_col[tt] = (int32_t)col;
     }
     P.m = col;
+    P.row_tile.resize(n);
+    for (int tt = 0; tt < N; tt++)
+        for (int32_t i = P.tile_start[tt]; i < P.tile_start[tt + 1]; i++) P.row_tile[i] = tt;
     // K extent of each 64-column tile of X = Q Y: rows of Y up to the end of
     // the last column's block, rounded up to the 32-row stage of the split GEMM
     for (int64_t j0 = 0; j0 < P.m; j0 += kSplitColTile) {
@@ -221,6 +246,7 @@ using namespace evec;
 // ---------------------------------------------------------------------------
 struct evec_ctx {
     int device = 0;
+    int nsm = 148;   // streaming multiprocessors of the device
     cudaStream_t stream = nullptr;
     // device workspace
     double *diag_d = nullptr; size_t diag_cap = 0;
@@ -235,7 +261,10 @@ struct evec_ctx {
     __nv_bfloat16 *slA = nullptr, *slB = nullptr; size_t slA_cap = 0, slB_cap = 0;
     unsigned long long *rmax = nullptr, *cmax = nullptr; size_t rmax_cap = 0, cmax_cap = 0;
     int *ea = nullptr, *eb = nullptr; size_t ea_cap = 0, eb_cap = 0;
-    const int32_t *bt_kend_d = nullptr;
+    const int32_t *bt_kend_d = nullptr, *row_tile_d = nullptr, *prow0_d = nullptr,
+                  *pea_d = nullptr;
+    __nv_bfloat16 *panels = nullptr; size_t panels_cap = 0;
+    int *ea_panels = nullptr; size_t ea_panels_cap = 0;
     // host-buffer entry point
     double *hT = nullptr, *hQ = nullptr, *hX = nullptr; size_t hT_cap = 0, hQ_cap = 0, hX_cap = 0;
     int32_t *hE = nullptr; size_t hE_cap = 0;
@@ -372,7 +401,8 @@ evec_status upload_plan(evec_handle h, Plan &dp) {
     const size_t nd = P.unit_lam.size() + P.unit_own.size() + P.col_lam_re.size() + P.col_lam_im.size();
     const size_t ni = 6 * N1 + P.blk_start.size() + P.unit_col.size() + P.unit_blk.size() +
                       P.unit_tile.size() + P.col_unit.size() + P.ord_real.size() +
-                      P.ord_cplx.size() + P.bt_kend.size();
+                      P.ord_cplx.size() + P.bt_kend.size() + P.row_tile.size() +
+                      P.prow0.size() + P.pea.size();
     const size_t bytes = nd * 8 + ni * 4 + P.blk_size.size() + 64;
     EVEC_TRY(grow_host(&h->plan_h, &h->plan_h_cap, bytes));
     EVEC_TRY(grow_device(&h->plan_d, &h->plan_cap, bytes));
@@ -410,6 +440,9 @@ evec_status upload_plan(evec_handle h, Plan &dp) {
     dp.tile_real = (const int32_t *)put(P.tile_real.data(), N1 * 4, 4);
     dp.tile_cplx = (const int32_t *)put(P.tile_cplx.data(), N1 * 4, 4);
     h->bt_kend_d = (const int32_t *)put(P.bt_kend.data(), P.bt_kend.size() * 4, 4);
+    h->row_tile_d = (const int32_t *)put(P.row_tile.data(), P.row_tile.size() * 4, 4);
+    h->prow0_d = (const int32_t *)put(P.prow0.data(), P.prow0.size() * 4, 4);
+    h->pea_d = (const int32_t *)put(P.pea.data(), P.pea.size() * 4, 4);
     dp.blk_size = (const int8_t *)put(P.blk_size.data(), P.blk_size.size(), 1);
     EVEC_CUDA(cudaMemcpyAsync(h->plan_d, h->plan_h, off, cudaMemcpyHostToDevice, h->stream));
     return EVEC_OK;
@@ -474,6 +507,11 @@ evec_status evec_create(evec_handle *h, int device, void *cuda_stream) {
     if (!c) return EVEC_ENOMEM;
     c->device = device;
     c->stream = (cudaStream_t)cuda_stream;
+    if (cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+        c->nsm < 1) {
+        cudaGetLastError();
+        c->nsm = 1;
+    }
     if (cudaMalloc((void **)&c->status_d, sizeof(DevStatus)) != cudaSuccess ||
         cudaMallocHost((void **)&c->status_h, sizeof(DevStatus)) != cudaSuccess) {
         cudaGetLastError();
@@ -499,7 +537,8 @@ evec_status evec_destroy(evec_handle h) {
     cudaGetLastError();
     void *dev[] = {h->diag_d, h->plan_d, h->Y, h->seg_e, h->seg_dx, h->seg_dy, h->seg_nu,
                    h->tau, h->blk_tau, h->status_d, h->hT, h->hQ, h->hX, h->hE, h->hL,
-                   h->slA, h->slB, h->rmax, h->cmax, h->ea, h->eb};
+                   h->slA, h->slB, h->rmax, h->cmax, h->ea, h->eb, h->panels,
+                   h->ea_panels};
     for (void *p : dev)
         if (p) cudaFree(p);
     for (auto &t : h->live) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
@@ -582,8 +621,8 @@ evec_status evec_standard(evec_handle h, int64_t n, const double *T, int64_t ldt
         return EVEC_EINVAL;
     const int mode = opt ? opt->mode : EVEC_FP64;
     if (mode != EVEC_FP64 && mode != EVEC_SPLIT) return EVEC_EINVAL;
-    const int slices = (opt && opt->slices) ? opt->slices : 7;
-    if (slices < 2 || slices > 7) return EVEC_EINVAL;
+    const int slices = (opt && opt->slices) ? opt->slices : 8;
+    if (slices < 2 || slices > 8) return EVEC_EINVAL;
     const int nb = resolve_tile(opt);
     if (nb < 16 || nb > kMaxTile) return EVEC_EINVAL;
     if (n == 0) return EVEC_OK;
@@ -598,6 +637,26 @@ evec_status evec_standard(evec_handle h, int64_t n, const double *T, int64_t ldt
     if (m == 0) return EVEC_OK;
     const int N = (int)HP.tile_start.size() - 1;
 
+    if (mode == EVEC_SPLIT) {   // panel layout of the split tile updates
+        HostPlan &WP = h->plan;
+        WP.prow0.assign(N + 1, 0);
+        WP.pea.assign(N + 1, 0);
+        int rows = 0, eas = 0;
+        for (int s = 1; s < N; s++) {
+            const int mpad = split_pad_m(WP.tile_start[s]);
+            WP.prow0[s] = rows;
+            WP.pea[s] = eas;
+            rows += slices * mpad;
+            eas += mpad;
+        }
+        WP.prow0[N] = rows;
+        WP.pea[N] = eas;
+        WP.panel_rows = rows;
+    } else {
+        h->plan.prow0.clear();
+        h->plan.pea.clear();
+        h->plan.panel_rows = 0;
+    }
     Plan dp;
     EVEC_TRY(upload_plan(h, dp));
     double *Y = X;
@@ -615,30 +674,69 @@ evec_status evec_standard(evec_handle h, int64_t n, const double *T, int64_t ldt
     EVEC_TRY(grow_device(&h->tau, &h->tau_cap, (size_t)N * (size_t)N));
     EVEC_TRY(grow_device(&h->blk_tau, &h->blk_tau_cap, HP.blk_start.size()));
 
+    if (Q && mode == EVEC_SPLIT) {   // all split workspace is sized before the first launch
+        const int Mp = split_pad_m((int)n), Np = split_pad_n((int)m), Kp = split_pad_k((int)n);
+        EVEC_TRY(grow_device(&h->slA, &h->slA_cap, (size_t)slices * Mp * Kp));
+        EVEC_TRY(grow_device(&h->slB, &h->slB_cap, (size_t)slices * Np * Kp));
+        EVEC_TRY(grow_device(&h->rmax, &h->rmax_cap, (size_t)Mp));
+        EVEC_TRY(grow_device(&h->ea, &h->ea_cap, (size_t)Mp));
+    }
     cudaStream_t st = h->stream;
     timed(h, EVEC_K_NORMS,
           [&] { launch_tile_norms(T, ldt, dp, h->tau, h->blk_tau, h->status_d, st); });
+    SplitUpdateCtx sctx;
+    if (mode == EVEC_SPLIT) {
+        const int Kp = HP.max_tile <= 64 ? 64 : 128;
+        const int Np = split_pad_n((int)m);
+        EVEC_TRY(grow_device(&h->panels, &h->panels_cap,
+                             (size_t)std::max(HP.panel_rows, 128) * Kp));
+        EVEC_TRY(grow_device(&h->ea_panels, &h->ea_panels_cap,
+                             (size_t)std::max(HP.pea[N], 1)));
+        EVEC_TRY(grow_device(&h->slB, &h->slB_cap, (size_t)slices * Np * Kp));
+        EVEC_TRY(grow_device(&h->cmax, &h->cmax_cap, (size_t)Np));
+        EVEC_TRY(grow_device(&h->eb, &h->eb_cap, (size_t)Np));
+        cudaError_t ce = cudaSuccess;
+        timed(h, EVEC_K_TILE_UPDATE, [&] {
+            ce = split_update_prepare(T, ldt, (int)n, N, HP.max_tile, dp.tile_start, h->prow0_d,
+                                      h->pea_d, HP.panel_rows, slices, (int)m, h->panels,
+                                      h->ea_panels, h->slB, &sctx, st);
+        });
+        EVEC_CUDA(ce);
+    }
     for (int s = N - 1; s >= 0; s--) {
         timed(h, EVEC_K_DIAG_SOLVE, [&] {
             launch_diag_solve(s, T, ldt, dp, HP.tile_start.data(), HP.tile_real.data(),
                               HP.tile_cplx.data(), h->tau,
                               h->blk_tau, Y, ldy, h->seg_e, h->seg_nu, h->seg_dx, h->seg_dy, st);
         });
-        if (s > 0 && HP.tile_col[s] < m)
-            timed(h, EVEC_K_TILE_UPDATE, [&] {
-                launch_tile_update(s, T, ldt, dp, HP.max_tile, HP.tile_col.data(), Y, ldy,
-                                   h->seg_dx, h->seg_dy, h->seg_nu, st);
-            });
+        if (s > 0 && HP.tile_col[s] < m) {
+            if (mode == EVEC_SPLIT) {
+                cudaError_t ce = cudaSuccess;
+                timed(h, EVEC_K_TILE_UPDATE, [&] {
+                    if (sctx.Kp == 64)
+                        ce = split_update_step_resident(
+                            sctx, HP.tile_start[s], HP.tile_start[s + 1] - HP.tile_start[s],
+                            HP.prow0[s], HP.pea[s], HP.tile_col[s], (int)m, Y, ldy,
+                            h->ea_panels, h->slB, h->eb, h->row_tile_d, h->seg_dx, h->seg_dy,
+                            h->seg_nu, &h->status_d->timeout, h->nsm, st);
+                    else
+                    ce = split_update_step(sctx, HP.tile_start[s],
+                                           HP.tile_start[s + 1] - HP.tile_start[s], HP.prow0[s],
+                                           HP.pea[s], HP.tile_col[s], (int)m, Y, ldy, h->ea_panels,
+                                           h->slB, h->cmax, h->eb, h->row_tile_d, h->seg_dx,
+                                           h->seg_dy, h->seg_nu, &h->status_d->timeout, st);
+                });
+                EVEC_CUDA(ce);
+            } else {
+                timed(h, EVEC_K_TILE_UPDATE, [&] {
+                    launch_tile_update(s, T, ldt, dp, HP.max_tile, HP.tile_col.data(), Y, ldy,
+                                       h->seg_dx, h->seg_dy, h->seg_nu, st);
+                });
+            }
+        }
     }
     timed(h, EVEC_K_FINALIZE, [&] { launch_finalize(dp, Y, ldy, h->seg_e, scale_exp, st); });
     if (Q && mode == EVEC_SPLIT) {
-        const int Mp = split_pad_m((int)n), Np = split_pad_n((int)m), Kp = split_pad_k((int)n);
-        EVEC_TRY(grow_device(&h->slA, &h->slA_cap, (size_t)slices * Mp * Kp));
-        EVEC_TRY(grow_device(&h->slB, &h->slB_cap, (size_t)slices * Np * Kp));
-        EVEC_TRY(grow_device(&h->rmax, &h->rmax_cap, (size_t)Mp));
-        EVEC_TRY(grow_device(&h->cmax, &h->cmax_cap, (size_t)Np));
-        EVEC_TRY(grow_device(&h->ea, &h->ea_cap, (size_t)Mp));
-        EVEC_TRY(grow_device(&h->eb, &h->eb_cap, (size_t)Np));
         cudaError_t ce = cudaSuccess;
         timed(h, EVEC_K_BACKTRANSFORM, [&] {
             ce = launch_split_gemm(Q, ldq, Y, ldy, (int)n, (int)m, (int)n, slices, h->bt_kend_d, X,

@@ -522,10 +522,12 @@ __device__ void diag_tile(int s, int list_pos0, const double *__restrict__ T, in
             seg_e[at] = ne;
             seg_dx[at] = ne - es;
             seg_dy[at] = ownu ? kFresh : ne - e_r;
+            seg_nu[at] = 0.0;   // the update of this step writes the new maximum
             if (C) {
                 seg_e[at + 1] = ne;
                 seg_dx[at + 1] = ne - es;
                 seg_dy[at + 1] = ownu ? kFresh : ne - e_r;
+                seg_nu[at + 1] = 0.0;
             }
         }
     }

@@ -4,84 +4,53 @@
 // splitting of the operands into small-integer slices whose products are
 // exact in FP32): every row of A is normalised by a power of two 2^ea_i so
 // |a~| < 1/2, every column of B by 2^eb_j; each normalised value is written
-// in balanced base 2^7 with S digits, x~ = sum_p d_p 2^(-7p), |d_p| <= 64,
-// and slice p holds d_p 2^(-7p) as an exact BF16 number.  For every digit
-// diagonal D = p + q (p + q <= S + 1 in 1-based terms) the products
-// A_p B_q are multiples of 2^(-7D) bounded by 2^12 2^(-7D); a diagonal
-// has at most 7 terms, so its sum over K = 512 stays below 2^24 units and
-// is exact in the FP32 tensor-core accumulator.  Each diagonal has its own
-// TMEM accumulator; every 512 of K the epilogue warps drain them into a
-// double-float (hi, lo) FP32 accumulator, and at the end
-// C_ij = 2^(ea_i + eb_j) (hi + lo) in FP64.  Truncation after S = 7
-// slices leaves 2^-49 of the row / column maxima; the double-float sum
-// keeps 48 bits.
+// in balanced base 2^7 with S <= 8 digits, x~ = sum_p d_p 2^(-7(p+1)),
+// |d_p| <= 64, and slice p holds d_p 2^(-7(p+1)) as an exact BF16 number.
+// Only the digit diagonals D = p + q < S are formed (S (S + 1) / 2 slice
+// products).  A diagonal's products are multiples of 2^(-7(D+2)) bounded by
+// 2^12 of those units; a diagonal has at most 8 terms, so its sum over
+// K = 512 stays within 2^24 units and is exact in the FP32 tensor-core
+// accumulator.  Each diagonal has its own TMEM accumulator; every 512 of K
+// the epilogue warps drain them into a double-float (hi, lo) FP32
+// accumulator, and at the end C_ij = 2^(ea_i + eb_j) (hi + lo) in FP64.
+// The digits and the dropped diagonals leave about 2^(1 - 7S) of the row /
+// column maxima per product term (2^-48 at S = 7, 2^-55 at S = 8); the
+// double-float accumulator keeps 48 bits of the running sum.
 //
 // Kernel layout: CTA tile 128 x 64, K staged 32 at a time (SWIZZLE_64B TMA
-// boxes; 2 stages x (S tiles of A + S tiles of B) = 2 x 84 KB), 512 TMEM
-// columns (7 diagonals x 64).  Warps 0-7: epilogue (TMEM lane quarter
+// boxes; 2 stages x (8 tiles of A + 8 tiles of B) = 2 x 96 KB), 512 TMEM
+// columns (8 diagonals x 64).  Warps 0-7: epilogue (TMEM lane quarter
 // w % 4, column half w / 4); warp 8: TMEM allocation + MMA issue (one
 // thread); warp 9: TMA producer (one thread).  Every mbarrier wait is
 // bounded; a wait that gives up sets *err and the roles stop issuing work.
-#include <cuda.h>
-#include <cudaTypedefs.h>
-#include <cuda_bf16.h>
-#include <cuda_runtime.h>
-
+//
+// Two epilogues: the back-transformation writes C = 2^(ea + eb) (A B); the
+// tile update of step s (Sec. 3.4, Z <- Y - T X) applies, per row i (tile
+// row r) and column j, Y_ij <- 2^dy[r, j] Y_ij - 2^(ea_i + eb_j + dx[r, j])
+// (A~ B~)_ij and merges |Y_ij| into the column maximum of segment (r, j)
+// (shared-memory maxima per CTA, one global atomicMax per (r, j) and CTA).
 #include <mutex>
 
-#include "evec_internal.cuh"
+#include "split_common.cuh"
 
 namespace evec {
 
-constexpr int kSplitMaxS = 7;
-constexpr int kTM = 128, kTN = 64, kTK = 32;
+constexpr int kTN = 64;
 constexpr int kStageA = kTM * kTK * 2;             // 8 KB per slice tile
 constexpr int kStageB = kTN * kTK * 2;             // 4 KB per slice tile
 constexpr int kStageBytes = kSplitMaxS * (kStageA + kStageB);
 constexpr int kChunkStages = 16;                   // 512 of K per exact drain
 constexpr int kSplitThreads = 320;
-constexpr int kTmemCols = 512;
-constexpr long kWaitLimit = 1L << 26;
 
-size_t split_smem_bytes() { return 1024 + 2 * (size_t)kStageBytes + 128; }
+// stage buffers, barriers, then the update epilogue's tables: column maxima
+// red[12][64] (u64), scale exponents sdx / sdy [12][64] and eb [64] (int)
+size_t split_smem_bytes() {
+    return 1024 + 2 * (size_t)kStageBytes + 128 + 12 * 64 * 8 + 2 * 12 * 64 * 4 + 64 * 4;
+}
 
 // ---------------------------------------------------------------------------
-// slicing
+// slicing kernels
 // ---------------------------------------------------------------------------
-
-// balanced base-2^7 digits of x * 2^-e (|x| < 2^(e-1)), most significant
-// first, by integer arithmetic on the IEEE encoding
-__device__ __forceinline__ void digits7(double x, int e, int S, int *d) {
-    const long long bits = __double_as_longlong(x);
-    const int E = (int)((bits >> 52) & 0x7ff);
-    long long mant = bits & ((1LL << 52) - 1);
-    if (E) mant |= (1LL << 52);
-    const int shift = (E ? E : 1) - 1075 + 7 * S - e;   // x 2^(7S - e) = mant 2^shift
-    long long I;
-    if (mant == 0) I = 0;
-    else if (shift >= 0) I = mant << shift;             // |I| < 2^(7S-1): no overflow
-    else if (shift > -62) I = (mant + (1LL << (-shift - 1))) >> (-shift);
-    else I = 0;
-    if (bits < 0) I = -I;
-    for (int p = S - 1; p >= 1; p--) {
-        long long r = I & 127;
-        if (r >= 64) r -= 128;
-        d[p] = (int)r;
-        I = (I - r) >> 7;
-    }
-    d[0] = (int)I;                                      // |d_0| <= 64
-}
-
-__device__ __forceinline__ __nv_bfloat16 digit_bf16(int d, int p) {
-    // d 2^(-7(p+1)) is exact in BF16 (|d| <= 64)
-    return __float2bfloat16_rn((float)d * __int_as_float((127 - 7 * (p + 1)) << 23));
-}
-
-__device__ __forceinline__ int exp_from_max(unsigned long long mb) {
-    // |x| <= max < 2^(ilog2(max) + 1)  ->  e = ilog2(max) + 2 gives |x 2^-e| < 1/2
-    if (mb == 0) return 0;
-    return ilog2_abs(__longlong_as_double((long long)mb)) + 2;
-}
 
 // row maxima of the column-major M x K matrix A (bit patterns, atomicMax)
 __global__ void k_row_max(const double *__restrict__ A, int64_t lda, int M, int K,
@@ -108,7 +77,7 @@ __global__ void __launch_bounds__(256) k_slice_rows(const double *__restrict__ A
     for (int e = tid; e < 32 * 64; e += 256) {
         const int r = e % 32, c = e / 32;
         const int i = i0 + r, k = k0 + c;
-        int d[kSplitMaxS] = {0, 0, 0, 0, 0, 0, 0};
+        int d[kSplitMaxS] = {0, 0, 0, 0, 0, 0, 0, 0};
         if (i < M && k < K) {
             const int ex = exp_from_max(rowmax[i]);
             digits7(A[i + (int64_t)k * lda], ex, S, d);
@@ -149,7 +118,7 @@ __global__ void k_slice_cols(const double *__restrict__ B, int64_t ldb, int K, i
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y;
     if (k >= Kpad) return;
-    int d[kSplitMaxS] = {0, 0, 0, 0, 0, 0, 0};
+    int d[kSplitMaxS] = {0, 0, 0, 0, 0, 0, 0, 0};
     if (j < N && k < K) digits7(B[k + (int64_t)j * ldb], exp_from_max(colmax[j]), S, d);
     for (int p = 0; p < S; p++) out[((size_t)p * Npad + j) * Kpad + k] = digit_bf16(d[p], p);
     if (k == 0) eb[j] = (j < N) ? exp_from_max(colmax[j]) : 0;
@@ -159,79 +128,41 @@ __global__ void k_slice_cols(const double *__restrict__ B, int64_t ldb, int K, i
 // tcgen05 GEMM
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ uint32_t saddr(const void *p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *err) {
-    for (long it = 0; it < kWaitLimit; it++) {
-        uint32_t done;
-        asm volatile(
-            "{\n.reg .pred P1;\nmbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n"
-            "selp.b32 %0, 1, 0, P1;\n}\n"
-            : "=r"(done)
-            : "r"(bar), "r"(parity)
-            : "memory");
-        if (done) return true;
-        if ((it & 1023) == 1023 && *(volatile int *)err) return false;
-    }
-    atomicExch(err, 1);
-    return false;
-}
-
-// K-major, 64-byte swizzle: 8-row atoms of 64 B, atoms 512 B apart
-__device__ __forceinline__ uint64_t desc_sw64(uint32_t a) {
-    uint64_t d = 0;
-    d |= (uint64_t)((a & 0x3FFFF) >> 4);
-    d |= (uint64_t)1 << 16;
-    d |= (uint64_t)(512 >> 4) << 32;
-    d |= (uint64_t)1 << 46;
-    d |= (uint64_t)4 << 61;
-    return d;
-}
-
-__device__ __forceinline__ void tma2d(uint32_t dst, const CUtensorMap *tm, int x, int y,
-                                      uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, "
-        "{%2, %3}], [%4];" ::"r"(dst),
-        "l"((uint64_t)tm), "r"(x), "r"(y), "r"(bar)
-        : "memory");
-}
-
-__device__ __forceinline__ void df_add(float &hi, float &lo, float x) {
-    const float s = hi + x;
-    const float bp = s - hi;
-    const float e = (hi - (s - bp)) + (x - bp);
-    lo = lo + e;
-    const float h2 = s + lo;
-    lo = lo - (h2 - s);
-    hi = h2;
-}
-
-#define TMEM_LD8(taddr, r)                                                                   \
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"     \
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),     \
-                   "=r"(r[6]), "=r"(r[7])                                                      \
-                 : "r"(taddr))
+struct SplitUpd {
+    const int32_t *row_tile;     // global row -> tile index
+    const int32_t *dx, *dy;      // [ntiles][m] scale exponents of the step
+    unsigned long long *nu;      // [ntiles][m] column maxima (bit patterns)
+    int64_t m;                   // row length of the segment arrays
+    int col0;                    // global column of local column 0
+};
+constexpr int kMaxSlots = 12;    // tile rows met by one 128-row CTA tile (tiles >= 15 rows)
 
 // C[i, j] (FP64, column-major, rows < M, cols < N) = 2^(ea_i + eb_j) *
-// sum_k A~_ik B~_kj over k < kend[N tile]
+// sum_k A~_ik B~_kj over k < K (kend[N tile], or kuni when kend is null);
+// with UPD the tile-update epilogue instead.  A slice p of this product
+// starts at row aRow0 + p * aMpad of the A tensor map.
+template <bool UPD>
 __global__ void __launch_bounds__(kSplitThreads, 1)
     k_split_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                 int S, int M, int N, int Mpad, int Npad, const int *__restrict__ kend,
-                 const int *__restrict__ ea, const int *__restrict__ eb,
-                 double *__restrict__ C, int64_t ldc, int *err) {
+                 int S, int M, int N, int aRow0, int aMpad, int Npad, const int *__restrict__ kend,
+                 int kuni, const int *__restrict__ ea, const int *__restrict__ eb,
+                 double *__restrict__ C, int64_t ldc, SplitUpd upd, int *err) {
     extern __shared__ unsigned char smraw[];
     unsigned char *base = (unsigned char *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
     uint64_t *bars = (uint64_t *)(base + 2 * kStageBytes);
     // bars[0..1] full, bars[2..3] empty, bars[4] acc_full, bars[5] acc_empty
     uint32_t *tmem_holder = (uint32_t *)(bars + 8);
+    unsigned long long *red = (unsigned long long *)(bars + 16);   // [kMaxSlots][kTN]
+    int *sdx = (int *)(red + kMaxSlots * kTN);                        // [kMaxSlots][kTN]
+    int *sdy = sdx + kMaxSlots * kTN;                                 // [kMaxSlots][kTN]
+    int *seb = sdy + kMaxSlots * kTN;                                 // [kTN]
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nt = gridDim.x - 1 - blockIdx.x;   // heaviest column tiles first
     const int mt = blockIdx.y;
     const int n0 = nt * kTN, m0 = mt * kTM;
-    const int K = kend[nt];
+    const int K = kend ? kend[nt] : kuni;
+    if (UPD)
+        for (int i = tid; i < kMaxSlots * kTN; i += kSplitThreads) red[i] = 0ull;
     const int nst = K / kTK;
     const int chunks = (nst + kChunkStages - 1) / kChunkStages;
 
@@ -267,7 +198,8 @@ __global__ void __launch_bounds__(kSplitThreads, 1)
                 unsigned char *sa = base + st * kStageBytes;
                 unsigned char *sb = sa + kSplitMaxS * kStageA;
                 for (int p = 0; p < S; p++)
-                    tma2d(saddr(sa + p * kStageA), &tmA, it * kTK, p * Mpad + m0, saddr(&bars[st]));
+                    tma2d(saddr(sa + p * kStageA), &tmA, it * kTK, aRow0 + p * aMpad + m0,
+                          saddr(&bars[st]));
                 for (int q = 0; q < S; q++)
                     tma2d(saddr(sb + q * kStageB), &tmB, it * kTK, q * Npad + n0, saddr(&bars[st]));
                 issued = it + 1;
@@ -290,9 +222,9 @@ __global__ void __launch_bounds__(kSplitThreads, 1)
                 const uint32_t sa = saddr(base + st * kStageBytes);
                 const uint32_t sb = sa + kSplitMaxS * kStageA;
                 for (int p = 0; p < S; p++)
-                    for (int q = 0; p + q < S; q++) {
-                        const int dgl = p + q;
+                    for (int q = 0; p + q < S; q++)
                         for (int kk = 0; kk < kTK / 16; kk++) {
+                            const int dgl = p + q;
                             // the first product of a diagonal in a chunk overwrites it
                             const int acc = (sic == 0 && kk == 0 && p == 0) ? 0 : 1;
                             const uint64_t ad = desc_sw64(sa + p * kStageA + kk * 32);
@@ -303,7 +235,6 @@ __global__ void __launch_bounds__(kSplitThreads, 1)
                                     tmem + dgl * kTN),
                                 "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
                         }
-                    }
                 asm volatile(
                     "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                         saddr(&bars[2 + st])));
@@ -317,6 +248,23 @@ __global__ void __launch_bounds__(kSplitThreads, 1)
         const int quarter = warp & 3, half = warp >> 2;
         const int row = m0 + quarter * 32 + lane;
         const int cb0 = half * 32;
+        if (UPD) {   // exponent tables of this CTA's (tile row, column) pairs
+            const int rlo = upd.row_tile[m0], rhi = upd.row_tile[min(m0 + kTM, M) - 1];
+            const int cnt = (rhi - rlo + 1) * kTN;
+            for (int i = tid; i < cnt; i += 256) {
+                const int sl = i / kTN, c = i % kTN, col = n0 + c;
+                int dxv = 0, dyv = kFresh;
+                if (col < N) {
+                    const int64_t at = (int64_t)(rlo + sl) * upd.m + upd.col0 + col;
+                    dxv = upd.dx[at];
+                    dyv = upd.dy[at];
+                }
+                sdx[i] = dxv;
+                sdy[i] = dyv;
+            }
+            if (tid < kTN) seb[tid] = (n0 + tid < N) ? eb[n0 + tid] : 0;
+            asm volatile("bar.sync 1, 256;" ::: "memory");
+        }
         float hi[32], lo[32];
 #pragma unroll
         for (int j = 0; j < 32; j++) { hi[j] = 0.0f; lo[j] = 0.0f; }
@@ -342,16 +290,18 @@ __global__ void __launch_bounds__(kSplitThreads, 1)
                 asm volatile("tcgen05.wait::ld.sync.aligned;");
 #pragma unroll
                 for (int j = 0; j < 8; j++) {
-                    // diagonals 3.. (small) summed in FP32 first, then the
-                    // leading three and that sum added exactly
+                    // diagonal D is below about 2^(-7D) of diagonal 0:
+                    // diagonals 5.. are summed in FP32 (rounding near 2^-58
+                    // of the leading term), diagonals 0-4 and that sum are
+                    // added to the double-float accumulator one by one
                     float small = 0.0f;
 #pragma unroll
-                    for (int dgl = kSplitMaxS - 1; dgl >= 3; dgl--)
+                    for (int dgl = kSplitMaxS - 1; dgl >= 5; dgl--)
                         small += __uint_as_float(v[dgl][j]);
                     const int jj = cb * 8 + j;
-                    df_add(hi[jj], lo[jj], __uint_as_float(v[0][j]));
-                    df_add(hi[jj], lo[jj], __uint_as_float(v[1][j]));
-                    df_add(hi[jj], lo[jj], __uint_as_float(v[2][j]));
+#pragma unroll
+                    for (int dgl = 0; dgl < 5; dgl++)
+                        df_add(hi[jj], lo[jj], __uint_as_float(v[dgl][j]));
                     df_add(hi[jj], lo[jj], small);
                 }
             }
@@ -360,19 +310,80 @@ __global__ void __launch_bounds__(kSplitThreads, 1)
             if (lane == 0)
                 asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(&bars[5])));
         }
-        if (row < M) {
+        if (!UPD && row < M) {
             const int er = ea[row];
 #pragma unroll
             for (int j = 0; j < 32; j++) {
                 const int col = n0 + cb0 + j;
                 if (col < N)
-                    C[row + (int64_t)col * ldc] =
-                        scale2((double)hi[j] + (double)lo[j], er + eb[col]);
+                    C[row + (int64_t)col * ldc] = df_to_double(hi[j], lo[j], er + eb[col]);
+            }
+        }
+        if (UPD) {
+            // rows of one tile row r are a contiguous run of lanes: the
+            // column maximum of each run is a segmented suffix max over
+            // shuffles, and the run's first lane merges it into red[]
+            const bool rv = row < M;
+            const int slot = rv ? upd.row_tile[row] - upd.row_tile[m0] : kMaxSlots;
+            const int er = rv ? ea[row] : 0;
+            unsigned same = 0;   // bit k: lane + 2^k lies in the same run
+#pragma unroll
+            for (int k = 0; k < 5; k++) {
+                const int o = __shfl_down_sync(0xffffffffu, slot, 1 << k);
+                if (lane + (1 << k) < 32 && o == slot) same |= 1u << k;
+            }
+            const int up = __shfl_up_sync(0xffffffffu, slot, 1);
+            const bool head = rv && (lane == 0 || up != slot);
+            const int sbase = rv ? slot * kTN : 0;
+            double *crow = C + row + (int64_t)upd.col0 * ldc;
+#pragma unroll
+            for (int g = 0; g < 4; g++) {   // 8 columns: loads first, then the updates
+                double oldv[8];
+#pragma unroll
+                for (int q = 0; q < 8; q++) {
+                    const int c = cb0 + g * 8 + q;
+                    oldv[q] = 0.0;
+                    if (rv && n0 + c < N && sdy[sbase + c] != kFresh)
+                        oldv[q] = crow[(int64_t)(n0 + c) * ldc];
+                }
+#pragma unroll
+                for (int q = 0; q < 8; q++) {
+                    const int j = g * 8 + q, c = cb0 + j;
+                    if (n0 + c >= N) break;   // warp-uniform
+                    unsigned long long b = 0ull;
+                    if (rv) {
+                        const int dyv = sdy[sbase + c];
+                        const double prod =
+                            df_to_double(hi[j], lo[j], er + seb[c] + sdx[sbase + c]);
+                        double v;
+                        if (dyv == kFresh) v = -prod;
+                        else if (dyv >= -1022 && dyv <= 1023)   // old 2^dy exact in the FMA
+                            v = fma(oldv[q], pow2_normal(dyv), -prod);
+                        else v = scale2(oldv[q], dyv) - prod;
+                        crow[(int64_t)(n0 + c) * ldc] = v;
+                        b = (unsigned long long)abs_bits(v);
+                    }
+#pragma unroll
+                    for (int k = 0; k < 5; k++) {
+                        const unsigned long long o = __shfl_down_sync(0xffffffffu, b, 1 << k);
+                        if ((same >> k) & 1u) b = max(b, o);
+                    }
+                    if (head && b) atomicMax(&red[slot * kTN + c], b);
+                }
             }
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
+    if (UPD) {
+        const int r0 = upd.row_tile[m0];
+        for (int i = tid; i < kMaxSlots * kTN; i += kSplitThreads) {
+            const unsigned long long v = red[i];
+            const int col = n0 + i % kTN;
+            if (v != 0ull && col < N)
+                atomicMax(&upd.nu[(int64_t)(r0 + i / kTN) * upd.m + upd.col0 + col], v);
+        }
+    }
     if (warp == 8)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                      "r"(kTmemCols));
@@ -385,7 +396,7 @@ __global__ void __launch_bounds__(kSplitThreads, 1)
 static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 static std::once_flag g_encode_once;
 
-static bool get_encoder() {
+bool get_encoder() {
     std::call_once(g_encode_once, [] {
         cudaDriverEntryPointQueryResult q;
         void *fn = nullptr;
@@ -399,7 +410,7 @@ static bool get_encoder() {
     return g_encode != nullptr;
 }
 
-static bool make_map(CUtensorMap *tm, void *ptr, int rows, int kpad, int box_rows) {
+bool make_map(CUtensorMap *tm, void *ptr, int rows, int kpad, int box_rows) {
     const cuuint64_t dims[2] = {(cuuint64_t)kpad, (cuuint64_t)rows};
     const cuuint64_t strides[1] = {(cuuint64_t)kpad * 2};
     const cuuint32_t box[2] = {(cuuint32_t)kTK, (cuuint32_t)box_rows};
@@ -437,9 +448,118 @@ cudaError_t launch_split_gemm(const double *A, int64_t lda, const double *B, int
     if (!make_map(&tmA, sa, S * Mpad, Kpad, kTM) || !make_map(&tmB, sb, S * Npad, Kpad, kTN))
         return cudaErrorInvalidValue;
     const size_t smem = split_smem_bytes();
-    cudaFuncSetAttribute(k_split_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_split_gemm<<<dim3(Npad / kTN, Mpad / kTM), kSplitThreads, smem, st>>>(
-        tmA, tmB, S, M, N, Mpad, Npad, kend, ea, eb, C, ldc, err);
+    cudaFuncSetAttribute(k_split_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    SplitUpd none = {};
+    k_split_gemm<false><<<dim3(Npad / kTN, Mpad / kTM), kSplitThreads, smem, st>>>(
+        tmA, tmB, S, M, N, 0, Mpad, Npad, kend, 0, ea, eb, C, ldc, none, err);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// tile updates in split precision
+// ---------------------------------------------------------------------------
+
+// Slices of every panel T[0:t0_s, tile s] (s >= 1) at once: panel s holds
+// S slices of Mpad_s = roundup(t0_s, 128) rows x Kp columns starting at row
+// prow0[s] of the buffer; row exponents (per panel row) at pea[s] + i.
+// One CTA per 32 rows of one panel; 256 threads.
+__global__ void __launch_bounds__(256)
+    k_slice_panels(const double *__restrict__ T, int64_t ldt, const int32_t *__restrict__ tstart,
+                   const int32_t *__restrict__ prow0, const int32_t *__restrict__ pea, int S,
+                   int Kp, __nv_bfloat16 *__restrict__ out, int *__restrict__ ea) {
+    const int s = blockIdx.y + 1;
+    const int t0 = tstart[s], ts = tstart[s + 1] - t0;
+    const int mpad = (t0 + kTM - 1) / kTM * kTM;
+    const int i0 = blockIdx.x * 32;
+    if (i0 >= mpad) return;
+    __shared__ long long rm[32][9];
+    __shared__ int rex[32];
+    __shared__ __nv_bfloat16 sd[kSplitMaxS][32][64 + 2];
+    const int tid = threadIdx.x;
+    {   // row maxima over the panel's columns: 8 threads per row
+        const int r = tid / 8, part = tid % 8;
+        const int i = i0 + r;
+        long long b = 0;
+        if (i < t0)
+            for (int k = part; k < ts; k += 8) b = max(b, abs_bits(T[i + (int64_t)(t0 + k) * ldt]));
+        rm[r][part] = b;
+    }
+    __syncthreads();
+    if (tid < 32) {
+        long long b = 0;
+        for (int q = 0; q < 8; q++) b = max(b, rm[tid][q]);
+        rex[tid] = exp_from_max((unsigned long long)b);
+        ea[pea[s] + i0 + tid] = rex[tid];
+    }
+    __syncthreads();
+    for (int kh = 0; kh < Kp; kh += 64) {   // 64 columns at a time
+        for (int e = tid; e < 32 * 64; e += 256) {
+            const int r = e % 32, c = e / 32;
+            const int i = i0 + r, k = kh + c;
+            int d[kSplitMaxS] = {0, 0, 0, 0, 0, 0, 0, 0};
+            if (i < t0 && k < ts) digits7(T[i + (int64_t)(t0 + k) * ldt], rex[r], S, d);
+            for (int p = 0; p < S; p++) sd[p][r][c] = digit_bf16(d[p], p);
+        }
+        __syncthreads();
+        for (int e = tid; e < 32 * 64; e += 256) {
+            const int r = e / 64, c = e % 64;
+            for (int p = 0; p < S; p++)
+                out[((size_t)prow0[s] + (size_t)p * mpad + i0 + r) * Kp + kh + c] = sd[p][r][c];
+        }
+        __syncthreads();
+    }
+}
+
+// Once per call: slice every panel of T; encode the two tensor maps.
+cudaError_t split_update_prepare(const double *T, int64_t ldt, int n, int ntiles, int maxtile,
+                                 const int32_t *tstart_d, const int32_t *prow0_d,
+                                 const int32_t *pea_d, int total_rows, int S, int m,
+                                 __nv_bfloat16 *panels, int *ea_panels, __nv_bfloat16 *sb,
+                                 SplitUpdateCtx *ctx, cudaStream_t st) {
+    if (!get_encoder()) return cudaErrorInvalidValue;
+    ctx->S = S;
+    ctx->Kp = maxtile <= 64 ? 64 : 128;
+    ctx->Npad = split_pad_n(m);
+    if (ntiles > 1) {
+        const int maxblocks = split_pad_m(n) / 32;   // >= roundup(t0_s, 128) / 32 for all s
+        k_slice_panels<<<dim3(maxblocks, ntiles - 1), 256, 0, st>>>(
+            T, ldt, tstart_d, prow0_d, pea_d, S, ctx->Kp, panels, ea_panels);
+    }
+    if (!make_map(&ctx->tmA, panels, total_rows > 0 ? total_rows : kTM, ctx->Kp, kTM) ||
+        !make_map(&ctx->tmB, sb, S * ctx->Npad, ctx->Kp, kTN) ||
+        !make_map(&ctx->tmB32, sb, S * ctx->Npad, ctx->Kp, 32))
+        return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+// Step s: slice X_s = Y[t0_s:t1_s, col0:m], then Y_r -= T_rs X_s for all rows
+// above tile s with the robust epilogue.
+cudaError_t split_update_step(const SplitUpdateCtx &ctx, int t0, int ts, int prow0, int pea,
+                              int col0, int m, double *Y, int64_t ldy, const int *ea_panels,
+                              __nv_bfloat16 *sb, unsigned long long *colmax, int *eb,
+                              const int32_t *row_tile, const int32_t *dx, const int32_t *dy,
+                              double *seg_nu, int *err, cudaStream_t st) {
+    const int N = m - col0;
+    if (N <= 0 || t0 <= 0) return cudaSuccess;
+    const double *B = Y + t0 + (int64_t)col0 * ldy;
+    k_col_max<<<(N + 7) / 8, 256, 0, st>>>(B, ldy, ts, N, colmax);
+    k_slice_cols<<<dim3((ctx.Kp + 255) / 256, split_pad_n(N)), 256, 0, st>>>(
+        B, ldy, ts, N, ctx.S, colmax, sb, ctx.Npad, ctx.Kp, eb);
+    const int mpad = (t0 + kTM - 1) / kTM * kTM;
+    const size_t smem = split_smem_bytes();
+    cudaFuncSetAttribute(k_split_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    SplitUpd upd;
+    upd.row_tile = row_tile;
+    upd.dx = dx;
+    upd.dy = dy;
+    upd.nu = (unsigned long long *)seg_nu;
+    upd.m = m;
+    upd.col0 = col0;
+    k_split_gemm<true><<<dim3(split_pad_n(N) / kTN, mpad / kTM), kSplitThreads, smem, st>>>(
+        ctx.tmA, ctx.tmB, ctx.S, t0, N, prow0, mpad, ctx.Npad, nullptr, (ts + kTK - 1) / kTK * kTK,
+        ea_panels + pea, eb, Y, ldy, upd, err);
     return cudaGetLastError();
 }
 
