@@ -200,8 +200,12 @@ __global__ void __launch_bounds__(kSplitThreads, 1)
                 for (int p = 0; p < S; p++)
                     tma2d(saddr(sa + p * kStageA), &tmA, it * kTK, aRow0 + p * aMpad + m0,
                           saddr(&bars[st]));
-                for (int q = 0; q < S; q++)
-                    tma2d(saddr(sb + q * kStageB), &tmB, it * kTK, q * Npad + n0, saddr(&bars[st]));
+                // B as [column half c][slice q] boxes of 32 rows, so the
+                // slices of one half lie one after another
+                for (int c = 0; c < 2; c++)
+                    for (int q = 0; q < S; q++)
+                        tma2d(saddr(sb + (c * kSplitMaxS + q) * (kStageB / 2)), &tmB, it * kTK,
+                              q * Npad + n0 + c * 32, saddr(&bars[st]));
                 issued = it + 1;
             }
             // the copies of the last stages have landed before the CTA ends
@@ -210,8 +214,7 @@ __global__ void __launch_bounds__(kSplitThreads, 1)
         }
     } else if (warp == 8) {
         if (lane == 0) {   // MMA issue
-            const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) |
-                                   ((uint32_t)(kTN >> 3) << 17) | ((uint32_t)(kTM >> 4) << 24);
+            const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTM >> 4) << 24);
             for (int it = 0; it < nst; it++) {
                 const int st = it & 1;
                 const int c = it / kChunkStages, sic = it % kChunkStages;
@@ -221,20 +224,28 @@ __global__ void __launch_bounds__(kSplitThreads, 1)
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 const uint32_t sa = saddr(base + st * kStageBytes);
                 const uint32_t sb = sa + kSplitMaxS * kStageA;
-                for (int p = 0; p < S; p++)
-                    for (int q = 0; p + q < S; q++)
-                        for (int kk = 0; kk < kTK / 16; kk++) {
-                            const int dgl = p + q;
-                            // the first product of a diagonal in a chunk overwrites it
-                            const int acc = (sic == 0 && kk == 0 && p == 0) ? 0 : 1;
+                // One MMA of A_p against the S - p slices of a column half
+                // (N = 32 (S - p)), written at column 32 p of the half's 256,
+                // adds A_p B_q to diagonal p + q for every q: 2 S wide MMAs
+                // per K step instead of S (S + 1) narrow ones (narrow MMAs
+                // complete one at a time).
+                for (int kk = 0; kk < kTK / 16; kk++)
+                    for (int hf = 0; hf < 2; hf++) {
+                        const uint64_t bd =
+                            desc_sw64(sb + hf * kSplitMaxS * (kStageB / 2) + kk * 32);
+                        for (int p = 0; p < S; p++) {
+                            const uint32_t id = idesc | ((uint32_t)(((S - p) * 32) >> 3) << 17);
                             const uint64_t ad = desc_sw64(sa + p * kStageA + kk * 32);
-                            const uint64_t bd = desc_sw64(sb + q * kStageB + kk * 32);
+                            // the first K step of a chunk overwrites (p = 0
+                            // covers every diagonal of the half)
+                            const int acc = (sic == 0 && kk == 0 && p == 0) ? 0 : 1;
                             asm volatile(
                                 "{\n.reg .pred pp;\nsetp.ne.b32 pp, %4, 0;\n"
                                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, pp;\n}\n" ::"r"(
-                                    tmem + dgl * kTN),
-                                "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+                                    tmem + (uint32_t)(hf * 256 + p * 32)),
+                                "l"(ad), "l"(bd), "r"(id), "r"(acc));
                         }
+                    }
                 asm volatile(
                     "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                         saddr(&bars[2 + st])));
@@ -280,7 +291,7 @@ __global__ void __launch_bounds__(kSplitThreads, 1)
                 for (int dgl = 0; dgl < kSplitMaxS; dgl++) {
                     if (dgl < S) {
                         const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) +
-                                            (uint32_t)(dgl * kTN + cb0 + cb * 8);
+                                            (uint32_t)(half * 256 + dgl * 32 + cb * 8);
                         TMEM_LD8(ta, v[dgl]);
                     } else {
 #pragma unroll
@@ -445,7 +456,7 @@ cudaError_t launch_split_gemm(const double *A, int64_t lda, const double *B, int
     k_slice_cols<<<dim3((Kpad + 255) / 256, Npad), 256, 0, st>>>(B, ldb, K, N, S, colmax, sb,
                                                                   Npad, Kpad, eb);
     CUtensorMap tmA, tmB;
-    if (!make_map(&tmA, sa, S * Mpad, Kpad, kTM) || !make_map(&tmB, sb, S * Npad, Kpad, kTN))
+    if (!make_map(&tmA, sa, S * Mpad, Kpad, kTM) || !make_map(&tmB, sb, S * Npad, Kpad, 32))
         return cudaErrorInvalidValue;
     const size_t smem = split_smem_bytes();
     cudaFuncSetAttribute(k_split_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -527,7 +538,6 @@ cudaError_t split_update_prepare(const double *T, int64_t ldt, int n, int ntiles
             T, ldt, tstart_d, prow0_d, pea_d, S, ctx->Kp, panels, ea_panels);
     }
     if (!make_map(&ctx->tmA, panels, total_rows > 0 ? total_rows : kTM, ctx->Kp, kTM) ||
-        !make_map(&ctx->tmB, sb, S * ctx->Npad, ctx->Kp, kTN) ||
         !make_map(&ctx->tmB32, sb, S * ctx->Npad, ctx->Kp, 32))
         return cudaErrorInvalidValue;
     return cudaGetLastError();
@@ -558,7 +568,7 @@ cudaError_t split_update_step(const SplitUpdateCtx &ctx, int t0, int ts, int pro
     upd.m = m;
     upd.col0 = col0;
     k_split_gemm<true><<<dim3(split_pad_n(N) / kTN, mpad / kTM), kSplitThreads, smem, st>>>(
-        ctx.tmA, ctx.tmB, ctx.S, t0, N, prow0, mpad, ctx.Npad, nullptr, (ts + kTK - 1) / kTK * kTK,
+        ctx.tmA, ctx.tmB32, ctx.S, t0, N, prow0, mpad, ctx.Npad, nullptr, (ts + kTK - 1) / kTK * kTK,
         ea_panels + pea, eb, Y, ldy, upd, err);
     return cudaGetLastError();
 }

@@ -152,9 +152,9 @@ bool get_encoder();
 bool make_map(CUtensorMap *tm, void *ptr, int rows, int kpad, int box_rows);
 
 // per-call state of the split tile updates: the tensor maps of the panel
-// slices (A) and of one step's column slices (B)
+// slices (A, 128-row boxes) and of one step's column slices (B, 32-row boxes)
 struct SplitUpdateCtx {
-    CUtensorMap tmA, tmB, tmB32;
+    CUtensorMap tmA, tmB32;
     int S, Kp, Npad;
 };
 
