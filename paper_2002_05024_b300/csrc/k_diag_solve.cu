@@ -248,6 +248,7 @@ __device__ void diag_tile(int s, int list_pos0, const double *__restrict__ T, in
     constexpr int kThreads = 32 * W;
     constexpr int kUnits = Lanes<C>::U * W;
     constexpr int ys = kUnits + 1;
+    constexpr int FW = C ? 8 : 4;                      // factor doubles per block
     const int t0 = P.tile_start[s];
     const int ts = P.tile_start[s + 1] - t0;
     const int kb0 = P.tile_blk[s], kb1 = P.tile_blk[s + 1];
@@ -262,9 +263,9 @@ __device__ void diag_tile(int s, int list_pos0, const double *__restrict__ T, in
     double *btau = Ts + ts * ts;                       // [kMaxTile]
     double *umu = btau + kMaxTile;                     // [kUnits]
     double *yr = umu + kUnits;                         // [ts][ys]
-    double *yi = yr + ts * ys;                         // [ts][ys]
-    double *fac = yi + ts * ys;                        // [kUnits][ts][8]
-    int *bq = (int *)(fac + (size_t)kUnits * ts * 8);  // [kMaxTile]
+    double *yi = yr + ts * ys;                         // [ts][ys], complex units only
+    double *fac = yi + (C ? ts * ys : 0);              // [kUnits][ts][FW]
+    int *bq = (int *)(fac + (size_t)kUnits * ts * FW); // [kMaxTile]
     int *bsz = bq + kMaxTile;                          // [kMaxTile]
     int *btf = bsz + kMaxTile;                         // [kMaxTile] exponent field of btau
     int *ford = btf + kMaxTile;                        // [kMaxTile] 1x1 blocks, then 2x2
@@ -310,10 +311,9 @@ __device__ void diag_tile(int s, int list_pos0, const double *__restrict__ T, in
         if (c >= 0 && !uown[uu]) {
             cp_async8(&yr[i * ys + uu], &Y[(t0 + i) + (int64_t)c * ldy]);
             if (C) cp_async8(&yi[i * ys + uu], &Y[(t0 + i) + (int64_t)(c + 1) * ldy]);
-            else yi[i * ys + uu] = 0.0;
         } else {
             yr[i * ys + uu] = 0.0;
-            yi[i * ys + uu] = 0.0;
+            if (C) yi[i * ys + uu] = 0.0;
         }
     }
     asm volatile("cp.async.commit_group;");
@@ -333,7 +333,7 @@ __device__ void diag_tile(int s, int list_pos0, const double *__restrict__ T, in
     const double smin = fmax(kUlp * (fabs(lr) + fabs(li)), kSafeMin * ((double)P.n / kUlp));
     double *myr = yr + slot;
     double *myi = yi + slot;
-    double *myfac = fac + (size_t)slot * ts * 8;
+    double *myfac = fac + (size_t)slot * ts * FW;
     int *myfacp = facp + slot * ts;
 
     // factors of every block this unit solves, spread over its lanes in
@@ -343,9 +343,13 @@ __device__ void diag_tile(int s, int list_pos0, const double *__restrict__ T, in
             const int kk = ford[f];
             if (own && kb0 + kk >= kown) continue;
             const Fac F = factor<C>(bsz[kk], Ts, ts, bq[kk], lr, li, smin);
-            double *fp = myfac + kk * 8;
-            fp[0] = F.ia.re; fp[1] = F.ia.im; fp[2] = F.l.re; fp[3] = F.l.im;
-            fp[4] = F.g.re;  fp[5] = F.g.im;  fp[6] = F.iu.re; fp[7] = F.iu.im;
+            double *fp = myfac + kk * FW;
+            if (C) {
+                fp[0] = F.ia.re; fp[1] = F.ia.im; fp[2] = F.l.re; fp[3] = F.l.im;
+                fp[4] = F.g.re;  fp[5] = F.g.im;  fp[6] = F.iu.re; fp[7] = F.iu.im;
+            } else {
+                fp[0] = F.ia.re; fp[1] = F.l.re; fp[2] = F.g.re; fp[3] = F.iu.re;
+            }
             myfacp[kk] = F.pr | (F.pc << 1);
         }
     }
@@ -381,11 +385,18 @@ __device__ void diag_tile(int s, int list_pos0, const double *__restrict__ T, in
         const Cx r1 = bs == 2 ? Cx{myr[(q + 1) * ys], C ? myi[(q + 1) * ys] : 0.0} : Cx{0.0, 0.0};
         Fac F;
         {
-            const double *fp = myfac + kk * 8;
-            F.ia = {fp[0], C ? fp[1] : 0.0};
-            F.l = {fp[2], C ? fp[3] : 0.0};
-            F.g = {fp[4], C ? fp[5] : 0.0};
-            F.iu = {fp[6], C ? fp[7] : 0.0};
+            const double *fp = myfac + kk * FW;
+            if (C) {
+                F.ia = {fp[0], fp[1]};
+                F.l = {fp[2], fp[3]};
+                F.g = {fp[4], fp[5]};
+                F.iu = {fp[6], fp[7]};
+            } else {
+                F.ia = {fp[0], 0.0};
+                F.l = {fp[1], 0.0};
+                F.g = {fp[2], 0.0};
+                F.iu = {fp[3], 0.0};
+            }
             const int pp = myfacp[kk];
             F.pr = pp & 1;
             F.pc = pp >> 1;
@@ -554,8 +565,9 @@ __global__ void __launch_bounds__(32 * W)
 template <int W, bool C>
 static size_t diag_smem_bytes(int t) {
     constexpr int kUnits = Lanes<C>::U * W;
-    return sizeof(double) * ((size_t)t * t + kMaxTile + kUnits + 2 * (size_t)t * (kUnits + 1) +
-                             (size_t)kUnits * t * 8) +
+    constexpr int FW = C ? 8 : 4;
+    return sizeof(double) * ((size_t)t * t + kMaxTile + kUnits +
+                             (C ? 2 : 1) * (size_t)t * (kUnits + 1) + (size_t)kUnits * t * FW) +
            sizeof(int) * (4 * (size_t)kMaxTile + 3 * kUnits + (size_t)kUnits * t);
 }
 
@@ -575,6 +587,9 @@ static void launch_w(int s, int ts, int nr, int nc, const double *T, int64_t ldt
     if (rct + cct == 0) return;
     cudaFuncSetAttribute(k_diag_solve<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)diag_smem<W>(W == 4 ? 64 : kMaxTile));
+    // two CTAs per SM (about 82 KB each for 64-row tiles)
+    cudaFuncSetAttribute(k_diag_solve<W>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         cudaSharedmemCarveoutMaxShared);
     k_diag_solve<W><<<rct + cct, 32 * W, diag_smem<W>(ts), st>>>(
         s, rct, T, ldt, p, tau, blk_tau, Y, ldy, seg_e, seg_nu, seg_dx, seg_dy);
 }
