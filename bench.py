@@ -58,7 +58,7 @@ def parse_args():
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--mode", choices=["fp64", "split"], default="split")
     ap.add_argument("--slices", type=int, default=0)
-    ap.add_argument("--cpu-sample", type=int, default=1024,
+    ap.add_argument("--cpu-sample", type=int, default=4096,
                     help="columns of the CPU-oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -72,7 +72,8 @@ def workload(n):
 
 def flop_counts(n, blocks, tile_start, with_q=True):
     """Algorithmic FP64 flops: total per the method's definition, and the
-    parts done by the tile-update GEMMs and by the back-transformation."""
+    parts done by the tile-update GEMMs and by the back-transformation (the
+    diagonal-tile solves do the rest of the substitution: total - upd - bt)."""
     tile_start = np.asarray(tile_start)
     total = 0.0
     upd = 0.0
@@ -89,6 +90,78 @@ def flop_counts(n, blocks, tile_start, with_q=True):
             for s in range(1, c):
                 upd += 2.0 * tile_start[s] * (tile_start[s + 1] - tile_start[s])
     return total, upd, bt
+
+
+# kernel class -> source files whose content a stored DRAM-traffic figure
+# belongs to (per mode)
+KERNEL_SOURCES = {
+    ("diag_solve", "fp64"): ["k_diag_solve.cu"], ("diag_solve", "split"): ["k_diag_solve.cu"],
+    ("tile_update", "fp64"): ["k_gemm.cu"],
+    ("tile_update", "split"): ["k_split_update.cu", "k_split.cu", "split_common.cuh"],
+    ("backtransform", "fp64"): ["k_gemm.cu"],
+    ("backtransform", "split"): ["k_split.cu", "split_common.cuh"],
+}
+TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
+
+
+def source_digest(files):
+    import hashlib
+    h = hashlib.sha1()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_2002_05024_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def stored_traffic(kernel, mode, n, tile):
+    """DRAM bytes per launch from the committed ncu summary, or None when
+    there is none for this kernel, workload and mode, or when the kernel's
+    source changed since the capture."""
+    try:
+        rec = json.load(open(TRAFFIC))[f"{kernel}/{mode}/n{n}/tile{tile}"]
+    except Exception:
+        return None
+    files = KERNEL_SOURCES.get((kernel, mode))
+    if not files or rec.get("source_sha1") != source_digest(files):
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+def rooflines(prof, steps, mode, slices, F_diag, F_upd, F_bt, peaks, n, tile):
+    """Per kernel class: algorithmic work per step / event-timed kernel time
+    per step against the unit that bounds it.  Diagonal solves and FP64-mode
+    GEMMs: FP64 flops on the FP64 pipe ("alu"; peak from the measured DFMA
+    rate x SMs x max clock).  Split-mode GEMMs: the S (S + 1) / 2 BF16 slice
+    products the method needs per FP64 multiply-add, on the tensor cores
+    ("tensor"; peak = the measured sustained cuBLAS BF16 rate, as these
+    kernels run inside a long step)."""
+    sm_max = float(peaks.get("sm_max_mhz", 2032.0))
+    fp64_peak = N_SMS * FP64_FLOP_PER_CLK_PER_SM * sm_max * 1e6 / 1e12
+    bf16 = peaks.get("bf16_tflops_sustained")
+    bf16_src = "of measured (sustained cuBLAS BF16)" if bf16 else "of fallback"
+    bf16 = float(bf16 or 1400.0)
+    pairs = slices * (slices + 1) // 2
+    work = {"diag_solve": (F_diag, False), "tile_update": (F_upd, mode == "split"),
+            "backtransform": (F_bt, mode == "split")}
+    out = {}
+    for k, (ms, nl) in prof.items():
+        if k not in work or ms <= 0 or nl <= 0:
+            continue
+        f64, tensor = work[k]
+        sec = ms / steps / 1e3
+        if tensor:
+            alg, peak, bound, src = pairs * f64, bf16, "tensor", bf16_src
+        else:
+            alg, peak, bound, src = f64, fp64_peak, "alu", \
+                "of derived FP64 peak (measured 4 flop/clk/SM x 148 SMs x max SM clock)"
+        achieved = alg / sec / 1e12
+        tr = stored_traffic(k, mode, n, tile)
+        out[k] = {"kernel": k, "bound": bound, "achieved": achieved, "peak": peak,
+                  "unit": "TFLOP/s", "frac": achieved / peak, "traffic": tr,
+                  "peak_source": src, "launches_per_step": nl / steps,
+                  "ms_per_step": ms / steps,
+                  "alg_flops_per_launch": alg / (nl / steps)}
+    return out
 
 
 def measured_peaks():
@@ -143,9 +216,12 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(T, blocks, Q, sample_cols, seed=5):
+def cpu_baseline(T, blocks, Q, sample_cols, seed=5, gpu=None):
     """The oracle, as it stands, on a seeded random sample of the workload's
-    columns, on all host cores."""
+    columns, on all host cores.  With gpu = (X, scale_exp) of the timed run,
+    the sampled columns are also compared with the GPU's (largest exponent
+    difference and normwise relative difference after bringing both to one
+    exponent)."""
     import oracle
     n = T.shape[0]
     rng = np.random.default_rng(seed)
@@ -164,10 +240,56 @@ def cpu_baseline(T, blocks, Q, sample_cols, seed=5):
     dt = time.perf_counter() - t
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     threads = int(os.environ.get("OMP_NUM_THREADS", cores))
-    return {"value": X.shape[1] / dt, "unit": "columns/s", "cores": threads, "kind": "oracle",
-            "columns": X.shape[1], "seconds": dt,
-            "sample": f"{X.shape[1]} randomly chosen columns (seed {seed}) of the n={n} "
-                      f"workload incl. back-transformation, {dt:.2f} s"}
+    out = {"value": X.shape[1] / dt, "unit": "columns/s", "cores": threads, "kind": "oracle",
+           "columns": X.shape[1], "seconds": dt,
+           "sample": f"{X.shape[1]} randomly chosen columns (seed {seed}) of the n={n} "
+                     f"workload incl. back-transformation, {dt:.2f} s"}
+    if gpu is not None:
+        Xg, eg = gpu
+        col, oc, max_de, max_rel = 0, 0, 0, 0.0
+        for p, sz in blocks:
+            if sel[p]:
+                de = int(e[oc]) - int(eg[col])
+                a = X[:, oc:oc + sz]
+                b = np.ldexp(Xg[:, col:col + sz], de)
+                rel = np.max(np.abs(a - b).sum(axis=1)) / np.max(np.abs(a).sum(axis=1))
+                max_de, max_rel = max(max_de, abs(de)), max(max_rel, float(rel))
+                oc += sz
+            col += sz
+        out["gpu_vs_oracle"] = {"columns": oc, "max_exponent_diff": max_de,
+                                "max_rel_diff": max_rel}
+    return out
+
+
+def residual_sample(T, Q, X, lr, li, blocks, k=16, seed=7):
+    """Normalised residual ||T y - lambda y||_1 / (||T||_1 ||y||_1 u) of k
+    seeded random eigenvalues of the GPU result, y = Q^T x in long double
+    (the Schur-coordinate residual of x; no product with Q enters it)."""
+    n = T.shape[0]
+    rng = np.random.default_rng(seed)
+    starts, col = [], 0
+    for p, sz in blocks:
+        starts.append((col, sz))
+        col += sz
+    pick = rng.choice(len(starts), size=min(k, len(starts)), replace=False)
+    Tl = T.astype(np.longdouble)
+    Ql = Q.astype(np.longdouble)
+    T1 = np.abs(Tl).sum(axis=0).max()
+    worst = 0.0
+    for b in pick:
+        c, sz = starts[b]
+        if sz == 2:
+            x = X[:, c].astype(np.longdouble) + 1j * X[:, c + 1].astype(np.longdouble)
+            lam = np.longdouble(lr[c]) + 1j * np.longdouble(li[c])
+            y = Ql.T @ x.real + 1j * (Ql.T @ x.imag)
+            r = (Tl @ y.real + 1j * (Tl @ y.imag)) - lam * y
+        else:
+            y = Ql.T @ X[:, c].astype(np.longdouble)
+            r = Tl @ y - np.longdouble(lr[c]) * y
+        res = np.abs(r).sum() / (T1 * np.abs(y).sum() * np.finfo(np.float64).eps / 2)
+        worst = max(worst, float(res))
+    return {"eigenvalues": int(len(pick)), "max_normalised_residual": worst,
+            "max_over_n": worst / n, "gate": "<= 10 n"}
 
 
 def run_reference(args, rank, world):
@@ -221,6 +343,7 @@ def run_ours(args, rank, world, local_rank):
     _, tile_start = ev.plan_query(d, np.ascontiguousarray(np.diagonal(T, -1)),
                                   np.ascontiguousarray(np.diagonal(T, 1)), None, args.tile or 64)
     F, F_upd, F_bt = flop_counts(n, blocks, tile_start)
+    F_diag = max(F - F_upd - F_bt, 0.0)
 
     dT = torch.from_numpy(T).to(dev)
     dQ = torch.from_numpy(Q).to(dev)
@@ -275,18 +398,12 @@ def run_ours(args, rank, world, local_rank):
     tflops = world * F * args.steps / (elapsed_ms / 1e3) / 1e12
 
     # roofline of the dominant kernel (largest share of event-timed time)
-    kernel, (kms, kn) = max(prof.items(), key=lambda kv: kv[1][0])
     peaks = measured_peaks()
-    sm_max = float(peaks.get("sm_max_mhz", 2032.0))
-    fp64_peak = N_SMS * FP64_FLOP_PER_CLK_PER_SM * sm_max * 1e6 / 1e12
-    alg = {"backtransform": F_bt, "tile_update": F_upd}.get(kernel)
-    roofline = None
-    if alg is not None and kn:
-        per_launch = alg / (kn / args.steps)
-        achieved = per_launch / (kms / kn / 1e3) / 1e12
-        roofline = {"kernel": kernel, "bound": "alu", "achieved": achieved, "peak": fp64_peak,
-                    "unit": "TFLOP/s", "frac": achieved / fp64_peak, "traffic": None,
-                    "peak_source": "FP64 DFMA: 4 flop/clk/SM (measured) x 148 SMs x max SM clock"}
+    slices = (args.slices or 8) if args.mode == "split" else 0
+    tile = args.tile or 64
+    roofs = rooflines(prof, args.steps, args.mode, slices, F_diag, F_upd, F_bt, peaks, n, tile)
+    dominant = max(prof.items(), key=lambda kv: kv[1][0])[0]
+    roofline = roofs.get(dominant)
     gpu_launches = sum(c for _, c in prof.values())
 
     # end to end through the host-buffer entry point (pinned host memory)
@@ -331,25 +448,34 @@ def run_ours(args, rank, world, local_rank):
         if dist:
             dist.destroy_process_group()
         return
+    Xh, eh = X.cpu().numpy(), e.cpu().numpy()
+    quality = residual_sample(T, Q, Xh, lr.cpu().numpy(), li.cpu().numpy(), blocks)
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(T, blocks, Q, args.cpu_sample)
+        cpu = cpu_baseline(T, blocks, Q, args.cpu_sample, gpu=(Xh, eh))
         cpu.pop("columns")
         cpu.pop("seconds")
     line = {
         "metric": "eigvec columns/s (robust FP64 eigenvectors incl. back-transformation)",
         "value": value, "unit": "columns/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.mode == "fp64" else "bf16 slice products + f64",
+        "data": "synthetic",
         "config": {"workload": f"config-0 Schur form n={n} + Q (64 Householder reflectors), "
-                               f"all {m} columns, FP64",
+                               f"all {m} columns, "
+                               + ("FP64" if args.mode == "fp64" else
+                                  f"split precision ({slices} BF16 slices, FP32 exact "
+                                  "accumulation, FP64 recombination)"),
                    "n": n, "columns": m, "tile": args.tile or 64, "mode": args.mode,
                    "slices": (args.slices or 8) if args.mode == "split" else None,
                    "parallelism": "replicas",
                    "l2": "inputs larger than L2 (T, Q, X 128 MiB each)"},
         "tflops_fp64": tflops,
+        "quality": quality,
         "flops_per_step": F,
         "roofline": roofline,
+        "rooflines": roofs,
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
         "gpu_launches": gpu_launches,
         "clocks": clocks,

@@ -164,9 +164,10 @@ enum {
     EVEC_K_GATHER = 0,       /* diagonal gather for the plan */
     EVEC_K_NORMS = 1,        /* tile norms + input validation */
     EVEC_K_DIAG_SOLVE = 2,   /* robust diagonal-tile solves + decisions */
-    EVEC_K_TILE_UPDATE = 3,  /* FP64 off-diagonal tile updates */
+    EVEC_K_TILE_UPDATE = 3,  /* off-diagonal tile updates (FP64, or split:
+                                slicing + tensor-core products) */
     EVEC_K_FINALIZE = 4,     /* consolidation + canonical form */
-    EVEC_K_BACKTRANSFORM = 5,/* X = Q Y */
+    EVEC_K_BACKTRANSFORM = 5,/* X = Q Y (FP64, or split: slicing + products) */
     EVEC_K_CANONICALIZE = 6, /* canonical form after Q */
     EVEC_K_COUNT = 7
 };
@@ -176,9 +177,10 @@ enum {
 evec_status evec_profile(evec_handle h, int enable);
 
 /* Synchronise the handle's stream and return, per kernel class, the summed
- * event-timed milliseconds and the number of launches since the previous
- * read (arrays of nk entries, nk <= EVEC_K_COUNT; either may be NULL); then
- * reset the counters. */
+ * event-timed milliseconds and the number of kernel launches since the
+ * previous read (arrays of nk entries, nk <= EVEC_K_COUNT; either may be
+ * NULL); then reset the counters.  Kernels launched back to back for one
+ * operation (a slicing kernel and its product) share one timed interval. */
 evec_status evec_profile_read(evec_handle h, double *ms, int64_t *launches, int nk);
 
 /* Limits of evec_standard_noalloc. */

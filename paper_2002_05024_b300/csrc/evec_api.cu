@@ -29,7 +29,7 @@ void launch_gather_diagonals(const double *T, int64_t ldt, int64_t n, double *ou
                              cudaStream_t st);
 void launch_tile_norms(const double *T, int64_t ldt, const Plan &p, double *tau,
                        double *blk_tau, DevStatus *status, cudaStream_t st);
-void launch_diag_solve(int s, const double *T, int64_t ldt, const Plan &p,
+int launch_diag_solve(int s, const double *T, int64_t ldt, const Plan &p,
                        const int32_t *tile_start_h, const int32_t *tile_real_h,
                        const int32_t *tile_cplx_h,
                        const double *tau, const double *blk_tau, double *Y, int64_t ldy,
@@ -278,6 +278,7 @@ struct evec_ctx {
     struct Timed {
         int kind;
         cudaEvent_t a, b;
+        int nk;   // kernels launched in the interval
     };
     bool profiling = false;
     std::vector<Timed> live;
@@ -366,16 +367,17 @@ cudaEvent_t take_event(evec_handle h) {
     return e;
 }
 
-// Run one launch, bracketed by events when the handle is profiling.
+// Run one operation (launch() returns the number of kernels it launched),
+// bracketed by events when the handle is profiling.
 template <class F>
 void timed(evec_handle h, int kind, F &&launch) {
     if (!h->profiling) { launch(); return; }
     cudaEvent_t a = take_event(h), b = take_event(h);
-    if (!a || !b) { launch(); return; }
+    if (!a || !b) { h->prof_n[kind] += launch(); return; }
     cudaEventRecord(a, h->stream);
-    launch();
+    const int nk = launch();
     cudaEventRecord(b, h->stream);
-    h->live.push_back({kind, a, b});
+    h->live.push_back({kind, a, b, nk});
 }
 
 // Read T's three central diagonals and build the host plan.
@@ -384,7 +386,10 @@ evec_status plan_device_matrix(evec_handle h, int64_t n, const double *T, int64_
     const size_t cnt = (size_t)(3 * n > 2 ? 3 * n - 2 : 1);
     EVEC_TRY(grow_device(&h->diag_d, &h->diag_cap, cnt));
     EVEC_TRY(grow_host(&h->diag_h, &h->diag_h_cap, cnt));
-    timed(h, EVEC_K_GATHER, [&] { launch_gather_diagonals(T, ldt, n, h->diag_d, h->stream); });
+    timed(h, EVEC_K_GATHER, [&] {
+        launch_gather_diagonals(T, ldt, n, h->diag_d, h->stream);
+        return 1;
+    });
     EVEC_CUDA(cudaGetLastError());
     EVEC_CUDA(cudaMemcpyAsync(h->diag_h, h->diag_d, cnt * sizeof(double),
                               cudaMemcpyDeviceToHost, h->stream));
@@ -566,7 +571,7 @@ evec_status evec_profile_read(evec_handle h, double *ms, int64_t *launches, int 
         float e = 0.0f;
         if (cudaEventElapsedTime(&e, t.a, t.b) == cudaSuccess) h->prof_ms[t.kind] += e;
         else cudaGetLastError();
-        h->prof_n[t.kind] += 1;
+        h->prof_n[t.kind] += t.nk;
         h->spare.push_back(t.a);
         h->spare.push_back(t.b);
     }
@@ -682,8 +687,10 @@ evec_status evec_standard(evec_handle h, int64_t n, const double *T, int64_t ldt
         EVEC_TRY(grow_device(&h->ea, &h->ea_cap, (size_t)Mp));
     }
     cudaStream_t st = h->stream;
-    timed(h, EVEC_K_NORMS,
-          [&] { launch_tile_norms(T, ldt, dp, h->tau, h->blk_tau, h->status_d, st); });
+    timed(h, EVEC_K_NORMS, [&] {
+        launch_tile_norms(T, ldt, dp, h->tau, h->blk_tau, h->status_d, st);
+        return 1;
+    });
     SplitUpdateCtx sctx;
     if (mode == EVEC_SPLIT) {
         const int Kp = HP.max_tile <= 64 ? 64 : 128;
@@ -700,12 +707,13 @@ evec_status evec_standard(evec_handle h, int64_t n, const double *T, int64_t ldt
             ce = split_update_prepare(T, ldt, (int)n, N, HP.max_tile, dp.tile_start, h->prow0_d,
                                       h->pea_d, HP.panel_rows, slices, (int)m, h->panels,
                                       h->ea_panels, h->slB, &sctx, st);
+            return N > 1 ? 1 : 0;
         });
         EVEC_CUDA(ce);
     }
     for (int s = N - 1; s >= 0; s--) {
         timed(h, EVEC_K_DIAG_SOLVE, [&] {
-            launch_diag_solve(s, T, ldt, dp, HP.tile_start.data(), HP.tile_real.data(),
+            return launch_diag_solve(s, T, ldt, dp, HP.tile_start.data(), HP.tile_real.data(),
                               HP.tile_cplx.data(), h->tau,
                               h->blk_tau, Y, ldy, h->seg_e, h->seg_nu, h->seg_dx, h->seg_dy, st);
         });
@@ -713,42 +721,58 @@ evec_status evec_standard(evec_handle h, int64_t n, const double *T, int64_t ldt
             if (mode == EVEC_SPLIT) {
                 cudaError_t ce = cudaSuccess;
                 timed(h, EVEC_K_TILE_UPDATE, [&] {
-                    if (sctx.Kp == 64)
+                    if (sctx.Kp == 64) {   // slicing + panel-resident product
                         ce = split_update_step_resident(
                             sctx, HP.tile_start[s], HP.tile_start[s + 1] - HP.tile_start[s],
                             HP.prow0[s], HP.pea[s], HP.tile_col[s], (int)m, Y, ldy,
                             h->ea_panels, h->slB, h->eb, h->row_tile_d, h->seg_dx, h->seg_dy,
                             h->seg_nu, &h->status_d->timeout, h->nsm, st);
-                    else
+                        return 2;
+                    }
+                    // column maxima + slicing + streamed product
                     ce = split_update_step(sctx, HP.tile_start[s],
                                            HP.tile_start[s + 1] - HP.tile_start[s], HP.prow0[s],
                                            HP.pea[s], HP.tile_col[s], (int)m, Y, ldy, h->ea_panels,
                                            h->slB, h->cmax, h->eb, h->row_tile_d, h->seg_dx,
                                            h->seg_dy, h->seg_nu, &h->status_d->timeout, st);
+                    return 3;
                 });
                 EVEC_CUDA(ce);
             } else {
                 timed(h, EVEC_K_TILE_UPDATE, [&] {
                     launch_tile_update(s, T, ldt, dp, HP.max_tile, HP.tile_col.data(), Y, ldy,
                                        h->seg_dx, h->seg_dy, h->seg_nu, st);
+                    return 1;
                 });
             }
         }
     }
-    timed(h, EVEC_K_FINALIZE, [&] { launch_finalize(dp, Y, ldy, h->seg_e, scale_exp, st); });
+    timed(h, EVEC_K_FINALIZE, [&] {
+        launch_finalize(dp, Y, ldy, h->seg_e, scale_exp, st);
+        return 1;
+    });
     if (Q && mode == EVEC_SPLIT) {
         cudaError_t ce = cudaSuccess;
         timed(h, EVEC_K_BACKTRANSFORM, [&] {
             ce = launch_split_gemm(Q, ldq, Y, ldy, (int)n, (int)m, (int)n, slices, h->bt_kend_d, X,
                                    ldx, h->slA, h->slB, h->rmax, h->cmax, h->ea, h->eb,
                                    &h->status_d->timeout, st);
+            return 5;   // row / column maxima, two slicing kernels, product
         });
         EVEC_CUDA(ce);
-        timed(h, EVEC_K_CANONICALIZE, [&] { launch_canonicalize(dp, X, ldx, scale_exp, st); });
+        timed(h, EVEC_K_CANONICALIZE, [&] {
+            launch_canonicalize(dp, X, ldx, scale_exp, st);
+            return 1;
+        });
     } else if (Q) {
-        timed(h, EVEC_K_BACKTRANSFORM,
-              [&] { launch_backtransform(Q, ldq, dp, Y, ldy, X, ldx, st); });
-        timed(h, EVEC_K_CANONICALIZE, [&] { launch_canonicalize(dp, X, ldx, scale_exp, st); });
+        timed(h, EVEC_K_BACKTRANSFORM, [&] {
+            launch_backtransform(Q, ldq, dp, Y, ldy, X, ldx, st);
+            return 1;
+        });
+        timed(h, EVEC_K_CANONICALIZE, [&] {
+            launch_canonicalize(dp, X, ldx, scale_exp, st);
+            return 1;
+        });
     }
     EVEC_CUDA(cudaGetLastError());
     // eigenvalues per column, from the pinned plan buffer

@@ -37,7 +37,7 @@ void launch_gather_diagonals(const double *T, int64_t ldt, int64_t n, double *ou
                              cudaStream_t st);
 void launch_tile_norms(const double *T, int64_t ldt, const Plan &p, double *tau,
                        double *blk_tau, DevStatus *status, cudaStream_t st);
-void launch_diag_solve(int s, const double *T, int64_t ldt, const Plan &p,
+int launch_diag_solve(int s, const double *T, int64_t ldt, const Plan &p,
                        const int32_t *tile_start_h, const int32_t *tile_real_h,
                        const int32_t *tile_cplx_h,
                        const double *tau, const double *blk_tau, double *Y, int64_t ldy,

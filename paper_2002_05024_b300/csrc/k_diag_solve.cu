@@ -577,14 +577,14 @@ static size_t diag_smem(int t) {
 }
 
 template <int W>
-static void launch_w(int s, int ts, int nr, int nc, const double *T, int64_t ldt, const Plan &p,
+static int launch_w(int s, int ts, int nr, int nc, const double *T, int64_t ldt, const Plan &p,
                      const double *tau, const double *blk_tau, double *Y, int64_t ldy,
                      int32_t *seg_e, double *seg_nu, int32_t *seg_dx, int32_t *seg_dy,
                      cudaStream_t st) {
     constexpr int ur = Lanes<false>::U * W, uc = Lanes<true>::U * W;
     const int rct = (nr + ur - 1) / ur;
     const int cct = (nc + uc - 1) / uc;
-    if (rct + cct == 0) return;
+    if (rct + cct == 0) return 0;
     cudaFuncSetAttribute(k_diag_solve<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)diag_smem<W>(W == 4 ? 64 : kMaxTile));
     // two CTAs per SM (about 82 KB each for 64-row tiles)
@@ -592,9 +592,11 @@ static void launch_w(int s, int ts, int nr, int nc, const double *T, int64_t ldt
                          cudaSharedmemCarveoutMaxShared);
     k_diag_solve<W><<<rct + cct, 32 * W, diag_smem<W>(ts), st>>>(
         s, rct, T, ldt, p, tau, blk_tau, Y, ldy, seg_e, seg_nu, seg_dx, seg_dy);
+    return 1;
 }
 
-void launch_diag_solve(int s, const double *T, int64_t ldt, const Plan &p,
+// Returns the number of kernels launched (0 when no column is active).
+int launch_diag_solve(int s, const double *T, int64_t ldt, const Plan &p,
                        const int32_t *tile_start_h, const int32_t *tile_real_h,
                        const int32_t *tile_cplx_h, const double *tau, const double *blk_tau,
                        double *Y, int64_t ldy, int32_t *seg_e, double *seg_nu, int32_t *seg_dx,
@@ -604,9 +606,8 @@ void launch_diag_solve(int s, const double *T, int64_t ldt, const Plan &p,
     const int nc = p.ncplx - tile_cplx_h[s];
     // four warps share a tile of up to 64 rows; two for larger tiles
     if (ts <= 64)
-        launch_w<4>(s, ts, nr, nc, T, ldt, p, tau, blk_tau, Y, ldy, seg_e, seg_nu, seg_dx, seg_dy, st);
-    else
-        launch_w<2>(s, ts, nr, nc, T, ldt, p, tau, blk_tau, Y, ldy, seg_e, seg_nu, seg_dx, seg_dy, st);
+        return launch_w<4>(s, ts, nr, nc, T, ldt, p, tau, blk_tau, Y, ldy, seg_e, seg_nu, seg_dx, seg_dy, st);
+    return launch_w<2>(s, ts, nr, nc, T, ldt, p, tau, blk_tau, Y, ldy, seg_e, seg_nu, seg_dx, seg_dy, st);
 }
 
 }  // namespace evec
