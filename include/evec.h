@@ -169,7 +169,8 @@ enum {
     EVEC_K_FINALIZE = 4,     /* consolidation + canonical form */
     EVEC_K_BACKTRANSFORM = 5,/* X = Q Y (FP64, or split: slicing + products) */
     EVEC_K_CANONICALIZE = 6, /* canonical form after Q */
-    EVEC_K_COUNT = 7
+    EVEC_K_BATCHED = 7,      /* the persistent kernel of evec_batched */
+    EVEC_K_COUNT = 8
 };
 
 /* Enable (1) or disable (0) per-kernel timing: while enabled, every kernel
@@ -182,6 +183,47 @@ evec_status evec_profile(evec_handle h, int enable);
  * NULL); then reset the counters.  Kernels launched back to back for one
  * operation (a slicing kernel and its product) share one timed interval. */
 evec_status evec_profile_read(evec_handle h, double *ms, int64_t *launches, int nk);
+
+/* ---- batched mode --------------------------------------------------------
+ * count independent real Schur forms packed in one device buffer: T_i
+ * (order n_host[i], column-major, leading dimension n_i) starts at
+ * T_packed + t_off_host[i].  select_host: n_i bytes per matrix, back to back
+ * in matrix order, with the meaning of evec_standard's mask (NULL: every
+ * eigenvector of every matrix).  Host arrays are read during the call.
+ */
+
+/* Output columns m_i of each matrix (m_host: count entries, host). */
+evec_status evec_batched_count(evec_handle h, int64_t count, const int64_t *n_host,
+                               const double *T_packed, const int64_t *t_off_host,
+                               const uint8_t *select_host, int64_t *m_host);
+
+/*
+ * Right eigenvectors of every matrix (evec_standard without Q, per matrix) in
+ * one persistent launch: a device work queue hands whole matrices to CTAs,
+ * largest estimated work first; the device part of the call (plan upload,
+ * queue reset, launch) is a CUDA graph, replayed while the batch layout and
+ * buffers stay the same.  Outputs packed in matrix order: X_i (n_i x m_i,
+ * leading dimension n_i) at X_packed + sum_{k<i} n_k m_k; scale_exp_i and
+ * lam_re_i / lam_im_i (m_i each; lam may be NULL) at offset sum_{k<i} m_k.
+ * opt->mode: EVEC_FP64 only (EVEC_SPLIT returns EVEC_EINVAL in this mode).
+ * opt->tile: 16..64 for every matrix, or 0 = the tile of each matrix's size
+ * class from the handle's table, tuned on first use of a class by timing
+ * 16, 32 and 64 on up to eight of the batch's matrices of that class.
+ * Device-side errors (evec_sync / opt->check): index = element offset in
+ * T_packed.
+ */
+evec_status evec_batched(evec_handle h, int64_t count, const int64_t *n_host,
+                         const double *T_packed, const int64_t *t_off_host,
+                         const uint8_t *select_host, double *X_packed, int32_t *scale_exp_packed,
+                         double *lam_re_packed, double *lam_im_packed, const evec_opts *opt);
+
+/* Size classes of the tile table: n <= 64, <= 128, <= 256, <= 512, larger. */
+#define EVEC_SIZE_CLASSES 5
+
+/* The handle's tile table (mode = evec_mode, size_class < EVEC_SIZE_CLASSES);
+ * tile 0 = not tuned yet.  evec_tune_set accepts 0 (forget) or 16..64. */
+evec_status evec_tune_get(evec_handle h, int mode, int size_class, int *tile);
+evec_status evec_tune_set(evec_handle h, int mode, int size_class, int tile);
 
 /* Limits of evec_standard_noalloc. */
 #define EVEC_NOALLOC_MAX_N 512

@@ -30,7 +30,7 @@ EVEC_OK, EVEC_EINVAL, EVEC_ENOTSCHUR, EVEC_ENONFINITE = 0, 1, 2, 3
 EVEC_ENOMEM, EVEC_ECUDA, EVEC_ETIMEOUT, EVEC_ERESIDUAL = 4, 5, 6, 7
 EVEC_ECAPACITY = 8
 KERNELS = ("gather", "tile_norms", "diag_solve", "tile_update", "finalize",
-           "backtransform", "canonicalize")
+           "backtransform", "canonicalize", "batched")
 
 
 class EvecError(RuntimeError):
@@ -87,9 +87,14 @@ def lib() -> ctypes.CDLL:
         L.evec_last_cuda_error.restype = ctypes.c_char_p
         L.evec_strerror.argtypes = [ctypes.c_int]
         L.evec_strerror.restype = ctypes.c_char_p
+        L.evec_batched_count.argtypes = [p, i64, p, p, p, p, p]
+        L.evec_batched.argtypes = [p, i64, p, p, p, p, p, p, p, p, ctypes.POINTER(_Opts)]
+        L.evec_tune_get.argtypes = [p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+        L.evec_tune_set.argtypes = [p, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         for f in ("evec_create", "evec_destroy", "evec_set_stream", "evec_count",
                   "evec_standard", "evec_standard_host", "evec_sync", "evec_plan_query",
-                  "evec_profile", "evec_profile_read"):
+                  "evec_profile", "evec_profile_read", "evec_batched_count", "evec_batched",
+                  "evec_tune_get", "evec_tune_set"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
         return L
@@ -299,3 +304,96 @@ def standard_host(T, Q=None, select=None, tile: int = 0, device: int = 0,
 
 def sync(device=None):
     handle(device).sync()
+
+
+# ---------------------------------------------------------------------------
+# batched mode
+# ---------------------------------------------------------------------------
+SIZE_CLASSES = 5   # n <= 64, <= 128, <= 256, <= 512, larger
+
+
+def pack_batch(Ts, device=None):
+    """Pack square matrices (numpy or torch, any layout) column-major into one
+    CUDA tensor; returns (packed, n array, element offsets)."""
+    import torch
+    ns = np.array([int(t.shape[0]) for t in Ts], dtype=np.int64)
+    offs = np.zeros(len(Ts), dtype=np.int64)
+    if len(Ts):
+        offs[1:] = np.cumsum(ns * ns)[:-1]
+    host = np.empty(int((ns * ns).sum()), dtype=np.float64)
+    for t, n, o in zip(Ts, ns, offs):
+        a = t.detach().cpu().numpy() if hasattr(t, "detach") else np.asarray(t)
+        host[o:o + n * n] = np.asarray(a, dtype=np.float64).ravel(order="F")
+    dev = torch.device("cuda", device if device is not None else torch.cuda.current_device())
+    return torch.from_numpy(host).to(dev), ns, offs
+
+
+def batched_packed(T_packed, ns, t_offs, select=None, tile: int = 0, mode: str = "fp64",
+                   check: bool = False):
+    """evec_batched on a packed device buffer.  select: concatenated n_i-byte
+    masks or None.  Returns (X_packed, scale_exp, lam_re, lam_im, m) with the
+    output packing of the C entry point (X_i at sum_{k<i} n_k m_k, leading
+    dimension n_i; the others at sum_{k<i} m_k)."""
+    import torch
+    h = handle(T_packed.device.index)
+    ns = np.ascontiguousarray(ns, dtype=np.int64)
+    t_offs = np.ascontiguousarray(t_offs, dtype=np.int64)
+    sel = None if select is None else np.ascontiguousarray(select, dtype=np.uint8)
+    if sel is not None and sel.shape != (int(ns.sum()),):
+        raise ValueError("selection must hold n_i bytes per matrix")
+    m = np.zeros(len(ns), dtype=np.int64)
+    _check(lib().evec_batched_count(h.ptr, len(ns), _np_ptr(ns), T_packed.data_ptr(),
+                                    _np_ptr(t_offs), _np_ptr(sel), _np_ptr(m)),
+           "evec_batched_count")
+    dev = T_packed.device
+    X = torch.empty(int((ns * m).sum()), dtype=torch.float64, device=dev)
+    e = torch.empty(int(m.sum()), dtype=torch.int32, device=dev)
+    lr = torch.empty(int(m.sum()), dtype=torch.float64, device=dev)
+    li = torch.empty(int(m.sum()), dtype=torch.float64, device=dev)
+    opts = _opts(tile, False, mode)
+    st = lib().evec_batched(h.ptr, len(ns), _np_ptr(ns), T_packed.data_ptr(), _np_ptr(t_offs),
+                            _np_ptr(sel), X.data_ptr(), e.data_ptr(), lr.data_ptr(),
+                            li.data_ptr(), ctypes.byref(opts))
+    _check(st, "evec_batched")
+    if check:
+        h.sync()
+    return X, e, lr, li, m
+
+
+def batched(Ts, selects=None, tile: int = 0, mode: str = "fp64", check: bool = True):
+    """Eigenvectors of a list of quasi-triangular matrices in one persistent
+    launch.  Returns a list of (X_i (n_i, m_i), scale_exp_i, lam_re_i,
+    lam_im_i) CUDA tensors, X_i column-major."""
+    Tp, ns, offs = pack_batch(Ts)
+    sel = None
+    if selects is not None:
+        sel = np.concatenate([np.ones(n, np.uint8) if s is None else
+                              np.ascontiguousarray(s, dtype=np.uint8) for s, n in zip(selects, ns)])
+    X, e, lr, li, m = batched_packed(Tp, ns, offs, sel, tile, mode, check)
+    out = []
+    xo = eo = 0
+    for n, mi in zip(ns, m):
+        n, mi = int(n), int(mi)
+        out.append((X[xo:xo + n * mi].view(mi, n).t(), e[eo:eo + mi], lr[eo:eo + mi],
+                    li[eo:eo + mi]))
+        xo += n * mi
+        eo += mi
+    return out
+
+
+def tune_table(device: int = 0, mode: str = "fp64"):
+    """The handle's tile per size class (0 = not tuned yet)."""
+    h = handle(device)
+    out = []
+    for c in range(SIZE_CLASSES):
+        t = ctypes.c_int(0)
+        _check(lib().evec_tune_get(h.ptr, MODES[mode], c, ctypes.byref(t)), "evec_tune_get")
+        out.append(t.value)
+    return out
+
+
+def set_tune_table(table, device: int = 0, mode: str = "fp64"):
+    """Load a tile table (e.g. one saved as JSON by an earlier run)."""
+    h = handle(device)
+    for c, t in enumerate(table):
+        _check(lib().evec_tune_set(h.ptr, MODES[mode], c, int(t)), "evec_tune_set")

@@ -1,0 +1,528 @@
+// diag_tile.cuh -- the robust diagonal-tile solve of one tile for a chunk of
+// units, as a device function: used by the per-step kernel (k_diag_solve.cu)
+// and by the batched persistent kernel (k_batched.cu).  The design notes are
+// at the top of k_diag_solve.cu.
+#pragma once
+
+#include "evec_internal.cuh"
+
+namespace evec {
+
+namespace {
+
+template <bool C>
+struct Lanes {
+    static constexpr int G = C ? 16 : 8;     // lanes per unit
+    static constexpr int U = 32 / G;         // units per warp
+};
+
+struct Cx {
+    double re, im;
+};
+
+template <bool C>
+__device__ __forceinline__ Cx cmul(Cx a, Cx b) {
+    if (!C) return {a.re * b.re, 0.0};
+    return {fma(a.re, b.re, -a.im * b.im), fma(a.re, b.im, a.im * b.re)};
+}
+__device__ __forceinline__ Cx csub(Cx a, Cx b) { return {a.re - b.re, a.im - b.im}; }
+__device__ __forceinline__ Cx cscale(Cx a, int k) { return {scale2(a.re, k), scale2(a.im, k)}; }
+__device__ __forceinline__ long long cbits(Cx a) { return max(abs_bits(a.re), abs_bits(a.im)); }
+
+// 1 / a, a != 0: (re - i im) / (re^2 + im^2) after an exact power-of-two
+// normalisation of a.
+__device__ __forceinline__ Cx crcp(Cx a) {
+    if (a.im == 0.0) return {rcp_fast(a.re), 0.0};
+    const int k = ilog2_abs(__longlong_as_double(cbits(a)));
+    const double ar = scale2(a.re, -k), ai = scale2(a.im, -k);
+    const double id = rcp_fast(fma(ar, ar, ai * ai));
+    return {scale2(ar * id, -k), scale2(-ai * id, -k)};
+}
+
+// Factors of the shifted block system M = T_qq - lambda I (complete
+// pivoting for 2x2, pivots below smin replaced by smin).
+struct Fac {
+    Cx ia, l, g, iu;
+    int pr, pc;
+};
+
+// |a|_max key for pivot choice: high word of the larger component (the order
+// of non-negative doubles restricted to their high words; ties arbitrary)
+__device__ __forceinline__ int pkey(Cx a) {
+    return max(__double2hiint(a.re) & 0x7fffffff, __double2hiint(a.im) & 0x7fffffff);
+}
+// "below smin" on exponent fields: |a|_max < 2^(field(smin) - 1023) <= smin
+__device__ __forceinline__ bool tiny(Cx a, int fsmin) {
+    return max(efield(a.re), efield(a.im)) < fsmin;
+}
+
+template <bool C>
+__device__ Fac factor(int bs, const double *Ts, int ts, int q, double lr, double li, double smin) {
+    Fac F;
+    F.pr = F.pc = 0;
+    F.l = F.g = F.iu = {0.0, 0.0};
+    const int fsmin = efield(smin);
+    if (bs == 1) {
+        Cx p = {Ts[q + q * ts] - lr, C ? -li : 0.0};
+        if (tiny(p, fsmin)) p = {smin, 0.0};
+        F.ia = crcp(p);
+        return F;
+    }
+    Cx M[2][2];
+#pragma unroll
+    for (int a = 0; a < 2; a++)
+#pragma unroll
+        for (int b = 0; b < 2; b++) {
+            const double t = Ts[(q + a) + (q + b) * ts];
+            M[a][b] = (a == b) ? Cx{t - lr, C ? -li : 0.0} : Cx{t, 0.0};
+        }
+    int best = -1;
+#pragma unroll
+    for (int a = 0; a < 2; a++)
+#pragma unroll
+        for (int b = 0; b < 2; b++) {
+            const int v = pkey(M[a][b]);
+            if (v > best) { best = v; F.pr = a; F.pc = b; }
+        }
+    Cx a11 = M[F.pr][F.pc];
+    const Cx a12 = M[F.pr][1 - F.pc], a21 = M[1 - F.pr][F.pc], a22 = M[1 - F.pr][1 - F.pc];
+    if (tiny(a11, fsmin)) a11 = {smin, 0.0};
+    F.ia = crcp(a11);
+    F.l = cmul<C>(a21, F.ia);
+    F.g = cmul<C>(a12, F.ia);
+    Cx u = csub(a22, cmul<C>(F.l, a12));
+    if (tiny(u, fsmin)) u = {smin, 0.0};
+    F.iu = crcp(u);
+    return F;
+}
+
+template <bool C>
+__device__ __forceinline__ void apply(const Fac &F, int bs, Cx r0, Cx r1, Cx &z0, Cx &z1) {
+    if (bs == 1) {
+        z0 = cmul<C>(r0, F.ia);
+        z1 = {0.0, 0.0};
+        return;
+    }
+    const Cx d1 = F.pr == 0 ? r0 : r1, d2 = F.pr == 0 ? r1 : r0;
+    Cx t;   // d2 - l d1, fused
+    if (C) {
+        t.re = fma(-F.l.re, d1.re, fma(F.l.im, d1.im, d2.re));
+        t.im = fma(-F.l.re, d1.im, fma(-F.l.im, d1.re, d2.im));
+    } else {
+        t = {fma(-F.l.re, d1.re, d2.re), 0.0};
+    }
+    const Cx w2 = cmul<C>(t, F.iu);
+    Cx w1;  // d1 ia - g w2, fused
+    if (C) {
+        w1.re = fma(d1.re, F.ia.re, fma(-d1.im, F.ia.im, fma(-F.g.re, w2.re, F.g.im * w2.im)));
+        w1.im = fma(d1.re, F.ia.im, fma(d1.im, F.ia.re, fma(-F.g.re, w2.im, -F.g.im * w2.re)));
+    } else {
+        w1 = {fma(d1.re, F.ia.re, -F.g.re * w2.re), 0.0};
+    }
+    z0 = F.pc == 0 ? w1 : w2;
+    z1 = F.pc == 0 ? w2 : w1;
+}
+
+// Solve with the division protection: the unnormalised application is
+// exact up to rounding whenever its result is finite and <= Omega (an
+// intermediate overflow always leaves an Inf or NaN in the result);
+// otherwise normalise the right-hand side, apply again and fit sc <= 0.
+template <bool C>
+__device__ __forceinline__ int solve(const Fac &F, int bs, Cx r0, Cx r1, Cx &z0, Cx &z1) {
+    apply<C>(F, bs, r0, r1, z0, z1);
+    // |z| < 2^1020 (and finite) on the exponent fields alone
+    const int fz = max(max(efield(z0.re), efield(z0.im)), max(efield(z1.re), efield(z1.im)));
+    if (fz <= 2042) return 0;
+    const long long rb = max(cbits(r0), cbits(r1));
+    if (rb == 0) { z0 = {0.0, 0.0}; z1 = {0.0, 0.0}; return 0; }
+    const int kr = ilog2_abs(__longlong_as_double(rb)) + 1;
+    Cx h0, h1;
+    apply<C>(F, bs, cscale(r0, -kr), cscale(r1, -kr), h0, h1);
+    const long long hb = max(cbits(h0), cbits(h1));
+    if (hb == 0) { z0 = {0.0, 0.0}; z1 = {0.0, 0.0}; return 0; }
+    int sc = kOmegaExp - ilog2_abs(__longlong_as_double(hb)) - 1 - kr;
+    if (sc > 0) sc = 0;
+    z0 = cscale(h0, kr + sc);
+    z1 = cscale(h1, kr + sc);
+    return sc;
+}
+
+template <int G>
+__device__ __forceinline__ long long group_max_bits(long long v) {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__device__ __forceinline__ void cp_async8(void *smem_dst, const void *gsrc) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gsrc));
+}
+
+// rows [0, q) of one unit -= T[0:q, q-block] z: the lane's rows g, g + G, ...
+// with a trip count uniform across the warp, two rows per step (loads first)
+template <bool C, int BS, int G>
+__device__ __forceinline__ void update_rows(double *myr, double *myi, const double *c0,
+                                            const double *c1, int q, int g, Cx z0, Cx z1,
+                                            int ys) {
+    const int n = (q + G - 1) / G;
+    int j = 0;
+    for (; j + 2 <= n; j += 2) {
+        const int i0 = g + G * j, i1 = i0 + G;
+        const bool ok1 = i1 < q;            // only the last pair can be partial
+        const double a0 = myr[i0 * ys], a1 = ok1 ? myr[i1 * ys] : 0.0;
+        const double b0 = C ? myi[i0 * ys] : 0.0, b1 = (C && ok1) ? myi[i1 * ys] : 0.0;
+        const double t0 = c0[i0], t1 = ok1 ? c0[i1] : 0.0;
+        const double u0 = BS == 2 ? c1[i0] : 0.0, u1 = (BS == 2 && ok1) ? c1[i1] : 0.0;
+        double v0 = fma(-t0, z0.re, a0), v1 = fma(-t1, z0.re, a1);
+        if (BS == 2) { v0 = fma(-u0, z1.re, v0); v1 = fma(-u1, z1.re, v1); }
+        myr[i0 * ys] = v0;
+        if (ok1) myr[i1 * ys] = v1;
+        if (C) {
+            double w0 = fma(-t0, z0.im, b0), w1 = fma(-t1, z0.im, b1);
+            if (BS == 2) { w0 = fma(-u0, z1.im, w0); w1 = fma(-u1, z1.im, w1); }
+            myi[i0 * ys] = w0;
+            if (ok1) myi[i1 * ys] = w1;
+        }
+    }
+    if (j < n) {
+        const int i = g + G * j;
+        if (i < q) {
+            double v = fma(-c0[i], z0.re, myr[i * ys]);
+            if (BS == 2) v = fma(-c1[i], z1.re, v);
+            myr[i * ys] = v;
+            if (C) {
+                double w = fma(-c0[i], z0.im, myi[i * ys]);
+                if (BS == 2) w = fma(-c1[i], z1.im, w);
+                myi[i * ys] = w;
+            }
+        }
+    }
+}
+
+// The whole kernel for one kind of unit (real or complex) and W warps.
+template <int W, bool C>
+__device__ void diag_tile(int s, int list_pos0, const double *__restrict__ T, int64_t ldt,
+                          const Plan &P, const double *__restrict__ tau,
+                          const double *__restrict__ blk_tau, double *__restrict__ Y, int64_t ldy,
+                          int32_t *__restrict__ seg_e, double *__restrict__ seg_nu,
+                          int32_t *__restrict__ seg_dx, int32_t *__restrict__ seg_dy,
+                          double *smem) {
+    constexpr int G = Lanes<C>::G;
+    constexpr int kThreads = 32 * W;
+    constexpr int kUnits = Lanes<C>::U * W;
+    constexpr int ys = kUnits + 1;
+    constexpr int FW = C ? 8 : 4;                      // factor doubles per block
+    const int t0 = P.tile_start[s];
+    const int ts = P.tile_start[s + 1] - t0;
+    const int kb0 = P.tile_blk[s], kb1 = P.tile_blk[s + 1];
+    const int nbt = kb1 - kb0;
+    const int32_t *ord = C ? P.ord_cplx : P.ord_real;
+    const int list_end = C ? P.ncplx : P.nreal;
+    const int64_t m = P.m;
+    const int tid = threadIdx.x;
+
+    // shared layout
+    double *Ts = smem;                                 // ts x ts, ld ts
+    double *btau = Ts + ts * ts;                       // [kMaxTile]
+    double *umu = btau + kMaxTile;                     // [kUnits]
+    double *yr = umu + kUnits;                         // [ts][ys]
+    double *yi = yr + ts * ys;                         // [ts][ys], complex units only
+    double *fac = yi + (C ? ts * ys : 0);              // [kUnits][ts][FW]
+    int *bq = (int *)(fac + (size_t)kUnits * ts * FW); // [kMaxTile]
+    int *bsz = bq + kMaxTile;                          // [kMaxTile]
+    int *btf = bsz + kMaxTile;                         // [kMaxTile] exponent field of btau
+    int *ford = btf + kMaxTile;                        // [kMaxTile] 1x1 blocks, then 2x2
+    int *ucol = ford + kMaxTile;                       // [kUnits] column, -1 = none
+    int *uown = ucol + kUnits;                         // [kUnits]
+    int *ue = uown + kUnits;                           // [kUnits]
+    int *facp = ue + kUnits;                           // [kUnits][ts] pivot positions
+
+    // diagonal tile (upper part and first subdiagonal only), asynchronously
+    for (int idx = tid; idx < ts * ts; idx += kThreads) {
+        const int i = idx % ts, j = idx / ts;
+        if (i <= j + 1) cp_async8(&Ts[idx], T + (t0 + i) + (int64_t)(t0 + j) * ldt);
+        else Ts[idx] = 0.0;
+    }
+    asm volatile("cp.async.commit_group;");
+    for (int k = tid; k < nbt; k += kThreads) {
+        bq[k] = P.blk_start[kb0 + k] - t0;
+        bsz[k] = P.blk_size[kb0 + k];
+        btau[k] = blk_tau[kb0 + k];
+        btf[k] = efield(blk_tau[kb0 + k]);
+    }
+    if (tid < kUnits) {
+        const int pos = list_pos0 + tid;
+        int c = -1, own = 0;
+        if (pos < list_end) {
+            const int u = ord[pos];
+            c = P.unit_col[u];
+            own = P.unit_tile[u] == s;
+        }
+        ucol[tid] = c;
+        uown[tid] = own;
+    }
+    __syncthreads();   // block list and unit map are read by every warp below
+    if (tid == 0) {    // factor order: all 1x1 blocks, then all 2x2 blocks
+        int f = 0;
+        for (int k = 0; k < nbt; k++) if (bsz[k] == 1) ford[f++] = k;
+        for (int k = 0; k < nbt; k++) if (bsz[k] == 2) ford[f++] = k;
+    }
+    // the segments, column by column (coalesced); own units start at zero
+    for (int idx = tid; idx < kUnits * ts; idx += kThreads) {
+        const int uu = idx / ts, i = idx % ts;
+        const int c = ucol[uu];
+        if (c >= 0 && !uown[uu]) {
+            cp_async8(&yr[i * ys + uu], &Y[(t0 + i) + (int64_t)c * ldy]);
+            if (C) cp_async8(&yi[i * ys + uu], &Y[(t0 + i) + (int64_t)(c + 1) * ldy]);
+        } else {
+            yr[i * ys + uu] = 0.0;
+            if (C) yi[i * ys + uu] = 0.0;
+        }
+    }
+    asm volatile("cp.async.commit_group;");
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+
+    // ---- one unit per G lanes --------------------------------------------
+    const int slot = tid / G, g = tid % G;
+    const int pos = list_pos0 + slot;
+    const bool valid = pos < list_end;
+    const int u = valid ? ord[pos] : 0;
+    const int col = valid ? P.unit_col[u] : 0;
+    const int kown = valid ? P.unit_blk[u] : -1;
+    const bool own = valid && P.unit_tile[u] == s;
+    const double lr = valid ? P.unit_lam[2 * u] : 0.0;
+    const double li = (C && valid) ? P.unit_lam[2 * u + 1] : 0.0;
+    const double smin = fmax(kUlp * (fabs(lr) + fabs(li)), kSafeMin * ((double)P.n / kUlp));
+    double *myr = yr + slot;
+    double *myi = yi + slot;
+    double *myfac = fac + (size_t)slot * ts * FW;
+    int *myfacp = facp + slot * ts;
+
+    // factors of every block this unit solves, spread over its lanes in
+    // size order (lanes of a warp take the same branch)
+    if (valid) {
+        for (int f = g; f < nbt; f += G) {
+            const int kk = ford[f];
+            if (own && kb0 + kk >= kown) continue;
+            const Fac F = factor<C>(bsz[kk], Ts, ts, bq[kk], lr, li, smin);
+            double *fp = myfac + kk * FW;
+            if (C) {
+                fp[0] = F.ia.re; fp[1] = F.ia.im; fp[2] = F.l.re; fp[3] = F.l.im;
+                fp[4] = F.g.re;  fp[5] = F.g.im;  fp[6] = F.iu.re; fp[7] = F.iu.im;
+            } else {
+                fp[0] = F.ia.re; fp[1] = F.l.re; fp[2] = F.g.re; fp[3] = F.iu.re;
+            }
+            myfacp[kk] = F.pr | (F.pc << 1);
+        }
+    }
+
+    int e = 0;
+    long long nbits = 0;
+    if (valid && !own) {
+        e = seg_e[(int64_t)s * m + col];
+        for (int i = g; i < ts; i += G) {
+            nbits = max(nbits, abs_bits(myr[i * ys]));
+            if (C) nbits = max(nbits, abs_bits(myi[i * ys]));
+        }
+    }
+    int Enu = efield(__longlong_as_double(group_max_bits<G>(nbits))) - 1022;   // nu < 2^Enu
+    __syncwarp();
+
+    auto scale_rows = [&](int k) {
+        for (int i = g; i < ts; i += G) {
+            myr[i * ys] = scale2(myr[i * ys], k);
+            if (C) myi[i * ys] = scale2(myi[i * ys], k);
+        }
+    };
+
+    for (int k = kb1 - 1; k >= kb0; k--) {
+        const int kk = k - kb0;
+        const int q = bq[kk];
+        const int bs = bsz[kk];
+        const int ftq = btf[kk];
+        const bool act = valid && (!own || k <= kown);
+        const bool solving = act && !(own && k == kown);
+        Cx z0 = {0.0, 0.0}, z1 = {0.0, 0.0};
+        const Cx r0 = {myr[q * ys], C ? myi[q * ys] : 0.0};
+        const Cx r1 = bs == 2 ? Cx{myr[(q + 1) * ys], C ? myi[(q + 1) * ys] : 0.0} : Cx{0.0, 0.0};
+        Fac F;
+        {
+            const double *fp = myfac + kk * FW;
+            if (C) {
+                F.ia = {fp[0], fp[1]};
+                F.l = {fp[2], fp[3]};
+                F.g = {fp[4], fp[5]};
+                F.iu = {fp[6], fp[7]};
+            } else {
+                F.ia = {fp[0], 0.0};
+                F.l = {fp[1], 0.0};
+                F.g = {fp[2], 0.0};
+                F.iu = {fp[3], 0.0};
+            }
+            const int pp = myfacp[kk];
+            F.pr = pp & 1;
+            F.pc = pp >> 1;
+        }
+        __syncwarp();
+        if (act) {
+            int sc = 0;
+            if (!solving) {
+                const double *o = P.unit_own + 4 * u;
+                z0 = {o[0], C ? o[2] : 0.0};
+                z1 = {o[1], C ? o[3] : 0.0};
+            } else {
+                sc = solve<C>(F, bs, r0, r1, z0, z1);
+            }
+            if (sc != 0) {
+                scale_rows(sc);
+                Enu += sc;
+                e += sc;
+            }
+            if (g == q % G) { myr[q * ys] = z0.re; if (C) myi[q * ys] = z0.im; }
+            if (bs == 2 && g == (q + 1) % G) {
+                myr[(q + 1) * ys] = z1.re;
+                if (C) myi[(q + 1) * ys] = z1.im;
+            }
+        }
+        // protection of the update of rows [0, q): fast test on exponents,
+        // exact FP64 test only when it cannot decide
+        int fmu = max(max(efield(z0.re), efield(z0.im)), max(efield(z1.re), efield(z1.im)));
+        const bool trig = act && q > 0 && (Enu > 1019 || fmu + ftq > 3063);
+        if (__any_sync(0xffffffffu, trig)) {
+            long long b = 0;
+            if (trig)
+                for (int i = g; i < q; i += G) {
+                    b = max(b, abs_bits(myr[i * ys]));
+                    if (C) b = max(b, abs_bits(myi[i * ys]));
+                }
+            b = group_max_bits<G>(b);
+            if (trig) {
+                double nu = __longlong_as_double(b);
+                const double mu = __longlong_as_double(max(cbits(z0), cbits(z1)));
+                const int g2 = protect_update(nu, btau[kk], mu);
+                if (g2 != 0) {
+                    scale_rows(g2);
+                    z0 = cscale(z0, g2);
+                    z1 = cscale(z1, g2);
+                    nu = scale2(nu, g2);
+                    e += g2;
+                    fmu = max(max(efield(z0.re), efield(z0.im)), max(efield(z1.re), efield(z1.im)));
+                }
+                Enu = efield(nu) - 1022;
+            }
+        }
+        if (act && q > 0) {
+            const double *c0 = Ts + q * ts;
+            if (bs == 1) update_rows<C, 1, G>(myr, myi, c0, c0, q, g, z0, z1, ys);
+            else update_rows<C, 2, G>(myr, myi, c0, c0 + ts, q, g, z0, z1, ys);
+            Enu = max(Enu, fmu + ftq - 2044) + 1;
+        }
+        __syncwarp();
+    }
+    // segment maxima per column, exponent
+    {
+        long long br = 0, bi = 0;
+        for (int i = g; i < ts; i += G) {
+            br = max(br, abs_bits(myr[i * ys]));
+            if (C) bi = max(bi, abs_bits(myi[i * ys]));
+        }
+        br = group_max_bits<G>(br);
+        bi = group_max_bits<G>(bi);
+        if (g == 0) {
+            ue[slot] = e;
+            umu[slot] = __longlong_as_double(max(br, bi));
+            if (valid) {
+                seg_e[(int64_t)s * m + col] = e;
+                seg_nu[(int64_t)s * m + col] = __longlong_as_double(br);
+                if (C) {
+                    seg_e[(int64_t)s * m + col + 1] = e;
+                    seg_nu[(int64_t)s * m + col + 1] = __longlong_as_double(bi);
+                }
+            }
+        }
+    }
+    __syncthreads();
+
+    // ---- write-back and the decisions for the tiles above ------------------
+    for (int idx = tid; idx < kUnits * ts; idx += kThreads) {
+        const int uu = idx / ts, i = idx % ts;
+        const int c = ucol[uu];
+        if (c >= 0) {
+            Y[(t0 + i) + (int64_t)c * ldy] = yr[i * ys + uu];
+            if (C) Y[(t0 + i) + (int64_t)(c + 1) * ldy] = yi[i * ys + uu];
+        }
+    }
+    // consolidation + protection decisions (Sec. 3.4): thread -> (unit,
+    // tile row), consecutive threads on consecutive columns; four items per
+    // thread per round so their loads are in flight together
+    constexpr int kBatch = 4;
+    const int items = kUnits * s;
+    for (int base = tid; base < items; base += kBatch * kThreads) {
+        int er[kBatch];
+        double nur[kBatch];
+#pragma unroll
+        for (int j = 0; j < kBatch; j++) {
+            const int idx = base + j * kThreads;
+            er[j] = 0;
+            nur[j] = 0.0;
+            if (idx < items) {
+                const int uu = idx % kUnits, r = idx / kUnits;
+                const int c = ucol[uu];
+                if (c >= 0 && !uown[uu]) {
+                    const int64_t at = (int64_t)r * m + c;
+                    er[j] = seg_e[at];
+                    nur[j] = seg_nu[at];
+                    if (C) nur[j] = fmax(nur[j], seg_nu[at + 1]);
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kBatch; j++) {
+            const int idx = base + j * kThreads;
+            if (idx >= items) continue;
+            const int uu = idx % kUnits, r = idx / kUnits;
+            const int c = ucol[uu];
+            if (c < 0) continue;
+            const int64_t at = (int64_t)r * m + c;
+            const int es = ue[uu];
+            const bool ownu = uown[uu];
+            const int e_r = ownu ? es : er[j];
+            const int a = min(e_r, es);
+            const double nup = ownu ? 0.0 : scale2(nur[j], a - e_r);
+            const double mup = scale2(umu[uu], a - es);
+            const int g2 = protect_update(nup, tau[(int64_t)r * P.ntiles + s], mup);
+            const int ne = a + g2;
+            seg_e[at] = ne;
+            seg_dx[at] = ne - es;
+            seg_dy[at] = ownu ? kFresh : ne - e_r;
+            seg_nu[at] = 0.0;   // the update of this step writes the new maximum
+            if (C) {
+                seg_e[at + 1] = ne;
+                seg_dx[at + 1] = ne - es;
+                seg_dy[at + 1] = ownu ? kFresh : ne - e_r;
+                seg_nu[at + 1] = 0.0;
+            }
+        }
+    }
+}
+
+}  // namespace
+
+// dynamic shared memory of diag_tile<W, C> for a tile of t rows
+template <int W, bool C>
+inline size_t diag_smem_bytes(int t) {
+    constexpr int kUnits = Lanes<C>::U * W;
+    constexpr int FW = C ? 8 : 4;
+    return sizeof(double) * ((size_t)t * t + kMaxTile + kUnits +
+                             (C ? 2 : 1) * (size_t)t * (kUnits + 1) + (size_t)kUnits * t * FW) +
+           sizeof(int) * (4 * (size_t)kMaxTile + 3 * kUnits + (size_t)kUnits * t);
+}
+
+template <int W>
+inline size_t diag_smem(int t) {
+    return std::max(diag_smem_bytes<W, false>(t), diag_smem_bytes<W, true>(t));
+}
+
+}  // namespace evec

@@ -59,6 +59,11 @@ cudaError_t split_update_prepare(const double *T, int64_t ldt, int n, int ntiles
                                  const int32_t *pea_d, int total_rows, int S, int m,
                                  __nv_bfloat16 *panels, int *ea_panels, __nv_bfloat16 *sb,
                                  SplitUpdateCtx *ctx, cudaStream_t st);
+size_t batch_item_bytes();
+cudaError_t launch_batched(const BatchItem *items, int count, int *queue, DevStatus *status,
+                           int nsm, cudaStream_t st);
+void launch_gather_batched(const double *T, const int64_t *t_off, const int64_t *row_off,
+                           int count, int64_t total_rows, double *out, cudaStream_t st);
 cudaError_t split_update_step_resident(const SplitUpdateCtx &ctx, int t0, int ts, int prow0,
                                        int pea, int col0, int m, double *Y, int64_t ldy,
                                        const int *ea_panels, __nv_bfloat16 *sb, int *eb,
@@ -274,6 +279,18 @@ struct evec_ctx {
     unsigned char *plan_h = nullptr; size_t plan_h_cap = 0;
     DevStatus *status_h = nullptr;
     HostPlan plan;
+    // batched mode
+    int64_t *boff_d = nullptr; size_t boff_cap = 0;   // t_off, row_off (device)
+    int64_t *boff_h = nullptr; size_t boff_h_cap = 0; // the same, pinned staging
+    unsigned char *bws = nullptr; size_t bws_cap = 0;  // per-matrix workspaces
+    unsigned char *bplan_d = nullptr; size_t bplan_cap = 0;
+    unsigned char *bplan_h = nullptr; size_t bplan_h_cap = 0;
+    int *queue_d = nullptr;
+    int tune[2][EVEC_SIZE_CLASSES] = {{0}};
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t bexec = nullptr;
+    std::vector<uint64_t> bkey;   // what the cached graph was captured for
+    std::vector<HostPlan> bplans;
     // per-kernel event timing
     struct Timed {
         int kind;
@@ -400,55 +417,77 @@ evec_status plan_device_matrix(evec_handle h, int64_t n, const double *T, int64_
 
 // Pack the host plan into one pinned buffer, copy it to the device, and fill
 // the device-pointer view.
-evec_status upload_plan(evec_handle h, Plan &dp) {
-    const HostPlan &P = h->plan;
-    const size_t N1 = P.tile_start.size();
-    const size_t nd = P.unit_lam.size() + P.unit_own.size() + P.col_lam_re.size() + P.col_lam_im.size();
-    const size_t ni = 6 * N1 + P.blk_start.size() + P.unit_col.size() + P.unit_blk.size() +
-                      P.unit_tile.size() + P.col_unit.size() + P.ord_real.size() +
-                      P.ord_cplx.size() + P.bt_kend.size() + P.row_tile.size() +
-                      P.prow0.size() + P.pea.size();
-    const size_t bytes = nd * 8 + ni * 4 + P.blk_size.size() + 64;
-    EVEC_TRY(grow_host(&h->plan_h, &h->plan_h_cap, bytes));
-    EVEC_TRY(grow_device(&h->plan_d, &h->plan_cap, bytes));
+// Lays arrays out in a host staging buffer and yields the device addresses
+// of the same offsets in a device buffer of the same layout (host == nullptr:
+// sizes only).
+struct Packer {
+    unsigned char *host = nullptr;
+    unsigned char *dev = nullptr;
     size_t off = 0;
-    auto put = [&](const void *src, size_t nbytes, size_t align) -> const void * {
+    const void *put(const void *src, size_t nbytes, size_t align) {
         off = (off + align - 1) / align * align;
-        if (nbytes) memcpy(h->plan_h + off, src, nbytes);
-        const void *dev = h->plan_d + off;
+        if (host && src && nbytes) memcpy(host + off, src, nbytes);   // src null: reserve
+        const void *d = dev ? dev + off : nullptr;
         off += nbytes;
-        return dev;
-    };
+        return d;
+    }
+};
+
+// The device view of one host plan (the arrays every kernel reads).
+void pack_plan(Packer &pk, const HostPlan &P, Plan &dp) {
+    const size_t N1 = P.tile_start.size();
     dp.n = P.n;
     dp.m = P.m;
     dp.ntiles = (int32_t)(N1 - 1);
     dp.nblk = (int32_t)P.blk_start.size();
     dp.nunits = (int32_t)P.unit_col.size();
     dp.nb = P.nb;
-    dp.unit_lam = (const double *)put(P.unit_lam.data(), P.unit_lam.size() * 8, 8);
-    dp.unit_own = (const double *)put(P.unit_own.data(), P.unit_own.size() * 8, 8);
-    put(P.col_lam_re.data(), P.col_lam_re.size() * 8, 8);
-    put(P.col_lam_im.data(), P.col_lam_im.size() * 8, 8);
-    dp.tile_start = (const int32_t *)put(P.tile_start.data(), N1 * 4, 4);
-    dp.tile_blk = (const int32_t *)put(P.tile_blk.data(), N1 * 4, 4);
-    dp.tile_unit = (const int32_t *)put(P.tile_unit.data(), N1 * 4, 4);
-    dp.tile_col = (const int32_t *)put(P.tile_col.data(), N1 * 4, 4);
-    dp.blk_start = (const int32_t *)put(P.blk_start.data(), P.blk_start.size() * 4, 4);
-    dp.unit_col = (const int32_t *)put(P.unit_col.data(), P.unit_col.size() * 4, 4);
-    dp.unit_blk = (const int32_t *)put(P.unit_blk.data(), P.unit_blk.size() * 4, 4);
-    dp.unit_tile = (const int32_t *)put(P.unit_tile.data(), P.unit_tile.size() * 4, 4);
-    dp.col_unit = (const int32_t *)put(P.col_unit.data(), P.col_unit.size() * 4, 4);
+    dp.unit_lam = (const double *)pk.put(P.unit_lam.data(), P.unit_lam.size() * 8, 8);
+    dp.unit_own = (const double *)pk.put(P.unit_own.data(), P.unit_own.size() * 8, 8);
+    dp.tile_start = (const int32_t *)pk.put(P.tile_start.data(), N1 * 4, 4);
+    dp.tile_blk = (const int32_t *)pk.put(P.tile_blk.data(), N1 * 4, 4);
+    dp.tile_unit = (const int32_t *)pk.put(P.tile_unit.data(), N1 * 4, 4);
+    dp.tile_col = (const int32_t *)pk.put(P.tile_col.data(), N1 * 4, 4);
+    dp.blk_start = (const int32_t *)pk.put(P.blk_start.data(), P.blk_start.size() * 4, 4);
+    dp.unit_col = (const int32_t *)pk.put(P.unit_col.data(), P.unit_col.size() * 4, 4);
+    dp.unit_blk = (const int32_t *)pk.put(P.unit_blk.data(), P.unit_blk.size() * 4, 4);
+    dp.unit_tile = (const int32_t *)pk.put(P.unit_tile.data(), P.unit_tile.size() * 4, 4);
+    dp.col_unit = (const int32_t *)pk.put(P.col_unit.data(), P.col_unit.size() * 4, 4);
     dp.nreal = (int32_t)P.ord_real.size();
     dp.ncplx = (int32_t)P.ord_cplx.size();
-    dp.ord_real = (const int32_t *)put(P.ord_real.data(), P.ord_real.size() * 4, 4);
-    dp.ord_cplx = (const int32_t *)put(P.ord_cplx.data(), P.ord_cplx.size() * 4, 4);
-    dp.tile_real = (const int32_t *)put(P.tile_real.data(), N1 * 4, 4);
-    dp.tile_cplx = (const int32_t *)put(P.tile_cplx.data(), N1 * 4, 4);
-    h->bt_kend_d = (const int32_t *)put(P.bt_kend.data(), P.bt_kend.size() * 4, 4);
-    h->row_tile_d = (const int32_t *)put(P.row_tile.data(), P.row_tile.size() * 4, 4);
-    h->prow0_d = (const int32_t *)put(P.prow0.data(), P.prow0.size() * 4, 4);
-    h->pea_d = (const int32_t *)put(P.pea.data(), P.pea.size() * 4, 4);
-    dp.blk_size = (const int8_t *)put(P.blk_size.data(), P.blk_size.size(), 1);
+    dp.ord_real = (const int32_t *)pk.put(P.ord_real.data(), P.ord_real.size() * 4, 4);
+    dp.ord_cplx = (const int32_t *)pk.put(P.ord_cplx.data(), P.ord_cplx.size() * 4, 4);
+    dp.tile_real = (const int32_t *)pk.put(P.tile_real.data(), N1 * 4, 4);
+    dp.tile_cplx = (const int32_t *)pk.put(P.tile_cplx.data(), N1 * 4, 4);
+    dp.blk_size = (const int8_t *)pk.put(P.blk_size.data(), P.blk_size.size(), 1);
+}
+
+static size_t plan_bytes(const HostPlan &P) {
+    Packer pk;
+    Plan dp;
+    pack_plan(pk, P, dp);
+    return pk.off;
+}
+
+evec_status upload_plan(evec_handle h, Plan &dp) {
+    const HostPlan &P = h->plan;
+    const size_t bytes = plan_bytes(P) + 16 * (P.col_lam_re.size() + 8) +
+                         4 * (P.bt_kend.size() + P.row_tile.size() + P.prow0.size() +
+                              P.pea.size() + 64);
+    EVEC_TRY(grow_host(&h->plan_h, &h->plan_h_cap, bytes));
+    EVEC_TRY(grow_device(&h->plan_d, &h->plan_cap, bytes));
+    Packer pk;
+    pk.host = h->plan_h;
+    pk.dev = h->plan_d;
+    // the eigenvalues per column first: evec_standard copies them from here
+    pk.put(P.col_lam_re.data(), P.col_lam_re.size() * 8, 8);
+    pk.put(P.col_lam_im.data(), P.col_lam_im.size() * 8, 8);
+    pack_plan(pk, P, dp);
+    h->bt_kend_d = (const int32_t *)pk.put(P.bt_kend.data(), P.bt_kend.size() * 4, 4);
+    h->row_tile_d = (const int32_t *)pk.put(P.row_tile.data(), P.row_tile.size() * 4, 4);
+    h->prow0_d = (const int32_t *)pk.put(P.prow0.data(), P.prow0.size() * 4, 4);
+    h->pea_d = (const int32_t *)pk.put(P.pea.data(), P.pea.size() * 4, 4);
+    const size_t off = pk.off;
     EVEC_CUDA(cudaMemcpyAsync(h->plan_d, h->plan_h, off, cudaMemcpyHostToDevice, h->stream));
     return EVEC_OK;
 }
@@ -543,12 +582,14 @@ evec_status evec_destroy(evec_handle h) {
     void *dev[] = {h->diag_d, h->plan_d, h->Y, h->seg_e, h->seg_dx, h->seg_dy, h->seg_nu,
                    h->tau, h->blk_tau, h->status_d, h->hT, h->hQ, h->hX, h->hE, h->hL,
                    h->slA, h->slB, h->rmax, h->cmax, h->ea, h->eb, h->panels,
-                   h->ea_panels};
+                   h->ea_panels, h->boff_d, h->bws, h->bplan_d, h->queue_d};
     for (void *p : dev)
         if (p) cudaFree(p);
     for (auto &t : h->live) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
     for (cudaEvent_t e : h->spare) cudaEventDestroy(e);
-    void *host[] = {h->diag_h, h->plan_h, h->status_h};
+    if (h->bexec) cudaGraphExecDestroy(h->bexec);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    void *host[] = {h->diag_h, h->plan_h, h->status_h, h->boff_h, h->bplan_h};
     for (void *p : host)
         if (p) cudaFreeHost(p);
     cudaGetLastError();
@@ -775,12 +816,11 @@ evec_status evec_standard(evec_handle h, int64_t n, const double *T, int64_t ldt
         });
     }
     EVEC_CUDA(cudaGetLastError());
-    // eigenvalues per column, from the pinned plan buffer
-    const size_t lam_off = (HP.unit_lam.size() + HP.unit_own.size()) * 8;
+    // eigenvalues per column, from the start of the pinned plan buffer
     if (lam_re)
-        EVEC_CUDA(cudaMemcpyAsync(lam_re, h->plan_h + lam_off, m * 8, cudaMemcpyHostToDevice, st));
+        EVEC_CUDA(cudaMemcpyAsync(lam_re, h->plan_h, m * 8, cudaMemcpyHostToDevice, st));
     if (lam_im)
-        EVEC_CUDA(cudaMemcpyAsync(lam_im, h->plan_h + lam_off + m * 8, m * 8,
+        EVEC_CUDA(cudaMemcpyAsync(lam_im, h->plan_h + m * 8, m * 8,
                                   cudaMemcpyHostToDevice, st));
     if (opt && opt->check) return evec_sync(h, nullptr);
     return EVEC_OK;
@@ -824,3 +864,336 @@ evec_status evec_standard_host(evec_handle h, int64_t n, const double *T_host,
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// batched mode
+// ---------------------------------------------------------------------------
+namespace evec {
+
+static int size_class(int64_t n) {
+    return n <= 64 ? 0 : n <= 128 ? 1 : n <= 256 ? 2 : n <= 512 ? 3 : 4;
+}
+
+// One gather launch and one copy for the diagonals of every matrix, then the
+// host plans (tile tiles[i] for matrix i; only the matrices in idx).
+static evec_status batched_plans(evec_handle h, int64_t count, const int64_t *n_host,
+                                 const double *T_packed, const int64_t *t_off_host,
+                                 const uint8_t *select_host, const std::vector<int> &tiles,
+                                 const std::vector<int> &idx, std::vector<HostPlan> &plans,
+                                 int64_t *bad) {
+    int64_t total = 0;
+    for (int64_t i = 0; i < count; i++) {
+        if (n_host[i] < 0 || t_off_host[i] < 0) return EVEC_EINVAL;
+        total += n_host[i];
+    }
+    EVEC_TRY(grow_host(&h->boff_h, &h->boff_h_cap, (size_t)(2 * count + 1)));
+    EVEC_TRY(grow_device(&h->boff_d, &h->boff_cap, (size_t)(2 * count + 1)));
+    int64_t *toff = h->boff_h, *roff = h->boff_h + count;
+    int64_t acc = 0;
+    for (int64_t i = 0; i < count; i++) {
+        toff[i] = t_off_host[i];
+        roff[i] = acc;
+        acc += n_host[i];
+    }
+    roff[count] = acc;
+    const size_t cnt = (size_t)std::max<int64_t>(3 * total, 1);
+    EVEC_TRY(grow_device(&h->diag_d, &h->diag_cap, cnt));
+    EVEC_TRY(grow_host(&h->diag_h, &h->diag_h_cap, cnt));
+    EVEC_CUDA(cudaMemcpyAsync(h->boff_d, h->boff_h, (2 * count + 1) * sizeof(int64_t),
+                              cudaMemcpyHostToDevice, h->stream));
+    timed(h, EVEC_K_GATHER, [&] {
+        launch_gather_batched(T_packed, h->boff_d, h->boff_d + count, (int)count, total,
+                              h->diag_d, h->stream);
+        return total > 0 ? 1 : 0;
+    });
+    EVEC_CUDA(cudaGetLastError());
+    EVEC_CUDA(cudaMemcpyAsync(h->diag_h, h->diag_d, cnt * sizeof(double), cudaMemcpyDeviceToHost,
+                              h->stream));
+    EVEC_CUDA(cudaStreamSynchronize(h->stream));
+    plans.resize(count);
+    int64_t sel_off = 0;
+    std::vector<int64_t> sel0(count);
+    for (int64_t i = 0; i < count; i++) {
+        sel0[i] = sel_off;
+        sel_off += n_host[i];
+    }
+    for (int i : idx) {
+        const int64_t n = n_host[i];
+        const double *d = h->diag_h + 3 * roff[i];
+        int64_t b = -1;
+        evec_status st = build_plan(n, d, d + n, d + 2 * n - 1,
+                                    select_host ? select_host + sel0[i] : nullptr, tiles[i], n,
+                                    plans[i], &b);
+        if (st) {   // element offset in the packed input (a row: its diagonal entry)
+            if (bad) *bad = b < 0 ? -1 : t_off_host[i] + (st == EVEC_ENOTSCHUR ? b + b * n : b);
+            return st;
+        }
+    }
+    return EVEC_OK;
+}
+
+}  // namespace evec
+
+extern "C" evec_status evec_batched_count(evec_handle h, int64_t count, const int64_t *n_host,
+                                          const double *T_packed, const int64_t *t_off_host,
+                                          const uint8_t *select_host, int64_t *m_host) {
+    if (!h || count < 0 || (count > 0 && (!n_host || !t_off_host || !m_host || !T_packed)))
+        return EVEC_EINVAL;
+    if (count == 0) return EVEC_OK;
+    DeviceGuard g(h->device);
+    if (!g.ok) return EVEC_ECUDA;
+    std::vector<int> tiles(count, 64), idx(count);
+    for (int64_t i = 0; i < count; i++) idx[i] = (int)i;
+    EVEC_TRY(batched_plans(h, count, n_host, T_packed, t_off_host, select_host, tiles, idx,
+                           h->bplans, nullptr));
+    for (int64_t i = 0; i < count; i++) m_host[i] = h->bplans[i].m;
+    return EVEC_OK;
+}
+
+namespace evec {
+
+// Pack the plans of the matrices in idx (those with columns), order them by
+// estimated work, and run the persistent kernel once; through the cached
+// graph when use_graph.
+static evec_status run_batch(evec_handle h, int64_t count, const int64_t *n_host,
+                             const double *T_packed, const int64_t *t_off_host,
+                             const std::vector<int> &idx, const std::vector<HostPlan> &plans,
+                             double *X_packed, int32_t *scale_exp_packed, double *lam_re,
+                             double *lam_im, bool use_graph) {
+    // output offsets (all matrices, matrix order)
+    std::vector<int64_t> xo(count), eo(count);
+    int64_t xacc = 0, eacc = 0;
+    for (int64_t i = 0; i < count; i++) {
+        xo[i] = xacc;
+        eo[i] = eacc;
+        xacc += n_host[i] * plans[i].m;
+        eacc += plans[i].m;
+    }
+    std::vector<std::pair<double, int>> order;
+    for (int i : idx) {
+        const HostPlan &P = plans[i];
+        if (P.m == 0) continue;
+        double w = (double)P.n;
+        for (size_t u = 0; u < P.unit_col.size(); u++) {
+            const double k = P.blk_start[P.unit_blk[u]];
+            w += k * k * (P.unit_lam[2 * u + 1] != 0.0 ? 2.0 : 1.0);
+        }
+        order.push_back({-w, i});
+    }
+    std::sort(order.begin(), order.end());
+    const int nb = (int)order.size();
+    // sizes: lam (all), items, plans; workspaces
+    Packer sz;
+    sz.put(nullptr, (size_t)eacc * 8, 8);
+    sz.put(nullptr, (size_t)eacc * 8, 8);
+    sz.put(nullptr, (size_t)nb * batch_item_bytes(), 16);
+    auto r16 = [](size_t b) { return (b + 15) / 16 * 16; };
+    size_t wsb = 0;
+    for (auto &o : order) {
+        const HostPlan &P = plans[o.second];
+        Plan dp;
+        pack_plan(sz, P, dp);
+        const size_t N = P.tile_start.size() - 1, segs = N * (size_t)P.m;
+        wsb += r16(8 * N * N) + r16(8 * P.blk_start.size()) + r16(8 * segs) + 3 * r16(4 * segs);
+    }
+    EVEC_TRY(grow_host(&h->bplan_h, &h->bplan_h_cap, sz.off + 64));
+    EVEC_TRY(grow_device(&h->bplan_d, &h->bplan_cap, sz.off + 64));
+    EVEC_TRY(grow_device(&h->bws, &h->bws_cap, std::max<size_t>(wsb, 64)));
+    if (!h->queue_d) EVEC_CUDA(cudaMalloc((void **)&h->queue_d, sizeof(int)));
+    Packer pk;
+    pk.host = h->bplan_h;
+    pk.dev = h->bplan_d;
+    {   // eigenvalues per column, matrix order
+        std::vector<double> re(eacc), im(eacc);
+        for (int64_t i = 0; i < count; i++) {
+            const HostPlan &P = plans[i];
+            std::copy(P.col_lam_re.begin(), P.col_lam_re.end(), re.begin() + eo[i]);
+            std::copy(P.col_lam_im.begin(), P.col_lam_im.end(), im.begin() + eo[i]);
+        }
+        pk.put(re.data(), re.size() * 8, 8);
+        pk.put(im.data(), im.size() * 8, 8);
+    }
+    const size_t items_off = (pk.off + 15) / 16 * 16;
+    pk.put(nullptr, (size_t)nb * batch_item_bytes(), 16);
+    std::vector<BatchItem> items(nb);
+    size_t wo = 0;
+    for (int q = 0; q < nb; q++) {
+        const int i = order[q].second;
+        const HostPlan &P = plans[i];
+        BatchItem &B = items[q];
+        pack_plan(pk, P, B.P);
+        B.T = T_packed + t_off_host[i];
+        B.ldt = n_host[i];
+        B.t_base = t_off_host[i];
+        B.X = X_packed + xo[i];
+        B.ldx = n_host[i];
+        B.scale_exp = scale_exp_packed + eo[i];
+        const size_t N = P.tile_start.size() - 1, segs = N * (size_t)P.m;
+        auto take = [&](size_t bytes) {   // the same rounding as wsb above
+            unsigned char *p = h->bws + wo;
+            wo += r16(bytes);
+            return p;
+        };
+        B.tau = (double *)take(8 * N * N);
+        B.blk_tau = (double *)take(8 * P.blk_start.size());
+        B.seg_nu = (double *)take(8 * segs);
+        B.seg_e = (int32_t *)take(4 * segs);
+        B.seg_dx = (int32_t *)take(4 * segs);
+        B.seg_dy = (int32_t *)take(4 * segs);
+    }
+    memcpy(h->bplan_h + items_off, items.data(), (size_t)nb * sizeof(BatchItem));
+    const size_t bytes = pk.off;
+    const BatchItem *items_d = (const BatchItem *)(h->bplan_d + items_off);
+    cudaStream_t st = h->stream;
+    auto enqueue = [&](cudaStream_t s2) -> cudaError_t {
+        cudaError_t e = cudaMemcpyAsync(h->bplan_d, h->bplan_h, bytes, cudaMemcpyHostToDevice, s2);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->queue_d, 0, sizeof(int), s2);
+        if (e == cudaSuccess && nb > 0)
+            e = launch_batched(items_d, nb, h->queue_d, h->status_d, h->nsm, s2);
+        return e;
+    };
+    if (!use_graph) {
+        cudaError_t le = cudaSuccess;
+        timed(h, EVEC_K_BATCHED, [&] {
+            le = enqueue(st);
+            return nb > 0 ? 1 : 0;
+        });
+        EVEC_CUDA(le);
+    } else {
+        // everything the captured nodes hold: sizes, buffers, the kernel's
+        // arguments (the matrices' own pointers travel in the copied items)
+        std::vector<uint64_t> key = {(uint64_t)nb, (uint64_t)bytes, (uint64_t)items_off,
+                                     (uint64_t)h->bplan_d, (uint64_t)h->bplan_h,
+                                     (uint64_t)h->bws, (uint64_t)h->queue_d,
+                                     (uint64_t)h->status_d};
+        if (!h->bexec || key != h->bkey) {
+            if (h->bexec) {
+                cudaGraphExecDestroy(h->bexec);
+                h->bexec = nullptr;
+            }
+            if (!h->cap_stream)
+                EVEC_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+            // launch attributes are set outside the capture
+            EVEC_CUDA(launch_batched(nullptr, 0, nullptr, nullptr, h->nsm, h->cap_stream));
+            EVEC_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e = enqueue(h->cap_stream);
+            cudaGraph_t graph = nullptr;
+            cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &graph);
+            if (e == cudaSuccess) e = e2;
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&h->bexec, graph, 0);
+            if (graph) cudaGraphDestroy(graph);
+            EVEC_CUDA(e);
+            h->bkey = key;
+        }
+        cudaError_t le = cudaSuccess;
+        timed(h, EVEC_K_BATCHED, [&] {
+            le = cudaGraphLaunch(h->bexec, st);
+            return nb > 0 ? 1 : 0;
+        });
+        EVEC_CUDA(le);
+    }
+    EVEC_CUDA(cudaGetLastError());
+    if (lam_re && eacc)
+        EVEC_CUDA(cudaMemcpyAsync(lam_re, h->bplan_h, eacc * 8, cudaMemcpyHostToDevice, st));
+    if (lam_im && eacc)
+        EVEC_CUDA(cudaMemcpyAsync(lam_im, h->bplan_h + eacc * 8, eacc * 8, cudaMemcpyHostToDevice,
+                                  st));
+    return EVEC_OK;
+}
+
+}  // namespace evec
+
+extern "C" evec_status evec_batched(evec_handle h, int64_t count, const int64_t *n_host,
+                                    const double *T_packed, const int64_t *t_off_host,
+                                    const uint8_t *select_host, double *X_packed,
+                                    int32_t *scale_exp_packed, double *lam_re_packed,
+                                    double *lam_im_packed, const evec_opts *opt) {
+    if (!h || count < 0 || count > INT32_MAX ||
+        (count > 0 && (!n_host || !t_off_host || !T_packed)))
+        return EVEC_EINVAL;
+    const int mode = opt ? opt->mode : EVEC_FP64;
+    if (mode != EVEC_FP64) return EVEC_EINVAL;
+    const int tile = opt ? opt->tile : 0;
+    if (tile != 0 && (tile < 16 || tile > 64)) return EVEC_EINVAL;
+    if (count == 0) return EVEC_OK;
+    DeviceGuard g(h->device);
+    if (!g.ok) return EVEC_ECUDA;
+    int64_t bad = -1;
+    std::vector<int> tiles(count, tile ? tile : 64), all(count);
+    for (int64_t i = 0; i < count; i++) all[i] = (int)i;
+    std::vector<HostPlan> &plans = h->bplans;
+    EVEC_TRY(batched_plans(h, count, n_host, T_packed, t_off_host, select_host, tiles, all, plans,
+                           &bad));
+    int64_t mtot = 0;
+    for (int64_t i = 0; i < count; i++) mtot += plans[i].m;
+    if (mtot > 0 && (!X_packed || !scale_exp_packed)) return EVEC_EINVAL;
+    if (tile == 0) {
+        // the tile of each size class: tuned on first use by timing the
+        // candidates on up to eight of the batch's matrices of the class
+        for (int c = 0; c < EVEC_SIZE_CLASSES; c++) {
+            std::vector<int> members;
+            for (int64_t i = 0; i < count; i++)
+                if (size_class(n_host[i]) == c && plans[i].m > 0) members.push_back((int)i);
+            if (members.empty() || h->tune[mode][c]) continue;
+            std::sort(members.begin(), members.end(),
+                      [&](int a, int b) { return n_host[a] > n_host[b]; });
+            if (members.size() > 8) members.resize(8);
+            double best_ms = 0.0;
+            int best = 64;
+            for (int cand : {16, 32, 64}) {
+                std::vector<int> tl(count, cand);
+                std::vector<HostPlan> tp;
+                EVEC_TRY(batched_plans(h, count, n_host, T_packed, t_off_host, select_host, tl,
+                                       members, tp, &bad));
+                cudaEvent_t a = nullptr, b = nullptr;
+                EVEC_CUDA(cudaEventCreate(&a));
+                EVEC_CUDA(cudaEventCreate(&b));
+                cudaEventRecord(a, h->stream);
+                evec_status st = run_batch(h, count, n_host, T_packed, t_off_host, members, tp,
+                                           X_packed, scale_exp_packed, nullptr, nullptr, false);
+                cudaEventRecord(b, h->stream);
+                cudaEventSynchronize(b);
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, a, b);
+                cudaEventDestroy(a);
+                cudaEventDestroy(b);
+                EVEC_TRY(st);
+                if (best_ms == 0.0 || ms < best_ms) {
+                    best_ms = ms;
+                    best = cand;
+                }
+            }
+            h->tune[mode][c] = best;
+        }
+        bool rebuild = false;
+        for (int64_t i = 0; i < count; i++) {
+            const int t = h->tune[mode][size_class(n_host[i])];
+            if (t && t != tiles[i]) {
+                tiles[i] = t;
+                rebuild = true;
+            }
+        }
+        if (rebuild)
+            EVEC_TRY(batched_plans(h, count, n_host, T_packed, t_off_host, select_host, tiles,
+                                   all, plans, &bad));
+    }
+    EVEC_TRY(run_batch(h, count, n_host, T_packed, t_off_host, all, plans, X_packed,
+                       scale_exp_packed, lam_re_packed, lam_im_packed, true));
+    if (opt && opt->check) return evec_sync(h, nullptr);
+    return EVEC_OK;
+}
+
+extern "C" evec_status evec_tune_get(evec_handle h, int mode, int size_class, int *tile) {
+    if (!h || !tile || mode < 0 || mode > 1 || size_class < 0 || size_class >= EVEC_SIZE_CLASSES)
+        return EVEC_EINVAL;
+    *tile = h->tune[mode][size_class];
+    return EVEC_OK;
+}
+
+extern "C" evec_status evec_tune_set(evec_handle h, int mode, int size_class, int tile) {
+    if (!h || mode < 0 || mode > 1 || size_class < 0 || size_class >= EVEC_SIZE_CLASSES ||
+        (tile != 0 && (tile < 16 || tile > 64)))
+        return EVEC_EINVAL;
+    h->tune[mode][size_class] = tile;
+    return EVEC_OK;
+}

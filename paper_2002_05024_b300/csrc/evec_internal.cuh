@@ -62,6 +62,19 @@ struct Plan {
     const int32_t *tile_cplx;   // [ntiles + 1]
 };
 
+// One matrix of the batched mode: its plan, input, output and workspaces.
+struct BatchItem {
+    Plan P;
+    const double *T;
+    int64_t ldt;
+    int64_t t_base;   // element offset of T in the packed input (error indices)
+    double *X;
+    int64_t ldx;
+    int32_t *scale_exp;
+    double *tau, *blk_tau, *seg_nu;
+    int32_t *seg_e, *seg_dx, *seg_dy;
+};
+
 // ---------------------------------------------------------------------------
 // exact power-of-two scaling, from the IEEE-754 binary64 encoding
 // ---------------------------------------------------------------------------

@@ -27,6 +27,37 @@ void launch_gather_diagonals(const double *T, int64_t ldt, int64_t n, double *ou
     k_gather_diagonals<<<(unsigned)blocks, threads, 0, st>>>(T, ldt, n, out);
 }
 
+// The same three diagonals for a batch: matrix i (order n_i, column-major,
+// ld = n_i, at T + t_off[i]) owns rows [row_off[i], row_off[i + 1]) of the
+// batch and writes diag / sub / super at 3 row_off[i] + (0, n_i, 2 n_i - 1).
+__global__ void k_gather_batched(const double *__restrict__ T, const int64_t *__restrict__ t_off,
+                                 const int64_t *__restrict__ row_off, int count,
+                                 int64_t total_rows, double *__restrict__ out) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= total_rows) return;
+    int lo = 0, hi = count - 1;   // last matrix with row_off[i] <= g
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (row_off[mid] <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    const int64_t n = row_off[lo + 1] - row_off[lo], r = g - row_off[lo];
+    const double *A = T + t_off[lo];
+    double *o = out + 3 * row_off[lo];
+    o[r] = A[r + r * n];
+    if (r + 1 < n) {
+        o[n + r] = A[(r + 1) + r * n];
+        o[2 * n - 1 + r] = A[r + (r + 1) * n];
+    }
+}
+
+void launch_gather_batched(const double *T, const int64_t *t_off, const int64_t *row_off,
+                           int count, int64_t total_rows, double *out, cudaStream_t st) {
+    if (total_rows <= 0) return;
+    k_gather_batched<<<(unsigned)((total_rows + 255) / 256), 256, 0, st>>>(T, t_off, row_off, count,
+                                                                           total_rows, out);
+}
+
 __device__ __forceinline__ void check_entry(double v, long long idx, DevStatus *st) {
     if (!isfinite(v)) report(st, 3 /* EVEC_ENONFINITE */, idx);
     else if (fabs(v) > kInputMax) report(st, 1 /* EVEC_EINVAL */, idx);
