@@ -61,6 +61,10 @@ def parse_args():
     ap.add_argument("--cpu-sample", type=int, default=4096,
                     help="columns of the CPU-oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["single", "batched"], default="single",
+                    help="single: one n x n Schur form with Q (default); batched: the "
+                         "2000-matrix batch of evec_batched")
+    ap.add_argument("--batch", type=int, default=2000)
     return ap.parse_args()
 
 
@@ -487,6 +491,154 @@ def run_ours(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+def run_batched(args, rank, world, local_rank):
+    """The batched workload: --batch independent Schur forms, sizes
+    log-uniform in [32, 1024], every 10th clustered-adversarial, 30% of the
+    blocks selected, no Q; one evec_batched call per step (persistent
+    launch).  Also times the same batch matrix by matrix through
+    evec_standard ("plain") on the same GPU."""
+    import ctypes  # noqa: F401
+
+    import torch
+
+    import paper_2002_05024_b300 as ev
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    sizes, Ts, sels = workloads.batch_inputs(args.batch)
+    Tp, ns, offs = ev.pack_batch(Ts, device=local_rank)
+    sel = np.concatenate(sels)
+    mode = args.mode if args.mode == "fp64" else "fp64"   # the batched kernel runs FP64
+    out = ev.batched_packed(Tp, ns, offs, sel, tile=args.tile, mode=mode)
+    m = out[4]
+    cols = int(m.sum())
+    F = 0.0
+    for T, s_ in zip(Ts, sels):
+        n = T.shape[0]
+        i = 0
+        while i < n:
+            sz = 2 if i + 1 < n and T[i + 1, i] != 0.0 else 1
+            if s_[i] or (sz == 2 and s_[i + 1]):
+                F += sz * float(i) * float(i)
+            i += sz
+    for _ in range(args.warmup):
+        ev.batched_packed(Tp, ns, offs, sel, tile=args.tile, mode=mode, out=out)
+    torch.cuda.synchronize(dev)
+    h = ev.handle(local_rank)
+    h.profile(True)
+    h.profile_read()
+    sampler = ClockSampler() if rank == 0 else None
+    if dist:
+        dist.barrier()
+    stream = torch.cuda.current_stream(dev)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        ev.batched_packed(Tp, ns, offs, sel, tile=args.tile, mode=mode, out=out)
+    t1.record(stream)
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    elapsed = t0.elapsed_time(t1)
+    clocks = sampler.stop() if sampler else None
+    prof = h.profile_read()
+    h.profile(False)
+    ev.sync(local_rank)
+    if dist:
+        tt = torch.tensor([elapsed], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        elapsed = float(tt.item())
+    value = world * cols * args.steps / (elapsed / 1e3)
+    # the same batch, matrix by matrix through evec_standard
+    dTs = [torch.from_numpy(np.asfortranarray(T)).to(dev) for T in Ts]
+    for _ in range(2):
+        for T, s_ in zip(dTs, sels):
+            ev.standard(T, select=s_, tile=64)
+    torch.cuda.synchronize(dev)
+    w0 = time.perf_counter()
+    for T, s_ in zip(dTs, sels):
+        ev.standard(T, select=s_, tile=64)
+    torch.cuda.synchronize(dev)
+    plain = cols / (time.perf_counter() - w0)
+    # end to end: the packed inputs from pinned host memory, results back
+    hT = torch.empty(Tp.numel(), dtype=torch.float64, pin_memory=True)
+    hT.copy_(Tp.cpu())
+    hX = torch.empty(out[0].numel(), dtype=torch.float64, pin_memory=True)
+    hE = torch.empty(out[1].numel(), dtype=torch.int32, pin_memory=True)
+    w0 = time.perf_counter()
+    for _ in range(args.steps):
+        Tp.copy_(hT, non_blocking=True)
+        ev.batched_packed(Tp, ns, offs, sel, tile=args.tile, mode=mode, out=out)
+        hX.copy_(out[0], non_blocking=True)
+        hE.copy_(out[1], non_blocking=True)
+        torch.cuda.synchronize(dev)
+    e2e = {"value": world * cols * args.steps / (time.perf_counter() - w0),
+           "unit": "columns/s", "h2d_bytes_per_step": Tp.numel() * 8,
+           "d2h_bytes_per_step": out[0].numel() * 8 + out[1].numel() * 4}
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    peaks = measured_peaks()
+    fp64_peak = N_SMS * FP64_FLOP_PER_CLK_PER_SM * float(peaks.get("sm_max_mhz", 2032.0)) / 1e6
+    kms = prof.get("batched", (0.0, 0))[0] / args.steps
+    achieved = F / (kms / 1e3) / 1e12 if kms > 0 else None
+    roofline = {"kernel": "k_batched", "bound": "alu", "achieved": achieved, "peak": fp64_peak,
+                "unit": "TFLOP/s", "frac": achieved / fp64_peak if achieved else None,
+                "traffic": None,
+                "peak_source": "of derived FP64 peak (measured 4 flop/clk/SM x 148 SMs x max "
+                               "SM clock)",
+                "launches_per_step": prof.get("batched", (0.0, 0))[1] / args.steps}
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        rng = np.random.default_rng(9)
+        pick = rng.choice(len(Ts), size=min(len(Ts), 200), replace=False)
+        t = time.perf_counter()
+        cc = 0
+        for i in pick:
+            X, _, _, _ = oracle.standard(Ts[i], select=sels[i])
+            cc += X.shape[1]
+        dt = time.perf_counter() - t
+        cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+        cpu = {"value": cc / dt, "unit": "columns/s",
+               "cores": int(os.environ.get("OMP_NUM_THREADS", cores)), "kind": "oracle",
+               "sample": f"{len(pick)} randomly chosen matrices of the batch ({cc} columns), "
+                         f"{dt:.2f} s"}
+    line = {
+        "metric": "eigvec columns/s, batched (robust FP64 eigenvectors, many Schur forms)",
+        "value": value, "unit": "columns/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"batch of {args.batch} Schur forms, n log-uniform in [32, 1024] "
+                               "(config-0, every 10th clustered adversarial), 30% of blocks "
+                               "selected, no Q, one persistent launch per step",
+                   "matrices": args.batch, "columns": cols, "tile": args.tile or "tuned",
+                   "tile_table": ev.tune_table(local_rank), "mode": mode,
+                   "parallelism": "replicas",
+                   "l2": f"inputs {Tp.numel() * 8 / 2**30:.1f} GiB, larger than L2"},
+        "plain_value": plain,
+        "plain": "the same batch through evec_standard, one call per matrix (columns/s)",
+        "tflops_fp64": F * args.steps / (elapsed / 1e3) / 1e12,
+        "flops_per_step": F,
+        "roofline": roofline,
+        "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+        "gpu_launches": sum(c for _, c in prof.values()),
+        "clocks": clocks,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
 def main():
     args = parse_args()
     rank = int(os.environ.get("RANK", 0))
@@ -494,6 +646,8 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload == "batched":
+        run_batched(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 

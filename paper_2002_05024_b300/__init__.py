@@ -328,13 +328,8 @@ def pack_batch(Ts, device=None):
     return torch.from_numpy(host).to(dev), ns, offs
 
 
-def batched_packed(T_packed, ns, t_offs, select=None, tile: int = 0, mode: str = "fp64",
-                   check: bool = False):
-    """evec_batched on a packed device buffer.  select: concatenated n_i-byte
-    masks or None.  Returns (X_packed, scale_exp, lam_re, lam_im, m) with the
-    output packing of the C entry point (X_i at sum_{k<i} n_k m_k, leading
-    dimension n_i; the others at sum_{k<i} m_k)."""
-    import torch
+def batched_count(T_packed, ns, t_offs, select=None):
+    """Output columns m_i of each matrix of a packed batch."""
     h = handle(T_packed.device.index)
     ns = np.ascontiguousarray(ns, dtype=np.int64)
     t_offs = np.ascontiguousarray(t_offs, dtype=np.int64)
@@ -345,11 +340,30 @@ def batched_packed(T_packed, ns, t_offs, select=None, tile: int = 0, mode: str =
     _check(lib().evec_batched_count(h.ptr, len(ns), _np_ptr(ns), T_packed.data_ptr(),
                                     _np_ptr(t_offs), _np_ptr(sel), _np_ptr(m)),
            "evec_batched_count")
-    dev = T_packed.device
-    X = torch.empty(int((ns * m).sum()), dtype=torch.float64, device=dev)
-    e = torch.empty(int(m.sum()), dtype=torch.int32, device=dev)
-    lr = torch.empty(int(m.sum()), dtype=torch.float64, device=dev)
-    li = torch.empty(int(m.sum()), dtype=torch.float64, device=dev)
+    return m
+
+
+def batched_packed(T_packed, ns, t_offs, select=None, tile: int = 0, mode: str = "fp64",
+                   check: bool = False, out=None):
+    """evec_batched on a packed device buffer.  select: concatenated n_i-byte
+    masks or None.  Returns (X_packed, scale_exp, lam_re, lam_im, m) with the
+    output packing of the C entry point (X_i at sum_{k<i} n_k m_k, leading
+    dimension n_i; the others at sum_{k<i} m_k).  out = (X, e, lr, li, m)
+    from an earlier call on the same batch layout skips the column count."""
+    import torch
+    h = handle(T_packed.device.index)
+    ns = np.ascontiguousarray(ns, dtype=np.int64)
+    t_offs = np.ascontiguousarray(t_offs, dtype=np.int64)
+    sel = None if select is None else np.ascontiguousarray(select, dtype=np.uint8)
+    if out is not None:
+        X, e, lr, li, m = out
+    else:
+        m = batched_count(T_packed, ns, t_offs, sel)
+        dev = T_packed.device
+        X = torch.empty(int((ns * m).sum()), dtype=torch.float64, device=dev)
+        e = torch.empty(int(m.sum()), dtype=torch.int32, device=dev)
+        lr = torch.empty(int(m.sum()), dtype=torch.float64, device=dev)
+        li = torch.empty(int(m.sum()), dtype=torch.float64, device=dev)
     opts = _opts(tile, False, mode)
     st = lib().evec_batched(h.ptr, len(ns), _np_ptr(ns), T_packed.data_ptr(), _np_ptr(t_offs),
                             _np_ptr(sel), X.data_ptr(), e.data_ptr(), lr.data_ptr(),
