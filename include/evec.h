@@ -184,6 +184,27 @@ evec_status evec_profile(evec_handle h, int enable);
  * operation (a slicing kernel and its product) share one timed interval. */
 evec_status evec_profile_read(evec_handle h, double *ms, int64_t *launches, int nk);
 
+/*
+ * Generalized right eigenvectors of the pencil (S, T) (Sec. 2: (S - lambda T)
+ * y = 0, solved as (beta S - alpha T) y = 0): S upper quasi-triangular (1x1 /
+ * 2x2 diagonal blocks, not necessarily standardized), T upper triangular
+ * with a diagonal positive 2x2 block under each 2x2 block of S (else
+ * EVEC_ENOTSCHUR); T's strictly lower part is not read.  Optional Z (NULL:
+ * X = Y) for X = Z Y.  Per eigenvalue: 1x1 block (alpha, beta) = (S_pp,
+ * T_pp) with beta >= 0; 2x2 block lambda = h +- i sqrt(-g) of det(S_b -
+ * lambda T_b) = 0, alpha = lambda d1, beta = d1; both scaled by one power of
+ * two so that max(|alpha|, beta) is in [1, 2).  Outputs and canonical form
+ * as evec_standard; alpha_re, alpha_im, beta (length m, device, may be NULL)
+ * per column (a pair: alpha_im = +w, -w).  Every bound is
+ * |beta| |S_rs| + |alpha|_1 |T_rs|.  opt->tile: 16..64 (0 = 64); opt->mode
+ * EVEC_SPLIT runs the back-transformation X = Z Y in split precision.
+ */
+evec_status evec_generalized(evec_handle h, int64_t n, const double *S, int64_t lds,
+                             const double *T, int64_t ldt, const double *Z, int64_t ldz,
+                             const uint8_t *select_host, double *X, int64_t ldx,
+                             int32_t *scale_exp, double *alpha_re, double *alpha_im,
+                             double *beta, const evec_opts *opt);
+
 /* ---- batched mode --------------------------------------------------------
  * count independent real Schur forms packed in one device buffer: T_i
  * (order n_host[i], column-major, leading dimension n_i) starts at

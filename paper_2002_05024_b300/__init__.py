@@ -87,6 +87,8 @@ def lib() -> ctypes.CDLL:
         L.evec_last_cuda_error.restype = ctypes.c_char_p
         L.evec_strerror.argtypes = [ctypes.c_int]
         L.evec_strerror.restype = ctypes.c_char_p
+        L.evec_generalized.argtypes = [p, i64, p, i64, p, i64, p, i64, p, p, i64, p, p, p, p,
+                                       ctypes.POINTER(_Opts)]
         L.evec_batched_count.argtypes = [p, i64, p, p, p, p, p]
         L.evec_batched.argtypes = [p, i64, p, p, p, p, p, p, p, p, ctypes.POINTER(_Opts)]
         L.evec_tune_get.argtypes = [p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
@@ -94,6 +96,7 @@ def lib() -> ctypes.CDLL:
         for f in ("evec_create", "evec_destroy", "evec_set_stream", "evec_count",
                   "evec_standard", "evec_standard_host", "evec_sync", "evec_plan_query",
                   "evec_profile", "evec_profile_read", "evec_batched_count", "evec_batched",
+                  "evec_generalized",
                   "evec_tune_get", "evec_tune_set"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
@@ -274,6 +277,55 @@ def standard(T, Q=None, select=None, tile: int = 0, check: bool = False, out=Non
     if check:
         h.sync()
     return X, e, lr, li
+
+
+def _pencil_columns(S, sel):
+    """Output columns of a pencil: S's blocks from its first subdiagonal (a
+    pair counts 2 when either eigenvalue is selected)."""
+    import torch
+    sub = torch.diagonal(S, -1).cpu().numpy()
+    n = S.shape[0]
+    m = i = 0
+    while i < n:
+        sz = 2 if i + 1 < n and sub[i] != 0.0 else 1
+        if sel is None or sel[i] or (sz == 2 and sel[i + 1]):
+            m += sz
+        i += sz
+    return m
+
+
+def generalized(S, T, Z=None, select=None, tile: int = 0, check: bool = False,
+                mode: str = "fp64", slices: int = 0):
+    """Generalized eigenvectors of the pencil (S, T) (optionally X = Z Y).
+
+    Returns (X, scale_exp, alpha_re, alpha_im, beta) as CUDA tensors; X is
+    (n, m) column-major; column j is the eigenvector of alpha_j / beta_j."""
+    import torch
+    n = S.shape[0]
+    lds = _check_colmajor(S, "S", n)
+    ldt = _check_colmajor(T, "T", n)
+    ldz = _check_colmajor(Z, "Z", n) if Z is not None else max(n, 1)
+    sel = _mask(select, n)
+    dev = S.device
+    h = handle(dev.index)
+    m = _pencil_columns(S, sel) if n else 0
+    X = torch.empty((m, n), dtype=torch.float64, device=dev).t()
+    e = torch.empty(m, dtype=torch.int32, device=dev)
+    ar = torch.empty(m, dtype=torch.float64, device=dev)
+    ai = torch.empty(m, dtype=torch.float64, device=dev)
+    be = torch.empty(m, dtype=torch.float64, device=dev)
+    if m == 0:
+        return X, e, ar, ai, be
+    ldx = X.stride(1) if m > 1 else max(n, 1)
+    opts = _opts(tile, False, mode, slices)
+    st = lib().evec_generalized(h.ptr, n, S.data_ptr(), lds, T.data_ptr(), ldt,
+                                Z.data_ptr() if Z is not None else None, ldz, _np_ptr(sel),
+                                X.data_ptr(), ldx, e.data_ptr(), ar.data_ptr(), ai.data_ptr(),
+                                be.data_ptr(), ctypes.byref(opts))
+    _check(st, "evec_generalized")
+    if check:
+        h.sync()
+    return X, e, ar, ai, be
 
 
 def standard_host(T, Q=None, select=None, tile: int = 0, device: int = 0,

@@ -56,26 +56,20 @@ __device__ __forceinline__ bool tiny(Cx a, int fsmin) {
     return max(efield(a.re), efield(a.im)) < fsmin;
 }
 
+// LU with complete pivoting of the 1x1 / 2x2 block system M (pivots below
+// smin replaced by smin)
 template <bool C>
-__device__ Fac factor(int bs, const double *Ts, int ts, int q, double lr, double li, double smin) {
+__device__ Fac factor_matrix(int bs, Cx (&M)[2][2], double smin) {
     Fac F;
     F.pr = F.pc = 0;
     F.l = F.g = F.iu = {0.0, 0.0};
     const int fsmin = efield(smin);
     if (bs == 1) {
-        Cx p = {Ts[q + q * ts] - lr, C ? -li : 0.0};
+        Cx p = M[0][0];
         if (tiny(p, fsmin)) p = {smin, 0.0};
         F.ia = crcp(p);
         return F;
     }
-    Cx M[2][2];
-#pragma unroll
-    for (int a = 0; a < 2; a++)
-#pragma unroll
-        for (int b = 0; b < 2; b++) {
-            const double t = Ts[(q + a) + (q + b) * ts];
-            M[a][b] = (a == b) ? Cx{t - lr, C ? -li : 0.0} : Cx{t, 0.0};
-        }
     int best = -1;
 #pragma unroll
     for (int a = 0; a < 2; a++)
@@ -94,6 +88,38 @@ __device__ Fac factor(int bs, const double *Ts, int ts, int q, double lr, double
     if (tiny(u, fsmin)) u = {smin, 0.0};
     F.iu = crcp(u);
     return F;
+}
+
+// factors of T_qq - lambda I
+template <bool C>
+__device__ Fac factor(int bs, const double *Ts, int ts, int q, double lr, double li, double smin) {
+    Cx M[2][2];
+#pragma unroll
+    for (int a = 0; a < 2; a++)
+#pragma unroll
+        for (int b = 0; b < 2; b++) {
+            if (a >= bs || b >= bs) { M[a][b] = {0.0, 0.0}; continue; }
+            const double t = Ts[(q + a) + (q + b) * ts];
+            M[a][b] = (a == b) ? Cx{t - lr, C ? -li : 0.0} : Cx{t, 0.0};
+        }
+    return factor_matrix<C>(bs, M, smin);
+}
+
+// factors of beta S_qq - alpha T_qq (pencil; T upper triangular)
+template <bool C>
+__device__ Fac factor_pencil(int bs, const double *Ss, const double *Tt, int ts, int q, double ar,
+                             double ai, double be, double smin) {
+    Cx M[2][2];
+#pragma unroll
+    for (int a = 0; a < 2; a++)
+#pragma unroll
+        for (int b = 0; b < 2; b++) {
+            if (a >= bs || b >= bs) { M[a][b] = {0.0, 0.0}; continue; }
+            const double sv = Ss[(q + a) + (q + b) * ts];
+            const double tv = b >= a ? Tt[(q + a) + (q + b) * ts] : 0.0;
+            M[a][b] = {be * sv - ar * tv, C ? -ai * tv : 0.0};
+        }
+    return factor_matrix<C>(bs, M, smin);
 }
 
 template <bool C>
@@ -201,13 +227,39 @@ __device__ __forceinline__ void update_rows(double *myr, double *myi, const doub
 }
 
 // The whole kernel for one kind of unit (real or complex) and W warps.
-template <int W, bool C>
+// pencils: rows [0, q) -= S[0:q, block] (beta z) - T[0:q, block] (alpha z),
+// with zb = beta z and wz = alpha z precomputed per block
+template <bool C, int BS, int G>
+__device__ __forceinline__ void update_rows_pencil(double *myr, double *myi, const double *s0,
+                                                   const double *s1, const double *t0c,
+                                                   const double *t1c, int q, int g, Cx zb0, Cx zb1,
+                                                   Cx wz0, Cx wz1, int ys) {
+    const int n = (q + G - 1) / G;
+    for (int j = 0; j < n; j++) {
+        const int i = g + G * j;
+        if (i >= q) continue;
+        const double a = myr[i * ys];
+        const double b = C ? myi[i * ys] : 0.0;
+        const double sa = s0[i], ta = t0c[i];
+        const double sb = BS == 2 ? s1[i] : 0.0, tb = BS == 2 ? t1c[i] : 0.0;
+        double v = fma(ta, wz0.re, fma(-sa, zb0.re, a));
+        if (BS == 2) v = fma(tb, wz1.re, fma(-sb, zb1.re, v));
+        myr[i * ys] = v;
+        if (C) {
+            double w = fma(ta, wz0.im, fma(-sa, zb0.im, b));
+            if (BS == 2) w = fma(tb, wz1.im, fma(-sb, zb1.im, w));
+            myi[i * ys] = w;
+        }
+    }
+}
+
+template <int W, bool C, bool GEN = false>
 __device__ void diag_tile(int s, int list_pos0, const double *__restrict__ T, int64_t ldt,
                           const Plan &P, const double *__restrict__ tau,
                           const double *__restrict__ blk_tau, double *__restrict__ Y, int64_t ldy,
                           int32_t *__restrict__ seg_e, double *__restrict__ seg_nu,
                           int32_t *__restrict__ seg_dx, int32_t *__restrict__ seg_dy,
-                          double *smem) {
+                          double *smem, const Pencil &pen = Pencil()) {
     constexpr int G = Lanes<C>::G;
     constexpr int kThreads = 32 * W;
     constexpr int kUnits = Lanes<C>::U * W;
@@ -237,6 +289,11 @@ __device__ void diag_tile(int s, int list_pos0, const double *__restrict__ T, in
     int *uown = ucol + kUnits;                         // [kUnits]
     int *ue = uown + kUnits;                           // [kUnits]
     int *facp = ue + kUnits;                           // [kUnits][ts] pivot positions
+    int *uidx = facp + kUnits * ts;                    // [kUnits] unit index
+    // pencils: T's tile, its in-tile block norms, per-unit block bounds
+    double *Bt = (double *)(((uintptr_t)(uidx + kUnits) + 15) & ~(uintptr_t)15);   // ts x ts
+    double *btauB = Bt + (GEN ? ts * ts : 0);          // [kMaxTile]
+    double *utau = btauB + (GEN ? kMaxTile : 0);       // [kUnits][ts]
 
     // diagonal tile (upper part and first subdiagonal only), asynchronously
     for (int idx = tid; idx < ts * ts; idx += kThreads) {
@@ -244,23 +301,31 @@ __device__ void diag_tile(int s, int list_pos0, const double *__restrict__ T, in
         if (i <= j + 1) cp_async8(&Ts[idx], T + (t0 + i) + (int64_t)(t0 + j) * ldt);
         else Ts[idx] = 0.0;
     }
+    if constexpr (GEN)
+        for (int idx = tid; idx < ts * ts; idx += kThreads) {
+            const int i = idx % ts, j = idx / ts;
+            if (i <= j) cp_async8(&Bt[idx], pen.T + (t0 + i) + (int64_t)(t0 + j) * pen.ldt);
+            else Bt[idx] = 0.0;
+        }
     asm volatile("cp.async.commit_group;");
     for (int k = tid; k < nbt; k += kThreads) {
         bq[k] = P.blk_start[kb0 + k] - t0;
         bsz[k] = P.blk_size[kb0 + k];
         btau[k] = blk_tau[kb0 + k];
         btf[k] = efield(blk_tau[kb0 + k]);
+        if constexpr (GEN) btauB[k] = pen.blk_tau[kb0 + k];
     }
     if (tid < kUnits) {
         const int pos = list_pos0 + tid;
-        int c = -1, own = 0;
+        int c = -1, own = 0, ui = 0;
         if (pos < list_end) {
-            const int u = ord[pos];
-            c = P.unit_col[u];
-            own = P.unit_tile[u] == s;
+            ui = ord[pos];
+            c = P.unit_col[ui];
+            own = P.unit_tile[ui] == s;
         }
         ucol[tid] = c;
         uown[tid] = own;
+        uidx[tid] = ui;
     }
     __syncthreads();   // block list and unit map are read by every warp below
     if (tid == 0) {    // factor order: all 1x1 blocks, then all 2x2 blocks
@@ -294,7 +359,10 @@ __device__ void diag_tile(int s, int list_pos0, const double *__restrict__ T, in
     const bool own = valid && P.unit_tile[u] == s;
     const double lr = valid ? P.unit_lam[2 * u] : 0.0;
     const double li = (C && valid) ? P.unit_lam[2 * u + 1] : 0.0;
-    const double smin = fmax(kUlp * (fabs(lr) + fabs(li)), kSafeMin * ((double)P.n / kUlp));
+    const double be = (GEN && valid) ? P.unit_beta[u] : 1.0;
+    const double smin = GEN ? (valid ? P.unit_smin[u] : 1.0)
+                            : fmax(kUlp * (fabs(lr) + fabs(li)), kSafeMin * ((double)P.n / kUlp));
+    double *myutau = utau + (size_t)slot * ts;
     double *myr = yr + slot;
     double *myi = yi + slot;
     double *myfac = fac + (size_t)slot * ts * FW;
@@ -306,7 +374,14 @@ __device__ void diag_tile(int s, int list_pos0, const double *__restrict__ T, in
         for (int f = g; f < nbt; f += G) {
             const int kk = ford[f];
             if (own && kb0 + kk >= kown) continue;
-            const Fac F = factor<C>(bsz[kk], Ts, ts, bq[kk], lr, li, smin);
+            Fac F;
+            if constexpr (GEN) {
+                F = factor_pencil<C>(bsz[kk], Ts, Bt, ts, bq[kk], lr, li, be, smin);
+                // bound of the in-tile update from block kk for this unit
+                myutau[kk] = fabs(be) * btau[kk] + (fabs(lr) + fabs(li)) * btauB[kk];
+            } else {
+                F = factor<C>(bsz[kk], Ts, ts, bq[kk], lr, li, smin);
+            }
             double *fp = myfac + kk * FW;
             if (C) {
                 fp[0] = F.ia.re; fp[1] = F.ia.im; fp[2] = F.l.re; fp[3] = F.l.im;
@@ -341,7 +416,8 @@ __device__ void diag_tile(int s, int list_pos0, const double *__restrict__ T, in
         const int kk = k - kb0;
         const int q = bq[kk];
         const int bs = bsz[kk];
-        const int ftq = btf[kk];
+        const double tauk = GEN ? myutau[kk] : btau[kk];
+        const int ftq = GEN ? efield(tauk) : btf[kk];
         const bool act = valid && (!own || k <= kown);
         const bool solving = act && !(own && k == kown);
         Cx z0 = {0.0, 0.0}, z1 = {0.0, 0.0};
@@ -401,7 +477,7 @@ __device__ void diag_tile(int s, int list_pos0, const double *__restrict__ T, in
             if (trig) {
                 double nu = __longlong_as_double(b);
                 const double mu = __longlong_as_double(max(cbits(z0), cbits(z1)));
-                const int g2 = protect_update(nu, btau[kk], mu);
+                const int g2 = protect_update(nu, tauk, mu);
                 if (g2 != 0) {
                     scale_rows(g2);
                     z0 = cscale(z0, g2);
@@ -415,8 +491,20 @@ __device__ void diag_tile(int s, int list_pos0, const double *__restrict__ T, in
         }
         if (act && q > 0) {
             const double *c0 = Ts + q * ts;
-            if (bs == 1) update_rows<C, 1, G>(myr, myi, c0, c0, q, g, z0, z1, ys);
-            else update_rows<C, 2, G>(myr, myi, c0, c0 + ts, q, g, z0, z1, ys);
+            if constexpr (GEN) {
+                const double *d0 = Bt + q * ts;
+                const Cx zb0 = {be * z0.re, be * z0.im}, zb1 = {be * z1.re, be * z1.im};
+                const Cx wz0 = cmul<C>(Cx{lr, li}, z0), wz1 = cmul<C>(Cx{lr, li}, z1);
+                if (bs == 1)
+                    update_rows_pencil<C, 1, G>(myr, myi, c0, c0, d0, d0, q, g, zb0, zb1, wz0,
+                                                wz1, ys);
+                else
+                    update_rows_pencil<C, 2, G>(myr, myi, c0, c0 + ts, d0, d0 + ts, q, g, zb0,
+                                                zb1, wz0, wz1, ys);
+            } else {
+                if (bs == 1) update_rows<C, 1, G>(myr, myi, c0, c0, q, g, z0, z1, ys);
+                else update_rows<C, 2, G>(myr, myi, c0, c0 + ts, q, g, z0, z1, ys);
+            }
             Enu = max(Enu, fmu + ftq - 2044) + 1;
         }
         __syncwarp();
@@ -492,7 +580,14 @@ __device__ void diag_tile(int s, int list_pos0, const double *__restrict__ T, in
             const int a = min(e_r, es);
             const double nup = ownu ? 0.0 : scale2(nur[j], a - e_r);
             const double mup = scale2(umu[uu], a - es);
-            const int g2 = protect_update(nup, tau[(int64_t)r * P.ntiles + s], mup);
+            double trs = tau[(int64_t)r * P.ntiles + s];
+            if constexpr (GEN) {   // |beta| |S_rs| + |alpha|_1 |T_rs| for this unit
+                const int ui = uidx[uu];
+                trs = fabs(P.unit_beta[ui]) * trs +
+                      (fabs(P.unit_lam[2 * ui]) + fabs(P.unit_lam[2 * ui + 1])) *
+                          pen.tau[(int64_t)r * P.ntiles + s];
+            }
+            const int g2 = protect_update(nup, trs, mup);
             const int ne = a + g2;
             seg_e[at] = ne;
             seg_dx[at] = ne - es;
@@ -510,19 +605,20 @@ __device__ void diag_tile(int s, int list_pos0, const double *__restrict__ T, in
 
 }  // namespace
 
-// dynamic shared memory of diag_tile<W, C> for a tile of t rows
-template <int W, bool C>
+// dynamic shared memory of diag_tile<W, C, GEN> for a tile of t rows
+template <int W, bool C, bool GEN = false>
 inline size_t diag_smem_bytes(int t) {
     constexpr int kUnits = Lanes<C>::U * W;
     constexpr int FW = C ? 8 : 4;
     return sizeof(double) * ((size_t)t * t + kMaxTile + kUnits +
                              (C ? 2 : 1) * (size_t)t * (kUnits + 1) + (size_t)kUnits * t * FW) +
-           sizeof(int) * (4 * (size_t)kMaxTile + 3 * kUnits + (size_t)kUnits * t);
+           sizeof(int) * (4 * (size_t)kMaxTile + 4 * kUnits + (size_t)kUnits * t) + 16 +
+           (GEN ? sizeof(double) * ((size_t)t * t + kMaxTile + (size_t)kUnits * t) : 0);
 }
 
-template <int W>
+template <int W, bool GEN = false>
 inline size_t diag_smem(int t) {
-    return std::max(diag_smem_bytes<W, false>(t), diag_smem_bytes<W, true>(t));
+    return std::max(diag_smem_bytes<W, false, GEN>(t), diag_smem_bytes<W, true, GEN>(t));
 }
 
 }  // namespace evec

@@ -28,13 +28,13 @@ namespace evec {
 void launch_gather_diagonals(const double *T, int64_t ldt, int64_t n, double *out,
                              cudaStream_t st);
 void launch_tile_norms(const double *T, int64_t ldt, const Plan &p, double *tau,
-                       double *blk_tau, DevStatus *status, cudaStream_t st);
+                       double *blk_tau, DevStatus *status, cudaStream_t st, int lower = 1);
 int launch_diag_solve(int s, const double *T, int64_t ldt, const Plan &p,
                        const int32_t *tile_start_h, const int32_t *tile_real_h,
                        const int32_t *tile_cplx_h,
                        const double *tau, const double *blk_tau, double *Y, int64_t ldy,
                        int32_t *seg_e, double *seg_nu, int32_t *seg_dx, int32_t *seg_dy,
-                       cudaStream_t st);
+                       cudaStream_t st, const Pencil *pen = nullptr);
 void launch_tile_update(int s, const double *T, int64_t ldt, const Plan &p, int max_tile,
                         const int32_t *tile_col_h, double *Y, int64_t ldy,
                         const int32_t *seg_dx, const int32_t *seg_dy, double *seg_nu,
@@ -54,12 +54,20 @@ int split_pad_m(int M);
 int split_pad_n(int N);
 int split_pad_k(int K);
 constexpr int kSplitColTile = 64;
-cudaError_t split_update_prepare(const double *T, int64_t ldt, int n, int ntiles, int maxtile,
+cudaError_t split_update_prepare(const double *T, int64_t ldt, const double *T2, int64_t ldt2,
+                                 int n, int ntiles, int maxtile,
                                  const int32_t *tstart_d, const int32_t *prow0_d,
                                  const int32_t *pea_d, int total_rows, int S, int m,
                                  __nv_bfloat16 *panels, int *ea_panels, __nv_bfloat16 *sb,
                                  SplitUpdateCtx *ctx, cudaStream_t st);
 size_t batch_item_bytes();
+void launch_pencil_rhs(int s, const Plan &p, const int32_t *tile_col_h, const double *Y,
+                       int64_t ldy, double *W, int64_t ldw, cudaStream_t st);
+int launch_tile_update_pencil(int s, const double *S, int64_t lds, const double *T2,
+                              int64_t ldt2, const Plan &p, const int32_t *tile_start_h,
+                              const int32_t *tile_col_h, double *Y, int64_t ldy,
+                              const int32_t *seg_dx, const int32_t *seg_dy, double *seg_nu,
+                              double *W, int64_t ldw, cudaStream_t st);
 cudaError_t launch_batched(const BatchItem *items, int count, int *queue, DevStatus *status,
                            int nsm, cudaStream_t st);
 void launch_gather_batched(const double *T, const int64_t *t_off, const int64_t *row_off,
@@ -69,12 +77,14 @@ cudaError_t split_update_step_resident(const SplitUpdateCtx &ctx, int t0, int ts
                                        const int *ea_panels, __nv_bfloat16 *sb, int *eb,
                                        const int32_t *row_tile, const int32_t *dx,
                                        const int32_t *dy, double *seg_nu, int *err, int nsm,
-                                       cudaStream_t st);
+                                       cudaStream_t st, const double *rhs = nullptr,
+                                       int64_t ldr = 0);
 cudaError_t split_update_step(const SplitUpdateCtx &ctx, int t0, int ts, int prow0, int pea,
                               int col0, int m, double *Y, int64_t ldy, const int *ea_panels,
                               __nv_bfloat16 *sb, unsigned long long *colmax, int *eb,
                               const int32_t *row_tile, const int32_t *dx, const int32_t *dy,
-                              double *seg_nu, int *err, cudaStream_t st);
+                              double *seg_nu, int *err, cudaStream_t st,
+                              const double *rhs = nullptr, int64_t ldr = 0);
 
 // ---------------------------------------------------------------------------
 // host plan
@@ -93,6 +103,15 @@ struct HostPlan {
     int panel_rows = 0;
     std::vector<int8_t> blk_size;
     std::vector<double> unit_lam, unit_own, col_lam_re, col_lam_im;
+    // pencils (S, T): beta and smin per unit, beta per column
+    std::vector<double> unit_beta, unit_smin, col_beta;
+};
+
+// The second matrix of a pencil for the planner: its diagonal and first
+// superdiagonal (T[i, i + 1]).
+struct PencilDiags {
+    const double *diag;
+    const double *sup;
 };
 
 static evec_status check_value(double v, int64_t idx, int64_t *bad) {
@@ -105,9 +124,19 @@ static evec_status check_value(double v, int64_t idx, int64_t *bad) {
 // boundaries never split a 2x2 block, and the unit / column maps of the
 // selection.  diag[n], sub[n-1] (T[i+1, i]), sup[n-1] (T[i, i+1]).
 // Linear indices in *bad refer to a column-major matrix with ld = ld_report.
+//
+// With pen (a pencil (S, T), Sec. 2: (S - lambda T) y = 0 in the homogeneous
+// form (beta S - alpha T) y = 0), diag/sub/sup are S's and pen holds T's;
+// 2x2 blocks of S need not be standardized, but T's block under each of them
+// must be diagonal positive.  Per unit (alpha, beta): 1x1 (S_pp, T_pp) with
+// beta >= 0; 2x2 lambda = h +- i sqrt(-g) from the block of S and diag(d1, d2),
+// alpha = lambda d1, beta = d1; both scaled by one power of two so that
+// max(|alpha|, beta) lies in [1, 2).  The block part of the eigenvector is
+// the null vector of beta S_b - alpha T_b.
 static evec_status build_plan(int64_t n, const double *diag, const double *sub,
                               const double *sup, const uint8_t *select, int nb,
-                              int64_t ld_report, HostPlan &P, int64_t *bad) {
+                              int64_t ld_report, HostPlan &P, int64_t *bad,
+                              const PencilDiags *pen = nullptr) {
     P = HostPlan();
     P.n = n;
     P.nb = nb;
@@ -120,14 +149,29 @@ static evec_status build_plan(int64_t n, const double *diag, const double *sub,
             st = check_value(sup[i], i + (i + 1) * ld_report, bad);
             if (st) return st;
         }
+        if (pen) {
+            st = check_value(pen->diag[i], i + i * ld_report, bad);
+            if (st) return st;
+            if (i + 1 < n) {
+                st = check_value(pen->sup[i], i + (i + 1) * ld_report, bad);
+                if (st) return st;
+            }
+        }
     }
+    double smax = 0.0, tmax = 0.0;   // pencils: max |S_ii|, max |T_ii| (smin)
+    if (pen)
+        for (int64_t i = 0; i < n; i++) {
+            smax = std::max(smax, fabs(diag[i]));
+            tmax = std::max(tmax, fabs(pen->diag[i]));
+        }
     // blocks
     std::vector<int8_t> in_pair_second(n, 0);
     for (int64_t i = 0; i < n;) {
         if (i + 1 < n && sub[i] != 0.0) {
             if (i + 2 < n && sub[i + 1] != 0.0) { if (bad) *bad = i + 1; return EVEC_ENOTSCHUR; }
             const double b = sup[i], c = sub[i];
-            if (diag[i] != diag[i + 1] || !((b > 0.0 && c < 0.0) || (b < 0.0 && c > 0.0))) {
+            if (!pen &&
+                (diag[i] != diag[i + 1] || !((b > 0.0 && c < 0.0) || (b < 0.0 && c > 0.0)))) {
                 if (bad) *bad = i;
                 return EVEC_ENOTSCHUR;
             }
@@ -177,33 +221,86 @@ static evec_status build_plan(int64_t n, const double *diag, const double *sub,
         }
         const int64_t p = P.blk_start[k];
         const int bs = P.blk_size[k];
+        double ar = 0.0, ai = 0.0, be = 1.0, own[4] = {1.0, 0.0, 0.0, 0.0};
+        if (pen) {   // (alpha, beta) of the block, the null vector of its pencil
+            if (bs == 1) {
+                ar = diag[p];
+                be = pen->diag[p];
+                if (be < 0.0) { be = -be; ar = -ar; }
+                if (ar == 0.0 && be == 0.0) {
+                    if (bad) *bad = p;
+                    return EVEC_ENOTSCHUR;
+                }
+            } else {
+                const double s11 = diag[p], s12 = sup[p], s21 = sub[p], s22 = diag[p + 1];
+                const double d1 = pen->diag[p], d2 = pen->diag[p + 1];
+                if (!(d1 > 0.0 && d2 > 0.0) || pen->sup[p] != 0.0) {
+                    if (bad) *bad = p;
+                    return EVEC_ENOTSCHUR;
+                }
+                const double u = s11 / d1, v = s22 / d2;
+                const double hh = 0.5 * (u + v), dd = 0.5 * (u - v);
+                const double g = dd * dd + (s12 / d1) * (s21 / d2);
+                if (!(g < 0.0)) {
+                    if (bad) *bad = p;
+                    return EVEC_ENOTSCHUR;
+                }
+                ar = hh * d1;
+                ai = sqrt(-g) * d1;
+                be = d1;
+            }
+            const double mx = std::max(std::max(fabs(ar), fabs(ai)), be);
+            if (!isfinite(mx) || mx == 0.0) {
+                if (bad) *bad = p;
+                return EVEC_EINVAL;
+            }
+            const int e2 = ilogb(mx);
+            ar = ldexp(ar, -e2);
+            ai = ldexp(ai, -e2);
+            be = ldexp(be, -e2);
+            if (bs == 2) {
+                const double s11 = diag[p], s12 = sup[p], s21 = sub[p], s22 = diag[p + 1];
+                const double d1 = pen->diag[p], d2 = pen->diag[p + 1];
+                const double m12 = be * s12, m21 = be * s21;
+                if (fabs(m12) >= fabs(m21)) {   // (1, -m11 / m12)
+                    const double m11r = be * s11 - ar * d1, m11i = -ai * d1;
+                    own[0] = 1.0; own[1] = -m11r / m12; own[2] = 0.0; own[3] = -m11i / m12;
+                } else {                        // (-m22 i / m21, i)
+                    const double m22r = be * s22 - ar * d2, m22i = -ai * d2;
+                    own[0] = m22i / m21; own[1] = 0.0; own[2] = -m22r / m21; own[3] = 1.0;
+                }
+            }
+        } else if (bs == 1) {
+            ar = diag[p];
+        } else {
+            const double a = diag[p], b = sup[p], c = sub[p];
+            const double w = sqrt(fabs(b)) * sqrt(fabs(c));
+            ar = a;
+            ai = w;
+            // null vector of [[-i w, b], [c, -i w]]: (1, i w / b) or (-w / c, i)
+            if (fabs(b) >= fabs(c)) { own[0] = 1.0; own[1] = 0.0; own[2] = 0.0; own[3] = w / b; }
+            else { own[0] = -w / c; own[1] = 0.0; own[2] = 0.0; own[3] = 1.0; }
+        }
         const bool sel = select == nullptr || select[p] || (bs == 2 && select[p + 1]);
         if (!sel) continue;
         const int32_t u = (int32_t)P.unit_col.size();
         P.unit_col.push_back((int32_t)col);
         P.unit_blk.push_back((int32_t)k);
         P.unit_tile.push_back(t);
-        if (bs == 1) {
-            P.unit_lam.push_back(diag[p]);
-            P.unit_lam.push_back(0.0);
-            P.unit_own.insert(P.unit_own.end(), {1.0, 0.0, 0.0, 0.0});
+        P.unit_lam.push_back(ar);
+        P.unit_lam.push_back(ai);
+        P.unit_own.insert(P.unit_own.end(), {own[0], own[1], own[2], own[3]});
+        if (pen) {
+            P.unit_beta.push_back(be);
+            const double smlnum = kSafeMin * ((double)n / kUlp);
+            P.unit_smin.push_back(std::max(kUlp * (fabs(be) * smax + (fabs(ar) + fabs(ai)) * tmax),
+                                           smlnum));
+        }
+        for (int j = 0; j < bs; j++) {
             P.col_unit.push_back(u);
-            P.col_lam_re.push_back(diag[p]);
-            P.col_lam_im.push_back(0.0);
-        } else {
-            const double a = diag[p], b = sup[p], c = sub[p];
-            const double w = sqrt(fabs(b)) * sqrt(fabs(c));
-            P.unit_lam.push_back(a);
-            P.unit_lam.push_back(w);
-            // null vector of [[-i w, b], [c, -i w]]: (1, i w / b) or (-w / c, i)
-            if (fabs(b) >= fabs(c)) P.unit_own.insert(P.unit_own.end(), {1.0, 0.0, 0.0, w / b});
-            else P.unit_own.insert(P.unit_own.end(), {-w / c, 0.0, 0.0, 1.0});
-            P.col_unit.push_back(u);
-            P.col_unit.push_back(u);
-            P.col_lam_re.push_back(a);
-            P.col_lam_re.push_back(a);
-            P.col_lam_im.push_back(w);
-            P.col_lam_im.push_back(-w);
+            P.col_lam_re.push_back(ar);
+            P.col_lam_im.push_back(j == 0 ? ai : -ai);
+            if (pen) P.col_beta.push_back(be);
         }
         col += bs;
     }
@@ -279,6 +376,10 @@ struct evec_ctx {
     unsigned char *plan_h = nullptr; size_t plan_h_cap = 0;
     DevStatus *status_h = nullptr;
     HostPlan plan;
+    // pencils: T's norms, the right-hand side of the updates
+    double *tauT = nullptr; size_t tauT_cap = 0;
+    double *blk_tauT = nullptr; size_t blk_tauT_cap = 0;
+    double *pW = nullptr; size_t pW_cap = 0;
     // batched mode
     int64_t *boff_d = nullptr; size_t boff_cap = 0;   // t_off, row_off (device)
     int64_t *boff_h = nullptr; size_t boff_h_cap = 0; // the same, pinned staging
@@ -459,6 +560,12 @@ void pack_plan(Packer &pk, const HostPlan &P, Plan &dp) {
     dp.ord_cplx = (const int32_t *)pk.put(P.ord_cplx.data(), P.ord_cplx.size() * 4, 4);
     dp.tile_real = (const int32_t *)pk.put(P.tile_real.data(), N1 * 4, 4);
     dp.tile_cplx = (const int32_t *)pk.put(P.tile_cplx.data(), N1 * 4, 4);
+    dp.unit_beta = P.unit_beta.empty()
+                       ? nullptr
+                       : (const double *)pk.put(P.unit_beta.data(), P.unit_beta.size() * 8, 8);
+    dp.unit_smin = P.unit_smin.empty()
+                       ? nullptr
+                       : (const double *)pk.put(P.unit_smin.data(), P.unit_smin.size() * 8, 8);
     dp.blk_size = (const int8_t *)pk.put(P.blk_size.data(), P.blk_size.size(), 1);
 }
 
@@ -471,7 +578,7 @@ static size_t plan_bytes(const HostPlan &P) {
 
 evec_status upload_plan(evec_handle h, Plan &dp) {
     const HostPlan &P = h->plan;
-    const size_t bytes = plan_bytes(P) + 16 * (P.col_lam_re.size() + 8) +
+    const size_t bytes = plan_bytes(P) + 24 * (P.col_lam_re.size() + 8) +
                          4 * (P.bt_kend.size() + P.row_tile.size() + P.prow0.size() +
                               P.pea.size() + 64);
     EVEC_TRY(grow_host(&h->plan_h, &h->plan_h_cap, bytes));
@@ -482,6 +589,7 @@ evec_status upload_plan(evec_handle h, Plan &dp) {
     // the eigenvalues per column first: evec_standard copies them from here
     pk.put(P.col_lam_re.data(), P.col_lam_re.size() * 8, 8);
     pk.put(P.col_lam_im.data(), P.col_lam_im.size() * 8, 8);
+    pk.put(P.col_beta.data(), P.col_beta.size() * 8, 8);
     pack_plan(pk, P, dp);
     h->bt_kend_d = (const int32_t *)pk.put(P.bt_kend.data(), P.bt_kend.size() * 4, 4);
     h->row_tile_d = (const int32_t *)pk.put(P.row_tile.data(), P.row_tile.size() * 4, 4);
@@ -582,7 +690,8 @@ evec_status evec_destroy(evec_handle h) {
     void *dev[] = {h->diag_d, h->plan_d, h->Y, h->seg_e, h->seg_dx, h->seg_dy, h->seg_nu,
                    h->tau, h->blk_tau, h->status_d, h->hT, h->hQ, h->hX, h->hE, h->hL,
                    h->slA, h->slB, h->rmax, h->cmax, h->ea, h->eb, h->panels,
-                   h->ea_panels, h->boff_d, h->bws, h->bplan_d, h->queue_d};
+                   h->ea_panels, h->boff_d, h->bws, h->bplan_d, h->queue_d, h->tauT,
+                   h->blk_tauT, h->pW};
     for (void *p : dev)
         if (p) cudaFree(p);
     for (auto &t : h->live) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
@@ -659,6 +768,30 @@ evec_status evec_sync(evec_handle h, int64_t *bad_index) {
     return (evec_status)s.code;
 }
 
+// Panel layout of the split tile updates (slices 0: none): panel s (rows
+// above tile s, rounded up to 128) at row prow0[s] of the slice buffer, its
+// row exponents at pea[s].
+static void split_panel_layout(HostPlan &P, int slices) {
+    P.prow0.clear();
+    P.pea.clear();
+    P.panel_rows = 0;
+    if (!slices) return;
+    const int N = (int)P.tile_start.size() - 1;
+    P.prow0.assign(N + 1, 0);
+    P.pea.assign(N + 1, 0);
+    int rows = 0, eas = 0;
+    for (int s = 1; s < N; s++) {
+        const int mpad = split_pad_m(P.tile_start[s]);
+        P.prow0[s] = rows;
+        P.pea[s] = eas;
+        rows += slices * mpad;
+        eas += mpad;
+    }
+    P.prow0[N] = rows;
+    P.pea[N] = eas;
+    P.panel_rows = rows;
+}
+
 evec_status evec_standard(evec_handle h, int64_t n, const double *T, int64_t ldt,
                           const double *Q, int64_t ldq, const uint8_t *select_host,
                           double *X, int64_t ldx, int32_t *scale_exp, double *lam_re,
@@ -683,26 +816,7 @@ evec_status evec_standard(evec_handle h, int64_t n, const double *T, int64_t ldt
     if (m == 0) return EVEC_OK;
     const int N = (int)HP.tile_start.size() - 1;
 
-    if (mode == EVEC_SPLIT) {   // panel layout of the split tile updates
-        HostPlan &WP = h->plan;
-        WP.prow0.assign(N + 1, 0);
-        WP.pea.assign(N + 1, 0);
-        int rows = 0, eas = 0;
-        for (int s = 1; s < N; s++) {
-            const int mpad = split_pad_m(WP.tile_start[s]);
-            WP.prow0[s] = rows;
-            WP.pea[s] = eas;
-            rows += slices * mpad;
-            eas += mpad;
-        }
-        WP.prow0[N] = rows;
-        WP.pea[N] = eas;
-        WP.panel_rows = rows;
-    } else {
-        h->plan.prow0.clear();
-        h->plan.pea.clear();
-        h->plan.panel_rows = 0;
-    }
+    split_panel_layout(h->plan, mode == EVEC_SPLIT ? slices : 0);
     Plan dp;
     EVEC_TRY(upload_plan(h, dp));
     double *Y = X;
@@ -745,7 +859,8 @@ evec_status evec_standard(evec_handle h, int64_t n, const double *T, int64_t ldt
         EVEC_TRY(grow_device(&h->eb, &h->eb_cap, (size_t)Np));
         cudaError_t ce = cudaSuccess;
         timed(h, EVEC_K_TILE_UPDATE, [&] {
-            ce = split_update_prepare(T, ldt, (int)n, N, HP.max_tile, dp.tile_start, h->prow0_d,
+            ce = split_update_prepare(T, ldt, nullptr, 0, (int)n, N, HP.max_tile, dp.tile_start,
+                                      h->prow0_d,
                                       h->pea_d, HP.panel_rows, slices, (int)m, h->panels,
                                       h->ea_panels, h->slB, &sctx, st);
             return N > 1 ? 1 : 0;
@@ -1195,5 +1310,181 @@ extern "C" evec_status evec_tune_set(evec_handle h, int mode, int size_class, in
         (tile != 0 && (tile < 16 || tile > 64)))
         return EVEC_EINVAL;
     h->tune[mode][size_class] = tile;
+    return EVEC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// generalized problem (pencil (S, T))
+// ---------------------------------------------------------------------------
+extern "C" evec_status evec_generalized(evec_handle h, int64_t n, const double *S, int64_t lds,
+                                        const double *T, int64_t ldt, const double *Z,
+                                        int64_t ldz, const uint8_t *select_host, double *X,
+                                        int64_t ldx, int32_t *scale_exp, double *alpha_re,
+                                        double *alpha_im, double *beta, const evec_opts *opt) {
+    if (!h || n < 0 || !ld_ok(lds, n) || !ld_ok(ldt, n) || !ld_ok(ldx, n) ||
+        (Z && !ld_ok(ldz, n)))
+        return EVEC_EINVAL;
+    const int mode = opt ? opt->mode : EVEC_FP64;
+    if (mode != EVEC_FP64 && mode != EVEC_SPLIT) return EVEC_EINVAL;
+    const int slices = (opt && opt->slices) ? opt->slices : 8;
+    if (slices < 2 || slices > 8) return EVEC_EINVAL;
+    const int nb = (opt && opt->tile) ? opt->tile : 64;
+    if (nb < 16 || nb > 64) return EVEC_EINVAL;
+    if (n == 0) return EVEC_OK;
+    if (!S || !T || !X || !scale_exp) return EVEC_EINVAL;
+    DeviceGuard g(h->device);
+    if (!g.ok) return EVEC_ECUDA;
+
+    // plan: S's three central diagonals, T's diagonal and superdiagonal
+    const size_t cnt = (size_t)(3 * n > 2 ? 3 * n - 2 : 1);
+    EVEC_TRY(grow_device(&h->diag_d, &h->diag_cap, 2 * cnt));
+    EVEC_TRY(grow_host(&h->diag_h, &h->diag_h_cap, 2 * cnt));
+    timed(h, EVEC_K_GATHER, [&] {
+        launch_gather_diagonals(S, lds, n, h->diag_d, h->stream);
+        launch_gather_diagonals(T, ldt, n, h->diag_d + cnt, h->stream);
+        return 2;
+    });
+    EVEC_CUDA(cudaGetLastError());
+    EVEC_CUDA(cudaMemcpyAsync(h->diag_h, h->diag_d, 2 * cnt * sizeof(double),
+                              cudaMemcpyDeviceToHost, h->stream));
+    EVEC_CUDA(cudaStreamSynchronize(h->stream));
+    {
+        const double *d = h->diag_h, *dt = h->diag_h + cnt;
+        PencilDiags pd = {dt, dt + 2 * n - 1};
+        int64_t bad = -1;
+        EVEC_TRY(build_plan(n, d, d + n, d + 2 * n - 1, select_host, nb, lds, h->plan, &bad,
+                            &pd));
+    }
+    HostPlan &HP = h->plan;
+    split_panel_layout(HP, mode == EVEC_SPLIT ? slices : 0);
+    const int64_t m = HP.m;
+    if (m == 0) return EVEC_OK;
+    const int N = (int)HP.tile_start.size() - 1;
+    Plan dp;
+    EVEC_TRY(upload_plan(h, dp));
+    double *Y = X;
+    int64_t ldy = ldx;
+    if (Z) {
+        EVEC_TRY(grow_device(&h->Y, &h->Y_cap, (size_t)n * (size_t)m));
+        Y = h->Y;
+        ldy = n;
+    }
+    const size_t segs = (size_t)N * (size_t)m;
+    EVEC_TRY(grow_device(&h->seg_e, &h->segi_cap[0], segs));
+    EVEC_TRY(grow_device(&h->seg_dx, &h->segi_cap[1], segs));
+    EVEC_TRY(grow_device(&h->seg_dy, &h->segi_cap[2], segs));
+    EVEC_TRY(grow_device(&h->seg_nu, &h->segn_cap, segs));
+    EVEC_TRY(grow_device(&h->tau, &h->tau_cap, (size_t)N * (size_t)N));
+    EVEC_TRY(grow_device(&h->blk_tau, &h->blk_tau_cap, HP.blk_start.size()));
+    EVEC_TRY(grow_device(&h->tauT, &h->tauT_cap, (size_t)N * (size_t)N));
+    EVEC_TRY(grow_device(&h->blk_tauT, &h->blk_tauT_cap, HP.blk_start.size()));
+    const int64_t ldw = 2 * 64;
+    EVEC_TRY(grow_device(&h->pW, &h->pW_cap, (size_t)ldw * (size_t)m));
+    if (Z && mode == EVEC_SPLIT) {
+        const int Mp = split_pad_m((int)n), Np = split_pad_n((int)m), Kp = split_pad_k((int)n);
+        EVEC_TRY(grow_device(&h->slA, &h->slA_cap, (size_t)slices * Mp * Kp));
+        EVEC_TRY(grow_device(&h->slB, &h->slB_cap, (size_t)slices * Np * Kp));
+        EVEC_TRY(grow_device(&h->rmax, &h->rmax_cap, (size_t)Mp));
+        EVEC_TRY(grow_device(&h->ea, &h->ea_cap, (size_t)Mp));
+        EVEC_TRY(grow_device(&h->cmax, &h->cmax_cap, (size_t)Np));
+        EVEC_TRY(grow_device(&h->eb, &h->eb_cap, (size_t)Np));
+    }
+    cudaStream_t st = h->stream;
+    timed(h, EVEC_K_NORMS, [&] {
+        launch_tile_norms(S, lds, dp, h->tau, h->blk_tau, h->status_d, st, 1);
+        launch_tile_norms(T, ldt, dp, h->tauT, h->blk_tauT, h->status_d, st, 0);
+        return 2;
+    });
+    Pencil pen;
+    pen.T = T;
+    pen.ldt = ldt;
+    pen.tau = h->tauT;
+    pen.blk_tau = h->blk_tauT;
+    SplitUpdateCtx sctx;
+    if (mode == EVEC_SPLIT) {   // panels of [S T] (K = 2 |tile|)
+        const int Kp = 2 * HP.max_tile <= 64 ? 64 : 128;
+        const int Np = split_pad_n((int)m);
+        EVEC_TRY(grow_device(&h->panels, &h->panels_cap,
+                             (size_t)std::max(HP.panel_rows, 128) * Kp));
+        EVEC_TRY(grow_device(&h->ea_panels, &h->ea_panels_cap, (size_t)std::max(HP.pea[N], 1)));
+        EVEC_TRY(grow_device(&h->slB, &h->slB_cap, (size_t)slices * Np * Kp));
+        EVEC_TRY(grow_device(&h->cmax, &h->cmax_cap, (size_t)Np));
+        EVEC_TRY(grow_device(&h->eb, &h->eb_cap, (size_t)Np));
+        cudaError_t ce = cudaSuccess;
+        timed(h, EVEC_K_TILE_UPDATE, [&] {
+            ce = split_update_prepare(S, lds, T, ldt, (int)n, N, HP.max_tile, dp.tile_start,
+                                      h->prow0_d, h->pea_d, HP.panel_rows, slices, (int)m,
+                                      h->panels, h->ea_panels, h->slB, &sctx, st);
+            return N > 1 ? 1 : 0;
+        });
+        EVEC_CUDA(ce);
+    }
+    for (int s = N - 1; s >= 0; s--) {
+        timed(h, EVEC_K_DIAG_SOLVE, [&] {
+            return launch_diag_solve(s, S, lds, dp, HP.tile_start.data(), HP.tile_real.data(),
+                                     HP.tile_cplx.data(), h->tau, h->blk_tau, Y, ldy, h->seg_e,
+                                     h->seg_nu, h->seg_dx, h->seg_dy, st, &pen);
+        });
+        if (s > 0 && HP.tile_col[s] < m) {
+            if (mode == EVEC_SPLIT) {
+                cudaError_t ce = cudaSuccess;
+                timed(h, EVEC_K_TILE_UPDATE, [&] {
+                    launch_pencil_rhs(s, dp, HP.tile_col.data(), Y, ldy, h->pW, ldw, st);
+                    const int t0 = HP.tile_start[s], ts = HP.tile_start[s + 1] - t0;
+                    if (sctx.Kp == 64) {
+                        ce = split_update_step_resident(
+                            sctx, t0, ts, HP.prow0[s], HP.pea[s], HP.tile_col[s], (int)m, Y, ldy,
+                            h->ea_panels, h->slB, h->eb, h->row_tile_d, h->seg_dx, h->seg_dy,
+                            h->seg_nu, &h->status_d->timeout, h->nsm, st, h->pW, ldw);
+                        return 3;
+                    }
+                    ce = split_update_step(sctx, t0, ts, HP.prow0[s], HP.pea[s], HP.tile_col[s],
+                                           (int)m, Y, ldy, h->ea_panels, h->slB, h->cmax, h->eb,
+                                           h->row_tile_d, h->seg_dx, h->seg_dy, h->seg_nu,
+                                           &h->status_d->timeout, st, h->pW, ldw);
+                    return 4;
+                });
+                EVEC_CUDA(ce);
+            } else {
+                timed(h, EVEC_K_TILE_UPDATE, [&] {
+                    return launch_tile_update_pencil(s, S, lds, T, ldt, dp, HP.tile_start.data(),
+                                                     HP.tile_col.data(), Y, ldy, h->seg_dx,
+                                                     h->seg_dy, h->seg_nu, h->pW, ldw, st);
+                });
+            }
+        }
+    }
+    timed(h, EVEC_K_FINALIZE, [&] {
+        launch_finalize(dp, Y, ldy, h->seg_e, scale_exp, st);
+        return 1;
+    });
+    if (Z && mode == EVEC_SPLIT) {
+        cudaError_t ce = cudaSuccess;
+        timed(h, EVEC_K_BACKTRANSFORM, [&] {
+            ce = launch_split_gemm(Z, ldz, Y, ldy, (int)n, (int)m, (int)n, slices, h->bt_kend_d, X,
+                                   ldx, h->slA, h->slB, h->rmax, h->cmax, h->ea, h->eb,
+                                   &h->status_d->timeout, st);
+            return 5;
+        });
+        EVEC_CUDA(ce);
+    } else if (Z) {
+        timed(h, EVEC_K_BACKTRANSFORM, [&] {
+            launch_backtransform(Z, ldz, dp, Y, ldy, X, ldx, st);
+            return 1;
+        });
+    }
+    if (Z)
+        timed(h, EVEC_K_CANONICALIZE, [&] {
+            launch_canonicalize(dp, X, ldx, scale_exp, st);
+            return 1;
+        });
+    EVEC_CUDA(cudaGetLastError());
+    if (alpha_re)
+        EVEC_CUDA(cudaMemcpyAsync(alpha_re, h->plan_h, m * 8, cudaMemcpyHostToDevice, st));
+    if (alpha_im)
+        EVEC_CUDA(cudaMemcpyAsync(alpha_im, h->plan_h + m * 8, m * 8, cudaMemcpyHostToDevice, st));
+    if (beta)
+        EVEC_CUDA(cudaMemcpyAsync(beta, h->plan_h + 2 * m * 8, m * 8, cudaMemcpyHostToDevice, st));
+    if (opt && opt->check) return evec_sync(h, nullptr);
     return EVEC_OK;
 }

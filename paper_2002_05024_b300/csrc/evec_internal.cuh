@@ -60,6 +60,18 @@ struct Plan {
     const int32_t *ord_cplx;    // [ncplx]
     const int32_t *tile_real;   // [ntiles + 1] first position in ord_real with tile >= s
     const int32_t *tile_cplx;   // [ntiles + 1]
+    // pencils (beta S - alpha T) only, else null: unit_lam holds alpha
+    const double *unit_beta;    // [nunits]
+    const double *unit_smin;    // [nunits] perturbation threshold of the small solves
+};
+
+// The second matrix T of a pencil (upper triangular) with its tile norms
+// (tau[r * N + s] = |T_rs|_inf) and in-tile block column norms.
+struct Pencil {
+    const double *T = nullptr;
+    int64_t ldt = 0;
+    const double *tau = nullptr;
+    const double *blk_tau = nullptr;
 };
 
 // One matrix of the batched mode: its plan, input, output and workspaces.

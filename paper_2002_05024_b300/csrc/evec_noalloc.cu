@@ -36,13 +36,13 @@ namespace evec {
 void launch_gather_diagonals(const double *T, int64_t ldt, int64_t n, double *out,
                              cudaStream_t st);
 void launch_tile_norms(const double *T, int64_t ldt, const Plan &p, double *tau,
-                       double *blk_tau, DevStatus *status, cudaStream_t st);
+                       double *blk_tau, DevStatus *status, cudaStream_t st, int lower = 1);
 int launch_diag_solve(int s, const double *T, int64_t ldt, const Plan &p,
                        const int32_t *tile_start_h, const int32_t *tile_real_h,
                        const int32_t *tile_cplx_h,
                        const double *tau, const double *blk_tau, double *Y, int64_t ldy,
                        int32_t *seg_e, double *seg_nu, int32_t *seg_dx, int32_t *seg_dy,
-                       cudaStream_t st);
+                       cudaStream_t st, const Pencil *pen = nullptr);
 void launch_tile_update(int s, const double *T, int64_t ldt, const Plan &p, int max_tile,
                         const int32_t *tile_col_h, double *Y, int64_t ldy,
                         const int32_t *seg_dx, const int32_t *seg_dy, double *seg_nu,

@@ -35,11 +35,12 @@ struct GemmSmem {
 //   A(i, k) = A[i + k * lda], rows i < a_rows (rows beyond read as 0)
 //   B(k, j) = B[k + j * ldb], columns j < ncols
 //   scale_b: B column j is multiplied by 2^sm.bexp[j] while staged (exact)
+//   zero: start from acc = 0 (else accumulate onto acc)
 template <int BM>
 __device__ __forceinline__ void dfma_mainloop(const double *__restrict__ A, int64_t lda, int a_rows,
                                               const double *__restrict__ B, int64_t ldb, int K,
                                               int ncols, GemmSmem<BM> &sm, bool scale_b,
-                                              double (&acc)[BM / 16][4]) {
+                                              double (&acc)[BM / 16][4], bool zero = true) {
     constexpr int MI = BM / 16;
     constexpr int A_PER = BM * kBK / kThreads;   // A elements per thread per chunk
     constexpr int B_PER = kBK * kBN / kThreads;  // = 4
@@ -75,10 +76,11 @@ __device__ __forceinline__ void dfma_mainloop(const double *__restrict__ A, int6
         }
     };
 
+    if (zero)
 #pragma unroll
-    for (int i = 0; i < MI; i++)
+        for (int i = 0; i < MI; i++)
 #pragma unroll
-        for (int j = 0; j < 4; j++) acc[i][j] = 0.0;
+            for (int j = 0; j < 4; j++) acc[i][j] = 0.0;
 
     if (K <= 0) return;
     load(0);
@@ -111,11 +113,16 @@ __device__ __forceinline__ void dfma_mainloop(const double *__restrict__ A, int6
 // ---------------------------------------------------------------------------
 // tile update at step s: grid (column blocks, r = 0..s-1)
 // ---------------------------------------------------------------------------
-template <int BM>
+// GEN (pencil beta S - alpha T): T holds S, B2 / ldb2 the second matrix, and
+// the right-hand side comes from W = [beta X_s; -(alpha X_s)] (2 K x active
+// columns, ld ldw) instead of Y: acc = S_rs W_top + T_rs W_bottom.
+template <int BM, bool GEN>
 __global__ void __launch_bounds__(kThreads)
     k_tile_update(int s, const double *__restrict__ T, int64_t ldt, Plan P,
                   double *__restrict__ Y, int64_t ldy, const int32_t *__restrict__ seg_dx,
-                  const int32_t *__restrict__ seg_dy, double *__restrict__ seg_nu) {
+                  const int32_t *__restrict__ seg_dy, double *__restrict__ seg_nu,
+                  const double *__restrict__ B2, int64_t ldb2, const double *__restrict__ W,
+                  int64_t ldw) {
     extern __shared__ __align__(16) unsigned char smraw[];
     GemmSmem<BM> &sm = *reinterpret_cast<GemmSmem<BM> *>(smraw);
     __shared__ int sdy[kBN];
@@ -145,8 +152,16 @@ __global__ void __launch_bounds__(kThreads)
     __syncthreads();
 
     double acc[MI][4];
-    dfma_mainloop<BM>(T + r0 + (int64_t)k0 * ldt, ldt, rows, Y + k0 + j0 * ldy, ldy, K, ncols,
-                      sm, true, acc);
+    if (!GEN) {
+        dfma_mainloop<BM>(T + r0 + (int64_t)k0 * ldt, ldt, rows, Y + k0 + j0 * ldy, ldy, K, ncols,
+                          sm, true, acc);
+    } else {
+        const double *w = W + (j0 - P.tile_col[s]) * ldw;
+        dfma_mainloop<BM>(T + r0 + (int64_t)k0 * ldt, ldt, rows, w, ldw, K, ncols, sm, true, acc);
+        __syncthreads();   // the staging buffers are reused
+        dfma_mainloop<BM>(B2 + r0 + (int64_t)k0 * ldb2, ldb2, rows, w + K, ldw, K, ncols, sm, true,
+                          acc, false);
+    }
 
     double cmax[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
@@ -218,9 +233,33 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
+// W = [beta X_s; -(alpha X_s)] for the active columns of step s (pencils):
+// column c of unit u (alpha = ar + i ai, beta) and its pair partner give
+// (alpha x)_re = ar xr - ai xi, (alpha x)_im = ar xi + ai xr.
+__global__ void k_pencil_rhs(int s, Plan P, const double *__restrict__ Y, int64_t ldy,
+                             double *__restrict__ W, int64_t ldw) {
+    const int t0 = P.tile_start[s], K = P.tile_start[s + 1] - t0;
+    const int64_t c = P.tile_col[s] + blockIdx.x;
+    const int k = threadIdx.x;
+    if (k >= K || c >= P.m) return;
+    const int u = P.col_unit[c];
+    const int cu = P.unit_col[u];
+    const double ar = P.unit_lam[2 * u], ai = P.unit_lam[2 * u + 1], be = P.unit_beta[u];
+    const double x = Y[(t0 + k) + c * ldy];
+    double ax;
+    if (ai == 0.0) ax = ar * x;
+    else if (c == cu) ax = fma(ar, x, -ai * Y[(t0 + k) + (c + 1) * ldy]);   // real part
+    else ax = fma(ar, x, ai * Y[(t0 + k) + (c - 1) * ldy]);                 // imaginary part
+    double *w = W + (c - P.tile_col[s]) * ldw;
+    w[k] = be * x;
+    w[K + k] = -ax;
+}
+
 template <int BM>
 static void set_smem_attr() {
-    cudaFuncSetAttribute(k_tile_update<BM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_tile_update<BM, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(GemmSmem<BM>));
+    cudaFuncSetAttribute(k_tile_update<BM, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sizeof(GemmSmem<BM>));
     cudaFuncSetAttribute(k_backtransform<BM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sizeof(GemmSmem<BM>));
@@ -236,13 +275,41 @@ void launch_tile_update(int s, const double *T, int64_t ldt, const Plan &p, int 
     dim3 grid((unsigned)((cols + kBN - 1) / kBN), (unsigned)s);
     if (max_tile <= 64) {
         set_smem_attr<64>();
-        k_tile_update<64><<<grid, kThreads, sizeof(GemmSmem<64>), st>>>(s, T, ldt, p, Y, ldy,
-                                                                        seg_dx, seg_dy, seg_nu);
+        k_tile_update<64, false><<<grid, kThreads, sizeof(GemmSmem<64>), st>>>(
+            s, T, ldt, p, Y, ldy, seg_dx, seg_dy, seg_nu, nullptr, 0, nullptr, 0);
     } else {
         set_smem_attr<128>();
-        k_tile_update<128><<<grid, kThreads, sizeof(GemmSmem<128>), st>>>(s, T, ldt, p, Y, ldy,
-                                                                          seg_dx, seg_dy, seg_nu);
+        k_tile_update<128, false><<<grid, kThreads, sizeof(GemmSmem<128>), st>>>(
+            s, T, ldt, p, Y, ldy, seg_dx, seg_dy, seg_nu, nullptr, 0, nullptr, 0);
     }
+}
+
+// W = [beta X_s; -(alpha X_s)] of step s (tiles of at most 64 rows).
+void launch_pencil_rhs(int s, const Plan &p, const int32_t *tile_col_h, const double *Y,
+                       int64_t ldy, double *W, int64_t ldw, cudaStream_t st) {
+    const int64_t cols = p.m - tile_col_h[s];
+    if (cols <= 0) return;
+    k_pencil_rhs<<<(unsigned)cols, 64, 0, st>>>(s, p, Y, ldy, W, ldw);
+}
+
+// Pencils (tiles of at most 64 rows): W = [beta X_s; -(alpha X_s)], then
+// Y_r <- 2^dy Y_r - (S_rs W_top + T_rs W_bottom) 2^dx.  W: 2 * 64 x m
+// doubles, ld ldw >= 2 |tile s|.  Returns the number of kernels launched.
+int launch_tile_update_pencil(int s, const double *S, int64_t lds, const double *T2,
+                              int64_t ldt2, const Plan &p, const int32_t *tile_start_h,
+                              const int32_t *tile_col_h, double *Y, int64_t ldy,
+                              const int32_t *seg_dx, const int32_t *seg_dy, double *seg_nu,
+                              double *W, int64_t ldw, cudaStream_t st) {
+    if (s <= 0) return 0;
+    const int64_t cols = p.m - tile_col_h[s];
+    if (cols <= 0) return 0;
+    launch_pencil_rhs(s, p, tile_col_h, Y, ldy, W, ldw, st);
+    dim3 grid((unsigned)((cols + kBN - 1) / kBN), (unsigned)s);
+    set_smem_attr<64>();
+    k_tile_update<64, true><<<grid, kThreads, sizeof(GemmSmem<64>), st>>>(
+        s, S, lds, p, Y, ldy, seg_dx, seg_dy, seg_nu, T2, ldt2, W, ldw);
+    (void)tile_start_h;
+    return 2;
 }
 
 void launch_backtransform(const double *Q, int64_t ldq, const Plan &p, const double *Y,

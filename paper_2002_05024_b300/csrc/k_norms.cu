@@ -71,10 +71,12 @@ __device__ __forceinline__ double warp_max(double v) {
 
 // One CTA of 128 threads per tile pair (r, s), r <= s; blockIdx.x runs over
 // the upper triangle of the tile grid, column by column.
+// lower = 0: T is upper triangular (the second matrix of a pencil) and its
+// first subdiagonal is neither read nor validated.
 __global__ void __launch_bounds__(128) k_tile_norms(const double *__restrict__ T, int64_t ldt,
                                                     Plan P, double *__restrict__ tau,
                                                     double *__restrict__ blk_tau,
-                                                    DevStatus *status) {
+                                                    DevStatus *status, int lower) {
     const int idx = blockIdx.x;
     int s = (int)((sqrt(8.0 * idx + 1.0) - 1.0) * 0.5);
     while (s * (s + 1) / 2 > idx) s--;
@@ -107,7 +109,7 @@ __global__ void __launch_bounds__(128) k_tile_norms(const double *__restrict__ T
     // diagonal tile: validate the upper part and the first subdiagonal
     for (int j = c0; j < c1; j++) {
         const int i = r0 + tid;
-        if (i < r1 && i <= j + 1)
+        if (i < r1 && i <= j + lower)
             check_entry(T[i + (int64_t)j * ldt], (long long)i + (long long)j * ldt, status);
     }
     // in-tile block column norms: one warp per block
@@ -128,10 +130,10 @@ __global__ void __launch_bounds__(128) k_tile_norms(const double *__restrict__ T
 }
 
 void launch_tile_norms(const double *T, int64_t ldt, const Plan &p, double *tau,
-                       double *blk_tau, DevStatus *status, cudaStream_t st) {
+                       double *blk_tau, DevStatus *status, cudaStream_t st, int lower) {
     int64_t N = p.ntiles;
     int64_t pairs = N * (N + 1) / 2;
-    k_tile_norms<<<(unsigned)pairs, 128, 0, st>>>(T, ldt, p, tau, blk_tau, status);
+    k_tile_norms<<<(unsigned)pairs, 128, 0, st>>>(T, ldt, p, tau, blk_tau, status, lower);
 }
 
 }  // namespace evec

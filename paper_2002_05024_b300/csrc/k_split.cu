@@ -476,11 +476,17 @@ cudaError_t launch_split_gemm(const double *A, int64_t lda, const double *B, int
 // prow0[s] of the buffer; row exponents (per panel row) at pea[s] + i.
 // One CTA per 32 rows of one panel; 256 threads.
 __global__ void __launch_bounds__(256)
-    k_slice_panels(const double *__restrict__ T, int64_t ldt, const int32_t *__restrict__ tstart,
+    k_slice_panels(const double *__restrict__ T, int64_t ldt, const double *__restrict__ T2,
+                   int64_t ldt2, const int32_t *__restrict__ tstart,
                    const int32_t *__restrict__ prow0, const int32_t *__restrict__ pea, int S,
                    int Kp, __nv_bfloat16 *__restrict__ out, int *__restrict__ ea) {
     const int s = blockIdx.y + 1;
     const int t0 = tstart[s], ts = tstart[s + 1] - t0;
+    // panel row i: T[i, tile s], then (pencils) T2[i, tile s]
+    const int kw = T2 ? 2 * ts : ts;
+    auto at = [&](int i, int k) -> double {
+        return k < ts ? T[i + (int64_t)(t0 + k) * ldt] : T2[i + (int64_t)(t0 + k - ts) * ldt2];
+    };
     const int mpad = (t0 + kTM - 1) / kTM * kTM;
     const int i0 = blockIdx.x * 32;
     if (i0 >= mpad) return;
@@ -493,7 +499,7 @@ __global__ void __launch_bounds__(256)
         const int i = i0 + r;
         long long b = 0;
         if (i < t0)
-            for (int k = part; k < ts; k += 8) b = max(b, abs_bits(T[i + (int64_t)(t0 + k) * ldt]));
+            for (int k = part; k < kw; k += 8) b = max(b, abs_bits(at(i, k)));
         rm[r][part] = b;
     }
     __syncthreads();
@@ -509,7 +515,7 @@ __global__ void __launch_bounds__(256)
             const int r = e % 32, c = e / 32;
             const int i = i0 + r, k = kh + c;
             int d[kSplitMaxS] = {0, 0, 0, 0, 0, 0, 0, 0};
-            if (i < t0 && k < ts) digits7(T[i + (int64_t)(t0 + k) * ldt], rex[r], S, d);
+            if (i < t0 && k < kw) digits7(at(i, k), rex[r], S, d);
             for (int p = 0; p < S; p++) sd[p][r][c] = digit_bf16(d[p], p);
         }
         __syncthreads();
@@ -522,20 +528,22 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-// Once per call: slice every panel of T; encode the two tensor maps.
-cudaError_t split_update_prepare(const double *T, int64_t ldt, int n, int ntiles, int maxtile,
+// Once per call: slice every panel of T (pencils: of [S T], K = 2 |tile|);
+// encode the two tensor maps.
+cudaError_t split_update_prepare(const double *T, int64_t ldt, const double *T2, int64_t ldt2,
+                                 int n, int ntiles, int maxtile,
                                  const int32_t *tstart_d, const int32_t *prow0_d,
                                  const int32_t *pea_d, int total_rows, int S, int m,
                                  __nv_bfloat16 *panels, int *ea_panels, __nv_bfloat16 *sb,
                                  SplitUpdateCtx *ctx, cudaStream_t st) {
     if (!get_encoder()) return cudaErrorInvalidValue;
     ctx->S = S;
-    ctx->Kp = maxtile <= 64 ? 64 : 128;
+    ctx->Kp = (T2 ? 2 * maxtile : maxtile) <= 64 ? 64 : 128;
     ctx->Npad = split_pad_n(m);
     if (ntiles > 1) {
         const int maxblocks = split_pad_m(n) / 32;   // >= roundup(t0_s, 128) / 32 for all s
         k_slice_panels<<<dim3(maxblocks, ntiles - 1), 256, 0, st>>>(
-            T, ldt, tstart_d, prow0_d, pea_d, S, ctx->Kp, panels, ea_panels);
+            T, ldt, T2, ldt2, tstart_d, prow0_d, pea_d, S, ctx->Kp, panels, ea_panels);
     }
     if (!make_map(&ctx->tmA, panels, total_rows > 0 ? total_rows : kTM, ctx->Kp, kTM) ||
         !make_map(&ctx->tmB32, sb, S * ctx->Npad, ctx->Kp, 32))
@@ -545,17 +553,22 @@ cudaError_t split_update_prepare(const double *T, int64_t ldt, int n, int ntiles
 
 // Step s: slice X_s = Y[t0_s:t1_s, col0:m], then Y_r -= T_rs X_s for all rows
 // above tile s with the robust epilogue.
+// rhs (pencils): the right-hand side [beta X_s; -(alpha X_s)] (2 |tile| rows,
+// ld ldr) replaces X_s = Y[t0 : t0 + ts, col0 : m].
 cudaError_t split_update_step(const SplitUpdateCtx &ctx, int t0, int ts, int prow0, int pea,
                               int col0, int m, double *Y, int64_t ldy, const int *ea_panels,
                               __nv_bfloat16 *sb, unsigned long long *colmax, int *eb,
                               const int32_t *row_tile, const int32_t *dx, const int32_t *dy,
-                              double *seg_nu, int *err, cudaStream_t st) {
+                              double *seg_nu, int *err, cudaStream_t st, const double *rhs,
+                              int64_t ldr) {
     const int N = m - col0;
     if (N <= 0 || t0 <= 0) return cudaSuccess;
-    const double *B = Y + t0 + (int64_t)col0 * ldy;
-    k_col_max<<<(N + 7) / 8, 256, 0, st>>>(B, ldy, ts, N, colmax);
+    const double *B = rhs ? rhs : Y + t0 + (int64_t)col0 * ldy;
+    const int64_t ldb = rhs ? ldr : ldy;
+    const int K = rhs ? 2 * ts : ts;
+    k_col_max<<<(N + 7) / 8, 256, 0, st>>>(B, ldb, K, N, colmax);
     k_slice_cols<<<dim3((ctx.Kp + 255) / 256, split_pad_n(N)), 256, 0, st>>>(
-        B, ldy, ts, N, ctx.S, colmax, sb, ctx.Npad, ctx.Kp, eb);
+        B, ldb, K, N, ctx.S, colmax, sb, ctx.Npad, ctx.Kp, eb);
     const int mpad = (t0 + kTM - 1) / kTM * kTM;
     const size_t smem = split_smem_bytes();
     cudaFuncSetAttribute(k_split_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -568,7 +581,7 @@ cudaError_t split_update_step(const SplitUpdateCtx &ctx, int t0, int ts, int pro
     upd.m = m;
     upd.col0 = col0;
     k_split_gemm<true><<<dim3(split_pad_n(N) / kTN, mpad / kTM), kSplitThreads, smem, st>>>(
-        ctx.tmA, ctx.tmB32, ctx.S, t0, N, prow0, mpad, ctx.Npad, nullptr, (ts + kTK - 1) / kTK * kTK,
+        ctx.tmA, ctx.tmB32, ctx.S, t0, N, prow0, mpad, ctx.Npad, nullptr, (K + kTK - 1) / kTK * kTK,
         ea_panels + pea, eb, Y, ldy, upd, err);
     return cudaGetLastError();
 }

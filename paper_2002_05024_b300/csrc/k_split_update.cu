@@ -366,17 +366,20 @@ __global__ void __launch_bounds__(256)
 
 // Step s of the split tile updates, panel-resident form (tiles <= 64 rows):
 // slice X_s = Y[t0 : t0 + ts, col0 : m], then update every row above tile s.
+// rhs (pencils, 2 |tile| <= 64): the right-hand side [beta X_s; -(alpha X_s)]
+// (ld ldr) replaces X_s.
 cudaError_t split_update_step_resident(const SplitUpdateCtx &ctx, int t0, int ts, int prow0,
                                        int pea, int col0, int m, double *Y, int64_t ldy,
                                        const int *ea_panels, __nv_bfloat16 *sb, int *eb,
                                        const int32_t *row_tile, const int32_t *dx,
                                        const int32_t *dy, double *seg_nu, int *err, int nsm,
-                                       cudaStream_t st) {
+                                       cudaStream_t st, const double *rhs, int64_t ldr) {
     const int N = m - col0;
     if (N <= 0 || t0 <= 0) return cudaSuccess;
     const int Nr = (N + kUN - 1) / kUN * kUN;
-    k_slice_xs<<<Nr / 8, 256, 0, st>>>(Y + t0 + (int64_t)col0 * ldy, ldy, ts, N, Nr, ctx.S, sb,
-                                       ctx.Npad, eb);
+    const int K = rhs ? 2 * ts : ts;
+    k_slice_xs<<<Nr / 8, 256, 0, st>>>(rhs ? rhs : Y + t0 + (int64_t)col0 * ldy, rhs ? ldr : ldy,
+                                       K, N, Nr, ctx.S, sb, ctx.Npad, eb);
     const int mpad = (t0 + kTM - 1) / kTM * kTM;
     const int gy = mpad / kTM;
     const int ntN = Nr / kUN;
@@ -384,7 +387,7 @@ cudaError_t split_update_step_resident(const SplitUpdateCtx &ctx, int t0, int ts
     const size_t smem = split_update_smem_bytes();
     cudaFuncSetAttribute(k_split_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_split_update<<<dim3(gx, gy), kUThreads, smem, st>>>(
-        ctx.tmA, ctx.tmB32, ctx.S, t0, N, prow0, mpad, ctx.Npad, (ts + kTK - 1) / kTK * kTK,
+        ctx.tmA, ctx.tmB32, ctx.S, t0, N, prow0, mpad, ctx.Npad, (K + kTK - 1) / kTK * kTK,
         ea_panels + pea, eb, Y, ldy, row_tile, dx, dy, (unsigned long long *)seg_nu, m, col0,
         err);
     return cudaGetLastError();
