@@ -92,6 +92,21 @@ typedef struct {
                     the device status directly */
     int slices;  /* EVEC_SPLIT: digit slices per operand, 2..8; 0 = 8
                     (relative error of a product ~2^(-7 slices)) */
+    int refine;  /* EVEC_SPLIT, evec_standard: nonzero = one residual-
+                    correction sweep after the solve: the residual
+                    r = -(T - lambda I) y in FP64 on the rows above each
+                    column's block, formed on the solver's scaled segments
+                    (each tile row in its own power-of-two scale), the
+                    correction (T - lambda I) d = r solved by the same
+                    robust tiled solver, y <- y + d exactly (power-of-two
+                    scaling, one FP64 addition per entry).  A column whose
+                    correction exceeds 2^(20 - 7 slices) of it keeps its
+                    unrefined value: there the residual's own FP64
+                    rounding, amplified by an ill-conditioned column,
+                    outweighs the split error.  Costs one FP64 product of
+                    about n^3 / 3 flops for all columns, and an extra
+                    n x m FP64 workspace.  Ignored in EVEC_FP64 mode and
+                    for pencils. */
 } evec_opts;
 
 /* Create a handle on CUDA device `device` that launches on `cuda_stream`
@@ -170,7 +185,10 @@ enum {
     EVEC_K_BACKTRANSFORM = 5,/* X = Q Y (FP64, or split: slicing + products) */
     EVEC_K_CANONICALIZE = 6, /* canonical form after Q */
     EVEC_K_BATCHED = 7,      /* the persistent kernel of evec_batched */
-    EVEC_K_COUNT = 8
+    EVEC_K_REFINE = 8,       /* residual, right-hand side, correction add
+                                (the correction solve itself counts under
+                                EVEC_K_DIAG_SOLVE / EVEC_K_TILE_UPDATE) */
+    EVEC_K_COUNT = 9
 };
 
 /* Enable (1) or disable (0) per-kernel timing: while enabled, every kernel

@@ -30,7 +30,7 @@ EVEC_OK, EVEC_EINVAL, EVEC_ENOTSCHUR, EVEC_ENONFINITE = 0, 1, 2, 3
 EVEC_ENOMEM, EVEC_ECUDA, EVEC_ETIMEOUT, EVEC_ERESIDUAL = 4, 5, 6, 7
 EVEC_ECAPACITY = 8
 KERNELS = ("gather", "tile_norms", "diag_solve", "tile_update", "finalize",
-           "backtransform", "canonicalize", "batched")
+           "backtransform", "canonicalize", "batched", "refine")
 
 
 class EvecError(RuntimeError):
@@ -47,7 +47,7 @@ class EvecError(RuntimeError):
 
 class _Opts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int), ("tile", ctypes.c_int), ("check", ctypes.c_int),
-                ("slices", ctypes.c_int)]
+                ("slices", ctypes.c_int), ("refine", ctypes.c_int)]
 
 
 MODES = {"fp64": 0, "split": 1}
@@ -127,8 +127,8 @@ def _mask(select, n):
     return s
 
 
-def _opts(tile, check, mode="fp64", slices=0):
-    return _Opts(MODES[mode], int(tile), 1 if check else 0, int(slices))
+def _opts(tile, check, mode="fp64", slices=0, refine=False):
+    return _Opts(MODES[mode], int(tile), 1 if check else 0, int(slices), 1 if refine else 0)
 
 
 # ---------------------------------------------------------------------------
@@ -244,9 +244,10 @@ def count(T, select=None) -> int:
 
 
 def standard(T, Q=None, select=None, tile: int = 0, check: bool = False, out=None,
-             mode: str = "fp64", slices: int = 0):
+             mode: str = "fp64", slices: int = 0, refine: bool = False):
     """Eigenvectors of the quasi-triangular T (optionally X = Q Y).
 
+    refine (split mode): one FP64 residual-correction sweep after the solve.
     Returns (X, scale_exp, lam_re, lam_im) as CUDA tensors; X is (n, m)
     column-major.  The call is asynchronous on the current stream; device
     detected input errors surface at ``sync()`` (or immediately with
@@ -269,7 +270,7 @@ def standard(T, Q=None, select=None, tile: int = 0, check: bool = False, out=Non
     ldx = X.stride(1) if m > 1 else max(n, 1)
     if m == 0:
         return X, e, lr, li
-    opts = _opts(tile, False, mode, slices)
+    opts = _opts(tile, False, mode, slices, refine)
     st = lib().evec_standard(h.ptr, n, T.data_ptr(), ldt, Q.data_ptr() if Q is not None else None,
                              ldq, _np_ptr(sel), X.data_ptr(), ldx, e.data_ptr(), lr.data_ptr(),
                              li.data_ptr(), ctypes.byref(opts))
@@ -329,7 +330,7 @@ def generalized(S, T, Z=None, select=None, tile: int = 0, check: bool = False,
 
 
 def standard_host(T, Q=None, select=None, tile: int = 0, device: int = 0,
-                  mode: str = "fp64", slices: int = 0):
+                  mode: str = "fp64", slices: int = 0, refine: bool = False):
     """The same computation from host numpy arrays (column-major float64);
     copies in, computes, copies out.  Returns numpy arrays."""
     Tf = np.asfortranarray(T, dtype=np.float64)
@@ -347,7 +348,7 @@ def standard_host(T, Q=None, select=None, tile: int = 0, device: int = 0,
     import torch
     h = handle(device)
     h.set_stream(torch.cuda.current_stream(device).cuda_stream)
-    opts = _opts(tile, False, mode, slices)
+    opts = _opts(tile, False, mode, slices, refine)
     st = lib().evec_standard_host(h.ptr, n, _np_ptr(Tf), _np_ptr(Qf), _np_ptr(sel), _np_ptr(X),
                                   _np_ptr(e), _np_ptr(lr), _np_ptr(li), ctypes.byref(opts))
     _check(st, "evec_standard_host")

@@ -253,7 +253,11 @@ __device__ __forceinline__ void update_rows_pencil(double *myr, double *myi, con
     }
 }
 
-template <int W, bool C, bool GEN = false>
+// RHS: the segments start from a given right-hand side instead of the
+// eigenvector's own block: every unit (own tile included) loads its rows of
+// Y with exponents seg_e and maxima seg_nu, the own block is fixed at zero,
+// and no segment is fresh (the correction solve of the residual sweep).
+template <int W, bool C, bool GEN = false, bool RHS = false>
 __device__ void diag_tile(int s, int list_pos0, const double *__restrict__ T, int64_t ldt,
                           const Plan &P, const double *__restrict__ tau,
                           const double *__restrict__ blk_tau, double *__restrict__ Y, int64_t ldy,
@@ -337,7 +341,7 @@ __device__ void diag_tile(int s, int list_pos0, const double *__restrict__ T, in
     for (int idx = tid; idx < kUnits * ts; idx += kThreads) {
         const int uu = idx / ts, i = idx % ts;
         const int c = ucol[uu];
-        if (c >= 0 && !uown[uu]) {
+        if (c >= 0 && (RHS || !uown[uu])) {
             cp_async8(&yr[i * ys + uu], &Y[(t0 + i) + (int64_t)c * ldy]);
             if (C) cp_async8(&yi[i * ys + uu], &Y[(t0 + i) + (int64_t)(c + 1) * ldy]);
         } else {
@@ -395,7 +399,7 @@ __device__ void diag_tile(int s, int list_pos0, const double *__restrict__ T, in
 
     int e = 0;
     long long nbits = 0;
-    if (valid && !own) {
+    if (valid && (RHS || !own)) {
         e = seg_e[(int64_t)s * m + col];
         for (int i = g; i < ts; i += G) {
             nbits = max(nbits, abs_bits(myr[i * ys]));
@@ -445,9 +449,14 @@ __device__ void diag_tile(int s, int list_pos0, const double *__restrict__ T, in
         if (act) {
             int sc = 0;
             if (!solving) {
-                const double *o = P.unit_own + 4 * u;
-                z0 = {o[0], C ? o[2] : 0.0};
-                z1 = {o[1], C ? o[3] : 0.0};
+                if (RHS) {   // the own block stays fixed: its correction is zero
+                    z0 = {0.0, 0.0};
+                    z1 = {0.0, 0.0};
+                } else {
+                    const double *o = P.unit_own + 4 * u;
+                    z0 = {o[0], C ? o[2] : 0.0};
+                    z1 = {o[1], C ? o[3] : 0.0};
+                }
             } else {
                 sc = solve<C>(F, bs, r0, r1, z0, z1);
             }
@@ -558,7 +567,7 @@ __device__ void diag_tile(int s, int list_pos0, const double *__restrict__ T, in
             if (idx < items) {
                 const int uu = idx % kUnits, r = idx / kUnits;
                 const int c = ucol[uu];
-                if (c >= 0 && !uown[uu]) {
+                if (c >= 0 && (RHS || !uown[uu])) {
                     const int64_t at = (int64_t)r * m + c;
                     er[j] = seg_e[at];
                     nur[j] = seg_nu[at];
@@ -575,7 +584,7 @@ __device__ void diag_tile(int s, int list_pos0, const double *__restrict__ T, in
             if (c < 0) continue;
             const int64_t at = (int64_t)r * m + c;
             const int es = ue[uu];
-            const bool ownu = uown[uu];
+            const bool ownu = !RHS && uown[uu];   // fresh segments above the own block
             const int e_r = ownu ? es : er[j];
             const int a = min(e_r, es);
             const double nup = ownu ? 0.0 : scale2(nur[j], a - e_r);

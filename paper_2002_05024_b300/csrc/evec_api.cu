@@ -34,7 +34,15 @@ int launch_diag_solve(int s, const double *T, int64_t ldt, const Plan &p,
                        const int32_t *tile_cplx_h,
                        const double *tau, const double *blk_tau, double *Y, int64_t ldy,
                        int32_t *seg_e, double *seg_nu, int32_t *seg_dx, int32_t *seg_dy,
-                       cudaStream_t st, const Pencil *pen = nullptr);
+                       cudaStream_t st, const Pencil *pen = nullptr, bool rhs = false);
+void launch_residual(const double *T, int64_t ldt, const Plan &p, int ntiles, int max_tile,
+                     const double *Y, int64_t ldy, const int32_t *seg_e,
+                     const int32_t *row_tile, double *R, int64_t ldr, cudaStream_t st);
+void launch_rhs_init(const Plan &p, const double *R, int64_t ldr, double *seg_nu,
+                     cudaStream_t st);
+void launch_refine_combine(const Plan &p, double *Y, int64_t ldy, const int32_t *ey,
+                           const double *D, int64_t ldd, const int32_t *ed, int max_rel,
+                           cudaStream_t st);
 void launch_tile_update(int s, const double *T, int64_t ldt, const Plan &p, int max_tile,
                         const int32_t *tile_col_h, double *Y, int64_t ldy,
                         const int32_t *seg_dx, const int32_t *seg_dy, double *seg_nu,
@@ -354,6 +362,8 @@ struct evec_ctx {
     double *diag_d = nullptr; size_t diag_cap = 0;
     unsigned char *plan_d = nullptr; size_t plan_cap = 0;
     double *Y = nullptr; size_t Y_cap = 0;
+    double *Rd = nullptr; size_t Rd_cap = 0;   // residual / correction (refine)
+    int32_t *seg_ey = nullptr; size_t seg_ey_cap = 0;   // exponents of y (refine)
     int32_t *seg_e = nullptr, *seg_dx = nullptr, *seg_dy = nullptr; size_t segi_cap[3] = {0, 0, 0};
     double *seg_nu = nullptr; size_t segn_cap = 0;
     double *tau = nullptr; size_t tau_cap = 0;
@@ -691,7 +701,7 @@ evec_status evec_destroy(evec_handle h) {
                    h->tau, h->blk_tau, h->status_d, h->hT, h->hQ, h->hX, h->hE, h->hL,
                    h->slA, h->slB, h->rmax, h->cmax, h->ea, h->eb, h->panels,
                    h->ea_panels, h->boff_d, h->bws, h->bplan_d, h->queue_d, h->tauT,
-                   h->blk_tauT, h->pW};
+                   h->blk_tauT, h->pW, h->Rd, h->seg_ey};
     for (void *p : dev)
         if (p) cudaFree(p);
     for (auto &t : h->live) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
@@ -806,6 +816,7 @@ evec_status evec_standard(evec_handle h, int64_t n, const double *T, int64_t ldt
     if (nb < 16 || nb > kMaxTile) return EVEC_EINVAL;
     if (n == 0) return EVEC_OK;
     if (!T || !X || !scale_exp) return EVEC_EINVAL;
+    const bool refine = mode == EVEC_SPLIT && opt && opt->refine;
     DeviceGuard g(h->device);
     if (!g.ok) return EVEC_ECUDA;
 
@@ -833,6 +844,10 @@ evec_status evec_standard(evec_handle h, int64_t n, const double *T, int64_t ldt
     EVEC_TRY(grow_device(&h->seg_nu, &h->segn_cap, segs));
     EVEC_TRY(grow_device(&h->tau, &h->tau_cap, (size_t)N * (size_t)N));
     EVEC_TRY(grow_device(&h->blk_tau, &h->blk_tau_cap, HP.blk_start.size()));
+    if (refine) {
+        EVEC_TRY(grow_device(&h->Rd, &h->Rd_cap, (size_t)n * (size_t)m));
+        EVEC_TRY(grow_device(&h->seg_ey, &h->seg_ey_cap, segs));
+    }
 
     if (Q && mode == EVEC_SPLIT) {   // all split workspace is sized before the first launch
         const int Mp = split_pad_m((int)n), Np = split_pad_n((int)m), Kp = split_pad_k((int)n);
@@ -867,11 +882,14 @@ evec_status evec_standard(evec_handle h, int64_t n, const double *T, int64_t ldt
         });
         EVEC_CUDA(ce);
     }
+    // the tiled robust solve over Y (rhs: Y holds a right-hand side with
+    // its segments initialised, no own blocks are placed)
+    auto sweep = [&](double *Y, int64_t ldy, bool rhs) -> evec_status {
     for (int s = N - 1; s >= 0; s--) {
         timed(h, EVEC_K_DIAG_SOLVE, [&] {
             return launch_diag_solve(s, T, ldt, dp, HP.tile_start.data(), HP.tile_real.data(),
-                              HP.tile_cplx.data(), h->tau,
-                              h->blk_tau, Y, ldy, h->seg_e, h->seg_nu, h->seg_dx, h->seg_dy, st);
+                              HP.tile_cplx.data(), h->tau, h->blk_tau, Y, ldy, h->seg_e,
+                              h->seg_nu, h->seg_dx, h->seg_dy, st, nullptr, rhs);
         });
         if (s > 0 && HP.tile_col[s] < m) {
             if (mode == EVEC_SPLIT) {
@@ -903,8 +921,30 @@ evec_status evec_standard(evec_handle h, int64_t n, const double *T, int64_t ldt
             }
         }
     }
+    return EVEC_OK;
+    };
+    EVEC_TRY(sweep(Y, ldy, false));
+    if (refine) {   // residual-correction sweep on the solved segments
+        double *D = h->Rd;
+        const int64_t ldd = n;
+        EVEC_CUDA(cudaMemcpyAsync(h->seg_ey, h->seg_e, segs * sizeof(int32_t),
+                                  cudaMemcpyDeviceToDevice, st));
+        timed(h, EVEC_K_REFINE, [&] {
+            launch_residual(T, ldt, dp, N, HP.max_tile, Y, ldy, h->seg_ey, h->row_tile_d, D,
+                            ldd, st);
+            launch_rhs_init(dp, D, ldd, h->seg_nu, st);
+            return 2;
+        });
+        EVEC_TRY(sweep(D, ldd, true));
+        timed(h, EVEC_K_REFINE, [&] {
+            // corrections up to 2^(20 - 7 slices) of the column: the split
+            // error with up to 2^20 of growth through the solve
+            launch_refine_combine(dp, Y, ldy, h->seg_ey, D, ldd, h->seg_e, 20 - 7 * slices, st);
+            return 1;
+        });
+    }
     timed(h, EVEC_K_FINALIZE, [&] {
-        launch_finalize(dp, Y, ldy, h->seg_e, scale_exp, st);
+        launch_finalize(dp, Y, ldy, refine ? h->seg_ey : h->seg_e, scale_exp, st);
         return 1;
     });
     if (Q && mode == EVEC_SPLIT) {

@@ -45,7 +45,7 @@
 namespace evec {
 
 
-template <int W, bool GEN>
+template <int W, bool GEN, bool RHS>
 __global__ void __launch_bounds__(32 * W)
     k_diag_solve(int s, int nreal_ctas, const double *__restrict__ T, int64_t ldt, Plan P,
                  const double *__restrict__ tau, const double *__restrict__ blk_tau,
@@ -54,16 +54,16 @@ __global__ void __launch_bounds__(32 * W)
                  int32_t *__restrict__ seg_dy, Pencil pen) {
     extern __shared__ double smem[];
     if ((int)blockIdx.x < nreal_ctas)
-        diag_tile<W, false, GEN>(s, P.tile_real[s] + blockIdx.x * (Lanes<false>::U * W), T, ldt,
+        diag_tile<W, false, GEN, RHS>(s, P.tile_real[s] + blockIdx.x * (Lanes<false>::U * W), T, ldt,
                                  P, tau, blk_tau, Y, ldy, seg_e, seg_nu, seg_dx, seg_dy, smem,
                                  pen);
     else
-        diag_tile<W, true, GEN>(s, P.tile_cplx[s] + (blockIdx.x - nreal_ctas) * (Lanes<true>::U * W),
+        diag_tile<W, true, GEN, RHS>(s, P.tile_cplx[s] + (blockIdx.x - nreal_ctas) * (Lanes<true>::U * W),
                                 T, ldt, P, tau, blk_tau, Y, ldy, seg_e, seg_nu, seg_dx, seg_dy,
                                 smem, pen);
 }
 
-template <int W, bool GEN>
+template <int W, bool GEN, bool RHS>
 static int launch_w(int s, int ts, int nr, int nc, const double *T, int64_t ldt, const Plan &p,
                     const double *tau, const double *blk_tau, double *Y, int64_t ldy,
                     int32_t *seg_e, double *seg_nu, int32_t *seg_dx, int32_t *seg_dy,
@@ -72,35 +72,41 @@ static int launch_w(int s, int ts, int nr, int nc, const double *T, int64_t ldt,
     const int rct = (nr + ur - 1) / ur;
     const int cct = (nc + uc - 1) / uc;
     if (rct + cct == 0) return 0;
-    cudaFuncSetAttribute(k_diag_solve<W, GEN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_diag_solve<W, GEN, RHS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)diag_smem<W, GEN>(W == 4 ? 64 : kMaxTile));
     // two CTAs per SM (about 82 KB each for 64-row tiles; pencils: one)
-    cudaFuncSetAttribute(k_diag_solve<W, GEN>, cudaFuncAttributePreferredSharedMemoryCarveout,
+    cudaFuncSetAttribute(k_diag_solve<W, GEN, RHS>, cudaFuncAttributePreferredSharedMemoryCarveout,
                          cudaSharedmemCarveoutMaxShared);
-    k_diag_solve<W, GEN><<<rct + cct, 32 * W, diag_smem<W, GEN>(ts), st>>>(
+    k_diag_solve<W, GEN, RHS><<<rct + cct, 32 * W, diag_smem<W, GEN>(ts), st>>>(
         s, rct, T, ldt, p, tau, blk_tau, Y, ldy, seg_e, seg_nu, seg_dx, seg_dy, pen);
     return 1;
 }
 
 // Returns the number of kernels launched (0 when no column is active).
 // pen: the pencil's second matrix (tiles of at most 64 rows), or null.
+// rhs: solve from the right-hand side already in Y (standard problem).
 int launch_diag_solve(int s, const double *T, int64_t ldt, const Plan &p,
                       const int32_t *tile_start_h, const int32_t *tile_real_h,
                       const int32_t *tile_cplx_h, const double *tau, const double *blk_tau,
                       double *Y, int64_t ldy, int32_t *seg_e, double *seg_nu, int32_t *seg_dx,
-                      int32_t *seg_dy, cudaStream_t st, const Pencil *pen) {
+                      int32_t *seg_dy, cudaStream_t st, const Pencil *pen, bool rhs) {
     const int ts = tile_start_h[s + 1] - tile_start_h[s];
     const int nr = p.nreal - tile_real_h[s];
     const int nc = p.ncplx - tile_cplx_h[s];
     if (pen)
-        return launch_w<4, true>(s, ts, nr, nc, T, ldt, p, tau, blk_tau, Y, ldy, seg_e, seg_nu,
-                                 seg_dx, seg_dy, *pen, st);
+        return launch_w<4, true, false>(s, ts, nr, nc, T, ldt, p, tau, blk_tau, Y, ldy, seg_e,
+                                        seg_nu, seg_dx, seg_dy, *pen, st);
     // four warps share a tile of up to 64 rows; two for larger tiles
+    if (rhs)
+        return ts <= 64 ? launch_w<4, false, true>(s, ts, nr, nc, T, ldt, p, tau, blk_tau, Y, ldy,
+                                                   seg_e, seg_nu, seg_dx, seg_dy, Pencil(), st)
+                        : launch_w<2, false, true>(s, ts, nr, nc, T, ldt, p, tau, blk_tau, Y, ldy,
+                                                   seg_e, seg_nu, seg_dx, seg_dy, Pencil(), st);
     if (ts <= 64)
-        return launch_w<4, false>(s, ts, nr, nc, T, ldt, p, tau, blk_tau, Y, ldy, seg_e, seg_nu,
-                                  seg_dx, seg_dy, Pencil(), st);
-    return launch_w<2, false>(s, ts, nr, nc, T, ldt, p, tau, blk_tau, Y, ldy, seg_e, seg_nu,
-                              seg_dx, seg_dy, Pencil(), st);
+        return launch_w<4, false, false>(s, ts, nr, nc, T, ldt, p, tau, blk_tau, Y, ldy, seg_e,
+                                         seg_nu, seg_dx, seg_dy, Pencil(), st);
+    return launch_w<2, false, false>(s, ts, nr, nc, T, ldt, p, tau, blk_tau, Y, ldy, seg_e,
+                                     seg_nu, seg_dx, seg_dy, Pencil(), st);
 }
 
 }  // namespace evec

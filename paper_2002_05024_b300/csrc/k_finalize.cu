@@ -64,7 +64,9 @@ __global__ void __launch_bounds__(kWarps * 32)
     int t = INT32_MIN;
 #pragma unroll
     for (int w = 0; w < kWarps; w++) t = max(t, sbest[w]);
-    // the own block is never zero, so t is set
+    // an eigenvector's own block is never zero; a correction (residual
+    // sweep) can be: then every entry is zero and any t will do
+    if (t == INT32_MIN) t = 0;
 
     // pass 2: one exact scaling per entry
     for (int r = warp; r <= c; r += kWarps) {
@@ -121,6 +123,124 @@ __global__ void __launch_bounds__(kWarps * 32)
         scale_exp[col] -= t2;
         if (cplx) scale_exp[col + 1] -= t2;
     }
+}
+
+// Right-hand side of the correction solve: the residual R holds, per
+// segment, -(T - lambda I) y in that segment's own scale 2^e_r (the
+// exponents of the solve stay in seg_e); its segment maxima start seg_nu.
+// One CTA per unit.
+__global__ void __launch_bounds__(kWarps * 32)
+    k_rhs_init(Plan P, const double *__restrict__ R, int64_t ldr, double *__restrict__ seg_nu) {
+    const int u = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t m = P.m;
+    const int col = P.unit_col[u];
+    const bool cplx = P.unit_lam[2 * u + 1] != 0.0;
+    const int c = P.unit_tile[u];
+    for (int r = warp; r <= c; r += kWarps) {
+        const int a = P.tile_start[r], b = P.tile_start[r + 1];
+        double mr = 0.0, mi = 0.0;
+        for (int i = a + lane; i < b; i += 32) {
+            mr = fmax(mr, fabs(R[i + col * ldr]));
+            if (cplx) mi = fmax(mi, fabs(R[i + (col + 1) * ldr]));
+        }
+        mr = warp_max(mr);
+        mi = warp_max(mi);
+        if (lane == 0) {
+            seg_nu[(int64_t)r * m + col] = mr;
+            if (cplx) seg_nu[(int64_t)r * m + col + 1] = mi;
+        }
+    }
+}
+
+// y <- y + d, segment by segment: y_r = Y_r 2^-ey_r, d_r = D_r 2^-ed_r, so
+// Y_r <- Y_r + D_r 2^(ey_r - ed_r) (exact power-of-two scaling, one FP64
+// addition per entry), the exponents of y unchanged.  With
+//   t_y = max_r floor(log2 |Y_r|) - ey_r,  t_d = the same for D,
+// the correction is taken only if |d| / |y| < 2^(t_d + 1 - t_y) stays at or
+// below 2^max_rel and no scaled segment of D reaches 2^1000.  The caller
+// sets max_rel from the split error (products carry ~2^(-7 slices) of their
+// row / column maxima, grown through the solve): a larger correction is not
+// that error but the FP64 rounding of the residual amplified by
+// (T - lambda I)^-1 (an ill-conditioned column, clustered eigenvalues), and
+// there the unrefined column is the better one.  One CTA per unit.
+__global__ void __launch_bounds__(kWarps * 32)
+    k_refine_combine(Plan P, double *__restrict__ Y, int64_t ldy,
+                     const int32_t *__restrict__ ey, const double *__restrict__ D, int64_t ldd,
+                     const int32_t *__restrict__ ed, int max_rel) {
+    const int u = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t m = P.m;
+    const int col = P.unit_col[u];
+    const bool cplx = P.unit_lam[2 * u + 1] != 0.0;
+    const int c = P.unit_tile[u];
+    const int kb = P.unit_blk[u];
+    const int pend = P.blk_start[kb];   // rows above the block; the block is fixed
+    __shared__ int sty[kWarps], std_[kWarps], sover[kWarps];
+    int ty = INT32_MIN, td = INT32_MIN, over = 0;   // over: too large or not finite
+    for (int r = warp; r <= c; r += kWarps) {
+        const int a = P.tile_start[r];
+        const int b = min(P.tile_start[r + 1], P.blk_start[kb] + P.blk_size[kb]);
+        double my = 0.0, md = 0.0;
+        for (int i = a + lane; i < b; i += 32) {
+            double vy = fabs(Y[i + col * ldy]), vd = fabs(D[i + col * ldd]);
+            if (cplx) {
+                vy += fabs(Y[i + (col + 1) * ldy]);
+                vd += fabs(D[i + (col + 1) * ldd]);
+            }
+            my = fmax(my, vy);
+            md = fmax(md, vd);
+            if (!isfinite(vd)) over = 1;
+        }
+        my = warp_max(my);
+        md = warp_max(md);
+        const int64_t at = (int64_t)r * m + col;
+        if (my > 0.0) ty = max(ty, ilog2_abs(my) - ey[at]);
+        if (md > 0.0) {
+            td = max(td, ilog2_abs(md) - ed[at]);
+            if (ilog2_abs(md) + ey[at] - ed[at] >= 1000) over = 1;
+        }
+    }
+    ty = warp_imax(ty);
+    td = warp_imax(td);
+    over = warp_imax(over);
+    if (lane == 0) {
+        sty[warp] = ty;
+        std_[warp] = td;
+        sover[warp] = over;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int w = 0; w < kWarps; w++) {
+        ty = max(ty, sty[w]);
+        td = max(td, std_[w]);
+        over |= sover[w];
+    }
+    // no correction (td unset), or one too large to be the split error
+    if (td == INT32_MIN || over || ty == INT32_MIN || td + 1 - ty > max_rel) return;
+    for (int r = warp; r <= c; r += kWarps) {
+        const int a = P.tile_start[r];
+        const int b = min(P.tile_start[r + 1], pend);
+        const int64_t at = (int64_t)r * m + col;
+        const int k = ey[at] - ed[at];
+        for (int i = a + lane; i < b; i += 32) {
+            Y[i + col * ldy] += scale2(D[i + col * ldd], k);
+            if (cplx) Y[i + (col + 1) * ldy] += scale2(D[i + (col + 1) * ldd], k);
+        }
+    }
+}
+
+void launch_rhs_init(const Plan &p, const double *R, int64_t ldr, double *seg_nu,
+                     cudaStream_t st) {
+    if (p.nunits <= 0) return;
+    k_rhs_init<<<p.nunits, kWarps * 32, 0, st>>>(p, R, ldr, seg_nu);
+}
+
+void launch_refine_combine(const Plan &p, double *Y, int64_t ldy, const int32_t *ey,
+                           const double *D, int64_t ldd, const int32_t *ed, int max_rel,
+                           cudaStream_t st) {
+    if (p.nunits <= 0) return;
+    k_refine_combine<<<p.nunits, kWarps * 32, 0, st>>>(p, Y, ldy, ey, D, ldd, ed, max_rel);
 }
 
 void launch_finalize(const Plan &p, double *Y, int64_t ldy, const int32_t *seg_e,

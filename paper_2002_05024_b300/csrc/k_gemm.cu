@@ -233,6 +233,180 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
+// Residual of the solved segments (the residual-correction sweep), before
+// the consolidation: segment r of column j holds y_r = Y_r 2^-e_r, and the
+// exponents never increase going up a column (e_r <= e_s for r < s: every
+// decision takes a = min(e_r, e_s) and only scales down).  In segment r's
+// own scale
+//   R_r = -[(T_rr - lambda I) Y_r + sum_{s > r} T_rs (2^(e_r - e_s) Y_s)],
+// every factor 2^(e_r - e_s) <= 1, so nothing overflows and no row loses
+// the precision that a single exponent per column (the canonical form,
+// which flushes a column with 2^1000+ of growth to zero near its block)
+// would take away.  One CTA per (column block of 64, row tile r); row tile
+// r is one tile, so one exponent per column; K runs from the tile's first
+// row to the last column's block.  Rows at or below column j's block get
+// 0.  The diagonal is left out of the product and applied as
+// (t_ii - a) Y_i, the shifted entry the backsubstitution itself divides by:
+// t_ii Y_i and a Y_i separately would cancel and leave u |Y_i| of rounding
+// in place of u |t_ii - a| |Y_i|.  For a pair (Re, Im) of lambda = a + i w:
+// ((T - lambda I) y)_re = (T - a) y_re + w y_im,
+// ((T - lambda I) y)_im = (T - a) y_im - w y_re.
+template <int BM>
+__global__ void __launch_bounds__(kThreads)
+    k_residual(const double *__restrict__ T, int64_t ldt, Plan P, const double *__restrict__ Y,
+               int64_t ldy, const int32_t *__restrict__ seg_e,
+               const int32_t *__restrict__ row_tile, double *__restrict__ R, int64_t ldr) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    GemmSmem<BM> &sm = *reinterpret_cast<GemmSmem<BM> *>(smraw);
+    __shared__ int s_bend[kBN], s_er[kBN];
+    constexpr int MI = BM / 16;
+    constexpr int A_PER = BM * kBK / kThreads;
+    constexpr int B_PER = kBK * kBN / kThreads;
+    const int64_t m = P.m;
+    const int64_t nblk_cols = (m + kBN - 1) / kBN;
+    const int64_t j0 = (nblk_cols - 1 - blockIdx.x) * kBN;   // heaviest blocks first
+    const int ncols = (int)min((int64_t)kBN, m - j0);
+    const int r = blockIdx.y;
+    const int i0 = P.tile_start[r];
+    const int rows = P.tile_start[r + 1] - i0;
+    const int tid = threadIdx.x;
+    if (tid < kBN) {
+        int be = 0, er = 0;
+        if (tid < ncols) {
+            const int u = P.col_unit[j0 + tid];
+            const int kb = P.unit_blk[u];
+            be = P.blk_start[kb] + P.blk_size[kb];
+            if (r <= P.unit_tile[u]) er = seg_e[(int64_t)r * m + j0 + tid];
+        }
+        s_bend[tid] = be;
+        s_er[tid] = er;
+    }
+    __syncthreads();
+    const int K = s_bend[ncols - 1];   // block ends grow with the column
+    double acc[MI][4];
+#pragma unroll
+    for (int i = 0; i < MI; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) acc[i][j] = 0.0;
+
+    if (i0 < K) {
+        const double *A = T + i0 + (int64_t)i0 * ldt;
+        const int KL = K - i0;
+        double ra[A_PER], rb[B_PER];
+        // A(i, k) = T(i0 + i, i0 + k) on and above the subdiagonal, diagonal
+        // excluded; B(k, j) = Y(i0 + k, j0 + j) 2^(e_r - e_s(k)) above the
+        // column's block end, else 0
+        auto load = [&](int kb) {
+#pragma unroll
+            for (int t = 0; t < A_PER; t++) {
+                const int e = tid + kThreads * t;
+                const int i = e % BM, k = kb + e / BM;
+                ra[t] = (i < rows && k < KL && k + 1 >= i && k != i)
+                            ? A[i + (int64_t)k * ldt]
+                            : 0.0;
+            }
+#pragma unroll
+            for (int t = 0; t < B_PER; t++) {
+                const int e = tid + kThreads * t;
+                const int k = kb + e % kBK, j = e / kBK;
+                const int gk = i0 + k;
+                double v = 0.0;
+                if (j < ncols && gk < s_bend[j]) {
+                    v = Y[gk + (j0 + j) * ldy];
+                    const int es = seg_e[(int64_t)row_tile[gk] * m + j0 + j];
+                    v = scale2(v, s_er[j] - es);
+                }
+                rb[t] = v;
+            }
+        };
+        auto store = [&](int buf) {
+#pragma unroll
+            for (int t = 0; t < A_PER; t++) {
+                const int e = tid + kThreads * t;
+                sm.A[buf][e / BM][e % BM] = ra[t];
+            }
+#pragma unroll
+            for (int t = 0; t < B_PER; t++) {
+                const int e = tid + kThreads * t;
+                sm.B[buf][e % kBK][e / kBK] = rb[t];
+            }
+        };
+        const int tx = tid & 15, ty = tid >> 4;
+        load(0);
+        store(0);
+        __syncthreads();
+        int buf = 0;
+        for (int kb = 0; kb < KL; kb += kBK) {
+            const bool more = kb + kBK < KL;
+            if (more) load(kb + kBK);
+#pragma unroll
+            for (int k = 0; k < kBK; k++) {
+                double a[MI], b[4];
+#pragma unroll
+                for (int i = 0; i < MI; i++) a[i] = sm.A[buf][k][ty + 16 * i];
+#pragma unroll
+                for (int j = 0; j < 4; j++) b[j] = sm.B[buf][k][tx + 16 * j];
+#pragma unroll
+                for (int i = 0; i < MI; i++)
+#pragma unroll
+                    for (int j = 0; j < 4; j++) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+            }
+            if (more) {
+                store(buf ^ 1);
+                __syncthreads();
+                buf ^= 1;
+            }
+        }
+    }
+    const int tx = tid & 15, ty = tid >> 4;
+#pragma unroll
+    for (int jj = 0; jj < 4; jj++) {
+        const int jl = tx + 16 * jj;
+        if (jl >= ncols) continue;
+        const int64_t j = j0 + jl;
+        const int u = P.col_unit[j];
+        const int pj = P.blk_start[P.unit_blk[u]];
+        const double lr = P.unit_lam[2 * u], li = P.unit_lam[2 * u + 1];
+        const bool re = j == P.unit_col[u];
+        const double *y = Y + j * ldy;
+        const double *yp = Y + (re ? j + 1 : j - 1) * ldy;   // the pair's other column
+        double *c = R + j * ldr;
+#pragma unroll
+        for (int i = 0; i < MI; i++) {
+            const int row = ty + 16 * i;
+            if (row >= rows) continue;
+            const int64_t gi = i0 + row;
+            double v = 0.0;
+            if (gi < pj) {   // same tile: Y_i is already in this scale
+                v = -fma(T[gi + gi * ldt] - lr, y[gi], acc[i][jj]);
+                if (li != 0.0) v = re ? fma(-li, yp[gi], v) : fma(li, yp[gi], v);
+            }
+            c[gi] = v;
+        }
+    }
+}
+
+template <int BM>
+static void launch_residual_bm(const double *T, int64_t ldt, const Plan &p, int ntiles,
+                               const double *Y, int64_t ldy, const int32_t *seg_e,
+                               const int32_t *row_tile, double *R, int64_t ldr, cudaStream_t st) {
+    cudaFuncSetAttribute(k_residual<BM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(GemmSmem<BM>));
+    dim3 grid((unsigned)((p.m + kBN - 1) / kBN), (unsigned)ntiles);
+    k_residual<BM><<<grid, kThreads, sizeof(GemmSmem<BM>), st>>>(T, ldt, p, Y, ldy, seg_e,
+                                                                 row_tile, R, ldr);
+}
+
+void launch_residual(const double *T, int64_t ldt, const Plan &p, int ntiles, int max_tile,
+                     const double *Y, int64_t ldy, const int32_t *seg_e,
+                     const int32_t *row_tile, double *R, int64_t ldr, cudaStream_t st) {
+    if (p.m <= 0 || ntiles <= 0) return;
+    if (max_tile <= 64)
+        launch_residual_bm<64>(T, ldt, p, ntiles, Y, ldy, seg_e, row_tile, R, ldr, st);
+    else
+        launch_residual_bm<128>(T, ldt, p, ntiles, Y, ldy, seg_e, row_tile, R, ldr, st);
+}
+
 // W = [beta X_s; -(alpha X_s)] for the active columns of step s (pencils):
 // column c of unit u (alpha = ar + i ai, beta) and its pair partner give
 // (alpha x)_re = ar xr - ai xi, (alpha x)_im = ar xi + ai xr.

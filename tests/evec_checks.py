@@ -179,6 +179,53 @@ def mp_canonical(y, pair):
     return xr, xi, -t
 
 
+# ---------------------------------------------------------------------------
+# Extended-precision reference for large n (numpy longdouble: a 64-bit
+# significand, 11 bits beyond FP64, and a 15-bit exponent, so an eigenvector
+# growing by up to 2^16000 stays in range with no scaling).  The same
+# textbook backsubstitution as mp_eigvec, vectorised row by row, for a real
+# eigenvalue (a 1x1 block at row p, y_p = 1).
+# ---------------------------------------------------------------------------
+
+def longdouble_is_extended():
+    return np.finfo(np.longdouble).nmant >= 63 and np.finfo(np.longdouble).maxexp >= 16384
+
+
+def ld_real_eigvec(T, blocks, p):
+    """y[0 : p + 1] of the eigenvalue T[p, p]; blocks = [(row, size)] of T."""
+    LD = np.longdouble
+    lam = LD(T[p, p])
+    TL = np.asarray(T[:p + 1, :p + 1], dtype=LD)
+    y = np.zeros(p + 1, LD)
+    y[p] = 1
+    for q, sz in reversed([b for b in blocks if b[0] < p]):
+        if sz == 1:
+            y[q] = -(TL[q, q + 1:] @ y[q + 1:]) / (TL[q, q] - lam)
+        else:
+            r0 = -(TL[q, q + 2:] @ y[q + 2:])
+            r1 = -(TL[q + 1, q + 2:] @ y[q + 2:])
+            a, b = TL[q, q] - lam, TL[q, q + 1]
+            c, d = TL[q + 1, q], TL[q + 1, q + 1] - lam
+            det = a * d - b * c
+            y[q] = (d * r0 - b * r1) / det
+            y[q + 1] = (a * r1 - c * r0) / det
+    return y
+
+
+def extended_errors(yref, x, e):
+    """(direction error, error with the scale) of the canonical column x with
+    exponent e (true vector x 2^-e) against the extended reference yref:
+    the first after scaling x onto yref at yref's largest entry, the second
+    as returned; both max-norm, relative to max |yref|."""
+    LD = np.longdouble
+    x = np.asarray(x[:len(yref)], dtype=LD)
+    den = np.max(np.abs(yref))
+    k = int(np.argmax(np.abs(yref)))
+    direction = float(np.max(np.abs(yref - x * (yref[k] / x[k]))) / den)
+    scaled = float(np.max(np.abs(yref - np.ldexp(x, -int(e)))) / den)
+    return direction, scaled
+
+
 def ulp_scale_ok(e, lo=-(2 ** 31) + 1, hi=2 ** 31 - 1):
     return all(lo <= int(v) <= hi for v in e)
 

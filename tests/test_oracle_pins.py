@@ -16,7 +16,8 @@ import pytest
 import oracle
 import workloads
 from evec_checks import (U, canonical_norms, column_groups, compare_canonical,
-                         complex_columns, mp_canonical, mp_eigvec,
+                         complex_columns, extended_errors, ld_real_eigvec,
+                         longdouble_is_extended, mp_canonical, mp_eigvec,
                          standard_residuals)
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "hand_examples.json")
@@ -287,6 +288,55 @@ def test_mpmath_adversarial_small():
     _, bad = oracle.naive_standard(T)
     assert bad > 0
     _mp_compare(T, blocks, X, e, li, tol=1e-4)
+
+
+def _ld_to_mpf(v):
+    # exact: a longdouble is m 2^ex with a 64-bit integer significand
+    import mpmath as mp
+    m, ex = np.frexp(v)
+    return mp.mpf(int(np.ldexp(m, 64))) * mp.mpf(2) ** (int(ex) - 64)
+
+
+@pytest.mark.skipif(not longdouble_is_extended(), reason="no extended long double")
+def test_extended_reference_against_mpmath():
+    # the longdouble backsubstitution (the large-n reference) against the
+    # 256-bit one on a config-0 matrix and on a growth witness past 2^1024
+    import mpmath as mp
+    T, blocks = workloads.config0_schur(40, seed=77)
+    rng = np.random.default_rng(8)
+    n = 40
+    A = np.triu(rng.standard_normal((n, n)) * 1e3, 1)
+    A[np.arange(n), np.arange(n)] = 0.5 + (rng.permutation(n) - 20) * 1e-9
+    past_double = False
+    for M, blk in ((T, blocks), (A, [(i, 1) for i in range(n)])):
+        for p, sz in blk:
+            if sz != 1 or p < 5:
+                continue
+            y_mp, _ = mp_eigvec(M, p, 1)
+            y_ld = ld_real_eigvec(M, blk, p)
+            top = max(abs(v) for v in y_mp[:p + 1])
+            past_double |= top > mp.mpf(2) ** 1024
+            for i in range(p + 1):
+                assert abs(y_mp[i].real - _ld_to_mpf(y_ld[i])) <= mp.mpf(1e-15) * top, (p, i)
+    assert past_double
+
+
+@pytest.mark.skipif(not longdouble_is_extended(), reason="no extended long double")
+def test_oracle_against_extended_reference():
+    # n = 600 config-0: every real column of the oracle agrees with the
+    # extended-precision backsubstitution in direction to 1e-13 and, with
+    # its exponent, to 1e-10
+    n = 600
+    T, blocks = workloads.config0_schur(n, seed=workloads.SEED_BASE + 9)
+    X, e, lr, li = oracle.standard(T)
+    col = 0
+    worst = (0.0, 0.0)
+    for p, sz in blocks:
+        if sz == 1 and p % 7 == 0:
+            d, s = extended_errors(ld_real_eigvec(T, blocks, p), X[:, col], e[col])
+            worst = (max(worst[0], d), max(worst[1], s))
+        col += sz
+    assert worst[0] <= 1e-13 and worst[1] <= 1e-10, worst
 
 
 def test_mpmath_pairs_dense():
