@@ -58,6 +58,8 @@ def parse_args():
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--mode", choices=["fp64", "split"], default="split")
     ap.add_argument("--slices", type=int, default=0)
+    ap.add_argument("--refine", action="store_true",
+                    help="split mode: one FP64 residual-correction sweep after the solve")
     ap.add_argument("--cpu-sample", type=int, default=4096,
                     help="columns of the CPU-oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -75,16 +77,21 @@ def workload(n):
     return T, blocks, Q
 
 
-def flop_counts(n, blocks, tile_start, with_q=True):
+def flop_counts(n, blocks, tile_start, with_q=True, res=None):
     """Algorithmic FP64 flops: total per the method's definition, and the
     parts done by the tile-update GEMMs and by the back-transformation (the
-    diagonal-tile solves do the rest of the substitution: total - upd - bt)."""
+    diagonal-tile solves do the rest of the substitution: total - upd - bt).
+    res (a list): receives the flops of the residual -(T - lambda I) y of the
+    correction sweep, 2 (p (p + size) - p (p - 1) / 2) per column of a block
+    at row p (rows above the block, T quasi-triangular)."""
     tile_start = np.asarray(tile_start)
     total = 0.0
     upd = 0.0
     bt = 0.0
+    r = 0.0
     for p, sz in blocks:
         k = p
+        r += sz * 2.0 * (k * (k + sz) - k * (k - 1) / 2.0)
         for _ in range(sz):
             total += k * k + (2.0 * n * (k + sz) if with_q else 0.0)
             bt += 2.0 * n * (k + sz) if with_q else 0.0
@@ -94,13 +101,17 @@ def flop_counts(n, blocks, tile_start, with_q=True):
             upd += 2.0 * t0c * (p + sz - t0c)
             for s in range(1, c):
                 upd += 2.0 * tile_start[s] * (tile_start[s + 1] - tile_start[s])
+    if res is not None:
+        res.append(r)
     return total, upd, bt
 
 
 # kernel class -> source files whose content a stored DRAM-traffic figure
 # belongs to (per mode)
 KERNEL_SOURCES = {
-    ("diag_solve", "fp64"): ["k_diag_solve.cu"], ("diag_solve", "split"): ["k_diag_solve.cu"],
+    ("diag_solve", "fp64"): ["k_diag_solve.cu", "diag_tile.cuh"],
+    ("diag_solve", "split"): ["k_diag_solve.cu", "diag_tile.cuh"],
+    ("refine", "split"): ["k_gemm.cu", "k_finalize.cu"],
     ("tile_update", "fp64"): ["k_gemm.cu"],
     ("tile_update", "split"): ["k_split_update.cu", "k_split.cu", "split_common.cuh"],
     ("backtransform", "fp64"): ["k_gemm.cu"],
@@ -132,22 +143,26 @@ def stored_traffic(kernel, mode, n, tile):
     return rec.get("dram_bytes_per_launch")
 
 
-def rooflines(prof, steps, mode, slices, F_diag, F_upd, F_bt, peaks, n, tile):
+def rooflines(prof, steps, mode, slices, F_diag, F_upd, F_bt, peaks, n, tile, F_res=0.0,
+              sweeps=1):
     """Per kernel class: algorithmic work per step / event-timed kernel time
     per step against the unit that bounds it.  Diagonal solves and FP64-mode
     GEMMs: FP64 flops on the FP64 pipe ("alu"; peak from the measured DFMA
     rate x SMs x max clock).  Split-mode GEMMs: the S (S + 1) / 2 BF16 slice
     products the method needs per FP64 multiply-add, on the tensor cores
     ("tensor"; peak = the measured sustained cuBLAS BF16 rate, as these
-    kernels run inside a long step)."""
+    kernels run inside a long step).  With the residual-correction sweep
+    (sweeps = 2) the solve kernels run twice per step, and "refine" is the
+    FP64 residual product (F_res) with its two small companions."""
     sm_max = float(peaks.get("sm_max_mhz", 2032.0))
     fp64_peak = N_SMS * FP64_FLOP_PER_CLK_PER_SM * sm_max * 1e6 / 1e12
     bf16 = peaks.get("bf16_tflops_sustained")
     bf16_src = "of measured (sustained cuBLAS BF16)" if bf16 else "of fallback"
     bf16 = float(bf16 or 1400.0)
     pairs = slices * (slices + 1) // 2
-    work = {"diag_solve": (F_diag, False), "tile_update": (F_upd, mode == "split"),
-            "backtransform": (F_bt, mode == "split")}
+    work = {"diag_solve": (sweeps * F_diag, False),
+            "tile_update": (sweeps * F_upd, mode == "split"),
+            "backtransform": (F_bt, mode == "split"), "refine": (F_res, False)}
     out = {}
     for k, (ms, nl) in prof.items():
         if k not in work or ms <= 0 or nl <= 0:
@@ -347,8 +362,11 @@ def run_ours(args, rank, world, local_rank):
     d = np.ascontiguousarray(np.diagonal(T))
     _, tile_start = ev.plan_query(d, np.ascontiguousarray(np.diagonal(T, -1)),
                                   np.ascontiguousarray(np.diagonal(T, 1)), None, args.tile or 64)
-    F, F_upd, F_bt = flop_counts(n, blocks, tile_start)
+    res = []
+    F, F_upd, F_bt = flop_counts(n, blocks, tile_start, res=res)
     F_diag = max(F - F_upd - F_bt, 0.0)
+    refine = bool(args.refine and args.mode == "split")
+    F_res = res[0] if refine else 0.0
 
     dT = torch.from_numpy(T).to(dev)
     dQ = torch.from_numpy(Q).to(dev)
@@ -360,7 +378,8 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.current_stream(dev)
 
     def step():
-        ev.standard(dT, dQ, tile=args.tile, out=out, mode=args.mode, slices=args.slices)
+        ev.standard(dT, dQ, tile=args.tile, out=out, mode=args.mode, slices=args.slices,
+                    refine=refine)
 
     for _ in range(args.warmup):
         step()
@@ -406,7 +425,8 @@ def run_ours(args, rank, world, local_rank):
     peaks = measured_peaks()
     slices = (args.slices or 8) if args.mode == "split" else 0
     tile = args.tile or 64
-    roofs = rooflines(prof, args.steps, args.mode, slices, F_diag, F_upd, F_bt, peaks, n, tile)
+    roofs = rooflines(prof, args.steps, args.mode, slices, F_diag, F_upd, F_bt, peaks, n, tile,
+                      F_res=F_res, sweeps=2 if refine else 1)
     dominant = max(prof.items(), key=lambda kv: kv[1][0])[0]
     roofline = roofs.get(dominant)
     gpu_launches = sum(c for _, c in prof.values())
@@ -423,7 +443,7 @@ def run_ours(args, rank, world, local_rank):
         hE = pin((m,), torch.int32)
         hLr = pin((m,), torch.float64)
         hLi = pin((m,), torch.float64)
-        opts = ev._opts(args.tile, False, args.mode, args.slices)
+        opts = ev._opts(args.tile, False, args.mode, args.slices, refine)
         hh = ev.handle(local_rank)
         P = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
 
@@ -471,9 +491,12 @@ def run_ours(args, rank, world, local_rank):
                                f"all {m} columns, "
                                + ("FP64" if args.mode == "fp64" else
                                   f"split precision ({slices} BF16 slices, FP32 exact "
-                                  "accumulation, FP64 recombination)"),
+                                  "accumulation, FP64 recombination)"
+                                  + (", then one FP64 residual-correction sweep"
+                                     if refine else "")),
                    "n": n, "columns": m, "tile": args.tile or 64, "mode": args.mode,
                    "slices": (args.slices or 8) if args.mode == "split" else None,
+                   "refine": refine,
                    "parallelism": "replicas",
                    "l2": "inputs larger than L2 (T, Q, X 128 MiB each)"},
         "tflops_fp64": tflops,
