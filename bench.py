@@ -519,8 +519,9 @@ def run_batched(args, rank, world, local_rank):
     """The batched workload: --batch independent Schur forms, sizes
     log-uniform in [32, 1024], every 10th clustered-adversarial, 30% of the
     blocks selected, no Q; one evec_batched call per step (persistent
-    launch).  Also times the same batch matrix by matrix through
-    evec_standard ("plain") on the same GPU."""
+    launch; FP64, or --mode split: the updates as BF16 slice products inside
+    the persistent kernel).  Also times the same batch matrix by matrix
+    through evec_standard ("plain", FP64) on the same GPU."""
     import ctypes  # noqa: F401
 
     import torch
@@ -536,8 +537,9 @@ def run_batched(args, rank, world, local_rank):
     sizes, Ts, sels = workloads.batch_inputs(args.batch)
     Tp, ns, offs = ev.pack_batch(Ts, device=local_rank)
     sel = np.concatenate(sels)
-    mode = args.mode if args.mode == "fp64" else "fp64"   # the batched kernel runs FP64
-    out = ev.batched_packed(Tp, ns, offs, sel, tile=args.tile, mode=mode)
+    mode = args.mode
+    slices = (args.slices or 8) if mode == "split" else 0
+    out = ev.batched_packed(Tp, ns, offs, sel, tile=args.tile, mode=mode, slices=args.slices)
     m = out[4]
     cols = int(m.sum())
     F = 0.0
@@ -550,8 +552,26 @@ def run_batched(args, rank, world, local_rank):
                 F += sz * float(i) * float(i)
             i += sz
     for _ in range(args.warmup):
-        ev.batched_packed(Tp, ns, offs, sel, tile=args.tile, mode=mode, out=out)
+        ev.batched_packed(Tp, ns, offs, sel, tile=args.tile, mode=mode, out=out,
+                          slices=args.slices)
     torch.cuda.synchronize(dev)
+    # the update share of F with each matrix's tile (the tuned table)
+    table = ev.tune_table(local_rank, mode)
+    F_upd = 0.0
+    for T, s_ in zip(Ts, sels):
+        n = T.shape[0]
+        c = 0 if n <= 64 else 1 if n <= 128 else 2 if n <= 256 else 3 if n <= 512 else 4
+        nb = args.tile or table[c] or 64
+        blocks, i = [], 0
+        while i < n:
+            sz = 2 if i + 1 < n and T[i + 1, i] != 0.0 else 1
+            if s_[i] or (sz == 2 and s_[i + 1]):
+                blocks.append((i, sz))
+            i += sz
+        _, ts = ev.plan_query(np.ascontiguousarray(np.diagonal(T)),
+                              np.ascontiguousarray(np.diagonal(T, -1)),
+                              np.ascontiguousarray(np.diagonal(T, 1)), None, nb)
+        F_upd += flop_counts(n, blocks, ts, with_q=False)[1]
     h = ev.handle(local_rank)
     h.profile(True)
     h.profile_read()
@@ -563,7 +583,8 @@ def run_batched(args, rank, world, local_rank):
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record(stream)
     for _ in range(args.steps):
-        ev.batched_packed(Tp, ns, offs, sel, tile=args.tile, mode=mode, out=out)
+        ev.batched_packed(Tp, ns, offs, sel, tile=args.tile, mode=mode, out=out,
+                          slices=args.slices)
     t1.record(stream)
     torch.cuda.synchronize(dev)
     if dist:
@@ -597,7 +618,8 @@ def run_batched(args, rank, world, local_rank):
     w0 = time.perf_counter()
     for _ in range(args.steps):
         Tp.copy_(hT, non_blocking=True)
-        ev.batched_packed(Tp, ns, offs, sel, tile=args.tile, mode=mode, out=out)
+        ev.batched_packed(Tp, ns, offs, sel, tile=args.tile, mode=mode, out=out,
+                          slices=args.slices)
         hX.copy_(out[0], non_blocking=True)
         hE.copy_(out[1], non_blocking=True)
         torch.cuda.synchronize(dev)
@@ -611,13 +633,31 @@ def run_batched(args, rank, world, local_rank):
     peaks = measured_peaks()
     fp64_peak = N_SMS * FP64_FLOP_PER_CLK_PER_SM * float(peaks.get("sm_max_mhz", 2032.0)) / 1e6
     kms = prof.get("batched", (0.0, 0))[0] / args.steps
+    launches = prof.get("batched", (0.0, 0))[1] / args.steps
     achieved = F / (kms / 1e3) / 1e12 if kms > 0 else None
-    roofline = {"kernel": "k_batched", "bound": "alu", "achieved": achieved, "peak": fp64_peak,
-                "unit": "TFLOP/s", "frac": achieved / fp64_peak if achieved else None,
-                "traffic": None,
-                "peak_source": "of derived FP64 peak (measured 4 flop/clk/SM x 148 SMs x max "
-                               "SM clock)",
-                "launches_per_step": prof.get("batched", (0.0, 0))[1] / args.steps}
+    fp64_view = {"kernel": "k_batched", "bound": "alu", "achieved": achieved, "peak": fp64_peak,
+                 "unit": "TFLOP/s", "frac": achieved / fp64_peak if achieved else None,
+                 "traffic": None,
+                 "peak_source": "of derived FP64 peak (measured 4 flop/clk/SM x 148 SMs x max "
+                                "SM clock)",
+                 "launches_per_step": launches, "alg_flops_per_launch": F / max(launches, 1)}
+    roofline = fp64_view
+    rooflines = {"fp64": fp64_view}
+    if mode == "split" and kms > 0:
+        # the updates' slice products on the tensor cores (S (S + 1) / 2 per
+        # FP64 multiply-add) against the sustained BF16 rate; the diagonal
+        # solves (F - F_upd) stay on the FP64 pipe inside the same kernel
+        bf16 = float(peaks.get("bf16_tflops_sustained") or 1400.0)
+        pairs = slices * (slices + 1) // 2
+        ach = pairs * F_upd / (kms / 1e3) / 1e12
+        roofline = {"kernel": "k_batched (split)", "bound": "tensor", "achieved": ach,
+                    "peak": bf16, "unit": "TFLOP/s", "frac": ach / bf16, "traffic": None,
+                    "peak_source": "of measured (sustained cuBLAS BF16)"
+                    if peaks.get("bf16_tflops_sustained") else "of fallback",
+                    "launches_per_step": launches,
+                    "alg_flops_per_launch": pairs * F_upd / max(launches, 1),
+                    "fp64_flops_of_diagonal_solves_per_launch": (F - F_upd) / max(launches, 1)}
+        rooflines["tensor"] = roofline
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         import oracle
@@ -639,19 +679,23 @@ def run_batched(args, rank, world, local_rank):
         "metric": "eigvec columns/s, batched (robust FP64 eigenvectors, many Schur forms)",
         "value": value, "unit": "columns/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if mode == "fp64" else "bf16 slice products + f64", "data": "synthetic",
         "config": {"workload": f"batch of {args.batch} Schur forms, n log-uniform in [32, 1024] "
                                "(config-0, every 10th clustered adversarial), 30% of blocks "
                                "selected, no Q, one persistent launch per step",
                    "matrices": args.batch, "columns": cols, "tile": args.tile or "tuned",
-                   "tile_table": ev.tune_table(local_rank), "mode": mode,
+                   "tile_table": ev.tune_table(local_rank, mode), "mode": mode,
+                   "slices": slices or None,
                    "parallelism": "replicas",
                    "l2": f"inputs {Tp.numel() * 8 / 2**30:.1f} GiB, larger than L2"},
         "plain_value": plain,
         "plain": "the same batch through evec_standard, one call per matrix (columns/s)",
         "tflops_fp64": F * args.steps / (elapsed / 1e3) / 1e12,
         "flops_per_step": F,
+        "update_flops_per_step": F_upd,
         "roofline": roofline,
+        "rooflines": rooflines,
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
         "gpu_launches": sum(c for _, c in prof.values()),
         "clocks": clocks,

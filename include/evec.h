@@ -244,7 +244,11 @@ evec_status evec_batched_count(evec_handle h, int64_t count, const int64_t *n_ho
  * buffers stay the same.  Outputs packed in matrix order: X_i (n_i x m_i,
  * leading dimension n_i) at X_packed + sum_{k<i} n_k m_k; scale_exp_i and
  * lam_re_i / lam_im_i (m_i each; lam may be NULL) at offset sum_{k<i} m_k.
- * opt->mode: EVEC_FP64 only (EVEC_SPLIT returns EVEC_EINVAL in this mode).
+ * opt->mode: EVEC_FP64, or EVEC_SPLIT (opt->slices digit slices, 2..8;
+ * 0 = 8): the updates of every matrix as BF16 slice products on the tensor
+ * cores inside the same persistent kernel (each CTA holds 256 TMEM columns;
+ * two CTAs per SM); the diagonal solves, decisions and canonical form stay
+ * FP64.  opt->refine is ignored here.
  * opt->tile: 16..64 for every matrix, or 0 = the tile of each matrix's size
  * class from the handle's table, tuned on first use of a class by timing
  * 16, 32 and 64 on up to eight of the batch's matrices of that class.

@@ -397,7 +397,7 @@ def batched_count(T_packed, ns, t_offs, select=None):
 
 
 def batched_packed(T_packed, ns, t_offs, select=None, tile: int = 0, mode: str = "fp64",
-                   check: bool = False, out=None):
+                   check: bool = False, out=None, slices: int = 0):
     """evec_batched on a packed device buffer.  select: concatenated n_i-byte
     masks or None.  Returns (X_packed, scale_exp, lam_re, lam_im, m) with the
     output packing of the C entry point (X_i at sum_{k<i} n_k m_k, leading
@@ -417,7 +417,7 @@ def batched_packed(T_packed, ns, t_offs, select=None, tile: int = 0, mode: str =
         e = torch.empty(int(m.sum()), dtype=torch.int32, device=dev)
         lr = torch.empty(int(m.sum()), dtype=torch.float64, device=dev)
         li = torch.empty(int(m.sum()), dtype=torch.float64, device=dev)
-    opts = _opts(tile, False, mode)
+    opts = _opts(tile, False, mode, slices)
     st = lib().evec_batched(h.ptr, len(ns), _np_ptr(ns), T_packed.data_ptr(), _np_ptr(t_offs),
                             _np_ptr(sel), X.data_ptr(), e.data_ptr(), lr.data_ptr(),
                             li.data_ptr(), ctypes.byref(opts))
@@ -427,7 +427,8 @@ def batched_packed(T_packed, ns, t_offs, select=None, tile: int = 0, mode: str =
     return X, e, lr, li, m
 
 
-def batched(Ts, selects=None, tile: int = 0, mode: str = "fp64", check: bool = True):
+def batched(Ts, selects=None, tile: int = 0, mode: str = "fp64", check: bool = True,
+            slices: int = 0):
     """Eigenvectors of a list of quasi-triangular matrices in one persistent
     launch.  Returns a list of (X_i (n_i, m_i), scale_exp_i, lam_re_i,
     lam_im_i) CUDA tensors, X_i column-major."""
@@ -436,7 +437,7 @@ def batched(Ts, selects=None, tile: int = 0, mode: str = "fp64", check: bool = T
     if selects is not None:
         sel = np.concatenate([np.ones(n, np.uint8) if s is None else
                               np.ascontiguousarray(s, dtype=np.uint8) for s, n in zip(selects, ns)])
-    X, e, lr, li, m = batched_packed(Tp, ns, offs, sel, tile, mode, check)
+    X, e, lr, li, m = batched_packed(Tp, ns, offs, sel, tile, mode, check, slices=slices)
     out = []
     xo = eo = 0
     for n, mi in zip(ns, m):

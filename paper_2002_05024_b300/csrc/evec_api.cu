@@ -77,7 +77,7 @@ int launch_tile_update_pencil(int s, const double *S, int64_t lds, const double 
                               const int32_t *seg_dx, const int32_t *seg_dy, double *seg_nu,
                               double *W, int64_t ldw, cudaStream_t st);
 cudaError_t launch_batched(const BatchItem *items, int count, int *queue, DevStatus *status,
-                           int nsm, cudaStream_t st);
+                           int nsm, cudaStream_t st, int S);
 void launch_gather_batched(const double *T, const int64_t *t_off, const int64_t *row_off,
                            int count, int64_t total_rows, double *out, cudaStream_t st);
 cudaError_t split_update_step_resident(const SplitUpdateCtx &ctx, int t0, int ts, int prow0,
@@ -1114,7 +1114,7 @@ static evec_status run_batch(evec_handle h, int64_t count, const int64_t *n_host
                              const double *T_packed, const int64_t *t_off_host,
                              const std::vector<int> &idx, const std::vector<HostPlan> &plans,
                              double *X_packed, int32_t *scale_exp_packed, double *lam_re,
-                             double *lam_im, bool use_graph) {
+                             double *lam_im, bool use_graph, int slices) {
     // output offsets (all matrices, matrix order)
     std::vector<int64_t> xo(count), eo(count);
     int64_t xacc = 0, eacc = 0;
@@ -1204,7 +1204,7 @@ static evec_status run_batch(evec_handle h, int64_t count, const int64_t *n_host
         cudaError_t e = cudaMemcpyAsync(h->bplan_d, h->bplan_h, bytes, cudaMemcpyHostToDevice, s2);
         if (e == cudaSuccess) e = cudaMemsetAsync(h->queue_d, 0, sizeof(int), s2);
         if (e == cudaSuccess && nb > 0)
-            e = launch_batched(items_d, nb, h->queue_d, h->status_d, h->nsm, s2);
+            e = launch_batched(items_d, nb, h->queue_d, h->status_d, h->nsm, s2, slices);
         return e;
     };
     if (!use_graph) {
@@ -1220,7 +1220,7 @@ static evec_status run_batch(evec_handle h, int64_t count, const int64_t *n_host
         std::vector<uint64_t> key = {(uint64_t)nb, (uint64_t)bytes, (uint64_t)items_off,
                                      (uint64_t)h->bplan_d, (uint64_t)h->bplan_h,
                                      (uint64_t)h->bws, (uint64_t)h->queue_d,
-                                     (uint64_t)h->status_d};
+                                     (uint64_t)h->status_d, (uint64_t)slices};
         if (!h->bexec || key != h->bkey) {
             if (h->bexec) {
                 cudaGraphExecDestroy(h->bexec);
@@ -1229,7 +1229,7 @@ static evec_status run_batch(evec_handle h, int64_t count, const int64_t *n_host
             if (!h->cap_stream)
                 EVEC_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
             // launch attributes are set outside the capture
-            EVEC_CUDA(launch_batched(nullptr, 0, nullptr, nullptr, h->nsm, h->cap_stream));
+            EVEC_CUDA(launch_batched(nullptr, 0, nullptr, nullptr, h->nsm, h->cap_stream, slices));
             EVEC_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
             cudaError_t e = enqueue(h->cap_stream);
             cudaGraph_t graph = nullptr;
@@ -1267,7 +1267,9 @@ extern "C" evec_status evec_batched(evec_handle h, int64_t count, const int64_t 
         (count > 0 && (!n_host || !t_off_host || !T_packed)))
         return EVEC_EINVAL;
     const int mode = opt ? opt->mode : EVEC_FP64;
-    if (mode != EVEC_FP64) return EVEC_EINVAL;
+    if (mode != EVEC_FP64 && mode != EVEC_SPLIT) return EVEC_EINVAL;
+    const int slices = mode == EVEC_SPLIT ? ((opt && opt->slices) ? opt->slices : 8) : 0;
+    if (mode == EVEC_SPLIT && (slices < 2 || slices > 8)) return EVEC_EINVAL;
     const int tile = opt ? opt->tile : 0;
     if (tile != 0 && (tile < 16 || tile > 64)) return EVEC_EINVAL;
     if (count == 0) return EVEC_OK;
@@ -1305,7 +1307,8 @@ extern "C" evec_status evec_batched(evec_handle h, int64_t count, const int64_t 
                 EVEC_CUDA(cudaEventCreate(&b));
                 cudaEventRecord(a, h->stream);
                 evec_status st = run_batch(h, count, n_host, T_packed, t_off_host, members, tp,
-                                           X_packed, scale_exp_packed, nullptr, nullptr, false);
+                                           X_packed, scale_exp_packed, nullptr, nullptr, false,
+                                           slices);
                 cudaEventRecord(b, h->stream);
                 cudaEventSynchronize(b);
                 float ms = 0.0f;
@@ -1333,7 +1336,7 @@ extern "C" evec_status evec_batched(evec_handle h, int64_t count, const int64_t 
                                    all, plans, &bad));
     }
     EVEC_TRY(run_batch(h, count, n_host, T_packed, t_off_host, all, plans, X_packed,
-                       scale_exp_packed, lam_re_packed, lam_im_packed, true));
+                       scale_exp_packed, lam_re_packed, lam_im_packed, true, slices));
     if (opt && opt->check) return evec_sync(h, nullptr);
     return EVEC_OK;
 }

@@ -11,7 +11,18 @@
 // form.  CTAs never wait on one another; the queue is the only shared state.
 // Matrices of this workload are small (n <= 1024), so one SM per matrix
 // keeps each solve's data in L1/L2 and the device busy across the batch.
+//
+// Split precision (S > 0): the updates run as BF16 digit-slice products on
+// the tensor cores, the same arithmetic as the single-matrix split update
+// (balanced 7-bit digits after power-of-two row / column normalisation,
+// one TMEM accumulator per digit diagonal, FP64 recombination) at CTA
+// scope: per 128-row block of the rows above tile s and 32-column chunk of
+// the active columns, the CTA slices T's rows and X_s's columns straight
+// into shared memory (K-major, 64-byte swizzle), one thread issues the
+// concatenated MMAs, and the 4 warps drain their TMEM lane quarters.  Each
+// CTA holds 256 TMEM columns (8 diagonals x 32 columns); two CTAs per SM.
 #include "diag_tile.cuh"
+#include "split_common.cuh"
 
 namespace evec {
 
@@ -175,6 +186,246 @@ __device__ void cta_tile_update(const BatchItem &B, int s, double *smem) {
     __syncthreads();
 }
 
+// ---------------------------------------------------------------------------
+// split-precision update of step s (S > 0)
+// ---------------------------------------------------------------------------
+constexpr int kBSN = 32;                          // columns per chunk
+constexpr int kBSBoxA = kTM * kTK * 2;            // 8 KB: 128 rows x 32 K (one slice)
+constexpr int kBSBoxB = kBSN * kTK * 2;           // 2 KB: 32 columns x 32 K
+constexpr int kBSSlots = 10;                      // tiles met by 128 rows (tiles >= 15 rows)
+constexpr int kBSTmemCols = kSplitMaxS * kBSN;    // 256
+// dynamic smem of the split update, from a 1024-byte aligned base
+constexpr size_t kBSOffB = (size_t)kSplitMaxS * kBSBoxA;              // 64 KB
+constexpr size_t kBSOffTab = kBSOffB + (size_t)kSplitMaxS * kBSBoxB;  // + 16 KB
+// tables: nu [slots][32] u64, dx / dy [slots][32], ea / rt [128], eb [32]
+constexpr size_t kBSTabBytes =
+    (size_t)kBSSlots * kBSN * 8 + 2 * kBSSlots * kBSN * 4 + 2 * kTM * 4 + kBSN * 4;
+constexpr size_t kBSBytes = 1024 + kBSOffTab + kBSTabBytes;
+
+__device__ __forceinline__ void bsum2_add(float &hi, float &lo, float x) {
+    const float s = hi + x;
+    const float bp = s - hi;
+    lo += (hi - (s - bp)) + (x - bp);
+    hi = s;
+}
+
+// byte offset of element (row, k) (k < 32) in a K-major, 64-byte swizzled box
+// of 64-byte rows: 16-byte chunk c of row r sits at chunk c ^ ((r >> 1) & 3)
+__device__ __forceinline__ int sw64_off(int r, int c) { return r * 64 + ((c ^ ((r >> 1) & 3)) << 4); }
+
+// 8 values -> S slices of 8 BF16 digits each, stored as one 16-byte chunk
+// per slice at dst + p * stride
+__device__ __forceinline__ void slice8_store(const double (&x)[8], int e, int S,
+                                             unsigned char *dst, int stride) {
+    uint32_t w[kSplitMaxS][4];
+#pragma unroll
+    for (int p = 0; p < kSplitMaxS; p++)
+#pragma unroll
+        for (int q = 0; q < 4; q++) w[p][q] = 0u;
+#pragma unroll
+    for (int t = 0; t < 8; t++) {
+        int d[kSplitMaxS];
+#pragma unroll
+        for (int p = 0; p < kSplitMaxS; p++) d[p] = 0;
+        digits7(x[t], e, S, d);
+#pragma unroll
+        for (int p = 0; p < kSplitMaxS; p++) {
+            const uint32_t h = (uint32_t)__bfloat16_as_ushort(digit_bf16(d[p], p));
+            w[p][t >> 1] |= (t & 1) ? (h << 16) : h;
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < kSplitMaxS; p++)
+        if (p < S)
+            *(uint4 *)(dst + (size_t)p * stride) = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
+}
+
+// Y_r <- 2^dy Y_r - T_rs (2^dx X_s) for all r < s, as split products.
+// Returns false if a bounded wait gave up (status->timeout is set).
+__device__ bool cta_split_update(const BatchItem &B, int s, int S, unsigned char *sm,
+                                 uint32_t tmem, uint64_t *bar, uint32_t &phase, int *err) {
+    const Plan &P = B.P;
+    const int64_t m = P.m;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    unsigned char *sA = sm;
+    unsigned char *sB = sm + kBSOffB;
+    unsigned long long *snu = (unsigned long long *)(sm + kBSOffTab);   // [slots][32]
+    int *sdx = (int *)(snu + kBSSlots * kBSN);                           // [slots][32]
+    int *sdy = sdx + kBSSlots * kBSN;
+    int *sea = sdy + kBSSlots * kBSN;                                    // [128]
+    int *srt = sea + kTM;                                                // [128]
+    int *seb = srt + kTM;                                                // [32]
+    const int k0 = P.tile_start[s], K = P.tile_start[s + 1] - k0;
+    const int halves = (K + kTK - 1) / kTK;
+    const int t0 = k0;   // rows above tile s
+    double *Y = B.X;
+    const int64_t ldy = B.ldx;
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTM >> 4) << 24);
+    for (int rb0 = 0; rb0 < t0; rb0 += kTM) {
+        const int rows = min(kTM, t0 - rb0);
+        const int row = rb0 + tid;
+        const bool rv = tid < rows;
+        // row tile and row exponent over the tile's K columns
+        {
+            int r = 0;
+            if (rv) {
+                int lo = 0, hi = s - 1;   // tile_start[lo] <= row < tile_start[hi + 1]
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (P.tile_start[mid] <= row) lo = mid;
+                    else hi = mid - 1;
+                }
+                r = lo;
+            }
+            long long mb = 0;
+            if (rv)
+                for (int k = 0; k < K; k++)
+                    mb = max(mb, abs_bits(B.T[row + (int64_t)(k0 + k) * B.ldt]));
+            srt[tid] = rv ? r : -1;
+            sea[tid] = exp_from_max((unsigned long long)mb);
+        }
+        __syncthreads();
+        const int rfirst = srt[0];
+        const int nslots = srt[rows - 1] - rfirst + 1;
+        const int myslot = rv ? srt[tid] - rfirst : 0;
+        const int er = sea[tid];
+        for (int64_t j0 = P.tile_col[s]; j0 < m; j0 += kBSN) {
+            const int nc = (int)min((int64_t)kBSN, m - j0);
+            // column exponents of X_s and the chunk's tables
+            if (tid < kBSN) {
+                long long mb = 0;
+                if (tid < nc)
+                    for (int k = 0; k < K; k++)
+                        mb = max(mb, abs_bits(Y[(k0 + k) + (j0 + tid) * ldy]));
+                seb[tid] = exp_from_max((unsigned long long)mb);
+            }
+            for (int idx = tid; idx < nslots * kBSN; idx += kBThreads) {
+                const int sl = idx / kBSN, j = idx % kBSN;
+                const int64_t at = (int64_t)(rfirst + sl) * m + j0 + j;
+                sdx[idx] = j < nc ? B.seg_dx[at] : 0;
+                sdy[idx] = j < nc ? B.seg_dy[at] : kFresh;
+                snu[idx] = 0ull;
+            }
+            __syncthreads();
+            for (int h = 0; h < halves; h++) {
+                // A: thread = row, four 8-K chunks; B: thread = (column, chunk)
+                for (int c = 0; c < 4; c++) {
+                    double x[8];
+#pragma unroll
+                    for (int t = 0; t < 8; t++) {
+                        const int k = h * kTK + c * 8 + t;
+                        x[t] = (rv && k < K) ? B.T[row + (int64_t)(k0 + k) * B.ldt] : 0.0;
+                    }
+                    slice8_store(x, er, S, sA + sw64_off(tid, c), kBSBoxA);
+                }
+                {
+                    const int j = tid >> 2, c = tid & 3;
+                    double x[8];
+#pragma unroll
+                    for (int t = 0; t < 8; t++) {
+                        const int k = h * kTK + c * 8 + t;
+                        x[t] = (j < nc && k < K) ? Y[(k0 + k) + (j0 + j) * ldy] : 0.0;
+                    }
+                    slice8_store(x, seb[j], S, sB + sw64_off(j, c), kBSBoxB);
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncthreads();
+                if (tid == 0) {
+                    asm volatile("tcgen05.fence::after_thread_sync;");
+                    // the B slices lie one after another (slice q at rows 32 q):
+                    // A_p against slices 0 .. S-1-p (N = 32 (S - p)) at TMEM
+                    // column 32 p adds A_p B_q to diagonal p + q for every q
+                    for (int kin = 0; kin < 2; kin++) {
+                        const uint64_t bd = desc_sw64(saddr(sB) + kin * 32);
+                        for (int p = 0; p < S; p++) {
+                            const uint32_t id =
+                                idesc | ((uint32_t)(((S - p) * kBSN) >> 3) << 17);
+                            const uint64_t ad = desc_sw64(saddr(sA + p * kBSBoxA) + kin * 32);
+                            const int acc = (h == 0 && kin == 0 && p == 0) ? 0 : 1;
+                            asm volatile(
+                                "{\n.reg .pred pp;\nsetp.ne.b32 pp, %4, 0;\n"
+                                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, pp;\n}\n" ::"r"(
+                                    tmem + (uint32_t)(p * kBSN)),
+                                "l"(ad), "l"(bd), "r"(id), "r"(acc));
+                        }
+                    }
+                    asm volatile(
+                        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 "
+                        "[%0];" ::"r"(saddr(bar)));
+                }
+                const bool ok = mbar_wait(saddr(bar), phase, err);
+                phase ^= 1u;
+                if (__syncthreads_or(!ok)) return false;
+            }
+            // epilogue: thread = row (TMEM lane), 4 groups of 8 columns
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+            for (int g = 0; g < 4; g++) {
+                if (g * 8 >= nc) break;   // block-uniform
+                float hi[8], lo[8], sum5[8];
+#pragma unroll
+                for (int q = 0; q < 8; q++) {
+                    hi[q] = 0.0f;
+                    lo[q] = 0.0f;
+                    sum5[q] = 0.0f;
+                }
+                // diagonals 0-4 through the two-sum, 5.. summed in FP32 first
+#pragma unroll
+                for (int d0 = 0; d0 < kSplitMaxS; d0 += 2) {
+                    if (d0 < S) {
+                        uint32_t v[2][8];
+                        TMEM_LD8(tl + (uint32_t)(d0 * kBSN + g * 8), v[0]);
+                        if (d0 + 1 < S) TMEM_LD8(tl + (uint32_t)((d0 + 1) * kBSN + g * 8), v[1]);
+                        asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+                        for (int e = 0; e < 2; e++) {
+                            const int d = d0 + e;
+                            if (d < S) {
+#pragma unroll
+                                for (int q = 0; q < 8; q++) {
+                                    const float xv = __uint_as_float(v[e][q]);
+                                    if (d == 0) hi[q] = xv;
+                                    else if (d < 5) bsum2_add(hi[q], lo[q], xv);
+                                    else sum5[q] += xv;
+                                }
+                            }
+                        }
+                    }
+                }
+                if (S > 5)
+#pragma unroll
+                    for (int q = 0; q < 8; q++) bsum2_add(hi[q], lo[q], sum5[q]);
+#pragma unroll
+                for (int q = 0; q < 8; q++) {
+                    const int jl = g * 8 + q;
+                    if (!rv || jl >= nc) continue;
+                    const int dx = sdx[myslot * kBSN + jl], dy = sdy[myslot * kBSN + jl];
+                    const float h2 = hi[q] + lo[q];
+                    const float l2 = lo[q] - (h2 - hi[q]);
+                    const double Pv = df_to_double(h2, l2, er + seb[jl] + dx);
+                    double *yp = Y + row + (j0 + jl) * ldy;
+                    double y;
+                    if (dy == kFresh) y = -Pv;
+                    else if (dy >= -1022 && dy <= 1023) y = fma(*yp, pow2_normal(dy), -Pv);
+                    else y = scale2(*yp, dy) - Pv;
+                    *yp = y;
+                    atomicMax(&snu[myslot * kBSN + jl], (unsigned long long)abs_bits(y));
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncthreads();
+            for (int idx = tid; idx < nslots * kBSN; idx += kBThreads) {
+                const int sl = idx / kBSN, j = idx % kBSN;
+                if (j < nc && snu[idx])
+                    atomicMax((unsigned long long *)&B.seg_nu[(int64_t)(rfirst + sl) * m + j0 + j],
+                              snu[idx]);
+            }
+            __syncthreads();
+        }
+    }
+    return true;
+}
+
 // Consolidation of one unit's column(s) into canonical form (as k_finalize,
 // with the CTA's 4 warps).  smem: 4 ints.
 __device__ void cta_finalize_unit(const BatchItem &B, int u, int *sbest) {
@@ -230,12 +481,35 @@ __device__ void cta_finalize_unit(const BatchItem &B, int u, int *sbest) {
 
 }  // namespace
 
+template <bool SPLIT>
 __global__ void __launch_bounds__(kBThreads)
-    k_batched(const BatchItem *__restrict__ items, int count, int *queue, DevStatus *status) {
+    k_batched(const BatchItem *__restrict__ items, int count, int *queue, DevStatus *status,
+              int S) {
     extern __shared__ double smem[];
     __shared__ int next;
     __shared__ int sbest[kBThreads / 32];
-    for (;;) {
+    __shared__ uint64_t mbar;
+    __shared__ uint32_t tmem_holder;
+    uint32_t tmem = 0, phase = 0;
+    unsigned char *sbase = (unsigned char *)(((uintptr_t)smem + 1023) & ~(uintptr_t)1023);
+    if constexpr (SPLIT) {
+        if (threadIdx.x < 32) {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                             saddr(&tmem_holder)),
+                         "r"(kBSTmemCols));
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+        }
+        if (threadIdx.x == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(&mbar)), "r"(1));
+            asm volatile("fence.mbarrier_init.release.cluster;");
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        tmem = tmem_holder;
+    }
+    bool alive = true;
+    while (alive) {
         if (threadIdx.x == 0) next = atomicAdd(queue, 1);
         __syncthreads();
         const int k = next;
@@ -257,37 +531,60 @@ __global__ void __launch_bounds__(kBThreads)
                 __syncthreads();
             }
             if (s > 0 && P.tile_col[s] < P.m) {
-                cta_tile_update(B, s, smem);
+                if constexpr (SPLIT) {
+                    if (!cta_split_update(B, s, S, sbase, tmem, &mbar, phase,
+                                          &status->timeout)) {
+                        alive = false;
+                        break;
+                    }
+                } else {
+                    cta_tile_update(B, s, smem);
+                }
                 __syncthreads();
             }
         }
+        if (!alive) break;
         for (int u = 0; u < P.nunits; u++) cta_finalize_unit(B, u, sbest);
         __syncthreads();
     }
+    if constexpr (SPLIT) {
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
+        if (threadIdx.x < 32)
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                         "r"(kBSTmemCols));
+    }
 }
 
-size_t batched_smem_bytes() {
+size_t batched_smem_bytes(bool split) {
     const size_t upd = sizeof(double) * (64 * 65 + 64 * 64 + 8 * 64) + sizeof(int) * 128;
-    return std::max(diag_smem<4>(64), upd);
+    // the split variant aligns its operand tiles to 1024 bytes; its size
+    // also keeps at most two CTAs (2 x 256 TMEM columns) on an SM
+    const size_t base = std::max(diag_smem<4>(64), upd);
+    return split ? std::max(base + 1024, kBSBytes) : base;
 }
 
-// One persistent launch: grid = SMs x CTAs per SM (occupancy query).
+// One persistent launch: grid = SMs x CTAs per SM (occupancy query); S > 0
+// runs the split-precision variant (S digit slices).
 cudaError_t launch_batched(const BatchItem *items, int count, int *queue, DevStatus *status,
-                           int nsm, cudaStream_t st) {
-    const size_t smem = batched_smem_bytes();
-    cudaFuncSetAttribute(k_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(k_batched, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           int nsm, cudaStream_t st, int S) {
+    const bool split = S > 0;
+    const size_t smem = batched_smem_bytes(split);
+    auto kern = split ? k_batched<true> : k_batched<false>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                          cudaSharedmemCarveoutMaxShared);
     int per_sm = 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batched, kBThreads, smem) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBThreads, smem) !=
             cudaSuccess ||
         per_sm < 1) {
         cudaGetLastError();
         per_sm = 1;
     }
+    if (split) per_sm = std::min(per_sm, kTmemCols / kBSTmemCols);
     const int grid = std::min(count, nsm * per_sm);
     if (grid <= 0) return cudaSuccess;
-    k_batched<<<grid, kBThreads, smem, st>>>(items, count, queue, status);
+    kern<<<grid, kBThreads, smem, st>>>(items, count, queue, status, S);
     return cudaGetLastError();
 }
 

@@ -37,11 +37,15 @@ __device__ __forceinline__ void digits7(double x, int e, int S, int *d) {
     else if (shift > -62) I = (mant + (1LL << (-shift - 1))) >> (-shift);
     else I = 0;
     if (bits < 0) I = -I;
-    for (int p = S - 1; p >= 1; p--) {
-        long long r = I & 127;
-        if (r >= 64) r -= 128;
-        d[p] = (int)r;
-        I = (I - r) >> 7;
+    // unrolled over the largest S with a predicate, so d stays in registers
+#pragma unroll
+    for (int p = kSplitMaxS - 1; p >= 1; p--) {
+        if (p < S) {
+            long long r = I & 127;
+            if (r >= 64) r -= 128;
+            d[p] = (int)r;
+            I = (I - r) >> 7;
+        }
     }
     d[0] = (int)I;                                      // |d_0| <= 64
 }
