@@ -184,6 +184,22 @@ def rooflines(prof, steps, mode, slices, F_diag, F_upd, F_bt, peaks, n, tile, F_
     return out
 
 
+def profiled_steps(h, step, steps, dev, k=3):
+    """Per-kernel CUDA-event times of k extra steps, after the timed region
+    (the events recorded around every launch are kept out of the timed
+    steps), scaled to `steps` steps: {kind: (ms, launches)}."""
+    import torch
+    k = max(1, min(k, steps))
+    h.profile(True)
+    h.profile_read()
+    for _ in range(k):
+        step()
+    torch.cuda.synchronize(dev)
+    prof = h.profile_read()
+    h.profile(False)
+    return {kind: (ms * steps / k, int(round(c * steps / k))) for kind, (ms, c) in prof.items()}
+
+
 def measured_peaks():
     try:
         return json.load(open(MEASURED))
@@ -386,8 +402,6 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize(dev)
     ev.sync(local_rank)
     h = ev.handle(local_rank)
-    h.profile(True)
-    h.profile_read()
 
     gpu_id = None
     try:
@@ -409,9 +423,8 @@ def run_ours(args, rank, world, local_rank):
         dist.barrier()
     elapsed_ms = t0.elapsed_time(t1)
     clocks = sampler.stop() if sampler else None
-    prof = h.profile_read()
-    h.profile(False)
     ev.sync(local_rank)
+    prof = profiled_steps(h, step, args.steps, dev)
     if dist:
         tt = torch.tensor([elapsed_ms], device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -573,8 +586,6 @@ def run_batched(args, rank, world, local_rank):
                               np.ascontiguousarray(np.diagonal(T, 1)), None, nb)
         F_upd += flop_counts(n, blocks, ts, with_q=False)[1]
     h = ev.handle(local_rank)
-    h.profile(True)
-    h.profile_read()
     sampler = ClockSampler() if rank == 0 else None
     if dist:
         dist.barrier()
@@ -591,8 +602,9 @@ def run_batched(args, rank, world, local_rank):
         dist.barrier()
     elapsed = t0.elapsed_time(t1)
     clocks = sampler.stop() if sampler else None
-    prof = h.profile_read()
-    h.profile(False)
+    prof = profiled_steps(
+        h, lambda: ev.batched_packed(Tp, ns, offs, sel, tile=args.tile, mode=mode, out=out,
+                                     slices=args.slices), args.steps, dev)
     ev.sync(local_rank)
     if dist:
         tt = torch.tensor([elapsed], device=dev)
@@ -742,8 +754,6 @@ def run_generalized(args, rank, world, local_rank):
         out = step()
     torch.cuda.synchronize(dev)
     h = ev.handle(local_rank)
-    h.profile(True)
-    h.profile_read()
     sampler = ClockSampler() if rank == 0 else None
     if dist:
         dist.barrier()
@@ -759,8 +769,7 @@ def run_generalized(args, rank, world, local_rank):
         dist.barrier()
     elapsed = t0.elapsed_time(t1)
     clocks = sampler.stop() if sampler else None
-    prof = h.profile_read()
-    h.profile(False)
+    prof = profiled_steps(h, step, args.steps, dev)
     ev.sync(local_rank)
     if dist:
         tt = torch.tensor([elapsed], device=dev)

@@ -10,10 +10,12 @@ namespace evec {
 
 namespace {
 
-template <bool C>
+// GR lanes per real unit (8, 16 or 32), twice that (at most a warp) per
+// complex pair
+template <bool C, int GR = 8>
 struct Lanes {
-    static constexpr int G = C ? 16 : 8;     // lanes per unit
-    static constexpr int U = 32 / G;         // units per warp
+    static constexpr int G = C ? (2 * GR < 32 ? 2 * GR : 32) : GR;   // lanes per unit
+    static constexpr int U = 32 / G;                                   // units per warp
 };
 
 struct Cx {
@@ -186,42 +188,41 @@ __device__ __forceinline__ void cp_async8(void *smem_dst, const void *gsrc) {
 }
 
 // rows [0, q) of one unit -= T[0:q, q-block] z: the lane's rows g, g + G, ...
+// from the highest down (the rows of the next block to solve come first),
 // with a trip count uniform across the warp, two rows per step (loads first)
 template <bool C, int BS, int G>
 __device__ __forceinline__ void update_rows(double *myr, double *myi, const double *c0,
                                             const double *c1, int q, int g, Cx z0, Cx z1,
                                             int ys) {
     const int n = (q + G - 1) / G;
-    int j = 0;
-    for (; j + 2 <= n; j += 2) {
-        const int i0 = g + G * j, i1 = i0 + G;
-        const bool ok1 = i1 < q;            // only the last pair can be partial
-        const double a0 = myr[i0 * ys], a1 = ok1 ? myr[i1 * ys] : 0.0;
-        const double b0 = C ? myi[i0 * ys] : 0.0, b1 = (C && ok1) ? myi[i1 * ys] : 0.0;
-        const double t0 = c0[i0], t1 = ok1 ? c0[i1] : 0.0;
-        const double u0 = BS == 2 ? c1[i0] : 0.0, u1 = (BS == 2 && ok1) ? c1[i1] : 0.0;
+    int j = n - 1;
+    for (; j >= 1; j -= 2) {
+        const int i0 = g + G * j, i1 = i0 - G;
+        const bool ok0 = i0 < q;            // only the highest row can be beyond q
+        const double a0 = ok0 ? myr[i0 * ys] : 0.0, a1 = myr[i1 * ys];
+        const double b0 = (C && ok0) ? myi[i0 * ys] : 0.0, b1 = C ? myi[i1 * ys] : 0.0;
+        const double t0 = ok0 ? c0[i0] : 0.0, t1 = c0[i1];
+        const double u0 = (BS == 2 && ok0) ? c1[i0] : 0.0, u1 = BS == 2 ? c1[i1] : 0.0;
         double v0 = fma(-t0, z0.re, a0), v1 = fma(-t1, z0.re, a1);
         if (BS == 2) { v0 = fma(-u0, z1.re, v0); v1 = fma(-u1, z1.re, v1); }
-        myr[i0 * ys] = v0;
-        if (ok1) myr[i1 * ys] = v1;
+        if (ok0) myr[i0 * ys] = v0;
+        myr[i1 * ys] = v1;
         if (C) {
             double w0 = fma(-t0, z0.im, b0), w1 = fma(-t1, z0.im, b1);
             if (BS == 2) { w0 = fma(-u0, z1.im, w0); w1 = fma(-u1, z1.im, w1); }
-            myi[i0 * ys] = w0;
-            if (ok1) myi[i1 * ys] = w1;
+            if (ok0) myi[i0 * ys] = w0;
+            myi[i1 * ys] = w1;
         }
     }
-    if (j < n) {
-        const int i = g + G * j;
-        if (i < q) {
-            double v = fma(-c0[i], z0.re, myr[i * ys]);
-            if (BS == 2) v = fma(-c1[i], z1.re, v);
-            myr[i * ys] = v;
-            if (C) {
-                double w = fma(-c0[i], z0.im, myi[i * ys]);
-                if (BS == 2) w = fma(-c1[i], z1.im, w);
-                myi[i * ys] = w;
-            }
+    if (j == 0 && g < q) {
+        const int i = g;
+        double v = fma(-c0[i], z0.re, myr[i * ys]);
+        if (BS == 2) v = fma(-c1[i], z1.re, v);
+        myr[i * ys] = v;
+        if (C) {
+            double w = fma(-c0[i], z0.im, myi[i * ys]);
+            if (BS == 2) w = fma(-c1[i], z1.im, w);
+            myi[i * ys] = w;
         }
     }
 }
@@ -235,7 +236,7 @@ __device__ __forceinline__ void update_rows_pencil(double *myr, double *myi, con
                                                    const double *t1c, int q, int g, Cx zb0, Cx zb1,
                                                    Cx wz0, Cx wz1, int ys) {
     const int n = (q + G - 1) / G;
-    for (int j = 0; j < n; j++) {
+    for (int j = n - 1; j >= 0; j--) {   // highest rows first
         const int i = g + G * j;
         if (i >= q) continue;
         const double a = myr[i * ys];
@@ -257,16 +258,16 @@ __device__ __forceinline__ void update_rows_pencil(double *myr, double *myi, con
 // eigenvector's own block: every unit (own tile included) loads its rows of
 // Y with exponents seg_e and maxima seg_nu, the own block is fixed at zero,
 // and no segment is fresh (the correction solve of the residual sweep).
-template <int W, bool C, bool GEN = false, bool RHS = false>
+template <int W, bool C, bool GEN = false, bool RHS = false, int GR = 8>
 __device__ void diag_tile(int s, int list_pos0, const double *__restrict__ T, int64_t ldt,
                           const Plan &P, const double *__restrict__ tau,
                           const double *__restrict__ blk_tau, double *__restrict__ Y, int64_t ldy,
                           int32_t *__restrict__ seg_e, double *__restrict__ seg_nu,
                           int32_t *__restrict__ seg_dx, int32_t *__restrict__ seg_dy,
                           double *smem, const Pencil &pen = Pencil()) {
-    constexpr int G = Lanes<C>::G;
+    constexpr int G = Lanes<C, GR>::G;
     constexpr int kThreads = 32 * W;
-    constexpr int kUnits = Lanes<C>::U * W;
+    constexpr int kUnits = Lanes<C, GR>::U * W;
     constexpr int ys = kUnits + 1;
     constexpr int FW = C ? 8 : 4;                      // factor doubles per block
     const int t0 = P.tile_start[s];
@@ -337,19 +338,8 @@ __device__ void diag_tile(int s, int list_pos0, const double *__restrict__ T, in
         for (int k = 0; k < nbt; k++) if (bsz[k] == 1) ford[f++] = k;
         for (int k = 0; k < nbt; k++) if (bsz[k] == 2) ford[f++] = k;
     }
-    // the segments, column by column (coalesced); own units start at zero
-    for (int idx = tid; idx < kUnits * ts; idx += kThreads) {
-        const int uu = idx / ts, i = idx % ts;
-        const int c = ucol[uu];
-        if (c >= 0 && (RHS || !uown[uu])) {
-            cp_async8(&yr[i * ys + uu], &Y[(t0 + i) + (int64_t)c * ldy]);
-            if (C) cp_async8(&yi[i * ys + uu], &Y[(t0 + i) + (int64_t)(c + 1) * ldy]);
-        } else {
-            yr[i * ys + uu] = 0.0;
-            if (C) yi[i * ys + uu] = 0.0;
-        }
-    }
-    asm volatile("cp.async.commit_group;");
+    // the tile, then the block factors below (they need only T and the
+    // shifts); the segments follow
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();
 
@@ -397,6 +387,22 @@ __device__ void diag_tile(int s, int list_pos0, const double *__restrict__ T, in
         }
     }
 
+    // the segments, column by column (coalesced); own units start at zero
+    for (int idx = tid; idx < kUnits * ts; idx += kThreads) {
+        const int uu = idx / ts, i = idx % ts;
+        const int c = ucol[uu];
+        if (c >= 0 && (RHS || !uown[uu])) {
+            cp_async8(&yr[i * ys + uu], &Y[(t0 + i) + (int64_t)c * ldy]);
+            if (C) cp_async8(&yi[i * ys + uu], &Y[(t0 + i) + (int64_t)(c + 1) * ldy]);
+        } else {
+            yr[i * ys + uu] = 0.0;
+            if (C) yi[i * ys + uu] = 0.0;
+        }
+    }
+    asm volatile("cp.async.commit_group;");
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+
     int e = 0;
     long long nbits = 0;
     if (valid && (RHS || !own)) {
@@ -416,6 +422,15 @@ __device__ void diag_tile(int s, int list_pos0, const double *__restrict__ T, in
         }
     };
 
+    // The update of the rows above a solved block is applied at the start of
+    // the next block step (pending: block row pq, size pbs, solution pz0 /
+    // pz1; pq <= 0 = none).  Each lane walks its own rows from the highest
+    // down, so the next block's rows are updated first; their owner lanes
+    // then hand them to the unit's other lanes by shuffle.  No lane reads
+    // another lane's rows in shared memory, so the chain has no warp
+    // barrier and no shared-memory round trip between the solves.
+    int pq = 0, pbs = 1;
+    Cx pz0 = {0.0, 0.0}, pz1 = {0.0, 0.0};
     for (int k = kb1 - 1; k >= kb0; k--) {
         const int kk = k - kb0;
         const int q = bq[kk];
@@ -424,9 +439,40 @@ __device__ void diag_tile(int s, int list_pos0, const double *__restrict__ T, in
         const int ftq = GEN ? efield(tauk) : btf[kk];
         const bool act = valid && (!own || k <= kown);
         const bool solving = act && !(own && k == kown);
+        if (pq > 0) {   // rows [0, pq) -= (block pq) pz; pq = q + bs
+            const double *c0 = Ts + pq * ts;
+            if constexpr (GEN) {
+                const double *d0 = Bt + pq * ts;
+                const Cx zb0 = {be * pz0.re, be * pz0.im}, zb1 = {be * pz1.re, be * pz1.im};
+                const Cx wz0 = cmul<C>(Cx{lr, li}, pz0), wz1 = cmul<C>(Cx{lr, li}, pz1);
+                if (pbs == 1)
+                    update_rows_pencil<C, 1, G>(myr, myi, c0, c0, d0, d0, pq, g, zb0, zb1, wz0,
+                                                wz1, ys);
+                else
+                    update_rows_pencil<C, 2, G>(myr, myi, c0, c0 + ts, d0, d0 + ts, pq, g, zb0,
+                                                zb1, wz0, wz1, ys);
+            } else {
+                if (pbs == 1) update_rows<C, 1, G>(myr, myi, c0, c0, pq, g, pz0, pz1, ys);
+                else update_rows<C, 2, G>(myr, myi, c0, c0 + ts, pq, g, pz0, pz1, ys);
+            }
+        }
+        // the block's right-hand side from its owner lanes
+        const int o0 = q % G, o1 = (q + 1) % G;
+        double a0 = 0.0, b0 = 0.0, a1 = 0.0, b1 = 0.0;
+        if (g == o0) {
+            a0 = myr[q * ys];
+            if (C) b0 = myi[q * ys];
+        }
+        if (bs == 2 && g == o1) {
+            a1 = myr[(q + 1) * ys];
+            if (C) b1 = myi[(q + 1) * ys];
+        }
         Cx z0 = {0.0, 0.0}, z1 = {0.0, 0.0};
-        const Cx r0 = {myr[q * ys], C ? myi[q * ys] : 0.0};
-        const Cx r1 = bs == 2 ? Cx{myr[(q + 1) * ys], C ? myi[(q + 1) * ys] : 0.0} : Cx{0.0, 0.0};
+        const Cx r0 = {__shfl_sync(0xffffffffu, a0, o0, G),
+                       C ? __shfl_sync(0xffffffffu, b0, o0, G) : 0.0};
+        Cx r1 = {0.0, 0.0};
+        if (bs == 2)
+            r1 = {__shfl_sync(0xffffffffu, a1, o1, G), C ? __shfl_sync(0xffffffffu, b1, o1, G) : 0.0};
         Fac F;
         {
             const double *fp = myfac + kk * FW;
@@ -445,7 +491,6 @@ __device__ void diag_tile(int s, int list_pos0, const double *__restrict__ T, in
             F.pr = pp & 1;
             F.pc = pp >> 1;
         }
-        __syncwarp();
         if (act) {
             int sc = 0;
             if (!solving) {
@@ -465,14 +510,15 @@ __device__ void diag_tile(int s, int list_pos0, const double *__restrict__ T, in
                 Enu += sc;
                 e += sc;
             }
-            if (g == q % G) { myr[q * ys] = z0.re; if (C) myi[q * ys] = z0.im; }
-            if (bs == 2 && g == (q + 1) % G) {
+            if (g == o0) { myr[q * ys] = z0.re; if (C) myi[q * ys] = z0.im; }
+            if (bs == 2 && g == o1) {
                 myr[(q + 1) * ys] = z1.re;
                 if (C) myi[(q + 1) * ys] = z1.im;
             }
         }
         // protection of the update of rows [0, q): fast test on exponents,
-        // exact FP64 test only when it cannot decide
+        // exact FP64 test only when it cannot decide (the rows already hold
+        // every earlier block's update)
         int fmu = max(max(efield(z0.re), efield(z0.im)), max(efield(z1.re), efield(z1.im)));
         const bool trig = act && q > 0 && (Enu > 1019 || fmu + ftq > 3063);
         if (__any_sync(0xffffffffu, trig)) {
@@ -498,26 +544,18 @@ __device__ void diag_tile(int s, int list_pos0, const double *__restrict__ T, in
                 Enu = efield(nu) - 1022;
             }
         }
+        // the update with this block's z runs at the start of the next step
         if (act && q > 0) {
-            const double *c0 = Ts + q * ts;
-            if constexpr (GEN) {
-                const double *d0 = Bt + q * ts;
-                const Cx zb0 = {be * z0.re, be * z0.im}, zb1 = {be * z1.re, be * z1.im};
-                const Cx wz0 = cmul<C>(Cx{lr, li}, z0), wz1 = cmul<C>(Cx{lr, li}, z1);
-                if (bs == 1)
-                    update_rows_pencil<C, 1, G>(myr, myi, c0, c0, d0, d0, q, g, zb0, zb1, wz0,
-                                                wz1, ys);
-                else
-                    update_rows_pencil<C, 2, G>(myr, myi, c0, c0 + ts, d0, d0 + ts, q, g, zb0,
-                                                zb1, wz0, wz1, ys);
-            } else {
-                if (bs == 1) update_rows<C, 1, G>(myr, myi, c0, c0, q, g, z0, z1, ys);
-                else update_rows<C, 2, G>(myr, myi, c0, c0 + ts, q, g, z0, z1, ys);
-            }
+            pq = q;
+            pbs = bs;
+            pz0 = z0;
+            pz1 = z1;
             Enu = max(Enu, fmu + ftq - 2044) + 1;
+        } else {
+            pq = 0;
         }
-        __syncwarp();
     }
+    __syncwarp();
     // segment maxima per column, exponent
     {
         long long br = 0, bi = 0;
@@ -614,10 +652,10 @@ __device__ void diag_tile(int s, int list_pos0, const double *__restrict__ T, in
 
 }  // namespace
 
-// dynamic shared memory of diag_tile<W, C, GEN> for a tile of t rows
-template <int W, bool C, bool GEN = false>
+// dynamic shared memory of diag_tile<W, C, GEN, *, GR> for a tile of t rows
+template <int W, bool C, bool GEN = false, int GR = 8>
 inline size_t diag_smem_bytes(int t) {
-    constexpr int kUnits = Lanes<C>::U * W;
+    constexpr int kUnits = Lanes<C, GR>::U * W;
     constexpr int FW = C ? 8 : 4;
     return sizeof(double) * ((size_t)t * t + kMaxTile + kUnits +
                              (C ? 2 : 1) * (size_t)t * (kUnits + 1) + (size_t)kUnits * t * FW) +
@@ -625,9 +663,9 @@ inline size_t diag_smem_bytes(int t) {
            (GEN ? sizeof(double) * ((size_t)t * t + kMaxTile + (size_t)kUnits * t) : 0);
 }
 
-template <int W, bool GEN = false>
+template <int W, bool GEN = false, int GR = 8>
 inline size_t diag_smem(int t) {
-    return std::max(diag_smem_bytes<W, false, GEN>(t), diag_smem_bytes<W, true, GEN>(t));
+    return std::max(diag_smem_bytes<W, false, GEN, GR>(t), diag_smem_bytes<W, true, GEN, GR>(t));
 }
 
 }  // namespace evec

@@ -45,7 +45,7 @@
 namespace evec {
 
 
-template <int W, bool GEN, bool RHS>
+template <int W, bool GEN, bool RHS, int GR>
 __global__ void __launch_bounds__(32 * W)
     k_diag_solve(int s, int nreal_ctas, const double *__restrict__ T, int64_t ldt, Plan P,
                  const double *__restrict__ tau, const double *__restrict__ blk_tau,
@@ -54,32 +54,60 @@ __global__ void __launch_bounds__(32 * W)
                  int32_t *__restrict__ seg_dy, Pencil pen) {
     extern __shared__ double smem[];
     if ((int)blockIdx.x < nreal_ctas)
-        diag_tile<W, false, GEN, RHS>(s, P.tile_real[s] + blockIdx.x * (Lanes<false>::U * W), T, ldt,
-                                 P, tau, blk_tau, Y, ldy, seg_e, seg_nu, seg_dx, seg_dy, smem,
-                                 pen);
+        diag_tile<W, false, GEN, RHS, GR>(s, P.tile_real[s] + blockIdx.x * (Lanes<false, GR>::U * W),
+                                          T, ldt, P, tau, blk_tau, Y, ldy, seg_e, seg_nu, seg_dx,
+                                          seg_dy, smem, pen);
     else
-        diag_tile<W, true, GEN, RHS>(s, P.tile_cplx[s] + (blockIdx.x - nreal_ctas) * (Lanes<true>::U * W),
-                                T, ldt, P, tau, blk_tau, Y, ldy, seg_e, seg_nu, seg_dx, seg_dy,
-                                smem, pen);
+        diag_tile<W, true, GEN, RHS, GR>(
+            s, P.tile_cplx[s] + (blockIdx.x - nreal_ctas) * (Lanes<true, GR>::U * W), T, ldt, P,
+            tau, blk_tau, Y, ldy, seg_e, seg_nu, seg_dx, seg_dy, smem, pen);
 }
 
-template <int W, bool GEN, bool RHS>
+template <int W, bool GEN, bool RHS, int GR = 8>
 static int launch_w(int s, int ts, int nr, int nc, const double *T, int64_t ldt, const Plan &p,
                     const double *tau, const double *blk_tau, double *Y, int64_t ldy,
                     int32_t *seg_e, double *seg_nu, int32_t *seg_dx, int32_t *seg_dy,
                     const Pencil &pen, cudaStream_t st) {
-    constexpr int ur = Lanes<false>::U * W, uc = Lanes<true>::U * W;
+    constexpr int ur = Lanes<false, GR>::U * W, uc = Lanes<true, GR>::U * W;
     const int rct = (nr + ur - 1) / ur;
     const int cct = (nc + uc - 1) / uc;
     if (rct + cct == 0) return 0;
-    cudaFuncSetAttribute(k_diag_solve<W, GEN, RHS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)diag_smem<W, GEN>(W == 4 ? 64 : kMaxTile));
-    // two CTAs per SM (about 82 KB each for 64-row tiles; pencils: one)
-    cudaFuncSetAttribute(k_diag_solve<W, GEN, RHS>, cudaFuncAttributePreferredSharedMemoryCarveout,
+    cudaFuncSetAttribute(k_diag_solve<W, GEN, RHS, GR>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)diag_smem<W, GEN, GR>(W == 4 ? 64 : kMaxTile));
+    // two CTAs per SM at 8 lanes per unit (about 82 KB each for 64-row
+    // tiles; pencils: one), more with more lanes per unit
+    cudaFuncSetAttribute(k_diag_solve<W, GEN, RHS, GR>,
+                         cudaFuncAttributePreferredSharedMemoryCarveout,
                          cudaSharedmemCarveoutMaxShared);
-    k_diag_solve<W, GEN, RHS><<<rct + cct, 32 * W, diag_smem<W, GEN>(ts), st>>>(
+    k_diag_solve<W, GEN, RHS, GR><<<rct + cct, 32 * W, diag_smem<W, GEN, GR>(ts), st>>>(
         s, rct, T, ldt, p, tau, blk_tau, Y, ldy, seg_e, seg_nu, seg_dx, seg_dy, pen);
     return 1;
+}
+
+// Lanes per real unit for a step with nr real and nc complex active units.
+// A unit's chain is latency-bound: per block step its lanes issue the
+// update of the rows above as ceil(q / G) dependent-issue DFMAs, so more
+// lanes per unit shorten every step while the sub-partitions have warps to
+// spare; with many units the FP64 issue slots fill up and the solve work
+// that every lane of a unit repeats makes wide units the slower choice.
+// Largest GR with about 2.5 warps per SM sub-partition at most.
+static int pick_lanes(int nr, int nc) {
+    static int nsm = 0;
+    if (nsm == 0) {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+            nsm = v;
+        else
+            nsm = 148;
+    }
+    const double cap = 2.5 * 4.0 * nsm;
+    for (int gr : {32, 16}) {
+        const double warps = nr * gr / 32.0 + nc * std::min(2 * gr, 32) / 32.0;
+        if (warps <= cap) return gr;
+    }
+    return 8;
 }
 
 // Returns the number of kernels launched (0 when no column is active).
@@ -97,16 +125,24 @@ int launch_diag_solve(int s, const double *T, int64_t ldt, const Plan &p,
         return launch_w<4, true, false>(s, ts, nr, nc, T, ldt, p, tau, blk_tau, Y, ldy, seg_e,
                                         seg_nu, seg_dx, seg_dy, *pen, st);
     // four warps share a tile of up to 64 rows; two for larger tiles
-    if (rhs)
-        return ts <= 64 ? launch_w<4, false, true>(s, ts, nr, nc, T, ldt, p, tau, blk_tau, Y, ldy,
-                                                   seg_e, seg_nu, seg_dx, seg_dy, Pencil(), st)
-                        : launch_w<2, false, true>(s, ts, nr, nc, T, ldt, p, tau, blk_tau, Y, ldy,
-                                                   seg_e, seg_nu, seg_dx, seg_dy, Pencil(), st);
-    if (ts <= 64)
-        return launch_w<4, false, false>(s, ts, nr, nc, T, ldt, p, tau, blk_tau, Y, ldy, seg_e,
-                                         seg_nu, seg_dx, seg_dy, Pencil(), st);
-    return launch_w<2, false, false>(s, ts, nr, nc, T, ldt, p, tau, blk_tau, Y, ldy, seg_e,
-                                     seg_nu, seg_dx, seg_dy, Pencil(), st);
+    if (ts > 64)
+        return rhs ? launch_w<2, false, true>(s, ts, nr, nc, T, ldt, p, tau, blk_tau, Y, ldy,
+                                              seg_e, seg_nu, seg_dx, seg_dy, Pencil(), st)
+                   : launch_w<2, false, false>(s, ts, nr, nc, T, ldt, p, tau, blk_tau, Y, ldy,
+                                               seg_e, seg_nu, seg_dx, seg_dy, Pencil(), st);
+    const int gr = pick_lanes(nr, nc);
+#define EVEC_DIAG_LAUNCH(R, G_)                                                                  \
+    return launch_w<4, false, R, G_>(s, ts, nr, nc, T, ldt, p, tau, blk_tau, Y, ldy, seg_e,       \
+                                     seg_nu, seg_dx, seg_dy, Pencil(), st)
+    if (rhs) {
+        if (gr == 32) EVEC_DIAG_LAUNCH(true, 32);
+        if (gr == 16) EVEC_DIAG_LAUNCH(true, 16);
+        EVEC_DIAG_LAUNCH(true, 8);
+    }
+    if (gr == 32) EVEC_DIAG_LAUNCH(false, 32);
+    if (gr == 16) EVEC_DIAG_LAUNCH(false, 16);
+    EVEC_DIAG_LAUNCH(false, 8);
+#undef EVEC_DIAG_LAUNCH
 }
 
 }  // namespace evec
