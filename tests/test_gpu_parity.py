@@ -160,6 +160,29 @@ def test_deterministic_and_power_of_two_invariant():
     np.testing.assert_array_equal(e1, e3)
 
 
+@pytest.mark.parametrize("mode", ["fp64", "split"])
+def test_subset_columns_bit_identical_to_all_columns(mode):
+    # columns are independent in the method: a subset's columns equal the
+    # same columns of the all-columns run bit for bit.  The subset has far
+    # fewer active units per step, so its diagonal solves run with more
+    # lanes per unit (16 / 32 instead of 8): this pins those variants to
+    # the default one.
+    n = 1500
+    T, blocks = workloads.config0_schur(n, seed=77)
+    Q = workloads.householder_orthogonal(n, seed=78)
+    Xa, ea, _, _ = _gpu(T, Q, tile=64, mode=mode)
+    sel = workloads.random_eigen_selection(n, blocks, 0.1, seed=79)
+    Xs, es, _, _ = _gpu(T, Q, select=sel, tile=64, mode=mode)
+    cols, col = [], 0
+    for p, sz in blocks:
+        if sel[p] or (sz == 2 and sel[p + 1]):
+            cols.extend(range(col, col + sz))
+        col += sz
+    assert Xs.shape[1] == len(cols) > 0
+    np.testing.assert_array_equal(Xs, Xa[:, cols])
+    np.testing.assert_array_equal(es, ea[cols])
+
+
 # ---------------------------------------------------------------------------
 # full size, in the benchmark's launch configuration (tile 64, with Q):
 # the GPU computes every column, the oracle a seeded sample of columns
