@@ -183,6 +183,27 @@ def test_subset_columns_bit_identical_to_all_columns(mode):
     np.testing.assert_array_equal(es, ea[cols])
 
 
+def test_plan_reuse_follows_the_diagonals_and_selection():
+    # the handle reuses its plan when T's three central diagonals, the
+    # selection and the tile are those of the last call; anything else
+    # replans.  Same diagonals with a different upper part, a changed
+    # eigenvalue, a changed selection, then the first matrix again: each
+    # result matches the oracle for its own input.
+    n = 400
+    T1, blocks = workloads.config0_schur(n, seed=301)
+    T2 = T1.copy()
+    rng = np.random.default_rng(302)
+    iu = np.triu_indices(n, 2)
+    T2[iu] = rng.standard_normal(len(iu[0]))        # same diagonals, new upper part
+    T3 = T1.copy()
+    p = next(q for q, sz in blocks if sz == 1 and q > 10)
+    T3[p, p] += 0.125                               # one eigenvalue moved
+    sel = workloads.random_eigen_selection(n, blocks, 0.3, seed=303)
+    for T, s in ((T1, None), (T2, None), (T3, None), (T3, sel), (T1, None)):
+        X, e, lr, li = _gpu(T, tile=32, select=s)
+        _parity(T, None, X, e, lr, li, select=s)
+
+
 # ---------------------------------------------------------------------------
 # full size, in the benchmark's launch configuration (tile 64, with Q):
 # the GPU computes every column, the oracle a seeded sample of columns
