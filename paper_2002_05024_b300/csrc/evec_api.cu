@@ -444,6 +444,15 @@ struct evec_ctx {
     int *queue_d = nullptr;
     int tune[2][EVEC_SIZE_CLASSES] = {{0}};
     cudaStream_t cap_stream = nullptr;
+    // evec_standard_host: Q's copy (q_src, q_bytes) is issued by
+    // evec_standard on copy_stream once its own small copies are queued
+    // (they would otherwise wait behind it) and runs beside the solve;
+    // q_ready marks its end, wait_q makes the back-transformation wait
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_prior = nullptr, q_ready = nullptr;
+    const double *q_src = nullptr;
+    size_t q_bytes = 0;
+    bool wait_q = false;
     cudaGraphExec_t bexec = nullptr;
     std::vector<uint64_t> bkey;   // what the cached graph was captured for
     std::vector<HostPlan> bplans;
@@ -773,6 +782,9 @@ evec_status evec_destroy(evec_handle h) {
     for (cudaEvent_t e : h->spare) cudaEventDestroy(e);
     if (h->bexec) cudaGraphExecDestroy(h->bexec);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
+    if (h->ev_prior) cudaEventDestroy(h->ev_prior);
+    if (h->q_ready) cudaEventDestroy(h->q_ready);
     void *host[] = {h->diag_h, h->plan_h, h->status_h, h->boff_h, h->bplan_h};
     for (void *p : host)
         if (p) cudaFreeHost(p);
@@ -895,6 +907,22 @@ evec_status evec_standard(evec_handle h, int64_t n, const double *T, int64_t ldt
     split_panel_layout(h->plan, mode == EVEC_SPLIT ? slices : 0);
     Plan dp;
     EVEC_TRY(upload_plan(h, dp));
+    if (h->q_src && Q == h->hQ) {
+        // the host entry point's Q: copied on a second stream beside the
+        // solve, after the handle's earlier work (which may still read the
+        // buffer) and after this call's small copies
+        if (!h->copy_stream)
+            EVEC_CUDA(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
+        if (!h->ev_prior) EVEC_CUDA(cudaEventCreateWithFlags(&h->ev_prior, cudaEventDisableTiming));
+        if (!h->q_ready) EVEC_CUDA(cudaEventCreateWithFlags(&h->q_ready, cudaEventDisableTiming));
+        EVEC_CUDA(cudaEventRecord(h->ev_prior, h->stream));
+        EVEC_CUDA(cudaStreamWaitEvent(h->copy_stream, h->ev_prior, 0));
+        EVEC_CUDA(cudaMemcpyAsync(h->hQ, h->q_src, h->q_bytes, cudaMemcpyHostToDevice,
+                                  h->copy_stream));
+        EVEC_CUDA(cudaEventRecord(h->q_ready, h->copy_stream));
+        h->q_src = nullptr;
+        h->wait_q = true;
+    }
     double *Y = X;
     int64_t ldy = ldx;
     if (Q) {
@@ -1012,6 +1040,10 @@ evec_status evec_standard(evec_handle h, int64_t n, const double *T, int64_t ldt
         launch_finalize(dp, Y, ldy, refine ? h->seg_ey : h->seg_e, scale_exp, st);
         return 1;
     });
+    if (Q && h->wait_q) {   // Q still arriving on the copy stream (host entry point)
+        EVEC_CUDA(cudaStreamWaitEvent(st, h->q_ready, 0));
+        h->wait_q = false;
+    }
     if (Q && mode == EVEC_SPLIT) {
         cudaError_t ce = cudaSuccess;
         timed(h, EVEC_K_BACKTRANSFORM, [&] {
@@ -1058,20 +1090,28 @@ evec_status evec_standard_host(evec_handle h, int64_t n, const double *T_host,
     EVEC_TRY(grow_device(&h->hT, &h->hT_cap, nn));
     cudaStream_t st = h->stream;
     EVEC_CUDA(cudaMemcpyAsync(h->hT, T_host, nn * 8, cudaMemcpyHostToDevice, st));
-    if (Q_host) {
+    h->wait_q = false;
+    h->q_src = nullptr;
+    if (Q_host) {   // Q is read only by the back-transformation (see q_src)
         EVEC_TRY(grow_device(&h->hQ, &h->hQ_cap, nn));
-        EVEC_CUDA(cudaMemcpyAsync(h->hQ, Q_host, nn * 8, cudaMemcpyHostToDevice, st));
+        h->q_src = Q_host;
+        h->q_bytes = nn * 8;
     }
     // the output size needs the plan; evec_standard plans again (cheap, host)
     int64_t bad = -1;
     EVEC_TRY(plan_device_matrix(h, n, h->hT, n, select_host, resolve_tile(opt), &bad));
     const int64_t m = h->plan.m;
-    if (m == 0) return EVEC_OK;
+    if (m == 0) {
+        h->q_src = nullptr;
+        return EVEC_OK;
+    }
     EVEC_TRY(grow_device(&h->hX, &h->hX_cap, (size_t)n * (size_t)m));
     EVEC_TRY(grow_device(&h->hE, &h->hE_cap, (size_t)m));
     EVEC_TRY(grow_device(&h->hL, &h->hL_cap, 2 * (size_t)m));
-    EVEC_TRY(evec_standard(h, n, h->hT, n, Q_host ? h->hQ : nullptr, n, select_host, h->hX, n,
-                           h->hE, h->hL, h->hL + m, opt));
+    const evec_status es = evec_standard(h, n, h->hT, n, Q_host ? h->hQ : nullptr, n,
+                                         select_host, h->hX, n, h->hE, h->hL, h->hL + m, opt);
+    h->q_src = nullptr;
+    EVEC_TRY(es);
     if (X_host)
         EVEC_CUDA(cudaMemcpyAsync(X_host, h->hX, (size_t)n * m * 8, cudaMemcpyDeviceToHost, st));
     if (scale_exp_host)
