@@ -55,6 +55,15 @@ void launch_backtransform(const double *Q, int64_t ldq, const Plan &p, const dou
                           int64_t ldy, double *X, int64_t ldx, cudaStream_t st);
 void launch_canonicalize(const Plan &p, double *X, int64_t ldx, int32_t *scale_exp,
                          cudaStream_t st);
+cudaError_t split_gemm_rows(const double *A, int64_t lda, int M, int K, int S,
+                            __nv_bfloat16 *sa, unsigned long long *rowmax, int *ea,
+                            cudaStream_t st);
+cudaError_t split_gemm_cols(const double *B, int64_t ldb, int M, int N, int K, int S,
+                            const int *kend, double *C, int64_t ldc, const __nv_bfloat16 *sa,
+                            __nv_bfloat16 *sb, unsigned long long *colmax, const int *ea,
+                            int *eb, int *err, cudaStream_t st);
+void launch_canonicalize_range(const Plan &p, double *X, int64_t ldx, int32_t *scale_exp, int u0,
+                               int u1, cudaStream_t st);
 cudaError_t launch_split_gemm(const double *A, int64_t lda, const double *B, int64_t ldb, int M,
                               int N, int K, int S, const int *kend, double *C, int64_t ldc,
                               __nv_bfloat16 *sa, __nv_bfloat16 *sb, unsigned long long *rowmax,
@@ -453,6 +462,11 @@ struct evec_ctx {
     const double *q_src = nullptr;
     size_t q_bytes = 0;
     bool wait_q = false;
+    // evec_standard_host, split mode with Q: the result's host destination
+    // (leading dimension n); evec_standard copies X there chunk by chunk as
+    // the back-transformation finishes it and clears x_dst
+    double *x_dst = nullptr;
+    cudaEvent_t x_part = nullptr, x_done = nullptr;
     cudaGraphExec_t bexec = nullptr;
     std::vector<uint64_t> bkey;   // what the cached graph was captured for
     std::vector<HostPlan> bplans;
@@ -783,6 +797,8 @@ evec_status evec_destroy(evec_handle h) {
     if (h->bexec) cudaGraphExecDestroy(h->bexec);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
+    if (h->x_part) cudaEventDestroy(h->x_part);
+    if (h->x_done) cudaEventDestroy(h->x_done);
     if (h->ev_prior) cudaEventDestroy(h->ev_prior);
     if (h->q_ready) cudaEventDestroy(h->q_ready);
     void *host[] = {h->diag_h, h->plan_h, h->status_h, h->boff_h, h->bplan_h};
@@ -1044,7 +1060,61 @@ evec_status evec_standard(evec_handle h, int64_t n, const double *T, int64_t ldt
         EVEC_CUDA(cudaStreamWaitEvent(st, h->q_ready, 0));
         h->wait_q = false;
     }
-    if (Q && mode == EVEC_SPLIT) {
+    if (Q && mode == EVEC_SPLIT && h->x_dst && ldx == n) {
+        // host destination (host entry point): the back-transformation and
+        // the canonical form in chunks of columns, each chunk's finished
+        // units copied to the host on the copy stream while the next chunk
+        // computes
+        if (!h->copy_stream)
+            EVEC_CUDA(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
+        if (!h->x_part) EVEC_CUDA(cudaEventCreateWithFlags(&h->x_part, cudaEventDisableTiming));
+        if (!h->x_done) EVEC_CUDA(cudaEventCreateWithFlags(&h->x_done, cudaEventDisableTiming));
+        double *dst = h->x_dst;
+        h->x_dst = nullptr;
+        cudaError_t ce = cudaSuccess;
+        timed(h, EVEC_K_BACKTRANSFORM, [&] {
+            ce = split_gemm_rows(Q, ldq, (int)n, (int)n, slices, h->slA, h->rmax, h->ea, st);
+            return 2;
+        });
+        EVEC_CUDA(ce);
+        // chunks of whole 64-column tiles (the K extents are per tile), about
+        // four per call
+        const int64_t chunk = std::max<int64_t>(kSplitColTile,
+                                                (m + 4 * kSplitColTile - 1) / (4 * kSplitColTile) *
+                                                    kSplitColTile);
+        const int nu = (int)HP.unit_col.size();
+        int u = 0;
+        for (int64_t c0 = 0; c0 < m; c0 += chunk) {
+            const int64_t c1 = std::min(m, c0 + chunk);
+            timed(h, EVEC_K_BACKTRANSFORM, [&] {
+                ce = split_gemm_cols(Y + c0 * ldy, ldy, (int)n, (int)(c1 - c0), (int)n, slices,
+                                     h->bt_kend_d + c0 / kSplitColTile, X + c0 * ldx, ldx,
+                                     h->slA, h->slB, h->cmax, h->ea, h->eb,
+                                     &h->status_d->timeout, st);
+                return 3;
+            });
+            EVEC_CUDA(ce);
+            // the units whose columns are all computed (a pair may straddle)
+            int u1 = u;
+            while (u1 < nu && HP.unit_col[u1] + (HP.unit_lam[2 * u1 + 1] != 0.0 ? 2 : 1) <= c1)
+                u1++;
+            if (u1 == u) continue;
+            timed(h, EVEC_K_CANONICALIZE, [&] {
+                launch_canonicalize_range(dp, X, ldx, scale_exp, u, u1, st);
+                return 1;
+            });
+            const int64_t col0 = HP.unit_col[u], col1 = u1 < nu ? HP.unit_col[u1] : m;
+            EVEC_CUDA(cudaEventRecord(h->x_part, st));
+            EVEC_CUDA(cudaStreamWaitEvent(h->copy_stream, h->x_part, 0));
+            EVEC_CUDA(cudaMemcpyAsync(dst + col0 * n, X + col0 * ldx,
+                                      (size_t)(col1 - col0) * n * sizeof(double),
+                                      cudaMemcpyDeviceToHost, h->copy_stream));
+            u = u1;
+        }
+        // the handle's stream waits for the last copy
+        EVEC_CUDA(cudaEventRecord(h->x_done, h->copy_stream));
+        EVEC_CUDA(cudaStreamWaitEvent(st, h->x_done, 0));
+    } else if (Q && mode == EVEC_SPLIT) {
         cudaError_t ce = cudaSuccess;
         timed(h, EVEC_K_BACKTRANSFORM, [&] {
             ce = launch_split_gemm(Q, ldq, Y, ldy, (int)n, (int)m, (int)n, slices, h->bt_kend_d, X,
@@ -1108,11 +1178,14 @@ evec_status evec_standard_host(evec_handle h, int64_t n, const double *T_host,
     EVEC_TRY(grow_device(&h->hX, &h->hX_cap, (size_t)n * (size_t)m));
     EVEC_TRY(grow_device(&h->hE, &h->hE_cap, (size_t)m));
     EVEC_TRY(grow_device(&h->hL, &h->hL_cap, 2 * (size_t)m));
+    h->x_dst = X_host;
     const evec_status es = evec_standard(h, n, h->hT, n, Q_host ? h->hQ : nullptr, n,
                                          select_host, h->hX, n, h->hE, h->hL, h->hL + m, opt);
     h->q_src = nullptr;
+    const bool x_copied = X_host && !h->x_dst;   // done chunk by chunk inside
+    h->x_dst = nullptr;
     EVEC_TRY(es);
-    if (X_host)
+    if (X_host && !x_copied)
         EVEC_CUDA(cudaMemcpyAsync(X_host, h->hX, (size_t)n * m * 8, cudaMemcpyDeviceToHost, st));
     if (scale_exp_host)
         EVEC_CUDA(cudaMemcpyAsync(scale_exp_host, h->hE, m * 4, cudaMemcpyDeviceToHost, st));

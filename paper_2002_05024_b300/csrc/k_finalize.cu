@@ -91,8 +91,9 @@ __global__ void __launch_bounds__(kWarps * 32)
 // Re-canonicalise after the back-transformation: X[:, unit] <- X * 2^-t2,
 // t2 = floor(log2 |X|), scale_exp -= t2.
 __global__ void __launch_bounds__(kWarps * 32)
-    k_canonicalize(Plan P, double *__restrict__ X, int64_t ldx, int32_t *__restrict__ scale_exp) {
-    const int u = blockIdx.x;
+    k_canonicalize(Plan P, double *__restrict__ X, int64_t ldx, int32_t *__restrict__ scale_exp,
+                   int u0) {
+    const int u = u0 + blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t n = P.n;
     const int col = P.unit_col[u];
@@ -252,7 +253,14 @@ void launch_finalize(const Plan &p, double *Y, int64_t ldy, const int32_t *seg_e
 void launch_canonicalize(const Plan &p, double *X, int64_t ldx, int32_t *scale_exp,
                          cudaStream_t st) {
     if (p.nunits <= 0) return;
-    k_canonicalize<<<p.nunits, kWarps * 32, 0, st>>>(p, X, ldx, scale_exp);
+    k_canonicalize<<<p.nunits, kWarps * 32, 0, st>>>(p, X, ldx, scale_exp, 0);
+}
+
+// the same for units [u0, u1)
+void launch_canonicalize_range(const Plan &p, double *X, int64_t ldx, int32_t *scale_exp, int u0,
+                               int u1, cudaStream_t st) {
+    if (u1 <= u0) return;
+    k_canonicalize<<<u1 - u0, kWarps * 32, 0, st>>>(p, X, ldx, scale_exp, u0);
 }
 
 }  // namespace evec

@@ -441,22 +441,32 @@ int split_pad_k(int K) { return (K + 63) / 64 * 64; }
 // [Mpad], colmax [Npad] u64; ea [Mpad], eb [Npad] int; kend [N tiles]
 // (device, multiples of 32, <= Kpad).  Returns cudaErrorInvalidValue when
 // a tensor map cannot be encoded.
-cudaError_t launch_split_gemm(const double *A, int64_t lda, const double *B, int64_t ldb, int M,
-                              int N, int K, int S, const int *kend, double *C, int64_t ldc,
-                              __nv_bfloat16 *sa, __nv_bfloat16 *sb, unsigned long long *rowmax,
-                              unsigned long long *colmax, int *ea, int *eb, int *err,
-                              cudaStream_t st) {
-    if (!get_encoder()) return cudaErrorInvalidValue;
-    const int Mpad = split_pad_m(M), Npad = split_pad_n(N), Kpad = split_pad_k(K);
+// C = A B split in two parts, so that B's columns can be taken in chunks:
+// the row slices of A (once), then per chunk the column slices of B and
+// the product.
+cudaError_t split_gemm_rows(const double *A, int64_t lda, int M, int K, int S,
+                            __nv_bfloat16 *sa, unsigned long long *rowmax, int *ea,
+                            cudaStream_t st) {
+    const int Mpad = split_pad_m(M), Kpad = split_pad_k(K);
     cudaMemsetAsync(rowmax, 0, sizeof(unsigned long long) * Mpad, st);
     k_row_max<<<dim3((M + 255) / 256, (K + 255) / 256), 256, 0, st>>>(A, lda, M, K, rowmax);
     k_slice_rows<<<dim3(Kpad / 64, Mpad / 32), 256, 0, st>>>(A, lda, M, K, S, rowmax, sa, Mpad,
                                                               Kpad, ea);
+    return cudaGetLastError();
+}
+
+cudaError_t split_gemm_cols(const double *B, int64_t ldb, int M, int N, int K, int S,
+                            const int *kend, double *C, int64_t ldc, const __nv_bfloat16 *sa,
+                            __nv_bfloat16 *sb, unsigned long long *colmax, const int *ea,
+                            int *eb, int *err, cudaStream_t st) {
+    if (!get_encoder()) return cudaErrorInvalidValue;
+    const int Mpad = split_pad_m(M), Npad = split_pad_n(N), Kpad = split_pad_k(K);
     k_col_max<<<(N + 7) / 8, 256, 0, st>>>(B, ldb, K, N, colmax);
     k_slice_cols<<<dim3((Kpad + 255) / 256, Npad), 256, 0, st>>>(B, ldb, K, N, S, colmax, sb,
                                                                   Npad, Kpad, eb);
     CUtensorMap tmA, tmB;
-    if (!make_map(&tmA, sa, S * Mpad, Kpad, kTM) || !make_map(&tmB, sb, S * Npad, Kpad, 32))
+    if (!make_map(&tmA, (void *)sa, S * Mpad, Kpad, kTM) ||
+        !make_map(&tmB, sb, S * Npad, Kpad, 32))
         return cudaErrorInvalidValue;
     const size_t smem = split_smem_bytes();
     cudaFuncSetAttribute(k_split_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -465,6 +475,17 @@ cudaError_t launch_split_gemm(const double *A, int64_t lda, const double *B, int
     k_split_gemm<false><<<dim3(Npad / kTN, Mpad / kTM), kSplitThreads, smem, st>>>(
         tmA, tmB, S, M, N, 0, Mpad, Npad, kend, 0, ea, eb, C, ldc, none, err);
     return cudaGetLastError();
+}
+
+cudaError_t launch_split_gemm(const double *A, int64_t lda, const double *B, int64_t ldb, int M,
+                              int N, int K, int S, const int *kend, double *C, int64_t ldc,
+                              __nv_bfloat16 *sa, __nv_bfloat16 *sb, unsigned long long *rowmax,
+                              unsigned long long *colmax, int *ea, int *eb, int *err,
+                              cudaStream_t st) {
+    if (!get_encoder()) return cudaErrorInvalidValue;
+    cudaError_t e = split_gemm_rows(A, lda, M, K, S, sa, rowmax, ea, st);
+    if (e != cudaSuccess) return e;
+    return split_gemm_cols(B, ldb, M, N, K, S, kend, C, ldc, sa, sb, colmax, ea, eb, err, st);
 }
 
 // ---------------------------------------------------------------------------

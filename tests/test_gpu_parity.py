@@ -135,12 +135,18 @@ def test_errors_are_reported():
     _parity(T, None, X, e, lr, li)
 
 
-def test_host_entry_point_matches_device():
-    n = 300
-    T, _ = workloads.config0_schur(n, seed=12)
-    Q = workloads.householder_orthogonal(n, seed=13)
-    X, e, lr, li = _gpu(T, Q, tile=64)
-    Xh, eh, lrh, lih = ev.standard_host(T, Q, tile=64)
+@pytest.mark.parametrize("n,mode,frac", [(300, "fp64", None), (701, "split", None),
+                                         (1300, "split", 0.6)])
+def test_host_entry_point_matches_device(n, mode, frac):
+    # the host-buffer entry point copies Q beside the solve and, in split
+    # mode, brings X back in column chunks as the back-transformation
+    # finishes them (pairs can straddle a chunk): the result equals the
+    # device entry point's bit for bit
+    T, blocks = workloads.config0_schur(n, seed=12 + n)
+    Q = workloads.householder_orthogonal(n, seed=13 + n)
+    sel = None if frac is None else workloads.random_eigen_selection(n, blocks, frac, seed=n)
+    X, e, lr, li = _gpu(T, Q, select=sel, tile=64, mode=mode)
+    Xh, eh, lrh, lih = ev.standard_host(T, Q, select=sel, tile=64, mode=mode)
     np.testing.assert_array_equal(X, Xh)
     np.testing.assert_array_equal(e, eh)
     np.testing.assert_array_equal(lr, lrh)
