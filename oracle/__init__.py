@@ -72,6 +72,8 @@ class Oracle:
         lib.evo_generalized.argtypes = [i64, p, i64, p, i64, p, i64, p, p, i64,
                                         p, p, p, p, ctypes.c_int, p]
         lib.evo_generalized.restype = ctypes.c_int
+        lib.evo_trsolve.argtypes = [i64, p, i64, i64, p, i64, p, i64, p, ctypes.c_int, p]
+        lib.evo_trsolve.restype = ctypes.c_int
         lib.evo_naive_standard.argtypes = [i64, p, i64, p, p, i64]
         lib.evo_naive_standard.restype = i64
         self.lib = lib
@@ -130,6 +132,23 @@ class Oracle:
             raise OracleError(st, int(bad[0]))
         return X, e, ar, ai, be
 
+    def trsolve(self, S, B, threads: int = 0):
+        """Robust solve of S x_j = b_j for every column of B (S upper
+        quasi-triangular).  Returns (X, scale_exp): x_j = X[:, j] *
+        2**(-scale_exp[j]), |X[:, j]|_inf in [1, 2)."""
+        S = _fortran(S)
+        B = _fortran(np.atleast_2d(B.T).T if np.ndim(B) == 1 else B)
+        n = S.shape[0]
+        nrhs = B.shape[1]
+        X = np.zeros((n, nrhs), dtype=np.float64, order="F")
+        e = np.zeros(nrhs, dtype=np.int32)
+        bad = np.full(1, -1, dtype=np.int64)
+        st = self.lib.evo_trsolve(n, _ptr(S), max(n, 1), nrhs, _ptr(B), max(n, 1), _ptr(X),
+                                  max(n, 1), _ptr(e), int(threads), _ptr(bad))
+        if st:
+            raise OracleError(st, int(bad[0]))
+        return X, e
+
     def naive_standard(self, S, select=None):
         """Unscaled textbook substitution (overflow witness).  Returns
         (X, number of columns containing Inf or NaN)."""
@@ -185,3 +204,7 @@ def generalized(S, T, Z=None, select=None, threads: int = 0):
 
 def naive_standard(S, select=None):
     return default().naive_standard(S, select)
+
+
+def trsolve(S, B, threads: int = 0):
+    return default().trsolve(S, B, threads)

@@ -10,6 +10,9 @@
  *   - generalized eigenvectors of a pair (S, T),
  *     (S - lambda_i T) y_i = 0, in homogeneous form          (Sec. 2, Eq. evec_solve)
  *   - back-transformation x_i = Q y_i  /  x_i = Z y_i       (Sec. 2, Eq. evec_backtransform)
+ *   - the robust triangular solve with many right-hand sides that the
+ *     eigenvector solve generalises (Sec. 3.4, the LAPACK xLATRS lineage):
+ *     T x_j = b_j for every column of B, each x_j = X[:, j] / 2^scale_exp[j]
  *   - robustness: every intermediate and final value stays in range; the
  *     vector is returned as  y = x / alpha  with alpha an integer power of
  *     two (the augmented representation of Sec. 3.4), the exponent held in a
@@ -703,6 +706,131 @@ int evo_generalized(int64_t n, const double *S, int64_t lds, const double *T, in
     }
 done:
     free(blk); free(tauS); free(tauT); free(lre); free(lim); free(lbe); free(own); free(jobs);
+    return st;
+}
+
+/* ------------------------------------------------------------------ */
+/* Robust triangular solve, many right-hand sides                       */
+/* ------------------------------------------------------------------ */
+
+/*
+ * T x = b for one column, robustly: the backsubstitution of solve_one with
+ * the shift 0 and a general right-hand side instead of an eigenvector's
+ * own block.  Every diagonal block is solved (pivots below
+ * smlnum = 2^-1022 n / ulp perturbed up to it), and every update is
+ * protected.  On return y = x * 2^e.
+ */
+static void solve_rhs(const problem_t *P, const double *b, double *y, int64_t *e_out)
+{
+    const int64_t n = P->n;
+    const block_t *B = P->blk;
+    const double smin = SAFMIN * ((double)n / ULP);
+    const double zero2[2] = {0.0, 0.0};
+    int64_t e = 0;
+    memcpy(y, b, sizeof(double) * n);
+    for (int64_t cur = P->nblk - 1; cur >= 0; cur--) {
+        const int64_t i0 = B[cur].start;
+        const int ib = B[cur].size;
+        double mr[4], mi[4] = {0.0, 0.0, 0.0, 0.0}, rr[2], zr[2], zi[2];
+        for (int a = 0; a < ib; a++) {
+            for (int c = 0; c < ib; c++) mr[a * ib + c] = AT(P->S, P->lds, i0 + a, i0 + c);
+            rr[a] = y[i0 + a];
+        }
+        int64_t s = small_solve(ib, mr, mi, rr, zero2, smin, zr, zi);
+        if (s != 0) {
+            scale_vec(n, y, s);
+            e += s;
+        }
+        for (int a = 0; a < ib; a++) y[i0 + a] = zr[a];
+        if (i0 == 0) break;
+        /* protect, then r[0:i0] -= T[0:i0, block] z */
+        double nu = 0.0, mu = 0.0;
+        for (int64_t r = 0; r < i0; r++)
+            if (fabs(y[r]) > nu) nu = fabs(y[r]);
+        for (int a = 0; a < ib; a++)
+            if (fabs(y[i0 + a]) > mu) mu = fabs(y[i0 + a]);
+        s = protect_update(nu, P->tauS[cur], mu);
+        if (s != 0) {
+            scale_vec(n, y, s);
+            e += s;
+        }
+        for (int a = 0; a < ib; a++) {
+            const double z = y[i0 + a];
+            const double *Tc = &AT(P->S, P->lds, 0, i0 + a);
+            for (int64_t r = 0; r < i0; r++) y[r] -= Tc[r] * z;
+        }
+    }
+    *e_out = e;
+}
+
+/*
+ * Robust triangular solve: for each column b_j of B (n x nrhs, ld ldb),
+ * the solution of T x_j = b_j as X[:, j] * 2^(-scale_exp[j]) with
+ * |X[:, j]|_inf in [1, 2) (X[:, j] = 0 and scale_exp[j] = 0 for b_j = 0).
+ * T (ld ldt) is upper quasi-triangular: 1x1 and 2x2 diagonal blocks from
+ * its first subdiagonal, a 2x2 block in any form.  Entries of T (upper
+ * part and first subdiagonal) and of B must be finite and at most 2^1000
+ * in magnitude; *bad is i + j n for T and n n + i + j n for B.
+ */
+int evo_trsolve(int64_t n, const double *S, int64_t lds, int64_t nrhs, const double *Bm,
+                int64_t ldb, double *X, int64_t ldx, int32_t *scale_exp, int nthreads,
+                int64_t *bad)
+{
+    if (n < 0 || nrhs < 0 || lds < (n > 0 ? n : 1) || ldb < (n > 0 ? n : 1) ||
+        ldx < (n > 0 ? n : 1))
+        return EVO_EINVAL;
+    if (n == 0 || nrhs == 0) return EVO_OK;
+    int st = check_entries(n, S, lds, 1, bad);
+    if (st) return st;
+    for (int64_t j = 0; j < nrhs; j++)
+        for (int64_t i = 0; i < n; i++) {
+            double v = AT(Bm, ldb, i, j);
+            if (!isfinite(v) || fabs(v) > INPUT_MAX) {
+                if (bad) *bad = n * n + i + j * n;
+                return isfinite(v) ? EVO_EINVAL : EVO_ENONFINITE;
+            }
+        }
+    block_t *blk = (block_t *)malloc(sizeof(block_t) * n);
+    double *tau = (double *)malloc(sizeof(double) * n);
+    int64_t nblk = 0;
+    if (!blk || !tau) { st = EVO_ENOMEM; goto done; }
+    st = scan_blocks(n, S, lds, 0, blk, &nblk, bad);
+    if (st) goto done;
+    for (int64_t k = 0; k < nblk; k++)
+        tau[k] = block_col_norm(S, lds, blk[k].start, blk[k].start, blk[k].size);
+    {
+        problem_t P = {n, S, lds, NULL, 0, blk, nblk, tau, NULL, 0.0, 0.0};
+#ifdef _OPENMP
+        if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+        (void)nthreads;
+#endif
+#pragma omp parallel
+        {
+            double *y = (double *)malloc(sizeof(double) * n);
+            if (!y) {
+#pragma omp atomic write
+                st = EVO_ENOMEM;
+            }
+#pragma omp for schedule(dynamic, 1)
+            for (int64_t j = 0; j < nrhs; j++) {
+                if (!y) continue;
+                int64_t e = 0;
+                solve_rhs(&P, &AT(Bm, ldb, 0, j), y, &e);
+                e -= canonicalize(n, y, NULL, 0);
+                if (e > INT32_MAX || e < INT32_MIN) {
+#pragma omp atomic write
+                    st = EVO_EINVAL;
+                    continue;
+                }
+                memcpy(&AT(X, ldx, 0, j), y, sizeof(double) * n);
+                scale_exp[j] = (int32_t)e;
+            }
+            free(y);
+        }
+    }
+done:
+    free(blk); free(tau);
     return st;
 }
 
