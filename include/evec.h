@@ -223,6 +223,31 @@ evec_status evec_generalized(evec_handle h, int64_t n, const double *S, int64_t 
                              int32_t *scale_exp, double *alpha_re, double *alpha_im,
                              double *beta, const evec_opts *opt);
 
+/*
+ * Robust triangular solve with many right-hand sides (the LAPACK xLATRS
+ * generalisation the eigenvector solve of Sec. 3.4 rests on): for every
+ * column b_j of B, the solution of T x_j = b_j, returned as
+ *   x_j = X[:, j] * 2^(-scale_exp[j]),  max_i |X[i, j]| in [1, 2)
+ * (X[:, j] = 0 and scale_exp[j] = 0 for b_j = 0), computed by the tiled
+ * steps of evec_standard with shift 0 and b_j as the starting segments:
+ * every intermediate stays below 2^1020, pivots below 2^-1022 n / ulp are
+ * perturbed up to it (a singular T still gives a finite X).
+ *   T [ldt x n]: upper quasi-triangular, 1x1 and 2x2 diagonal blocks from
+ *     its first subdiagonal (a 2x2 block in any form; no two consecutive
+ *     nonzero subdiagonal entries, else EVEC_ENOTSCHUR); the strictly lower
+ *     part below the first subdiagonal is not read.
+ *   B [ldb x nrhs], X [ldx x nrhs], scale_exp [nrhs]: device pointers on
+ *     the handle's device; X may equal B (ldx == ldb) for an in-place solve.
+ *   opt: mode (EVEC_FP64 or EVEC_SPLIT updates), tile, slices, check as for
+ *     evec_standard; refine is ignored.
+ * Errors: EVEC_EINVAL (bad argument or an entry above 2^1000),
+ * EVEC_ENOTSCHUR, EVEC_ENONFINITE; device-detected ones through evec_sync
+ * with index i + j ldt for T and ldt n + i + j ldb for B.
+ */
+evec_status evec_trsolve(evec_handle h, int64_t n, const double *T, int64_t ldt, int64_t nrhs,
+                         const double *B, int64_t ldb, double *X, int64_t ldx,
+                         int32_t *scale_exp, const evec_opts *opt);
+
 /* ---- batched mode --------------------------------------------------------
  * count independent real Schur forms packed in one device buffer: T_i
  * (order n_host[i], column-major, leading dimension n_i) starts at

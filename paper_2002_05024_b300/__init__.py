@@ -87,6 +87,8 @@ def lib() -> ctypes.CDLL:
         L.evec_last_cuda_error.restype = ctypes.c_char_p
         L.evec_strerror.argtypes = [ctypes.c_int]
         L.evec_strerror.restype = ctypes.c_char_p
+        L.evec_trsolve.argtypes = [p, i64, p, i64, i64, p, i64, p, i64, p,
+                                   ctypes.POINTER(_Opts)]
         L.evec_generalized.argtypes = [p, i64, p, i64, p, i64, p, i64, p, p, i64, p, p, p, p,
                                        ctypes.POINTER(_Opts)]
         L.evec_batched_count.argtypes = [p, i64, p, p, p, p, p]
@@ -195,13 +197,15 @@ def colmajor(t):
     return t.t().contiguous().t()
 
 
-def _check_colmajor(t, name, n=None):
+def _check_colmajor(t, name, n=None, ncols=None):
     import torch
     if t.dtype != torch.float64 or not t.is_cuda or t.dim() != 2:
         raise ValueError(f"{name} must be a float64 CUDA matrix")
     rows, cols = t.shape
-    if n is not None and (rows != n or cols != n):
-        raise ValueError(f"{name} must be {n} x {n}")
+    if ncols is None:
+        ncols = n
+    if n is not None and (rows != n or cols != ncols):
+        raise ValueError(f"{name} must be {n} x {ncols}")
     if rows > 1 and t.stride(0) != 1:
         raise ValueError(f"{name} must be column-major (stride(0) == 1); use colmajor()")
     ld = t.stride(1) if cols > 1 else max(rows, 1)
@@ -327,6 +331,41 @@ def generalized(S, T, Z=None, select=None, tile: int = 0, check: bool = False,
     if check:
         h.sync()
     return X, e, ar, ai, be
+
+
+def trsolve(T, B, tile: int = 0, check: bool = False, mode: str = "fp64", slices: int = 0,
+            out=None):
+    """Robust solve of T x_j = b_j for every column of B (T upper
+    quasi-triangular, CUDA tensors, column-major).  Returns (X, scale_exp)
+    with x_j = X[:, j] * 2**(-scale_exp[j]), |X[:, j]|_inf in [1, 2); out =
+    (X, e) to write into (X may be B for an in-place solve)."""
+    import torch
+    n = T.shape[0]
+    ldt = _check_colmajor(T, "T", n)
+    if B.dim() == 1:
+        B = B.view(n, 1)
+    nrhs = B.shape[1]
+    ldb = _check_colmajor(B, "B", n, nrhs)
+    h = handle(T.device.index)
+    if out is not None:
+        X, e = out
+        if X.dim() == 1:
+            X = X.view(n, 1)
+        if e.dtype != torch.int32 or not e.is_cuda or e.numel() < nrhs:
+            raise ValueError(f"scale_exp must be an int32 CUDA vector of {nrhs} entries")
+    else:
+        X = torch.empty((nrhs, n), dtype=torch.float64, device=T.device).t()
+        e = torch.empty(nrhs, dtype=torch.int32, device=T.device)
+    ldx = _check_colmajor(X, "X", n, nrhs)
+    if n == 0 or nrhs == 0:
+        return X, e
+    opts = _opts(tile, False, mode, slices)
+    st = lib().evec_trsolve(h.ptr, n, T.data_ptr(), ldt, nrhs, B.data_ptr(), ldb, X.data_ptr(),
+                            ldx, e.data_ptr(), ctypes.byref(opts))
+    _check(st, "evec_trsolve")
+    if check:
+        h.sync()
+    return X, e
 
 
 def standard_host(T, Q=None, select=None, tile: int = 0, device: int = 0,

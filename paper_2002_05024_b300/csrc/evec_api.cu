@@ -42,6 +42,8 @@ void launch_residual(const double *T, int64_t ldt, const Plan &p, int ntiles, in
                      const int32_t *row_tile, double *R, int64_t ldr, cudaStream_t st);
 void launch_rhs_init(const Plan &p, const double *R, int64_t ldr, double *seg_nu,
                      cudaStream_t st);
+void launch_check_rhs(const double *B, int64_t ldb, int64_t n, int64_t nrhs, int64_t base,
+                      DevStatus *status, cudaStream_t st);
 void launch_refine_combine(const Plan &p, double *Y, int64_t ldy, const int32_t *ey,
                            const double *D, int64_t ldd, const int32_t *ed, int max_rel,
                            cudaStream_t st);
@@ -398,6 +400,91 @@ static evec_status build_plan(int64_t n, const double *diag, const double *sub,
             P.tile_cplx[tt] = (int32_t)ic;
         }
     }
+    return EVEC_OK;
+}
+
+// Plan of the robust triangular solve T x_j = b_j (evec_trsolve): T's block
+// structure and tiles as for the eigenvectors (a 2x2 block in any form),
+// and one real unit per right-hand side with shift 0, active in every tile:
+// its "own" tile is the last and its own block a sentinel past the last
+// block (start n, size 0), so every diagonal block is solved and the
+// segments run down to row n.
+static evec_status build_solve_plan(int64_t n, const double *diag, const double *sub,
+                                    const double *sup, int64_t nrhs, int nb, int64_t ld_report,
+                                    HostPlan &P, int64_t *bad) {
+    P.reset();
+    P.n = n;
+    P.nb = nb;
+    for (int64_t i = 0; i < n; i++) {
+        evec_status st = check_value(diag[i], i + i * ld_report, bad);
+        if (st) return st;
+        if (i + 1 < n) {
+            st = check_value(sub[i], (i + 1) + i * ld_report, bad);
+            if (st) return st;
+            st = check_value(sup[i], i + (i + 1) * ld_report, bad);
+            if (st) return st;
+        }
+    }
+    std::vector<int8_t> in_pair_second(n, 0);
+    for (int64_t i = 0; i < n;) {
+        if (i + 1 < n && sub[i] != 0.0) {
+            if (i + 2 < n && sub[i + 1] != 0.0) { if (bad) *bad = i + 1; return EVEC_ENOTSCHUR; }
+            P.blk_start.push_back((int32_t)i);
+            P.blk_size.push_back(2);
+            in_pair_second[i + 1] = 1;
+            i += 2;
+        } else {
+            P.blk_start.push_back((int32_t)i);
+            P.blk_size.push_back(1);
+            i += 1;
+        }
+    }
+    const int64_t nblk = (int64_t)P.blk_start.size();
+    P.tile_start.push_back(0);
+    while (P.tile_start.back() < n) {
+        int64_t b = P.tile_start.back() + nb;
+        if (b >= n) b = n;
+        else if (in_pair_second[b]) b -= 1;
+        P.tile_start.push_back((int32_t)b);
+    }
+    const int N = (int)P.tile_start.size() - 1;
+    P.max_tile = 0;
+    for (int t = 0; t < N; t++)
+        P.max_tile = std::max(P.max_tile, P.tile_start[t + 1] - P.tile_start[t]);
+    P.tile_blk.assign(N + 1, 0);
+    {
+        int t = 0;
+        for (int64_t k = 0; k < nblk; k++)
+            while (P.blk_start[k] >= P.tile_start[t + 1]) { t++; P.tile_blk[t] = (int32_t)k; }
+        for (int tt = t + 1; tt <= N; tt++) P.tile_blk[tt] = (int32_t)nblk;
+    }
+    P.blk_start.push_back((int32_t)n);   // the sentinel own block of every unit
+    P.blk_size.push_back(0);
+    P.tile_unit.assign(N + 1, 0);
+    P.tile_col.assign(N + 1, 0);
+    P.tile_unit[N] = (int32_t)nrhs;
+    P.tile_col[N] = (int32_t)nrhs;
+    P.tile_real.assign(N + 1, 0);
+    P.tile_cplx.assign(N + 1, 0);
+    P.tile_real[N] = (int32_t)nrhs;
+    for (int64_t j = 0; j < nrhs; j++) {
+        P.unit_col.push_back((int32_t)j);
+        P.unit_blk.push_back((int32_t)nblk);
+        P.unit_tile.push_back(N - 1);
+        P.unit_lam.push_back(0.0);
+        P.unit_lam.push_back(0.0);
+        P.unit_own.insert(P.unit_own.end(), {0.0, 0.0, 0.0, 0.0});
+        P.col_unit.push_back((int32_t)j);
+        P.col_lam_re.push_back(0.0);
+        P.col_lam_im.push_back(0.0);
+        P.ord_real.push_back((int32_t)j);
+    }
+    P.m = nrhs;
+    P.row_tile.resize(n);
+    for (int tt = 0; tt < N; tt++)
+        for (int32_t i = P.tile_start[tt]; i < P.tile_start[tt + 1]; i++) P.row_tile[i] = tt;
+    for (int64_t j0 = 0; j0 < P.m; j0 += kSplitColTile)
+        P.bt_kend.push_back((int32_t)((n + 31) / 32 * 32));
     return EVEC_OK;
 }
 
@@ -895,6 +982,54 @@ static void split_panel_layout(HostPlan &P, int slices) {
     P.panel_rows = rows;
 }
 
+// The tiled robust solve over Y, steps s = N-1 .. 0: diagonal-tile solves
+// and decisions, then the update of the rows above in FP64 or as split
+// products (rhs: Y holds a right-hand side with its segments initialised,
+// and no own block is placed).
+static evec_status sweep_steps(evec_handle h, const HostPlan &HP, const Plan &dp,
+                               const double *T, int64_t ldt, double *Y, int64_t ldy, bool rhs,
+                               int mode, const SplitUpdateCtx &sctx, cudaStream_t st) {
+    const int N = (int)HP.tile_start.size() - 1;
+    const int64_t m = HP.m;
+    for (int s = N - 1; s >= 0; s--) {
+        timed(h, EVEC_K_DIAG_SOLVE, [&] {
+            return launch_diag_solve(s, T, ldt, dp, HP.tile_start.data(), HP.tile_real.data(),
+                                     HP.tile_cplx.data(), h->tau, h->blk_tau, Y, ldy, h->seg_e,
+                                     h->seg_nu, h->seg_dx, h->seg_dy, st, nullptr, rhs);
+        });
+        if (s > 0 && HP.tile_col[s] < m) {
+            if (mode == EVEC_SPLIT) {
+                cudaError_t ce = cudaSuccess;
+                timed(h, EVEC_K_TILE_UPDATE, [&] {
+                    if (sctx.Kp == 64) {   // slicing + panel-resident product
+                        ce = split_update_step_resident(
+                            sctx, HP.tile_start[s], HP.tile_start[s + 1] - HP.tile_start[s],
+                            HP.prow0[s], HP.pea[s], HP.tile_col[s], (int)m, Y, ldy,
+                            h->ea_panels, h->slB, h->eb, h->row_tile_d, h->seg_dx, h->seg_dy,
+                            h->seg_nu, &h->status_d->timeout, h->nsm, st);
+                        return 2;
+                    }
+                    // column maxima + slicing + streamed product
+                    ce = split_update_step(sctx, HP.tile_start[s],
+                                           HP.tile_start[s + 1] - HP.tile_start[s], HP.prow0[s],
+                                           HP.pea[s], HP.tile_col[s], (int)m, Y, ldy, h->ea_panels,
+                                           h->slB, h->cmax, h->eb, h->row_tile_d, h->seg_dx,
+                                           h->seg_dy, h->seg_nu, &h->status_d->timeout, st);
+                    return 3;
+                });
+                EVEC_CUDA(ce);
+            } else {
+                timed(h, EVEC_K_TILE_UPDATE, [&] {
+                    launch_tile_update(s, T, ldt, dp, HP.max_tile, HP.tile_col.data(), Y, ldy,
+                                       h->seg_dx, h->seg_dy, h->seg_nu, st);
+                    return 1;
+                });
+            }
+        }
+    }
+    return EVEC_OK;
+}
+
 evec_status evec_standard(evec_handle h, int64_t n, const double *T, int64_t ldt,
                           const double *Q, int64_t ldq, const uint8_t *select_host,
                           double *X, int64_t ldx, int32_t *scale_exp, double *lam_re,
@@ -991,46 +1126,8 @@ evec_status evec_standard(evec_handle h, int64_t n, const double *T, int64_t ldt
         });
         EVEC_CUDA(ce);
     }
-    // the tiled robust solve over Y (rhs: Y holds a right-hand side with
-    // its segments initialised, no own blocks are placed)
-    auto sweep = [&](double *Y, int64_t ldy, bool rhs) -> evec_status {
-    for (int s = N - 1; s >= 0; s--) {
-        timed(h, EVEC_K_DIAG_SOLVE, [&] {
-            return launch_diag_solve(s, T, ldt, dp, HP.tile_start.data(), HP.tile_real.data(),
-                              HP.tile_cplx.data(), h->tau, h->blk_tau, Y, ldy, h->seg_e,
-                              h->seg_nu, h->seg_dx, h->seg_dy, st, nullptr, rhs);
-        });
-        if (s > 0 && HP.tile_col[s] < m) {
-            if (mode == EVEC_SPLIT) {
-                cudaError_t ce = cudaSuccess;
-                timed(h, EVEC_K_TILE_UPDATE, [&] {
-                    if (sctx.Kp == 64) {   // slicing + panel-resident product
-                        ce = split_update_step_resident(
-                            sctx, HP.tile_start[s], HP.tile_start[s + 1] - HP.tile_start[s],
-                            HP.prow0[s], HP.pea[s], HP.tile_col[s], (int)m, Y, ldy,
-                            h->ea_panels, h->slB, h->eb, h->row_tile_d, h->seg_dx, h->seg_dy,
-                            h->seg_nu, &h->status_d->timeout, h->nsm, st);
-                        return 2;
-                    }
-                    // column maxima + slicing + streamed product
-                    ce = split_update_step(sctx, HP.tile_start[s],
-                                           HP.tile_start[s + 1] - HP.tile_start[s], HP.prow0[s],
-                                           HP.pea[s], HP.tile_col[s], (int)m, Y, ldy, h->ea_panels,
-                                           h->slB, h->cmax, h->eb, h->row_tile_d, h->seg_dx,
-                                           h->seg_dy, h->seg_nu, &h->status_d->timeout, st);
-                    return 3;
-                });
-                EVEC_CUDA(ce);
-            } else {
-                timed(h, EVEC_K_TILE_UPDATE, [&] {
-                    launch_tile_update(s, T, ldt, dp, HP.max_tile, HP.tile_col.data(), Y, ldy,
-                                       h->seg_dx, h->seg_dy, h->seg_nu, st);
-                    return 1;
-                });
-            }
-        }
-    }
-    return EVEC_OK;
+    auto sweep = [&](double *Yb, int64_t ldyb, bool rhs) {
+        return sweep_steps(h, HP, dp, T, ldt, Yb, ldyb, rhs, mode, sctx, st);
     };
     EVEC_TRY(sweep(Y, ldy, false));
     if (refine) {   // residual-correction sweep on the solved segments
@@ -1144,6 +1241,102 @@ evec_status evec_standard(evec_handle h, int64_t n, const double *T, int64_t ldt
     if (lam_im)
         EVEC_CUDA(cudaMemcpyAsync(lam_im, h->plan_h + m * 8, m * 8,
                                   cudaMemcpyHostToDevice, st));
+    if (opt && opt->check) return evec_sync(h, nullptr);
+    return EVEC_OK;
+}
+
+// Robust triangular solve with many right-hand sides (the xLATRS
+// generalisation the eigenvector solve rests on, Sec. 3.4): the same tiled
+// steps with shift 0 and the right-hand sides as the starting segments.
+evec_status evec_trsolve(evec_handle h, int64_t n, const double *T, int64_t ldt, int64_t nrhs,
+                         const double *B, int64_t ldb, double *X, int64_t ldx,
+                         int32_t *scale_exp, const evec_opts *opt) {
+    if (!h || n < 0 || nrhs < 0 || nrhs > INT32_MAX || !ld_ok(ldt, n) || !ld_ok(ldb, n) ||
+        !ld_ok(ldx, n))
+        return EVEC_EINVAL;
+    const int mode = opt ? opt->mode : EVEC_FP64;
+    if (mode != EVEC_FP64 && mode != EVEC_SPLIT) return EVEC_EINVAL;
+    const int slices = (opt && opt->slices) ? opt->slices : 8;
+    if (slices < 2 || slices > 8) return EVEC_EINVAL;
+    const int nb = resolve_tile(opt);
+    if (nb < 16 || nb > kMaxTile) return EVEC_EINVAL;
+    if (n == 0 || nrhs == 0) return EVEC_OK;
+    if (!T || !B || !X || !scale_exp) return EVEC_EINVAL;
+    DeviceGuard g(h->device);
+    if (!g.ok) return EVEC_ECUDA;
+    cudaStream_t st = h->stream;
+
+    // T's three central diagonals -> the plan (any 2x2 block form)
+    const size_t cnt = (size_t)(3 * n > 2 ? 3 * n - 2 : 1);
+    EVEC_TRY(grow_device(&h->diag_d, &h->diag_cap, cnt));
+    EVEC_TRY(grow_host(&h->diag_h, &h->diag_h_cap, cnt));
+    timed(h, EVEC_K_GATHER, [&] {
+        launch_gather_diagonals(T, ldt, n, h->diag_d, st);
+        return 1;
+    });
+    EVEC_CUDA(cudaGetLastError());
+    EVEC_CUDA(cudaMemcpyAsync(h->diag_h, h->diag_d, cnt * sizeof(double), cudaMemcpyDeviceToHost,
+                              st));
+    EVEC_CUDA(cudaStreamSynchronize(st));
+    h->pkey.valid = false;   // h->plan now holds a solve plan
+    int64_t bad = -1;
+    const double *d = h->diag_h;
+    EVEC_TRY(build_solve_plan(n, d, d + n, d + 2 * n - 1, nrhs, nb, ldt, h->plan, &bad));
+    const HostPlan &HP = h->plan;
+    const int64_t m = HP.m;
+    const int N = (int)HP.tile_start.size() - 1;
+    split_panel_layout(h->plan, mode == EVEC_SPLIT ? slices : 0);
+    Plan dp;
+    EVEC_TRY(upload_plan(h, dp));
+
+    const size_t segs = (size_t)N * (size_t)m;
+    EVEC_TRY(grow_device(&h->seg_e, &h->segi_cap[0], segs));
+    EVEC_TRY(grow_device(&h->seg_dx, &h->segi_cap[1], segs));
+    EVEC_TRY(grow_device(&h->seg_dy, &h->segi_cap[2], segs));
+    EVEC_TRY(grow_device(&h->seg_nu, &h->segn_cap, segs));
+    EVEC_TRY(grow_device(&h->tau, &h->tau_cap, (size_t)N * (size_t)N));
+    EVEC_TRY(grow_device(&h->blk_tau, &h->blk_tau_cap, HP.blk_start.size()));
+    timed(h, EVEC_K_NORMS, [&] {
+        launch_tile_norms(T, ldt, dp, h->tau, h->blk_tau, h->status_d, st);
+        launch_check_rhs(B, ldb, n, nrhs, ldt * n, h->status_d, st);
+        return 2;
+    });
+    // the right-hand sides are the starting segments: exponent 0, their
+    // maxima per tile
+    if (X != B || ldx != ldb)
+        EVEC_CUDA(cudaMemcpy2DAsync(X, ldx * sizeof(double), B, ldb * sizeof(double),
+                                    n * sizeof(double), nrhs, cudaMemcpyDeviceToDevice, st));
+    EVEC_CUDA(cudaMemsetAsync(h->seg_e, 0, segs * sizeof(int32_t), st));
+    timed(h, EVEC_K_REFINE, [&] {
+        launch_rhs_init(dp, X, ldx, h->seg_nu, st);
+        return 1;
+    });
+    SplitUpdateCtx sctx;
+    if (mode == EVEC_SPLIT) {
+        const int Kp = HP.max_tile <= 64 ? 64 : 128;
+        const int Np = split_pad_n((int)m);
+        EVEC_TRY(grow_device(&h->panels, &h->panels_cap,
+                             (size_t)std::max(HP.panel_rows, 128) * Kp));
+        EVEC_TRY(grow_device(&h->ea_panels, &h->ea_panels_cap,
+                             (size_t)std::max(HP.pea[N], 1)));
+        EVEC_TRY(grow_device(&h->slB, &h->slB_cap, (size_t)slices * Np * Kp));
+        EVEC_TRY(grow_device(&h->cmax, &h->cmax_cap, (size_t)Np));
+        EVEC_TRY(grow_device(&h->eb, &h->eb_cap, (size_t)Np));
+        cudaError_t ce = cudaSuccess;
+        timed(h, EVEC_K_TILE_UPDATE, [&] {
+            ce = split_update_prepare(T, ldt, nullptr, 0, (int)n, N, HP.max_tile, dp.tile_start,
+                                      h->prow0_d, h->pea_d, HP.panel_rows, slices, (int)m,
+                                      h->panels, h->ea_panels, h->slB, &sctx, st);
+            return N > 1 ? 1 : 0;
+        });
+        EVEC_CUDA(ce);
+    }
+    EVEC_TRY(sweep_steps(h, HP, dp, T, ldt, X, ldx, true, mode, sctx, st));
+    timed(h, EVEC_K_FINALIZE, [&] {
+        launch_finalize(dp, X, ldx, h->seg_e, scale_exp, st);
+        return 1;
+    });
+    EVEC_CUDA(cudaGetLastError());
     if (opt && opt->check) return evec_sync(h, nullptr);
     return EVEC_OK;
 }

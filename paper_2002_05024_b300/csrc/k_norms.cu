@@ -6,6 +6,8 @@
 // bounds the in-tile update from diagonal block k (start q).  The kernel
 // also validates every referenced entry (finite, |t| <= 2^1000).
 // Reads the upper triangle of T once: HBM-bound, n (n + 1) / 2 * 8 bytes.
+#include <algorithm>
+
 #include "evec_internal.cuh"
 
 namespace evec {
@@ -126,6 +128,28 @@ __global__ void __launch_bounds__(128) k_tile_norms(const double *__restrict__ T
         }
         mx = warp_max(mx);
         if (lane == 0) blk_tau[k] = mx;
+    }
+}
+
+// Validation of the right-hand sides of the triangular solve: every entry
+// of B (n x nrhs, ld ldb) finite and at most 2^1000 in magnitude; an entry
+// is reported as ldt n + i + j ldb (B placed after T).
+__global__ void k_check_rhs(const double *__restrict__ B, int64_t ldb, int64_t n, int64_t nrhs,
+                            int64_t base, DevStatus *status) {
+    const int64_t j = blockIdx.y;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        check_entry(B[i + j * ldb], (long long)(base + i + j * ldb), status);
+}
+
+void launch_check_rhs(const double *B, int64_t ldb, int64_t n, int64_t nrhs, int64_t base,
+                      DevStatus *status, cudaStream_t st) {
+    if (n <= 0 || nrhs <= 0) return;
+    const unsigned gx = (unsigned)std::min<int64_t>((n + 255) / 256, 64);
+    for (int64_t j0 = 0; j0 < nrhs; j0 += 65535) {
+        const unsigned gy = (unsigned)std::min<int64_t>(nrhs - j0, 65535);
+        k_check_rhs<<<dim3(gx, gy), 256, 0, st>>>(B + j0 * ldb, ldb, n, gy,
+                                                  base + j0 * ldb, status);
     }
 }
 
