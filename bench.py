@@ -63,10 +63,13 @@ def parse_args():
     ap.add_argument("--cpu-sample", type=int, default=4096,
                     help="columns of the CPU-oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["single", "batched", "generalized"], default="single",
+    ap.add_argument("--workload", choices=["single", "batched", "generalized", "trsolve"],
+                    default="single",
                     help="single: one n x n Schur form with Q (default); batched: the "
                          "2000-matrix batch of evec_batched; generalized: an n x n pencil "
-                         "(S, T) with Z (use --n 8192)")
+                         "(S, T) with Z (use --n 8192); trsolve: robust solve of an n x n "
+                         "quasi-triangular T with --nrhs right-hand sides")
+    ap.add_argument("--nrhs", type=int, default=0, help="trsolve: right-hand sides (default n)")
     ap.add_argument("--batch", type=int, default=2000)
     return ap.parse_args()
 
@@ -129,12 +132,13 @@ def source_digest(files):
     return h.hexdigest()[:16]
 
 
-def stored_traffic(kernel, mode, n, tile):
+def stored_traffic(kernel, mode, n, tile, prefix=""):
     """DRAM bytes per launch from the committed ncu summary, or None when
     there is none for this kernel, workload and mode, or when the kernel's
-    source changed since the capture."""
+    source changed since the capture (prefix: "" for the eigenvector
+    workload, "trsolve:" for the triangular solve)."""
     try:
-        rec = json.load(open(TRAFFIC))[f"{kernel}/{mode}/n{n}/tile{tile}"]
+        rec = json.load(open(TRAFFIC))[f"{prefix}{kernel}/{mode}/n{n}/tile{tile}"]
     except Exception:
         return None
     files = KERNEL_SOURCES.get((kernel, mode))
@@ -144,7 +148,7 @@ def stored_traffic(kernel, mode, n, tile):
 
 
 def rooflines(prof, steps, mode, slices, F_diag, F_upd, F_bt, peaks, n, tile, F_res=0.0,
-              sweeps=1):
+              sweeps=1, prefix=""):
     """Per kernel class: algorithmic work per step / event-timed kernel time
     per step against the unit that bounds it.  Diagonal solves and FP64-mode
     GEMMs: FP64 flops on the FP64 pipe ("alu"; peak from the measured DFMA
@@ -175,7 +179,7 @@ def rooflines(prof, steps, mode, slices, F_diag, F_upd, F_bt, peaks, n, tile, F_
             alg, peak, bound, src = f64, fp64_peak, "alu", \
                 "of derived FP64 peak (measured 4 flop/clk/SM x 148 SMs x max SM clock)"
         achieved = alg / sec / 1e12
-        tr = stored_traffic(k, mode, n, tile)
+        tr = stored_traffic(k, mode, n, tile, prefix)
         out[k] = {"kernel": k, "bound": bound, "achieved": achieved, "peak": peak,
                   "unit": "TFLOP/s", "frac": achieved / peak, "traffic": tr,
                   "peak_source": src, "launches_per_step": nl / steps,
@@ -328,9 +332,41 @@ def residual_sample(T, Q, X, lr, li, blocks, k=16, seed=7):
             "max_over_n": worst / n, "gate": "<= 10 n"}
 
 
+def run_reference_trsolve(args):
+    n = args.n
+    nrhs = args.nrhs or n
+    T, _, B = workloads.solve_system(n, nrhs)
+    per_step = max(16, args.cpu_sample // 4)
+    times, cols = [], []
+    for i in range(args.warmup + args.steps):
+        r = trsolve_cpu_baseline(T, B, per_step, seed=1000 + i)
+        if i >= args.warmup:
+            cols.append(r["columns"])
+            times.append(r["seconds"])
+    value = sum(cols) / sum(times)
+    line = {
+        "impl": "reference",
+        "metric": "right-hand sides/s (robust FP64 triangular solve with per-column scaling)",
+        "value": value, "unit": "right-hand sides/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"quasi-triangular T n={n}, B n x {nrhs} (oracle samples)"},
+        "cpu_baseline": {"value": value, "unit": "right-hand sides/s", "cores": r["cores"],
+                         "kind": "oracle",
+                         "sample": f"{per_step} random right-hand sides per step of the "
+                                   f"n={n} system, on the host cores"},
+        "e2e": {"value": value, "unit": "right-hand sides/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
+    if args.workload == "trsolve":
+        return run_reference_trsolve(args)
     T, blocks, Q = workload(args.n)
     per_step = max(16, args.cpu_sample // 4)
     times, cols = [], []
@@ -826,6 +862,209 @@ def run_generalized(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+def solve_tiles(n, sub, nb):
+    """Tile boundaries of the solve (rows; a 2x2 block is never cut): the
+    plan's own rule, restated for the flop accounting."""
+    ts = [0]
+    while ts[-1] < n:
+        b = ts[-1] + nb
+        if b >= n:
+            b = n
+        elif sub[b - 1] != 0.0:   # b is the second row of a 2x2 block
+            b -= 1
+        ts.append(b)
+    return ts
+
+
+def trsolve_cpu_baseline(T, B, cols, seed=5, gpu=None):
+    """The oracle's robust triangular solve, as it stands, on `cols` seeded
+    random right-hand sides of the workload, on all host cores; with gpu =
+    (X, scale_exp) the sampled columns are compared with the GPU's."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    nrhs = B.shape[1]
+    pick = np.sort(rng.choice(nrhs, size=min(cols, nrhs), replace=False))
+    Bs = np.asfortranarray(B[:, pick])
+    oracle.build()
+    t = time.perf_counter()
+    X, e = oracle.trsolve(T, Bs)
+    dt = time.perf_counter() - t
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    out = {"value": len(pick) / dt, "unit": "right-hand sides/s",
+           "cores": int(os.environ.get("OMP_NUM_THREADS", cores)), "kind": "oracle",
+           "columns": len(pick), "seconds": dt,
+           "sample": f"{len(pick)} randomly chosen right-hand sides (seed {seed}) of the "
+                     f"n={T.shape[0]} system, {dt:.2f} s"}
+    if gpu is not None:
+        Xg, eg = gpu
+        de = e.astype(np.int64) - eg[pick].astype(np.int64)
+        a = X
+        b = np.ldexp(Xg[:, pick], de[None, :])
+        rel = np.abs(a - b).max(axis=0) / np.maximum(np.abs(a).max(axis=0), 1e-300)
+        out["gpu_vs_oracle"] = {"columns": len(pick), "max_exponent_diff": int(np.abs(de).max()),
+                                "max_rel_diff": float(rel.max())}
+    return out
+
+
+def run_trsolve(args, rank, world, local_rank):
+    """The robust triangular solve T X = B diag(2^scale_exp)^-1 with many
+    right-hand sides: T the n x n quasi-triangular system of
+    workloads.solve_system (config-0 block structure, well conditioned), B
+    n x nrhs N(0, 1).  Algorithmic flops n^2 per right-hand side (one
+    multiply-add per entry of the strictly upper part, one division per
+    row), of which the tile updates do 2 r_s b_s for tile s (r_s rows above
+    it, b_s its rows) and the diagonal-tile solves the rest."""
+    import torch
+
+    import paper_2002_05024_b300 as ev
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    n = args.n
+    nrhs = args.nrhs or n
+    T, blocks, B = workloads.solve_system(n, nrhs)
+    tile = args.tile or 64
+    ts = solve_tiles(n, np.diagonal(T, -1), tile)
+    F = float(n) * n * nrhs
+    F_upd = sum(2.0 * ts[s] * (ts[s + 1] - ts[s]) for s in range(1, len(ts) - 1)) * nrhs
+    F_diag = F - F_upd
+    dT = torch.from_numpy(T).to(dev)
+    dB = torch.from_numpy(B).to(dev)
+    X = torch.empty((nrhs, n), dtype=torch.float64, device=dev).t()
+    e = torch.empty(nrhs, dtype=torch.int32, device=dev)
+
+    def step():
+        ev.trsolve(dT, dB, tile=args.tile, mode=args.mode, slices=args.slices, out=(X, e))
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    ev.sync(local_rank)
+    h = ev.handle(local_rank)
+    gpu_id = None
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    sampler = ClockSampler(gpu_id) if rank == 0 else None
+    if dist:
+        dist.barrier()
+    stream = torch.cuda.current_stream(dev)
+    torch.cuda.synchronize(dev)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        step()
+    t1.record(stream)
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    elapsed = t0.elapsed_time(t1)
+    clocks = sampler.stop() if sampler else None
+    ev.sync(local_rank)
+    prof = profiled_steps(h, step, args.steps, dev)
+    if dist:
+        tt = torch.tensor([elapsed], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        elapsed = float(tt.item())
+    peaks = measured_peaks()
+    slices = (args.slices or 8) if args.mode == "split" else 0
+    roofs = rooflines(prof, args.steps, args.mode, slices, F_diag, F_upd, 0.0, peaks, n, tile,
+                      prefix="trsolve:")
+    dominant = max(prof.items(), key=lambda kv: kv[1][0])[0]
+
+    # end to end through the public call: T and B from pinned host memory,
+    # X and the exponents back, every step
+    e2e = None
+    if not os.environ.get("EVEC_BENCH_NO_E2E"):
+        hT = torch.empty((n, n), dtype=torch.float64, pin_memory=True).t()
+        hT.copy_(torch.from_numpy(T))
+        hB = torch.empty((nrhs, n), dtype=torch.float64, pin_memory=True).t()
+        hB.copy_(torch.from_numpy(B))
+        hX = torch.empty((nrhs, n), dtype=torch.float64, pin_memory=True).t()
+        hE = torch.empty(nrhs, dtype=torch.int32, pin_memory=True)
+
+        def host_step():
+            dT.copy_(hT, non_blocking=True)
+            dB.copy_(hB, non_blocking=True)
+            step()
+            hX.copy_(X, non_blocking=True)
+            hE.copy_(e, non_blocking=True)
+            torch.cuda.synchronize(dev)
+
+        for _ in range(args.warmup):
+            host_step()
+        if dist:
+            dist.barrier()
+        w0 = time.perf_counter()
+        for _ in range(args.steps):
+            host_step()
+        w = time.perf_counter() - w0
+        if dist:
+            tt = torch.tensor([w], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            w = float(tt.item())
+        e2e = {"value": world * nrhs * args.steps / w, "unit": "right-hand sides/s",
+               "h2d_bytes_per_step": 8 * n * (n + nrhs),
+               "d2h_bytes_per_step": 8 * n * nrhs + 4 * nrhs}
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    Xh, eh = X.cpu().numpy(), e.cpu().numpy()
+    # normalised residual ||T x - b||_1 / (||T||_1 ||x||_1 u) of 16 sampled
+    # right-hand sides, in long double
+    rng = np.random.default_rng(7)
+    Tl = T.astype(np.longdouble)
+    T1 = np.abs(Tl).sum(axis=0).max()
+    worst = 0.0
+    for j in rng.choice(nrhs, size=min(16, nrhs), replace=False):
+        x = np.ldexp(Xh[:, j], -int(eh[j])).astype(np.longdouble)
+        r = Tl @ x - B[:, j].astype(np.longdouble)
+        worst = max(worst, float(np.abs(r).sum() / (T1 * np.abs(x).sum() * 2.0 ** -53)))
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = trsolve_cpu_baseline(T, B, args.cpu_sample, gpu=(Xh, eh))
+        cpu.pop("columns")
+        cpu.pop("seconds")
+    line = {
+        "metric": "right-hand sides/s (robust FP64 triangular solve with per-column scaling)",
+        "value": world * nrhs * args.steps / (elapsed / 1e3), "unit": "right-hand sides/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": elapsed / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64" if args.mode == "fp64" else "bf16 slice products + f64",
+        "data": "synthetic",
+        "config": {"workload": f"quasi-triangular T n={n} (config-0 blocks, well conditioned), "
+                               f"B n x {nrhs} N(0, 1), "
+                               + ("FP64" if args.mode == "fp64" else
+                                  f"split precision ({slices} BF16 slices)"),
+                   "n": n, "nrhs": nrhs, "tile": tile, "mode": args.mode,
+                   "slices": slices or None, "parallelism": "replicas",
+                   "l2": f"inputs larger than L2 (T {8 * n * n >> 20} MiB, B and X "
+                         f"{8 * n * nrhs >> 20} MiB each)"},
+        "tflops_fp64": F * args.steps / (elapsed / 1e3) / 1e12,
+        "flops_per_step": F,
+        "quality": {"right_hand_sides": int(min(16, nrhs)), "max_normalised_residual": worst,
+                    "max_over_n": worst / n, "gate": "<= 10 n"},
+        "roofline": roofs.get(dominant),
+        "rooflines": roofs,
+        "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+        "gpu_launches": sum(c for _, c in prof.values()),
+        "clocks": clocks,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
 def main():
     args = parse_args()
     rank = int(os.environ.get("RANK", 0))
@@ -837,6 +1076,8 @@ def main():
         run_batched(args, rank, world, local_rank)
     elif args.workload == "generalized":
         run_generalized(args, rank, world, local_rank)
+    elif args.workload == "trsolve":
+        run_trsolve(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 

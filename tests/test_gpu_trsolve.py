@@ -17,18 +17,7 @@ pytestmark = pytest.mark.gpu
 
 
 def _well_conditioned(n, seed):
-    # config-0 block structure; 1x1 pivots moved to [1, 2) in magnitude,
-    # 2x2 blocks shifted and made non-standard, upper part N(0, 1/n)
-    T, blocks = workloads.config0_schur(n, seed=seed)
-    rng = np.random.default_rng(seed + 1)
-    iu = np.triu_indices(n, 1)
-    T[iu] /= np.sqrt(n)
-    for p, sz in blocks:
-        if sz == 1:
-            T[p, p] = np.sign(T[p, p] or 1.0) * (1.0 + abs(T[p, p]))
-        else:
-            T[p, p] += 1.5
-            T[p + 1, p + 1] += 1.5 + rng.uniform(0.0, 0.25)
+    T, blocks, _ = workloads.solve_system(n, 0, seed=seed)
     return T, blocks
 
 
@@ -153,8 +142,7 @@ def test_trsolve_full_size_sampled(mode):
     # the benchmark's solve: n = 4096, 4096 right-hand sides, tile 64; 24
     # sampled columns against the oracle
     n = 4096
-    T, _ = _well_conditioned(n, seed=workloads.SEED_BASE + 7)
-    B = np.random.default_rng(workloads.SEED_BASE + 8).standard_normal((n, n))
+    T, _, B = workloads.solve_system(n, n)
     X, e = _gpu(T, B, tile=0, mode=mode)
     assert np.isfinite(X).all()
     cols = np.sort(np.random.default_rng(9).choice(n, 24, replace=False))

@@ -16,4 +16,5 @@ from .schur_inputs import (  # noqa: F401
     generalized_pair,
     householder_orthogonal,
     random_eigen_selection,
+    solve_system,
 )

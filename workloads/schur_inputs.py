@@ -153,6 +153,28 @@ def generalized_pair(n: int, seed: int = SEED_BASE + 4):
     return S, T, blocks
 
 
+def solve_system(n: int, nrhs: int, seed: int = SEED_BASE + 7):
+    """A quasi-triangular system T X = B for the robust triangular solve:
+    the config-0 block structure, 1x1 pivots moved to magnitude [1, 2)
+    (sign kept), 2x2 blocks shifted by 1.5 on the diagonal with the second
+    entry a further U[0, 0.25] up (no longer in standard form), the strictly
+    upper part scaled to N(0, 1/n) so that T is well conditioned; B is
+    N(0, 1), n x nrhs, column-major."""
+    rng = _rng(seed)
+    T, blocks = config0_schur(n, seed=int(rng.integers(1 << 62)))
+    iu = np.triu_indices(n, 1)
+    T[iu] /= np.sqrt(n)
+    shift = rng.uniform(0.0, 0.25, size=n)
+    for p, sz in blocks:
+        if sz == 1:
+            T[p, p] = (1.0 if T[p, p] >= 0 else -1.0) * (1.0 + abs(T[p, p]))
+        else:
+            T[p, p] += 1.5
+            T[p + 1, p + 1] += 1.5 + shift[p]
+    B = np.asfortranarray(rng.standard_normal((n, nrhs)))
+    return T, blocks, B
+
+
 def random_eigen_selection(n: int, blocks, fraction: float, seed: int):
     """Eigenvalue selection mask (uint8, length n): ``fraction`` of the
     eigenvalues chosen uniformly at random (the paper's experiment picks 35%
