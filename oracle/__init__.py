@@ -69,6 +69,8 @@ class Oracle:
         lib.evo_standard.argtypes = [i64, p, i64, p, i64, p, p, i64, p, p, p,
                                      ctypes.c_int, p]
         lib.evo_standard.restype = ctypes.c_int
+        lib.evo_standard_left.argtypes = lib.evo_standard.argtypes
+        lib.evo_standard_left.restype = ctypes.c_int
         lib.evo_generalized.argtypes = [i64, p, i64, p, i64, p, i64, p, p, i64,
                                         p, p, p, p, ctypes.c_int, p]
         lib.evo_generalized.restype = ctypes.c_int
@@ -90,9 +92,11 @@ class Oracle:
             raise OracleError(st, int(bad[0]))
         return int(m[0])
 
-    def standard(self, S, Q=None, select=None, threads: int = 0):
+    def standard(self, S, Q=None, select=None, threads: int = 0, left: bool = False):
         """Eigenvectors of the quasi-triangular S (optionally back-transformed
-        by Q).  Returns (X, scale_exp, lam_re, lam_im)."""
+        by Q).  Returns (X, scale_exp, lam_re, lam_im).  left: the left
+        eigenvectors, u^H S = lambda u^H (pairs: columns Re u, Im u for
+        lambda = a + i w, w > 0), zero above their block."""
         S = _fortran(S)
         n = S.shape[0]
         sel = _mask(select, n)
@@ -103,9 +107,9 @@ class Oracle:
         li = np.zeros(m)
         Qf = None if Q is None else _fortran(Q)
         bad = np.full(1, -1, dtype=np.int64)
-        st = self.lib.evo_standard(n, _ptr(S), max(n, 1), _ptr(Qf), max(n, 1), _ptr(sel),
-                                   _ptr(X), max(n, 1), _ptr(e), _ptr(lr), _ptr(li),
-                                   int(threads), _ptr(bad))
+        fn = self.lib.evo_standard_left if left else self.lib.evo_standard
+        st = fn(n, _ptr(S), max(n, 1), _ptr(Qf), max(n, 1), _ptr(sel), _ptr(X), max(n, 1),
+                _ptr(e), _ptr(lr), _ptr(li), int(threads), _ptr(bad))
         if st:
             raise OracleError(st, int(bad[0]))
         return X, e, lr, li
@@ -196,6 +200,11 @@ def count(S, select=None) -> int:
 
 def standard(S, Q=None, select=None, threads: int = 0):
     return default().standard(S, Q, select, threads)
+
+
+def left(S, Q=None, select=None, threads: int = 0):
+    """Left eigenvectors u^H S = lambda u^H (see Oracle.standard)."""
+    return default().standard(S, Q, select, threads, left=True)
 
 
 def generalized(S, T, Z=None, select=None, threads: int = 0):

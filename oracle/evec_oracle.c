@@ -10,6 +10,9 @@
  *   - generalized eigenvectors of a pair (S, T),
  *     (S - lambda_i T) y_i = 0, in homogeneous form          (Sec. 2, Eq. evec_solve)
  *   - back-transformation x_i = Q y_i  /  x_i = Z y_i       (Sec. 2, Eq. evec_backtransform)
+ *   - left eigenvectors of S, u_i^H S = lambda_i u_i^H, by robust forward
+ *     substitution (the transposed problem of Sec. 2), back-transformed
+ *     by the same Q
  *   - the robust triangular solve with many right-hand sides that the
  *     eigenvector solve generalises (Sec. 3.4, the LAPACK xLATRS lineage):
  *     T x_j = b_j for every column of B, each x_j = X[:, j] / 2^scale_exp[j]
@@ -261,6 +264,20 @@ static double block_col_norm(const double *A, int64_t lda, int64_t rows, int64_t
     return m;
 }
 
+/* |A[r0:r0+rows, c0:n]^T|_inf (largest column sum of the block rows right of
+ * column c0): the bound of a forward-substitution update from those rows. */
+static double block_row_norm(const double *A, int64_t lda, int64_t n, int64_t r0, int rows,
+                             int64_t c0)
+{
+    double m = 0.0;
+    for (int64_t c = c0; c < n; c++) {
+        double s = 0.0;
+        for (int a = 0; a < rows; a++) s += fabs(AT(A, lda, r0 + a, c));
+        if (s > m) m = s;
+    }
+    return m;
+}
+
 /* Number of output columns: a 2x2 block is selected when either of its two
  * eigenvalues is, and then yields two real columns (Re, Im). */
 static int64_t count_columns(const block_t *blk, int64_t nblk, const uint8_t *select)
@@ -285,6 +302,7 @@ typedef struct {
     const block_t *blk; int64_t nblk;
     const double *tauS;               /* per block: |S[0:start, block]|_inf */
     const double *tauT;               /* per block: |T[0:start, block]|_inf */
+    const double *tauL;               /* per block: |S[block, end:n]^T|_inf (left) */
     double smax, tmax;                /* max |S_ii|, max |T_ii| (generalized smin) */
 } problem_t;
 
@@ -404,6 +422,98 @@ static void solve_one(const problem_t *P, int generalized, int64_t k,
     *e_out = e;
 }
 
+/*
+ * Left eigenvector of block k of the standard problem, lambda = ar + i ai.
+ * A left eigenvector satisfies u^H S = lambda u^H; with w = conj(u) this is
+ * w^T (S - lambda I) = 0, the transposed system, solved by forward
+ * substitution over the blocks after k: w is zero above block k, fixed on
+ * it by own_r/own_i, and each later block i solves
+ *   (S_ii - lambda I)^T w_i = r_i,   r = -(S[rows before i, block i])^T w,
+ * with r accumulated block by block through protected updates (the bound of
+ * an update from block q is |S[block q, after q]^T|_inf).  On return w (wr,
+ * wi) holds w_true * 2^e; rows above the block are 0.
+ */
+static void solve_one_left(const problem_t *P, int64_t k, double ar, double ai,
+                           const double *own_r, const double *own_i,
+                           double *wr, double *wi, int64_t *e_out)
+{
+    const int64_t n = P->n;
+    const int cplx = ai != 0.0;
+    const block_t *B = P->blk;
+    const int64_t p = B[k].start;
+    const int bs = B[k].size;
+    int64_t e = 0;
+    double smin = ULP * cabs1(ar, ai);
+    double smlnum = SAFMIN * ((double)n / ULP);
+    if (smin < smlnum) smin = smlnum;
+
+    memset(wr, 0, sizeof(double) * n);
+    if (cplx) memset(wi, 0, sizeof(double) * n);
+    for (int j = 0; j < bs; j++) {
+        wr[p + j] = own_r[j];
+        if (cplx) wi[p + j] = own_i[j];
+    }
+    int64_t cur = k;            /* the block whose part of w was just fixed */
+    for (;;) {
+        const int64_t q = B[cur].start;
+        const int cb = B[cur].size;
+        const int64_t q1 = q + cb;
+        if (q1 < n) {
+            /* --- protect, then apply r[q1:n] -= S[block, q1:n]^T z ------ */
+            double nu = 0.0, mu = 0.0;
+            for (int64_t r = q1; r < n; r++) {
+                double a = fabs(wr[r]);
+                if (cplx && fabs(wi[r]) > a) a = fabs(wi[r]);
+                if (a > nu) nu = a;
+            }
+            for (int j = 0; j < cb; j++) {
+                double a = fabs(wr[q + j]);
+                if (cplx && fabs(wi[q + j]) > a) a = fabs(wi[q + j]);
+                if (a > mu) mu = a;
+            }
+            int64_t s = protect_update(nu, P->tauL[cur], mu);
+            if (s != 0) {
+                scale_vec(n, wr, s);
+                if (cplx) scale_vec(n, wi, s);
+                e += s;
+            }
+            for (int j = 0; j < cb; j++) {
+                const double zr = wr[q + j], zi = cplx ? wi[q + j] : 0.0;
+                for (int64_t c = q1; c < n; c++) {
+                    const double sv = AT(P->S, P->lds, q + j, c);
+                    wr[c] -= sv * zr;
+                    if (cplx) wi[c] -= sv * zi;
+                }
+            }
+        }
+        if (cur == P->nblk - 1) break;
+        /* --- solve the next block down: (S_ii - lambda I)^T z = r_i ------ */
+        cur += 1;
+        const int64_t i0 = B[cur].start;
+        const int ib = B[cur].size;
+        double mr[4], mi[4], rr[2], ri[2], zr[2], zi[2];
+        for (int a = 0; a < ib; a++) {
+            for (int b = 0; b < ib; b++) {
+                mr[a * ib + b] = AT(P->S, P->lds, i0 + b, i0 + a) - (a == b ? ar : 0.0);
+                mi[a * ib + b] = (a == b ? -ai : 0.0);
+            }
+            rr[a] = wr[i0 + a];
+            ri[a] = cplx ? wi[i0 + a] : 0.0;
+        }
+        int64_t s = small_solve(ib, mr, mi, rr, ri, smin, zr, zi);
+        if (s != 0) {
+            scale_vec(n, wr, s);
+            if (cplx) scale_vec(n, wi, s);
+            e += s;
+        }
+        for (int a = 0; a < ib; a++) {
+            wr[i0 + a] = zr[a];
+            if (cplx) wi[i0 + a] = zi[a];
+        }
+    }
+    *e_out = e;
+}
+
 /* Canonical form: scale by 2^-t with t = floor(log2 |y|), |y| = max_i |y_i|
  * (complex: max_i |re_i| + |im_i|), so |x| lies in [1, 2).  Returns t. */
 static int64_t canonicalize(int64_t n, double *yr, double *yi, int cplx)
@@ -441,7 +551,7 @@ typedef struct {
     int64_t col;       /* first output column */
 } job_t;
 
-static int run_jobs(const problem_t *P, int generalized, const double *Q, int64_t ldq,
+static int run_jobs(const problem_t *P, int generalized, int left, const double *Q, int64_t ldq,
                     const job_t *jobs, int64_t njobs,
                     const double *lre, const double *lim, const double *lbeta,
                     const double *own, /* per block: 4 values (own_r[2], own_i[2]) */
@@ -471,7 +581,15 @@ static int run_jobs(const problem_t *P, int generalized, const double *Q, int64_
             const double ar = lre[k], ai = lim[k], beta = lbeta ? lbeta[k] : 1.0;
             const int cplx = ai != 0.0;
             int64_t e = 0;
-            solve_one(P, generalized, k, ar, ai, beta, &own[4 * k], &own[4 * k + 2], yr, yi, &e);
+            if (left) {
+                /* w = conj(u): the stored columns are (Re u, Im u) */
+                solve_one_left(P, k, ar, ai, &own[4 * k], &own[4 * k + 2], yr, yi, &e);
+                if (cplx)
+                    for (int64_t r = 0; r < n; r++) yi[r] = -yi[r];
+            } else {
+                solve_one(P, generalized, k, ar, ai, beta, &own[4 * k], &own[4 * k + 2], yr, yi,
+                          &e);
+            }
             int64_t tcan = canonicalize(n, yr, yi, cplx);
             e -= tcan;
             if (Q) {
@@ -516,15 +634,11 @@ int evo_count(int64_t n, const double *S, int64_t lds, const uint8_t *select,
     return st;
 }
 
-/*
- * Standard problem: right eigenvectors of the quasi-triangular S
- * (column-major, ld lds), optional Q (NULL: X = Y).  Output columns follow
- * the block order; a 2x2 block yields (Re, Im) of the eigenvector of
- * lambda = a + i w with w > 0.  lam_re/lam_im (length m, may be NULL).
- */
-int evo_standard(int64_t n, const double *S, int64_t lds, const double *Q, int64_t ldq,
-                 const uint8_t *select, double *X, int64_t ldx, int32_t *scale_exp,
-                 double *lam_re, double *lam_im, int nthreads, int64_t *bad)
+/* Right (left = 0) or left (left = 1) eigenvectors of the standard problem. */
+static int standard_impl(int left, int64_t n, const double *S, int64_t lds, const double *Q,
+                         int64_t ldq, const uint8_t *select, double *X, int64_t ldx,
+                         int32_t *scale_exp, double *lam_re, double *lam_im, int nthreads,
+                         int64_t *bad)
 {
     if (n < 0 || lds < (n > 0 ? n : 1) || ldx < (n > 0 ? n : 1)) return EVO_EINVAL;
     if (Q && ldq < (n > 0 ? n : 1)) return EVO_EINVAL;
@@ -545,7 +659,8 @@ int evo_standard(int64_t n, const double *S, int64_t lds, const double *Q, int64
     int64_t njobs = 0, col = 0;
     for (int64_t k = 0; k < nblk; k++) {
         const int64_t p = blk[k].start;
-        tau[k] = block_col_norm(S, lds, p, p, blk[k].size);
+        tau[k] = left ? block_row_norm(S, lds, n, p, blk[k].size, p + blk[k].size)
+                      : block_col_norm(S, lds, p, p, blk[k].size);
         double *o = &own[4 * k];
         if (blk[k].size == 1) {
             lre[k] = AT(S, lds, p, p); lim[k] = 0.0;
@@ -555,9 +670,17 @@ int evo_standard(int64_t n, const double *S, int64_t lds, const double *Q, int64
             double a = AT(S, lds, p, p), b = AT(S, lds, p, p + 1), c = AT(S, lds, p + 1, p);
             double w = sqrt(fabs(b)) * sqrt(fabs(c));
             lre[k] = a; lim[k] = w;
-            /* null vector of [[-iw, b], [c, -iw]] */
-            if (fabs(b) >= fabs(c)) { o[0] = 1.0; o[1] = 0.0; o[2] = 0.0; o[3] = w / b; }
-            else { o[0] = -w / c; o[1] = 0.0; o[2] = 0.0; o[3] = 1.0; }
+            if (!left) {
+                /* null vector of [[-iw, b], [c, -iw]] */
+                if (fabs(b) >= fabs(c)) { o[0] = 1.0; o[1] = 0.0; o[2] = 0.0; o[3] = w / b; }
+                else { o[0] = -w / c; o[1] = 0.0; o[2] = 0.0; o[3] = 1.0; }
+            } else {
+                /* null vector of the transpose [[-iw, c], [b, -iw]] (w^T of
+                   the block part), in the row-reversed form of the right
+                   convention: (iw/b, 1) if |b| >= |c|, else (i, -w/c) */
+                if (fabs(b) >= fabs(c)) { o[0] = 0.0; o[1] = 1.0; o[2] = w / b; o[3] = 0.0; }
+                else { o[0] = 0.0; o[1] = -w / c; o[2] = 1.0; o[3] = 0.0; }
+            }
         }
         int sel = select == NULL || select[p] || (blk[k].size == 2 && select[p + 1]);
         if (sel) {
@@ -568,12 +691,43 @@ int evo_standard(int64_t n, const double *S, int64_t lds, const double *Q, int64
         }
     }
     {
-        problem_t P = {n, S, lds, NULL, 0, blk, nblk, tau, NULL, 0.0, 0.0};
-        st = run_jobs(&P, 0, Q, ldq, jobs, njobs, lre, lim, NULL, own, X, ldx, scale_exp, nthreads);
+        problem_t P = {n, S, lds, NULL, 0, blk, nblk, left ? NULL : tau, NULL,
+                       left ? tau : NULL, 0.0, 0.0};
+        st = run_jobs(&P, 0, left, Q, ldq, jobs, njobs, lre, lim, NULL, own, X, ldx, scale_exp,
+                      nthreads);
     }
 done:
     free(blk); free(tau); free(lre); free(lim); free(own); free(jobs);
     return st;
+}
+
+/*
+ * Standard problem: right eigenvectors of the quasi-triangular S
+ * (column-major, ld lds), optional Q (NULL: X = Y).  Output columns follow
+ * the block order; a 2x2 block yields (Re, Im) of the eigenvector of
+ * lambda = a + i w with w > 0.  lam_re/lam_im (length m, may be NULL).
+ */
+int evo_standard(int64_t n, const double *S, int64_t lds, const double *Q, int64_t ldq,
+                 const uint8_t *select, double *X, int64_t ldx, int32_t *scale_exp,
+                 double *lam_re, double *lam_im, int nthreads, int64_t *bad)
+{
+    return standard_impl(0, n, S, lds, Q, ldq, select, X, ldx, scale_exp, lam_re, lam_im,
+                         nthreads, bad);
+}
+
+/*
+ * Left eigenvectors of the quasi-triangular S: u_i^H S = lambda_i u_i^H
+ * (Sec. 2's eigenvector problem for S^T), optional Q (x_i = Q u_i, the
+ * left eigenvectors of Q S Q^T).  Same arguments, column order, eigenvalue
+ * outputs and canonical form as evo_standard; a 2x2 block yields (Re u,
+ * Im u) for lambda = a + i w, w > 0, and u is zero above its block.
+ */
+int evo_standard_left(int64_t n, const double *S, int64_t lds, const double *Q, int64_t ldq,
+                      const uint8_t *select, double *X, int64_t ldx, int32_t *scale_exp,
+                      double *lam_re, double *lam_im, int nthreads, int64_t *bad)
+{
+    return standard_impl(1, n, S, lds, Q, ldq, select, X, ldx, scale_exp, lam_re, lam_im,
+                         nthreads, bad);
 }
 
 /*
@@ -701,8 +855,8 @@ int evo_generalized(int64_t n, const double *S, int64_t lds, const double *T, in
         }
     }
     {
-        problem_t P = {n, S, lds, T, ldt, blk, nblk, tauS, tauT, smax, tmax};
-        st = run_jobs(&P, 1, Z, ldz, jobs, njobs, lre, lim, lbe, own, X, ldx, scale_exp, nthreads);
+        problem_t P = {n, S, lds, T, ldt, blk, nblk, tauS, tauT, NULL, smax, tmax};
+        st = run_jobs(&P, 1, 0, Z, ldz, jobs, njobs, lre, lim, lbe, own, X, ldx, scale_exp, nthreads);
     }
 done:
     free(blk); free(tauS); free(tauT); free(lre); free(lim); free(lbe); free(own); free(jobs);
@@ -799,7 +953,7 @@ int evo_trsolve(int64_t n, const double *S, int64_t lds, int64_t nrhs, const dou
     for (int64_t k = 0; k < nblk; k++)
         tau[k] = block_col_norm(S, lds, blk[k].start, blk[k].start, blk[k].size);
     {
-        problem_t P = {n, S, lds, NULL, 0, blk, nblk, tau, NULL, 0.0, 0.0};
+        problem_t P = {n, S, lds, NULL, 0, blk, nblk, tau, NULL, NULL, 0.0, 0.0};
 #ifdef _OPENMP
         if (nthreads > 0) omp_set_num_threads(nthreads);
 #else

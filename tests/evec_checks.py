@@ -57,6 +57,17 @@ def standard_residuals(T, X, lam_re, lam_im):
     return np.array(res)
 
 
+def left_residuals(T, X, lam_re, lam_im):
+    """||u^H T - lambda u^H||_1 / (||T||_inf ||u||_1 u) per eigenvalue, for
+    left eigenvectors stored as (Re u, Im u): the residual of
+    T^T conj(u) = lambda conj(u)."""
+    Xc = np.array(X, dtype=np.float64, copy=True)
+    for j, pair in column_groups(lam_im):
+        if pair:
+            Xc[:, j + 1] = -Xc[:, j + 1]
+    return standard_residuals(np.ascontiguousarray(T.T), Xc, lam_re, lam_im)
+
+
 def generalized_residuals(S, T, X, a_re, a_im, beta):
     """||beta S x - alpha T x||_1 / ((|beta| ||S||_1 + |alpha| ||T||_1) ||x||_1 u)."""
     S1 = np.abs(S).sum(axis=0).max()
@@ -159,6 +170,19 @@ def mp_eigvec(T, p, size, prec=256):
             y[q] = (rhs[0] * m22 - m12 * rhs[1]) / det
             y[q + 1] = (m11 * rhs[1] - m21 * rhs[0]) / det
     return y, lam
+
+
+def mp_left_eigvec(T, p, size, prec=256):
+    """Left eigenvector u (u^H T = lambda u^H) of the block at p, from the
+    right-eigenvector reference on the flipped matrix T' = J T^T J (J the
+    reversal permutation): T' is upper quasi-triangular with the same
+    blocks, T'(J conj(u)) = lambda (J conj(u)), so u = conj(J y') with y'
+    the eigenvector of T' for the block at n - p - size.  Returns (u, lam)."""
+    import mpmath as mp
+    n = T.shape[0]
+    Tf = np.ascontiguousarray(T.T[::-1, ::-1])
+    y, lam = mp_eigvec(Tf, n - p - size, size, prec)
+    return [mp.conj(v) for v in reversed(y)], lam
 
 
 def mp_canonical(y, pair):

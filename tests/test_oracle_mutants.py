@@ -16,7 +16,8 @@ import pytest
 import oracle
 import workloads
 from evec_checks import (U, canonical_norms, column_groups, generalized_residuals,
-                         mp_canonical, mp_eigvec, standard_residuals)
+                         left_residuals, mp_canonical, mp_eigvec, mp_left_eigvec,
+                         standard_residuals)
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "hand_examples.json")
 
@@ -46,6 +47,14 @@ MUTANTS = [
      "hr[colp[0]] = w1r; hi[colp[0]] = w1i;\n        hr[colp[1]] = w2r; hi[colp[1]] = w2i;",
      "hr[0] = w1r; hi[0] = w1i;\n        hr[1] = w2r; hi[1] = w2i;"),
     ("eigenvalue_imag_sign", "lre[k] = a; lim[k] = w;", "lre[k] = a; lim[k] = -w;"),
+    ("left_update_sign", "wr[c] -= sv * zr;", "wr[c] += sv * zr;"),
+    ("left_small_system_not_transposed",
+     "mr[a * ib + b] = AT(P->S, P->lds, i0 + b, i0 + a) - (a == b ? ar : 0.0);",
+     "mr[a * ib + b] = AT(P->S, P->lds, i0 + a, i0 + b) - (a == b ? ar : 0.0);"),
+    ("left_own_block_sign", "o[2] = w / b;", "o[2] = -w / b;"),
+    ("left_conjugation_dropped", "for (int64_t r = 0; r < n; r++) yi[r] = -yi[r];", "(void)0;"),
+    ("left_update_unprotected", "int64_t s = protect_update(nu, P->tauL[cur], mu);",
+     "int64_t s = 0;"),
 ]
 
 
@@ -126,12 +135,45 @@ def detector_failures(orc):
         B = Z @ T @ Z.T
         return np.isfinite(X).all() and generalized_residuals(A, B, X, ar, ai, be).max() <= 10 * 80
 
+    def left_residual():
+        X, e, lr, li = orc.standard(T0, left=True)
+        if not np.isfinite(X).all():
+            return False
+        nr = canonical_norms(X, li)
+        return left_residuals(T0, X, lr, li).max() <= 10 * 96 and nr.min() >= 1 and nr.max() < 2
+
+    def left_adversarial():
+        T, _ = workloads.adversarial_schur(128, seed=8)
+        X, e, lr, li = orc.standard(T, left=True)
+        return np.isfinite(X).all() and left_residuals(T, X, lr, li).max() <= 10 * 128
+
+    def left_brute_force():
+        T, blocks = workloads.config0_schur(20, seed=9)
+        X, e, lr, li = orc.standard(T, left=True)
+        col = 0
+        for (p, sz) in blocks:
+            u, _ = mp_left_eigvec(T, p, sz)
+            xr, xi, emp = mp_canonical(u, sz == 2)
+            de = int(e[col]) - emp
+            if abs(de) > 1:
+                return False
+            err = np.abs(np.ldexp(X[:, col], -de) - xr)
+            if sz == 2:
+                err = err + np.abs(np.ldexp(X[:, col + 1], -de) - xi)
+            if err.max() > 1e-12 * np.max(np.abs(xr) + np.abs(xi)):
+                return False
+            col += sz
+        return True
+
     check("golden", golden)
     check("residual_std", residual_std)
     check("residual_backtransformed", residual_backtransformed)
     check("adversarial", adversarial)
     check("brute_force", brute_force)
     check("generalized", generalized)
+    check("left_residual", left_residual)
+    check("left_adversarial", left_adversarial)
+    check("left_brute_force", left_brute_force)
     return fails
 
 
