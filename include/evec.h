@@ -144,6 +144,27 @@ evec_status evec_standard(evec_handle h, int64_t n, const double *T, int64_t ldt
                           double *lam_re, double *lam_im, const evec_opts *opt);
 
 /*
+ * Left eigenvectors of the quasi-triangular T: u_j^H T = lambda_j u_j^H (the
+ * eigenvector problem of Sec. 2 for T^T), optionally back-transformed by
+ * Q (x_j = Q u_j, the left eigenvectors of Q T Q^T).  Same arguments,
+ * selection, column order (T's block order), eigenvalue outputs, canonical
+ * form and errors as evec_standard (mode, tile, slices, refine and check
+ * as there).  u_j is zero above its block; for a 1x1 block u_p = 1, for a
+ * pair [[a, b], [c, a]] the columns are (Re u, Im u) for lambda = a + i w,
+ * w > 0, with the block part (-i w/b, 1) if |b| >= |c|, else (-i, -w/c).
+ * Computed as the right eigenvectors of the flipped form T' = J T^T J (J
+ * the reversal permutation; T' has T's blocks in reverse order) with
+ * Q J for the back-transformation, so the handle holds two extra n x n
+ * and one n x m FP64 workspaces.  A non-finite or over-range entry of T
+ * strictly above the first superdiagonal is reported at evec_sync with
+ * its index i + j ldt in T.
+ */
+evec_status evec_standard_left(evec_handle h, int64_t n, const double *T, int64_t ldt,
+                               const double *Q, int64_t ldq, const uint8_t *select_host,
+                               double *X, int64_t ldx, int32_t *scale_exp,
+                               double *lam_re, double *lam_im, const evec_opts *opt);
+
+/*
  * The same computation with HOST buffers (column-major, ld = n): copies
  * T (and Q) to the device, computes, copies X [n x m], scale_exp [m],
  * lam_re [m] and lam_im [m] back (each output may be NULL) and
@@ -188,7 +209,9 @@ enum {
     EVEC_K_REFINE = 8,       /* residual, right-hand side, correction add
                                 (the correction solve itself counts under
                                 EVEC_K_DIAG_SOLVE / EVEC_K_TILE_UPDATE) */
-    EVEC_K_COUNT = 9
+    EVEC_K_LEFT = 9,         /* evec_standard_left: the flipped T' and Q J,
+                                and the final scatter into T's column order */
+    EVEC_K_COUNT = 10
 };
 
 /* Enable (1) or disable (0) per-kernel timing: while enabled, every kernel

@@ -30,7 +30,7 @@ EVEC_OK, EVEC_EINVAL, EVEC_ENOTSCHUR, EVEC_ENONFINITE = 0, 1, 2, 3
 EVEC_ENOMEM, EVEC_ECUDA, EVEC_ETIMEOUT, EVEC_ERESIDUAL = 4, 5, 6, 7
 EVEC_ECAPACITY = 8
 KERNELS = ("gather", "tile_norms", "diag_solve", "tile_update", "finalize",
-           "backtransform", "canonicalize", "batched", "refine")
+           "backtransform", "canonicalize", "batched", "refine", "left")
 
 
 class EvecError(RuntimeError):
@@ -77,6 +77,7 @@ def lib() -> ctypes.CDLL:
         L.evec_count.argtypes = [p, i64, p, i64, p, ctypes.POINTER(i64)]
         L.evec_standard.argtypes = [p, i64, p, i64, p, i64, p, p, i64, p, p, p,
                                     ctypes.POINTER(_Opts)]
+        L.evec_standard_left.argtypes = L.evec_standard.argtypes
         L.evec_standard_host.argtypes = [p, i64, p, p, p, p, p, p, p, ctypes.POINTER(_Opts)]
         L.evec_sync.argtypes = [p, ctypes.POINTER(i64)]
         L.evec_plan_query.argtypes = [i64, p, p, p, p, ctypes.c_int, ctypes.POINTER(i64),
@@ -96,7 +97,8 @@ def lib() -> ctypes.CDLL:
         L.evec_tune_get.argtypes = [p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
         L.evec_tune_set.argtypes = [p, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         for f in ("evec_create", "evec_destroy", "evec_set_stream", "evec_count",
-                  "evec_standard", "evec_standard_host", "evec_sync", "evec_plan_query",
+                  "evec_standard", "evec_standard_left", "evec_standard_host", "evec_sync",
+                  "evec_plan_query", "evec_trsolve",
                   "evec_profile", "evec_profile_read", "evec_batched_count", "evec_batched",
                   "evec_generalized",
                   "evec_tune_get", "evec_tune_set"):
@@ -256,6 +258,19 @@ def standard(T, Q=None, select=None, tile: int = 0, check: bool = False, out=Non
     column-major.  The call is asynchronous on the current stream; device
     detected input errors surface at ``sync()`` (or immediately with
     check=True)."""
+    return _standard_call("evec_standard", T, Q, select, tile, check, out, mode, slices, refine)
+
+
+def left(T, Q=None, select=None, tile: int = 0, check: bool = False, out=None,
+         mode: str = "fp64", slices: int = 0, refine: bool = False):
+    """Left eigenvectors u^H T = lambda u^H (optionally X = Q U), same
+    arguments, outputs and column order as ``standard``; a pair gives
+    (Re u, Im u) for lambda = a + i w, w > 0."""
+    return _standard_call("evec_standard_left", T, Q, select, tile, check, out, mode, slices,
+                          refine)
+
+
+def _standard_call(fn, T, Q, select, tile, check, out, mode, slices, refine):
     import torch
     n = T.shape[0]
     ldt = _check_colmajor(T, "T", n)
@@ -275,10 +290,11 @@ def standard(T, Q=None, select=None, tile: int = 0, check: bool = False, out=Non
     if m == 0:
         return X, e, lr, li
     opts = _opts(tile, False, mode, slices, refine)
-    st = lib().evec_standard(h.ptr, n, T.data_ptr(), ldt, Q.data_ptr() if Q is not None else None,
-                             ldq, _np_ptr(sel), X.data_ptr(), ldx, e.data_ptr(), lr.data_ptr(),
-                             li.data_ptr(), ctypes.byref(opts))
-    _check(st, "evec_standard")
+    st = getattr(lib(), fn)(h.ptr, n, T.data_ptr(), ldt,
+                            Q.data_ptr() if Q is not None else None, ldq, _np_ptr(sel),
+                            X.data_ptr(), ldx, e.data_ptr(), lr.data_ptr(), li.data_ptr(),
+                            ctypes.byref(opts))
+    _check(st, fn)
     if check:
         h.sync()
     return X, e, lr, li

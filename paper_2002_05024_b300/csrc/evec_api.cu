@@ -42,6 +42,14 @@ void launch_residual(const double *T, int64_t ldt, const Plan &p, int ntiles, in
                      const int32_t *row_tile, double *R, int64_t ldr, cudaStream_t st);
 void launch_rhs_init(const Plan &p, const double *R, int64_t ldr, double *seg_nu,
                      cudaStream_t st);
+void launch_flip_transpose(const double *T, int64_t ldt, int64_t n, double *Tf, int64_t ldf,
+                           DevStatus *status, cudaStream_t st);
+void launch_reverse_cols(const double *Q, int64_t ldq, int64_t n, double *Qr, int64_t ldr,
+                         cudaStream_t st);
+void launch_left_output(const double *Xw, int64_t ldw, int64_t n, int64_t m, const int32_t *dst,
+                        int reverse, const int32_t *ew, const double *lrw, const double *liw,
+                        double *X, int64_t ldx, int32_t *e, double *lr, double *li,
+                        cudaStream_t st);
 void launch_check_rhs(const double *B, int64_t ldb, int64_t n, int64_t nrhs, int64_t base,
                       DevStatus *status, cudaStream_t st);
 void launch_refine_combine(const Plan &p, double *Y, int64_t ldy, const int32_t *ey,
@@ -522,6 +530,14 @@ struct evec_ctx {
     double *hT = nullptr, *hQ = nullptr, *hX = nullptr; size_t hT_cap = 0, hQ_cap = 0, hX_cap = 0;
     int32_t *hE = nullptr; size_t hE_cap = 0;
     double *hL = nullptr; size_t hL_cap = 0;
+    // left eigenvectors: the flipped T' = J T^T J, Q J, the result in T's
+    // column order before the final scatter, and that scatter's column map
+    double *lT = nullptr, *lQ = nullptr, *lX = nullptr; size_t lT_cap = 0, lQ_cap = 0, lX_cap = 0;
+    int32_t *lE = nullptr; size_t lE_cap = 0;
+    double *lL = nullptr; size_t lL_cap = 0;
+    int32_t *lmap_d = nullptr; size_t lmap_cap = 0;
+    std::vector<int32_t> lmap_h;
+    std::vector<uint8_t> lsel;
     // pinned host buffers
     double *diag_h = nullptr; size_t diag_h_cap = 0;
     unsigned char *plan_h = nullptr; size_t plan_h_cap = 0;
@@ -876,7 +892,8 @@ evec_status evec_destroy(evec_handle h) {
                    h->tau, h->blk_tau, h->status_d, h->hT, h->hQ, h->hX, h->hE, h->hL,
                    h->slA, h->slB, h->rmax, h->cmax, h->ea, h->eb, h->panels,
                    h->ea_panels, h->boff_d, h->bws, h->bplan_d, h->queue_d, h->tauT,
-                   h->blk_tauT, h->pW, h->Rd, h->seg_ey};
+                   h->blk_tauT, h->pW, h->Rd, h->seg_ey, h->lT, h->lQ, h->lX, h->lE, h->lL,
+                   h->lmap_d};
     for (void *p : dev)
         if (p) cudaFree(p);
     for (auto &t : h->live) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
@@ -1334,6 +1351,76 @@ evec_status evec_trsolve(evec_handle h, int64_t n, const double *T, int64_t ldt,
     EVEC_TRY(sweep_steps(h, HP, dp, T, ldt, X, ldx, true, mode, sctx, st));
     timed(h, EVEC_K_FINALIZE, [&] {
         launch_finalize(dp, X, ldx, h->seg_e, scale_exp, st);
+        return 1;
+    });
+    EVEC_CUDA(cudaGetLastError());
+    if (opt && opt->check) return evec_sync(h, nullptr);
+    return EVEC_OK;
+}
+
+// Left eigenvectors: the right-eigenvector path on T' = J T^T J (T's
+// blocks in reverse order; see k_left.cu) with Q J, then one scatter that
+// restores T's column order (a pair keeps its (Re, Im) order), reverses the
+// rows when there is no Q and negates the imaginary columns.
+evec_status evec_standard_left(evec_handle h, int64_t n, const double *T, int64_t ldt,
+                               const double *Q, int64_t ldq, const uint8_t *select_host,
+                               double *X, int64_t ldx, int32_t *scale_exp, double *lam_re,
+                               double *lam_im, const evec_opts *opt) {
+    if (!h || n < 0 || !ld_ok(ldt, n) || !ld_ok(ldx, n) || (Q && !ld_ok(ldq, n)))
+        return EVEC_EINVAL;
+    if (n == 0) return EVEC_OK;
+    if (!T || !X || !scale_exp) return EVEC_EINVAL;
+    const int nb = resolve_tile(opt);
+    if (nb < 16 || nb > kMaxTile) return EVEC_EINVAL;
+    DeviceGuard g(h->device);
+    if (!g.ok) return EVEC_ECUDA;
+    cudaStream_t st = h->stream;
+    const size_t nn = (size_t)n * (size_t)n;
+    EVEC_TRY(grow_device(&h->lT, &h->lT_cap, nn));
+    if (Q) EVEC_TRY(grow_device(&h->lQ, &h->lQ_cap, nn));
+    timed(h, EVEC_K_LEFT, [&] {
+        launch_flip_transpose(T, ldt, n, h->lT, n, h->status_d, st);
+        if (Q) launch_reverse_cols(Q, ldq, n, h->lQ, n, st);
+        return Q ? 2 : 1;
+    });
+    EVEC_CUDA(cudaGetLastError());
+    const uint8_t *sel = nullptr;
+    if (select_host) {
+        h->lsel.resize((size_t)n);
+        for (int64_t i = 0; i < n; i++) h->lsel[i] = select_host[n - 1 - i];
+        sel = h->lsel.data();
+    }
+    // the output size (evec_standard finds this plan again and reuses it)
+    int64_t bad = -1;
+    EVEC_TRY(plan_device_matrix(h, n, h->lT, n, sel, nb, &bad));
+    const int64_t m = h->plan.m;
+    if (m == 0) return (opt && opt->check) ? evec_sync(h, nullptr) : EVEC_OK;
+    EVEC_TRY(grow_device(&h->lX, &h->lX_cap, (size_t)n * (size_t)m));
+    EVEC_TRY(grow_device(&h->lE, &h->lE_cap, (size_t)m));
+    EVEC_TRY(grow_device(&h->lL, &h->lL_cap, 2 * (size_t)m));
+    EVEC_TRY(grow_device(&h->lmap_d, &h->lmap_cap, (size_t)m));
+    evec_opts o{};
+    if (opt) o = *opt;
+    o.check = 0;
+    EVEC_TRY(evec_standard(h, n, h->lT, n, Q ? h->lQ : nullptr, n, sel, h->lX, n, h->lE, h->lL,
+                           h->lL + m, &o));
+    // T' column c' -> T column: T' lists the blocks in reverse order, a
+    // pair (Re at c', Im at c' + 1) keeps its order; ~d marks a negated
+    // (imaginary) column
+    const HostPlan &HP = h->plan;
+    if ((int64_t)HP.col_lam_im.size() != m) return EVEC_EINVAL;
+    h->lmap_h.resize((size_t)m);
+    for (int64_t c = 0; c < m; c++) {
+        const double wi = HP.col_lam_im[c];
+        if (wi > 0.0) h->lmap_h[c] = (int32_t)(m - 2 - c);
+        else if (wi < 0.0) h->lmap_h[c] = ~(int32_t)(m - c);
+        else h->lmap_h[c] = (int32_t)(m - 1 - c);
+    }
+    EVEC_CUDA(cudaMemcpyAsync(h->lmap_d, h->lmap_h.data(), (size_t)m * sizeof(int32_t),
+                              cudaMemcpyHostToDevice, st));
+    timed(h, EVEC_K_LEFT, [&] {
+        launch_left_output(h->lX, n, n, m, h->lmap_d, Q ? 0 : 1, h->lE, h->lL, h->lL + m, X, ldx,
+                           scale_exp, lam_re, lam_im, st);
         return 1;
     });
     EVEC_CUDA(cudaGetLastError());
