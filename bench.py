@@ -70,6 +70,8 @@ def parse_args():
                          "(S, T) with Z (use --n 8192); trsolve: robust solve of an n x n "
                          "quasi-triangular T with --nrhs right-hand sides")
     ap.add_argument("--nrhs", type=int, default=0, help="trsolve: right-hand sides (default n)")
+    ap.add_argument("--side", choices=["right", "left"], default="right",
+                    help="single: right eigenvectors (default) or left ones (u^H T = lambda u^H)")
     ap.add_argument("--batch", type=int, default=2000)
     return ap.parse_args()
 
@@ -256,7 +258,7 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(T, blocks, Q, sample_cols, seed=5, gpu=None):
+def cpu_baseline(T, blocks, Q, sample_cols, seed=5, gpu=None, left=False):
     """The oracle, as it stands, on a seeded random sample of the workload's
     columns, on all host cores.  With gpu = (X, scale_exp) of the timed run,
     the sampled columns are also compared with the GPU's (largest exponent
@@ -276,14 +278,15 @@ def cpu_baseline(T, blocks, Q, sample_cols, seed=5, gpu=None):
         cols += sz
     oracle.build()
     t = time.perf_counter()
-    X, e, lr, li = oracle.standard(T, Q=Q, select=sel)
+    X, e, lr, li = (oracle.left if left else oracle.standard)(T, Q=Q, select=sel)
     dt = time.perf_counter() - t
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     threads = int(os.environ.get("OMP_NUM_THREADS", cores))
     out = {"value": X.shape[1] / dt, "unit": "columns/s", "cores": threads, "kind": "oracle",
            "columns": X.shape[1], "seconds": dt,
            "sample": f"{X.shape[1]} randomly chosen columns (seed {seed}) of the n={n} "
-                     f"workload incl. back-transformation, {dt:.2f} s"}
+                     f"workload incl. back-transformation"
+                     + (" (left eigenvectors)" if left else "") + f", {dt:.2f} s"}
     if gpu is not None:
         Xg, eg = gpu
         col, oc, max_de, max_rel = 0, 0, 0, 0.0
@@ -301,10 +304,18 @@ def cpu_baseline(T, blocks, Q, sample_cols, seed=5, gpu=None):
     return out
 
 
-def residual_sample(T, Q, X, lr, li, blocks, k=16, seed=7):
+def residual_sample(T, Q, X, lr, li, blocks, k=16, seed=7, left=False):
     """Normalised residual ||T y - lambda y||_1 / (||T||_1 ||y||_1 u) of k
     seeded random eigenvalues of the GPU result, y = Q^T x in long double
-    (the Schur-coordinate residual of x; no product with Q enters it)."""
+    (the Schur-coordinate residual of x; no product with Q enters it).
+    left: the residual of T^T conj(y) = lambda conj(y) (u^H T = lambda u^H)
+    with ||T^T||_1."""
+    if left:
+        T = np.ascontiguousarray(T.T)
+        X = np.array(X, copy=True)
+        for c in range(X.shape[1]):
+            if li[c] < 0:
+                X[:, c] = -X[:, c]
     n = T.shape[0]
     rng = np.random.default_rng(seed)
     starts, col = [], 0
@@ -371,7 +382,7 @@ def run_reference(args, rank, world):
     per_step = max(16, args.cpu_sample // 4)
     times, cols = [], []
     for i in range(args.warmup + args.steps):
-        r = cpu_baseline(T, blocks, Q, per_step, seed=1000 + i)
+        r = cpu_baseline(T, blocks, Q, per_step, seed=1000 + i, left=args.side == "left")
         if i >= args.warmup:
             cols.append(r["columns"])
             times.append(r["seconds"])
@@ -384,7 +395,9 @@ def run_reference(args, rank, world):
         "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": f"config-0 Schur form n={args.n} + Q, all columns (oracle samples)"},
+        "config": {"workload": f"config-0 Schur form n={args.n} + Q, all columns"
+                               + (", left eigenvectors" if args.side == "left" else "")
+                               + " (oracle samples)"},
         "cpu_baseline": {"value": value, "unit": "columns/s", "cores": cores, "kind": "oracle",
                          "sample": f"{per_step} random columns per step of the n={args.n} "
                                    "workload, on the host cores"},
@@ -429,9 +442,11 @@ def run_ours(args, rank, world, local_rank):
     out = (X, e, lr, li)
     stream = torch.cuda.current_stream(dev)
 
+    left = args.side == "left"
+    solve = ev.left if left else ev.standard
+
     def step():
-        ev.standard(dT, dQ, tile=args.tile, out=out, mode=args.mode, slices=args.slices,
-                    refine=refine)
+        solve(dT, dQ, tile=args.tile, out=out, mode=args.mode, slices=args.slices, refine=refine)
 
     for _ in range(args.warmup):
         step()
@@ -482,7 +497,44 @@ def run_ours(args, rank, world, local_rank):
 
     # end to end through the host-buffer entry point (pinned host memory)
     e2e = None
-    if not os.environ.get("EVEC_BENCH_NO_E2E"):
+    if left and not os.environ.get("EVEC_BENCH_NO_E2E"):
+        # no host-buffer entry point for the left vectors: the public call on
+        # device tensors with T and Q copied in from pinned memory and X,
+        # the exponents and eigenvalues copied out, every step
+        hT = torch.empty((n, n), dtype=torch.float64, pin_memory=True).t()
+        hT.copy_(torch.from_numpy(T))
+        hQ = torch.empty((n, n), dtype=torch.float64, pin_memory=True).t()
+        hQ.copy_(torch.from_numpy(Q))
+        hX = torch.empty((m, n), dtype=torch.float64, pin_memory=True).t()
+        hE = torch.empty(m, dtype=torch.int32, pin_memory=True)
+        hL = torch.empty((2, m), dtype=torch.float64, pin_memory=True)
+
+        def host_step():
+            dT.copy_(hT, non_blocking=True)
+            dQ.copy_(hQ, non_blocking=True)
+            step()
+            hX.copy_(X, non_blocking=True)
+            hE.copy_(e, non_blocking=True)
+            hL[0].copy_(lr, non_blocking=True)
+            hL[1].copy_(li, non_blocking=True)
+            torch.cuda.synchronize(dev)
+
+        for _ in range(args.warmup):
+            host_step()
+        if dist:
+            dist.barrier()
+        w0 = time.perf_counter()
+        for _ in range(args.steps):
+            host_step()
+        w = time.perf_counter() - w0
+        if dist:
+            tt = torch.tensor([w], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            w = float(tt.item())
+        e2e = {"value": world * m * args.steps / w, "unit": "columns/s",
+               "h2d_bytes_per_step": 2 * n * n * 8,
+               "d2h_bytes_per_step": n * m * 8 + m * 4 + 2 * m * 8}
+    elif not os.environ.get("EVEC_BENCH_NO_E2E"):
         pin = lambda shape, dt: torch.empty(shape, dtype=dt, pin_memory=True).numpy()  # noqa: E731
         hT = pin((n, n), torch.float64)
         hT[...] = T.T          # row-major view of the column-major bytes
@@ -523,10 +575,10 @@ def run_ours(args, rank, world, local_rank):
             dist.destroy_process_group()
         return
     Xh, eh = X.cpu().numpy(), e.cpu().numpy()
-    quality = residual_sample(T, Q, Xh, lr.cpu().numpy(), li.cpu().numpy(), blocks)
+    quality = residual_sample(T, Q, Xh, lr.cpu().numpy(), li.cpu().numpy(), blocks, left=left)
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(T, blocks, Q, args.cpu_sample, gpu=(Xh, eh))
+        cpu = cpu_baseline(T, blocks, Q, args.cpu_sample, gpu=(Xh, eh), left=left)
         cpu.pop("columns")
         cpu.pop("seconds")
     line = {
@@ -537,7 +589,7 @@ def run_ours(args, rank, world, local_rank):
         "dtype": "f64" if args.mode == "fp64" else "bf16 slice products + f64",
         "data": "synthetic",
         "config": {"workload": f"config-0 Schur form n={n} + Q (64 Householder reflectors), "
-                               f"all {m} columns, "
+                               f"all {m} " + ("left eigenvectors, " if left else "columns, ")
                                + ("FP64" if args.mode == "fp64" else
                                   f"split precision ({slices} BF16 slices, FP32 exact "
                                   "accumulation, FP64 recombination)"
@@ -545,7 +597,7 @@ def run_ours(args, rank, world, local_rank):
                                      if refine else "")),
                    "n": n, "columns": m, "tile": args.tile or 64, "mode": args.mode,
                    "slices": (args.slices or 8) if args.mode == "split" else None,
-                   "refine": refine,
+                   "refine": refine, "side": args.side,
                    "parallelism": "replicas",
                    "l2": "inputs larger than L2 (T, Q, X 128 MiB each)"},
         "tflops_fp64": tflops,
