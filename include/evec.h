@@ -308,6 +308,31 @@ evec_status evec_batched(evec_handle h, int64_t count, const int64_t *n_host,
                          const uint8_t *select_host, double *X_packed, int32_t *scale_exp_packed,
                          double *lam_re_packed, double *lam_im_packed, const evec_opts *opt);
 
+/*
+ * Generalized right eigenvectors of a batch of pencils (S_i, T_i) (the
+ * single-pencil computation of evec_generalized, without Z) in one
+ * persistent launch of the pencil variant of the batched kernel: each CTA
+ * takes whole pencils from the work queue, computes the norms of both
+ * matrices, runs the diagonal-tile solves of (beta S - alpha T) and the
+ * updates Y_r <- 2^dy Y_r - [S_rs (beta X~) - T_rs (alpha X~)] in FP64,
+ * and writes the canonical form.  S_i, T_i (n_i x n_i, leading dimension
+ * n_i) at S_packed + s_off_host[i] and T_packed + t_off_host[i], with the
+ * requirements of evec_generalized.  Output packing as evec_batched (X_i at
+ * sum_{k<i} n_k m_k; scale_exp_i, alpha_re_i, alpha_im_i, beta_i at
+ * sum_{k<i} m_k; the last three may be NULL); m_i from evec_batched_count
+ * on S_packed.  opt->mode must be EVEC_FP64; opt->tile 16..64, 0 = 32 (the
+ * solver holds both matrices' diagonal tiles).  Device-side errors
+ * (evec_sync / opt->check): index = element offset in S_packed or T_packed
+ * of the offending entry.
+ */
+evec_status evec_batched_generalized(evec_handle h, int64_t count, const int64_t *n_host,
+                                     const double *S_packed, const int64_t *s_off_host,
+                                     const double *T_packed, const int64_t *t_off_host,
+                                     const uint8_t *select_host, double *X_packed,
+                                     int32_t *scale_exp_packed, double *alpha_re_packed,
+                                     double *alpha_im_packed, double *beta_packed,
+                                     const evec_opts *opt);
+
 /* Size classes of the tile table: n <= 64, <= 128, <= 256, <= 512, larger. */
 #define EVEC_SIZE_CLASSES 5
 

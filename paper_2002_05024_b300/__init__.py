@@ -94,12 +94,15 @@ def lib() -> ctypes.CDLL:
                                        ctypes.POINTER(_Opts)]
         L.evec_batched_count.argtypes = [p, i64, p, p, p, p, p]
         L.evec_batched.argtypes = [p, i64, p, p, p, p, p, p, p, p, ctypes.POINTER(_Opts)]
+        L.evec_batched_generalized.argtypes = [p, i64, p, p, p, p, p, p, p, p, p, p, p,
+                                               ctypes.POINTER(_Opts)]
         L.evec_tune_get.argtypes = [p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
         L.evec_tune_set.argtypes = [p, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         for f in ("evec_create", "evec_destroy", "evec_set_stream", "evec_count",
                   "evec_standard", "evec_standard_left", "evec_standard_host", "evec_sync",
                   "evec_plan_query", "evec_trsolve",
                   "evec_profile", "evec_profile_read", "evec_batched_count", "evec_batched",
+                  "evec_batched_generalized",
                   "evec_generalized",
                   "evec_tune_get", "evec_tune_set"):
             getattr(L, f).restype = ctypes.c_int
@@ -499,6 +502,44 @@ def batched(Ts, selects=None, tile: int = 0, mode: str = "fp64", check: bool = T
         n, mi = int(n), int(mi)
         out.append((X[xo:xo + n * mi].view(mi, n).t(), e[eo:eo + mi], lr[eo:eo + mi],
                     li[eo:eo + mi]))
+        xo += n * mi
+        eo += mi
+    return out
+
+
+def batched_generalized(pairs, selects=None, tile: int = 0, check: bool = True):
+    """Generalized eigenvectors of a list of pencils [(S_i, T_i), ...] (numpy
+    or torch matrices, packed here) in one persistent launch (FP64).  Returns a list of
+    (X_i (n_i, m_i), scale_exp_i, alpha_re_i, alpha_im_i, beta_i)."""
+    import torch
+    Sp, ns, soffs = pack_batch([S for S, _ in pairs])
+    Tp, _, toffs = pack_batch([T for _, T in pairs])
+    sel = None
+    if selects is not None:
+        sel = np.concatenate([np.ones(n, np.uint8) if s is None else
+                              np.ascontiguousarray(s, dtype=np.uint8) for s, n in zip(selects, ns)])
+    m = batched_count(Sp, ns, soffs, sel)
+    dev = Sp.device
+    X = torch.empty(int((ns * m).sum()), dtype=torch.float64, device=dev)
+    e = torch.empty(int(m.sum()), dtype=torch.int32, device=dev)
+    ar = torch.empty(int(m.sum()), dtype=torch.float64, device=dev)
+    ai = torch.empty(int(m.sum()), dtype=torch.float64, device=dev)
+    be = torch.empty(int(m.sum()), dtype=torch.float64, device=dev)
+    h = handle(dev.index)
+    opts = _opts(tile, False, "fp64", 0)
+    st = lib().evec_batched_generalized(h.ptr, len(ns), _np_ptr(ns), Sp.data_ptr(),
+                                        _np_ptr(soffs), Tp.data_ptr(), _np_ptr(toffs),
+                                        _np_ptr(sel), X.data_ptr(), e.data_ptr(), ar.data_ptr(),
+                                        ai.data_ptr(), be.data_ptr(), ctypes.byref(opts))
+    _check(st, "evec_batched_generalized")
+    if check:
+        h.sync()
+    out = []
+    xo = eo = 0
+    for n, mi in zip(ns, m):
+        n, mi = int(n), int(mi)
+        out.append((X[xo:xo + n * mi].view(mi, n).t(), e[eo:eo + mi], ar[eo:eo + mi],
+                    ai[eo:eo + mi], be[eo:eo + mi]))
         xo += n * mi
         eo += mi
     return out

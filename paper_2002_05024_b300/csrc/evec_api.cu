@@ -98,7 +98,7 @@ int launch_tile_update_pencil(int s, const double *S, int64_t lds, const double 
                               const int32_t *seg_dx, const int32_t *seg_dy, double *seg_nu,
                               double *W, int64_t ldw, cudaStream_t st);
 cudaError_t launch_batched(const BatchItem *items, int count, int *queue, DevStatus *status,
-                           int nsm, cudaStream_t st, int S);
+                           int nsm, cudaStream_t st, int S, int gen_tile);
 void launch_gather_batched(const double *T, const int64_t *t_off, const int64_t *row_off,
                            int count, int64_t total_rows, double *out, cudaStream_t st);
 cudaError_t split_update_step_resident(const SplitUpdateCtx &ctx, int t0, int ts, int prow0,
@@ -1525,10 +1525,12 @@ static evec_status batched_gather(evec_handle h, int64_t count, const int64_t *n
     return EVEC_OK;
 }
 
+// diagT (pencils): T's gathered diagonals, the same layout as h->diag_h's
 static evec_status batched_build(evec_handle h, int64_t count, const int64_t *n_host,
                                  const int64_t *t_off_host, const uint8_t *select_host,
                                  const std::vector<int> &tiles, const std::vector<int> &idx,
-                                 std::vector<HostPlan> &plans, int64_t *bad) {
+                                 std::vector<HostPlan> &plans, int64_t *bad,
+                                 const double *diagT = nullptr) {
     std::vector<int64_t> roff(count + 1, 0);
     for (int64_t i = 0; i < count; i++) roff[i + 1] = roff[i] + n_host[i];
     plans.resize(count);
@@ -1548,9 +1550,11 @@ static evec_status batched_build(evec_handle h, int64_t count, const int64_t *n_
             const int i = idx[q];
             const int64_t n = n_host[i];
             const double *d = h->diag_h + 3 * roff[i];
+            PencilDiags pd = {nullptr, nullptr};
+            if (diagT) pd = {diagT + 3 * roff[i], diagT + 3 * roff[i] + 2 * n - 1};
             stat[q] = build_plan(n, d, d + n, d + 2 * n - 1,
                                  select_host ? select_host + sel0[i] : nullptr, tiles[i], n,
-                                 plans[i], &where[q]);
+                                 plans[i], &where[q], diagT ? &pd : nullptr);
         }
     };
     int64_t rows = 0;
@@ -1617,11 +1621,18 @@ namespace evec {
 // Pack the plans of the matrices in idx (those with columns), order them by
 // estimated work, and run the persistent kernel once; through the cached
 // graph when use_graph.
+// Pencils: T2_packed / t2_off_host hold the upper triangular T of each
+// pair (T_packed its S), beta_out receives beta per column, gen_tile is the
+// largest tile (no graph: use_graph must be false).
 static evec_status run_batch(evec_handle h, int64_t count, const int64_t *n_host,
                              const double *T_packed, const int64_t *t_off_host,
                              const std::vector<int> &idx, const std::vector<HostPlan> &plans,
                              double *X_packed, int32_t *scale_exp_packed, double *lam_re,
-                             double *lam_im, bool use_graph, int slices) {
+                             double *lam_im, bool use_graph, int slices,
+                             const double *T2_packed = nullptr,
+                             const int64_t *t2_off_host = nullptr, double *beta_out = nullptr,
+                             int gen_tile = 0) {
+    const bool gen = T2_packed != nullptr;
     h->bcall.valid = false;   // the pinned plan buffer is rewritten below
     // output offsets (all matrices, matrix order)
     std::vector<int64_t> xo(count), eo(count);
@@ -1649,6 +1660,7 @@ static evec_status run_batch(evec_handle h, int64_t count, const int64_t *n_host
     Packer sz;
     sz.put(nullptr, (size_t)eacc * 8, 8);
     sz.put(nullptr, (size_t)eacc * 8, 8);
+    if (gen) sz.put(nullptr, (size_t)eacc * 8, 8);
     sz.put(nullptr, (size_t)nb * batch_item_bytes(), 16);
     auto r16 = [](size_t b) { return (b + 15) / 16 * 16; };
     size_t wsb = 0;
@@ -1658,6 +1670,7 @@ static evec_status run_batch(evec_handle h, int64_t count, const int64_t *n_host
         pack_plan(sz, P, dp);
         const size_t N = P.tile_start.size() - 1, segs = N * (size_t)P.m;
         wsb += r16(8 * N * N) + r16(8 * P.blk_start.size()) + r16(8 * segs) + 3 * r16(4 * segs);
+        if (gen) wsb += r16(8 * N * N) + r16(8 * P.blk_start.size());
     }
     EVEC_TRY(grow_host(&h->bplan_h, &h->bplan_h_cap, sz.off + 64));
     EVEC_TRY(grow_device(&h->bplan_d, &h->bplan_cap, sz.off + 64));
@@ -1675,6 +1688,12 @@ static evec_status run_batch(evec_handle h, int64_t count, const int64_t *n_host
         }
         pk.put(re.data(), re.size() * 8, 8);
         pk.put(im.data(), im.size() * 8, 8);
+        if (gen) {
+            std::vector<double> be(eacc);
+            for (int64_t i = 0; i < count; i++)
+                std::copy(plans[i].col_beta.begin(), plans[i].col_beta.end(), be.begin() + eo[i]);
+            pk.put(be.data(), be.size() * 8, 8);
+        }
     }
     const size_t items_off = (pk.off + 15) / 16 * 16;
     pk.put(nullptr, (size_t)nb * batch_item_bytes(), 16);
@@ -1703,6 +1722,17 @@ static evec_status run_batch(evec_handle h, int64_t count, const int64_t *n_host
         B.seg_e = (int32_t *)take(4 * segs);
         B.seg_dx = (int32_t *)take(4 * segs);
         B.seg_dy = (int32_t *)take(4 * segs);
+        B.T2 = nullptr;
+        B.ldt2 = 0;
+        B.t2_base = 0;
+        B.tau2 = B.blk_tau2 = nullptr;
+        if (gen) {
+            B.T2 = T2_packed + t2_off_host[i];
+            B.ldt2 = n_host[i];
+            B.t2_base = t2_off_host[i];
+            B.tau2 = (double *)take(8 * N * N);
+            B.blk_tau2 = (double *)take(8 * P.blk_start.size());
+        }
     }
     memcpy(h->bplan_h + items_off, items.data(), (size_t)nb * sizeof(BatchItem));
     const size_t bytes = pk.off;
@@ -1712,7 +1742,8 @@ static evec_status run_batch(evec_handle h, int64_t count, const int64_t *n_host
         cudaError_t e = cudaMemcpyAsync(h->bplan_d, h->bplan_h, bytes, cudaMemcpyHostToDevice, s2);
         if (e == cudaSuccess) e = cudaMemsetAsync(h->queue_d, 0, sizeof(int), s2);
         if (e == cudaSuccess && nb > 0)
-            e = launch_batched(items_d, nb, h->queue_d, h->status_d, h->nsm, s2, slices);
+            e = launch_batched(items_d, nb, h->queue_d, h->status_d, h->nsm, s2, slices,
+                               gen_tile);
         return e;
     };
     if (!use_graph) {
@@ -1737,7 +1768,8 @@ static evec_status run_batch(evec_handle h, int64_t count, const int64_t *n_host
             if (!h->cap_stream)
                 EVEC_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
             // launch attributes are set outside the capture
-            EVEC_CUDA(launch_batched(nullptr, 0, nullptr, nullptr, h->nsm, h->cap_stream, slices));
+            EVEC_CUDA(
+                launch_batched(nullptr, 0, nullptr, nullptr, h->nsm, h->cap_stream, slices, 0));
             EVEC_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
             cudaError_t e = enqueue(h->cap_stream);
             cudaGraph_t graph = nullptr;
@@ -1761,6 +1793,9 @@ static evec_status run_batch(evec_handle h, int64_t count, const int64_t *n_host
     if (lam_im && eacc)
         EVEC_CUDA(cudaMemcpyAsync(lam_im, h->bplan_h + eacc * 8, eacc * 8, cudaMemcpyHostToDevice,
                                   st));
+    if (gen && beta_out && eacc)
+        EVEC_CUDA(cudaMemcpyAsync(beta_out, h->bplan_h + 2 * eacc * 8, eacc * 8,
+                                  cudaMemcpyHostToDevice, st));
     return EVEC_OK;
 }
 
@@ -1903,6 +1938,55 @@ extern "C" evec_status evec_batched(evec_handle h, int64_t count, const int64_t 
         K.eacc = mtot;
         K.valid = true;
     }
+    if (opt && opt->check) return evec_sync(h, nullptr);
+    return EVEC_OK;
+}
+
+// Batched pencils: S's and T's diagonals gathered (T's first, kept aside),
+// the pencil plans built on the host threads, one persistent launch of the
+// pencil variant.  No graph cache and no tile tuning: one tile for all.
+extern "C" evec_status evec_batched_generalized(
+    evec_handle h, int64_t count, const int64_t *n_host, const double *S_packed,
+    const int64_t *s_off_host, const double *T_packed, const int64_t *t_off_host,
+    const uint8_t *select_host, double *X_packed, int32_t *scale_exp_packed,
+    double *alpha_re_packed, double *alpha_im_packed, double *beta_packed,
+    const evec_opts *opt) {
+    if (!h || count < 0 || count > INT32_MAX ||
+        (count > 0 && (!n_host || !s_off_host || !t_off_host || !S_packed || !T_packed)))
+        return EVEC_EINVAL;
+    const int mode = opt ? opt->mode : EVEC_FP64;
+    if (mode != EVEC_FP64) return EVEC_EINVAL;
+    const int tile = (opt && opt->tile) ? opt->tile : 32;
+    if (tile < 16 || tile > 64) return EVEC_EINVAL;
+    if (count == 0) return EVEC_OK;
+    DeviceGuard g(h->device);
+    if (!g.ok) return EVEC_ECUDA;
+    int64_t rows = 0;
+    for (int64_t i = 0; i < count; i++) {
+        if (n_host[i] < 0 || t_off_host[i] < 0) return EVEC_EINVAL;
+        rows += n_host[i];
+    }
+    h->bcall.valid = false;
+    const size_t ndiag = (size_t)std::max<int64_t>(3 * rows, 1);
+    EVEC_TRY(batched_gather(h, count, n_host, T_packed, t_off_host));
+    std::vector<double> diagT(h->diag_h, h->diag_h + ndiag);
+    EVEC_TRY(batched_gather(h, count, n_host, S_packed, s_off_host));
+    std::vector<int> tiles(count, tile), all(count);
+    for (int64_t i = 0; i < count; i++) all[i] = (int)i;
+    std::vector<HostPlan> &plans = h->bplans;
+    int64_t bad = -1;
+    EVEC_TRY(batched_build(h, count, n_host, s_off_host, select_host, tiles, all, plans, &bad,
+                           diagT.data()));
+    int64_t mtot = 0;
+    int max_tile = 16;
+    for (int64_t i = 0; i < count; i++) {
+        mtot += plans[i].m;
+        max_tile = std::max(max_tile, plans[i].max_tile);
+    }
+    if (mtot > 0 && (!X_packed || !scale_exp_packed)) return EVEC_EINVAL;
+    EVEC_TRY(run_batch(h, count, n_host, S_packed, s_off_host, all, plans, X_packed,
+                       scale_exp_packed, alpha_re_packed, alpha_im_packed, false, 0, T_packed,
+                       t_off_host, beta_packed, max_tile));
     if (opt && opt->check) return evec_sync(h, nullptr);
     return EVEC_OK;
 }

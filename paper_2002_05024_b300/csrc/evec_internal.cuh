@@ -85,6 +85,12 @@ struct BatchItem {
     int32_t *scale_exp;
     double *tau, *blk_tau, *seg_nu;
     int32_t *seg_e, *seg_dx, *seg_dy;
+    // pencils (beta S - alpha T): T here is S, T2 the upper triangular T
+    // with its tile norms; null for a standard problem
+    const double *T2;
+    int64_t ldt2;
+    int64_t t2_base;
+    double *tau2, *blk_tau2;
 };
 
 // ---------------------------------------------------------------------------

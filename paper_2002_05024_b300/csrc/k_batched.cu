@@ -46,11 +46,14 @@ __device__ __forceinline__ void check_entry_b(double v, long long idx, DevStatus
     else if (fabs(v) > kInputMax) report(st, 1 /* EVEC_EINVAL */, idx);
 }
 
-// tau[r N + s] = |T_rs|_inf for r < s, the in-tile block column norms, and
-// validation of every referenced entry (upper part, first subdiagonal of
-// the diagonal tiles).  smem: kBThreads doubles.
-__device__ void cta_tile_norms(const BatchItem &B, double *red, DevStatus *status) {
-    const Plan &P = B.P;
+// tau[r N + s] = |M_rs|_inf for r < s, the in-tile block column norms, and
+// validation of every referenced entry (upper part, and with `lower` the
+// first subdiagonal of the diagonal tiles), errors at base + i + j ld.
+// M is the quasi-triangular matrix, or a pencil's upper triangular T.
+// smem: kBThreads doubles.
+__device__ void cta_tile_norms(const Plan &P, const double *M, int64_t ld, int64_t base,
+                               double *tau_out, double *blk_tau_out, bool lower, double *red,
+                               DevStatus *status) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int N = P.ntiles;
     for (int s = 0; s < N; s++) {
@@ -61,8 +64,8 @@ __device__ void cta_tile_norms(const BatchItem &B, double *red, DevStatus *statu
             for (int i = r0 + tid; i < r1; i += kBThreads) {
                 double rs = 0.0;
                 for (int j = c0; j < c1; j++) {
-                    const double v = B.T[i + (int64_t)j * B.ldt];
-                    check_entry_b(v, B.t_base + i + (int64_t)j * B.ldt, status);
+                    const double v = M[i + (int64_t)j * ld];
+                    check_entry_b(v, base + i + (int64_t)j * ld, status);
                     rs += fabs(v);
                 }
                 sum = fmax(sum, rs);
@@ -71,36 +74,39 @@ __device__ void cta_tile_norms(const BatchItem &B, double *red, DevStatus *statu
             if (lane == 0) red[warp] = sum;
             __syncthreads();
             if (tid == 0)
-                B.tau[(int64_t)r * N + s] = fmax(fmax(red[0], red[1]), fmax(red[2], red[3]));
+                tau_out[(int64_t)r * N + s] = fmax(fmax(red[0], red[1]), fmax(red[2], red[3]));
             __syncthreads();
         }
         for (int j = c0; j < c1; j++)
-            for (int i = c0 + tid; i < c1 && i <= j + 1; i += kBThreads)
-                check_entry_b(B.T[i + (int64_t)j * B.ldt], B.t_base + i + (int64_t)j * B.ldt,
-                              status);
+            for (int i = c0 + tid; i < c1 && i <= j + (lower ? 1 : 0); i += kBThreads)
+                check_entry_b(M[i + (int64_t)j * ld], base + i + (int64_t)j * ld, status);
         for (int k = P.tile_blk[s] + warp; k < P.tile_blk[s + 1]; k += kBThreads / 32) {
             const int q = P.blk_start[k];
             const int bs = P.blk_size[k];
             double mx = 0.0;
             for (int i = c0 + lane; i < q; i += 32) {
-                double a = fabs(B.T[i + (int64_t)q * B.ldt]);
-                if (bs == 2) a += fabs(B.T[i + (int64_t)(q + 1) * B.ldt]);
+                double a = fabs(M[i + (int64_t)q * ld]);
+                if (bs == 2) a += fabs(M[i + (int64_t)(q + 1) * ld]);
                 mx = fmax(mx, a);
             }
             mx = bwarp_max(mx);
-            if (lane == 0) B.blk_tau[k] = mx;
+            if (lane == 0) blk_tau_out[k] = mx;
         }
     }
 }
 
 // Updates of step s: for every 64-column block of the active columns and
 // every tile r < s, Y_r <- 2^dy Y_r - T_rs (2^dx X_s) with the new column
-// maxima.  Thread (tx, ty) = (tid % 16, tid / 16) owns rows ty + 8 i
+// maxima (GEN: Y_r <- 2^dy Y_r - [S_rs (beta X~) - T_rs (alpha X~)] with
+// X~ = 2^dx X_s, two accumulation passes over the same registers; alpha
+// mixes a pair's (Re, Im) columns, (alpha x)_re = ar xr - ai xi,
+// (alpha x)_im = ar xi + ai xr).  Thread (tx, ty) = (tid % 16, tid / 16) owns rows ty + 8 i
 // (i < 8) and columns tx + 16 j (j < 4) of the 64 x 64 block.  X_s is
 // staged scaled by 2^dx[r, j] before the product (exact): the protection
 // decisions bound the product of the scaled operands, not of the unscaled
 // ones, which may overflow.
 // smem: Bs [64][65], As [64][64], red [8][64] doubles, sdx / sdy [64] ints.
+template <bool GEN>
 __device__ void cta_tile_update(const BatchItem &B, int s, double *smem) {
     const Plan &P = B.P;
     const int64_t m = P.m;
@@ -127,32 +133,59 @@ __device__ void cta_tile_update(const BatchItem &B, int s, double *smem) {
                 sdx[tid] = dx;
                 sdy[tid] = dy;
             }
-            for (int e = tid; e < 64 * 64; e += kBThreads) {
-                const int i = e % 64, k = e / 64;
-                As[k * 64 + i] = (i < rows && k < K) ? B.T[(r0 + i) + (int64_t)(k0 + k) * B.ldt] : 0.0;
-            }
-            __syncthreads();   // sdx is read by the staging of X_s below
-            for (int e = tid; e < 64 * 64; e += kBThreads) {
-                const int k = e % 64, j = e / 64;
-                Bs[k * 65 + j] =
-                    (k < K && j < nc) ? scale2(Y[(k0 + k) + (j0 + j) * ldy], sdx[j]) : 0.0;
-            }
-            __syncthreads();
             double acc[8][4];
 #pragma unroll
             for (int i = 0; i < 8; i++)
 #pragma unroll
                 for (int j = 0; j < 4; j++) acc[i][j] = 0.0;
-            for (int k = 0; k < K; k++) {
-                double a[8], b[4];
+            // pass 0: A = T_rs (S_rs for a pencil); pass 1 (pencils): A = T2_rs
+            for (int pass = 0; pass < (GEN ? 2 : 1); pass++) {
+                const double *A = pass == 0 ? B.T : B.T2;
+                const int64_t lda = pass == 0 ? B.ldt : B.ldt2;
+                if (pass == 1) __syncthreads();   // the first pass's readers are done
+                for (int e = tid; e < 64 * 64; e += kBThreads) {
+                    const int i = e % 64, k = e / 64;
+                    As[k * 64 + i] =
+                        (i < rows && k < K) ? A[(r0 + i) + (int64_t)(k0 + k) * lda] : 0.0;
+                }
+                __syncthreads();   // sdx is read by the staging of X_s below
+                for (int e = tid; e < 64 * 64; e += kBThreads) {
+                    const int k = e % 64, j = e / 64;
+                    double v = 0.0;
+                    if (k < K && j < nc) {
+                        const int64_t c = j0 + j;
+                        v = scale2(Y[(k0 + k) + c * ldy], sdx[j]);
+                        if constexpr (GEN) {
+                            const int u = P.col_unit[c];
+                            const double ar = P.unit_lam[2 * u], ai = P.unit_lam[2 * u + 1];
+                            if (pass == 0) {
+                                v *= P.unit_beta[u];
+                            } else {
+                                double ax = ar * v;
+                                if (ai != 0.0) {   // the pair partner, same scale
+                                    const bool re = c == P.unit_col[u];
+                                    const double xp =
+                                        scale2(Y[(k0 + k) + (re ? c + 1 : c - 1) * ldy], sdx[j]);
+                                    ax = re ? fma(ar, v, -ai * xp) : fma(ar, v, ai * xp);
+                                }
+                                v = -ax;
+                            }
+                        }
+                    }
+                    Bs[k * 65 + j] = v;
+                }
+                __syncthreads();
+                for (int k = 0; k < K; k++) {
+                    double a[8], b[4];
 #pragma unroll
-                for (int i = 0; i < 8; i++) a[i] = As[k * 64 + ty + 8 * i];
+                    for (int i = 0; i < 8; i++) a[i] = As[k * 64 + ty + 8 * i];
 #pragma unroll
-                for (int j = 0; j < 4; j++) b[j] = Bs[k * 65 + tx + 16 * j];
+                    for (int j = 0; j < 4; j++) b[j] = Bs[k * 65 + tx + 16 * j];
 #pragma unroll
-                for (int i = 0; i < 8; i++)
+                    for (int i = 0; i < 8; i++)
 #pragma unroll
-                    for (int j = 0; j < 4; j++) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+                        for (int j = 0; j < 4; j++) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+                }
             }
             double cmax[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
@@ -481,7 +514,8 @@ __device__ void cta_finalize_unit(const BatchItem &B, int u, int *sbest) {
 
 }  // namespace
 
-template <bool SPLIT>
+// GEN: every item is a pencil (beta S - alpha T), FP64 updates only.
+template <bool SPLIT, bool GEN>
 __global__ void __launch_bounds__(kBThreads)
     k_batched(const BatchItem *__restrict__ items, int count, int *queue, DevStatus *status,
               int S) {
@@ -517,17 +551,26 @@ __global__ void __launch_bounds__(kBThreads)
         if (k >= count) break;
         const BatchItem B = items[k];
         const Plan &P = B.P;
-        cta_tile_norms(B, smem, status);
+        cta_tile_norms(P, B.T, B.ldt, B.t_base, B.tau, B.blk_tau, true, smem, status);
         __syncthreads();
+        Pencil pen;
+        if constexpr (GEN) {
+            cta_tile_norms(P, B.T2, B.ldt2, B.t2_base, B.tau2, B.blk_tau2, false, smem, status);
+            __syncthreads();
+            pen.T = B.T2;
+            pen.ldt = B.ldt2;
+            pen.tau = B.tau2;
+            pen.blk_tau = B.blk_tau2;
+        }
         for (int s = P.ntiles - 1; s >= 0; s--) {
             for (int pos = P.tile_real[s]; pos < P.nreal; pos += Lanes<false>::U * 4) {
-                diag_tile<4, false>(s, pos, B.T, B.ldt, P, B.tau, B.blk_tau, B.X, B.ldx,
-                                    B.seg_e, B.seg_nu, B.seg_dx, B.seg_dy, smem);
+                diag_tile<4, false, GEN>(s, pos, B.T, B.ldt, P, B.tau, B.blk_tau, B.X, B.ldx,
+                                         B.seg_e, B.seg_nu, B.seg_dx, B.seg_dy, smem, pen);
                 __syncthreads();
             }
             for (int pos = P.tile_cplx[s]; pos < P.ncplx; pos += Lanes<true>::U * 4) {
-                diag_tile<4, true>(s, pos, B.T, B.ldt, P, B.tau, B.blk_tau, B.X, B.ldx,
-                                   B.seg_e, B.seg_nu, B.seg_dx, B.seg_dy, smem);
+                diag_tile<4, true, GEN>(s, pos, B.T, B.ldt, P, B.tau, B.blk_tau, B.X, B.ldx,
+                                        B.seg_e, B.seg_nu, B.seg_dx, B.seg_dy, smem, pen);
                 __syncthreads();
             }
             if (s > 0 && P.tile_col[s] < P.m) {
@@ -538,7 +581,7 @@ __global__ void __launch_bounds__(kBThreads)
                         break;
                     }
                 } else {
-                    cta_tile_update(B, s, smem);
+                    cta_tile_update<GEN>(B, s, smem);
                 }
                 __syncthreads();
             }
@@ -556,8 +599,11 @@ __global__ void __launch_bounds__(kBThreads)
     }
 }
 
-size_t batched_smem_bytes(bool split) {
+// gen_tile > 0: a batch of pencils whose tiles have at most gen_tile rows
+// (the diagonal-tile solver also holds T's tile)
+size_t batched_smem_bytes(bool split, int gen_tile) {
     const size_t upd = sizeof(double) * (64 * 65 + 64 * 64 + 8 * 64) + sizeof(int) * 128;
+    if (gen_tile > 0) return std::max(diag_smem<4, true>(gen_tile), upd);
     // the split variant aligns its operand tiles to 1024 bytes; its size
     // also keeps at most two CTAs (2 x 256 TMEM columns) on an SM
     const size_t base = std::max(diag_smem<4>(64), upd);
@@ -565,12 +611,14 @@ size_t batched_smem_bytes(bool split) {
 }
 
 // One persistent launch: grid = SMs x CTAs per SM (occupancy query); S > 0
-// runs the split-precision variant (S digit slices).
+// runs the split-precision variant (S digit slices); gen_tile > 0 the
+// pencil variant (FP64, tiles of at most gen_tile rows).
 cudaError_t launch_batched(const BatchItem *items, int count, int *queue, DevStatus *status,
-                           int nsm, cudaStream_t st, int S) {
-    const bool split = S > 0;
-    const size_t smem = batched_smem_bytes(split);
-    auto kern = split ? k_batched<true> : k_batched<false>;
+                           int nsm, cudaStream_t st, int S, int gen_tile) {
+    const bool split = S > 0 && gen_tile == 0;
+    const size_t smem = batched_smem_bytes(split, gen_tile);
+    auto kern = gen_tile > 0 ? k_batched<false, true>
+                             : (split ? k_batched<true, false> : k_batched<false, false>);
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                          cudaSharedmemCarveoutMaxShared);

@@ -1,0 +1,128 @@
+"""Batched pencils (evec_batched_generalized: the persistent kernel's pencil
+variant) against the CPU oracle, pencil by pencil: (alpha, beta)
+bit-identical, exponents +-1, columns within 1e-10 normwise relative,
+normalised residual ||beta S y - alpha T y||_1 / ((|beta| ||S||_1 +
+|alpha| ||T||_1) ||y||_1 u) <= 10 n, zeros below each block; mixed sizes,
+selections, every tile, edge sizes and errors."""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2002_05024_b300 as ev
+import workloads
+from evec_checks import canonical_norms, compare_canonical, generalized_residuals
+
+pytestmark = pytest.mark.gpu
+
+
+def _batch(sizes, seed, fraction=None):
+    pairs, sels = [], []
+    for i, n in enumerate(sizes):
+        S, T, blocks = workloads.generalized_pair(int(n), seed=seed + i)
+        pairs.append((S, T))
+        if fraction is None:
+            sels.append(None)
+        else:
+            sels.append(workloads.random_eigen_selection(int(n), blocks, fraction, seed=seed + 500 + i))
+    return pairs, sels
+
+
+def _check(pairs, sels, outs, rel_tol=1e-10):
+    worst = 0.0
+    for (S, T), sel, out in zip(pairs, sels, outs):
+        X, e, ar, ai, be = (t.cpu().numpy() for t in out)
+        Xo, eo, aro, aio, beo = oracle.generalized(S, T, select=sel)
+        assert X.shape == Xo.shape
+        if Xo.shape[1] == 0:
+            continue
+        np.testing.assert_array_equal(ar, aro)
+        np.testing.assert_array_equal(ai, aio)
+        np.testing.assert_array_equal(be, beo)
+        assert np.isfinite(X).all()
+        nr = canonical_norms(X, ai)
+        assert nr.min() >= 1.0 and nr.max() < 2.0
+        de, rel = compare_canonical(Xo, eo, X, e, aio)
+        assert de <= 1, de
+        worst = max(worst, rel)
+        r = generalized_residuals(S, T, X, ar, ai, be)
+        assert r.max() <= 10 * S.shape[0], r.max()
+    assert worst <= rel_tol, worst
+    return worst
+
+
+@pytest.mark.parametrize("tile", [16, 32, 64])
+def test_batched_pencils_tiles(tile):
+    sizes = workloads.batch_sizes(24, seed=31, lo=8, hi=200)
+    pairs, sels = _batch(sizes, seed=1000 + tile)
+    outs = ev.batched_generalized(pairs, tile=tile)
+    _check(pairs, sels, outs)
+
+
+def test_batched_pencils_selection_and_edges():
+    sizes = [1, 2, 3, 40, 130, 7, 64, 65, 250]
+    pairs, sels = _batch(sizes, seed=77, fraction=0.3)
+    sels[1] = np.zeros(2, np.uint8)          # nothing selected in one pencil
+    outs = ev.batched_generalized(pairs, selects=sels)
+    _check(pairs, sels, outs)
+    # the selected columns agree with the same columns of the full result
+    full = ev.batched_generalized(pairs)
+    for (S, T), sel, o, f in zip(pairs, sels, outs, full):
+        if sel is None or not sel.any():
+            continue
+        n = S.shape[0]
+        cols, col, i = [], 0, 0
+        while i < n:
+            sz = 2 if i + 1 < n and S[i + 1, i] != 0.0 else 1
+            if sel[i] or (sz == 2 and sel[i + 1]):
+                cols.extend(range(col, col + sz))
+            col += sz
+            i += sz
+        Xf, ef, aif = (f[k].cpu().numpy() for k in (0, 1, 3))
+        de, rel = compare_canonical(Xf[:, cols], ef[cols], o[0].cpu().numpy(),
+                                    o[1].cpu().numpy(), aif[cols])
+        assert de == 0 and rel <= 1e-13, (de, rel)
+
+
+def test_batched_pencils_match_single_pencil_path():
+    # the persistent kernel and the single-pencil launches run the same
+    # per-tile steps: results agree to rounding
+    sizes = [90, 150, 33]
+    pairs, sels = _batch(sizes, seed=5)
+    outs = ev.batched_generalized(pairs, tile=32)
+    for (S, T), out in zip(pairs, outs):
+        dS = torch.from_numpy(np.asfortranarray(S)).cuda()
+        dT = torch.from_numpy(np.asfortranarray(T)).cuda()
+        X1, e1, ar1, ai1, be1 = ev.generalized(dS, dT, None, tile=32, check=True)
+        np.testing.assert_array_equal(out[2].cpu().numpy(), ar1.cpu().numpy())
+        np.testing.assert_array_equal(out[4].cpu().numpy(), be1.cpu().numpy())
+        de, rel = compare_canonical(X1.cpu().numpy(), e1.cpu().numpy(), out[0].cpu().numpy(),
+                                    out[1].cpu().numpy(), ai1.cpu().numpy())
+        assert de <= 1 and rel <= 1e-12, (de, rel)
+
+
+def test_batched_pencils_errors():
+    sizes = [40, 60, 30]
+    pairs, _ = _batch(sizes, seed=9)
+    S1, T1 = pairs[1]
+    bad = T1.copy()
+    bad[5, 50] = np.nan                      # T of the second pencil
+    pairs_bad = [pairs[0], (S1, bad), pairs[2]]
+    with pytest.raises(ev.EvecError) as ei:
+        ev.batched_generalized(pairs_bad)
+    assert ei.value.status == ev.EVEC_ENONFINITE
+    assert ei.value.bad == 40 * 40 + 5 + 50 * 60      # offset in the packed T
+    # split mode is not offered for pencils in the batch
+    Sp, ns, offs = ev.pack_batch([S for S, _ in pairs])
+    Tp, _, _ = ev.pack_batch([T for _, T in pairs])
+    h = ev.handle(0)
+    opts = ev._opts(0, False, "split", 0)
+    st = ev.lib().evec_batched_generalized(h.ptr, 3, ev._np_ptr(ns), Sp.data_ptr(),
+                                           ev._np_ptr(offs), Tp.data_ptr(), ev._np_ptr(offs),
+                                           None, None, None, None, None, None,
+                                           ctypes.byref(opts))
+    assert st == ev.EVEC_EINVAL
+    # the handle stays usable
+    _check(pairs, [None] * 3, ev.batched_generalized(pairs))
