@@ -63,12 +63,14 @@ def parse_args():
     ap.add_argument("--cpu-sample", type=int, default=4096,
                     help="columns of the CPU-oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["single", "batched", "generalized", "trsolve"],
+    ap.add_argument("--workload", choices=["single", "batched", "generalized", "trsolve",
+                                           "batched_generalized"],
                     default="single",
                     help="single: one n x n Schur form with Q (default); batched: the "
                          "2000-matrix batch of evec_batched; generalized: an n x n pencil "
                          "(S, T) with Z (use --n 8192); trsolve: robust solve of an n x n "
-                         "quasi-triangular T with --nrhs right-hand sides")
+                         "quasi-triangular T with --nrhs right-hand sides; "
+                         "batched_generalized: --batch pencils in one persistent launch")
     ap.add_argument("--nrhs", type=int, default=0, help="trsolve: right-hand sides (default n)")
     ap.add_argument("--side", choices=["right", "left"], default="right",
                     help="single: right eigenvectors (default) or left ones (u^H T = lambda u^H)")
@@ -807,6 +809,146 @@ def run_batched(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+def run_batched_generalized(args, rank, world, local_rank):
+    """Batched pencils: --batch independent pencils (S_i, T_i) built like the
+    single pencil workload (S config-0, T upper triangular, diagonal
+    U[0.5, 2], every 50th 1e-12), sizes log-uniform in [32, 1024], 30% of the
+    blocks selected, no Z; one evec_batched_generalized call per step (the
+    persistent kernel's pencil variant, FP64).  Algorithmic flops 2 k_j^2
+    per selected column (two products per substitution step)."""
+    import torch
+
+    import paper_2002_05024_b300 as ev
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    sizes, pairs, sels = workloads.batch_pencils(args.batch)
+    Sp, ns, soffs = ev.pack_batch([S for S, _ in pairs], device=local_rank)
+    Tp, _, toffs = ev.pack_batch([T for _, T in pairs], device=local_rank)
+    sel = np.concatenate(sels)
+    out = ev.batched_generalized_packed(Sp, Tp, ns, soffs, toffs, sel, tile=args.tile)
+    m = out[5]
+    cols = int(m.sum())
+    F = 0.0
+    for (S, _), s_ in zip(pairs, sels):
+        n = S.shape[0]
+        i = 0
+        while i < n:
+            sz = 2 if i + 1 < n and S[i + 1, i] != 0.0 else 1
+            if s_[i] or (sz == 2 and s_[i + 1]):
+                F += sz * 2.0 * float(i) * float(i)
+            i += sz
+
+    def step():
+        ev.batched_generalized_packed(Sp, Tp, ns, soffs, toffs, sel, tile=args.tile, out=out)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    h = ev.handle(local_rank)
+    sampler = ClockSampler() if rank == 0 else None
+    if dist:
+        dist.barrier()
+    stream = torch.cuda.current_stream(dev)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        step()
+    t1.record(stream)
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    elapsed = t0.elapsed_time(t1)
+    clocks = sampler.stop() if sampler else None
+    prof = profiled_steps(h, step, args.steps, dev)
+    ev.sync(local_rank)
+    if dist:
+        tt = torch.tensor([elapsed], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        elapsed = float(tt.item())
+    value = world * cols * args.steps / (elapsed / 1e3)
+    # end to end: S and T from pinned host memory, X and exponents back
+    hS = torch.empty(Sp.numel(), dtype=torch.float64, pin_memory=True)
+    hS.copy_(Sp.cpu())
+    hT = torch.empty(Tp.numel(), dtype=torch.float64, pin_memory=True)
+    hT.copy_(Tp.cpu())
+    hX = torch.empty(out[0].numel(), dtype=torch.float64, pin_memory=True)
+    hE = torch.empty(out[1].numel(), dtype=torch.int32, pin_memory=True)
+    w0 = time.perf_counter()
+    for _ in range(args.steps):
+        Sp.copy_(hS, non_blocking=True)
+        Tp.copy_(hT, non_blocking=True)
+        step()
+        hX.copy_(out[0], non_blocking=True)
+        hE.copy_(out[1], non_blocking=True)
+        torch.cuda.synchronize(dev)
+    e2e = {"value": world * cols * args.steps / (time.perf_counter() - w0),
+           "unit": "columns/s", "h2d_bytes_per_step": (Sp.numel() + Tp.numel()) * 8,
+           "d2h_bytes_per_step": out[0].numel() * 8 + out[1].numel() * 4}
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    peaks = measured_peaks()
+    fp64_peak = N_SMS * FP64_FLOP_PER_CLK_PER_SM * float(peaks.get("sm_max_mhz", 2032.0)) / 1e6
+    kms = prof.get("batched", (0.0, 0))[0] / args.steps
+    launches = prof.get("batched", (0.0, 0))[1] / args.steps
+    achieved = F / (kms / 1e3) / 1e12 if kms > 0 else None
+    roofline = {"kernel": "k_batched (pencils)", "bound": "alu", "achieved": achieved,
+                "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp64_peak if achieved else None, "traffic": None,
+                "peak_source": "of derived FP64 peak (measured 4 flop/clk/SM x 148 SMs x max "
+                               "SM clock)",
+                "launches_per_step": launches, "alg_flops_per_launch": F / max(launches, 1)}
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        rng = np.random.default_rng(9)
+        pick = rng.choice(len(pairs), size=min(len(pairs), 200), replace=False)
+        t = time.perf_counter()
+        cc = 0
+        for i in pick:
+            X = oracle.generalized(pairs[i][0], pairs[i][1], select=sels[i])[0]
+            cc += X.shape[1]
+        dt = time.perf_counter() - t
+        cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+        cpu = {"value": cc / dt, "unit": "columns/s",
+               "cores": int(os.environ.get("OMP_NUM_THREADS", cores)), "kind": "oracle",
+               "sample": f"{len(pick)} randomly chosen pencils of the batch ({cc} columns), "
+                         f"{dt:.2f} s"}
+    line = {
+        "metric": "eigvec columns/s, batched pencils (robust FP64 generalized eigenvectors)",
+        "value": value, "unit": "columns/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"batch of {args.batch} pencils, n log-uniform in [32, 1024] "
+                               "(S config-0, T diag U[0.5, 2] with every 50th 1e-12), 30% of "
+                               "blocks selected, no Z, one persistent launch per step",
+                   "matrices": args.batch, "columns": cols, "tile": args.tile or 32,
+                   "mode": "fp64", "parallelism": "replicas",
+                   "l2": f"inputs {(Sp.numel() + Tp.numel()) * 8 / 2**30:.1f} GiB, larger "
+                         "than L2"},
+        "tflops_fp64": F * args.steps / (elapsed / 1e3) / 1e12,
+        "flops_per_step": F,
+        "roofline": roofline,
+        "rooflines": {"fp64": roofline},
+        "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+        "gpu_launches": sum(c for _, c in prof.values()),
+        "clocks": clocks,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
 def run_generalized(args, rank, world, local_rank):
     """The pencil workload: S config-0 (n x n), T upper triangular with
     diagonal U[0.5, 2] (every 50th entry 1e-12) and N(0, 1) upper part, Z from
@@ -1130,6 +1272,8 @@ def main():
         run_generalized(args, rank, world, local_rank)
     elif args.workload == "trsolve":
         run_trsolve(args, rank, world, local_rank)
+    elif args.workload == "batched_generalized":
+        run_batched_generalized(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 

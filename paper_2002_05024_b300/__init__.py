@@ -507,33 +507,50 @@ def batched(Ts, selects=None, tile: int = 0, mode: str = "fp64", check: bool = T
     return out
 
 
+def batched_generalized_packed(S_packed, T_packed, ns, s_offs, t_offs, select=None,
+                               tile: int = 0, check: bool = False, out=None):
+    """evec_batched_generalized on packed device buffers (FP64).  Returns
+    (X_packed, scale_exp, alpha_re, alpha_im, beta, m) with the output
+    packing of evec_batched; out = that tuple from an earlier call on the
+    same layout skips the column count."""
+    import torch
+    h = handle(S_packed.device.index)
+    ns = np.ascontiguousarray(ns, dtype=np.int64)
+    s_offs = np.ascontiguousarray(s_offs, dtype=np.int64)
+    t_offs = np.ascontiguousarray(t_offs, dtype=np.int64)
+    sel = None if select is None else np.ascontiguousarray(select, dtype=np.uint8)
+    if out is not None:
+        X, e, ar, ai, be, m = out
+    else:
+        m = batched_count(S_packed, ns, s_offs, sel)
+        dev = S_packed.device
+        X = torch.empty(int((ns * m).sum()), dtype=torch.float64, device=dev)
+        e = torch.empty(int(m.sum()), dtype=torch.int32, device=dev)
+        ar = torch.empty(int(m.sum()), dtype=torch.float64, device=dev)
+        ai = torch.empty(int(m.sum()), dtype=torch.float64, device=dev)
+        be = torch.empty(int(m.sum()), dtype=torch.float64, device=dev)
+    opts = _opts(tile, False, "fp64", 0)
+    st = lib().evec_batched_generalized(h.ptr, len(ns), _np_ptr(ns), S_packed.data_ptr(),
+                                        _np_ptr(s_offs), T_packed.data_ptr(), _np_ptr(t_offs),
+                                        _np_ptr(sel), X.data_ptr(), e.data_ptr(), ar.data_ptr(),
+                                        ai.data_ptr(), be.data_ptr(), ctypes.byref(opts))
+    _check(st, "evec_batched_generalized")
+    if check:
+        h.sync()
+    return X, e, ar, ai, be, m
+
+
 def batched_generalized(pairs, selects=None, tile: int = 0, check: bool = True):
     """Generalized eigenvectors of a list of pencils [(S_i, T_i), ...] (numpy
-    or torch matrices, packed here) in one persistent launch (FP64).  Returns a list of
-    (X_i (n_i, m_i), scale_exp_i, alpha_re_i, alpha_im_i, beta_i)."""
-    import torch
+    or torch matrices, packed here) in one persistent launch (FP64).  Returns
+    a list of (X_i (n_i, m_i), scale_exp_i, alpha_re_i, alpha_im_i, beta_i)."""
     Sp, ns, soffs = pack_batch([S for S, _ in pairs])
     Tp, _, toffs = pack_batch([T for _, T in pairs])
     sel = None
     if selects is not None:
         sel = np.concatenate([np.ones(n, np.uint8) if s is None else
                               np.ascontiguousarray(s, dtype=np.uint8) for s, n in zip(selects, ns)])
-    m = batched_count(Sp, ns, soffs, sel)
-    dev = Sp.device
-    X = torch.empty(int((ns * m).sum()), dtype=torch.float64, device=dev)
-    e = torch.empty(int(m.sum()), dtype=torch.int32, device=dev)
-    ar = torch.empty(int(m.sum()), dtype=torch.float64, device=dev)
-    ai = torch.empty(int(m.sum()), dtype=torch.float64, device=dev)
-    be = torch.empty(int(m.sum()), dtype=torch.float64, device=dev)
-    h = handle(dev.index)
-    opts = _opts(tile, False, "fp64", 0)
-    st = lib().evec_batched_generalized(h.ptr, len(ns), _np_ptr(ns), Sp.data_ptr(),
-                                        _np_ptr(soffs), Tp.data_ptr(), _np_ptr(toffs),
-                                        _np_ptr(sel), X.data_ptr(), e.data_ptr(), ar.data_ptr(),
-                                        ai.data_ptr(), be.data_ptr(), ctypes.byref(opts))
-    _check(st, "evec_batched_generalized")
-    if check:
-        h.sync()
+    X, e, ar, ai, be, m = batched_generalized_packed(Sp, Tp, ns, soffs, toffs, sel, tile, check)
     out = []
     xo = eo = 0
     for n, mi in zip(ns, m):

@@ -10,6 +10,7 @@ from .schur_inputs import (  # noqa: F401
     SEED_BASE,
     adversarial_schur,
     batch_inputs,
+    batch_pencils,
     batch_sizes,
     block_selection,
     config0_schur,

@@ -225,3 +225,18 @@ def batch_inputs(count: int, seed: int = SEED_BASE + 3, fraction: float = 0.3,
         Ts.append(T)
         sels.append(block_selection(int(n), blocks, fraction, seed=s + 7))
     return sizes, Ts, sels
+
+
+def batch_pencils(count: int, seed: int = SEED_BASE + 5, fraction: float = 0.3):
+    """Batch of independent pencils (S_i, T_i) built like ``generalized_pair``:
+    sizes from ``batch_sizes``, member i with seed SEED_BASE*10 + 5000 + i,
+    ``fraction`` of each member's blocks selected.  Returns (sizes, list of
+    (S, T), list of selection masks)."""
+    sizes = batch_sizes(count, seed)
+    pairs, sels = [], []
+    for i, n in enumerate(sizes):
+        s = SEED_BASE * 10 + 5000 + i
+        S, T, blocks = generalized_pair(int(n), seed=s)
+        pairs.append((S, T))
+        sels.append(block_selection(int(n), blocks, fraction, seed=s + 7))
+    return sizes, pairs, sels
