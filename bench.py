@@ -72,6 +72,8 @@ def parse_args():
                          "quasi-triangular T with --nrhs right-hand sides; "
                          "batched_generalized: --batch pencils in one persistent launch")
     ap.add_argument("--nrhs", type=int, default=0, help="trsolve: right-hand sides (default n)")
+    ap.add_argument("--lookahead", action="store_true",
+                    help="split mode: the look-ahead schedule (evec_set_lookahead)")
     ap.add_argument("--side", choices=["right", "left"], default="right",
                     help="single: right eigenvectors (default) or left ones (u^H T = lambda u^H)")
     ap.add_argument("--batch", type=int, default=2000)
@@ -446,6 +448,7 @@ def run_ours(args, rank, world, local_rank):
 
     left = args.side == "left"
     solve = ev.left if left else ev.standard
+    ev.handle(local_rank).lookahead(args.lookahead)
 
     def step():
         solve(dT, dQ, tile=args.tile, out=out, mode=args.mode, slices=args.slices, refine=refine)
@@ -600,6 +603,7 @@ def run_ours(args, rank, world, local_rank):
                    "n": n, "columns": m, "tile": args.tile or 64, "mode": args.mode,
                    "slices": (args.slices or 8) if args.mode == "split" else None,
                    "refine": refine, "side": args.side,
+                   "lookahead": args.lookahead,
                    "parallelism": "replicas",
                    "l2": "inputs larger than L2 (T, Q, X 128 MiB each)"},
         "tflops_fp64": tflops,
@@ -1133,6 +1137,8 @@ def run_trsolve(args, rank, world, local_rank):
 
     def step():
         ev.trsolve(dT, dB, tile=args.tile, mode=args.mode, slices=args.slices, out=(X, e))
+
+    ev.handle(local_rank).lookahead(args.lookahead)
 
     for _ in range(args.warmup):
         step()

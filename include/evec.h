@@ -214,6 +214,16 @@ enum {
     EVEC_K_COUNT = 10
 };
 
+/* Look-ahead schedule of the split-mode solve (default off): the diagonal
+ * solve of step s leaves its protection decisions to a separate launch, and
+ * the update of step s is cut at the 128-row block holding tile s - 1: that
+ * head runs before the next diagonal solve, the rest on a second stream of
+ * the handle beside it, on the SMs the solve leaves free.  The results are
+ * bit-identical either way (same arithmetic per element).  On B300 at
+ * n = 4096 it is slower (the next diagonal solve needs most SMs, so the
+ * rest of the update runs on few), hence off by default. */
+evec_status evec_set_lookahead(evec_handle h, int enable);
+
 /* Enable (1) or disable (0) per-kernel timing: while enabled, every kernel
  * launch of the handle is bracketed by CUDA events on the handle's stream. */
 evec_status evec_profile(evec_handle h, int enable);

@@ -83,6 +83,7 @@ def lib() -> ctypes.CDLL:
         L.evec_plan_query.argtypes = [i64, p, p, p, p, ctypes.c_int, ctypes.POINTER(i64),
                                       ctypes.POINTER(i32), p, ctypes.POINTER(i64)]
         L.evec_profile.argtypes = [p, ctypes.c_int]
+        L.evec_set_lookahead.argtypes = [p, ctypes.c_int]
         L.evec_profile_read.argtypes = [p, p, p, ctypes.c_int]
         L.evec_last_cuda_error.argtypes = []
         L.evec_last_cuda_error.restype = ctypes.c_char_p
@@ -102,7 +103,7 @@ def lib() -> ctypes.CDLL:
                   "evec_standard", "evec_standard_left", "evec_standard_host", "evec_sync",
                   "evec_plan_query", "evec_trsolve",
                   "evec_profile", "evec_profile_read", "evec_batched_count", "evec_batched",
-                  "evec_batched_generalized",
+                  "evec_batched_generalized", "evec_set_lookahead",
                   "evec_generalized",
                   "evec_tune_get", "evec_tune_set"):
             getattr(L, f).restype = ctypes.c_int
@@ -159,6 +160,10 @@ class Handle:
         bad = ctypes.c_int64(-1)
         st = lib().evec_sync(self._h, ctypes.byref(bad))
         _check(st, "evec_sync", bad.value)
+
+    def lookahead(self, enable: bool):
+        """Look-ahead schedule of the split-mode solve (off by default)."""
+        _check(lib().evec_set_lookahead(self._h, 1 if enable else 0), "evec_set_lookahead")
 
     def profile(self, enable: bool):
         _check(lib().evec_profile(self._h, 1 if enable else 0), "evec_profile")

@@ -264,7 +264,7 @@ __device__ void diag_tile(int s, int list_pos0, const double *__restrict__ T, in
                           const double *__restrict__ blk_tau, double *__restrict__ Y, int64_t ldy,
                           int32_t *__restrict__ seg_e, double *__restrict__ seg_nu,
                           int32_t *__restrict__ seg_dx, int32_t *__restrict__ seg_dy,
-                          double *smem, const Pencil &pen = Pencil()) {
+                          double *smem, const Pencil &pen = Pencil(), bool decide = true) {
     constexpr int G = Lanes<C, GR>::G;
     constexpr int kThreads = 32 * W;
     constexpr int kUnits = Lanes<C, GR>::U * W;
@@ -592,8 +592,9 @@ __device__ void diag_tile(int s, int list_pos0, const double *__restrict__ T, in
     // consolidation + protection decisions (Sec. 3.4): thread -> (unit,
     // tile row), consecutive threads on consecutive columns; four items per
     // thread per round so their loads are in flight together
+    // (decide == false: a separate launch takes them, k_decide)
     constexpr int kBatch = 4;
-    const int items = kUnits * s;
+    const int items = decide ? kUnits * s : 0;
     for (int base = tid; base < items; base += kBatch * kThreads) {
         int er[kBatch];
         double nur[kBatch];

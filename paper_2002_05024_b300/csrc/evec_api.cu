@@ -36,7 +36,10 @@ int launch_diag_solve(int s, const double *T, int64_t ldt, const Plan &p,
                        const int32_t *tile_cplx_h,
                        const double *tau, const double *blk_tau, double *Y, int64_t ldy,
                        int32_t *seg_e, double *seg_nu, int32_t *seg_dx, int32_t *seg_dy,
-                       cudaStream_t st, const Pencil *pen = nullptr, bool rhs = false);
+                       cudaStream_t st, const Pencil *pen = nullptr, bool rhs = false,
+                       bool decide = true, int *sms = nullptr);
+void launch_decide(int s, const Plan &p, int64_t c0, const double *tau, int32_t *seg_e,
+                   double *seg_nu, int32_t *seg_dx, int32_t *seg_dy, bool rhs, cudaStream_t st);
 void launch_residual(const double *T, int64_t ldt, const Plan &p, int ntiles, int max_tile,
                      const double *Y, int64_t ldy, const int32_t *seg_e,
                      const int32_t *row_tile, double *R, int64_t ldr, cudaStream_t st);
@@ -108,6 +111,14 @@ cudaError_t split_update_step_resident(const SplitUpdateCtx &ctx, int t0, int ts
                                        const int32_t *dy, double *seg_nu, int *err, int nsm,
                                        cudaStream_t st, const double *rhs = nullptr,
                                        int64_t ldr = 0);
+cudaError_t split_slice_xs(const SplitUpdateCtx &ctx, int t0, int ts, int col0, int m,
+                           const double *Y, int64_t ldy, __nv_bfloat16 *sb, int *eb,
+                           cudaStream_t st, const double *rhs, int64_t ldr);
+cudaError_t split_update_rows(const SplitUpdateCtx &ctx, int t0, int ts, int prow0, int pea,
+                              int col0, int m, double *Y, int64_t ldy, const int *ea_panels,
+                              const int *eb, const int32_t *row_tile, const int32_t *dx,
+                              const int32_t *dy, double *seg_nu, int *err, int rb0, int rb1,
+                              int cap, cudaStream_t st, bool pencil);
 cudaError_t split_update_step(const SplitUpdateCtx &ctx, int t0, int ts, int prow0, int pea,
                               int col0, int m, double *Y, int64_t ldy, const int *ea_panels,
                               __nv_bfloat16 *sb, unsigned long long *colmax, int *eb,
@@ -561,6 +572,12 @@ struct evec_ctx {
     // (they would otherwise wait behind it) and runs beside the solve;
     // q_ready marks its end, wait_q makes the back-transformation wait
     cudaStream_t copy_stream = nullptr;
+    // look-ahead schedule of the split solve (opt-in): the update of the
+    // rows below the next diagonal tile runs on la_stream beside that
+    // tile's solve
+    bool lookahead = false;
+    cudaStream_t la_stream = nullptr;
+    cudaEvent_t ev_slice = nullptr, ev_tail = nullptr;
     cudaEvent_t ev_prior = nullptr, q_ready = nullptr;
     const double *q_src = nullptr;
     size_t q_bytes = 0;
@@ -671,14 +688,19 @@ cudaEvent_t take_event(evec_handle h) {
 // Run one operation (launch() returns the number of kernels it launched),
 // bracketed by events when the handle is profiling.
 template <class F>
-void timed(evec_handle h, int kind, F &&launch) {
+void timed_on(evec_handle h, int kind, cudaStream_t st, F &&launch) {
     if (!h->profiling) { launch(); return; }
     cudaEvent_t a = take_event(h), b = take_event(h);
     if (!a || !b) { h->prof_n[kind] += launch(); return; }
-    cudaEventRecord(a, h->stream);
+    cudaEventRecord(a, st);
     const int nk = launch();
-    cudaEventRecord(b, h->stream);
+    cudaEventRecord(b, st);
     h->live.push_back({kind, a, b, nk});
+}
+
+template <class F>
+void timed(evec_handle h, int kind, F &&launch) {
+    timed_on(h, kind, h->stream, launch);
 }
 
 // Read T's three central diagonals and build the host plan.
@@ -901,6 +923,9 @@ evec_status evec_destroy(evec_handle h) {
     if (h->bexec) cudaGraphExecDestroy(h->bexec);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
+    if (h->la_stream) cudaStreamDestroy(h->la_stream);
+    if (h->ev_slice) cudaEventDestroy(h->ev_slice);
+    if (h->ev_tail) cudaEventDestroy(h->ev_tail);
     if (h->x_part) cudaEventDestroy(h->x_part);
     if (h->x_done) cudaEventDestroy(h->x_done);
     if (h->ev_prior) cudaEventDestroy(h->ev_prior);
@@ -910,6 +935,12 @@ evec_status evec_destroy(evec_handle h) {
         if (p) cudaFreeHost(p);
     cudaGetLastError();
     delete h;
+    return EVEC_OK;
+}
+
+evec_status evec_set_lookahead(evec_handle h, int enable) {
+    if (!h) return EVEC_EINVAL;
+    h->lookahead = enable != 0;
     return EVEC_OK;
 }
 
@@ -1008,30 +1039,96 @@ static evec_status sweep_steps(evec_handle h, const HostPlan &HP, const Plan &dp
                                int mode, const SplitUpdateCtx &sctx, cudaStream_t st) {
     const int N = (int)HP.tile_start.size() - 1;
     const int64_t m = HP.m;
+    // Look-ahead (split mode, panel-resident updates): the diagonal solve
+    // of step s leaves its decisions to k_decide; the update of step s is
+    // cut at the 128-row block holding tile s - 1.  The head (those blocks)
+    // runs on the caller's stream before the solve of tile s - 1, the tail
+    // (all rows below) on la_stream beside that solve, on the SMs the solve
+    // leaves free (both update parts take a whole SM per CTA).  The
+    // decisions of step s - 1 wait for the tail.
+    const bool ahead = mode == EVEC_SPLIT && sctx.Kp == 64 && h->lookahead && N > 2;
+    if (ahead) {
+        if (!h->la_stream)
+            EVEC_CUDA(cudaStreamCreateWithFlags(&h->la_stream, cudaStreamNonBlocking));
+        if (!h->ev_slice) EVEC_CUDA(cudaEventCreateWithFlags(&h->ev_slice, cudaEventDisableTiming));
+        if (!h->ev_tail) EVEC_CUDA(cudaEventCreateWithFlags(&h->ev_tail, cudaEventDisableTiming));
+    }
+    bool tail_pending = false;
     for (int s = N - 1; s >= 0; s--) {
         timed(h, EVEC_K_DIAG_SOLVE, [&] {
             return launch_diag_solve(s, T, ldt, dp, HP.tile_start.data(), HP.tile_real.data(),
                                      HP.tile_cplx.data(), h->tau, h->blk_tau, Y, ldy, h->seg_e,
-                                     h->seg_nu, h->seg_dx, h->seg_dy, st, nullptr, rhs);
+                                     h->seg_nu, h->seg_dx, h->seg_dy, st, nullptr, rhs, !ahead);
         });
+        if (ahead) {
+            if (tail_pending) {
+                EVEC_CUDA(cudaStreamWaitEvent(st, h->ev_tail, 0));
+                tail_pending = false;
+            }
+            timed(h, EVEC_K_DIAG_SOLVE, [&] {
+                launch_decide(s, dp, HP.tile_col[s], h->tau, h->seg_e, h->seg_nu, h->seg_dx,
+                              h->seg_dy, rhs, st);
+                return s > 0 && HP.tile_col[s] < m ? 1 : 0;
+            });
+        }
         if (s > 0 && HP.tile_col[s] < m) {
             if (mode == EVEC_SPLIT) {
                 cudaError_t ce = cudaSuccess;
+                const int t0 = HP.tile_start[s], ts = HP.tile_start[s + 1] - t0;
+                if (ahead) {
+                    const int nrb = (t0 + kTM - 1) / kTM;
+                    const int hb0 = HP.tile_start[s - 1] / kTM;
+                    int csms = 0;   // SMs of the next diagonal solve
+                    launch_diag_solve(s - 1, T, ldt, dp, HP.tile_start.data(),
+                                      HP.tile_real.data(), HP.tile_cplx.data(), h->tau,
+                                      h->blk_tau, Y, ldy, h->seg_e, h->seg_nu, h->seg_dx,
+                                      h->seg_dy, st, nullptr, rhs, false, &csms);
+                    csms = std::min(std::max(csms, 16), std::max(h->nsm - 16, 16));
+                    timed(h, EVEC_K_TILE_UPDATE, [&] {
+                        ce = split_slice_xs(sctx, t0, ts, HP.tile_col[s], (int)m, Y, ldy, h->slB,
+                                            h->eb, st, nullptr, 0);
+                        return 1;
+                    });
+                    EVEC_CUDA(ce);
+                    if (hb0 > 0) {
+                        EVEC_CUDA(cudaEventRecord(h->ev_slice, st));
+                        EVEC_CUDA(cudaStreamWaitEvent(h->la_stream, h->ev_slice, 0));
+                        timed_on(h, EVEC_K_TILE_UPDATE, h->la_stream, [&] {
+                            ce = split_update_rows(sctx, t0, ts, HP.prow0[s], HP.pea[s],
+                                                   HP.tile_col[s], (int)m, Y, ldy, h->ea_panels,
+                                                   h->eb, h->row_tile_d, h->seg_dx, h->seg_dy,
+                                                   h->seg_nu, &h->status_d->timeout, 0, hb0,
+                                                   h->nsm - csms, h->la_stream, false);
+                            return 1;
+                        });
+                        EVEC_CUDA(ce);
+                        EVEC_CUDA(cudaEventRecord(h->ev_tail, h->la_stream));
+                        tail_pending = true;
+                    }
+                    timed(h, EVEC_K_TILE_UPDATE, [&] {
+                        ce = split_update_rows(sctx, t0, ts, HP.prow0[s], HP.pea[s],
+                                               HP.tile_col[s], (int)m, Y, ldy, h->ea_panels,
+                                               h->eb, h->row_tile_d, h->seg_dx, h->seg_dy,
+                                               h->seg_nu, &h->status_d->timeout, hb0, nrb,
+                                               hb0 > 0 ? csms : h->nsm, st, false);
+                        return 1;
+                    });
+                    EVEC_CUDA(ce);
+                    continue;
+                }
                 timed(h, EVEC_K_TILE_UPDATE, [&] {
                     if (sctx.Kp == 64) {   // slicing + panel-resident product
                         ce = split_update_step_resident(
-                            sctx, HP.tile_start[s], HP.tile_start[s + 1] - HP.tile_start[s],
-                            HP.prow0[s], HP.pea[s], HP.tile_col[s], (int)m, Y, ldy,
+                            sctx, t0, ts, HP.prow0[s], HP.pea[s], HP.tile_col[s], (int)m, Y, ldy,
                             h->ea_panels, h->slB, h->eb, h->row_tile_d, h->seg_dx, h->seg_dy,
                             h->seg_nu, &h->status_d->timeout, h->nsm, st);
                         return 2;
                     }
                     // column maxima + slicing + streamed product
-                    ce = split_update_step(sctx, HP.tile_start[s],
-                                           HP.tile_start[s + 1] - HP.tile_start[s], HP.prow0[s],
-                                           HP.pea[s], HP.tile_col[s], (int)m, Y, ldy, h->ea_panels,
-                                           h->slB, h->cmax, h->eb, h->row_tile_d, h->seg_dx,
-                                           h->seg_dy, h->seg_nu, &h->status_d->timeout, st);
+                    ce = split_update_step(sctx, t0, ts, HP.prow0[s], HP.pea[s], HP.tile_col[s],
+                                           (int)m, Y, ldy, h->ea_panels, h->slB, h->cmax, h->eb,
+                                           h->row_tile_d, h->seg_dx, h->seg_dy, h->seg_nu,
+                                           &h->status_d->timeout, st);
                     return 3;
                 });
                 EVEC_CUDA(ce);
@@ -1044,6 +1141,7 @@ static evec_status sweep_steps(evec_handle h, const HostPlan &HP, const Plan &dp
             }
         }
     }
+    if (tail_pending) EVEC_CUDA(cudaStreamWaitEvent(st, h->ev_tail, 0));
     return EVEC_OK;
 }
 

@@ -42,7 +42,8 @@ int launch_diag_solve(int s, const double *T, int64_t ldt, const Plan &p,
                        const int32_t *tile_cplx_h,
                        const double *tau, const double *blk_tau, double *Y, int64_t ldy,
                        int32_t *seg_e, double *seg_nu, int32_t *seg_dx, int32_t *seg_dy,
-                       cudaStream_t st, const Pencil *pen = nullptr, bool rhs = false);
+                       cudaStream_t st, const Pencil *pen = nullptr, bool rhs = false,
+                       bool decide = true, int *sms = nullptr);
 void launch_tile_update(int s, const double *T, int64_t ldt, const Plan &p, int max_tile,
                         const int32_t *tile_col_h, double *Y, int64_t ldy,
                         const int32_t *seg_dx, const int32_t *seg_dy, double *seg_nu,

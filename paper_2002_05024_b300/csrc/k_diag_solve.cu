@@ -51,23 +51,77 @@ __global__ void __launch_bounds__(32 * W)
                  const double *__restrict__ tau, const double *__restrict__ blk_tau,
                  double *__restrict__ Y, int64_t ldy, int32_t *__restrict__ seg_e,
                  double *__restrict__ seg_nu, int32_t *__restrict__ seg_dx,
-                 int32_t *__restrict__ seg_dy, Pencil pen) {
+                 int32_t *__restrict__ seg_dy, Pencil pen, int decide) {
     extern __shared__ double smem[];
     if ((int)blockIdx.x < nreal_ctas)
         diag_tile<W, false, GEN, RHS, GR>(s, P.tile_real[s] + blockIdx.x * (Lanes<false, GR>::U * W),
                                           T, ldt, P, tau, blk_tau, Y, ldy, seg_e, seg_nu, seg_dx,
-                                          seg_dy, smem, pen);
+                                          seg_dy, smem, pen, decide != 0);
     else
         diag_tile<W, true, GEN, RHS, GR>(
             s, P.tile_cplx[s] + (blockIdx.x - nreal_ctas) * (Lanes<true, GR>::U * W), T, ldt, P,
-            tau, blk_tau, Y, ldy, seg_e, seg_nu, seg_dx, seg_dy, smem, pen);
+            tau, blk_tau, Y, ldy, seg_e, seg_nu, seg_dx, seg_dy, smem, pen, decide != 0);
+}
+
+// The decisions of step s for every active column and tile r < s (the
+// last part of diag_tile, as its own launch when the diagonal solve ran
+// with decide = 0): thread -> (column, tile row), consecutive threads on
+// consecutive columns; a pair is handled at its real column.  Reads the
+// segment exponent and maximum the solve left in seg_e / seg_nu of tile s.
+template <bool RHS>
+__global__ void __launch_bounds__(256)
+    k_decide(int s, Plan P, const double *__restrict__ tau, int32_t *__restrict__ seg_e,
+             double *__restrict__ seg_nu, int32_t *__restrict__ seg_dx,
+             int32_t *__restrict__ seg_dy, int64_t c0) {
+    const int64_t m = P.m, ncols = m - c0;
+    const int64_t items = ncols * s;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < items;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = c0 + idx % ncols;
+        const int r = (int)(idx / ncols);
+        const int u = P.col_unit[c];
+        const bool cplx = P.unit_lam[2 * u + 1] != 0.0;
+        if (cplx && c != P.unit_col[u]) continue;
+        const int64_t as = (int64_t)s * m + c, at = (int64_t)r * m + c;
+        const int es = seg_e[as];
+        const double mus = cplx ? fmax(seg_nu[as], seg_nu[as + 1]) : seg_nu[as];
+        const bool ownu = !RHS && P.unit_tile[u] == s;   // fresh segments above the own block
+        const int e_r = ownu ? es : seg_e[at];
+        const double nur = ownu ? 0.0 : (cplx ? fmax(seg_nu[at], seg_nu[at + 1]) : seg_nu[at]);
+        const int a = min(e_r, es);
+        const double nup = ownu ? 0.0 : scale2(nur, a - e_r);
+        const double mup = scale2(mus, a - es);
+        const int g2 = protect_update(nup, tau[(int64_t)r * P.ntiles + s], mup);
+        const int ne = a + g2;
+        seg_e[at] = ne;
+        seg_dx[at] = ne - es;
+        seg_dy[at] = ownu ? kFresh : ne - e_r;
+        seg_nu[at] = 0.0;   // the update of this step writes the new maximum
+        if (cplx) {
+            seg_e[at + 1] = ne;
+            seg_dx[at + 1] = ne - es;
+            seg_dy[at + 1] = ownu ? kFresh : ne - e_r;
+            seg_nu[at + 1] = 0.0;
+        }
+    }
+}
+
+void launch_decide(int s, const Plan &p, int64_t c0, const double *tau, int32_t *seg_e,
+                   double *seg_nu, int32_t *seg_dx, int32_t *seg_dy, bool rhs, cudaStream_t st) {
+    const int64_t items = (p.m - c0) * s;
+    if (items <= 0) return;
+    const unsigned grid = (unsigned)std::min<int64_t>((items + 255) / 256, 4096);
+    if (rhs)
+        k_decide<true><<<grid, 256, 0, st>>>(s, p, tau, seg_e, seg_nu, seg_dx, seg_dy, c0);
+    else
+        k_decide<false><<<grid, 256, 0, st>>>(s, p, tau, seg_e, seg_nu, seg_dx, seg_dy, c0);
 }
 
 template <int W, bool GEN, bool RHS, int GR = 8>
 static int launch_w(int s, int ts, int nr, int nc, const double *T, int64_t ldt, const Plan &p,
                     const double *tau, const double *blk_tau, double *Y, int64_t ldy,
                     int32_t *seg_e, double *seg_nu, int32_t *seg_dx, int32_t *seg_dy,
-                    const Pencil &pen, cudaStream_t st) {
+                    const Pencil &pen, cudaStream_t st, bool decide, int *sms) {
     constexpr int ur = Lanes<false, GR>::U * W, uc = Lanes<true, GR>::U * W;
     const int rct = (nr + ur - 1) / ur;
     const int cct = (nc + uc - 1) / uc;
@@ -80,8 +134,21 @@ static int launch_w(int s, int ts, int nr, int nc, const double *T, int64_t ldt,
     cudaFuncSetAttribute(k_diag_solve<W, GEN, RHS, GR>,
                          cudaFuncAttributePreferredSharedMemoryCarveout,
                          cudaSharedmemCarveoutMaxShared);
-    k_diag_solve<W, GEN, RHS, GR><<<rct + cct, 32 * W, diag_smem<W, GEN, GR>(ts), st>>>(
-        s, rct, T, ldt, p, tau, blk_tau, Y, ldy, seg_e, seg_nu, seg_dx, seg_dy, pen);
+    const size_t smem = diag_smem<W, GEN, GR>(ts);
+    if (sms) {   // SMs the launch occupies in one wave (planning only: no launch)
+        int per = 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_diag_solve<W, GEN, RHS, GR>,
+                                                          32 * W, smem) != cudaSuccess ||
+            per < 1) {
+            cudaGetLastError();
+            per = 1;
+        }
+        *sms = (rct + cct + per - 1) / per;
+        return 0;
+    }
+    k_diag_solve<W, GEN, RHS, GR><<<rct + cct, 32 * W, smem, st>>>(
+        s, rct, T, ldt, p, tau, blk_tau, Y, ldy, seg_e, seg_nu, seg_dx, seg_dy, pen,
+        decide ? 1 : 0);
     return 1;
 }
 
@@ -117,23 +184,26 @@ int launch_diag_solve(int s, const double *T, int64_t ldt, const Plan &p,
                       const int32_t *tile_start_h, const int32_t *tile_real_h,
                       const int32_t *tile_cplx_h, const double *tau, const double *blk_tau,
                       double *Y, int64_t ldy, int32_t *seg_e, double *seg_nu, int32_t *seg_dx,
-                      int32_t *seg_dy, cudaStream_t st, const Pencil *pen, bool rhs) {
+                      int32_t *seg_dy, cudaStream_t st, const Pencil *pen, bool rhs,
+                      bool decide, int *sms) {
     const int ts = tile_start_h[s + 1] - tile_start_h[s];
     const int nr = p.nreal - tile_real_h[s];
     const int nc = p.ncplx - tile_cplx_h[s];
     if (pen)
         return launch_w<4, true, false>(s, ts, nr, nc, T, ldt, p, tau, blk_tau, Y, ldy, seg_e,
-                                        seg_nu, seg_dx, seg_dy, *pen, st);
+                                        seg_nu, seg_dx, seg_dy, *pen, st, decide, sms);
     // four warps share a tile of up to 64 rows; two for larger tiles
     if (ts > 64)
         return rhs ? launch_w<2, false, true>(s, ts, nr, nc, T, ldt, p, tau, blk_tau, Y, ldy,
-                                              seg_e, seg_nu, seg_dx, seg_dy, Pencil(), st)
+                                              seg_e, seg_nu, seg_dx, seg_dy, Pencil(), st,
+                                              decide, sms)
                    : launch_w<2, false, false>(s, ts, nr, nc, T, ldt, p, tau, blk_tau, Y, ldy,
-                                               seg_e, seg_nu, seg_dx, seg_dy, Pencil(), st);
+                                               seg_e, seg_nu, seg_dx, seg_dy, Pencil(), st,
+                                               decide, sms);
     const int gr = pick_lanes(nr, nc);
 #define EVEC_DIAG_LAUNCH(R, G_)                                                                  \
     return launch_w<4, false, R, G_>(s, ts, nr, nc, T, ldt, p, tau, blk_tau, Y, ldy, seg_e,       \
-                                     seg_nu, seg_dx, seg_dy, Pencil(), st)
+                                     seg_nu, seg_dx, seg_dy, Pencil(), st, decide, sms)
     if (rhs) {
         if (gr == 32) EVEC_DIAG_LAUNCH(true, 32);
         if (gr == 16) EVEC_DIAG_LAUNCH(true, 16);

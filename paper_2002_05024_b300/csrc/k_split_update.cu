@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(kUThreads, 1)
                    const int *__restrict__ eb, double *__restrict__ Y, int64_t ldy,
                    const int32_t *__restrict__ row_tile, const int32_t *__restrict__ dx,
                    const int32_t *__restrict__ dy, unsigned long long *__restrict__ nu, int64_t m,
-                   int col0, int *err) {
+                   int col0, int *err, int by0) {
     extern __shared__ unsigned char smraw[];
     unsigned char *base = (unsigned char *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
     unsigned char *sA = base;
@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(kUThreads, 1)
              *acc_empty = bars + 7, *t_full = bars + 9, *t_empty = bars + 11;
     uint32_t *tmem_holder = (uint32_t *)(bars + 13);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int m0 = blockIdx.y * kTM;
+    const int m0 = ((int)blockIdx.y + by0) * kTM;   // row blocks by0, by0 + 1, ...
     const int ntN = (N + kUN - 1) / kUN;
     const int nmine = (int)blockIdx.x < ntN ? (ntN - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     const int khalves = K / kTK;
@@ -364,33 +364,58 @@ __global__ void __launch_bounds__(256)
     if (lane == 0) eb[j] = e;
 }
 
-// Step s of the split tile updates, panel-resident form (tiles <= 64 rows):
-// slice X_s = Y[t0 : t0 + ts, col0 : m], then update every row above tile s.
-// rhs (pencils, 2 |tile| <= 64): the right-hand side [beta X_s; -(alpha X_s)]
-// (ld ldr) replaces X_s.
-cudaError_t split_update_step_resident(const SplitUpdateCtx &ctx, int t0, int ts, int prow0,
-                                       int pea, int col0, int m, double *Y, int64_t ldy,
-                                       const int *ea_panels, __nv_bfloat16 *sb, int *eb,
-                                       const int32_t *row_tile, const int32_t *dx,
-                                       const int32_t *dy, double *seg_nu, int *err, int nsm,
-                                       cudaStream_t st, const double *rhs, int64_t ldr) {
+// Step s of the split tile updates, panel-resident form (tiles <= 64 rows),
+// in two parts: split_slice_xs slices X_s = Y[t0 : t0 + ts, col0 : m] (or
+// the pencil right-hand side), split_update_rows updates the 128-row
+// blocks [rb0, rb1) of the rows above tile s on at most `cap` CTAs (one
+// per SM).  rhs (pencils, 2 |tile| <= 64): the right-hand side
+// [beta X_s; -(alpha X_s)] (ld ldr) replaces X_s, and split_update_rows
+// then takes pencil = true (K = 2 |tile|).
+cudaError_t split_slice_xs(const SplitUpdateCtx &ctx, int t0, int ts, int col0, int m,
+                           const double *Y, int64_t ldy, __nv_bfloat16 *sb, int *eb,
+                           cudaStream_t st, const double *rhs, int64_t ldr) {
     const int N = m - col0;
     if (N <= 0 || t0 <= 0) return cudaSuccess;
     const int Nr = (N + kUN - 1) / kUN * kUN;
     const int K = rhs ? 2 * ts : ts;
     k_slice_xs<<<Nr / 8, 256, 0, st>>>(rhs ? rhs : Y + t0 + (int64_t)col0 * ldy, rhs ? ldr : ldy,
                                        K, N, Nr, ctx.S, sb, ctx.Npad, eb);
+    return cudaGetLastError();
+}
+
+cudaError_t split_update_rows(const SplitUpdateCtx &ctx, int t0, int ts, int prow0, int pea,
+                              int col0, int m, double *Y, int64_t ldy, const int *ea_panels,
+                              const int *eb, const int32_t *row_tile, const int32_t *dx,
+                              const int32_t *dy, double *seg_nu, int *err, int rb0, int rb1,
+                              int cap, cudaStream_t st, bool pencil) {
+    const int N = m - col0;
+    if (N <= 0 || t0 <= 0 || rb1 <= rb0) return cudaSuccess;
+    const int Nr = (N + kUN - 1) / kUN * kUN;
+    const int K = pencil ? 2 * ts : ts;   // the pencil right-hand side has 2 |tile| rows
     const int mpad = (t0 + kTM - 1) / kTM * kTM;
-    const int gy = mpad / kTM;
+    const int gy = rb1 - rb0;
     const int ntN = Nr / kUN;
-    const int gx = std::max(1, std::min(ntN, nsm / gy));
+    const int gx = std::max(1, std::min(ntN, cap / gy));
     const size_t smem = split_update_smem_bytes();
     cudaFuncSetAttribute(k_split_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_split_update<<<dim3(gx, gy), kUThreads, smem, st>>>(
         ctx.tmA, ctx.tmB32, ctx.S, t0, N, prow0, mpad, ctx.Npad, (K + kTK - 1) / kTK * kTK,
         ea_panels + pea, eb, Y, ldy, row_tile, dx, dy, (unsigned long long *)seg_nu, m, col0,
-        err);
+        err, rb0);
     return cudaGetLastError();
+}
+
+cudaError_t split_update_step_resident(const SplitUpdateCtx &ctx, int t0, int ts, int prow0,
+                                       int pea, int col0, int m, double *Y, int64_t ldy,
+                                       const int *ea_panels, __nv_bfloat16 *sb, int *eb,
+                                       const int32_t *row_tile, const int32_t *dx,
+                                       const int32_t *dy, double *seg_nu, int *err, int nsm,
+                                       cudaStream_t st, const double *rhs, int64_t ldr) {
+    cudaError_t e = split_slice_xs(ctx, t0, ts, col0, m, Y, ldy, sb, eb, st, rhs, ldr);
+    if (e != cudaSuccess) return e;
+    return split_update_rows(ctx, t0, ts, prow0, pea, col0, m, Y, ldy, ea_panels, eb, row_tile,
+                             dx, dy, seg_nu, err, 0, (t0 + kTM - 1) / kTM, nsm, st,
+                             rhs != nullptr);
 }
 
 }  // namespace evec

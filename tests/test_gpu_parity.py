@@ -380,3 +380,32 @@ def test_split_full_size_config2_sampled():
     Y = Q.T @ X[:, cols]
     res = standard_residuals(T, Y, lr[cols], li[cols])
     assert res.max() <= 10 * n, res.max()
+
+
+@pytest.mark.parametrize("kind", ["standard", "refine", "trsolve"])
+def test_lookahead_schedule_is_bit_identical(kind):
+    # the look-ahead schedule (decisions as their own launch, each step's
+    # update split at the next diagonal tile and run beside its solve)
+    # changes the order of launches, not the arithmetic of any element
+    n = 613
+    T, _ = workloads.config0_schur(n, seed=404)
+    dT = torch.from_numpy(np.asfortranarray(T)).cuda()
+    h = ev.handle(0)
+    outs = []
+    for la in (False, True):
+        h.lookahead(la)
+        try:
+            if kind == "trsolve":
+                B = np.random.default_rng(5).standard_normal((n, 300))
+                dB = torch.from_numpy(np.asfortranarray(B)).cuda()
+                X, e = ev.trsolve(dT, dB, tile=64, check=True, mode="split")
+            else:
+                X, e, _, _ = ev.standard(dT, tile=64, check=True, mode="split",
+                                         slices=5 if kind == "refine" else 0,
+                                         refine=kind == "refine")
+        finally:
+            h.lookahead(False)
+        torch.cuda.synchronize()
+        outs.append((X.cpu().numpy(), e.cpu().numpy()))
+    np.testing.assert_array_equal(outs[0][0], outs[1][0])
+    np.testing.assert_array_equal(outs[0][1], outs[1][1])
