@@ -125,6 +125,8 @@ KERNEL_SOURCES = {
     ("tile_update", "split"): ["k_split_update.cu", "k_split.cu", "split_common.cuh"],
     ("backtransform", "fp64"): ["k_gemm.cu"],
     ("backtransform", "split"): ["k_split.cu", "split_common.cuh"],
+    ("left", "split"): ["k_left.cu"],
+    ("left", "fp64"): ["k_left.cu"],
 }
 TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
 
@@ -175,7 +177,7 @@ def rooflines(prof, steps, mode, slices, F_diag, F_upd, F_bt, peaks, n, tile, F_
             "backtransform": (F_bt, mode == "split"), "refine": (F_res, False)}
     out = {}
     for k, (ms, nl) in prof.items():
-        if k not in work or ms <= 0 or nl <= 0:
+        if k not in work or ms <= 0 or nl <= 0 or work[k][0] <= 0:
             continue
         f64, tensor = work[k]
         sec = ms / steps / 1e3
@@ -495,7 +497,7 @@ def run_ours(args, rank, world, local_rank):
     slices = (args.slices or 8) if args.mode == "split" else 0
     tile = args.tile or 64
     roofs = rooflines(prof, args.steps, args.mode, slices, F_diag, F_upd, F_bt, peaks, n, tile,
-                      F_res=F_res, sweeps=2 if refine else 1)
+                      F_res=F_res, sweeps=2 if refine else 1, prefix="left:" if left else "")
     dominant = max(prof.items(), key=lambda kv: kv[1][0])[0]
     roofline = roofs.get(dominant)
     gpu_launches = sum(c for _, c in prof.values())
