@@ -76,6 +76,8 @@ class Oracle:
         lib.evo_generalized.restype = ctypes.c_int
         lib.evo_trsolve.argtypes = [i64, p, i64, i64, p, i64, p, i64, p, ctypes.c_int, p]
         lib.evo_trsolve.restype = ctypes.c_int
+        lib.evo_hessenberg.argtypes = [i64, p, i64, p, i64, p, p]
+        lib.evo_hessenberg.restype = ctypes.c_int
         lib.evo_naive_standard.argtypes = [i64, p, i64, p, p, i64]
         lib.evo_naive_standard.restype = i64
         self.lib = lib
@@ -153,6 +155,20 @@ class Oracle:
             raise OracleError(st, int(bad[0]))
         return X, e
 
+    def hessenberg(self, A, calc_q: bool = True):
+        """Hessenberg reduction A = Q H Q^T by one Householder reflector per
+        column (unblocked).  Returns (H, Q or None, tau)."""
+        H = np.array(_fortran(A), order="F", copy=True)
+        n = H.shape[0]
+        Q = np.zeros((n, n), order="F") if calc_q else None
+        tau = np.zeros(max(n, 1))
+        bad = np.full(1, -1, dtype=np.int64)
+        st = self.lib.evo_hessenberg(n, _ptr(H), max(n, 1), _ptr(Q), max(n, 1), _ptr(tau),
+                                     _ptr(bad))
+        if st:
+            raise OracleError(st, int(bad[0]))
+        return H, Q, tau[:n]
+
     def naive_standard(self, S, select=None):
         """Unscaled textbook substitution (overflow witness).  Returns
         (X, number of columns containing Inf or NaN)."""
@@ -217,3 +233,7 @@ def naive_standard(S, select=None):
 
 def trsolve(S, B, threads: int = 0):
     return default().trsolve(S, B, threads)
+
+
+def hessenberg(A, calc_q: bool = True):
+    return default().hessenberg(A, calc_q)

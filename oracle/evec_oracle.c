@@ -13,6 +13,9 @@
  *   - left eigenvectors of S, u_i^H S = lambda_i u_i^H, by robust forward
  *     substitution (the transposed problem of Sec. 2), back-transformed
  *     by the same Q
+ *   - the Hessenberg reduction A = Q H Q^T that precedes the Schur form
+ *     (Sec. 3.1), by one Householder reflector per column applied from
+ *     both sides, unblocked
  *   - the robust triangular solve with many right-hand sides that the
  *     eigenvector solve generalises (Sec. 3.4, the LAPACK xLATRS lineage):
  *     T x_j = b_j for every column of B, each x_j = X[:, j] / 2^scale_exp[j]
@@ -1058,3 +1061,98 @@ int64_t evo_naive_standard(int64_t n, const double *S, int64_t lds, const uint8_
     free(blk); free(yi);
     return nonfinite;
 }
+
+/* ------------------------------------------------------------------ */
+/* Hessenberg reduction                                                 */
+/* ------------------------------------------------------------------ */
+
+/* |x|_2 of a vector, scaled by its largest magnitude so that no square
+ * overflows or underflows to zero before the sum. */
+static double scaled_norm2(int64_t len, const double *x, int64_t inc)
+{
+    double mx = 0.0;
+    for (int64_t i = 0; i < len; i++)
+        if (fabs(x[i * inc]) > mx) mx = fabs(x[i * inc]);
+    if (mx == 0.0) return 0.0;
+    double ss = 0.0;
+    for (int64_t i = 0; i < len; i++) {
+        double t = x[i * inc] / mx;
+        ss += t * t;
+    }
+    return mx * sqrt(ss);
+}
+
+/*
+ * Hessenberg reduction (Sec. 3.1: A = Q H Q^T with H upper Hessenberg and Q
+ * orthogonal, the first phase of the eigenvalue pipeline), the unblocked
+ * definition: for j = 0 .. n - 3 one Householder reflector
+ * P_j = I - tau_j w_j w_j^T annihilates A[j+2:n, j]; A <- P_j A P_j, and
+ * Q <- Q P_j (Q starts as the identity).  With alpha = A[j+1, j] and
+ * x = A[j+2:n, j]: if x = 0 then tau_j = 0 (P_j = I); otherwise
+ *   beta = -sign(alpha) |(alpha, x)|_2  (sign(0) = +1),
+ *   tau_j = (beta - alpha) / beta,  w_j = (0 .. 0, 1, x / (alpha - beta)),
+ * the 1 at row j + 1, so that P_j (alpha, x) = (beta, 0).  On return A
+ * holds H (exact zeros below the first subdiagonal), Q (if not NULL, ld
+ * ldq) the orthogonal factor and tau (if not NULL, length n) tau_j (0 for
+ * j >= n - 2).  Entries must be finite and at most 2^1000 in magnitude
+ * (*bad = i + j n).
+ */
+int evo_hessenberg(int64_t n, double *A, int64_t lda, double *Q, int64_t ldq, double *tau,
+                   int64_t *bad)
+{
+    if (n < 0 || lda < (n > 0 ? n : 1) || (Q && ldq < (n > 0 ? n : 1))) return EVO_EINVAL;
+    for (int64_t j = 0; j < n; j++)
+        for (int64_t i = 0; i < n; i++) {
+            double v = AT(A, lda, i, j);
+            if (!isfinite(v)) { if (bad) *bad = i + j * n; return EVO_ENONFINITE; }
+            if (fabs(v) > INPUT_MAX) { if (bad) *bad = i + j * n; return EVO_EINVAL; }
+        }
+    if (Q)
+        for (int64_t j = 0; j < n; j++)
+            for (int64_t i = 0; i < n; i++) AT(Q, ldq, i, j) = i == j ? 1.0 : 0.0;
+    if (tau)
+        for (int64_t j = 0; j < n; j++) tau[j] = 0.0;
+    double *w = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
+    if (!w) return EVO_ENOMEM;
+    for (int64_t j = 0; j + 2 < n; j++) {
+        const double alpha = AT(A, lda, j + 1, j);
+        const double xn = scaled_norm2(n - j - 2, &AT(A, lda, j + 2, j), 1);
+        if (xn == 0.0) continue;                       /* P_j = I */
+        double beta = scaled_norm2(2, (double[]){alpha, xn}, 1);
+        if (alpha >= 0.0) beta = -beta;
+        const double t = (beta - alpha) / beta;
+        const double d = alpha - beta;
+        for (int64_t i = 0; i < n; i++) w[i] = 0.0;
+        w[j + 1] = 1.0;
+        for (int64_t i = j + 2; i < n; i++) w[i] = AT(A, lda, i, j) / d;
+        /* column j: (beta, 0, ..., 0) below the diagonal */
+        AT(A, lda, j + 1, j) = beta;
+        for (int64_t i = j + 2; i < n; i++) AT(A, lda, i, j) = 0.0;
+        /* A <- P A on columns j+1 .. n-1 (rows j+1 .. n-1) */
+        for (int64_t c = j + 1; c < n; c++) {
+            double s = 0.0;
+            for (int64_t i = j + 1; i < n; i++) s += w[i] * AT(A, lda, i, c);
+            s *= t;
+            for (int64_t i = j + 1; i < n; i++) AT(A, lda, i, c) -= s * w[i];
+        }
+        /* A <- A P on all rows (columns j+1 .. n-1) */
+        for (int64_t r = 0; r < n; r++) {
+            double s = 0.0;
+            for (int64_t c = j + 1; c < n; c++) s += AT(A, lda, r, c) * w[c];
+            s *= t;
+            for (int64_t c = j + 1; c < n; c++) AT(A, lda, r, c) -= s * w[c];
+        }
+        /* Q <- Q P */
+        if (Q)
+            for (int64_t r = 0; r < n; r++) {
+                double s = 0.0;
+                for (int64_t c = j + 1; c < n; c++) s += AT(Q, ldq, r, c) * w[c];
+                s *= t;
+                for (int64_t c = j + 1; c < n; c++) AT(Q, ldq, r, c) -= s * w[c];
+            }
+        if (tau) tau[j] = t;
+    }
+    free(w);
+    return EVO_OK;
+}
+

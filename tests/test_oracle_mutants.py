@@ -12,6 +12,7 @@ import os
 
 import numpy as np
 import pytest
+import scipy.linalg as sl
 
 import oracle
 import workloads
@@ -55,6 +56,11 @@ MUTANTS = [
     ("left_conjugation_dropped", "for (int64_t r = 0; r < n; r++) yi[r] = -yi[r];", "(void)0;"),
     ("left_update_unprotected", "int64_t s = protect_update(nu, P->tauL[cur], mu);",
      "int64_t s = 0;"),
+    ("hessenberg_beta_sign", "if (alpha >= 0.0) beta = -beta;", "if (alpha < 0.0) beta = -beta;"),
+    ("hessenberg_tau", "const double t = (beta - alpha) / beta;",
+     "const double t = (beta - alpha) / alpha;"),
+    ("hessenberg_left_columns", "for (int64_t c = j + 1; c < n; c++) {\n            double s = 0.0;\n            for (int64_t i = j + 1",
+     "for (int64_t c = j + 2; c < n; c++) {\n            double s = 0.0;\n            for (int64_t i = j + 1"),
 ]
 
 
@@ -165,6 +171,13 @@ def detector_failures(orc):
             col += sz
         return True
 
+    def hessenberg():
+        A = np.random.default_rng(3).standard_normal((40, 40))
+        H, Q, _ = orc.hessenberg(A)
+        Hs, Qs = sl.hessenberg(A, calc_q=True)
+        return (np.abs(H - Hs).max() <= 1e-11 and np.abs(Q @ H @ Q.T - A).max() <= 1e-11 and
+                np.all(np.tril(H, -2) == 0.0))
+
     check("golden", golden)
     check("residual_std", residual_std)
     check("residual_backtransformed", residual_backtransformed)
@@ -174,6 +187,7 @@ def detector_failures(orc):
     check("left_residual", left_residual)
     check("left_adversarial", left_adversarial)
     check("left_brute_force", left_brute_force)
+    check("hessenberg", hessenberg)
     return fails
 
 
