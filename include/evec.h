@@ -165,6 +165,26 @@ evec_status evec_standard_left(evec_handle h, int64_t n, const double *T, int64_
                                double *lam_re, double *lam_im, const evec_opts *opt);
 
 /*
+ * Hessenberg reduction A = Q H Q^T (Sec. 3.1, the first phase of the
+ * eigenvalue pipeline), blocked by panels of 32 columns: each panel is
+ * reduced column by column with Householder reflectors P_j = I - tau_j w_j
+ * w_j^T (beta = -sign(alpha) |(alpha, x)|_2, alpha = A[j+1, j], x =
+ * A[j+2:n, j], norms scaled by their largest entry; tau_j = 0 when x = 0),
+ * accumulated in the compact WY form I - V T V^T with Y = A V T, whose
+ * columns need the matrix-vector product of the trailing matrix with w_j;
+ * then the trailing matrix gets (I - V T V^T)^T (A - Y V^T) and the rows
+ * above the panel A - Y V^T.  All FP64 on the device.
+ *   A [lda x n] (device): overwritten with H, exact zeros below the first
+ *     subdiagonal.  Entries must be finite and at most 2^1000 (else
+ *     EVEC_ENONFINITE / EVEC_EINVAL at evec_sync, index i + j lda).
+ *   Q [ldq x n] (device) or NULL: receives the orthogonal factor.
+ *   opt: only check is read.
+ * The handle keeps a workspace of about 5 * 32 n + n doubles.
+ */
+evec_status evec_hessenberg(evec_handle h, int64_t n, double *A, int64_t lda, double *Q,
+                            int64_t ldq, const evec_opts *opt);
+
+/*
  * The same computation with HOST buffers (column-major, ld = n): copies
  * T (and Q) to the device, computes, copies X [n x m], scale_exp [m],
  * lam_re [m] and lam_im [m] back (each output may be NULL) and
@@ -211,7 +231,10 @@ enum {
                                 EVEC_K_DIAG_SOLVE / EVEC_K_TILE_UPDATE) */
     EVEC_K_LEFT = 9,         /* evec_standard_left: the flipped T' and Q J,
                                 and the final scatter into T's column order */
-    EVEC_K_COUNT = 10
+    EVEC_K_HESS_PANEL = 10,  /* evec_hessenberg: panel reductions, with the
+                                trailing matrix-vector products */
+    EVEC_K_HESS_UPDATE = 11, /* evec_hessenberg: trailing / top updates, Q */
+    EVEC_K_COUNT = 12
 };
 
 /* Look-ahead schedule of the split-mode solve (default off): the diagonal

@@ -30,7 +30,8 @@ EVEC_OK, EVEC_EINVAL, EVEC_ENOTSCHUR, EVEC_ENONFINITE = 0, 1, 2, 3
 EVEC_ENOMEM, EVEC_ECUDA, EVEC_ETIMEOUT, EVEC_ERESIDUAL = 4, 5, 6, 7
 EVEC_ECAPACITY = 8
 KERNELS = ("gather", "tile_norms", "diag_solve", "tile_update", "finalize",
-           "backtransform", "canonicalize", "batched", "refine", "left")
+           "backtransform", "canonicalize", "batched", "refine", "left", "hess_panel",
+           "hess_update")
 
 
 class EvecError(RuntimeError):
@@ -84,6 +85,7 @@ def lib() -> ctypes.CDLL:
                                       ctypes.POINTER(i32), p, ctypes.POINTER(i64)]
         L.evec_profile.argtypes = [p, ctypes.c_int]
         L.evec_set_lookahead.argtypes = [p, ctypes.c_int]
+        L.evec_hessenberg.argtypes = [p, i64, p, i64, p, i64, ctypes.POINTER(_Opts)]
         L.evec_profile_read.argtypes = [p, p, p, ctypes.c_int]
         L.evec_last_cuda_error.argtypes = []
         L.evec_last_cuda_error.restype = ctypes.c_char_p
@@ -103,7 +105,7 @@ def lib() -> ctypes.CDLL:
                   "evec_standard", "evec_standard_left", "evec_standard_host", "evec_sync",
                   "evec_plan_query", "evec_trsolve",
                   "evec_profile", "evec_profile_read", "evec_batched_count", "evec_batched",
-                  "evec_batched_generalized", "evec_set_lookahead",
+                  "evec_batched_generalized", "evec_set_lookahead", "evec_hessenberg",
                   "evec_generalized",
                   "evec_tune_get", "evec_tune_set"):
             getattr(L, f).restype = ctypes.c_int
@@ -390,6 +392,28 @@ def trsolve(T, B, tile: int = 0, check: bool = False, mode: str = "fp64", slices
     if check:
         h.sync()
     return X, e
+
+
+def hessenberg(A, calc_q: bool = True, check: bool = False, overwrite: bool = False):
+    """Hessenberg reduction A = Q H Q^T of a float64 CUDA matrix
+    (column-major).  Returns (H, Q or None); with overwrite, H is A itself."""
+    import torch
+    n = A.shape[0]
+    lda = _check_colmajor(A, "A", n)
+    H = A if overwrite else A.t().contiguous().t()
+    Q = torch.empty((n, n), dtype=torch.float64, device=A.device).t() if calc_q else None
+    if n == 0:
+        return H, Q
+    h = handle(A.device.index)
+    opts = _opts(0, False, "fp64", 0)
+    st = lib().evec_hessenberg(h.ptr, n, H.data_ptr(), H.stride(1) if n > 1 else lda,
+                               Q.data_ptr() if Q is not None else None,
+                               Q.stride(1) if (Q is not None and n > 1) else max(n, 1),
+                               ctypes.byref(opts))
+    _check(st, "evec_hessenberg")
+    if check:
+        h.sync()
+    return H, Q
 
 
 def standard_host(T, Q=None, select=None, tile: int = 0, device: int = 0,

@@ -53,6 +53,12 @@ void launch_left_output(const double *Xw, int64_t ldw, int64_t n, int64_t m, con
                         int reverse, const int32_t *ew, const double *lrw, const double *liw,
                         double *X, int64_t ldx, int32_t *e, double *lr, double *li,
                         cudaStream_t st);
+size_t hessenberg_workspace(int64_t n);
+int hess_panel_width();
+void hess_init_q(int64_t n, double *Q, int64_t ldq, cudaStream_t st);
+int hess_panel(int64_t n, double *A, int64_t lda, int64_t k, int b, double *ws, cudaStream_t st);
+int hess_update(int64_t n, double *A, int64_t lda, double *Q, int64_t ldq, int64_t k, int b,
+                double *ws, cudaStream_t st);
 void launch_check_rhs(const double *B, int64_t ldb, int64_t n, int64_t nrhs, int64_t base,
                       DevStatus *status, cudaStream_t st);
 void launch_refine_combine(const Plan &p, double *Y, int64_t ldy, const int32_t *ey,
@@ -547,6 +553,7 @@ struct evec_ctx {
     int32_t *lE = nullptr; size_t lE_cap = 0;
     double *lL = nullptr; size_t lL_cap = 0;
     int32_t *lmap_d = nullptr; size_t lmap_cap = 0;
+    double *hs_ws = nullptr; size_t hs_ws_cap = 0;   // Hessenberg reduction
     std::vector<int32_t> lmap_h;
     std::vector<uint8_t> lsel;
     // pinned host buffers
@@ -915,7 +922,7 @@ evec_status evec_destroy(evec_handle h) {
                    h->slA, h->slB, h->rmax, h->cmax, h->ea, h->eb, h->panels,
                    h->ea_panels, h->boff_d, h->bws, h->bplan_d, h->queue_d, h->tauT,
                    h->blk_tauT, h->pW, h->Rd, h->seg_ey, h->lT, h->lQ, h->lX, h->lE, h->lL,
-                   h->lmap_d};
+                   h->lmap_d, h->hs_ws};
     for (void *p : dev)
         if (p) cudaFree(p);
     for (auto &t : h->live) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
@@ -2085,6 +2092,41 @@ extern "C" evec_status evec_batched_generalized(
     EVEC_TRY(run_batch(h, count, n_host, S_packed, s_off_host, all, plans, X_packed,
                        scale_exp_packed, alpha_re_packed, alpha_im_packed, false, 0, T_packed,
                        t_off_host, beta_packed, max_tile));
+    if (opt && opt->check) return evec_sync(h, nullptr);
+    return EVEC_OK;
+}
+
+// Hessenberg reduction A = Q H Q^T (Sec. 3.1), panels of hess_panel_width()
+// columns: the panel reduction (with its trailing matrix-vector products)
+// and the trailing / top updates, timed as two kernel classes.
+extern "C" evec_status evec_hessenberg(evec_handle h, int64_t n, double *A, int64_t lda,
+                                       double *Q, int64_t ldq, const evec_opts *opt) {
+    if (!h || n < 0 || !ld_ok(lda, n) || (Q && !ld_ok(ldq, n)) || n > INT32_MAX)
+        return EVEC_EINVAL;
+    if (n == 0) return EVEC_OK;
+    if (!A) return EVEC_EINVAL;
+    DeviceGuard g(h->device);
+    if (!g.ok) return EVEC_ECUDA;
+    cudaStream_t st = h->stream;
+    EVEC_TRY(grow_device(&h->hs_ws, &h->hs_ws_cap, hessenberg_workspace(n)));
+    timed(h, EVEC_K_NORMS, [&] {
+        launch_check_rhs(A, lda, n, n, 0, h->status_d, st);
+        return 1;
+    });
+    if (Q) {
+        timed(h, EVEC_K_HESS_UPDATE, [&] {
+            hess_init_q(n, Q, ldq, st);
+            return 1;
+        });
+    }
+    const int nbw = hess_panel_width();
+    for (int64_t k = 0; k + 2 < n; k += nbw) {
+        const int b = (int)std::min<int64_t>(nbw, n - 2 - k);
+        timed(h, EVEC_K_HESS_PANEL, [&] { return hess_panel(n, A, lda, k, b, h->hs_ws, st); });
+        timed(h, EVEC_K_HESS_UPDATE,
+              [&] { return hess_update(n, A, lda, Q, ldq, k, b, h->hs_ws, st); });
+    }
+    EVEC_CUDA(cudaGetLastError());
     if (opt && opt->check) return evec_sync(h, nullptr);
     return EVEC_OK;
 }

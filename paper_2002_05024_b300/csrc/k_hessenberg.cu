@@ -1,0 +1,432 @@
+// k_hessenberg.cu -- Hessenberg reduction A = Q H Q^T (Sec. 3.1), blocked by
+// panels of kHb columns as the paper describes:
+//   1. reduce the panel: column c = k + i of the panel gets the earlier
+//      reflectors of the panel from the right (x = A[:, c] - Y V^T e_c) and
+//      the left (x <- (I - V T V^T)^T x), then its reflector P_c = I - tau v
+//      v^T (beta = -sign(alpha) |(alpha, x)|_2, v = (1, x / (alpha - beta))
+//      below row c), and Y = A V T gains the column
+//      y = tau (A[:, c+1:n] v - Y (V^T v))  -- the large matrix-vector
+//      product over the part of the matrix that trails the column, the
+//      HBM-bound step (8 n (n - c - 1) bytes per column);
+//   2. update the trailing matrix: A <- (I - V T V^T)^T (A - Y V^T);
+//   3. update the top part from the right: A <- A - Y V^T (rows above the
+//      panel, which the left factor does not touch).
+// Q (optional) accumulates Q <- Q (I - V T V^T).  All FP64.  Reductions
+// across CTAs go through per-CTA partial sums and a second pass (no FP64
+// atomics), so the result does not depend on scheduling.
+#include <algorithm>
+
+#include "evec_internal.cuh"
+
+namespace evec {
+
+constexpr int kHb = 32;          // panel width
+constexpr int kHRowThreads = 256;
+constexpr int kHPartStride = 2 * kHb + 4;
+
+struct HessScal {
+    double tau, d, beta;
+};
+
+__device__ __forceinline__ double hwarp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// merge two (scale, sum of squares) pairs: sum_i x_i^2 = s^2 q
+__device__ __forceinline__ void ssq_merge(double &s, double &q, double s2, double q2) {
+    if (s2 == 0.0) return;
+    if (s < s2) {
+        const double r = s / s2;
+        q = q2 + q * r * r;
+        s = s2;
+    } else {
+        const double r = s2 / s;
+        q += q2 * r * r;
+    }
+}
+
+// Block-wide sums of nv values per thread (nv <= kHb), written to
+// part[blockIdx.x * kHPartStride + off + j].  smem: 8 x kHb doubles.
+__device__ void block_sums(double *vals, int nv, double *red, double *part, int off) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int j = 0; j < nv; j++) {
+        const double v = hwarp_sum(vals[j]);
+        if (lane == 0) red[warp * kHb + j] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < nv) {
+        double s = 0.0;
+        for (int w = 0; w < kHRowThreads / 32; w++) s += red[w * kHb + threadIdx.x];
+        part[(int64_t)blockIdx.x * kHPartStride + off + threadIdx.x] = s;
+    }
+    __syncthreads();
+}
+
+// 1. x = A[:, c] - Y[:, 0:i] V[c, 0:i]^T for every row; partial sums of
+//    V[:, 0:i]^T x.
+__global__ void __launch_bounds__(kHRowThreads)
+    k_hs_col(int64_t n, const double *__restrict__ A, int64_t lda, int64_t c, int i,
+             const double *__restrict__ Y, const double *__restrict__ V, double *__restrict__ x,
+             double *__restrict__ part) {
+    __shared__ double vc[kHb];
+    __shared__ double red[8 * kHb];
+    if (threadIdx.x < i) vc[threadIdx.x] = V[c + (int64_t)threadIdx.x * n];
+    __syncthreads();
+    double acc[kHb];
+#pragma unroll
+    for (int j = 0; j < kHb; j++) acc[j] = 0.0;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        double xr = A[r + c * lda];
+#pragma unroll
+        for (int j = 0; j < kHb; j++)
+            if (j < i) xr = fma(-Y[r + (int64_t)j * n], vc[j], xr);
+        x[r] = xr;
+#pragma unroll
+        for (int j = 0; j < kHb; j++)
+            if (j < i) acc[j] = fma(V[r + (int64_t)j * n], xr, acc[j]);
+    }
+    block_sums(acc, i, red, part, 0);
+}
+
+// 2. w = T[0:i, 0:i]^T (sum of the partials), one CTA.
+__global__ void k_hs_w(int i, int nparts, const double *__restrict__ part,
+                       const double *__restrict__ T, double *__restrict__ w) {
+    __shared__ double u[kHb];
+    const int j = threadIdx.x;
+    if (j < i) {
+        double s = 0.0;
+        for (int p = 0; p < nparts; p++) s += part[(int64_t)p * kHPartStride + j];
+        u[j] = s;
+    }
+    __syncthreads();
+    if (j < i) {   // (T^T u)_j = sum_{l <= j} T[l, j] u_l
+        double s = 0.0;
+        for (int l = 0; l <= j; l++) s = fma(T[l + j * kHb], u[l], s);
+        w[j] = s;
+    }
+}
+
+// 3. x <- x - V[:, 0:i] w; column c of A for rows <= c; partials of the
+//    norm of x[c+2:n] (scale, sum of squares) and of V[c+2:n, 0:i]^T x.
+__global__ void __launch_bounds__(kHRowThreads)
+    k_hs_apply(int64_t n, double *__restrict__ A, int64_t lda, int64_t c, int i,
+               const double *__restrict__ V, const double *__restrict__ w,
+               double *__restrict__ x, double *__restrict__ part) {
+    __shared__ double ws[kHb];
+    __shared__ double red[8 * kHb];
+    __shared__ double rs[8], rq[8];
+    if (threadIdx.x < i) ws[threadIdx.x] = w[threadIdx.x];
+    __syncthreads();
+    double acc[kHb];
+#pragma unroll
+    for (int j = 0; j < kHb; j++) acc[j] = 0.0;
+    double sc = 0.0, sq = 0.0;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        double xr = x[r];
+#pragma unroll
+        for (int j = 0; j < kHb; j++)
+            if (j < i) xr = fma(-V[r + (int64_t)j * n], ws[j], xr);
+        x[r] = xr;
+        if (r <= c) A[r + c * lda] = xr;
+        if (r >= c + 2) {
+            ssq_merge(sc, sq, fabs(xr), xr != 0.0 ? 1.0 : 0.0);
+#pragma unroll
+            for (int j = 0; j < kHb; j++)
+                if (j < i) acc[j] = fma(V[r + (int64_t)j * n], xr, acc[j]);
+        }
+    }
+    block_sums(acc, i, red, part, 0);
+    // (scale, ssq) over the block
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double s2 = __shfl_xor_sync(0xffffffffu, sc, o);
+        const double q2 = __shfl_xor_sync(0xffffffffu, sq, o);
+        ssq_merge(sc, sq, s2, q2);
+    }
+    if (lane == 0) { rs[warp] = sc; rq[warp] = sq; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0, q = 0.0;
+        for (int k = 0; k < kHRowThreads / 32; k++) ssq_merge(s, q, rs[k], rq[k]);
+        part[(int64_t)blockIdx.x * kHPartStride + kHb] = s;
+        part[(int64_t)blockIdx.x * kHPartStride + kHb + 1] = q;
+    }
+}
+
+// 4. The reflector of column c (one CTA): beta, tau, d = alpha - beta,
+//    s = V[:, 0:i]^T v, the new column of T, A[c+1, c] = beta.
+__global__ void k_hs_reflector(int64_t n, double *__restrict__ A, int64_t lda, int64_t c, int i,
+                               int nparts, const double *__restrict__ part,
+                               const double *__restrict__ x, const double *__restrict__ V,
+                               double *__restrict__ T, double *__restrict__ svec,
+                               HessScal *scal) {
+    __shared__ double sh[kHb];
+    __shared__ double s_tau, s_d;
+    const int j = threadIdx.x;
+    if (j == 0) {
+        double s = 0.0, q = 0.0;
+        for (int p = 0; p < nparts; p++)
+            ssq_merge(s, q, part[(int64_t)p * kHPartStride + kHb],
+                      part[(int64_t)p * kHPartStride + kHb + 1]);
+        const double xn = s * sqrt(q);
+        const double alpha = x[c + 1];
+        double tau = 0.0, d = 1.0, beta = alpha;
+        if (xn != 0.0) {
+            const double m = fmax(fabs(alpha), xn);
+            const double a = alpha / m, b = xn / m;
+            beta = m * sqrt(a * a + b * b);
+            if (alpha >= 0.0) beta = -beta;
+            tau = (beta - alpha) / beta;
+            d = alpha - beta;
+        }
+        s_tau = tau;
+        s_d = d;
+        scal->tau = tau;
+        scal->d = d;
+        scal->beta = beta;
+        A[(c + 1) + c * lda] = beta;
+    }
+    __syncthreads();
+    const double tau = s_tau, d = s_d;
+    if (j < i) {   // s_j = V[c+1, j] + (V[c+2:n, j]^T x[c+2:n]) / d
+        double q = 0.0;
+        for (int p = 0; p < nparts; p++) q += part[(int64_t)p * kHPartStride + j];
+        sh[j] = tau == 0.0 ? 0.0 : V[(c + 1) + (int64_t)j * n] + q / d;
+        svec[j] = sh[j];
+    }
+    __syncthreads();
+    if (j < i) {   // T[j, i] = -tau sum_{l >= j, l < i} T[j, l] s_l
+        double t = 0.0;
+        for (int l = j; l < i; l++) t = fma(T[j + l * kHb], sh[l], t);
+        T[j + i * kHb] = -tau * t;
+    }
+    if (j == 0) T[i + i * kHb] = tau;
+}
+
+// 5. v (column i of V): 0 above row c + 1, 1 at c + 1, x / d below; zeros
+//    below the subdiagonal of column c of A.
+__global__ void __launch_bounds__(kHRowThreads)
+    k_hs_v(int64_t n, double *__restrict__ A, int64_t lda, int64_t c, int i,
+           const double *__restrict__ x, double *__restrict__ V, const HessScal *scal) {
+    const double tau = scal->tau, d = scal->d;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        double v = 0.0;
+        if (r == c + 1) v = 1.0;
+        else if (r > c + 1 && tau != 0.0) v = x[r] / d;
+        V[r + (int64_t)i * n] = v;
+        if (r > c + 1) A[r + c * lda] = 0.0;
+    }
+}
+
+// 6. Y[:, i] = tau (A[:, c+1:n] v - Y[:, 0:i] s): 32 rows per CTA (lane =
+//    row), its 16 warps split the columns; every warp load is 256
+//    contiguous bytes of one column.
+constexpr int kGvWarps = 16;
+__global__ void __launch_bounds__(32 * kGvWarps)
+    k_hs_gemv(int64_t n, const double *__restrict__ A, int64_t lda, int64_t c, int i,
+              const double *__restrict__ V, const double *__restrict__ svec,
+              double *__restrict__ Y, const HessScal *scal) {
+    __shared__ double red[kGvWarps][33];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t r = (int64_t)blockIdx.x * 32 + lane;
+    const bool rv = r < n;
+    const double *v = V + (int64_t)i * n;
+    double acc = 0.0, acc2 = 0.0;
+    int64_t j = c + 1 + warp;
+    for (; j + kGvWarps < n; j += 2 * kGvWarps) {
+        const double a0 = rv ? A[r + j * lda] : 0.0;
+        const double a1 = rv ? A[r + (j + kGvWarps) * lda] : 0.0;
+        acc = fma(a0, v[j], acc);
+        acc2 = fma(a1, v[j + kGvWarps], acc2);
+    }
+    if (j < n && rv) acc = fma(A[r + j * lda], v[j], acc);
+    red[warp][lane] = acc + acc2;
+    __syncthreads();
+    if (warp == 0 && rv) {
+        double y = 0.0;
+        for (int w = 0; w < kGvWarps; w++) y += red[w][lane];
+        for (int l = 0; l < i; l++) y = fma(-Y[r + (int64_t)l * n], svec[l], y);
+        Y[r + (int64_t)i * n] = scal->tau * y;
+    }
+}
+
+// C = alpha op(A) op(B) + beta C (beta 0: C is not read); op(A) M x K,
+// op(B) K x N; 64 x 64 tiles, 16-deep K steps, 4 x 4 outputs per thread.
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(256)
+    k_hs_gemm(int M, int N, int K, double alpha, const double *__restrict__ A, int64_t lda,
+              const double *__restrict__ B, int64_t ldb, double beta, double *__restrict__ C,
+              int64_t ldc) {
+    __shared__ double As[16][64 + 1];
+    __shared__ double Bs[16][64 + 1];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int m0 = blockIdx.x * 64, n0 = blockIdx.y * 64;
+    double acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; a++)
+#pragma unroll
+        for (int b = 0; b < 4; b++) acc[a][b] = 0.0;
+    for (int k0 = 0; k0 < K; k0 += 16) {
+        for (int e = tid; e < 16 * 64; e += 256) {
+            int kk, mm;
+            if (TA) { mm = e / 16; kk = e % 16; }   // A[k + m lda]: k contiguous
+            else { kk = e / 64; mm = e % 64; }       // A[m + k lda]: m contiguous
+            const int gm = m0 + mm, gk = k0 + kk;
+            double v = 0.0;
+            if (gm < M && gk < K) v = TA ? A[gk + (int64_t)gm * lda] : A[gm + (int64_t)gk * lda];
+            As[kk][mm] = v;
+        }
+        for (int e = tid; e < 16 * 64; e += 256) {
+            int kk, nn;
+            if (TB) { kk = e / 64; nn = e % 64; }    // B[n + k ldb]: n contiguous
+            else { nn = e / 16; kk = e % 16; }       // B[k + n ldb]: k contiguous
+            const int gn = n0 + nn, gk = k0 + kk;
+            double v = 0.0;
+            if (gn < N && gk < K) v = TB ? B[gn + (int64_t)gk * ldb] : B[gk + (int64_t)gn * ldb];
+            Bs[kk][nn] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; kk++) {
+            double a[4], b[4];
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                a[q] = As[kk][ty + 16 * q];
+                b[q] = Bs[kk][tx + 16 * q];
+            }
+#pragma unroll
+            for (int p = 0; p < 4; p++)
+#pragma unroll
+                for (int q = 0; q < 4; q++) acc[p][q] = fma(a[p], b[q], acc[p][q]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int p = 0; p < 4; p++) {
+        const int gm = m0 + ty + 16 * p;
+        if (gm >= M) continue;
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const int gn = n0 + tx + 16 * q;
+            if (gn >= N) continue;
+            double *cp = C + gm + (int64_t)gn * ldc;
+            *cp = beta == 0.0 ? alpha * acc[p][q] : fma(alpha, acc[p][q], beta * *cp);
+        }
+    }
+}
+
+static void gemm(bool ta, bool tb, int M, int N, int K, double alpha, const double *A,
+                 int64_t lda, const double *B, int64_t ldb, double beta, double *C, int64_t ldc,
+                 cudaStream_t st) {
+    if (M <= 0 || N <= 0) return;
+    dim3 grid((unsigned)((M + 63) / 64), (unsigned)((N + 63) / 64));
+    if (ta && tb) k_hs_gemm<true, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    else if (ta) k_hs_gemm<true, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    else if (tb) k_hs_gemm<false, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    else k_hs_gemm<false, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+}
+
+__global__ void k_hs_eye(int64_t n, double *Q, int64_t ldq) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) Q[i + i * ldq] = 1.0;
+}
+
+int hess_panel_width() { return kHb; }
+
+static int hess_parts(int64_t n) {
+    return (int)std::max<int64_t>(
+        std::min<int64_t>((n + kHRowThreads - 1) / kHRowThreads, 128), 1);
+}
+
+// workspace doubles for order n: V, Y, VT, W (n x kHb each), Z (kHb x n), T
+// (kHb x kHb), x (n), w and s (kHb each), the per-CTA partials, scalars
+size_t hessenberg_workspace(int64_t n) {
+    return (size_t)(5 * n * kHb + kHb * kHb + n + 2 * kHb +
+                    (int64_t)hess_parts(n) * kHPartStride + 8);
+}
+
+struct HessWs {
+    double *V, *Y, *VT, *W, *Z, *T, *x, *wv, *sv, *part;
+    HessScal *scal;
+};
+
+static HessWs hess_ws(int64_t n, double *ws) {
+    HessWs w;
+    w.V = ws;
+    w.Y = w.V + n * kHb;
+    w.VT = w.Y + n * kHb;
+    w.W = w.VT + n * kHb;
+    w.Z = w.W + n * kHb;
+    w.T = w.Z + kHb * n;
+    w.x = w.T + kHb * kHb;
+    w.wv = w.x + n;
+    w.sv = w.wv + kHb;
+    w.part = w.sv + kHb;
+    w.scal = (HessScal *)(w.part + (int64_t)hess_parts(n) * kHPartStride);
+    return w;
+}
+
+// Q = I
+void hess_init_q(int64_t n, double *Q, int64_t ldq, cudaStream_t st) {
+    cudaMemset2DAsync(Q, ldq * sizeof(double), 0, n * sizeof(double), n, st);
+    k_hs_eye<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, Q, ldq);
+}
+
+// Step 1 for the panel of b columns at k: returns the kernels launched.
+int hess_panel(int64_t n, double *A, int64_t lda, int64_t k, int b, double *ws,
+               cudaStream_t st) {
+    const HessWs w = hess_ws(n, ws);
+    const int parts = hess_parts(n);
+    cudaMemsetAsync(w.T, 0, sizeof(double) * kHb * kHb, st);
+    for (int i = 0; i < b; i++) {
+        const int64_t c = k + i;
+        k_hs_col<<<parts, kHRowThreads, 0, st>>>(n, A, lda, c, i, w.Y, w.V, w.x, w.part);
+        k_hs_w<<<1, 32, 0, st>>>(i, parts, w.part, w.T, w.wv);
+        k_hs_apply<<<parts, kHRowThreads, 0, st>>>(n, A, lda, c, i, w.V, w.wv, w.x, w.part);
+        k_hs_reflector<<<1, 32, 0, st>>>(n, A, lda, c, i, parts, w.part, w.x, w.V, w.T, w.sv,
+                                         w.scal);
+        k_hs_v<<<parts, kHRowThreads, 0, st>>>(n, A, lda, c, i, w.x, w.V, w.scal);
+        k_hs_gemv<<<(unsigned)((n + 31) / 32), 32 * kGvWarps, 0, st>>>(n, A, lda, c, i, w.V,
+                                                                     w.sv, w.Y, w.scal);
+    }
+    return 6 * b;
+}
+
+// Steps 2 and 3 for the panel at k (b columns), and Q <- Q (I - V T V^T):
+// returns the kernels launched.
+int hess_update(int64_t n, double *A, int64_t lda, double *Q, int64_t ldq, int64_t k, int b,
+                double *ws, cudaStream_t st) {
+    const HessWs w = hess_ws(n, ws);
+    int ng = 0;
+    const int64_t j0 = k + b;            // first trailing column
+    const int nt = (int)(n - j0);
+    const int rows = (int)(n - k - 1);   // rows k+1 .. n-1 (V is zero above)
+    if (nt > 0) {
+        // A[:, j0:n] -= Y V[j0:n, :]^T (every row: the top part and the rest)
+        gemm(false, true, (int)n, nt, b, -1.0, w.Y, n, w.V + j0, n, 1.0, A + j0 * lda, lda, st);
+        // rows k+1 ..: A <- A - (V T^T) (V^T A)
+        gemm(true, false, b, nt, rows, 1.0, w.V + (k + 1), n, A + (k + 1) + j0 * lda, lda, 0.0,
+             w.Z, kHb, st);
+        gemm(false, true, rows, b, b, 1.0, w.V + (k + 1), n, w.T, kHb, 0.0, w.VT, n, st);
+        gemm(false, false, rows, nt, b, -1.0, w.VT, n, w.Z, kHb, 1.0, A + (k + 1) + j0 * lda, lda,
+             st);
+        ng += 4;
+    }
+    if (Q) {   // Q[:, k+1:n] -= (Q[:, k+1:n] V[k+1:n, :]) T V[k+1:n, :]^T
+        gemm(false, false, (int)n, b, rows, 1.0, Q + (k + 1) * ldq, ldq, w.V + (k + 1), n, 0.0,
+             w.W, n, st);
+        gemm(false, false, (int)n, b, b, 1.0, w.W, n, w.T, kHb, 0.0, w.VT, n, st);
+        gemm(false, true, (int)n, rows, b, -1.0, w.VT, n, w.V + (k + 1), n, 1.0,
+             Q + (k + 1) * ldq, ldq, st);
+        ng += 3;
+    }
+    return ng;
+}
+
+}  // namespace evec

@@ -1,0 +1,94 @@
+"""Hessenberg reduction on the GPU (evec_hessenberg: panels of 32 columns,
+compact WY updates) against the oracle's unblocked reduction: H and Q
+element by element within a rounding bound (16 n sqrt(n) u, relative to
+max |A| for H), exact zeros below the subdiagonal, orthogonality and the
+backward error of Q H Q^T; a leading dimension above n, the symmetric case,
+errors, and the benchmark's size n = 4096 through its invariants."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2002_05024_b300 as ev
+
+pytestmark = pytest.mark.gpu
+
+U = 2.0 ** -53
+
+
+def _gpu(A, calc_q=True):
+    dA = torch.from_numpy(np.asfortranarray(A)).cuda()
+    H, Q = ev.hessenberg(dA, calc_q=calc_q, check=True)
+    torch.cuda.synchronize()
+    return H.cpu().numpy(), (Q.cpu().numpy() if Q is not None else None)
+
+
+def _bound(n):
+    return 16 * n * np.sqrt(n) * U
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 33, 100, 257, 600])
+def test_hessenberg_against_oracle(n):
+    A = np.random.default_rng(n).standard_normal((n, n))
+    H, Q = _gpu(A)
+    Ho, Qo, _ = oracle.hessenberg(A)
+    nrm = np.abs(A).max()
+    assert np.all(np.tril(H, -2) == 0.0)
+    assert np.abs(H - Ho).max() <= _bound(n) * nrm, np.abs(H - Ho).max()
+    assert np.abs(Q - Qo).max() <= _bound(n), np.abs(Q - Qo).max()
+    assert np.abs(Q.T @ Q - np.eye(n)).max() <= 8 * n * U
+    assert np.abs(Q @ H @ Q.T - A).max() <= _bound(n) * nrm
+
+
+def test_hessenberg_leading_dimension_and_no_q():
+    n, ld = 150, 173
+    A = np.random.default_rng(5).standard_normal((n, n))
+    buf = torch.zeros((n, ld), dtype=torch.float64, device="cuda")
+    dA = buf.t()[:n, :]                      # column-major, leading dimension ld
+    dA.copy_(torch.from_numpy(A))
+    assert dA.stride() == (1, ld)
+    H, Q = ev.hessenberg(dA, calc_q=False, check=True, overwrite=True)
+    assert Q is None and H.data_ptr() == dA.data_ptr()
+    Ho, _, _ = oracle.hessenberg(A)
+    assert np.abs(H.cpu().numpy() - Ho).max() <= _bound(n) * np.abs(A).max()
+    # the rows between n and ld are not touched
+    assert torch.all(buf.t()[n:, :] == 0.0)
+
+
+def test_hessenberg_symmetric_gives_tridiagonal():
+    n = 300
+    B = np.random.default_rng(9).standard_normal((n, n))
+    A = B + B.T
+    H, Q = _gpu(A)
+    nrm = np.abs(A).max()
+    assert np.abs(np.triu(H, 2)).max() <= _bound(n) * nrm
+    assert np.abs(H - H.T).max() <= _bound(n) * nrm
+
+
+def test_hessenberg_errors():
+    n = 50
+    A = np.random.default_rng(1).standard_normal((n, n))
+    bad = A.copy()
+    bad[4, 7] = np.nan
+    with pytest.raises(ev.EvecError) as ei:
+        _gpu(bad)
+    assert ei.value.status == ev.EVEC_ENONFINITE and ei.value.bad == 4 + 7 * n
+    bad = A.copy()
+    bad[2, 3] = 2.0 ** 1001
+    with pytest.raises(ev.EvecError) as ei:
+        _gpu(bad)
+    assert ei.value.status == ev.EVEC_EINVAL and ei.value.bad == 2 + 3 * n
+    H, Q = _gpu(A)   # the handle stays usable
+    assert np.abs(Q @ H @ Q.T - A).max() <= _bound(n) * np.abs(A).max()
+
+
+def test_hessenberg_full_size_invariants():
+    # n = 4096 (the benchmark's size): zero pattern, orthogonality and the
+    # backward error, checked with the host BLAS
+    n = 4096
+    A = np.random.default_rng(2020).standard_normal((n, n))
+    H, Q = _gpu(A)
+    assert np.all(np.tril(H, -2) == 0.0)
+    assert np.abs(Q.T @ Q - np.eye(n)).max() <= 8 * n * U
+    R = Q @ H @ Q.T - A
+    assert np.abs(R).max() <= _bound(n) * np.abs(A).max(), np.abs(R).max()
