@@ -64,7 +64,7 @@ def parse_args():
                     help="columns of the CPU-oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=["single", "batched", "generalized", "trsolve",
-                                           "batched_generalized"],
+                                           "batched_generalized", "hessenberg"],
                     default="single",
                     help="single: one n x n Schur form with Q (default); batched: the "
                          "2000-matrix batch of evec_batched; generalized: an n x n pencil "
@@ -955,6 +955,161 @@ def run_batched_generalized(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+def hessenberg_counts(n):
+    """Algorithmic work of the Hessenberg reduction of order n with Q: flops
+    10/3 n^3 for H (the two-sided reflector products, LAPACK's count) plus
+    4/3 n^3 for forming Q, and the bytes the panel reductions' trailing
+    matrix-vector products read, sum_c 8 n (n - c - 1) over the reduced
+    columns c = 0 .. n - 3."""
+    F = 14.0 / 3.0 * n ** 3
+    Bpan = sum(8.0 * n * (n - c - 1) for c in range(max(n - 2, 0)))
+    return F, Bpan
+
+
+def run_hessenberg(args, rank, world, local_rank):
+    """Hessenberg reduction A = Q H Q^T of an n x n N(0, 1) matrix with Q
+    (evec_hessenberg).  Metric: reductions per second; rooflines: the panel
+    reductions against HBM (the bytes their trailing matrix-vector products
+    read), the updates against the FP64 pipe."""
+    import ctypes
+
+    import torch
+
+    import paper_2002_05024_b300 as ev
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    n = args.n
+    A = np.random.default_rng(workloads.SEED_BASE + 9).standard_normal((n, n))
+    dA0 = torch.from_numpy(np.asfortranarray(A)).to(dev)
+    dA = torch.empty((n, n), dtype=torch.float64, device=dev).t()
+    dQ = torch.empty((n, n), dtype=torch.float64, device=dev).t()
+    h = ev.handle(local_rank)
+    opts = ev._opts(0, False, "fp64", 0)
+
+    def step():
+        dA.copy_(dA0)
+        st = ev.lib().evec_hessenberg(h.ptr, n, dA.data_ptr(), n, dQ.data_ptr(), n,
+                                      ctypes.byref(opts))
+        if st:
+            raise ev.EvecError(st, "evec_hessenberg")
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    ev.sync(local_rank)
+    sampler = ClockSampler() if rank == 0 else None
+    if dist:
+        dist.barrier()
+    stream = torch.cuda.current_stream(dev)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        step()
+    t1.record(stream)
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    elapsed = t0.elapsed_time(t1)
+    clocks = sampler.stop() if sampler else None
+    prof = profiled_steps(h, step, args.steps, dev)
+    ev.sync(local_rank)
+    if dist:
+        tt = torch.tensor([elapsed], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        elapsed = float(tt.item())
+    # end to end: A in from pinned memory, H and Q out
+    hA = torch.empty((n, n), dtype=torch.float64, pin_memory=True).t()
+    hA.copy_(torch.from_numpy(A))
+    hH = torch.empty((n, n), dtype=torch.float64, pin_memory=True).t()
+    hQ = torch.empty((n, n), dtype=torch.float64, pin_memory=True).t()
+    w0 = time.perf_counter()
+    for _ in range(args.steps):
+        dA0.copy_(hA, non_blocking=True)
+        step()
+        hH.copy_(dA, non_blocking=True)
+        hQ.copy_(dQ, non_blocking=True)
+        torch.cuda.synchronize(dev)
+    e2e = {"value": world * args.steps / (time.perf_counter() - w0), "unit": "reductions/s",
+           "h2d_bytes_per_step": 8 * n * n, "d2h_bytes_per_step": 16 * n * n}
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    H, Q = dA.cpu().numpy(), dQ.cpu().numpy()
+    nrm = np.abs(A).max()
+    quality = {"max_backward_error_over_nu_maxA": float(np.abs(Q @ H @ Q.T - A).max() / (n * 2.0 ** -53 * nrm)),
+               "max_orthogonality_error_over_nu": float(np.abs(Q.T @ Q - np.eye(n)).max() / (n * 2.0 ** -53)),
+               "zeros_below_subdiagonal": bool(np.all(np.tril(H, -2) == 0.0))}
+    F, Bpan = hessenberg_counts(n)
+    peaks = measured_peaks()
+    fp64_peak = N_SMS * FP64_FLOP_PER_CLK_PER_SM * float(peaks.get("sm_max_mhz", 2032.0)) / 1e6
+    hbm = float(peaks.get("hbm_gbs") or 6400.0)
+    roofs = {}
+    pm, pn = prof.get("hess_panel", (0.0, 0))
+    if pm > 0:
+        ach = Bpan / (pm / args.steps / 1e3) / 1e9
+        roofs["hess_panel"] = {"kernel": "panel reduction (k_hs_gemv + 5 small kernels per column)",
+                               "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                               "frac": ach / hbm, "traffic": None,
+                               "peak_source": "of measured" if peaks.get("hbm_gbs") else "of fallback",
+                               "launches_per_step": pn / args.steps,
+                               "alg_bytes_per_step": Bpan, "ms_per_step": pm / args.steps}
+    um, un = prof.get("hess_update", (0.0, 0))
+    if um > 0:
+        Fu = F - 2.0 * Bpan / 8.0   # the products not done by the matrix-vector steps
+        ach = Fu / (um / args.steps / 1e3) / 1e12
+        roofs["hess_update"] = {"kernel": "trailing / top / Q updates (k_hs_gemm)", "bound": "alu",
+                                "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
+                                "frac": ach / fp64_peak, "traffic": None,
+                                "peak_source": "of derived FP64 peak (measured 4 flop/clk/SM x 148 "
+                                               "SMs x max SM clock)",
+                                "launches_per_step": un / args.steps, "alg_flops_per_step": Fu,
+                                "ms_per_step": um / args.steps}
+    dominant = max(roofs.items(), key=lambda kv: kv[1]["ms_per_step"])[0] if roofs else None
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        ns = min(n, 1024)
+        As = np.random.default_rng(3).standard_normal((ns, ns))
+        t = time.perf_counter()
+        oracle.hessenberg(As)
+        dt = time.perf_counter() - t
+        cpu = {"value": (1.0 / dt) * (ns / n) ** 3, "unit": "reductions/s", "cores": 1,
+               "kind": "oracle",
+               "sample": f"one unblocked reduction with Q at n = {ns} in {dt:.2f} s on one core, "
+                         f"extrapolated to n = {n} by (n / {ns})^3"}
+    line = {
+        "metric": "Hessenberg reductions/s (A = Q H Q^T with Q, FP64)",
+        "value": world * args.steps / (elapsed / 1e3), "unit": "reductions/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"Hessenberg reduction of an n={n} N(0, 1) matrix with Q, panels of "
+                               "32 columns", "n": n, "panel": 32, "parallelism": "replicas",
+                   "l2": f"inputs larger than L2 (A, H, Q {8 * n * n >> 20} MiB each)"},
+        "tflops_fp64": F * args.steps / (elapsed / 1e3) / 1e12,
+        "flops_per_step": F,
+        "quality": quality,
+        "roofline": roofs.get(dominant),
+        "rooflines": roofs,
+        "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+        "gpu_launches": sum(c for _, c in prof.values()),
+        "clocks": clocks,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
 def run_generalized(args, rank, world, local_rank):
     """The pencil workload: S config-0 (n x n), T upper triangular with
     diagonal U[0.5, 2] (every 50th entry 1e-12) and N(0, 1) upper part, Z from
@@ -1282,6 +1437,8 @@ def main():
         run_trsolve(args, rank, world, local_rank)
     elif args.workload == "batched_generalized":
         run_batched_generalized(args, rank, world, local_rank)
+    elif args.workload == "hessenberg":
+        run_hessenberg(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 

@@ -56,7 +56,8 @@ void launch_left_output(const double *Xw, int64_t ldw, int64_t n, int64_t m, con
 size_t hessenberg_workspace(int64_t n);
 int hess_panel_width();
 void hess_init_q(int64_t n, double *Q, int64_t ldq, cudaStream_t st);
-int hess_panel(int64_t n, double *A, int64_t lda, int64_t k, int b, double *ws, cudaStream_t st);
+int hess_panel(int64_t n, double *A, int64_t lda, int64_t k, int b, double *ws, int *err,
+               int nsm, cudaStream_t st);
 int hess_update(int64_t n, double *A, int64_t lda, double *Q, int64_t ldq, int64_t k, int b,
                 double *ws, cudaStream_t st);
 void launch_check_rhs(const double *B, int64_t ldb, int64_t n, int64_t nrhs, int64_t base,
@@ -2122,7 +2123,9 @@ extern "C" evec_status evec_hessenberg(evec_handle h, int64_t n, double *A, int6
     const int nbw = hess_panel_width();
     for (int64_t k = 0; k + 2 < n; k += nbw) {
         const int b = (int)std::min<int64_t>(nbw, n - 2 - k);
-        timed(h, EVEC_K_HESS_PANEL, [&] { return hess_panel(n, A, lda, k, b, h->hs_ws, st); });
+        timed(h, EVEC_K_HESS_PANEL, [&] {
+            return hess_panel(n, A, lda, k, b, h->hs_ws, &h->status_d->timeout, h->nsm, st);
+        });
         timed(h, EVEC_K_HESS_UPDATE,
               [&] { return hess_update(n, A, lda, Q, ldq, k, b, h->hs_ws, st); });
     }

@@ -256,59 +256,319 @@ __global__ void __launch_bounds__(32 * kGvWarps)
     }
 }
 
-// C = alpha op(A) op(B) + beta C (beta 0: C is not read); op(A) M x K,
-// op(B) K x N; 64 x 64 tiles, 16-deep K steps, 4 x 4 outputs per thread.
-template <bool TA, bool TB>
-__global__ void __launch_bounds__(256)
-    k_hs_gemm(int M, int N, int K, double alpha, const double *__restrict__ A, int64_t lda,
-              const double *__restrict__ B, int64_t ldb, double beta, double *__restrict__ C,
-              int64_t ldc) {
-    __shared__ double As[16][64 + 1];
-    __shared__ double Bs[16][64 + 1];
-    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    const int m0 = blockIdx.x * 64, n0 = blockIdx.y * 64;
-    double acc[4][4];
+// ---------------------------------------------------------------------------
+// The panel as one cooperative launch (the paper's monolithic "reduce the
+// panel" task): every CTA runs every column's phases, separated by a grid
+// barrier; the small reductions are repeated in every CTA instead of taking
+// another barrier.  The barrier waits are bounded: on expiry the kernel
+// sets *err and every CTA returns.
+// ---------------------------------------------------------------------------
+constexpr long kGridWaitLimit = 1L << 22;
+
+struct GridBar {
+    unsigned count, gen;
+};
+
+// Sense-reversing grid barrier over gridDim.x co-resident CTAs.  Returns
+// false (and sets *err) when the wait gave up.
+__device__ bool grid_barrier(GridBar *bar, int *err) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *vgen = &bar->gen;
+        const unsigned my_gen = *vgen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(&bar->count, 1u) + 1u;
+        int ok = 1;
+        if (arrived == gridDim.x) {
+            bar->count = 0;
+            __threadfence();
+            atomicAdd(&bar->gen, 1u);
+        } else {
+            long it = 0;
+            while (*vgen == my_gen) {
+                if (++it > kGridWaitLimit) {
+                    ok = 0;
+                    atomicExch(err, 1);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// scalars of the column every CTA derives from the partials
+struct ColScal {
+    double tau, d;
+    double w[kHb], s[kHb];
+};
+
+__global__ void __launch_bounds__(kHRowThreads)
+    k_hs_panel(int64_t n, double *__restrict__ A, int64_t lda, int64_t k, int b,
+               double *__restrict__ V, double *__restrict__ Y, double *__restrict__ T,
+               double *__restrict__ x, double *__restrict__ part, double *__restrict__ part2,
+               GridBar *bar, int *err) {
+    // part: the partials of phase 1 (read in phase 2), part2: those of
+    // phase 3 (read in phase 4) -- a CTA done with phase 2 must not
+    // overwrite the partials other CTAs are still reading
+    __shared__ ColScal cs;
+    __shared__ double red[8 * kHb];
+    __shared__ double rs[8], rq[8];
+    __shared__ double gv[8][33];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // only the first ceil(n / 256) CTAs own rows in the row phases (the
+    // others write zero partials): the reductions read those alone
+    const int nparts = (int)min((int64_t)gridDim.x, (n + kHRowThreads - 1) / kHRowThreads);
+    for (int i = 0; i < b; i++) {
+        const int64_t c = k + i;
+        // 1. x = A[:, c] - Y V[c, :]^T; partials of V^T x
+        {
+            if (tid < i) cs.s[tid] = V[c + (int64_t)tid * n];   // V[c, j], reused below
+            __syncthreads();
+            double acc[kHb];
 #pragma unroll
-    for (int a = 0; a < 4; a++)
+            for (int j = 0; j < kHb; j++) acc[j] = 0.0;
+            for (int64_t r = (int64_t)blockIdx.x * blockDim.x + tid; r < n; r += stride) {
+                double xr = A[r + c * lda];
+#pragma unroll
+                for (int j = 0; j < kHb; j++)
+                    if (j < i) xr = fma(-Y[r + (int64_t)j * n], cs.s[j], xr);
+                x[r] = xr;
+#pragma unroll
+                for (int j = 0; j < kHb; j++)
+                    if (j < i) acc[j] = fma(V[r + (int64_t)j * n], xr, acc[j]);
+            }
+            block_sums(acc, i, red, part, 0);
+        }
+        if (!grid_barrier(bar, err)) return;
+        // 2. w = T^T (sum of partials), in every CTA
+        if (tid < i) {
+            double u = 0.0;
+            for (int p = 0; p < nparts; p++) u += part[(int64_t)p * kHPartStride + tid];
+            cs.s[tid] = u;
+        }
+        __syncthreads();
+        if (tid < i) {
+            double w = 0.0;
+            for (int l = 0; l <= tid; l++) w = fma(T[l + tid * kHb], cs.s[l], w);
+            cs.w[tid] = w;
+        }
+        __syncthreads();
+        // 3. x -= V w; column c rows <= c; norm and V^T x partials below c + 1
+        {
+            double acc[kHb];
+#pragma unroll
+            for (int j = 0; j < kHb; j++) acc[j] = 0.0;
+            double sc = 0.0, sq = 0.0;
+            for (int64_t r = (int64_t)blockIdx.x * blockDim.x + tid; r < n; r += stride) {
+                double xr = x[r];
+#pragma unroll
+                for (int j = 0; j < kHb; j++)
+                    if (j < i) xr = fma(-V[r + (int64_t)j * n], cs.w[j], xr);
+                x[r] = xr;
+                if (r <= c) A[r + c * lda] = xr;
+                if (r >= c + 2) {
+                    ssq_merge(sc, sq, fabs(xr), xr != 0.0 ? 1.0 : 0.0);
+#pragma unroll
+                    for (int j = 0; j < kHb; j++)
+                        if (j < i) acc[j] = fma(V[r + (int64_t)j * n], xr, acc[j]);
+                }
+            }
+            block_sums(acc, i, red, part2, 0);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const double s2 = __shfl_xor_sync(0xffffffffu, sc, o);
+                const double q2 = __shfl_xor_sync(0xffffffffu, sq, o);
+                ssq_merge(sc, sq, s2, q2);
+            }
+            if (lane == 0) { rs[warp] = sc; rq[warp] = sq; }
+            __syncthreads();
+            if (tid == 0) {
+                double s0 = 0.0, q0 = 0.0;
+                for (int w8 = 0; w8 < kHRowThreads / 32; w8++) ssq_merge(s0, q0, rs[w8], rq[w8]);
+                part2[(int64_t)blockIdx.x * kHPartStride + kHb] = s0;
+                part2[(int64_t)blockIdx.x * kHPartStride + kHb + 1] = q0;
+            }
+        }
+        if (!grid_barrier(bar, err)) return;
+        // 4. the reflector, in every CTA (CTA 0 writes T, A[c+1, c])
+        if (tid == 0) {
+            double s0 = 0.0, q0 = 0.0;
+            for (int p = 0; p < nparts; p++)
+                ssq_merge(s0, q0, part2[(int64_t)p * kHPartStride + kHb],
+                          part2[(int64_t)p * kHPartStride + kHb + 1]);
+            const double xn = s0 * sqrt(q0);
+            const double alpha = x[c + 1];
+            double tau = 0.0, d = 1.0, beta = alpha;
+            if (xn != 0.0) {
+                const double mx = fmax(fabs(alpha), xn);
+                const double a = alpha / mx, bb = xn / mx;
+                beta = mx * sqrt(a * a + bb * bb);
+                if (alpha >= 0.0) beta = -beta;
+                tau = (beta - alpha) / beta;
+                d = alpha - beta;
+            }
+            cs.tau = tau;
+            cs.d = d;
+            if (blockIdx.x == 0) A[(c + 1) + c * lda] = beta;
+        }
+        __syncthreads();
+        if (tid < i) {
+            double q = 0.0;
+            for (int p = 0; p < nparts; p++) q += part2[(int64_t)p * kHPartStride + tid];
+            cs.s[tid] = cs.tau == 0.0 ? 0.0 : V[(c + 1) + (int64_t)tid * n] + q / cs.d;
+        }
+        __syncthreads();
+        if (blockIdx.x == 0) {
+            if (tid < i) {
+                double t = 0.0;
+                for (int l = tid; l < i; l++) t = fma(T[tid + l * kHb], cs.s[l], t);
+                T[tid + i * kHb] = -cs.tau * t;
+            }
+            if (tid == 0) T[i + i * kHb] = cs.tau;
+        }
+        // 5. v and the zeros below the subdiagonal of column c
+        for (int64_t r = (int64_t)blockIdx.x * blockDim.x + tid; r < n; r += stride) {
+            double v = 0.0;
+            if (r == c + 1) v = 1.0;
+            else if (r > c + 1 && cs.tau != 0.0) v = x[r] / cs.d;
+            V[r + (int64_t)i * n] = v;
+            if (r > c + 1) A[r + c * lda] = 0.0;
+        }
+        if (!grid_barrier(bar, err)) return;
+        // 6. Y[:, i] = tau (A[:, c+1:n] v - Y s): 32-row chunks, the CTA's 8
+        //    warps split the columns
+        {
+            const double *v = V + (int64_t)i * n;
+            const int64_t nchunks = (n + 31) / 32;
+            for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+                const int64_t r = ch * 32 + lane;
+                const bool rv = r < n;
+                // warp w takes columns c+1+w, +8, ...: eight loads in flight
+                // per lane (independent accumulators)
+                double as[8];
+#pragma unroll
+                for (int u = 0; u < 8; u++) as[u] = 0.0;
+                int64_t j = c + 1 + warp;
+                for (; j + 56 < n; j += 64) {
+                    double a[8];
+#pragma unroll
+                    for (int u = 0; u < 8; u++) a[u] = rv ? A[r + (j + 8 * u) * lda] : 0.0;
+#pragma unroll
+                    for (int u = 0; u < 8; u++) as[u] = fma(a[u], v[j + 8 * u], as[u]);
+                }
+                for (; j < n; j += 8)
+                    if (rv) as[0] = fma(A[r + j * lda], v[j], as[0]);
+                gv[warp][lane] = ((as[0] + as[1]) + (as[2] + as[3])) +
+                                 ((as[4] + as[5]) + (as[6] + as[7]));
+                __syncthreads();
+                if (warp == 0 && rv) {
+                    double y = 0.0;
+                    for (int w8 = 0; w8 < 8; w8++) y += gv[w8][lane];
+                    for (int l = 0; l < i; l++) y = fma(-Y[r + (int64_t)l * n], cs.s[l], y);
+                    Y[r + (int64_t)i * n] = cs.tau * y;
+                }
+                __syncthreads();
+            }
+        }
+        if (!grid_barrier(bar, err)) return;
+    }
+}
+
+// C = alpha op(A) op(B) + beta C (beta 0: C is not read); op(A) M x K,
+// op(B) K x N.  128 x 64 tiles, 16-deep K chunks double-buffered through
+// registers, 8 x 4 outputs per thread (256 threads); the shared rows are
+// padded so that the transposed operand stores do not collide in a bank.
+constexpr int kGM = 128, kGN = 64, kGK = 16;
+struct HsGemmSmem {
+    double A[2][kGK][kGM + 1];
+    double B[2][kGK][kGN + 1];
+};
+template <bool TA, bool TB>
+__device__ __forceinline__ void k_hs_gemm_body(int M, int N, int K, double alpha,
+                                               const double *__restrict__ A, int64_t lda,
+                                               const double *__restrict__ B, int64_t ldb,
+                                               double beta, double *__restrict__ C, int64_t ldc) {
+    extern __shared__ __align__(16) unsigned char hs_smraw[];
+    HsGemmSmem &sm = *reinterpret_cast<HsGemmSmem *>(hs_smraw);
+    auto &As = sm.A;
+    auto &Bs = sm.B;
+    constexpr int A_PER = kGM * kGK / 256, B_PER = kGK * kGN / 256;   // 8, 4
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int m0 = blockIdx.x * kGM, n0 = blockIdx.y * kGN;
+    double ra[A_PER], rb[B_PER];
+    auto load = [&](int k0) {
+#pragma unroll
+        for (int t = 0; t < A_PER; t++) {
+            const int e = tid + 256 * t;
+            const int mm = TA ? e / kGK : e % kGM, kk = TA ? e % kGK : e / kGM;
+            const int gm = m0 + mm, gk = k0 + kk;
+            ra[t] = (gm < M && gk < K) ? (TA ? A[gk + (int64_t)gm * lda] : A[gm + (int64_t)gk * lda])
+                                       : 0.0;
+        }
+#pragma unroll
+        for (int t = 0; t < B_PER; t++) {
+            const int e = tid + 256 * t;
+            const int nn = TB ? e % kGN : e / kGK, kk = TB ? e / kGN : e % kGK;
+            const int gn = n0 + nn, gk = k0 + kk;
+            rb[t] = (gn < N && gk < K) ? (TB ? B[gn + (int64_t)gk * ldb] : B[gk + (int64_t)gn * ldb])
+                                       : 0.0;
+        }
+    };
+    auto store = [&](int buf) {
+#pragma unroll
+        for (int t = 0; t < A_PER; t++) {
+            const int e = tid + 256 * t;
+            const int mm = TA ? e / kGK : e % kGM, kk = TA ? e % kGK : e / kGM;
+            As[buf][kk][mm] = ra[t];
+        }
+#pragma unroll
+        for (int t = 0; t < B_PER; t++) {
+            const int e = tid + 256 * t;
+            const int nn = TB ? e % kGN : e / kGK, kk = TB ? e / kGN : e % kGK;
+            Bs[buf][kk][nn] = rb[t];
+        }
+    };
+    double acc[8][4];
+#pragma unroll
+    for (int a = 0; a < 8; a++)
 #pragma unroll
         for (int b = 0; b < 4; b++) acc[a][b] = 0.0;
-    for (int k0 = 0; k0 < K; k0 += 16) {
-        for (int e = tid; e < 16 * 64; e += 256) {
-            int kk, mm;
-            if (TA) { mm = e / 16; kk = e % 16; }   // A[k + m lda]: k contiguous
-            else { kk = e / 64; mm = e % 64; }       // A[m + k lda]: m contiguous
-            const int gm = m0 + mm, gk = k0 + kk;
-            double v = 0.0;
-            if (gm < M && gk < K) v = TA ? A[gk + (int64_t)gm * lda] : A[gm + (int64_t)gk * lda];
-            As[kk][mm] = v;
-        }
-        for (int e = tid; e < 16 * 64; e += 256) {
-            int kk, nn;
-            if (TB) { kk = e / 64; nn = e % 64; }    // B[n + k ldb]: n contiguous
-            else { nn = e / 16; kk = e % 16; }       // B[k + n ldb]: k contiguous
-            const int gn = n0 + nn, gk = k0 + kk;
-            double v = 0.0;
-            if (gn < N && gk < K) v = TB ? B[gn + (int64_t)gk * ldb] : B[gk + (int64_t)gn * ldb];
-            Bs[kk][nn] = v;
-        }
+    if (K > 0) {
+        load(0);
+        store(0);
         __syncthreads();
+        int buf = 0;
+        for (int k0 = 0; k0 < K; k0 += kGK) {
+            const bool more = k0 + kGK < K;
+            if (more) load(k0 + kGK);
 #pragma unroll
-        for (int kk = 0; kk < 16; kk++) {
-            double a[4], b[4];
+            for (int kk = 0; kk < kGK; kk++) {
+                double a[8], b[4];
 #pragma unroll
-            for (int q = 0; q < 4; q++) {
-                a[q] = As[kk][ty + 16 * q];
-                b[q] = Bs[kk][tx + 16 * q];
+                for (int p = 0; p < 8; p++) a[p] = As[buf][kk][ty + 16 * p];
+#pragma unroll
+                for (int q = 0; q < 4; q++) b[q] = Bs[buf][kk][tx + 16 * q];
+#pragma unroll
+                for (int p = 0; p < 8; p++)
+#pragma unroll
+                    for (int q = 0; q < 4; q++) acc[p][q] = fma(a[p], b[q], acc[p][q]);
             }
-#pragma unroll
-            for (int p = 0; p < 4; p++)
-#pragma unroll
-                for (int q = 0; q < 4; q++) acc[p][q] = fma(a[p], b[q], acc[p][q]);
+            if (more) {
+                store(buf ^ 1);
+                __syncthreads();
+                buf ^= 1;
+            }
         }
-        __syncthreads();
     }
 #pragma unroll
-    for (int p = 0; p < 4; p++) {
+    for (int p = 0; p < 8; p++) {
         const int gm = m0 + ty + 16 * p;
         if (gm >= M) continue;
 #pragma unroll
@@ -321,15 +581,76 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(256)
+    k_hs_gemm(int M, int N, int K, double alpha, const double *__restrict__ A, int64_t lda,
+              const double *__restrict__ B, int64_t ldb, double beta, double *__restrict__ C,
+              int64_t ldc) {
+    k_hs_gemm_body<TA, TB>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+}
+
+// Split-K: the K range is cut into gridDim.z slices, each CTA writes its
+// partial tile to P[z] (M x N, ld M); k_hs_sum adds them (fixed order).
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(256)
+    k_hs_gemm_part(int M, int N, int K, int kc, const double *__restrict__ A, int64_t lda,
+                   const double *__restrict__ B, int64_t ldb, double *__restrict__ P) {
+    const int k0 = blockIdx.z * kc;
+    const int kl = min(kc, K - k0);
+    k_hs_gemm_body<TA, TB>(M, N, kl, 1.0, TA ? A + k0 : A + (int64_t)k0 * lda, lda,
+                           TB ? B + (int64_t)k0 * ldb : B + k0, ldb, 0.0,
+                           P + (int64_t)blockIdx.z * M * N, M);
+}
+
+__global__ void k_hs_sum(int M, int N, int splits, const double *__restrict__ P, double alpha,
+                         double beta, double *__restrict__ C, int64_t ldc) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)M * N) return;
+    const int64_t m = e % M, nn = e / M;
+    double acc = 0.0;
+    for (int z = 0; z < splits; z++) acc += P[(int64_t)z * M * N + e];
+    double *cp = C + m + nn * ldc;
+    *cp = beta == 0.0 ? alpha * acc : fma(alpha, acc, beta * *cp);
+}
+
+template <bool TA, bool TB>
+static void gemm_t(dim3 grid, int M, int N, int K, double alpha, const double *A, int64_t lda,
+                   const double *B, int64_t ldb, double beta, double *C, int64_t ldc,
+                   cudaStream_t st) {
+    const int smem = (int)sizeof(HsGemmSmem);
+    cudaFuncSetAttribute(k_hs_gemm<TA, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    k_hs_gemm<TA, TB><<<grid, 256, smem, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+}
+
+// C = alpha op(A) op(B) + beta C with the K range split over gridDim.z
+// when the M x N tiles alone would leave most SMs idle (the skinny products
+// A^T V and Q V); P: partial workspace of at least splits * M * N doubles.
+template <bool TA, bool TB>
+static void gemm_splitk(int M, int N, int K, double alpha, const double *A, int64_t lda,
+                        const double *B, int64_t ldb, double beta, double *C, int64_t ldc,
+                        double *P, int max_splits, cudaStream_t st) {
+    if (M <= 0 || N <= 0) return;
+    const int tiles = ((M + kGM - 1) / kGM) * ((N + kGN - 1) / kGN);
+    int splits = std::max(1, std::min(max_splits, 296 / std::max(tiles, 1)));
+    const int kc = ((K + splits - 1) / splits + kGK - 1) / kGK * kGK;
+    splits = std::max(1, (K + kc - 1) / std::max(kc, 1));
+    const int smem = (int)sizeof(HsGemmSmem);
+    cudaFuncSetAttribute(k_hs_gemm_part<TA, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    dim3 grid((unsigned)((M + kGM - 1) / kGM), (unsigned)((N + kGN - 1) / kGN), (unsigned)splits);
+    k_hs_gemm_part<TA, TB><<<grid, 256, smem, st>>>(M, N, K, kc, A, lda, B, ldb, P);
+    const int64_t tot = (int64_t)M * N;
+    k_hs_sum<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(M, N, splits, P, alpha, beta, C, ldc);
+}
+
 static void gemm(bool ta, bool tb, int M, int N, int K, double alpha, const double *A,
                  int64_t lda, const double *B, int64_t ldb, double beta, double *C, int64_t ldc,
                  cudaStream_t st) {
     if (M <= 0 || N <= 0) return;
-    dim3 grid((unsigned)((M + 63) / 64), (unsigned)((N + 63) / 64));
-    if (ta && tb) k_hs_gemm<true, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
-    else if (ta) k_hs_gemm<true, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
-    else if (tb) k_hs_gemm<false, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
-    else k_hs_gemm<false, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    dim3 grid((unsigned)((M + kGM - 1) / kGM), (unsigned)((N + kGN - 1) / kGN));
+    if (ta && tb) gemm_t<true, true>(grid, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st);
+    else if (ta) gemm_t<true, false>(grid, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st);
+    else if (tb) gemm_t<false, true>(grid, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st);
+    else gemm_t<false, false>(grid, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st);
 }
 
 __global__ void k_hs_eye(int64_t n, double *Q, int64_t ldq) {
@@ -344,16 +665,21 @@ static int hess_parts(int64_t n) {
         std::min<int64_t>((n + kHRowThreads - 1) / kHRowThreads, 128), 1);
 }
 
+constexpr int kHMaxCoop = 1024;   // partials rows reserved for the cooperative panel
+constexpr int kHSplits = 16;      // at most this many K slices in the skinny products
+
 // workspace doubles for order n: V, Y, VT, W (n x kHb each), Z (kHb x n), T
 // (kHb x kHb), x (n), w and s (kHb each), the per-CTA partials, scalars
 size_t hessenberg_workspace(int64_t n) {
     return (size_t)(5 * n * kHb + kHb * kHb + n + 2 * kHb +
-                    (int64_t)hess_parts(n) * kHPartStride + 8);
+                    2 * (int64_t)std::max(hess_parts(n), kHMaxCoop) * kHPartStride + 8 + 2 +
+                    (int64_t)kHSplits * n * kHb);
 }
 
 struct HessWs {
-    double *V, *Y, *VT, *W, *Z, *T, *x, *wv, *sv, *part;
+    double *V, *Y, *VT, *W, *Z, *T, *x, *wv, *sv, *part, *part2, *P;
     HessScal *scal;
+    GridBar *bar;
 };
 
 static HessWs hess_ws(int64_t n, double *ws) {
@@ -368,7 +694,10 @@ static HessWs hess_ws(int64_t n, double *ws) {
     w.wv = w.x + n;
     w.sv = w.wv + kHb;
     w.part = w.sv + kHb;
-    w.scal = (HessScal *)(w.part + (int64_t)hess_parts(n) * kHPartStride);
+    w.part2 = w.part + (int64_t)std::max(hess_parts(n), kHMaxCoop) * kHPartStride;
+    w.scal = (HessScal *)(w.part2 + (int64_t)std::max(hess_parts(n), kHMaxCoop) * kHPartStride);
+    w.bar = (GridBar *)(w.scal + 2);
+    w.P = (double *)(w.scal) + 10;
     return w;
 }
 
@@ -378,12 +707,36 @@ void hess_init_q(int64_t n, double *Q, int64_t ldq, cudaStream_t st) {
     k_hs_eye<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, Q, ldq);
 }
 
-// Step 1 for the panel of b columns at k: returns the kernels launched.
-int hess_panel(int64_t n, double *A, int64_t lda, int64_t k, int b, double *ws,
-               cudaStream_t st) {
+// Step 1 for the panel of b columns at k: one cooperative launch when the
+// device grants it (co-resident CTAs, bounded grid barriers), else six
+// launches per column.  Returns the kernels launched.
+int hess_panel(int64_t n, double *A, int64_t lda, int64_t k, int b, double *ws, int *err,
+               int nsm, cudaStream_t st) {
     const HessWs w = hess_ws(n, ws);
     const int parts = hess_parts(n);
     cudaMemsetAsync(w.T, 0, sizeof(double) * kHb * kHb, st);
+    {
+        static int per_sm = -1;
+        if (per_sm < 0) {
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hs_panel, kHRowThreads,
+                                                              0) != cudaSuccess)
+                per_sm = 0;
+            cudaGetLastError();
+        }
+        const int grid = std::min(std::min(per_sm, 2) * nsm, kHMaxCoop);
+        if (grid > 0) {
+            cudaMemsetAsync(w.bar, 0, sizeof(GridBar), st);
+            int64_t nn = n, kk = k;
+            int bb = b;
+            double *V = w.V, *Y = w.Y, *T = w.T, *x = w.x, *pa = w.part, *pb = w.part2;
+            GridBar *bar = w.bar;
+            void *args[] = {&nn, &A, &lda, &kk, &bb, &V, &Y, &T, &x, &pa, &pb, &bar, &err};
+            if (cudaLaunchCooperativeKernel((const void *)k_hs_panel, dim3(grid),
+                                            dim3(kHRowThreads), args, 0, st) == cudaSuccess)
+                return 1;
+            cudaGetLastError();   // not granted: the launch-per-step path below
+        }
+    }
     for (int i = 0; i < b; i++) {
         const int64_t c = k + i;
         k_hs_col<<<parts, kHRowThreads, 0, st>>>(n, A, lda, c, i, w.Y, w.V, w.x, w.part);
@@ -410,17 +763,18 @@ int hess_update(int64_t n, double *A, int64_t lda, double *Q, int64_t ldq, int64
     if (nt > 0) {
         // A[:, j0:n] -= Y V[j0:n, :]^T (every row: the top part and the rest)
         gemm(false, true, (int)n, nt, b, -1.0, w.Y, n, w.V + j0, n, 1.0, A + j0 * lda, lda, st);
-        // rows k+1 ..: A <- A - (V T^T) (V^T A)
-        gemm(true, false, b, nt, rows, 1.0, w.V + (k + 1), n, A + (k + 1) + j0 * lda, lda, 0.0,
-             w.Z, kHb, st);
+        // rows k+1 ..: A <- A - (V T^T) (V^T A), with Zt = A^T V (nt x b,
+        // the long dimension on the tile's 128 rows)
+        gemm_splitk<true, false>(nt, b, rows, 1.0, A + (k + 1) + j0 * lda, lda, w.V + (k + 1), n,
+                                 0.0, w.Z, n, w.P, kHSplits, st);
         gemm(false, true, rows, b, b, 1.0, w.V + (k + 1), n, w.T, kHb, 0.0, w.VT, n, st);
-        gemm(false, false, rows, nt, b, -1.0, w.VT, n, w.Z, kHb, 1.0, A + (k + 1) + j0 * lda, lda,
+        gemm(false, true, rows, nt, b, -1.0, w.VT, n, w.Z, n, 1.0, A + (k + 1) + j0 * lda, lda,
              st);
         ng += 4;
     }
     if (Q) {   // Q[:, k+1:n] -= (Q[:, k+1:n] V[k+1:n, :]) T V[k+1:n, :]^T
-        gemm(false, false, (int)n, b, rows, 1.0, Q + (k + 1) * ldq, ldq, w.V + (k + 1), n, 0.0,
-             w.W, n, st);
+        gemm_splitk<false, false>((int)n, b, rows, 1.0, Q + (k + 1) * ldq, ldq, w.V + (k + 1), n,
+                                  0.0, w.W, n, w.P, kHSplits, st);
         gemm(false, false, (int)n, b, b, 1.0, w.W, n, w.T, kHb, 0.0, w.VT, n, st);
         gemm(false, true, (int)n, rows, b, -1.0, w.VT, n, w.V + (k + 1), n, 1.0,
              Q + (k + 1) * ldq, ldq, st);
