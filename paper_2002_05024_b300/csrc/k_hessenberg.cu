@@ -450,23 +450,26 @@ __global__ void __launch_bounds__(kHRowThreads)
             for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
                 const int64_t r = ch * 32 + lane;
                 const bool rv = r < n;
-                // warp w takes columns c+1+w, +8, ...: eight loads in flight
-                // per lane (independent accumulators)
-                double as[8];
+                // warp w takes columns c+1+w, +8, ...: sixteen loads in
+                // flight per lane (independent accumulators)
+                constexpr int kU = 16;
+                double as[kU];
 #pragma unroll
-                for (int u = 0; u < 8; u++) as[u] = 0.0;
+                for (int u = 0; u < kU; u++) as[u] = 0.0;
                 int64_t j = c + 1 + warp;
-                for (; j + 56 < n; j += 64) {
-                    double a[8];
+                for (; j + 8 * (kU - 1) < n; j += 8 * kU) {
+                    double a[kU];
 #pragma unroll
-                    for (int u = 0; u < 8; u++) a[u] = rv ? A[r + (j + 8 * u) * lda] : 0.0;
+                    for (int u = 0; u < kU; u++) a[u] = rv ? A[r + (j + 8 * u) * lda] : 0.0;
 #pragma unroll
-                    for (int u = 0; u < 8; u++) as[u] = fma(a[u], v[j + 8 * u], as[u]);
+                    for (int u = 0; u < kU; u++) as[u] = fma(a[u], v[j + 8 * u], as[u]);
                 }
                 for (; j < n; j += 8)
                     if (rv) as[0] = fma(A[r + j * lda], v[j], as[0]);
-                gv[warp][lane] = ((as[0] + as[1]) + (as[2] + as[3])) +
-                                 ((as[4] + as[5]) + (as[6] + as[7]));
+                double g = 0.0;
+#pragma unroll
+                for (int u = 0; u < kU; u++) g += as[u];
+                gv[warp][lane] = g;
                 __syncthreads();
                 if (warp == 0 && rv) {
                     double y = 0.0;
