@@ -212,6 +212,24 @@ def profiled_steps(h, step, steps, dev, k=3):
     return {kind: (ms * steps / k, int(round(c * steps / k))) for kind, (ms, c) in prof.items()}
 
 
+def reduce_over_ranks(x, dist=None, device=None, op="max"):
+    """The max (or sum) of a float over the ranks of the default process
+    group (NCCL on the GPU, gloo on the host); x itself without a group."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64,
+                     device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, steps, seconds_max, world):
+    """Whole-job throughput: every rank processed units_per_rank units per
+    step (weak scaling); the slowest rank's time is the job's."""
+    return world * units_per_rank * steps / seconds_max
+
+
 def measured_peaks():
     try:
         return json.load(open(MEASURED))
@@ -483,13 +501,10 @@ def run_ours(args, rank, world, local_rank):
     clocks = sampler.stop() if sampler else None
     ev.sync(local_rank)
     prof = profiled_steps(h, step, args.steps, dev)
-    if dist:
-        tt = torch.tensor([elapsed_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(tt.item())
+    elapsed_ms = reduce_over_ranks(elapsed_ms, dist, dev)
 
     ms_per_step = elapsed_ms / args.steps
-    value = world * m * args.steps / (elapsed_ms / 1e3)
+    value = whole_job_rate(m, args.steps, elapsed_ms / 1e3, world)
     tflops = world * F * args.steps / (elapsed_ms / 1e3) / 1e12
 
     # roofline of the dominant kernel (largest share of event-timed time)
