@@ -399,11 +399,99 @@ def run_reference_trsolve(args):
     print(json.dumps(line), flush=True)
 
 
+def reference_line(args, metric, unit, workload, value, sample, ms_per_step, cores):
+    return {
+        "impl": "reference", "metric": metric, "value": value, "unit": unit,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": {"workload": workload},
+        "cpu_baseline": {"value": value, "unit": unit, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def run_reference_other(args):
+    """The oracle on bounded samples of the batched, pencil, batched-pencil
+    and Hessenberg workloads (same metric and unit as the GPU arm)."""
+    import oracle
+    oracle.build()
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    cores = int(os.environ.get("OMP_NUM_THREADS", cores))
+    units, secs = 0.0, 0.0
+    if args.workload in ("batched", "batched_generalized"):
+        if args.workload == "batched":
+            _, mats, sels = workloads.batch_inputs(args.batch)
+            run = lambda i: oracle.standard(mats[i], select=sels[i])[0].shape[1]  # noqa: E731
+            metric = "eigvec columns/s, batched (robust FP64 eigenvectors, many Schur forms)"
+            what = f"batch of {args.batch} Schur forms, n log-uniform in [32, 1024]"
+        else:
+            _, mats, sels = workloads.batch_pencils(args.batch)
+            run = lambda i: oracle.generalized(mats[i][0], mats[i][1],  # noqa: E731
+                                               select=sels[i])[0].shape[1]
+            metric = "eigvec columns/s, batched pencils (robust FP64 generalized eigenvectors)"
+            what = f"batch of {args.batch} pencils, n log-uniform in [32, 1024]"
+        per = max(8, min(len(mats), 50))
+        for i in range(args.warmup + args.steps):
+            pick = np.random.default_rng(2000 + i).choice(len(mats), size=per, replace=False)
+            t = time.perf_counter()
+            c = sum(run(int(k)) for k in pick)
+            dt = time.perf_counter() - t
+            if i >= args.warmup:
+                units += c
+                secs += dt
+        unit = "columns/s"
+        sample = f"{per} random matrices of the batch per step, on the host cores"
+    elif args.workload == "generalized":
+        n = args.n
+        S, T, blocks = workloads.generalized_pair(n, seed=workloads.SEED_BASE + 4)
+        Z = workloads.householder_orthogonal(n, seed=workloads.SEED_BASE + 104)
+        per = max(2, args.cpu_sample // 64)
+        for i in range(args.warmup + args.steps):
+            rng = np.random.default_rng(3000 + i)
+            sel = np.zeros(n, np.uint8)
+            for b in rng.choice(len(blocks), size=per, replace=False):
+                p, sz = blocks[b]
+                sel[p:p + sz] = 1
+            t = time.perf_counter()
+            c = oracle.generalized(S, T, Z, select=sel)[0].shape[1]
+            dt = time.perf_counter() - t
+            if i >= args.warmup:
+                units += c
+                secs += dt
+        unit = "columns/s"
+        metric = "eigvec columns/s, generalized (robust FP64 eigenvectors of a pencil incl. X = Z Y)"
+        what = f"pencil (S, T) n={n} with Z, all columns"
+        sample = f"{per} random eigenvalues per step of the n={n} pencil, on the host cores"
+    else:   # hessenberg: one unblocked reduction at a reduced order per step
+        n = args.n
+        ns = min(n, 768)
+        for i in range(args.warmup + args.steps):
+            A = np.random.default_rng(4000 + i).standard_normal((ns, ns))
+            t = time.perf_counter()
+            oracle.hessenberg(A)
+            dt = time.perf_counter() - t
+            if i >= args.warmup:
+                units += (ns / n) ** 3
+                secs += dt
+        unit = "reductions/s"
+        metric = "Hessenberg reductions/s (A = Q H Q^T with Q, FP64)"
+        what = f"Hessenberg reduction of an n={n} N(0, 1) matrix with Q"
+        sample = (f"one unblocked reduction with Q at n = {ns} per step on one core, counted as "
+                  f"(n / {ns})^3 reductions of order {n}")
+        cores = 1
+    value = units / secs if secs > 0 else 0.0
+    print(json.dumps(reference_line(args, metric, unit, what + " (oracle samples)", value, sample,
+                                    1e3 * secs / max(args.steps, 1), cores)), flush=True)
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
     if args.workload == "trsolve":
         return run_reference_trsolve(args)
+    if args.workload in ("batched", "batched_generalized", "generalized", "hessenberg"):
+        return run_reference_other(args)
     T, blocks, Q = workload(args.n)
     per_step = max(16, args.cpu_sample // 4)
     times, cols = [], []
