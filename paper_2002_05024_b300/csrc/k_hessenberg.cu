@@ -308,6 +308,53 @@ struct ColScal {
     double w[kHb], s[kHb];
 };
 
+// Block sums of the kHb values every thread holds in registers (zero
+// where unused), written to out[0 .. kHb): a reduce-scatter butterfly in
+// each warp (31 shuffles and 31 FP64 additions per lane instead of 5 per
+// value; lane j ends with the warp's sum of value j), then the warps' sums
+// in shared memory.  red: 8 x kHb doubles.
+__device__ __forceinline__ void block_sums_rs(double (&v)[kHb], double *red, double *out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const bool hi = (lane & o) != 0;
+#pragma unroll
+        for (int k = 0; k < o; k++) {
+            const double keep = hi ? v[o + k] : v[k];
+            const double send = hi ? v[k] : v[o + k];
+            v[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    red[warp * kHb + lane] = v[0];
+    __syncthreads();
+    if (threadIdx.x < kHb) {
+        double t = 0.0;
+#pragma unroll
+        for (int w = 0; w < kHRowThreads / 32; w++) t += red[w * kHb + threadIdx.x];
+        out[threadIdx.x] = t;
+    }
+    __syncthreads();
+}
+
+// Sum over nparts rows of the partials (value j = 0 .. kHb-1 at column
+// off + j) by all threads of the CTA: thread (group g, value j) sums rows
+// g, g + 8, ..., then the groups in shared memory.  red: 8 x kHb doubles.
+__device__ __forceinline__ void sum_partials(const double *part, int nparts, int off, double *red,
+                                             double *out) {
+    const int j = threadIdx.x & 31, g = threadIdx.x >> 5;
+    double t = 0.0;
+    for (int p = g; p < nparts; p += kHRowThreads / 32) t += part[(int64_t)p * kHPartStride + off + j];
+    red[g * kHb + j] = t;
+    __syncthreads();
+    if (threadIdx.x < kHb) {
+        double u = 0.0;
+#pragma unroll
+        for (int w = 0; w < kHRowThreads / 32; w++) u += red[w * kHb + threadIdx.x];
+        out[threadIdx.x] = u;
+    }
+    __syncthreads();
+}
+
 __global__ void __launch_bounds__(kHRowThreads)
     k_hs_panel(int64_t n, double *__restrict__ A, int64_t lda, int64_t k, int b,
                double *__restrict__ V, double *__restrict__ Y, double *__restrict__ T,
@@ -321,10 +368,12 @@ __global__ void __launch_bounds__(kHRowThreads)
     __shared__ double rs[8], rq[8];
     __shared__ double gv[8][33];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    // only the first ceil(n / 256) CTAs own rows in the row phases (the
-    // others write zero partials): the reductions read those alone
-    const int nparts = (int)min((int64_t)gridDim.x, (n + kHRowThreads - 1) / kHRowThreads);
+    // rows of the row phases: a contiguous block of rpc rows per CTA
+    // (ceil(n / grid) rounded up to 32), so that all SMs share the FP64
+    // work; the reductions read the partials of the row-owning CTAs
+    const int64_t rpc = ((n + gridDim.x - 1) / gridDim.x + 31) / 32 * 32;
+    const int64_t rbeg = (int64_t)blockIdx.x * rpc, rend = min(rbeg + rpc, n);
+    const int nparts = (int)min((int64_t)gridDim.x, (n + rpc - 1) / rpc);
     for (int i = 0; i < b; i++) {
         const int64_t c = k + i;
         // 1. x = A[:, c] - Y V[c, :]^T; partials of V^T x
@@ -334,7 +383,7 @@ __global__ void __launch_bounds__(kHRowThreads)
             double acc[kHb];
 #pragma unroll
             for (int j = 0; j < kHb; j++) acc[j] = 0.0;
-            for (int64_t r = (int64_t)blockIdx.x * blockDim.x + tid; r < n; r += stride) {
+            for (int64_t r = rbeg + tid; r < rend; r += blockDim.x) {
                 double xr = A[r + c * lda];
 #pragma unroll
                 for (int j = 0; j < kHb; j++)
@@ -344,16 +393,12 @@ __global__ void __launch_bounds__(kHRowThreads)
                 for (int j = 0; j < kHb; j++)
                     if (j < i) acc[j] = fma(V[r + (int64_t)j * n], xr, acc[j]);
             }
-            block_sums(acc, i, red, part, 0);
+            if ((int64_t)blockIdx.x < nparts)
+                block_sums_rs(acc, red, part + (int64_t)blockIdx.x * kHPartStride);
         }
         if (!grid_barrier(bar, err)) return;
         // 2. w = T^T (sum of partials), in every CTA
-        if (tid < i) {
-            double u = 0.0;
-            for (int p = 0; p < nparts; p++) u += part[(int64_t)p * kHPartStride + tid];
-            cs.s[tid] = u;
-        }
-        __syncthreads();
+        sum_partials(part, nparts, 0, red, cs.s);
         if (tid < i) {
             double w = 0.0;
             for (int l = 0; l <= tid; l++) w = fma(T[l + tid * kHb], cs.s[l], w);
@@ -366,7 +411,7 @@ __global__ void __launch_bounds__(kHRowThreads)
 #pragma unroll
             for (int j = 0; j < kHb; j++) acc[j] = 0.0;
             double sc = 0.0, sq = 0.0;
-            for (int64_t r = (int64_t)blockIdx.x * blockDim.x + tid; r < n; r += stride) {
+            for (int64_t r = rbeg + tid; r < rend; r += blockDim.x) {
                 double xr = x[r];
 #pragma unroll
                 for (int j = 0; j < kHb; j++)
@@ -380,7 +425,8 @@ __global__ void __launch_bounds__(kHRowThreads)
                         if (j < i) acc[j] = fma(V[r + (int64_t)j * n], xr, acc[j]);
                 }
             }
-            block_sums(acc, i, red, part2, 0);
+            if ((int64_t)blockIdx.x < nparts)
+                block_sums_rs(acc, red, part2 + (int64_t)blockIdx.x * kHPartStride);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
                 const double s2 = __shfl_xor_sync(0xffffffffu, sc, o);
@@ -397,12 +443,25 @@ __global__ void __launch_bounds__(kHRowThreads)
             }
         }
         if (!grid_barrier(bar, err)) return;
-        // 4. the reflector, in every CTA (CTA 0 writes T, A[c+1, c])
-        if (tid == 0) {
+        // 4. the reflector, in every CTA (CTA 0 writes T, A[c+1, c]); the
+        //    partials of V^T x below row c + 1 into cs.w (w is done with)
+        sum_partials(part2, nparts, 0, red, cs.w);
+        if (warp == 0) {   // (scale, ssq) merged by a warp tree
             double s0 = 0.0, q0 = 0.0;
-            for (int p = 0; p < nparts; p++)
+            for (int p = lane; p < nparts; p += 32)
                 ssq_merge(s0, q0, part2[(int64_t)p * kHPartStride + kHb],
                           part2[(int64_t)p * kHPartStride + kHb + 1]);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const double s2 = __shfl_xor_sync(0xffffffffu, s0, o);
+                const double q2 = __shfl_xor_sync(0xffffffffu, q0, o);
+                ssq_merge(s0, q0, s2, q2);
+            }
+            if (lane == 0) rs[0] = s0, rq[0] = q0;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            const double s0 = rs[0], q0 = rq[0];
             const double xn = s0 * sqrt(q0);
             const double alpha = x[c + 1];
             double tau = 0.0, d = 1.0, beta = alpha;
@@ -419,11 +478,8 @@ __global__ void __launch_bounds__(kHRowThreads)
             if (blockIdx.x == 0) A[(c + 1) + c * lda] = beta;
         }
         __syncthreads();
-        if (tid < i) {
-            double q = 0.0;
-            for (int p = 0; p < nparts; p++) q += part2[(int64_t)p * kHPartStride + tid];
-            cs.s[tid] = cs.tau == 0.0 ? 0.0 : V[(c + 1) + (int64_t)tid * n] + q / cs.d;
-        }
+        if (tid < i)
+            cs.s[tid] = cs.tau == 0.0 ? 0.0 : V[(c + 1) + (int64_t)tid * n] + cs.w[tid] / cs.d;
         __syncthreads();
         if (blockIdx.x == 0) {
             if (tid < i) {
@@ -434,7 +490,7 @@ __global__ void __launch_bounds__(kHRowThreads)
             if (tid == 0) T[i + i * kHb] = cs.tau;
         }
         // 5. v and the zeros below the subdiagonal of column c
-        for (int64_t r = (int64_t)blockIdx.x * blockDim.x + tid; r < n; r += stride) {
+        for (int64_t r = rbeg + tid; r < rend; r += blockDim.x) {
             double v = 0.0;
             if (r == c + 1) v = 1.0;
             else if (r > c + 1 && cs.tau != 0.0) v = x[r] / cs.d;
