@@ -353,8 +353,8 @@ evec_status evec_batched(evec_handle h, int64_t count, const int64_t *n_host,
  * requirements of evec_generalized.  Output packing as evec_batched (X_i at
  * sum_{k<i} n_k m_k; scale_exp_i, alpha_re_i, alpha_im_i, beta_i at
  * sum_{k<i} m_k; the last three may be NULL); m_i from evec_batched_count
- * on S_packed.  opt->mode must be EVEC_FP64; opt->tile 16..64, 0 = 32 (the
- * solver holds both matrices' diagonal tiles).  Device-side errors
+ * on S_packed.  opt->mode must be EVEC_FP64; opt->tile 16..64, 0 = 64 (the
+ * solver holds both matrices' diagonal tiles: one CTA per SM at 64).  Device-side errors
  * (evec_sync / opt->check): index = element offset in S_packed or T_packed
  * of the offending entry.
  */
