@@ -184,6 +184,13 @@ evec_status evec_standard_left(evec_handle h, int64_t n, const double *T, int64_
 evec_status evec_hessenberg(evec_handle h, int64_t n, double *A, int64_t lda, double *Q,
                             int64_t ldq, const evec_opts *opt);
 
+/* How evec_hessenberg reduces a panel: 1 (default) one cooperative launch
+ * per panel (every CTA co-resident, bounded grid barriers between the
+ * column phases; falls back to 0 when the device refuses the launch), 0
+ * six launches per column.  Same reflectors either way; the sums of the
+ * partial reductions group differently (results agree to rounding). */
+evec_status evec_set_hessenberg_panel(evec_handle h, int cooperative);
+
 /*
  * The same computation with HOST buffers (column-major, ld = n): copies
  * T (and Q) to the device, computes, copies X [n x m], scale_exp [m],

@@ -86,6 +86,7 @@ def lib() -> ctypes.CDLL:
         L.evec_profile.argtypes = [p, ctypes.c_int]
         L.evec_set_lookahead.argtypes = [p, ctypes.c_int]
         L.evec_hessenberg.argtypes = [p, i64, p, i64, p, i64, ctypes.POINTER(_Opts)]
+        L.evec_set_hessenberg_panel.argtypes = [p, ctypes.c_int]
         L.evec_profile_read.argtypes = [p, p, p, ctypes.c_int]
         L.evec_last_cuda_error.argtypes = []
         L.evec_last_cuda_error.restype = ctypes.c_char_p
@@ -106,6 +107,7 @@ def lib() -> ctypes.CDLL:
                   "evec_plan_query", "evec_trsolve",
                   "evec_profile", "evec_profile_read", "evec_batched_count", "evec_batched",
                   "evec_batched_generalized", "evec_set_lookahead", "evec_hessenberg",
+                  "evec_set_hessenberg_panel",
                   "evec_generalized",
                   "evec_tune_get", "evec_tune_set"):
             getattr(L, f).restype = ctypes.c_int
@@ -162,6 +164,12 @@ class Handle:
         bad = ctypes.c_int64(-1)
         st = lib().evec_sync(self._h, ctypes.byref(bad))
         _check(st, "evec_sync", bad.value)
+
+    def hessenberg_panel(self, cooperative: bool):
+        """Hessenberg panels as one cooperative launch (default) or six
+        launches per column."""
+        _check(lib().evec_set_hessenberg_panel(self._h, 1 if cooperative else 0),
+               "evec_set_hessenberg_panel")
 
     def lookahead(self, enable: bool):
         """Look-ahead schedule of the split-mode solve (off by default)."""

@@ -57,7 +57,7 @@ size_t hessenberg_workspace(int64_t n);
 int hess_panel_width();
 void hess_init_q(int64_t n, double *Q, int64_t ldq, cudaStream_t st);
 int hess_panel(int64_t n, double *A, int64_t lda, int64_t k, int b, double *ws, int *err,
-               int nsm, cudaStream_t st);
+               int nsm, bool cooperative, cudaStream_t st);
 int hess_update(int64_t n, double *A, int64_t lda, double *Q, int64_t ldq, int64_t k, int b,
                 double *ws, cudaStream_t st);
 void launch_check_rhs(const double *B, int64_t ldb, int64_t n, int64_t nrhs, int64_t base,
@@ -555,6 +555,7 @@ struct evec_ctx {
     double *lL = nullptr; size_t lL_cap = 0;
     int32_t *lmap_d = nullptr; size_t lmap_cap = 0;
     double *hs_ws = nullptr; size_t hs_ws_cap = 0;   // Hessenberg reduction
+    bool hess_coop = true;   // panel as one cooperative launch (else six launches per column)
     std::vector<int32_t> lmap_h;
     std::vector<uint8_t> lsel;
     // pinned host buffers
@@ -943,6 +944,12 @@ evec_status evec_destroy(evec_handle h) {
         if (p) cudaFreeHost(p);
     cudaGetLastError();
     delete h;
+    return EVEC_OK;
+}
+
+evec_status evec_set_hessenberg_panel(evec_handle h, int cooperative) {
+    if (!h) return EVEC_EINVAL;
+    h->hess_coop = cooperative != 0;
     return EVEC_OK;
 }
 
@@ -2127,7 +2134,8 @@ extern "C" evec_status evec_hessenberg(evec_handle h, int64_t n, double *A, int6
     for (int64_t k = 0; k + 2 < n; k += nbw) {
         const int b = (int)std::min<int64_t>(nbw, n - 2 - k);
         timed(h, EVEC_K_HESS_PANEL, [&] {
-            return hess_panel(n, A, lda, k, b, h->hs_ws, &h->status_d->timeout, h->nsm, st);
+            return hess_panel(n, A, lda, k, b, h->hs_ws, &h->status_d->timeout, h->nsm,
+                              h->hess_coop, st);
         });
         timed(h, EVEC_K_HESS_UPDATE,
               [&] { return hess_update(n, A, lda, Q, ldq, k, b, h->hs_ws, st); });

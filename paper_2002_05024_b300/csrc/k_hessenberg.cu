@@ -770,7 +770,7 @@ void hess_init_q(int64_t n, double *Q, int64_t ldq, cudaStream_t st) {
 // device grants it (co-resident CTAs, bounded grid barriers), else six
 // launches per column.  Returns the kernels launched.
 int hess_panel(int64_t n, double *A, int64_t lda, int64_t k, int b, double *ws, int *err,
-               int nsm, cudaStream_t st) {
+               int nsm, bool cooperative, cudaStream_t st) {
     const HessWs w = hess_ws(n, ws);
     const int parts = hess_parts(n);
     cudaMemsetAsync(w.T, 0, sizeof(double) * kHb * kHb, st);
@@ -782,7 +782,7 @@ int hess_panel(int64_t n, double *A, int64_t lda, int64_t k, int b, double *ws, 
                 per_sm = 0;
             cudaGetLastError();
         }
-        const int grid = std::min(std::min(per_sm, 2) * nsm, kHMaxCoop);
+        const int grid = cooperative ? std::min(std::min(per_sm, 2) * nsm, kHMaxCoop) : 0;
         if (grid > 0) {
             cudaMemsetAsync(w.bar, 0, sizeof(GridBar), st);
             int64_t nn = n, kk = k;

@@ -92,3 +92,25 @@ def test_hessenberg_full_size_invariants():
     assert np.abs(Q.T @ Q - np.eye(n)).max() <= 8 * n * U
     R = Q @ H @ Q.T - A
     assert np.abs(R).max() <= _bound(n) * np.abs(A).max(), np.abs(R).max()
+
+
+def test_hessenberg_panel_paths_agree():
+    # the six-launch panel path (used when a device refuses the cooperative
+    # launch) against the oracle and the cooperative path
+    n = 333
+    A = np.random.default_rng(31).standard_normal((n, n))
+    h = ev.handle(0)
+    out = {}
+    for coop in (False, True):
+        h.hessenberg_panel(coop)
+        try:
+            out[coop] = _gpu(A)
+        finally:
+            h.hessenberg_panel(True)
+    Ho, Qo, _ = oracle.hessenberg(A)
+    nrm = np.abs(A).max()
+    for coop, (H, Q) in out.items():
+        assert np.all(np.tril(H, -2) == 0.0)
+        assert np.abs(H - Ho).max() <= _bound(n) * nrm, (coop, np.abs(H - Ho).max())
+        assert np.abs(Q - Qo).max() <= _bound(n), coop
+    assert np.abs(out[False][0] - out[True][0]).max() <= _bound(n) * nrm
