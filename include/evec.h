@@ -73,7 +73,8 @@ typedef enum {
     EVEC_ENOMEM = 4,     /* device or host allocation failed */
     EVEC_ECUDA = 5,      /* CUDA runtime error */
     EVEC_ETIMEOUT = 6,   /* a bounded device-side wait gave up (reported by evec_sync) */
-    EVEC_ERESIDUAL = 7,  /* reserved: residual gate failed */
+    EVEC_ERESIDUAL = 7,  /* reserved (the residual gate of refine = 2 repeats
+                            the solve in FP64 rather than failing) */
     EVEC_ECAPACITY = 8   /* problem larger than evec_standard_noalloc's fixed scratch */
 } evec_status;
 
@@ -106,7 +107,13 @@ typedef struct {
                     outweighs the split error.  Costs one FP64 product of
                     about n^3 / 3 flops for all columns, and an extra
                     n x m FP64 workspace.  Ignored in EVEC_FP64 mode and
-                    for pencils. */
+                    for pencils.  2 = the sweep, then the residual gate of
+                    the refined vectors: ||(T - lambda I) y||_1 <=
+                    10 n ||T||_1 ||y||_1 u (u = 2^-53) per eigenvalue, from
+                    a second FP64 residual; if any eigenvalue fails, the
+                    matrix is solved again with 8 slices (and the gate), or
+                    in EVEC_FP64 mode when it already had 8
+                    (evec_gate_stats reports what happened). */
 } evec_opts;
 
 /* Create a handle on CUDA device `device` that launches on `cuda_stream`
@@ -243,6 +250,11 @@ enum {
     EVEC_K_HESS_UPDATE = 11, /* evec_hessenberg: trailing / top updates, Q */
     EVEC_K_COUNT = 12
 };
+
+/* The residual gate of the last evec_standard call with refine = 2:
+ * eigenvalues that failed it in the first solve, and the number of
+ * repeated solves (more slices, then FP64). */
+evec_status evec_gate_stats(evec_handle h, int64_t *failed_units, int *retries);
 
 /* Look-ahead schedule of the split-mode solve (default off): the diagonal
  * solve of step s leaves its protection decisions to a separate launch, and

@@ -87,6 +87,7 @@ def lib() -> ctypes.CDLL:
         L.evec_set_lookahead.argtypes = [p, ctypes.c_int]
         L.evec_hessenberg.argtypes = [p, i64, p, i64, p, i64, ctypes.POINTER(_Opts)]
         L.evec_set_hessenberg_panel.argtypes = [p, ctypes.c_int]
+        L.evec_gate_stats.argtypes = [p, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_int)]
         L.evec_profile_read.argtypes = [p, p, p, ctypes.c_int]
         L.evec_last_cuda_error.argtypes = []
         L.evec_last_cuda_error.restype = ctypes.c_char_p
@@ -107,7 +108,7 @@ def lib() -> ctypes.CDLL:
                   "evec_plan_query", "evec_trsolve",
                   "evec_profile", "evec_profile_read", "evec_batched_count", "evec_batched",
                   "evec_batched_generalized", "evec_set_lookahead", "evec_hessenberg",
-                  "evec_set_hessenberg_panel",
+                  "evec_set_hessenberg_panel", "evec_gate_stats",
                   "evec_generalized",
                   "evec_tune_get", "evec_tune_set"):
             getattr(L, f).restype = ctypes.c_int
@@ -140,7 +141,7 @@ def _mask(select, n):
 
 
 def _opts(tile, check, mode="fp64", slices=0, refine=False):
-    return _Opts(MODES[mode], int(tile), 1 if check else 0, int(slices), 1 if refine else 0)
+    return _Opts(MODES[mode], int(tile), 1 if check else 0, int(slices), int(refine))
 
 
 # ---------------------------------------------------------------------------
@@ -164,6 +165,14 @@ class Handle:
         bad = ctypes.c_int64(-1)
         st = lib().evec_sync(self._h, ctypes.byref(bad))
         _check(st, "evec_sync", bad.value)
+
+    def gate_stats(self):
+        """(eigenvalues that failed the residual gate in the last refine = 2
+        call's first solve, repeated solves)."""
+        f = ctypes.c_int64(0)
+        r = ctypes.c_int(0)
+        _check(lib().evec_gate_stats(self._h, ctypes.byref(f), ctypes.byref(r)), "evec_gate_stats")
+        return int(f.value), int(r.value)
 
     def hessenberg_panel(self, cooperative: bool):
         """Hessenberg panels as one cooperative launch (default) or six

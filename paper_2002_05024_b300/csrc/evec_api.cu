@@ -60,6 +60,9 @@ int hess_panel(int64_t n, double *A, int64_t lda, int64_t k, int b, double *ws, 
                int nsm, bool cooperative, cudaStream_t st);
 int hess_update(int64_t n, double *A, int64_t lda, double *Q, int64_t ldq, int64_t k, int b,
                 double *ws, cudaStream_t st);
+void launch_gate(const Plan &p, const double *Y, int64_t ldy, const int32_t *ey, const double *R,
+                 int64_t ldr, const double *T, int64_t ldt, double limit, void *buf,
+                 double *ratio, cudaStream_t st);
 void launch_check_rhs(const double *B, int64_t ldb, int64_t n, int64_t nrhs, int64_t base,
                       DevStatus *status, cudaStream_t st);
 void launch_refine_combine(const Plan &p, double *Y, int64_t ldy, const int32_t *ey,
@@ -555,6 +558,12 @@ struct evec_ctx {
     double *lL = nullptr; size_t lL_cap = 0;
     int32_t *lmap_d = nullptr; size_t lmap_cap = 0;
     double *hs_ws = nullptr; size_t hs_ws_cap = 0;   // Hessenberg reduction
+    // residual gate of the split solve (opts.refine >= 2): ||T||_1 and the
+    // failure count on the device; the last top-level call's statistics
+    unsigned long long *gate_d = nullptr;
+    int gate_depth = 0;
+    int64_t gate_failed = 0;
+    int gate_retries = 0;
     bool hess_coop = true;   // panel as one cooperative launch (else six launches per column)
     std::vector<int32_t> lmap_h;
     std::vector<uint8_t> lsel;
@@ -924,7 +933,7 @@ evec_status evec_destroy(evec_handle h) {
                    h->slA, h->slB, h->rmax, h->cmax, h->ea, h->eb, h->panels,
                    h->ea_panels, h->boff_d, h->bws, h->bplan_d, h->queue_d, h->tauT,
                    h->blk_tauT, h->pW, h->Rd, h->seg_ey, h->lT, h->lQ, h->lX, h->lE, h->lL,
-                   h->lmap_d, h->hs_ws};
+                   h->lmap_d, h->hs_ws, h->gate_d};
     for (void *p : dev)
         if (p) cudaFree(p);
     for (auto &t : h->live) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
@@ -950,6 +959,13 @@ evec_status evec_destroy(evec_handle h) {
 evec_status evec_set_hessenberg_panel(evec_handle h, int cooperative) {
     if (!h) return EVEC_EINVAL;
     h->hess_coop = cooperative != 0;
+    return EVEC_OK;
+}
+
+evec_status evec_gate_stats(evec_handle h, int64_t *failed_units, int *retries) {
+    if (!h) return EVEC_EINVAL;
+    if (failed_units) *failed_units = h->gate_failed;
+    if (retries) *retries = h->gate_retries;
     return EVEC_OK;
 }
 
@@ -1175,8 +1191,13 @@ evec_status evec_standard(evec_handle h, int64_t n, const double *T, int64_t ldt
     if (n == 0) return EVEC_OK;
     if (!T || !X || !scale_exp) return EVEC_EINVAL;
     const bool refine = mode == EVEC_SPLIT && opt && opt->refine;
+    const bool gate = refine && opt->refine >= 2;
     DeviceGuard g(h->device);
     if (!g.ok) return EVEC_ECUDA;
+    if (h->gate_depth == 0) {   // statistics of this top-level call
+        h->gate_failed = 0;
+        h->gate_retries = 0;
+    }
 
     int64_t bad = -1;
     EVEC_TRY(plan_device_matrix(h, n, T, ldt, select_host, nb, &bad));
@@ -1278,6 +1299,40 @@ evec_status evec_standard(evec_handle h, int64_t n, const double *T, int64_t ldt
             launch_refine_combine(dp, Y, ldy, h->seg_ey, D, ldd, h->seg_e, 20 - 7 * slices, st);
             return 1;
         });
+        if (gate) {
+            // the residual of the refined y on its segments, and the gate
+            // ||(T - lambda I) y||_1 <= 10 n ||T||_1 ||y||_1 u per unit; a
+            // failure re-runs the matrix with 8 slices, then in FP64
+            if (!h->gate_d) EVEC_CUDA(cudaMalloc((void **)&h->gate_d, 2 * sizeof(uint64_t)));
+            timed(h, EVEC_K_REFINE, [&] {
+                launch_residual(T, ldt, dp, N, HP.max_tile, Y, ldy, h->seg_ey, h->row_tile_d, D,
+                                ldd, st);
+                launch_gate(dp, Y, ldy, h->seg_ey, D, ldd, T, ldt, 10.0 * (double)n, h->gate_d,
+                            nullptr, st);
+                return 4;
+            });
+            EVEC_CUDA(cudaGetLastError());
+            int fails = 0;
+            EVEC_CUDA(cudaMemcpyAsync(&fails, h->gate_d + 1, sizeof(int), cudaMemcpyDeviceToHost,
+                                      st));
+            EVEC_CUDA(cudaStreamSynchronize(st));
+            if (h->gate_depth == 0) h->gate_failed = fails;
+            if (fails > 0) {
+                evec_opts o = *opt;
+                if (slices < 8) {
+                    o.slices = 8;
+                } else {
+                    o.mode = EVEC_FP64;
+                    o.refine = 0;
+                }
+                h->gate_retries++;
+                h->gate_depth++;
+                const evec_status rs = evec_standard(h, n, T, ldt, Q, ldq, select_host, X, ldx,
+                                                     scale_exp, lam_re, lam_im, &o);
+                h->gate_depth--;
+                return rs;
+            }
+        }
     }
     timed(h, EVEC_K_FINALIZE, [&] {
         launch_finalize(dp, Y, ldy, refine ? h->seg_ey : h->seg_e, scale_exp, st);

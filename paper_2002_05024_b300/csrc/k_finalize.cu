@@ -231,6 +231,111 @@ __global__ void __launch_bounds__(kWarps * 32)
     }
 }
 
+__device__ __forceinline__ double warp_sumd(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// ||T||_1 over the referenced part (upper triangle and first subdiagonal):
+// the largest column sum, merged by atomicMax on the bit patterns (the order
+// of non-negative doubles); one warp per column.
+__global__ void __launch_bounds__(kWarps * 32)
+    k_norm1(const double *__restrict__ T, int64_t ldt, int64_t n,
+            unsigned long long *__restrict__ out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t j = (int64_t)blockIdx.x * kWarps + warp;
+    if (j >= n) return;
+    const int64_t iend = min(j + 2, n);
+    double s = 0.0;
+    for (int64_t i = lane; i < iend; i += 32) s += fabs(T[i + j * ldt]);
+    s = warp_sumd(s);
+    if (lane == 0) atomicMax(out, (unsigned long long)__double_as_longlong(s));
+}
+
+// The residual gate of one unit (one CTA): the normalised residual
+// ||(T - lambda I) y||_1 / (||T||_1 ||y||_1 u), u = 2^-53 (pairs: sums of
+// |re| + |im|), from the segments Y_r (scale 2^-ey_r) and the residual R_r
+// in the same scales (k_residual; zero at and below the block).  Both sums
+// are taken in the common scale of the largest segment (exact powers of
+// two), so nothing overflows.  Units above `limit` (or not finite) are
+// counted in *fails; ratio[u] receives the value.
+__global__ void __launch_bounds__(kWarps * 32)
+    k_gate(Plan P, const double *__restrict__ Y, int64_t ldy, const int32_t *__restrict__ ey,
+           const double *__restrict__ R, int64_t ldr, const unsigned long long *__restrict__ tn,
+           double limit, int *__restrict__ fails, double *__restrict__ ratio) {
+    const int u = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t m = P.m;
+    const int col = P.unit_col[u];
+    const bool cplx = P.unit_lam[2 * u + 1] != 0.0;
+    const int c = P.unit_tile[u];
+    const int kb = P.unit_blk[u];
+    const int bend = P.blk_start[kb] + P.blk_size[kb];
+    __shared__ int sE[kWarps];
+    __shared__ double sy[kWarps], sr[kWarps];
+    int E = INT32_MIN;
+    for (int r = warp; r <= c; r += kWarps) {
+        const int a = P.tile_start[r], b = min(P.tile_start[r + 1], bend);
+        double my = 0.0;
+        for (int i = a + lane; i < b; i += 32) {
+            double v = fabs(Y[i + (int64_t)col * ldy]);
+            if (cplx) v += fabs(Y[i + (int64_t)(col + 1) * ldy]);
+            my = fmax(my, v);
+        }
+        my = warp_max(my);
+        if (my > 0.0) E = max(E, ilog2_abs(my) - ey[(int64_t)r * m + col]);
+    }
+    E = warp_imax(E);
+    if (lane == 0) sE[warp] = E;
+    __syncthreads();
+    int Eall = INT32_MIN;
+#pragma unroll
+    for (int w = 0; w < kWarps; w++) Eall = max(Eall, sE[w]);
+    double ty = 0.0, tr = 0.0;
+    if (Eall != INT32_MIN) {
+        for (int r = warp; r <= c; r += kWarps) {
+            const int a = P.tile_start[r], b = min(P.tile_start[r + 1], bend);
+            double yy = 0.0, rr = 0.0;
+            for (int i = a + lane; i < b; i += 32) {
+                yy += fabs(Y[i + (int64_t)col * ldy]);
+                rr += fabs(R[i + (int64_t)col * ldr]);
+                if (cplx) {
+                    yy += fabs(Y[i + (int64_t)(col + 1) * ldy]);
+                    rr += fabs(R[i + (int64_t)(col + 1) * ldr]);
+                }
+            }
+            yy = warp_sumd(yy);
+            rr = warp_sumd(rr);
+            const int k = -ey[(int64_t)r * m + col] - Eall;
+            ty += scale2(yy, k);
+            tr += scale2(rr, k);
+        }
+    }
+    if (lane == 0) { sy[warp] = ty; sr[warp] = tr; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double y1 = 0.0, r1 = 0.0;
+#pragma unroll
+        for (int w = 0; w < kWarps; w++) { y1 += sy[w]; r1 += sr[w]; }
+        const double tnorm = __longlong_as_double((long long)*tn);
+        const double q = r1 / (tnorm * y1 * 0x1p-53);
+        if (ratio) ratio[u] = q;
+        if (!(q <= limit)) atomicAdd(fails, 1);
+    }
+}
+
+void launch_gate(const Plan &p, const double *Y, int64_t ldy, const int32_t *ey, const double *R,
+                 int64_t ldr, const double *T, int64_t ldt, double limit, void *buf,
+                 double *ratio, cudaStream_t st) {
+    // buf: [0] ||T||_1 bits, [1] failure count (int)
+    unsigned long long *tn = (unsigned long long *)buf;
+    int *fails = (int *)(tn + 1);
+    cudaMemsetAsync(buf, 0, 2 * sizeof(unsigned long long), st);
+    k_norm1<<<(unsigned)((p.n + kWarps - 1) / kWarps), kWarps * 32, 0, st>>>(T, ldt, p.n, tn);
+    k_gate<<<p.nunits, kWarps * 32, 0, st>>>(p, Y, ldy, ey, R, ldr, tn, limit, fails, ratio);
+}
+
 void launch_rhs_init(const Plan &p, const double *R, int64_t ldr, double *seg_nu,
                      cudaStream_t st) {
     if (p.nunits <= 0) return;

@@ -232,3 +232,53 @@ def test_refine_full_size_config2_sampled():
             yref = ld_real_eigvec(T, blocks, p)
             d, s = extended_errors(yref, Q.T @ X[:, j], e[j])
             assert d <= 1e-12 and s <= 1e-9, (j, d, s)
+
+
+def _spread(n, seed):
+    # real eigenvalues spread over [-50, 50] (gaps up to 100): an error in
+    # a vector shows in its residual (T - lambda I) dy, unlike the clustered
+    # config-0 spectrum, where a residual gate passes errors that lie along
+    # nearby eigenvectors
+    rng = np.random.default_rng(seed)
+    T = np.triu(rng.standard_normal((n, n)), 1)
+    T[np.arange(n), np.arange(n)] = rng.permutation(np.linspace(-50.0, 50.0, n))
+    return T, [(i, 1) for i in range(n)]
+
+
+def test_residual_gate_repeats_a_failing_solve():
+    # refine = 2: after the sweep, the gate ||(T - lambda I) y||_1 <= 10 n
+    # ||T||_1 ||y||_1 u per eigenvalue.  At 2 slices (about 2^-14 per
+    # product, 2^-28 after one sweep) the spread spectrum fails it; the
+    # matrix is solved again with 8 slices and then meets the parity bar
+    n = 400
+    T, blocks = _spread(n, 61)
+    out = _gpu(T, tile=64, slices=2, refine=2)
+    failed, retries = ev.handle(0).gate_stats()
+    assert failed > 0 and retries >= 1, (failed, retries)
+    _zeros_below_blocks(blocks, out[0])
+    assert _against_oracle(T, None, out) <= REL_TOL
+
+
+def test_residual_gate_passes_at_8_slices():
+    n = 613
+    for T in (workloads.config0_schur(n, seed=62)[0], _spread(n, 65)[0]):
+        out = _gpu(T, tile=64, refine=2)
+        assert ev.handle(0).gate_stats() == (0, 0)
+        assert _against_oracle(T, None, out) <= REL_TOL
+
+
+def test_residual_gate_with_q_and_left():
+    n = 300
+    T, blocks = _spread(n, 63)
+    Q = workloads.householder_orthogonal(n, seed=64)
+    out = _gpu(T, Q, tile=32, slices=2, refine=2)
+    failed, retries = ev.handle(0).gate_stats()
+    assert failed > 0 and retries >= 1
+    assert _against_oracle(T, Q, out) <= REL_TOL
+    # the left eigenvectors run the same path on the flipped form
+    dT = torch.from_numpy(np.asfortranarray(T)).cuda()
+    X, e, lr, li = ev.left(dT, tile=32, check=True, mode="split", slices=2, refine=2)
+    assert ev.handle(0).gate_stats()[1] >= 1
+    Xo, eo, _, lio = oracle.left(T)
+    de, rel = compare_canonical(Xo, eo, X.cpu().numpy(), e.cpu().numpy(), lio)
+    assert de <= 1 and rel <= REL_TOL, (de, rel)
