@@ -355,6 +355,20 @@ __device__ __forceinline__ void sum_partials(const double *part, int nparts, int
     __syncthreads();
 }
 
+// Column norm thresholds on the high word of |x| (sign cleared): while the
+// largest entry lies in [2^-480, 2^480) the plain sum of squares neither
+// overflows nor drops a term that matters (a term below 2^-537 is under
+// 2^-114 of the largest square), so the reflector takes sqrt(alpha^2 +
+// sum x^2) directly; outside that range every CTA recomputes the norm with
+// a running scale.  The plain form keeps divisions off the column's
+// critical path: on this part a dependent FP64 operation costs a whole
+// pipe pass (64 cycles), a division about ten.
+constexpr unsigned kNrmLo = (1023u - 480u) << 20, kNrmHi = (1023u + 480u) << 20;
+
+__device__ __forceinline__ unsigned abs_hi(double v) {
+    return (unsigned)((unsigned long long)__double_as_longlong(v) >> 32) & 0x7fffffffu;
+}
+
 __global__ void __launch_bounds__(kHRowThreads)
     k_hs_panel(int64_t n, double *__restrict__ A, int64_t lda, int64_t k, int b,
                double *__restrict__ V, double *__restrict__ Y, double *__restrict__ T,
@@ -366,6 +380,7 @@ __global__ void __launch_bounds__(kHRowThreads)
     __shared__ ColScal cs;
     __shared__ double red[8 * kHb];
     __shared__ double rs[8], rq[8];
+    __shared__ unsigned rmh[8];
     __shared__ double gv[8][33];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     // rows of the row phases: a contiguous block of rpc rows per CTA
@@ -374,9 +389,14 @@ __global__ void __launch_bounds__(kHRowThreads)
     const int64_t rpc = ((n + gridDim.x - 1) / gridDim.x + 31) / 32 * 32;
     const int64_t rbeg = (int64_t)blockIdx.x * rpc, rend = min(rbeg + rpc, n);
     const int nparts = (int)min((int64_t)gridDim.x, (n + rpc - 1) / rpc);
+    // T and the subdiagonal entry are written by the last CTA, which owns
+    // no rows whenever the grid outnumbers the row blocks: its serial
+    // chain then runs while the row owners form v
+    const bool scalar_cta = blockIdx.x == gridDim.x - 1;
     for (int i = 0; i < b; i++) {
         const int64_t c = k + i;
-        // 1. x = A[:, c] - Y V[c, :]^T; partials of V^T x
+        // 1. x = A[:, c] - Y V[c, :]^T; partials of V^T x.  The sums run
+        //    as four interleaved chains (a chain link is a pipe pass).
         {
             if (tid < i) cs.s[tid] = V[c + (int64_t)tid * n];   // V[c, j], reused below
             __syncthreads();
@@ -384,10 +404,11 @@ __global__ void __launch_bounds__(kHRowThreads)
 #pragma unroll
             for (int j = 0; j < kHb; j++) acc[j] = 0.0;
             for (int64_t r = rbeg + tid; r < rend; r += blockDim.x) {
-                double xr = A[r + c * lda];
+                double x4[4] = {A[r + c * lda], 0.0, 0.0, 0.0};
 #pragma unroll
                 for (int j = 0; j < kHb; j++)
-                    if (j < i) xr = fma(-Y[r + (int64_t)j * n], cs.s[j], xr);
+                    if (j < i) x4[j & 3] = fma(-Y[r + (int64_t)j * n], cs.s[j], x4[j & 3]);
+                const double xr = (x4[0] + x4[1]) + (x4[2] + x4[3]);
                 x[r] = xr;
 #pragma unroll
                 for (int j = 0; j < kHb; j++)
@@ -400,33 +421,71 @@ __global__ void __launch_bounds__(kHRowThreads)
         // 2. w = T^T (sum of partials), in every CTA
         sum_partials(part, nparts, 0, red, cs.s);
         if (tid < i) {
-            double w = 0.0;
-            for (int l = 0; l <= tid; l++) w = fma(T[l + tid * kHb], cs.s[l], w);
-            cs.w[tid] = w;
+            double w4[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+            for (int l = 0; l < kHb; l++)
+                if (l <= tid) w4[l & 3] = fma(T[l + tid * kHb], cs.s[l], w4[l & 3]);
+            cs.w[tid] = (w4[0] + w4[1]) + (w4[2] + w4[3]);
         }
         __syncthreads();
-        // 3. x -= V w; column c rows <= c; norm and V^T x partials below c + 1
+        // 3. x -= V w; column c rows <= c; below row c + 1: the V^T x
+        //    partials, the sum of squares (value kHb - 1, which no V column
+        //    uses as i < kHb) and the largest high word of |x|
         {
             double acc[kHb];
 #pragma unroll
             for (int j = 0; j < kHb; j++) acc[j] = 0.0;
-            double sc = 0.0, sq = 0.0;
+            unsigned mh = 0;
             for (int64_t r = rbeg + tid; r < rend; r += blockDim.x) {
-                double xr = x[r];
+                double x4[4] = {x[r], 0.0, 0.0, 0.0};
 #pragma unroll
                 for (int j = 0; j < kHb; j++)
-                    if (j < i) xr = fma(-V[r + (int64_t)j * n], cs.w[j], xr);
+                    if (j < i) x4[j & 3] = fma(-V[r + (int64_t)j * n], cs.w[j], x4[j & 3]);
+                const double xr = (x4[0] + x4[1]) + (x4[2] + x4[3]);
                 x[r] = xr;
                 if (r <= c) A[r + c * lda] = xr;
                 if (r >= c + 2) {
-                    ssq_merge(sc, sq, fabs(xr), xr != 0.0 ? 1.0 : 0.0);
+                    acc[kHb - 1] = fma(xr, xr, acc[kHb - 1]);
+                    mh = max(mh, abs_hi(xr));
 #pragma unroll
                     for (int j = 0; j < kHb; j++)
                         if (j < i) acc[j] = fma(V[r + (int64_t)j * n], xr, acc[j]);
                 }
             }
-            if ((int64_t)blockIdx.x < nparts)
+            mh = __reduce_max_sync(0xffffffffu, mh);
+            if (lane == 0) rmh[warp] = mh;
+            if ((int64_t)blockIdx.x < nparts) {
+                // (its barriers make rmh visible)
                 block_sums_rs(acc, red, part2 + (int64_t)blockIdx.x * kHPartStride);
+                if (tid == 0) {
+                    unsigned m = 0;
+                    for (int w8 = 0; w8 < kHRowThreads / 32; w8++) m = max(m, rmh[w8]);
+                    reinterpret_cast<unsigned long long *>(
+                        part2)[(int64_t)blockIdx.x * kHPartStride + kHb] = m;
+                }
+            }
+        }
+        if (!grid_barrier(bar, err)) return;
+        // 4. the reflector, in every CTA; the partials of V^T x below row
+        //    c + 1 (and the sum of squares) into cs.w (w is done with)
+        sum_partials(part2, nparts, 0, red, cs.w);
+        if (warp == 0) {
+            unsigned m = 0;
+            for (int p = lane; p < nparts; p += 32)
+                m = max(m, (unsigned)reinterpret_cast<const unsigned long long *>(
+                               part2)[(int64_t)p * kHPartStride + kHb]);
+            m = __reduce_max_sync(0xffffffffu, m);
+            if (lane == 0) rmh[0] = m;
+        }
+        __syncthreads();
+        const double alpha = x[c + 1];
+        const bool plain = rmh[0] >= kNrmLo && rmh[0] < kNrmHi && abs_hi(alpha) < kNrmHi;
+        if (!plain) {   // (uniform) scaled sum of squares of x[c+2 : n], alike in every CTA
+            double sc = 0.0, sq = 0.0;
+            for (int64_t r = c + 2 + tid; r < n; r += blockDim.x) {
+                const double xr = x[r];
+                ssq_merge(sc, sq, fabs(xr), xr != 0.0 ? 1.0 : 0.0);
+            }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
                 const double s2 = __shfl_xor_sync(0xffffffffu, sc, o);
@@ -435,57 +494,42 @@ __global__ void __launch_bounds__(kHRowThreads)
             }
             if (lane == 0) { rs[warp] = sc; rq[warp] = sq; }
             __syncthreads();
-            if (tid == 0) {
-                double s0 = 0.0, q0 = 0.0;
-                for (int w8 = 0; w8 < kHRowThreads / 32; w8++) ssq_merge(s0, q0, rs[w8], rq[w8]);
-                part2[(int64_t)blockIdx.x * kHPartStride + kHb] = s0;
-                part2[(int64_t)blockIdx.x * kHPartStride + kHb + 1] = q0;
-            }
         }
-        if (!grid_barrier(bar, err)) return;
-        // 4. the reflector, in every CTA (CTA 0 writes T, A[c+1, c]); the
-        //    partials of V^T x below row c + 1 into cs.w (w is done with)
-        sum_partials(part2, nparts, 0, red, cs.w);
-        if (warp == 0) {   // (scale, ssq) merged by a warp tree
-            double s0 = 0.0, q0 = 0.0;
-            for (int p = lane; p < nparts; p += 32)
-                ssq_merge(s0, q0, part2[(int64_t)p * kHPartStride + kHb],
-                          part2[(int64_t)p * kHPartStride + kHb + 1]);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const double s2 = __shfl_xor_sync(0xffffffffu, s0, o);
-                const double q2 = __shfl_xor_sync(0xffffffffu, q0, o);
-                ssq_merge(s0, q0, s2, q2);
-            }
-            if (lane == 0) rs[0] = s0, rq[0] = q0;
-        }
-        __syncthreads();
         if (tid == 0) {
-            const double s0 = rs[0], q0 = rq[0];
-            const double xn = s0 * sqrt(q0);
-            const double alpha = x[c + 1];
             double tau = 0.0, d = 1.0, beta = alpha;
-            if (xn != 0.0) {
-                const double mx = fmax(fabs(alpha), xn);
-                const double a = alpha / mx, bb = xn / mx;
-                beta = mx * sqrt(a * a + bb * bb);
+            if (plain) {   // the sum of squares is positive here
+                beta = sqrt(fma(alpha, alpha, cs.w[kHb - 1]));
                 if (alpha >= 0.0) beta = -beta;
                 tau = (beta - alpha) / beta;
                 d = alpha - beta;
+            } else {
+                double s0 = 0.0, q0 = 0.0;
+                for (int w8 = 0; w8 < kHRowThreads / 32; w8++) ssq_merge(s0, q0, rs[w8], rq[w8]);
+                const double xn = s0 * sqrt(q0);
+                if (xn != 0.0) {
+                    const double mx = fmax(fabs(alpha), xn);
+                    const double a = alpha / mx, bb = xn / mx;
+                    beta = mx * sqrt(a * a + bb * bb);
+                    if (alpha >= 0.0) beta = -beta;
+                    tau = (beta - alpha) / beta;
+                    d = alpha - beta;
+                }
             }
             cs.tau = tau;
             cs.d = d;
-            if (blockIdx.x == 0) A[(c + 1) + c * lda] = beta;
+            if (scalar_cta) A[(c + 1) + c * lda] = beta;
         }
         __syncthreads();
         if (tid < i)
             cs.s[tid] = cs.tau == 0.0 ? 0.0 : V[(c + 1) + (int64_t)tid * n] + cs.w[tid] / cs.d;
         __syncthreads();
-        if (blockIdx.x == 0) {
+        if (scalar_cta) {
             if (tid < i) {
-                double t = 0.0;
-                for (int l = tid; l < i; l++) t = fma(T[tid + l * kHb], cs.s[l], t);
-                T[tid + i * kHb] = -cs.tau * t;
+                double t4[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+                for (int l = 0; l < kHb; l++)
+                    if (l >= tid && l < i) t4[l & 3] = fma(T[tid + l * kHb], cs.s[l], t4[l & 3]);
+                T[tid + i * kHb] = -cs.tau * ((t4[0] + t4[1]) + (t4[2] + t4[3]));
             }
             if (tid == 0) T[i + i * kHb] = cs.tau;
         }
@@ -507,7 +551,8 @@ __global__ void __launch_bounds__(kHRowThreads)
                 const int64_t r = ch * 32 + lane;
                 const bool rv = r < n;
                 // warp w takes columns c+1+w, +8, ...: sixteen loads in
-                // flight per lane (independent accumulators)
+                // flight per lane (independent accumulators; 32 measured
+                // the same, and a double-buffered batch was slower)
                 constexpr int kU = 16;
                 double as[kU];
 #pragma unroll
@@ -522,16 +567,20 @@ __global__ void __launch_bounds__(kHRowThreads)
                 }
                 for (; j < n; j += 8)
                     if (rv) as[0] = fma(A[r + j * lda], v[j], as[0]);
-                double g = 0.0;
 #pragma unroll
-                for (int u = 0; u < kU; u++) g += as[u];
-                gv[warp][lane] = g;
+                for (int h = kU / 2; h > 0; h >>= 1)
+#pragma unroll
+                    for (int u = 0; u < h; u++) as[u] += as[u + h];
+                gv[warp][lane] = as[0];
                 __syncthreads();
                 if (warp == 0 && rv) {
-                    double y = 0.0;
-                    for (int w8 = 0; w8 < 8; w8++) y += gv[w8][lane];
-                    for (int l = 0; l < i; l++) y = fma(-Y[r + (int64_t)l * n], cs.s[l], y);
-                    Y[r + (int64_t)i * n] = cs.tau * y;
+                    double y4[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+                    for (int w8 = 0; w8 < 8; w8++) y4[w8 & 3] += gv[w8][lane];
+#pragma unroll
+                    for (int l = 0; l < kHb; l++)
+                        if (l < i) y4[l & 3] = fma(-Y[r + (int64_t)l * n], cs.s[l], y4[l & 3]);
+                    Y[r + (int64_t)i * n] = cs.tau * ((y4[0] + y4[1]) + (y4[2] + y4[3]));
                 }
                 __syncthreads();
             }
@@ -541,32 +590,43 @@ __global__ void __launch_bounds__(kHRowThreads)
 }
 
 // C = alpha op(A) op(B) + beta C (beta 0: C is not read); op(A) M x K,
-// op(B) K x N.  128 x 64 tiles, 16-deep K chunks double-buffered through
-// registers, 8 x 4 outputs per thread (256 threads); the shared rows are
-// padded so that the transposed operand stores do not collide in a bank.
-constexpr int kGM = 128, kGN = 64, kGK = 16;
-struct HsGemmSmem {
-    double A[2][kGK][kGM + 1];
-    double B[2][kGK][kGN + 1];
+// op(B) K x N.  Tiles of GM x GN outputs, RM x 4 per thread (256 threads):
+// 128 x 64 (RM 8) for the rank-32 updates; 256 x 32 (RM 8) for the long
+// products with the panel's 32 columns, which a 64-wide tile would run at
+// half its multiply-adds; 32 x 32 (RM 1) for the small ones with K = 32,
+// which need the CTAs more than the reuse.  16-deep K chunks
+// double-buffered through registers; the shared rows are padded so that
+// the transposed operand stores do not collide in a bank.
+constexpr int kGK = 16;
+template <int GN, int RM>
+struct HsTile {
+    static constexpr int TX = GN / 4, TY = 256 / TX, GM = RM * TY;
 };
-template <bool TA, bool TB>
+template <int GN, int RM>
+struct HsGemmSmem {
+    double A[2][kGK][HsTile<GN, RM>::GM + 1];
+    double B[2][kGK][GN + 1];
+};
+template <int GN, int RM, bool TA, bool TB>
 __device__ __forceinline__ void k_hs_gemm_body(int M, int N, int K, double alpha,
                                                const double *__restrict__ A, int64_t lda,
                                                const double *__restrict__ B, int64_t ldb,
                                                double beta, double *__restrict__ C, int64_t ldc) {
+    using Tile = HsTile<GN, RM>;
+    constexpr int TX = Tile::TX, TY = Tile::TY, GM = Tile::GM;
     extern __shared__ __align__(16) unsigned char hs_smraw[];
-    HsGemmSmem &sm = *reinterpret_cast<HsGemmSmem *>(hs_smraw);
+    HsGemmSmem<GN, RM> &sm = *reinterpret_cast<HsGemmSmem<GN, RM> *>(hs_smraw);
     auto &As = sm.A;
     auto &Bs = sm.B;
-    constexpr int A_PER = kGM * kGK / 256, B_PER = kGK * kGN / 256;   // 8, 4
-    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    const int m0 = blockIdx.x * kGM, n0 = blockIdx.y * kGN;
+    constexpr int A_PER = GM * kGK / 256, B_PER = kGK * GN / 256;
+    const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
+    const int m0 = blockIdx.x * GM, n0 = blockIdx.y * GN;
     double ra[A_PER], rb[B_PER];
     auto load = [&](int k0) {
 #pragma unroll
         for (int t = 0; t < A_PER; t++) {
             const int e = tid + 256 * t;
-            const int mm = TA ? e / kGK : e % kGM, kk = TA ? e % kGK : e / kGM;
+            const int mm = TA ? e / kGK : e % GM, kk = TA ? e % kGK : e / GM;
             const int gm = m0 + mm, gk = k0 + kk;
             ra[t] = (gm < M && gk < K) ? (TA ? A[gk + (int64_t)gm * lda] : A[gm + (int64_t)gk * lda])
                                        : 0.0;
@@ -574,7 +634,7 @@ __device__ __forceinline__ void k_hs_gemm_body(int M, int N, int K, double alpha
 #pragma unroll
         for (int t = 0; t < B_PER; t++) {
             const int e = tid + 256 * t;
-            const int nn = TB ? e % kGN : e / kGK, kk = TB ? e / kGN : e % kGK;
+            const int nn = TB ? e % GN : e / kGK, kk = TB ? e / GN : e % kGK;
             const int gn = n0 + nn, gk = k0 + kk;
             rb[t] = (gn < N && gk < K) ? (TB ? B[gn + (int64_t)gk * ldb] : B[gk + (int64_t)gn * ldb])
                                        : 0.0;
@@ -584,19 +644,19 @@ __device__ __forceinline__ void k_hs_gemm_body(int M, int N, int K, double alpha
 #pragma unroll
         for (int t = 0; t < A_PER; t++) {
             const int e = tid + 256 * t;
-            const int mm = TA ? e / kGK : e % kGM, kk = TA ? e % kGK : e / kGM;
+            const int mm = TA ? e / kGK : e % GM, kk = TA ? e % kGK : e / GM;
             As[buf][kk][mm] = ra[t];
         }
 #pragma unroll
         for (int t = 0; t < B_PER; t++) {
             const int e = tid + 256 * t;
-            const int nn = TB ? e % kGN : e / kGK, kk = TB ? e / kGN : e % kGK;
+            const int nn = TB ? e % GN : e / kGK, kk = TB ? e / GN : e % kGK;
             Bs[buf][kk][nn] = rb[t];
         }
     };
-    double acc[8][4];
+    double acc[RM][4];
 #pragma unroll
-    for (int a = 0; a < 8; a++)
+    for (int a = 0; a < RM; a++)
 #pragma unroll
         for (int b = 0; b < 4; b++) acc[a][b] = 0.0;
     if (K > 0) {
@@ -609,13 +669,13 @@ __device__ __forceinline__ void k_hs_gemm_body(int M, int N, int K, double alpha
             if (more) load(k0 + kGK);
 #pragma unroll
             for (int kk = 0; kk < kGK; kk++) {
-                double a[8], b[4];
+                double a[RM], b[4];
 #pragma unroll
-                for (int p = 0; p < 8; p++) a[p] = As[buf][kk][ty + 16 * p];
+                for (int p = 0; p < RM; p++) a[p] = As[buf][kk][ty + TY * p];
 #pragma unroll
-                for (int q = 0; q < 4; q++) b[q] = Bs[buf][kk][tx + 16 * q];
+                for (int q = 0; q < 4; q++) b[q] = Bs[buf][kk][tx + TX * q];
 #pragma unroll
-                for (int p = 0; p < 8; p++)
+                for (int p = 0; p < RM; p++)
 #pragma unroll
                     for (int q = 0; q < 4; q++) acc[p][q] = fma(a[p], b[q], acc[p][q]);
             }
@@ -627,12 +687,12 @@ __device__ __forceinline__ void k_hs_gemm_body(int M, int N, int K, double alpha
         }
     }
 #pragma unroll
-    for (int p = 0; p < 8; p++) {
-        const int gm = m0 + ty + 16 * p;
+    for (int p = 0; p < RM; p++) {
+        const int gm = m0 + ty + TY * p;
         if (gm >= M) continue;
 #pragma unroll
         for (int q = 0; q < 4; q++) {
-            const int gn = n0 + tx + 16 * q;
+            const int gn = n0 + tx + TX * q;
             if (gn >= N) continue;
             double *cp = C + gm + (int64_t)gn * ldc;
             *cp = beta == 0.0 ? alpha * acc[p][q] : fma(alpha, acc[p][q], beta * *cp);
@@ -640,25 +700,25 @@ __device__ __forceinline__ void k_hs_gemm_body(int M, int N, int K, double alpha
     }
 }
 
-template <bool TA, bool TB>
+template <int GN, int RM, bool TA, bool TB>
 __global__ void __launch_bounds__(256)
     k_hs_gemm(int M, int N, int K, double alpha, const double *__restrict__ A, int64_t lda,
               const double *__restrict__ B, int64_t ldb, double beta, double *__restrict__ C,
               int64_t ldc) {
-    k_hs_gemm_body<TA, TB>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    k_hs_gemm_body<GN, RM, TA, TB>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
 }
 
 // Split-K: the K range is cut into gridDim.z slices, each CTA writes its
 // partial tile to P[z] (M x N, ld M); k_hs_sum adds them (fixed order).
-template <bool TA, bool TB>
+template <int GN, bool TA, bool TB>
 __global__ void __launch_bounds__(256)
     k_hs_gemm_part(int M, int N, int K, int kc, const double *__restrict__ A, int64_t lda,
                    const double *__restrict__ B, int64_t ldb, double *__restrict__ P) {
     const int k0 = blockIdx.z * kc;
     const int kl = min(kc, K - k0);
-    k_hs_gemm_body<TA, TB>(M, N, kl, 1.0, TA ? A + k0 : A + (int64_t)k0 * lda, lda,
-                           TB ? B + (int64_t)k0 * ldb : B + k0, ldb, 0.0,
-                           P + (int64_t)blockIdx.z * M * N, M);
+    k_hs_gemm_body<GN, 8, TA, TB>(M, N, kl, 1.0, TA ? A + k0 : A + (int64_t)k0 * lda, lda,
+                               TB ? B + (int64_t)k0 * ldb : B + k0, ldb, 0.0,
+                               P + (int64_t)blockIdx.z * M * N, M);
 }
 
 __global__ void k_hs_sum(int M, int N, int splits, const double *__restrict__ P, double alpha,
@@ -672,44 +732,59 @@ __global__ void k_hs_sum(int M, int N, int splits, const double *__restrict__ P,
     *cp = beta == 0.0 ? alpha * acc : fma(alpha, acc, beta * *cp);
 }
 
-template <bool TA, bool TB>
-static void gemm_t(dim3 grid, int M, int N, int K, double alpha, const double *A, int64_t lda,
+template <int GN, int RM, bool TA, bool TB>
+static void gemm_t(int M, int N, int K, double alpha, const double *A, int64_t lda,
                    const double *B, int64_t ldb, double beta, double *C, int64_t ldc,
                    cudaStream_t st) {
-    const int smem = (int)sizeof(HsGemmSmem);
-    cudaFuncSetAttribute(k_hs_gemm<TA, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    k_hs_gemm<TA, TB><<<grid, 256, smem, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    constexpr int GM = HsTile<GN, RM>::GM;
+    const int smem = (int)sizeof(HsGemmSmem<GN, RM>);
+    cudaFuncSetAttribute(k_hs_gemm<GN, RM, TA, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         smem);
+    dim3 grid((unsigned)((M + GM - 1) / GM), (unsigned)((N + GN - 1) / GN));
+    k_hs_gemm<GN, RM, TA, TB><<<grid, 256, smem, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C,
+                                                      ldc);
 }
 
 // C = alpha op(A) op(B) + beta C with the K range split over gridDim.z
 // when the M x N tiles alone would leave most SMs idle (the skinny products
-// A^T V and Q V); P: partial workspace of at least splits * M * N doubles.
+// A^T V and Q V, N = 32); P: partial workspace of at least splits * M * N
+// doubles.
 template <bool TA, bool TB>
 static void gemm_splitk(int M, int N, int K, double alpha, const double *A, int64_t lda,
                         const double *B, int64_t ldb, double beta, double *C, int64_t ldc,
                         double *P, int max_splits, cudaStream_t st) {
     if (M <= 0 || N <= 0) return;
-    const int tiles = ((M + kGM - 1) / kGM) * ((N + kGN - 1) / kGN);
+    constexpr int GN = 32, GM = HsTile<GN, 8>::GM;
+    const int tiles = ((M + GM - 1) / GM) * ((N + GN - 1) / GN);
     int splits = std::max(1, std::min(max_splits, 296 / std::max(tiles, 1)));
     const int kc = ((K + splits - 1) / splits + kGK - 1) / kGK * kGK;
     splits = std::max(1, (K + kc - 1) / std::max(kc, 1));
-    const int smem = (int)sizeof(HsGemmSmem);
-    cudaFuncSetAttribute(k_hs_gemm_part<TA, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    dim3 grid((unsigned)((M + kGM - 1) / kGM), (unsigned)((N + kGN - 1) / kGN), (unsigned)splits);
-    k_hs_gemm_part<TA, TB><<<grid, 256, smem, st>>>(M, N, K, kc, A, lda, B, ldb, P);
+    const int smem = (int)sizeof(HsGemmSmem<GN, 8>);
+    cudaFuncSetAttribute(k_hs_gemm_part<GN, TA, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         smem);
+    dim3 grid((unsigned)((M + GM - 1) / GM), (unsigned)((N + GN - 1) / GN), (unsigned)splits);
+    k_hs_gemm_part<GN, TA, TB><<<grid, 256, smem, st>>>(M, N, K, kc, A, lda, B, ldb, P);
     const int64_t tot = (int64_t)M * N;
     k_hs_sum<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(M, N, splits, P, alpha, beta, C, ldc);
+}
+
+template <int GN, int RM>
+static void gemm_n(bool ta, bool tb, int M, int N, int K, double alpha, const double *A,
+                   int64_t lda, const double *B, int64_t ldb, double beta, double *C, int64_t ldc,
+                   cudaStream_t st) {
+    if (ta && tb) gemm_t<GN, RM, true, true>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st);
+    else if (ta) gemm_t<GN, RM, true, false>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st);
+    else if (tb) gemm_t<GN, RM, false, true>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st);
+    else gemm_t<GN, RM, false, false>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st);
 }
 
 static void gemm(bool ta, bool tb, int M, int N, int K, double alpha, const double *A,
                  int64_t lda, const double *B, int64_t ldb, double beta, double *C, int64_t ldc,
                  cudaStream_t st) {
     if (M <= 0 || N <= 0) return;
-    dim3 grid((unsigned)((M + kGM - 1) / kGM), (unsigned)((N + kGN - 1) / kGN));
-    if (ta && tb) gemm_t<true, true>(grid, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st);
-    else if (ta) gemm_t<true, false>(grid, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st);
-    else if (tb) gemm_t<false, true>(grid, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st);
-    else gemm_t<false, false>(grid, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st);
+    if (N <= 32 && K <= 2 * kHb) gemm_n<32, 1>(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st);
+    else if (N <= 32) gemm_n<32, 8>(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st);
+    else gemm_n<64, 8>(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st);
 }
 
 __global__ void k_hs_eye(int64_t n, double *Q, int64_t ldq) {

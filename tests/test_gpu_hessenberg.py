@@ -114,3 +114,30 @@ def test_hessenberg_panel_paths_agree():
         assert np.abs(H - Ho).max() <= _bound(n) * nrm, (coop, np.abs(H - Ho).max())
         assert np.abs(Q - Qo).max() <= _bound(n), coop
     assert np.abs(out[False][0] - out[True][0]).max() <= _bound(n) * nrm
+
+
+@pytest.mark.parametrize("e2", [-900, 900])
+def test_hessenberg_extreme_scales(e2):
+    # entries near 2^900 and 2^-900: every column norm takes the scaled
+    # branch (the plain sum of squares would overflow or lose digits);
+    # scaling by a power of two commutes with the reduction
+    n = 200
+    A = np.random.default_rng(77).standard_normal((n, n))
+    H, Q = _gpu(np.ldexp(A, e2))
+    H = np.ldexp(H, -e2)
+    Ho, Qo, _ = oracle.hessenberg(A)
+    nrm = np.abs(A).max()
+    assert np.all(np.tril(H, -2) == 0.0)
+    assert np.abs(H - Ho).max() <= _bound(n) * nrm, np.abs(H - Ho).max()
+    assert np.abs(Q - Qo).max() <= _bound(n)
+    assert np.abs(Q @ H @ Q.T - A).max() <= _bound(n) * nrm
+
+
+def test_hessenberg_of_hessenberg_input_is_exact():
+    # every column is already zero below the subdiagonal: every reflector
+    # is the identity (tau = 0), so H = A and Q = I exactly
+    n = 150
+    A = np.triu(np.random.default_rng(12).standard_normal((n, n)), -1)
+    H, Q = _gpu(A)
+    np.testing.assert_array_equal(H, A)
+    np.testing.assert_array_equal(Q, np.eye(n))
