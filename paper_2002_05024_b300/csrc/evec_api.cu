@@ -59,7 +59,8 @@ void hess_init_q(int64_t n, double *Q, int64_t ldq, cudaStream_t st);
 int hess_panel(int64_t n, double *A, int64_t lda, int64_t k, int b, double *ws, int *err,
                int nsm, bool cooperative, cudaStream_t st);
 int hess_update(int64_t n, double *A, int64_t lda, double *Q, int64_t ldq, int64_t k, int b,
-                double *ws, cudaStream_t st);
+                double *ws, cudaStream_t st, cudaStream_t qst, cudaEvent_t fork,
+                cudaEvent_t join);
 void launch_gate(const Plan &p, const double *Y, int64_t ldy, const int32_t *ey, const double *R,
                  int64_t ldr, const double *T, int64_t ldt, double limit, void *buf,
                  double *ratio, cudaStream_t st);
@@ -2184,6 +2185,11 @@ extern "C" evec_status evec_hessenberg(evec_handle h, int64_t n, double *A, int6
             hess_init_q(n, Q, ldq, st);
             return 1;
         });
+        // the Q chain of each update runs on a second stream
+        if (!h->la_stream)
+            EVEC_CUDA(cudaStreamCreateWithFlags(&h->la_stream, cudaStreamNonBlocking));
+        if (!h->ev_slice) EVEC_CUDA(cudaEventCreateWithFlags(&h->ev_slice, cudaEventDisableTiming));
+        if (!h->ev_tail) EVEC_CUDA(cudaEventCreateWithFlags(&h->ev_tail, cudaEventDisableTiming));
     }
     const int nbw = hess_panel_width();
     for (int64_t k = 0; k + 2 < n; k += nbw) {
@@ -2193,7 +2199,10 @@ extern "C" evec_status evec_hessenberg(evec_handle h, int64_t n, double *A, int6
                               h->hess_coop, st);
         });
         timed(h, EVEC_K_HESS_UPDATE,
-              [&] { return hess_update(n, A, lda, Q, ldq, k, b, h->hs_ws, st); });
+              [&] {
+                  return hess_update(n, A, lda, Q, ldq, k, b, h->hs_ws, st, h->la_stream,
+                                     h->ev_slice, h->ev_tail);
+              });
     }
     EVEC_CUDA(cudaGetLastError());
     if (opt && opt->check) return evec_sync(h, nullptr);

@@ -747,15 +747,16 @@ static void gemm_t(int M, int N, int K, double alpha, const double *A, int64_t l
 
 // C = alpha op(A) op(B) + beta C with the K range split over gridDim.z
 // when the M x N tiles alone would leave most SMs idle (the skinny products
-// A^T V and Q V, N = 32); P: partial workspace of at least splits * M * N
-// doubles.
+// A^T V and Q V, N = 32): as many slices as fill both CTA slots of every
+// SM (2 x 148), within the partial workspace P of p_cap doubles.
 template <bool TA, bool TB>
 static void gemm_splitk(int M, int N, int K, double alpha, const double *A, int64_t lda,
                         const double *B, int64_t ldb, double beta, double *C, int64_t ldc,
-                        double *P, int max_splits, cudaStream_t st) {
+                        double *P, int64_t p_cap, cudaStream_t st) {
     if (M <= 0 || N <= 0) return;
     constexpr int GN = 32, GM = HsTile<GN, 8>::GM;
     const int tiles = ((M + GM - 1) / GM) * ((N + GN - 1) / GN);
+    const int max_splits = (int)std::min<int64_t>(1024, p_cap / ((int64_t)M * N));
     int splits = std::max(1, std::min(max_splits, 296 / std::max(tiles, 1)));
     const int kc = ((K + splits - 1) / splits + kGK - 1) / kGK * kGK;
     splits = std::max(1, (K + kc - 1) / std::max(kc, 1));
@@ -800,18 +801,19 @@ static int hess_parts(int64_t n) {
 }
 
 constexpr int kHMaxCoop = 1024;   // partials rows reserved for the cooperative panel
-constexpr int kHSplits = 16;      // at most this many K slices in the skinny products
+constexpr int kHSplits = 20;      // partial slices of n x kHb in each split-K workspace
 
-// workspace doubles for order n: V, Y, VT, W (n x kHb each), Z (kHb x n), T
-// (kHb x kHb), x (n), w and s (kHb each), the per-CTA partials, scalars
+// workspace doubles for order n: V, Y, VT, W, VTq (n x kHb each), Z (kHb x
+// n), T (kHb x kHb), x (n), w and s (kHb each), the per-CTA partials,
+// scalars, and the split-K partials of the A and the Q products
 size_t hessenberg_workspace(int64_t n) {
-    return (size_t)(5 * n * kHb + kHb * kHb + n + 2 * kHb +
+    return (size_t)(6 * n * kHb + kHb * kHb + n + 2 * kHb +
                     2 * (int64_t)std::max(hess_parts(n), kHMaxCoop) * kHPartStride + 8 + 2 +
-                    (int64_t)kHSplits * n * kHb);
+                    2 * (int64_t)kHSplits * n * kHb);
 }
 
 struct HessWs {
-    double *V, *Y, *VT, *W, *Z, *T, *x, *wv, *sv, *part, *part2, *P;
+    double *V, *Y, *VT, *W, *VTq, *Z, *T, *x, *wv, *sv, *part, *part2, *P, *Pq;
     HessScal *scal;
     GridBar *bar;
 };
@@ -822,7 +824,8 @@ static HessWs hess_ws(int64_t n, double *ws) {
     w.Y = w.V + n * kHb;
     w.VT = w.Y + n * kHb;
     w.W = w.VT + n * kHb;
-    w.Z = w.W + n * kHb;
+    w.VTq = w.W + n * kHb;
+    w.Z = w.VTq + n * kHb;
     w.T = w.Z + kHb * n;
     w.x = w.T + kHb * kHb;
     w.wv = w.x + n;
@@ -832,6 +835,7 @@ static HessWs hess_ws(int64_t n, double *ws) {
     w.scal = (HessScal *)(w.part2 + (int64_t)std::max(hess_parts(n), kHMaxCoop) * kHPartStride);
     w.bar = (GridBar *)(w.scal + 2);
     w.P = (double *)(w.scal) + 10;
+    w.Pq = w.P + (int64_t)kHSplits * n * kHb;
     return w;
 }
 
@@ -886,34 +890,48 @@ int hess_panel(int64_t n, double *A, int64_t lda, int64_t k, int b, double *ws, 
 }
 
 // Steps 2 and 3 for the panel at k (b columns), and Q <- Q (I - V T V^T):
-// returns the kernels launched.
+// returns the kernels launched.  With a second stream qst (and two events)
+// the Q chain runs there beside the A chain -- they share only V and T,
+// which the panel wrote before the fork -- so that each fills the other's
+// last partial wave; st waits for it before returning.
 int hess_update(int64_t n, double *A, int64_t lda, double *Q, int64_t ldq, int64_t k, int b,
-                double *ws, cudaStream_t st) {
+                double *ws, cudaStream_t st, cudaStream_t qst, cudaEvent_t fork,
+                cudaEvent_t join) {
     const HessWs w = hess_ws(n, ws);
+    const int64_t p_cap = (int64_t)kHSplits * n * kHb;
     int ng = 0;
     const int64_t j0 = k + b;            // first trailing column
     const int nt = (int)(n - j0);
     const int rows = (int)(n - k - 1);   // rows k+1 .. n-1 (V is zero above)
+    const bool side = Q && qst && fork && join;
+    if (Q) {   // Q[:, k+1:n] -= (Q[:, k+1:n] V[k+1:n, :]) T V[k+1:n, :]^T
+        cudaStream_t s = st;
+        if (side) {
+            cudaEventRecord(fork, st);
+            cudaStreamWaitEvent(qst, fork, 0);
+            s = qst;
+        }
+        gemm_splitk<false, false>((int)n, b, rows, 1.0, Q + (k + 1) * ldq, ldq, w.V + (k + 1), n,
+                                  0.0, w.W, n, w.Pq, p_cap, s);
+        gemm(false, false, (int)n, b, b, 1.0, w.W, n, w.T, kHb, 0.0, w.VTq, n, s);
+        gemm(false, true, (int)n, rows, b, -1.0, w.VTq, n, w.V + (k + 1), n, 1.0,
+             Q + (k + 1) * ldq, ldq, s);
+        if (side) cudaEventRecord(join, qst);
+        ng += 3;
+    }
     if (nt > 0) {
         // A[:, j0:n] -= Y V[j0:n, :]^T (every row: the top part and the rest)
         gemm(false, true, (int)n, nt, b, -1.0, w.Y, n, w.V + j0, n, 1.0, A + j0 * lda, lda, st);
         // rows k+1 ..: A <- A - (V T^T) (V^T A), with Zt = A^T V (nt x b,
-        // the long dimension on the tile's 128 rows)
+        // the long dimension on the tile's rows)
         gemm_splitk<true, false>(nt, b, rows, 1.0, A + (k + 1) + j0 * lda, lda, w.V + (k + 1), n,
-                                 0.0, w.Z, n, w.P, kHSplits, st);
+                                 0.0, w.Z, n, w.P, p_cap, st);
         gemm(false, true, rows, b, b, 1.0, w.V + (k + 1), n, w.T, kHb, 0.0, w.VT, n, st);
         gemm(false, true, rows, nt, b, -1.0, w.VT, n, w.Z, n, 1.0, A + (k + 1) + j0 * lda, lda,
              st);
         ng += 4;
     }
-    if (Q) {   // Q[:, k+1:n] -= (Q[:, k+1:n] V[k+1:n, :]) T V[k+1:n, :]^T
-        gemm_splitk<false, false>((int)n, b, rows, 1.0, Q + (k + 1) * ldq, ldq, w.V + (k + 1), n,
-                                  0.0, w.W, n, w.P, kHSplits, st);
-        gemm(false, false, (int)n, b, b, 1.0, w.W, n, w.T, kHb, 0.0, w.VT, n, st);
-        gemm(false, true, (int)n, rows, b, -1.0, w.VT, n, w.V + (k + 1), n, 1.0,
-             Q + (k + 1) * ldq, ldq, st);
-        ng += 3;
-    }
+    if (side) cudaStreamWaitEvent(st, join, 0);
     return ng;
 }
 
