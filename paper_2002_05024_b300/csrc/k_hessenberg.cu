@@ -312,20 +312,25 @@ struct ColScal {
 // where unused), written to out[0 .. kHb): a reduce-scatter butterfly in
 // each warp (31 shuffles and 31 FP64 additions per lane instead of 5 per
 // value; lane j ends with the warp's sum of value j), then the warps' sums
-// in shared memory.  red: 8 x kHb doubles.
-__device__ __forceinline__ void block_sums_rs(double (&v)[kHb], double *red, double *out) {
+// in shared memory.  A warp that held no rows (active false) skips the
+// butterfly: it would share an FP64 pipe with a warp that did.  red: 8 x
+// kHb doubles.
+__device__ __forceinline__ void block_sums_rs(double (&v)[kHb], bool active, double *red,
+                                              double *out) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (active) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const bool hi = (lane & o) != 0;
+        for (int o = 16; o > 0; o >>= 1) {
+            const bool hi = (lane & o) != 0;
 #pragma unroll
-        for (int k = 0; k < o; k++) {
-            const double keep = hi ? v[o + k] : v[k];
-            const double send = hi ? v[k] : v[o + k];
-            v[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+            for (int k = 0; k < o; k++) {
+                const double keep = hi ? v[o + k] : v[k];
+                const double send = hi ? v[k] : v[o + k];
+                v[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+            }
         }
     }
-    red[warp * kHb + lane] = v[0];
+    red[warp * kHb + lane] = active ? v[0] : 0.0;
     __syncthreads();
     if (threadIdx.x < kHb) {
         double t = 0.0;
@@ -389,6 +394,7 @@ __global__ void __launch_bounds__(kHRowThreads)
     const int64_t rpc = ((n + gridDim.x - 1) / gridDim.x + 31) / 32 * 32;
     const int64_t rbeg = (int64_t)blockIdx.x * rpc, rend = min(rbeg + rpc, n);
     const int nparts = (int)min((int64_t)gridDim.x, (n + rpc - 1) / rpc);
+    const bool warp_rows = rbeg + 32 * warp < rend;   // this warp holds rows
     // T and the subdiagonal entry are written by the last CTA, which owns
     // no rows whenever the grid outnumbers the row blocks: its serial
     // chain then runs while the row owners form v
@@ -415,7 +421,7 @@ __global__ void __launch_bounds__(kHRowThreads)
                     if (j < i) acc[j] = fma(V[r + (int64_t)j * n], xr, acc[j]);
             }
             if ((int64_t)blockIdx.x < nparts)
-                block_sums_rs(acc, red, part + (int64_t)blockIdx.x * kHPartStride);
+                block_sums_rs(acc, warp_rows, red, part + (int64_t)blockIdx.x * kHPartStride);
         }
         if (!grid_barrier(bar, err)) return;
         // 2. w = T^T (sum of partials), in every CTA
@@ -456,7 +462,7 @@ __global__ void __launch_bounds__(kHRowThreads)
             if (lane == 0) rmh[warp] = mh;
             if ((int64_t)blockIdx.x < nparts) {
                 // (its barriers make rmh visible)
-                block_sums_rs(acc, red, part2 + (int64_t)blockIdx.x * kHPartStride);
+                block_sums_rs(acc, warp_rows, red, part2 + (int64_t)blockIdx.x * kHPartStride);
                 if (tid == 0) {
                     unsigned m = 0;
                     for (int w8 = 0; w8 < kHRowThreads / 32; w8++) m = max(m, rmh[w8]);
@@ -542,14 +548,17 @@ __global__ void __launch_bounds__(kHRowThreads)
             if (r > c + 1) A[r + c * lda] = 0.0;
         }
         if (!grid_barrier(bar, err)) return;
-        // 6. Y[:, i] = tau (A[:, c+1:n] v - Y s): 32-row chunks, the CTA's 8
-        //    warps split the columns
+        // 6. Y[:, i] = tau (A[:, c+1:n] v - Y s) for the CTA's own rows, in
+        //    32-row chunks; the CTA's 8 warps split the columns.  No grid
+        //    barrier follows: until the next column's first barrier a CTA
+        //    touches only its own rows of A, x, Y and V (and reads V's row
+        //    c + 1, final since the last barrier), while the product of a
+        //    slower CTA reads only that CTA's rows and column i of V.
         {
             const double *v = V + (int64_t)i * n;
-            const int64_t nchunks = (n + 31) / 32;
-            for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
-                const int64_t r = ch * 32 + lane;
-                const bool rv = r < n;
+            for (int64_t r0 = rbeg; r0 < rend; r0 += 32) {
+                const int64_t r = r0 + lane;
+                const bool rv = r < rend;
                 // warp w takes columns c+1+w, +8, ...: sixteen loads in
                 // flight per lane (independent accumulators; 32 measured
                 // the same, and a double-buffered batch was slower)
@@ -585,7 +594,6 @@ __global__ void __launch_bounds__(kHRowThreads)
                 __syncthreads();
             }
         }
-        if (!grid_barrier(bar, err)) return;
     }
 }
 

@@ -141,3 +141,16 @@ def test_hessenberg_of_hessenberg_input_is_exact():
     H, Q = _gpu(A)
     np.testing.assert_array_equal(H, A)
     np.testing.assert_array_equal(Q, np.eye(n))
+
+
+def test_hessenberg_several_chunks_per_cta():
+    # n = 5000: more rows than 32 per CTA of the cooperative panel, so each
+    # CTA's product runs over several 32-row chunks; invariants with the
+    # host BLAS
+    n = 5000
+    A = np.random.default_rng(5000).standard_normal((n, n))
+    H, Q = _gpu(A)
+    assert np.all(np.tril(H, -2) == 0.0)
+    assert np.abs(Q.T @ Q - np.eye(n)).max() <= 8 * n * U
+    R = Q @ H @ Q.T - A
+    assert np.abs(R).max() <= _bound(n) * np.abs(A).max(), np.abs(R).max()
