@@ -78,6 +78,8 @@ class Oracle:
         lib.evo_trsolve.restype = ctypes.c_int
         lib.evo_hessenberg.argtypes = [i64, p, i64, p, i64, p, p]
         lib.evo_hessenberg.restype = ctypes.c_int
+        lib.evo_window_update.argtypes = [i64, p, i64, p, i64, ctypes.c_int, p, p, p, p]
+        lib.evo_window_update.restype = ctypes.c_int
         lib.evo_naive_standard.argtypes = [i64, p, i64, p, p, i64]
         lib.evo_naive_standard.restype = i64
         self.lib = lib
@@ -169,6 +171,27 @@ class Oracle:
             raise OracleError(st, int(bad[0]))
         return H, Q, tau[:n]
 
+    def window_update(self, T, Q, windows):
+        """Eigenvalue reordering's off-diagonal updates: for each (a, Z) in
+        windows, in order, T <- Zhat^T T Zhat and Q <- Q Zhat with Zhat the
+        identity carrying the k x k orthogonal Z on rows and columns
+        [a, a + k).  Returns updated copies (T, Q or None)."""
+        T = np.array(_fortran(T), order="F", copy=True)
+        n = T.shape[0]
+        Q = None if Q is None else np.array(_fortran(Q), order="F", copy=True)
+        begin = np.array([int(a) for a, _ in windows], dtype=np.int64)
+        size = np.array([np.asarray(Z).shape[0] for _, Z in windows], dtype=np.int32)
+        zoff = np.zeros(len(windows), dtype=np.int64)
+        if len(windows):
+            zoff[1:] = np.cumsum(size.astype(np.int64) ** 2)[:-1]
+        Zp = np.concatenate([np.asarray(Z, dtype=np.float64).ravel(order="F") for _, Z in windows]
+                            + [np.zeros(1)])
+        st = self.lib.evo_window_update(n, _ptr(T), max(n, 1), _ptr(Q), max(n, 1), len(windows),
+                                        _ptr(begin), _ptr(size), _ptr(Zp), _ptr(zoff))
+        if st:
+            raise OracleError(st, -1)
+        return T, Q
+
     def naive_standard(self, S, select=None):
         """Unscaled textbook substitution (overflow witness).  Returns
         (X, number of columns containing Inf or NaN)."""
@@ -237,3 +260,7 @@ def trsolve(S, B, threads: int = 0):
 
 def hessenberg(A, calc_q: bool = True):
     return default().hessenberg(A, calc_q)
+
+
+def window_update(T, Q, windows):
+    return default().window_update(T, Q, windows)

@@ -16,6 +16,10 @@
  *   - the Hessenberg reduction A = Q H Q^T that precedes the Schur form
  *     (Sec. 3.1), by one Householder reflector per column applied from
  *     both sides, unblocked
+ *   - the off-diagonal updates of eigenvalue reordering (Sec. 3, the
+ *     window, left-update and right-update tasks): each window's
+ *     accumulated orthogonal transform Z applied as T <- Zhat^T T Zhat,
+ *     Q <- Q Zhat (Zhat = I with Z on the window), window by window
  *   - the robust triangular solve with many right-hand sides that the
  *     eigenvector solve generalises (Sec. 3.4, the LAPACK xLATRS lineage):
  *     T x_j = b_j for every column of B, each x_j = X[:, j] / 2^scale_exp[j]
@@ -1156,3 +1160,62 @@ int evo_hessenberg(int64_t n, double *A, int64_t lda, double *Q, int64_t ldq, do
     return EVO_OK;
 }
 
+
+/*
+ * Eigenvalue reordering's off-diagonal updates (Sec. 3: a window task
+ * gathers its local transformations in an accumulator matrix; the left and
+ * right update tasks then apply it to the off-diagonal sections).  Windows
+ * are applied in the order given; window w covers rows and columns
+ * [a, a + k) with a = begin[w], k = size[w], and its accumulator Z is the
+ * k x k column-major matrix at Z + zoff[w].  With Zhat = diag(I_a, Z, I):
+ *   T <- Zhat^T T Zhat, touching only rows [a, a + k) from column a on (the
+ *   rows' entries left of the window are the zeros below the diagonal) and
+ *   columns [a, a + k) down to row a + k - 1 (the rows below are zero);
+ *   Q <- Q Zhat (all n rows of the window's columns).
+ * Plain definition: each updated entry is one dot product of length k.
+ */
+int evo_window_update(int64_t n, double *T, int64_t ldt, double *Q, int64_t ldq, int nwin,
+                      const int64_t *begin, const int32_t *size, const double *Z,
+                      const int64_t *zoff) {
+    if (n < 0 || ldt < (n > 0 ? n : 1) || (Q && ldq < (n > 0 ? n : 1)) || nwin < 0)
+        return EVO_EINVAL;
+    for (int w = 0; w < nwin; w++)
+        if (begin[w] < 0 || size[w] < 0 || begin[w] + size[w] > n || zoff[w] < 0)
+            return EVO_EINVAL;
+    double *t = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    if (!t) return EVO_ENOMEM;
+    for (int w = 0; w < nwin; w++) {
+        const int64_t a = begin[w], k = size[w], b = a + k;
+        const double *Zw = Z + zoff[w];
+        /* left: T[a:b, j] <- Z^T T[a:b, j] for j = a .. n-1 */
+        for (int64_t j = a; j < n; j++) {
+            for (int64_t i = 0; i < k; i++) {
+                double s = 0.0;
+                for (int64_t l = 0; l < k; l++) s += AT(Zw, k, l, i) * AT(T, ldt, a + l, j);
+                t[i] = s;
+            }
+            for (int64_t i = 0; i < k; i++) AT(T, ldt, a + i, j) = t[i];
+        }
+        /* right: T[r, a:b] <- T[r, a:b] Z for r = 0 .. b-1 */
+        for (int64_t r = 0; r < b; r++) {
+            for (int64_t i = 0; i < k; i++) {
+                double s = 0.0;
+                for (int64_t l = 0; l < k; l++) s += AT(T, ldt, r, a + l) * AT(Zw, k, l, i);
+                t[i] = s;
+            }
+            for (int64_t i = 0; i < k; i++) AT(T, ldt, r, a + i) = t[i];
+        }
+        /* Q[r, a:b] <- Q[r, a:b] Z for every row */
+        if (Q)
+            for (int64_t r = 0; r < n; r++) {
+                for (int64_t i = 0; i < k; i++) {
+                    double s = 0.0;
+                    for (int64_t l = 0; l < k; l++) s += AT(Q, ldq, r, a + l) * AT(Zw, k, l, i);
+                    t[i] = s;
+                }
+                for (int64_t i = 0; i < k; i++) AT(Q, ldq, r, a + i) = t[i];
+            }
+    }
+    free(t);
+    return EVO_OK;
+}

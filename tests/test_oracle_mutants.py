@@ -59,6 +59,13 @@ MUTANTS = [
     ("hessenberg_beta_sign", "if (alpha >= 0.0) beta = -beta;", "if (alpha < 0.0) beta = -beta;"),
     ("hessenberg_tau", "const double t = (beta - alpha) / beta;",
      "const double t = (beta - alpha) / alpha;"),
+    ("window_left_not_transposed",
+     "for (int64_t l = 0; l < k; l++) s += AT(Zw, k, l, i) * AT(T, ldt, a + l, j);",
+     "for (int64_t l = 0; l < k; l++) s += AT(Zw, k, i, l) * AT(T, ldt, a + l, j);"),
+    ("window_left_skips_block", "for (int64_t j = a; j < n; j++) {", "for (int64_t j = b; j < n; j++) {"),
+    ("window_right_rows_short", "for (int64_t r = 0; r < b; r++) {", "for (int64_t r = 0; r < a; r++) {"),
+    ("window_q_dropped", "        if (Q)\n            for (int64_t r = 0; r < n; r++) {\n                for (int64_t i = 0; i < k; i++) {",
+     "        if (0)\n            for (int64_t r = 0; r < n; r++) {\n                for (int64_t i = 0; i < k; i++) {"),
     ("hessenberg_left_columns", "for (int64_t c = j + 1; c < n; c++) {\n            double s = 0.0;\n            for (int64_t i = j + 1",
      "for (int64_t c = j + 2; c < n; c++) {\n            double s = 0.0;\n            for (int64_t i = j + 1"),
 ]
@@ -178,6 +185,27 @@ def detector_failures(orc):
         return (np.abs(H - Hs).max() <= 1e-11 and np.abs(Q @ H @ Q.T - A).max() <= 1e-11 and
                 np.all(np.tril(H, -2) == 0.0))
 
+    def window():
+        # an orthogonal similarity keeps Q T Q^T; a cyclic permutation
+        # window permutes by index arithmetic alone
+        n = 48
+        T, blocks = workloads.config0_schur(n, seed=21)
+        Q = workloads.householder_orthogonal(n, seed=22)
+        A = Q @ T @ Q.T
+        T2, Q2 = orc.window_update(T, Q, workloads.window_chain(n, 16, 16, seed=23,
+                                                                blocks=blocks))
+        ok = np.abs(Q2 @ T2 @ Q2.T - A).max() <= 1e-12 * np.abs(A).max()
+        a, k = 6, 5
+        P = np.zeros((k, k))
+        P[np.roll(np.arange(k), 1), np.arange(k)] = 1.0
+        T3, _ = orc.window_update(T, None, [(a, P)])
+        idx = np.arange(n)
+        idx[a:a + k] = a + np.roll(np.arange(k), 1)
+        Te = T.copy()
+        Te[a:a + k, a:] = T[idx[a:a + k], a:]
+        Te[:a + k, a:a + k] = Te[:a + k, idx[a:a + k]].copy()
+        return ok and np.array_equal(T3, Te)
+
     check("golden", golden)
     check("residual_std", residual_std)
     check("residual_backtransformed", residual_backtransformed)
@@ -188,6 +216,7 @@ def detector_failures(orc):
     check("left_adversarial", left_adversarial)
     check("left_brute_force", left_brute_force)
     check("hessenberg", hessenberg)
+    check("window", window)
     return fails
 
 

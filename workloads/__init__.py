@@ -2,7 +2,8 @@
 
 This package only draws random numbers and places them into matrices of the
 shapes the method consumes (real Schur forms, generalized Schur pairs,
-orthogonal factors, selection masks, batches of uneven sizes).  It holds none
+orthogonal factors, selection masks, batches of uneven sizes, chains of
+reordering windows with random orthogonal accumulators).  It holds none
 of the method's arithmetic, and both the CUDA path and the CPU oracle read
 their inputs from here.
 """
@@ -18,4 +19,5 @@ from .schur_inputs import (  # noqa: F401
     householder_orthogonal,
     random_eigen_selection,
     solve_system,
+    window_chain,
 )

@@ -240,3 +240,40 @@ def batch_pencils(count: int, seed: int = SEED_BASE + 5, fraction: float = 0.3):
         pairs.append((S, T))
         sels.append(block_selection(int(n), blocks, fraction, seed=s + 7))
     return sizes, pairs, sels
+
+
+def window_chain(n: int, k: int, stride: int, seed: int = SEED_BASE + 9, blocks=None):
+    """A chain of overlapping diagonal windows as eigenvalue reordering moves
+    a group of eigenvalues towards the top: windows of k rows and columns
+    starting at n - k, n - k - stride, ... and a top one from row 0 that
+    keeps the same overlap (stride = k: disjoint windows tiling the diagonal),
+    each with a random k x k orthogonal accumulator (QR of a Gaussian
+    matrix, columns signed so that R has a positive diagonal).  With the
+    Schur form's blocks [(p, size), ...] no window boundary falls inside a
+    2x2 block (a boundary there moves up by one row).  Returns a list of
+    (begin, Z) with Z column-major float64."""
+    rng = _rng(seed)
+    wins = []                      # (begin, size): the top one clipped at 0
+    a = n - k
+    while a > 0:
+        wins.append((a, k))
+        a -= stride
+    end = wins[-1][0] + k - stride if wins else n
+    if end > 0:
+        wins.append((0, min(end, n)))
+    if blocks is not None:
+        inner = {p + 1 for p, sz in blocks if sz == 2}
+        fixed = []
+        for a, kk in wins:
+            b = a + kk
+            a = a - 1 if a in inner else a
+            b = b - 1 if b in inner else b
+            if b > a:
+                fixed.append((a, b - a))
+        wins = fixed
+    out = []
+    for a, kk in wins:
+        Z, R = np.linalg.qr(rng.standard_normal((kk, kk)))
+        Z = Z * np.sign(np.where(np.diag(R) == 0.0, 1.0, np.diag(R)))
+        out.append((int(a), np.asfortranarray(Z)))
+    return out
