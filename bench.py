@@ -64,7 +64,7 @@ def parse_args():
                     help="columns of the CPU-oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=["single", "batched", "generalized", "trsolve",
-                                           "batched_generalized", "hessenberg"],
+                                           "batched_generalized", "hessenberg", "window"],
                     default="single",
                     help="single: one n x n Schur form with Q (default); batched: the "
                          "2000-matrix batch of evec_batched; generalized: an n x n pencil "
@@ -72,6 +72,8 @@ def parse_args():
                          "quasi-triangular T with --nrhs right-hand sides; "
                          "batched_generalized: --batch pencils in one persistent launch")
     ap.add_argument("--nrhs", type=int, default=0, help="trsolve: right-hand sides (default n)")
+    ap.add_argument("--window", type=int, default=128,
+                    help="window: rows and columns of each reordering window")
     ap.add_argument("--lookahead", action="store_true",
                     help="split mode: the look-ahead schedule (evec_set_lookahead)")
     ap.add_argument("--side", choices=["right", "left"], default="right",
@@ -129,6 +131,7 @@ KERNEL_SOURCES = {
     ("left", "fp64"): ["k_left.cu"],
     ("hess_panel", "fp64"): ["k_hessenberg.cu"],
     ("hess_update", "fp64"): ["k_hessenberg.cu"],
+    ("window", "fp64"): ["k_window.cu"],
 }
 TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
 
@@ -463,6 +466,25 @@ def run_reference_other(args):
         metric = "eigvec columns/s, generalized (robust FP64 eigenvectors of a pencil incl. X = Z Y)"
         what = f"pencil (S, T) n={n} with Z, all columns"
         sample = f"{per} random eigenvalues per step of the n={n} pencil, on the host cores"
+    elif args.workload == "window":
+        n, k = args.n, args.window
+        T, blocks = workloads.config0_schur(n, seed=workloads.SEED_BASE)
+        Q = workloads.householder_orthogonal(n, seed=workloads.SEED_BASE + 100)
+        wins = workloads.window_chain(n, k, k, seed=workloads.SEED_BASE + 9, blocks=blocks)
+        per = 2
+        for i in range(args.warmup + args.steps):
+            pick = np.random.default_rng(5000 + i).choice(len(wins), size=per, replace=False)
+            t = time.perf_counter()
+            oracle.window_update(T, Q, [wins[int(j)] for j in sorted(pick)])
+            dt = time.perf_counter() - t
+            if i >= args.warmup:
+                units += per
+                secs += dt
+        unit = "windows/s"
+        metric = "reordering windows/s (off-diagonal updates with Q, FP64)"
+        what = window_what(n, k, len(wins))
+        sample = f"{per} random windows of the chain per step, plain loops on one core"
+        cores = 1
     else:   # hessenberg: one unblocked reduction at a reduced order per step
         n = args.n
         ns = min(n, 768)
@@ -490,7 +512,7 @@ def run_reference(args, rank, world):
         return
     if args.workload == "trsolve":
         return run_reference_trsolve(args)
-    if args.workload in ("batched", "batched_generalized", "generalized", "hessenberg"):
+    if args.workload in ("batched", "batched_generalized", "generalized", "hessenberg", "window"):
         return run_reference_other(args)
     T, blocks, Q = workload(args.n)
     per_step = max(16, args.cpu_sample // 4)
@@ -1234,6 +1256,167 @@ def run_hessenberg(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+def window_what(n, k, count):
+    return (f"eigenvalue reordering's off-diagonal updates: {count} disjoint windows of {k} "
+            f"tiling the diagonal of an n={n} config-0 Schur form (boundaries off 2x2 blocks), "
+            f"random orthogonal accumulators, with Q")
+
+
+def window_flops(n, wins):
+    """FP64 flops of the left and right updates and Q: 2 k^2 ((n - a) + (a + k) + n)
+    per window."""
+    return sum(2.0 * Z.shape[0] ** 2 * ((n - a) + (a + Z.shape[0]) + n) for a, Z in wins)
+
+
+def run_window(args, rank, world, local_rank):
+    """Eigenvalue reordering's off-diagonal updates (evec_window_update):
+    the windows of one pass over the diagonal, each applied to T (left and
+    right updates) and Q.  Metric: windows per second; roofline: the FP64
+    products against the FP64 pipe."""
+    import ctypes
+
+    import torch
+
+    import paper_2002_05024_b300 as ev
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    n, k = args.n, args.window
+    T, blocks = workloads.config0_schur(n, seed=workloads.SEED_BASE)
+    Q = workloads.householder_orthogonal(n, seed=workloads.SEED_BASE + 100)
+    wins = workloads.window_chain(n, k, k, seed=workloads.SEED_BASE + 9, blocks=blocks)
+    dT = torch.from_numpy(np.asfortranarray(T)).to(dev)
+    dQ = torch.from_numpy(np.asfortranarray(Q)).to(dev)
+    begin, size, zoff, Zp = ev.pack_windows(wins, dev)
+    h = ev.handle(local_rank)
+    opts = ev._opts(0, False, "fp64", 0)
+
+    def step():
+        # each pass is one more orthogonal similarity of the same matrices
+        st = ev.lib().evec_window_update(h.ptr, n, dT.data_ptr(), n, dQ.data_ptr(), n,
+                                         len(wins), ev._np_ptr(begin), ev._np_ptr(size),
+                                         Zp.data_ptr(), ev._np_ptr(zoff), ctypes.byref(opts))
+        if st:
+            raise ev.EvecError(st, "evec_window_update")
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    ev.sync(local_rank)
+    sampler = ClockSampler() if rank == 0 else None
+    if dist:
+        dist.barrier()
+    stream = torch.cuda.current_stream(dev)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        step()
+    t1.record(stream)
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    elapsed = t0.elapsed_time(t1)
+    clocks = sampler.stop() if sampler else None
+    prof = profiled_steps(h, step, args.steps, dev)
+    ev.sync(local_rank)
+    if dist:
+        tt = torch.tensor([elapsed], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        elapsed = float(tt.item())
+    e2e = None
+    if not os.environ.get("EVEC_BENCH_NO_E2E"):
+        # T and Q in from pinned memory, T and Q out, every step
+        hT = torch.empty((n, n), dtype=torch.float64, pin_memory=True).t()
+        hQ = torch.empty((n, n), dtype=torch.float64, pin_memory=True).t()
+        hT.copy_(torch.from_numpy(T))
+        hQ.copy_(torch.from_numpy(Q))
+        oT = torch.empty((n, n), dtype=torch.float64, pin_memory=True).t()
+        oQ = torch.empty((n, n), dtype=torch.float64, pin_memory=True).t()
+        w0 = time.perf_counter()
+        for _ in range(args.steps):
+            dT.copy_(hT, non_blocking=True)
+            dQ.copy_(hQ, non_blocking=True)
+            step()
+            oT.copy_(dT, non_blocking=True)
+            oQ.copy_(dQ, non_blocking=True)
+            torch.cuda.synchronize(dev)
+        e2e = {"value": world * len(wins) * args.steps / (time.perf_counter() - w0),
+               "unit": "windows/s", "h2d_bytes_per_step": 16 * n * n,
+               "d2h_bytes_per_step": 16 * n * n}
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    # quality: one pass from the original matrices keeps Q T Q^T (disjoint
+    # windows: a similarity) and matches the oracle on three windows
+    dT.copy_(torch.from_numpy(np.asfortranarray(T)))
+    dQ.copy_(torch.from_numpy(np.asfortranarray(Q)))
+    step()
+    Tg, Qg = dT.cpu().numpy(), dQ.cpu().numpy()
+    A = Q @ T @ Q.T
+    quality = {"max_similarity_error_over_nu_maxA":
+               float(np.abs(Qg @ Tg @ Qg.T - A).max() / (n * 2.0 ** -53 * np.abs(A).max())),
+               "max_orthogonality_error_over_nu":
+               float(np.abs(Qg.T @ Qg - np.eye(n)).max() / (n * 2.0 ** -53))}
+    F = window_flops(n, wins)
+    peaks = measured_peaks()
+    fp64_peak = N_SMS * FP64_FLOP_PER_CLK_PER_SM * float(peaks.get("sm_max_mhz", 2032.0)) / 1e6
+    roof = None
+    wm, wn = prof.get("window", (0.0, 0))
+    if wm > 0:
+        ach = F / (wm / args.steps / 1e3) / 1e12
+        roof = {"kernel": "left and right updates (k_win_left, k_win_right)", "bound": "alu",
+                "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach / fp64_peak,
+                "traffic": stored_traffic("window", "fp64", n, k, "window:"),
+                "peak_source": "of derived FP64 peak (measured 4 flop/clk/SM x 148 SMs x max "
+                               "SM clock)",
+                "launches_per_step": wn / args.steps, "alg_flops_per_step": F,
+                "ms_per_step": wm / args.steps}
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        pick = [wins[0], wins[len(wins) // 2]]
+        t = time.perf_counter()
+        To, Qo = oracle.window_update(T, Q, pick)
+        dt = time.perf_counter() - t
+        dT.copy_(torch.from_numpy(np.asfortranarray(T)))
+        dQ.copy_(torch.from_numpy(np.asfortranarray(Q)))
+        ev.window_update(dT, dQ, pick, check=True)
+        quality["gpu_vs_oracle_two_windows"] = float(
+            max(np.abs(dT.cpu().numpy() - To).max(), np.abs(dQ.cpu().numpy() - Qo).max()))
+        cpu = {"value": len(pick) / dt, "unit": "windows/s", "cores": 1, "kind": "oracle",
+               "sample": f"{len(pick)} windows of the pass (the first and the middle one), "
+                         f"plain loops on one core, {dt:.2f} s"}
+    line = {
+        "metric": "reordering windows/s (off-diagonal updates with Q, FP64)",
+        "value": world * len(wins) * args.steps / (elapsed / 1e3), "unit": "windows/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": elapsed / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": window_what(n, k, len(wins)), "n": n, "window": k,
+                   "windows_per_step": len(wins), "parallelism": "replicas",
+                   "l2": f"inputs larger than L2 (T and Q {8 * n * n >> 20} MiB each)"},
+        "tflops_fp64": F * args.steps / (elapsed / 1e3) / 1e12,
+        "flops_per_step": F,
+        "quality": quality,
+        "roofline": roof,
+        "kernel_ms_per_step": {kk: v[0] / args.steps for kk, v in prof.items()},
+        "gpu_launches": sum(c for _, c in prof.values()),
+        "clocks": clocks,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
 def run_generalized(args, rank, world, local_rank):
     """The pencil workload: S config-0 (n x n), T upper triangular with
     diagonal U[0.5, 2] (every 50th entry 1e-12) and N(0, 1) upper part, Z from
@@ -1563,6 +1746,8 @@ def main():
         run_batched_generalized(args, rank, world, local_rank)
     elif args.workload == "hessenberg":
         run_hessenberg(args, rank, world, local_rank)
+    elif args.workload == "window":
+        run_window(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 

@@ -191,6 +191,36 @@ evec_status evec_standard_left(evec_handle h, int64_t n, const double *T, int64_
 evec_status evec_hessenberg(evec_handle h, int64_t n, double *A, int64_t lda, double *Q,
                             int64_t ldq, const evec_opts *opt);
 
+/*
+ * Off-diagonal updates of eigenvalue reordering (Sec. 3: a window task
+ * accumulates the local transformations of a diagonal window into an
+ * orthogonal k x k matrix Z; the left and right update tasks apply it to
+ * the off-diagonal sections as level-3 products).  Windows are applied in
+ * the order given.  Window w covers rows and columns [a, a + k), with
+ * a = begin_host[w] and k = size_host[w].  Its accumulator is the k x k
+ * column-major matrix at Z + zoff_host[w].  With Zhat = diag(I_a, Z, I):
+ *   T[a:a+k, a:n] <- Z^T T[a:a+k, a:n]   (left update; the window's rows
+ *                                         left of it are not read)
+ *   T[0:a+k, a:a+k] <- T[0:a+k, a:a+k] Z (right update; the rows below it
+ *                                         are not read)
+ *   Q[:, a:a+k] <- Q[:, a:a+k] Z          (when Q is non-NULL)
+ * This is T <- Zhat^T T Zhat, Q <- Q Zhat whenever the window's rows left
+ * of it and its columns below it hold zeros.  That holds for a quasi-
+ * triangular T whose windows do not split a 2x2 block, with
+ * accumulators that keep each window's diagonal block quasi-triangular, as
+ * a window task's do.  Otherwise the update is still the one stated above.
+ *   T [ldt x n], Q [ldq x n], Z: device pointers on the handle's device;
+ *     Z holds sum_w size_host[w]^2 doubles at the given offsets.
+ *   begin_host, size_host, zoff_host [nwin]: host arrays.
+ *   FP64 throughout; opt: only check (synchronise) is read.
+ * Errors: EVEC_EINVAL (n < 0, a bad leading dimension, a window outside
+ * [0, n), a size above 256, a negative offset).  Entries are not checked.
+ */
+evec_status evec_window_update(evec_handle h, int64_t n, double *T, int64_t ldt, double *Q,
+                               int64_t ldq, int nwin, const int64_t *begin_host,
+                               const int32_t *size_host, const double *Z,
+                               const int64_t *zoff_host, const evec_opts *opt);
+
 /* How evec_hessenberg reduces a panel: 1 (default) one cooperative launch
  * per panel (every CTA co-resident, bounded grid barriers between the
  * column phases; falls back to 0 when the device refuses the launch), 0
@@ -248,7 +278,8 @@ enum {
     EVEC_K_HESS_PANEL = 10,  /* evec_hessenberg: panel reductions, with the
                                 trailing matrix-vector products */
     EVEC_K_HESS_UPDATE = 11, /* evec_hessenberg: trailing / top updates, Q */
-    EVEC_K_COUNT = 12
+    EVEC_K_WINDOW = 12,      /* evec_window_update: left and right updates */
+    EVEC_K_COUNT = 13
 };
 
 /* The residual gate of the last evec_standard call with refine = 2:

@@ -31,7 +31,7 @@ EVEC_ENOMEM, EVEC_ECUDA, EVEC_ETIMEOUT, EVEC_ERESIDUAL = 4, 5, 6, 7
 EVEC_ECAPACITY = 8
 KERNELS = ("gather", "tile_norms", "diag_solve", "tile_update", "finalize",
            "backtransform", "canonicalize", "batched", "refine", "left", "hess_panel",
-           "hess_update")
+           "hess_update", "window")
 
 
 class EvecError(RuntimeError):
@@ -87,6 +87,8 @@ def lib() -> ctypes.CDLL:
         L.evec_set_lookahead.argtypes = [p, ctypes.c_int]
         L.evec_hessenberg.argtypes = [p, i64, p, i64, p, i64, ctypes.POINTER(_Opts)]
         L.evec_set_hessenberg_panel.argtypes = [p, ctypes.c_int]
+        L.evec_window_update.argtypes = [p, i64, p, i64, p, i64, ctypes.c_int, p, p, p, p,
+                                         ctypes.POINTER(_Opts)]
         L.evec_gate_stats.argtypes = [p, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_int)]
         L.evec_profile_read.argtypes = [p, p, p, ctypes.c_int]
         L.evec_last_cuda_error.argtypes = []
@@ -108,7 +110,7 @@ def lib() -> ctypes.CDLL:
                   "evec_plan_query", "evec_trsolve",
                   "evec_profile", "evec_profile_read", "evec_batched_count", "evec_batched",
                   "evec_batched_generalized", "evec_set_lookahead", "evec_hessenberg",
-                  "evec_set_hessenberg_panel", "evec_gate_stats",
+                  "evec_set_hessenberg_panel", "evec_gate_stats", "evec_window_update",
                   "evec_generalized",
                   "evec_tune_get", "evec_tune_set"):
             getattr(L, f).restype = ctypes.c_int
@@ -409,6 +411,44 @@ def trsolve(T, B, tile: int = 0, check: bool = False, mode: str = "fp64", slices
     if check:
         h.sync()
     return X, e
+
+
+def pack_windows(windows, device):
+    """[(begin, Z), ...] (Z k x k) -> (begin int64, size int32, zoff int64
+    host arrays, the Z matrices packed column-major into one float64
+    device vector)."""
+    import torch
+    begin = np.array([int(a) for a, _ in windows], dtype=np.int64)
+    size = np.array([int(Z.shape[0]) for _, Z in windows], dtype=np.int32)
+    zoff = np.zeros(len(windows), dtype=np.int64)
+    if len(windows):
+        zoff[1:] = np.cumsum(size.astype(np.int64) ** 2)[:-1]
+    parts = [torch.as_tensor(np.asarray(Z) if not torch.is_tensor(Z) else Z,
+                             dtype=torch.float64).t().reshape(-1) for _, Z in windows]
+    Zp = (torch.cat(parts) if parts else torch.zeros(1, dtype=torch.float64)).to(device)
+    return begin, size, zoff, Zp
+
+
+def window_update(T, Q, windows, check: bool = False, packed=None):
+    """Eigenvalue reordering's off-diagonal updates, in place: for each
+    (begin, Z) in windows, in order, T[a:b, a:] <- Z^T T[a:b, a:],
+    T[:b, a:b] <- T[:b, a:b] Z and Q[:, a:b] <- Q[:, a:b] Z (T, Q float64
+    CUDA, column-major; Q may be None).  packed: the result of
+    pack_windows, to skip packing.  Returns (T, Q)."""
+    n = T.shape[0]
+    ldt = _check_colmajor(T, "T", n)
+    ldq = _check_colmajor(Q, "Q", n) if Q is not None else 1
+    begin, size, zoff, Zp = packed if packed is not None else pack_windows(windows, T.device)
+    h = handle(T.device.index)
+    opts = _opts(0, False, "fp64", 0)
+    st = lib().evec_window_update(h.ptr, n, T.data_ptr(), ldt,
+                                  Q.data_ptr() if Q is not None else None, ldq, len(begin),
+                                  _np_ptr(begin), _np_ptr(size), Zp.data_ptr(), _np_ptr(zoff),
+                                  ctypes.byref(opts))
+    _check(st, "evec_window_update")
+    if check:
+        h.sync()
+    return T, Q
 
 
 def hessenberg(A, calc_q: bool = True, check: bool = False, overwrite: bool = False):

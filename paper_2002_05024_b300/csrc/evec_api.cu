@@ -61,6 +61,9 @@ int hess_panel(int64_t n, double *A, int64_t lda, int64_t k, int b, double *ws, 
 int hess_update(int64_t n, double *A, int64_t lda, double *Q, int64_t ldq, int64_t k, int b,
                 double *ws, cudaStream_t st, cudaStream_t qst, cudaEvent_t fork,
                 cudaEvent_t join);
+int window_max();
+int window_update(int64_t n, double *T, int64_t ldt, double *Q, int64_t ldq, int64_t a, int k,
+                  const double *Z, cudaStream_t st);
 void launch_gate(const Plan &p, const double *Y, int64_t ldy, const int32_t *ey, const double *R,
                  int64_t ldr, const double *T, int64_t ldt, double limit, void *buf,
                  double *ratio, cudaStream_t st);
@@ -2397,6 +2400,35 @@ extern "C" evec_status evec_generalized(evec_handle h, int64_t n, const double *
         EVEC_CUDA(cudaMemcpyAsync(alpha_im, h->plan_h + m * 8, m * 8, cudaMemcpyHostToDevice, st));
     if (beta)
         EVEC_CUDA(cudaMemcpyAsync(beta, h->plan_h + 2 * m * 8, m * 8, cudaMemcpyHostToDevice, st));
+    if (opt && opt->check) return evec_sync(h, nullptr);
+    return EVEC_OK;
+}
+
+extern "C" evec_status evec_window_update(evec_handle h, int64_t n, double *T, int64_t ldt,
+                                         double *Q, int64_t ldq, int nwin,
+                                         const int64_t *begin_host, const int32_t *size_host,
+                                         const double *Z, const int64_t *zoff_host,
+                                         const evec_opts *opt) {
+    if (!h || n < 0 || !ld_ok(ldt, n) || (Q && !ld_ok(ldq, n)) || nwin < 0 || n > INT32_MAX)
+        return EVEC_EINVAL;
+    if (nwin > 0 && (!begin_host || !size_host || !zoff_host || !Z)) return EVEC_EINVAL;
+    for (int w = 0; w < nwin; w++) {
+        const int64_t a = begin_host[w], k = size_host[w];
+        if (a < 0 || k < 0 || k > window_max() || a + k > n || zoff_host[w] < 0)
+            return EVEC_EINVAL;
+    }
+    if (n == 0 || nwin == 0) return EVEC_OK;
+    if (!T) return EVEC_EINVAL;
+    DeviceGuard g(h->device);
+    if (!g.ok) return EVEC_ECUDA;
+    cudaStream_t st = h->stream;
+    for (int w = 0; w < nwin; w++) {
+        timed(h, EVEC_K_WINDOW, [&] {
+            return window_update(n, T, ldt, Q, ldq, begin_host[w], size_host[w],
+                                 Z + zoff_host[w], st);
+        });
+    }
+    EVEC_CUDA(cudaGetLastError());
     if (opt && opt->check) return evec_sync(h, nullptr);
     return EVEC_OK;
 }

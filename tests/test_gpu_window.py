@@ -1,0 +1,117 @@
+"""Eigenvalue reordering's off-diagonal updates on the GPU
+(evec_window_update: the left and right update tasks applying each
+window's accumulator as FP64 products) against the oracle's plain loops:
+element by element within a dot-product rounding bound for chains of
+overlapping windows of every kernel variant (k up to 256, ragged n), exact
+results for permutation windows, the invariant Q T Q^T for disjoint
+windows at the benchmark's size, edge windows and errors."""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2002_05024_b300 as ev
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+U = 2.0 ** -53
+
+
+def _dev(A):
+    return torch.from_numpy(np.asfortranarray(A)).cuda()
+
+
+def _gpu(T, Q, windows):
+    dT = _dev(T)
+    dQ = _dev(Q) if Q is not None else None
+    ev.window_update(dT, dQ, windows, check=True)
+    return dT.cpu().numpy(), (dQ.cpu().numpy() if dQ is not None else None)
+
+
+def _bound(T, windows):
+    kmax = max(Z.shape[0] for _, Z in windows)
+    return 4 * kmax * len(windows) * U * max(1.0, np.abs(T).max())
+
+
+@pytest.mark.parametrize("k,stride", [(17, 9), (32, 16), (64, 40), (100, 50), (128, 64),
+                                      (200, 100), (256, 128)])
+def test_window_chain_against_oracle(k, stride):
+    n = 333 if k < 256 else 600
+    T, blocks = workloads.config0_schur(n, seed=k)
+    Q = workloads.householder_orthogonal(n, seed=k + 1)
+    w = workloads.window_chain(n, k, stride, seed=k + 2, blocks=blocks)
+    Tg, Qg = _gpu(T, Q, w)
+    To, Qo = oracle.window_update(T, Q, w)
+    assert np.abs(Tg - To).max() <= _bound(To, w), np.abs(Tg - To).max()
+    assert np.abs(Qg - Qo).max() <= _bound(Qo, w)
+
+
+def test_permutation_window_exact():
+    n, a, k = 150, 37, 45
+    T, _ = workloads.config0_schur(n, seed=3)
+    Q = workloads.householder_orthogonal(n, seed=4)
+    perm = np.roll(np.arange(k), 7)
+    P = np.zeros((k, k))
+    P[perm, np.arange(k)] = 1.0
+    Tg, Qg = _gpu(T, Q, [(a, P)])
+    To, Qo = oracle.window_update(T, Q, [(a, P)])
+    np.testing.assert_array_equal(Tg, To)
+    np.testing.assert_array_equal(Qg, Qo)
+
+
+def test_edge_windows_and_no_q():
+    n = 97
+    T, _ = workloads.config0_schur(n, seed=5)
+    rng = np.random.default_rng(6)
+    w = []
+    for a, k in ((0, 1), (96, 1), (0, 97), (60, 37), (0, 33)):
+        Z, _ = np.linalg.qr(rng.standard_normal((k, k)))
+        w.append((a, Z))
+    Tg, Qg = _gpu(T, None, w)
+    To, _ = oracle.window_update(T, None, w)
+    assert Qg is None
+    assert np.abs(Tg - To).max() <= _bound(To, w)
+    # no windows: nothing changes
+    Tn, _ = _gpu(T, None, [])
+    np.testing.assert_array_equal(Tn, T)
+
+
+def test_disjoint_windows_full_size_invariant():
+    # the benchmark's workload: n = 4096 with Q, disjoint windows of 128
+    # tiling the diagonal (boundaries off 2x2 blocks): Q T Q^T unchanged and
+    # Q orthogonal, with the host BLAS; three windows against the oracle
+    n = 4096
+    T, blocks = workloads.config0_schur(n, seed=workloads.SEED_BASE)
+    Q = workloads.householder_orthogonal(n, seed=workloads.SEED_BASE + 100)
+    w = workloads.window_chain(n, 128, 128, seed=workloads.SEED_BASE + 9, blocks=blocks)
+    Tg, Qg = _gpu(T, Q, w)
+    A = Q @ T @ Q.T
+    assert np.abs(Qg @ Tg @ Qg.T - A).max() <= 64 * n * U * np.abs(A).max()
+    assert np.abs(Qg.T @ Qg - np.eye(n)).max() <= 64 * n * U
+    sub = [w[0], w[len(w) // 2], w[-1]]
+    Ts, Qs = _gpu(T, Q, sub)
+    To, Qo = oracle.window_update(T, Q, sub)
+    assert np.abs(Ts - To).max() <= _bound(To, sub)
+    assert np.abs(Qs - Qo).max() <= _bound(Qo, sub)
+
+
+def test_window_errors():
+    n = 50
+    T, _ = workloads.config0_schur(n, seed=8)
+    dT = _dev(T)
+    for a, k in ((-1, 4), (48, 4), (0, 257)):
+        if k > n:
+            dT2 = _dev(np.eye(300))
+            with pytest.raises(ev.EvecError) as ei:
+                ev.window_update(dT2, None, [(a, np.eye(k))])
+        else:
+            with pytest.raises(ev.EvecError) as ei:
+                ev.window_update(dT, None, [(a, np.eye(k))])
+        assert ei.value.status == ev.EVEC_EINVAL
+    # nothing was applied, and the handle stays usable
+    np.testing.assert_array_equal(dT.cpu().numpy(), T)
+    Tg, _ = _gpu(T, None, [(3, np.eye(5))])
+    np.testing.assert_array_equal(Tg, T)
