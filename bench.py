@@ -1269,9 +1269,9 @@ def window_flops(n, wins):
 
 
 def run_window(args, rank, world, local_rank):
-    """Eigenvalue reordering's off-diagonal updates (evec_window_update):
-    the windows of one pass over the diagonal, each applied to T (left and
-    right updates) and Q.  Metric: windows per second; roofline: the FP64
+    """Eigenvalue reordering's off-diagonal updates (evec_window_update_set):
+    the disjoint windows of one pass over the diagonal applied as one
+    concurrent set to T (left and right updates) and Q.  Metric: windows per second; roofline: the FP64
     products against the FP64 pipe."""
     import ctypes
 
@@ -1297,11 +1297,12 @@ def run_window(args, rank, world, local_rank):
 
     def step():
         # each pass is one more orthogonal similarity of the same matrices
-        st = ev.lib().evec_window_update(h.ptr, n, dT.data_ptr(), n, dQ.data_ptr(), n,
-                                         len(wins), ev._np_ptr(begin), ev._np_ptr(size),
-                                         Zp.data_ptr(), ev._np_ptr(zoff), ctypes.byref(opts))
+        # the pass's windows are disjoint: one concurrent set
+        st = ev.lib().evec_window_update_set(h.ptr, n, dT.data_ptr(), n, dQ.data_ptr(), n,
+                                             len(wins), ev._np_ptr(begin), ev._np_ptr(size),
+                                             Zp.data_ptr(), ev._np_ptr(zoff), ctypes.byref(opts))
         if st:
-            raise ev.EvecError(st, "evec_window_update")
+            raise ev.EvecError(st, "evec_window_update_set")
 
     for _ in range(args.warmup):
         step()
@@ -1370,7 +1371,8 @@ def run_window(args, rank, world, local_rank):
     wm, wn = prof.get("window", (0.0, 0))
     if wm > 0:
         ach = F / (wm / args.steps / 1e3) / 1e12
-        roof = {"kernel": "left and right updates (k_win_left, k_win_right)", "bound": "alu",
+        roof = {"kernel": "left and right updates of the set (k_win_left_set, k_win_right_set)",
+                "bound": "alu",
                 "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach / fp64_peak,
                 "traffic": stored_traffic("window", "fp64", n, k, "window:"),
                 "peak_source": "of derived FP64 peak (measured 4 flop/clk/SM x 148 SMs x max "
@@ -1387,7 +1389,7 @@ def run_window(args, rank, world, local_rank):
         dt = time.perf_counter() - t
         dT.copy_(torch.from_numpy(np.asfortranarray(T)))
         dQ.copy_(torch.from_numpy(np.asfortranarray(Q)))
-        ev.window_update(dT, dQ, pick, check=True)
+        ev.window_update(dT, dQ, pick, check=True, disjoint=True)
         quality["gpu_vs_oracle_two_windows"] = float(
             max(np.abs(dT.cpu().numpy() - To).max(), np.abs(dQ.cpu().numpy() - Qo).max()))
         cpu = {"value": len(pick) / dt, "unit": "windows/s", "cores": 1, "kind": "oracle",

@@ -221,6 +221,21 @@ evec_status evec_window_update(evec_handle h, int64_t n, double *T, int64_t ldt,
                                const int32_t *size_host, const double *Z,
                                const int64_t *zoff_host, const evec_opts *opt);
 
+/*
+ * The same updates for a set of pairwise disjoint windows, applied
+ * concurrently (the paper's concurrent windows of different chains):
+ * disjoint windows' updates commute, since (Z'^T X) Z = Z'^T (X Z) on the
+ * block two windows share, so all left updates of T run in one launch,
+ * then all right updates, with all Q updates beside them.  The result
+ * equals evec_window_update on the same windows in any order, up to
+ * rounding.  Arguments and errors as evec_window_update; also EVEC_EINVAL
+ * when two windows of nonzero size overlap.
+ */
+evec_status evec_window_update_set(evec_handle h, int64_t n, double *T, int64_t ldt, double *Q,
+                                   int64_t ldq, int nwin, const int64_t *begin_host,
+                                   const int32_t *size_host, const double *Z,
+                                   const int64_t *zoff_host, const evec_opts *opt);
+
 /* How evec_hessenberg reduces a panel: 1 (default) one cooperative launch
  * per panel (every CTA co-resident, bounded grid barriers between the
  * column phases; falls back to 0 when the device refuses the launch), 0

@@ -89,6 +89,8 @@ def lib() -> ctypes.CDLL:
         L.evec_set_hessenberg_panel.argtypes = [p, ctypes.c_int]
         L.evec_window_update.argtypes = [p, i64, p, i64, p, i64, ctypes.c_int, p, p, p, p,
                                          ctypes.POINTER(_Opts)]
+        L.evec_window_update_set.argtypes = [p, i64, p, i64, p, i64, ctypes.c_int, p, p, p, p,
+                                             ctypes.POINTER(_Opts)]
         L.evec_gate_stats.argtypes = [p, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_int)]
         L.evec_profile_read.argtypes = [p, p, p, ctypes.c_int]
         L.evec_last_cuda_error.argtypes = []
@@ -111,6 +113,7 @@ def lib() -> ctypes.CDLL:
                   "evec_profile", "evec_profile_read", "evec_batched_count", "evec_batched",
                   "evec_batched_generalized", "evec_set_lookahead", "evec_hessenberg",
                   "evec_set_hessenberg_panel", "evec_gate_stats", "evec_window_update",
+                  "evec_window_update_set",
                   "evec_generalized",
                   "evec_tune_get", "evec_tune_set"):
             getattr(L, f).restype = ctypes.c_int
@@ -429,23 +432,23 @@ def pack_windows(windows, device):
     return begin, size, zoff, Zp
 
 
-def window_update(T, Q, windows, check: bool = False, packed=None):
+def window_update(T, Q, windows, check: bool = False, packed=None, disjoint: bool = False):
     """Eigenvalue reordering's off-diagonal updates, in place: for each
     (begin, Z) in windows, in order, T[a:b, a:] <- Z^T T[a:b, a:],
     T[:b, a:b] <- T[:b, a:b] Z and Q[:, a:b] <- Q[:, a:b] Z (T, Q float64
-    CUDA, column-major; Q may be None).  packed: the result of
-    pack_windows, to skip packing.  Returns (T, Q)."""
+    CUDA, column-major; Q may be None).  disjoint: the windows are pairwise
+    disjoint and are applied as one concurrent set (evec_window_update_set).
+    packed: the result of pack_windows, to skip packing.  Returns (T, Q)."""
     n = T.shape[0]
     ldt = _check_colmajor(T, "T", n)
     ldq = _check_colmajor(Q, "Q", n) if Q is not None else 1
     begin, size, zoff, Zp = packed if packed is not None else pack_windows(windows, T.device)
     h = handle(T.device.index)
     opts = _opts(0, False, "fp64", 0)
-    st = lib().evec_window_update(h.ptr, n, T.data_ptr(), ldt,
-                                  Q.data_ptr() if Q is not None else None, ldq, len(begin),
-                                  _np_ptr(begin), _np_ptr(size), Zp.data_ptr(), _np_ptr(zoff),
-                                  ctypes.byref(opts))
-    _check(st, "evec_window_update")
+    fn = lib().evec_window_update_set if disjoint else lib().evec_window_update
+    st = fn(h.ptr, n, T.data_ptr(), ldt, Q.data_ptr() if Q is not None else None, ldq, len(begin),
+            _np_ptr(begin), _np_ptr(size), Zp.data_ptr(), _np_ptr(zoff), ctypes.byref(opts))
+    _check(st, "evec_window_update_set" if disjoint else "evec_window_update")
     if check:
         h.sync()
     return T, Q

@@ -62,8 +62,16 @@ int hess_update(int64_t n, double *A, int64_t lda, double *Q, int64_t ldq, int64
                 double *ws, cudaStream_t st, cudaStream_t qst, cudaEvent_t fork,
                 cudaEvent_t join);
 int window_max();
-int window_update(int64_t n, double *T, int64_t ldt, double *Q, int64_t ldq, int64_t a, int k,
-                  const double *Z, cudaStream_t st);
+int window_update_t(int64_t n, double *T, int64_t ldt, int64_t a, int k, const double *Z,
+                    cudaStream_t st);
+int window_update_q(int64_t n, double *Q, int64_t ldq, int64_t a, int k, const double *Z,
+                    cudaStream_t st);
+int window_left_tiles(int64_t n, int64_t a);
+int window_right_tiles(int64_t rows);
+int window_update_set(int64_t n, double *T, int64_t ldt, double *Q, int64_t ldq, int kmax,
+                      const WinDesc *wl, int ctas_l, const WinDesc *wr, int ctas_r,
+                      const WinDesc *wq, int ctas_q, int nwin, const double *Z, cudaStream_t st,
+                      cudaStream_t qst);
 void launch_gate(const Plan &p, const double *Y, int64_t ldy, const int32_t *ey, const double *R,
                  int64_t ldr, const double *T, int64_t ldt, double limit, void *buf,
                  double *ratio, cudaStream_t st);
@@ -562,6 +570,7 @@ struct evec_ctx {
     double *lL = nullptr; size_t lL_cap = 0;
     int32_t *lmap_d = nullptr; size_t lmap_cap = 0;
     double *hs_ws = nullptr; size_t hs_ws_cap = 0;   // Hessenberg reduction
+    WinDesc *win_d = nullptr; size_t win_cap = 0;    // reordering window tables
     // residual gate of the split solve (opts.refine >= 2): ||T||_1 and the
     // failure count on the device; the last top-level call's statistics
     unsigned long long *gate_d = nullptr;
@@ -937,7 +946,7 @@ evec_status evec_destroy(evec_handle h) {
                    h->slA, h->slB, h->rmax, h->cmax, h->ea, h->eb, h->panels,
                    h->ea_panels, h->boff_d, h->bws, h->bplan_d, h->queue_d, h->tauT,
                    h->blk_tauT, h->pW, h->Rd, h->seg_ey, h->lT, h->lQ, h->lX, h->lE, h->lL,
-                   h->lmap_d, h->hs_ws, h->gate_d};
+                   h->lmap_d, h->hs_ws, h->gate_d, h->win_d};
     for (void *p : dev)
         if (p) cudaFree(p);
     for (auto &t : h->live) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
@@ -2422,12 +2431,100 @@ extern "C" evec_status evec_window_update(evec_handle h, int64_t n, double *T, i
     DeviceGuard g(h->device);
     if (!g.ok) return EVEC_ECUDA;
     cudaStream_t st = h->stream;
-    for (int w = 0; w < nwin; w++) {
-        timed(h, EVEC_K_WINDOW, [&] {
-            return window_update(n, T, ldt, Q, ldq, begin_host[w], size_host[w],
-                                 Z + zoff_host[w], st);
-        });
+    if (Q) {   // the Q updates run on a second stream beside the T chain
+        if (!h->la_stream)
+            EVEC_CUDA(cudaStreamCreateWithFlags(&h->la_stream, cudaStreamNonBlocking));
+        if (!h->ev_slice) EVEC_CUDA(cudaEventCreateWithFlags(&h->ev_slice, cudaEventDisableTiming));
+        if (!h->ev_tail) EVEC_CUDA(cudaEventCreateWithFlags(&h->ev_tail, cudaEventDisableTiming));
     }
+    timed(h, EVEC_K_WINDOW, [&] {
+        int ng = 0;
+        if (Q) {
+            cudaEventRecord(h->ev_slice, st);
+            cudaStreamWaitEvent(h->la_stream, h->ev_slice, 0);
+        }
+        for (int w = 0; w < nwin; w++) {
+            ng += window_update_t(n, T, ldt, begin_host[w], size_host[w], Z + zoff_host[w], st);
+            if (Q)
+                ng += window_update_q(n, Q, ldq, begin_host[w], size_host[w], Z + zoff_host[w],
+                                      h->la_stream);
+        }
+        if (Q) {
+            cudaEventRecord(h->ev_tail, h->la_stream);
+            cudaStreamWaitEvent(st, h->ev_tail, 0);
+        }
+        return ng;
+    });
+    EVEC_CUDA(cudaGetLastError());
+    if (opt && opt->check) return evec_sync(h, nullptr);
+    return EVEC_OK;
+}
+
+extern "C" evec_status evec_window_update_set(evec_handle h, int64_t n, double *T, int64_t ldt,
+                                             double *Q, int64_t ldq, int nwin,
+                                             const int64_t *begin_host, const int32_t *size_host,
+                                             const double *Z, const int64_t *zoff_host,
+                                             const evec_opts *opt) {
+    if (!h || n < 0 || !ld_ok(ldt, n) || (Q && !ld_ok(ldq, n)) || nwin < 0 || n > INT32_MAX)
+        return EVEC_EINVAL;
+    if (nwin > 0 && (!begin_host || !size_host || !zoff_host || !Z)) return EVEC_EINVAL;
+    std::vector<int> order;
+    for (int w = 0; w < nwin; w++) {
+        const int64_t a = begin_host[w], k = size_host[w];
+        if (a < 0 || k < 0 || k > window_max() || a + k > n || zoff_host[w] < 0)
+            return EVEC_EINVAL;
+        if (k > 0) order.push_back(w);
+    }
+    std::sort(order.begin(), order.end(),
+              [&](int x, int y) { return begin_host[x] < begin_host[y]; });
+    for (size_t i = 1; i < order.size(); i++)   // pairwise disjoint
+        if (begin_host[order[i]] < begin_host[order[i - 1]] + size_host[order[i - 1]])
+            return EVEC_EINVAL;
+    if (n == 0 || order.empty()) return EVEC_OK;
+    if (!T) return EVEC_EINVAL;
+    DeviceGuard g(h->device);
+    if (!g.ok) return EVEC_ECUDA;
+    const int m = (int)order.size();
+    std::vector<WinDesc> tab(3 * (size_t)m);   // left, T right, Q right
+    int64_t cl = 0, cr = 0, cq = 0;
+    int kmax = 0;
+    for (int i = 0; i < m; i++) {
+        const int w = order[i];
+        const int64_t a = begin_host[w];
+        const int k = size_host[w];
+        kmax = std::max(kmax, k);
+        tab[i] = {a, zoff_host[w], cl, k, 0};
+        tab[m + i] = {a, zoff_host[w], cr, k, 0};
+        tab[2 * m + i] = {a, zoff_host[w], cq, k, 0};
+        cl += window_left_tiles(n, a);
+        cr += window_right_tiles(a + k);
+        cq += window_right_tiles(n);
+    }
+    if (cl > INT32_MAX || cq > INT32_MAX) return EVEC_EINVAL;
+    cudaStream_t st = h->stream;
+    EVEC_TRY(grow_device(&h->win_d, &h->win_cap, tab.size()));
+    EVEC_CUDA(cudaMemcpyAsync(h->win_d, tab.data(), tab.size() * sizeof(WinDesc),
+                              cudaMemcpyHostToDevice, st));
+    if (Q) {
+        if (!h->la_stream)
+            EVEC_CUDA(cudaStreamCreateWithFlags(&h->la_stream, cudaStreamNonBlocking));
+        if (!h->ev_slice) EVEC_CUDA(cudaEventCreateWithFlags(&h->ev_slice, cudaEventDisableTiming));
+        if (!h->ev_tail) EVEC_CUDA(cudaEventCreateWithFlags(&h->ev_tail, cudaEventDisableTiming));
+    }
+    timed(h, EVEC_K_WINDOW, [&] {
+        if (Q) {   // the tables are on the device before the Q stream starts
+            cudaEventRecord(h->ev_slice, st);
+            cudaStreamWaitEvent(h->la_stream, h->ev_slice, 0);
+        }
+        const int ng = window_update_set(n, T, ldt, Q, ldq, kmax, h->win_d, (int)cl,
+                                         h->win_d + m, (int)cr, h->win_d + 2 * m, (int)cq, m, Z,
+                                         st, Q ? h->la_stream : st);
+        if (Q) {
+            cudaEventRecord(h->ev_tail, h->la_stream);
+            cudaStreamWaitEvent(st, h->ev_tail, 0);
+        }
+        return ng;
+    });
     EVEC_CUDA(cudaGetLastError());
     if (opt && opt->check) return evec_sync(h, nullptr);
     return EVEC_OK;

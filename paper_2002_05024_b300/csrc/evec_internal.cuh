@@ -184,4 +184,11 @@ __device__ __forceinline__ void report(DevStatus *st, int code, long long index)
     if (atomicCAS(&st->code, 0, code) == 0) st->index = index;
 }
 
+// One window of a disjoint set for the reordering updates: rows and
+// columns [a, a + k), accumulator at Z + zoff, first CTA of its tiles cta0.
+struct WinDesc {
+    int64_t a, zoff, cta0;
+    int k, pad;
+};
+
 }  // namespace evec

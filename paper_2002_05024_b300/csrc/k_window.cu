@@ -11,7 +11,8 @@
 // shared memory before it writes, so the update runs in place; Z streams
 // through shared memory in chunks of kWzc rows.  The left update must
 // finish before the right one reads the window's diagonal block, so the
-// two are separate launches on one stream.
+// two are separate launches on one stream; the Q updates read no part of T
+// and run on a second stream beside them.
 #include <algorithm>
 
 #include "evec_internal.cuh"
@@ -35,14 +36,14 @@ __device__ __forceinline__ void stage_z(const double *__restrict__ Z, int k, int
 // Left update, kWlc columns per CTA (from column a + blockIdx.x kWlc); lane
 // = output rows lane + 32 p (p < P, k <= 32 P), warp = columns warp + 8 q.
 template <int P>
-__global__ void __launch_bounds__(256)
-    k_win_left(int64_t n, double *__restrict__ T, int64_t ldt, int64_t a, int k,
-               const double *__restrict__ Z) {
+__device__ __forceinline__ void win_left_tile(int64_t n, double *__restrict__ T, int64_t ldt,
+                                              int64_t a, int k, const double *__restrict__ Z,
+                                              int64_t tile) {
     extern __shared__ __align__(16) double wsm[];
     double *Ws = wsm;                 // [kWlc][k]: column c of the strip at Ws + c k
     double *Zs = wsm + kWlc * k;      // [kWzc][k + 1]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t col0 = a + (int64_t)blockIdx.x * kWlc;
+    const int64_t col0 = a + tile * kWlc;
     const int ncol = (int)min((int64_t)kWlc, n - col0);
     for (int e = threadIdx.x; e < kWlc * k; e += blockDim.x) {
         const int l = e % k, c = e / k;
@@ -85,21 +86,17 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-// Right update, kWrr rows per CTA of T (blockIdx.y 0, rows [0, rows_t)) or
-// Q (blockIdx.y 1, rows [0, rows_q)); lane = row, warp = output columns
-// warp + 8 p (p < P, k <= 8 P).
+// Right update C[0:rows, a:a+k] <- C[0:rows, a:a+k] Z (C = T with rows =
+// a + k, or Q with rows = n), kWrr rows per CTA; lane = row, warp = output
+// columns warp + 8 p (p < P, k <= 8 P).
 template <int P>
-__global__ void __launch_bounds__(256)
-    k_win_right(int64_t rows_t, double *__restrict__ T, int64_t ldt, int64_t rows_q,
-                double *__restrict__ Q, int64_t ldq, int64_t a, int k,
-                const double *__restrict__ Z) {
+__device__ __forceinline__ void win_right_tile(int64_t rows, double *__restrict__ C, int64_t ld,
+                                               int64_t a, int k, const double *__restrict__ Z,
+                                               int64_t tile) {
     extern __shared__ __align__(16) double wsm[];
     double *Ws = wsm;                 // [k][kWrr]: row l of the strip's transpose
     double *Zs = wsm + kWrr * k;      // [kWzc][k + 1]
-    double *C = blockIdx.y ? Q : T;
-    const int64_t ld = blockIdx.y ? ldq : ldt, rows = blockIdx.y ? rows_q : rows_t;
-    const int64_t r0 = (int64_t)blockIdx.x * kWrr;
-    if (r0 >= rows) return;   // (uniform in the CTA)
+    const int64_t r0 = tile * kWrr;
     const int nr = (int)min((int64_t)kWrr, rows - r0);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int e = threadIdx.x; e < kWrr * k; e += blockDim.x) {
@@ -133,7 +130,92 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+template <int P>
+__global__ void __launch_bounds__(256)
+    k_win_left(int64_t n, double *__restrict__ T, int64_t ldt, int64_t a, int k,
+               const double *__restrict__ Z) {
+    win_left_tile<P>(n, T, ldt, a, k, Z, blockIdx.x);
+}
+
+template <int P>
+__global__ void __launch_bounds__(256)
+    k_win_right(int64_t rows, double *__restrict__ C, int64_t ld, int64_t a, int k,
+                const double *__restrict__ Z) {
+    win_right_tile<P>(rows, C, ld, a, k, Z, blockIdx.x);
+}
+
+// A set of pairwise disjoint windows in one launch: CTA blockIdx.x works
+// on window w with cta0[w] <= blockIdx.x < cta0[w + 1] (its tile index is
+// the difference).  Disjoint windows' updates commute, as (Z'^T X) Z =
+// Z'^T (X Z) on the block two of them share, so the left updates of the
+// whole set run in one launch, then the right updates.
+__device__ __forceinline__ int find_window(const WinDesc *wd, int nwin) {
+    int lo = 0, hi = nwin - 1;   // the last w with cta0 <= blockIdx.x
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) / 2;
+        if (wd[mid].cta0 <= (int64_t)blockIdx.x) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int P>
+__global__ void __launch_bounds__(256)
+    k_win_left_set(int64_t n, double *__restrict__ T, int64_t ldt, const WinDesc *__restrict__ wd,
+                   int nwin, const double *__restrict__ Z) {
+    const WinDesc d = wd[find_window(wd, nwin)];
+    win_left_tile<P>(n, T, ldt, d.a, d.k, Z + d.zoff, (int64_t)blockIdx.x - d.cta0);
+}
+
+// rows of window w: a + k for T (q false), n for Q
+template <int P>
+__global__ void __launch_bounds__(256)
+    k_win_right_set(int64_t n, double *__restrict__ C, int64_t ld, bool q,
+                    const WinDesc *__restrict__ wd, int nwin, const double *__restrict__ Z) {
+    const WinDesc d = wd[find_window(wd, nwin)];
+    win_right_tile<P>(q ? n : d.a + d.k, C, ld, d.a, d.k, Z + d.zoff,
+                      (int64_t)blockIdx.x - d.cta0);
+}
+
 int window_max() { return kWinMax; }
+int window_left_tiles(int64_t n, int64_t a) { return (int)((n - a + kWlc - 1) / kWlc); }
+int window_right_tiles(int64_t rows) { return (int)((rows + kWrr - 1) / kWrr); }
+
+template <int P>
+static void set_t(int64_t n, double *T, int64_t ldt, double *Q, int64_t ldq, int kmax,
+                  const WinDesc *wl, int ctas_l, const WinDesc *wr, int ctas_r,
+                  const WinDesc *wq, int ctas_q, int nwin, const double *Z, cudaStream_t st,
+                  cudaStream_t qst) {
+    const size_t sl = sizeof(double) * ((size_t)kWlc * kmax + (size_t)kWzc * (kmax + 1));
+    const size_t sr = sizeof(double) * ((size_t)kWrr * kmax + (size_t)kWzc * (kmax + 1));
+    constexpr int PL = (P + 3) / 4;   // left: k <= 32 PL; right: k <= 8 P
+    cudaFuncSetAttribute(k_win_left_set<PL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sl);
+    cudaFuncSetAttribute(k_win_right_set<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sr);
+    if (Q && ctas_q > 0)
+        k_win_right_set<P><<<ctas_q, 256, sr, qst>>>(n, Q, ldq, true, wq, nwin, Z);
+    k_win_left_set<PL><<<ctas_l, 256, sl, st>>>(n, T, ldt, wl, nwin, Z);
+    k_win_right_set<P><<<ctas_r, 256, sr, st>>>(n, T, ldt, false, wr, nwin, Z);
+}
+
+// The set's left updates of T, then its right updates, on st; its Q
+// updates on qst.  wl / wr / wq: device descriptor tables whose cta0 count
+// the left tiles, T's right tiles and Q's right tiles; kmax: the largest k.
+// Returns the kernels launched.
+int window_update_set(int64_t n, double *T, int64_t ldt, double *Q, int64_t ldq, int kmax,
+                      const WinDesc *wl, int ctas_l, const WinDesc *wr, int ctas_r,
+                      const WinDesc *wq, int ctas_q, int nwin, const double *Z, cudaStream_t st,
+                      cudaStream_t qst) {
+    if (nwin <= 0 || kmax <= 0) return 0;
+    if (kmax <= 32)
+        set_t<4>(n, T, ldt, Q, ldq, kmax, wl, ctas_l, wr, ctas_r, wq, ctas_q, nwin, Z, st, qst);
+    else if (kmax <= 64)
+        set_t<8>(n, T, ldt, Q, ldq, kmax, wl, ctas_l, wr, ctas_r, wq, ctas_q, nwin, Z, st, qst);
+    else if (kmax <= 128)
+        set_t<16>(n, T, ldt, Q, ldq, kmax, wl, ctas_l, wr, ctas_r, wq, ctas_q, nwin, Z, st, qst);
+    else
+        set_t<32>(n, T, ldt, Q, ldq, kmax, wl, ctas_l, wr, ctas_r, wq, ctas_q, nwin, Z, st, qst);
+    return Q ? 3 : 2;
+}
 
 template <int P>
 static void left_t(int64_t n, double *T, int64_t ldt, int64_t a, int k, const double *Z,
@@ -145,30 +227,42 @@ static void left_t(int64_t n, double *T, int64_t ldt, int64_t a, int k, const do
 }
 
 template <int P>
-static void right_t(int64_t rows_t, double *T, int64_t ldt, int64_t rows_q, double *Q,
-                    int64_t ldq, int64_t a, int k, const double *Z, cudaStream_t st) {
+static void right_t(int64_t rows, double *C, int64_t ld, int64_t a, int k, const double *Z,
+                    cudaStream_t st) {
     const size_t smem = sizeof(double) * ((size_t)kWrr * k + (size_t)kWzc * (k + 1));
     cudaFuncSetAttribute(k_win_right<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    const int64_t rows = std::max(rows_t, Q ? rows_q : 0);
-    dim3 grid((unsigned)((rows + kWrr - 1) / kWrr), Q ? 2u : 1u);
-    k_win_right<P><<<grid, 256, smem, st>>>(rows_t, T, ldt, rows_q, Q, ldq, a, k, Z);
+    const unsigned grid = (unsigned)((rows + kWrr - 1) / kWrr);
+    k_win_right<P><<<grid, 256, smem, st>>>(rows, C, ld, a, k, Z);
 }
 
-// One window (1 <= k <= kWinMax, a + k <= n): the left update, then the
-// right update of T and Q.  Returns the kernels launched.
-int window_update(int64_t n, double *T, int64_t ldt, double *Q, int64_t ldq, int64_t a, int k,
-                  const double *Z, cudaStream_t st) {
+static void right(int64_t rows, double *C, int64_t ld, int64_t a, int k, const double *Z,
+                  cudaStream_t st) {
+    if (k <= 32) right_t<4>(rows, C, ld, a, k, Z, st);
+    else if (k <= 64) right_t<8>(rows, C, ld, a, k, Z, st);
+    else if (k <= 128) right_t<16>(rows, C, ld, a, k, Z, st);
+    else right_t<32>(rows, C, ld, a, k, Z, st);
+}
+
+// One window of T (1 <= k <= kWinMax, a + k <= n): the left update, then
+// the right update.  Returns the kernels launched.
+int window_update_t(int64_t n, double *T, int64_t ldt, int64_t a, int k, const double *Z,
+                    cudaStream_t st) {
     if (k <= 0) return 0;
     if (k <= 32) left_t<1>(n, T, ldt, a, k, Z, st);
     else if (k <= 64) left_t<2>(n, T, ldt, a, k, Z, st);
     else if (k <= 128) left_t<4>(n, T, ldt, a, k, Z, st);
     else left_t<8>(n, T, ldt, a, k, Z, st);
-    const int64_t b = a + k;
-    if (k <= 32) right_t<4>(b, T, ldt, n, Q, ldq, a, k, Z, st);
-    else if (k <= 64) right_t<8>(b, T, ldt, n, Q, ldq, a, k, Z, st);
-    else if (k <= 128) right_t<16>(b, T, ldt, n, Q, ldq, a, k, Z, st);
-    else right_t<32>(b, T, ldt, n, Q, ldq, a, k, Z, st);
+    right(a + k, T, ldt, a, k, Z, st);
     return 2;
+}
+
+// The same window's Q[:, a:a+k] <- Q[:, a:a+k] Z.  It reads no part of T,
+// so the Q updates of a list of windows can run on their own stream.
+int window_update_q(int64_t n, double *Q, int64_t ldq, int64_t a, int k, const double *Z,
+                    cudaStream_t st) {
+    if (k <= 0) return 0;
+    right(n, Q, ldq, a, k, Z, st);
+    return 1;
 }
 
 }  // namespace evec

@@ -115,3 +115,58 @@ def test_window_errors():
     np.testing.assert_array_equal(dT.cpu().numpy(), T)
     Tg, _ = _gpu(T, None, [(3, np.eye(5))])
     np.testing.assert_array_equal(Tg, T)
+
+
+def _mixed_disjoint(n, seed):
+    # disjoint windows of mixed sizes (one per kernel variant), in shuffled order
+    rng = np.random.default_rng(seed)
+    out, a = [], 5
+    for k in (37, 64, 128, 200, 20, 256):
+        if a + k > n:
+            break
+        Z, _ = np.linalg.qr(rng.standard_normal((k, k)))
+        out.append((a, Z))
+        a += k + int(rng.integers(0, 9))
+    rng.shuffle(out)
+    return out
+
+
+def test_disjoint_set_against_oracle():
+    n = 777
+    T, _ = workloads.config0_schur(n, seed=41)
+    Q = workloads.householder_orthogonal(n, seed=42)
+    w = _mixed_disjoint(n, 43)
+    dT, dQ = _dev(T), _dev(Q)
+    ev.window_update(dT, dQ, w, check=True, disjoint=True)
+    To, Qo = oracle.window_update(T, Q, w)
+    assert np.abs(dT.cpu().numpy() - To).max() <= _bound(To, w)
+    assert np.abs(dQ.cpu().numpy() - Qo).max() <= _bound(Qo, w)
+    # without Q, and a zero-size window in the list
+    dT = _dev(T)
+    ev.window_update(dT, None, w + [(3, np.zeros((0, 0)))], check=True, disjoint=True)
+    assert np.abs(dT.cpu().numpy() - To).max() <= _bound(To, w)
+
+
+def test_disjoint_set_full_size_matches_sequential():
+    # the benchmark's windows: the set path against the one-window-at-a-time
+    # path (the same products, another order of the commuting updates)
+    n = 4096
+    T, blocks = workloads.config0_schur(n, seed=workloads.SEED_BASE)
+    Q = workloads.householder_orthogonal(n, seed=workloads.SEED_BASE + 100)
+    w = workloads.window_chain(n, 128, 128, seed=workloads.SEED_BASE + 9, blocks=blocks)
+    Ts, Qs = _dev(T), _dev(Q)
+    ev.window_update(Ts, Qs, w, check=True, disjoint=True)
+    Tq, Qq = _dev(T), _dev(Q)
+    ev.window_update(Tq, Qq, w, check=True)
+    assert torch.abs(Ts - Tq).max().item() <= _bound(T, w[:2])
+    assert torch.equal(Qs, Qq)   # Q's updates touch disjoint columns: same products
+
+
+def test_disjoint_set_rejects_overlap():
+    n = 60
+    T, _ = workloads.config0_schur(n, seed=44)
+    dT = _dev(T)
+    with pytest.raises(ev.EvecError) as ei:
+        ev.window_update(dT, None, [(0, np.eye(10)), (9, np.eye(5))], disjoint=True)
+    assert ei.value.status == ev.EVEC_EINVAL
+    np.testing.assert_array_equal(dT.cpu().numpy(), T)
