@@ -68,10 +68,11 @@ int window_update_q(int64_t n, double *Q, int64_t ldq, int64_t a, int k, const d
                     cudaStream_t st);
 int window_left_tiles(int64_t n, int64_t a);
 int window_right_tiles(int64_t rows);
-int window_update_set(int64_t n, double *T, int64_t ldt, double *Q, int64_t ldq, int kmax,
-                      const WinDesc *wl, int ctas_l, const WinDesc *wr, int ctas_r,
-                      const WinDesc *wq, int ctas_q, int nwin, const double *Z, cudaStream_t st,
-                      cudaStream_t qst);
+int window_class(int k);
+void window_set_left(int pclass, int64_t n, double *T, int64_t ldt, int kmax, const WinDesc *wl,
+                     int ctas, int nwin, const double *Z, cudaStream_t st);
+void window_set_right(int pclass, int64_t n, double *C, int64_t ld, bool q, int kmax,
+                      const WinDesc *wr, int ctas, int nwin, const double *Z, cudaStream_t st);
 void launch_gate(const Plan &p, const double *Y, int64_t ldy, const int32_t *ey, const double *R,
                  int64_t ldr, const double *T, int64_t ldt, double limit, void *buf,
                  double *ratio, cudaStream_t st);
@@ -2484,23 +2485,37 @@ extern "C" evec_status evec_window_update_set(evec_handle h, int64_t n, double *
     if (!T) return EVEC_EINVAL;
     DeviceGuard g(h->device);
     if (!g.ok) return EVEC_ECUDA;
-    const int m = (int)order.size();
-    std::vector<WinDesc> tab(3 * (size_t)m);   // left, T right, Q right
-    int64_t cl = 0, cr = 0, cq = 0;
-    int kmax = 0;
-    for (int i = 0; i < m; i++) {
-        const int w = order[i];
-        const int64_t a = begin_host[w];
-        const int k = size_host[w];
-        kmax = std::max(kmax, k);
-        tab[i] = {a, zoff_host[w], cl, k, 0};
-        tab[m + i] = {a, zoff_host[w], cr, k, 0};
-        tab[2 * m + i] = {a, zoff_host[w], cq, k, 0};
-        cl += window_left_tiles(n, a);
-        cr += window_right_tiles(a + k);
-        cq += window_right_tiles(n);
+    // one group of launches per kernel variant (window_class), so that no
+    // window runs with columns past its own k
+    struct Group {
+        int pclass, m, kmax;
+        size_t off;
+        int64_t cl, cr, cq;
+    };
+    std::vector<Group> groups;
+    std::vector<WinDesc> tab;
+    for (int pc : {4, 8, 16, 20, 32}) {
+        std::vector<int> ws;
+        for (int w : order)
+            if (window_class(size_host[w]) == pc) ws.push_back(w);
+        if (ws.empty()) continue;
+        Group gr{pc, (int)ws.size(), 0, tab.size(), 0, 0, 0};
+        tab.resize(tab.size() + 3 * ws.size());
+        for (int i = 0; i < gr.m; i++) {   // left, T right, Q right
+            const int w = ws[i];
+            const int64_t a = begin_host[w];
+            const int k = size_host[w];
+            gr.kmax = std::max(gr.kmax, k);
+            tab[gr.off + i] = {a, zoff_host[w], gr.cl, k, 0};
+            tab[gr.off + gr.m + i] = {a, zoff_host[w], gr.cr, k, 0};
+            tab[gr.off + 2 * gr.m + i] = {a, zoff_host[w], gr.cq, k, 0};
+            gr.cl += window_left_tiles(n, a);
+            gr.cr += window_right_tiles(a + k);
+            gr.cq += window_right_tiles(n);
+        }
+        if (gr.cl > INT32_MAX || gr.cq > INT32_MAX) return EVEC_EINVAL;
+        groups.push_back(gr);
     }
-    if (cl > INT32_MAX || cq > INT32_MAX) return EVEC_EINVAL;
     cudaStream_t st = h->stream;
     EVEC_TRY(grow_device(&h->win_d, &h->win_cap, tab.size()));
     EVEC_CUDA(cudaMemcpyAsync(h->win_d, tab.data(), tab.size() * sizeof(WinDesc),
@@ -2512,13 +2527,26 @@ extern "C" evec_status evec_window_update_set(evec_handle h, int64_t n, double *
         if (!h->ev_tail) EVEC_CUDA(cudaEventCreateWithFlags(&h->ev_tail, cudaEventDisableTiming));
     }
     timed(h, EVEC_K_WINDOW, [&] {
+        int ng = 0;
         if (Q) {   // the tables are on the device before the Q stream starts
             cudaEventRecord(h->ev_slice, st);
             cudaStreamWaitEvent(h->la_stream, h->ev_slice, 0);
+            for (const Group &gq : groups) {
+                window_set_right(gq.pclass, n, Q, ldq, true, gq.kmax, h->win_d + gq.off + 2 * gq.m,
+                                 (int)gq.cq, gq.m, Z, h->la_stream);
+                ng++;
+            }
         }
-        const int ng = window_update_set(n, T, ldt, Q, ldq, kmax, h->win_d, (int)cl,
-                                         h->win_d + m, (int)cr, h->win_d + 2 * m, (int)cq, m, Z,
-                                         st, Q ? h->la_stream : st);
+        for (const Group &gl : groups) {   // every left update before any right one
+            window_set_left(gl.pclass, n, T, ldt, gl.kmax, h->win_d + gl.off, (int)gl.cl, gl.m, Z,
+                            st);
+            ng++;
+        }
+        for (const Group &gr : groups) {
+            window_set_right(gr.pclass, n, T, ldt, false, gr.kmax, h->win_d + gr.off + gr.m,
+                             (int)gr.cr, gr.m, Z, st);
+            ng++;
+        }
         if (Q) {
             cudaEventRecord(h->ev_tail, h->la_stream);
             cudaStreamWaitEvent(st, h->ev_tail, 0);

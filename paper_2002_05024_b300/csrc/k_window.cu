@@ -181,40 +181,56 @@ int window_max() { return kWinMax; }
 int window_left_tiles(int64_t n, int64_t a) { return (int)((n - a + kWlc - 1) / kWlc); }
 int window_right_tiles(int64_t rows) { return (int)((rows + kWrr - 1) / kWrr); }
 
-template <int P>
-static void set_t(int64_t n, double *T, int64_t ldt, double *Q, int64_t ldq, int kmax,
-                  const WinDesc *wl, int ctas_l, const WinDesc *wr, int ctas_r,
-                  const WinDesc *wq, int ctas_q, int nwin, const double *Z, cudaStream_t st,
-                  cudaStream_t qst) {
-    const size_t sl = sizeof(double) * ((size_t)kWlc * kmax + (size_t)kWzc * (kmax + 1));
-    const size_t sr = sizeof(double) * ((size_t)kWrr * kmax + (size_t)kWzc * (kmax + 1));
-    constexpr int PL = (P + 3) / 4;   // left: k <= 32 PL; right: k <= 8 P
-    cudaFuncSetAttribute(k_win_left_set<PL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sl);
-    cudaFuncSetAttribute(k_win_right_set<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sr);
-    if (Q && ctas_q > 0)
-        k_win_right_set<P><<<ctas_q, 256, sr, qst>>>(n, Q, ldq, true, wq, nwin, Z);
-    k_win_left_set<PL><<<ctas_l, 256, sl, st>>>(n, T, ldt, wl, nwin, Z);
-    k_win_right_set<P><<<ctas_r, 256, sr, st>>>(n, T, ldt, false, wr, nwin, Z);
+// Kernel variant of a window of k rows: the right update's columns per
+// thread P (k <= 8 P); the left update's rows per lane are (P + 3) / 4.
+// A window takes the smallest variant that holds it, so that no thread
+// multiplies columns past k (the FP64 pipe would run them all the same).
+int window_class(int k) {
+    return k <= 32 ? 4 : k <= 64 ? 8 : k <= 128 ? 16 : k <= 160 ? 20 : 32;
 }
 
-// The set's left updates of T, then its right updates, on st; its Q
-// updates on qst.  wl / wr / wq: device descriptor tables whose cta0 count
-// the left tiles, T's right tiles and Q's right tiles; kmax: the largest k.
-// Returns the kernels launched.
-int window_update_set(int64_t n, double *T, int64_t ldt, double *Q, int64_t ldq, int kmax,
-                      const WinDesc *wl, int ctas_l, const WinDesc *wr, int ctas_r,
-                      const WinDesc *wq, int ctas_q, int nwin, const double *Z, cudaStream_t st,
-                      cudaStream_t qst) {
-    if (nwin <= 0 || kmax <= 0) return 0;
-    if (kmax <= 32)
-        set_t<4>(n, T, ldt, Q, ldq, kmax, wl, ctas_l, wr, ctas_r, wq, ctas_q, nwin, Z, st, qst);
-    else if (kmax <= 64)
-        set_t<8>(n, T, ldt, Q, ldq, kmax, wl, ctas_l, wr, ctas_r, wq, ctas_q, nwin, Z, st, qst);
-    else if (kmax <= 128)
-        set_t<16>(n, T, ldt, Q, ldq, kmax, wl, ctas_l, wr, ctas_r, wq, ctas_q, nwin, Z, st, qst);
-    else
-        set_t<32>(n, T, ldt, Q, ldq, kmax, wl, ctas_l, wr, ctas_r, wq, ctas_q, nwin, Z, st, qst);
-    return Q ? 3 : 2;
+template <int P>
+static void set_left_t(int64_t n, double *T, int64_t ldt, int kmax, const WinDesc *wl, int ctas,
+                       int nwin, const double *Z, cudaStream_t st) {
+    constexpr int PL = (P + 3) / 4;
+    const size_t sl = sizeof(double) * ((size_t)kWlc * kmax + (size_t)kWzc * (kmax + 1));
+    cudaFuncSetAttribute(k_win_left_set<PL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sl);
+    k_win_left_set<PL><<<ctas, 256, sl, st>>>(n, T, ldt, wl, nwin, Z);
+}
+
+template <int P>
+static void set_right_t(int64_t n, double *C, int64_t ld, bool q, int kmax, const WinDesc *wr,
+                        int ctas, int nwin, const double *Z, cudaStream_t st) {
+    const size_t sr = sizeof(double) * ((size_t)kWrr * kmax + (size_t)kWzc * (kmax + 1));
+    cudaFuncSetAttribute(k_win_right_set<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sr);
+    k_win_right_set<P><<<ctas, 256, sr, st>>>(n, C, ld, q, wr, nwin, Z);
+}
+
+// The left updates of a set of disjoint windows of one class (wl: their
+// descriptor table, cta0 counting left tiles; kmax: their largest k).
+void window_set_left(int pclass, int64_t n, double *T, int64_t ldt, int kmax, const WinDesc *wl,
+                     int ctas, int nwin, const double *Z, cudaStream_t st) {
+    if (ctas <= 0) return;
+    switch (pclass) {
+    case 4: set_left_t<4>(n, T, ldt, kmax, wl, ctas, nwin, Z, st); break;
+    case 8: set_left_t<8>(n, T, ldt, kmax, wl, ctas, nwin, Z, st); break;
+    case 16: set_left_t<16>(n, T, ldt, kmax, wl, ctas, nwin, Z, st); break;
+    case 20: set_left_t<20>(n, T, ldt, kmax, wl, ctas, nwin, Z, st); break;
+    default: set_left_t<32>(n, T, ldt, kmax, wl, ctas, nwin, Z, st); break;
+    }
+}
+
+// Their right updates of C = T (q false: rows a + k) or Q (q true: n rows).
+void window_set_right(int pclass, int64_t n, double *C, int64_t ld, bool q, int kmax,
+                      const WinDesc *wr, int ctas, int nwin, const double *Z, cudaStream_t st) {
+    if (ctas <= 0) return;
+    switch (pclass) {
+    case 4: set_right_t<4>(n, C, ld, q, kmax, wr, ctas, nwin, Z, st); break;
+    case 8: set_right_t<8>(n, C, ld, q, kmax, wr, ctas, nwin, Z, st); break;
+    case 16: set_right_t<16>(n, C, ld, q, kmax, wr, ctas, nwin, Z, st); break;
+    case 20: set_right_t<20>(n, C, ld, q, kmax, wr, ctas, nwin, Z, st); break;
+    default: set_right_t<32>(n, C, ld, q, kmax, wr, ctas, nwin, Z, st); break;
+    }
 }
 
 template <int P>
@@ -240,6 +256,7 @@ static void right(int64_t rows, double *C, int64_t ld, int64_t a, int k, const d
     if (k <= 32) right_t<4>(rows, C, ld, a, k, Z, st);
     else if (k <= 64) right_t<8>(rows, C, ld, a, k, Z, st);
     else if (k <= 128) right_t<16>(rows, C, ld, a, k, Z, st);
+    else if (k <= 160) right_t<20>(rows, C, ld, a, k, Z, st);
     else right_t<32>(rows, C, ld, a, k, Z, st);
 }
 
@@ -251,6 +268,7 @@ int window_update_t(int64_t n, double *T, int64_t ldt, int64_t a, int k, const d
     if (k <= 32) left_t<1>(n, T, ldt, a, k, Z, st);
     else if (k <= 64) left_t<2>(n, T, ldt, a, k, Z, st);
     else if (k <= 128) left_t<4>(n, T, ldt, a, k, Z, st);
+    else if (k <= 160) left_t<5>(n, T, ldt, a, k, Z, st);
     else left_t<8>(n, T, ldt, a, k, Z, st);
     right(a + k, T, ldt, a, k, Z, st);
     return 2;
