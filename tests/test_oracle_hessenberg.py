@@ -58,8 +58,9 @@ def test_already_hessenberg_is_left_alone():
     assert np.array_equal(H, A) and np.array_equal(Q, np.eye(n)) and np.all(tau == 0.0)
 
 
-@pytest.mark.parametrize("k", [-300, 200])
+@pytest.mark.parametrize("k", [-900, -300, 200, 900])
 def test_power_of_two_scaling(k):
+    # (the GPU test at 2^+-900 compares the scaled results with this oracle)
     A = _rand(60, 11)
     H, Q, tau = oracle.hessenberg(A)
     H2, Q2, tau2 = oracle.hessenberg(np.ldexp(A, k))
@@ -88,3 +89,4 @@ def test_errors():
     with pytest.raises(oracle.OracleError) as ei:
         oracle.hessenberg(bad)
     assert ei.value.status == oracle.EINVAL
+
