@@ -183,8 +183,9 @@ int window_right_tiles(int64_t rows) { return (int)((rows + kWrr - 1) / kWrr); }
 
 // Kernel variant of a window of k rows: the right update's columns per
 // thread P (k <= 8 P); the left update's rows per lane are (P + 3) / 4.
-// A window takes the smallest variant that holds it, so that no thread
-// multiplies columns past k (the FP64 pipe would run them all the same).
+// A window takes the smallest variant that holds it: a thread's columns
+// past k are multiplied all the same (the FP64 pipe runs them like the
+// others), so a variant twice too large costs twice the time.
 int window_class(int k) {
     return k <= 32 ? 4 : k <= 64 ? 8 : k <= 128 ? 16 : k <= 160 ? 20 : 32;
 }
