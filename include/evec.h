@@ -7,7 +7,7 @@
  * Schur form T (1x1 diagonal blocks for real eigenvalues, 2x2 blocks for
  * complex-conjugate pairs) and optionally its orthogonal factor Q, solve
  * (T - lambda_i I) y_i = 0 by backsubstitution for every selected eigenvalue
- * and return x_i = Q y_i.  The solve is robust (Sec. 3.4): no intermediate
+ * and return x_i = Q y_i.  The solve is robust (Sec. 3.3, "Robust computation of eigenvectors"): no intermediate
  * or final value overflows, because every tile segment of every column
  * carries an integer power-of-two scale factor (the augmented tile
  * <alpha, X> represents y_j = x_j / alpha_j) and every tile update
@@ -38,7 +38,7 @@
  *   max_i |X[i, p]| + |X[i, p+1]| lies in [1, 2) and both columns share one
  *   exponent).  scale_exp is int32 (the paper's 32-bit scale exponents).
  *   Entries far below the column maximum may underflow to subnormal or zero
- *   when the final consolidation (Sec. 3.4, post-processing) brings every
+ *   when the final consolidation (Sec. 3.3, post-processing) brings every
  *   segment of a column to one common exponent.
  * - The block part of each eigenvector is fixed: y_p = 1 for a 1x1 block at
  *   p; for a pair, (y_p, y_p+1) = (1, i w / b) when |b| >= |c|, otherwise
@@ -192,7 +192,7 @@ evec_status evec_hessenberg(evec_handle h, int64_t n, double *A, int64_t lda, do
                             int64_t ldq, const evec_opts *opt);
 
 /*
- * Off-diagonal updates of eigenvalue reordering (Sec. 3: a window task
+ * Off-diagonal updates of eigenvalue reordering (Sec. 3.2: a window task
  * accumulates the local transformations of a diagonal window into an
  * orthogonal k x k matrix Z; the left and right update tasks apply it to
  * the off-diagonal sections as level-3 products).  Windows are applied in
@@ -346,7 +346,7 @@ evec_status evec_generalized(evec_handle h, int64_t n, const double *S, int64_t 
 
 /*
  * Robust triangular solve with many right-hand sides (the LAPACK xLATRS
- * generalisation the eigenvector solve of Sec. 3.4 rests on): for every
+ * generalisation the eigenvector solve of Sec. 3.3 rests on): for every
  * column b_j of B, the solution of T x_j = b_j, returned as
  *   x_j = X[:, j] * 2^(-scale_exp[j]),  max_i |X[i, j]| in [1, 2)
  * (X[:, j] = 0 and scale_exp[j] = 0 for b_j = 0), computed by the tiled

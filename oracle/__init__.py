@@ -9,7 +9,7 @@ Functions return numpy arrays; matrices are float64 column-major.  The
 canonical output is X with |X[:, j]|_inf in [1, 2) (pairs share one exponent
 and use max_i |re_i| + |im_i|), and the true eigenvector is
 X[:, j] * 2**(-scale_exp[j])  (y_j = x_j / alpha_j with alpha_j =
-2**scale_exp[j], the augmented representation of Sec. 3.4).
+2**scale_exp[j], the augmented representation of Sec. 3.3).
 """
 from __future__ import annotations
 

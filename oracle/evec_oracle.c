@@ -16,28 +16,29 @@
  *   - the Hessenberg reduction A = Q H Q^T that precedes the Schur form
  *     (Sec. 3.1), by one Householder reflector per column applied from
  *     both sides, unblocked
- *   - the off-diagonal updates of eigenvalue reordering (Sec. 3, the
+ *   - the off-diagonal updates of eigenvalue reordering (Sec. 3.2, the
  *     window, left-update and right-update tasks): each window's
  *     accumulated orthogonal transform Z applied as T <- Zhat^T T Zhat,
  *     Q <- Q Zhat (Zhat = I with Z on the window), window by window
  *   - the robust triangular solve with many right-hand sides that the
- *     eigenvector solve generalises (Sec. 3.4, the LAPACK xLATRS lineage):
+ *     eigenvector solve generalises (Sec. 3.3, the LAPACK xLATRS lineage):
  *     T x_j = b_j for every column of B, each x_j = X[:, j] / 2^scale_exp[j]
  *   - robustness: every intermediate and final value stays in range; the
  *     vector is returned as  y = x / alpha  with alpha an integer power of
- *     two (the augmented representation of Sec. 3.4), the exponent held in a
- *     32-bit signed integer (Sec. 3.4, last paragraph).
+ *     two (the augmented representation of Sec. 3.3, "Robust computation of
+ *     eigenvectors"), the exponent held in a
+ *     32-bit signed integer (Sec. 3.3, last paragraph).
  *
  * Only tests/, the smoke check and the CPU-baseline leg of the benchmark may
  * load this library.  It shares no code with the CUDA path.
  *
  * One column at a time, one scale exponent per column (LAPACK xLATRS style,
- * Sec. 3.4): no tiling, no blocking.  OpenMP runs independent columns in
+ * Sec. 3.3): no tiling, no blocking.  OpenMP runs independent columns in
  * parallel; every column is computed by the same sequential code, so the
  * result does not depend on the thread count.
  *
  * Readings where the paper is silent (the paper states only the guarantee
- * "no overflow", Sec. 3.4):
+ * "no overflow", Sec. 3.3):
  *   OMEGA = 2^1020 is the overflow threshold for every intermediate value;
  *   inputs must satisfy |entry| <= 2^1000, so that any row sum of n <= 2^20
  *   entries stays below OMEGA.
@@ -192,7 +193,7 @@ static int64_t small_solve(int k, const double *mr, const double *mi,
 }
 
 /*
- * Update protection (Sec. 3.4: the preprocessing that makes z = y - T x
+ * Update protection (Sec. 3.3: the preprocessing that makes z = y - T x
  * safe).  Given nu = |r|_inf <= OMEGA, tau = |B|_inf <= OMEGA and
  * mu = |z|_inf, return q <= 0 such that 2^q nu + tau 2^q mu <= OMEGA.
  */
@@ -1162,7 +1163,7 @@ int evo_hessenberg(int64_t n, double *A, int64_t lda, double *Q, int64_t ldq, do
 
 
 /*
- * Eigenvalue reordering's off-diagonal updates (Sec. 3: a window task
+ * Eigenvalue reordering's off-diagonal updates (Sec. 3.2: a window task
  * gathers its local transformations in an accumulator matrix; the left and
  * right update tasks then apply it to the off-diagonal sections).  Windows
  * are applied in the order given; window w covers rows and columns

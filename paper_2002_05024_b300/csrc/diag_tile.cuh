@@ -589,7 +589,7 @@ __device__ void diag_tile(int s, int list_pos0, const double *__restrict__ T, in
             if (C) Y[(t0 + i) + (int64_t)(c + 1) * ldy] = yi[i * ys + uu];
         }
     }
-    // consolidation + protection decisions (Sec. 3.4): thread -> (unit,
+    // consolidation + protection decisions (Sec. 3.3): thread -> (unit,
     // tile row), consecutive threads on consecutive columns; four items per
     // thread per round so their loads are in flight together
     // (decide == false: a separate launch takes them, k_decide)

@@ -1445,7 +1445,7 @@ evec_status evec_standard(evec_handle h, int64_t n, const double *T, int64_t ldt
 }
 
 // Robust triangular solve with many right-hand sides (the xLATRS
-// generalisation the eigenvector solve rests on, Sec. 3.4): the same tiled
+// generalisation the eigenvector solve rests on, Sec. 3.3): the same tiled
 // steps with shift 0 and the right-hand sides as the starting segments.
 evec_status evec_trsolve(evec_handle h, int64_t n, const double *T, int64_t ldt, int64_t nrhs,
                          const double *B, int64_t ldb, double *X, int64_t ldx,

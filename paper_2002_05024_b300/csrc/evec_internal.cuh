@@ -7,7 +7,7 @@
 //                         major: index r * m + j.  Segment (r, j) is the part
 //                         of column j in the rows of tile r; it holds
 //                         y_true = Y * 2^(-seg_e) (the augmented tile
-//                         <alpha, X> of Sec. 3.4 with alpha = 2^seg_e).
+//                         <alpha, X> of Sec. 3.3 with alpha = 2^seg_e).
 //   tau [N x N]           tau[r * N + s] = |T_rs|_inf for r < s
 //   blk_tau [nblk]        |T[tile start : q, block q]|_inf inside the tile
 // Units: one unit per selected real eigenvalue (one column) or selected
@@ -133,7 +133,7 @@ __device__ __forceinline__ int ilog2_abs(double x) {
     return ex - 1023;
 }
 
-// Update protection (Sec. 3.4: before Z <- Y - T X, scale so the result
+// Update protection (Sec. 3.3: before Z <- Y - T X, scale so the result
 // cannot exceed the threshold).  nu = |y|, tau = |T|, mu = |x|, with
 // nu <= Omega and tau <= Omega.  Returns q <= 0 such that
 // 2^q nu + tau 2^q mu <= Omega.

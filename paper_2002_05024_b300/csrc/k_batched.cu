@@ -3,7 +3,7 @@
 // Each CTA (4 warps) takes the next matrix from a device work queue (an
 // atomic counter over the matrices, which the host orders by decreasing
 // estimated work, so the longest solves start first) and runs the whole
-// tiled robust solve of Sec. 3.4 for it on its own: tile norms and input
+// tiled robust solve of Sec. 3.3 for it on its own: tile norms and input
 // validation, then for s = N-1 .. 0 the diagonal-tile solves of every
 // active unit (the same device code as the per-step kernel, in chunks of
 // 16 real or 8 complex units) followed by the updates Y_r <- 2^dy Y_r -

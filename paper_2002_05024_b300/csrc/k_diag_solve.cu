@@ -1,6 +1,6 @@
 // k_diag_solve.cu -- robust shifted solves on one diagonal tile (Eq. evec_solve
 // restricted to the rows of tile s), then the consolidation/protection
-// decisions for every tile above it (Sec. 3.4, the preprocessing step of the
+// decisions for every tile above it (Sec. 3.3, the preprocessing step of the
 // update Z <- Y - T X).
 //
 // Work split: G lanes per unit -- G = 8 for a real eigenvalue, G = 16 for a

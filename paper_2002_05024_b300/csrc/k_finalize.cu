@@ -1,4 +1,4 @@
-// k_finalize.cu -- the post-processing of Sec. 3.4: all segments of each
+// k_finalize.cu -- the post-processing of Sec. 3.3: all segments of each
 // column brought to one consistent scaling, in canonical form.
 //
 // Segment r of column j holds y_true = Y * 2^(-e_r).  With

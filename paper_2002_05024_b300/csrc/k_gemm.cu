@@ -1,6 +1,6 @@
 // k_gemm.cu -- the dense contractions of the method, in FP64 on the DFMA pipe.
 //
-// tile update (Sec. 3.4, the single level-3 operation of Z <- Y - T X):
+// tile update (Sec. 3.3, the single level-3 operation of Z <- Y - T X):
 //   for every tile r < s and every active column j (its block in tile >= s)
 //     Y_r[:, j] <- 2^dy[r, j] Y_r[:, j] - T_rs (2^dx[r, j] X_s[:, j])
 //   with dy / dx from the diagonal-tile kernel (dy = fresh: Y_r[:, j] has not

@@ -1,4 +1,4 @@
-// k_norms.cu -- input gathering and tile norms (the bounds of Sec. 3.4).
+// k_norms.cu -- input gathering and tile norms (the bounds of Sec. 3.3).
 //
 // tau[r * N + s] = |T_rs|_inf (largest row sum of |T| over the rows of tile
 // r and the columns of tile s, r < s) bounds every off-diagonal tile update

@@ -25,7 +25,7 @@
 // bounded; a wait that gives up sets *err and the roles stop issuing work.
 //
 // Two epilogues: the back-transformation writes C = 2^(ea + eb) (A B); the
-// tile update of step s (Sec. 3.4, Z <- Y - T X) applies, per row i (tile
+// tile update of step s (Sec. 3.3, Z <- Y - T X) applies, per row i (tile
 // row r) and column j, Y_ij <- 2^dy[r, j] Y_ij - 2^(ea_i + eb_j + dx[r, j])
 // (A~ B~)_ij and merges |Y_ij| into the column maximum of segment (r, j)
 // (shared-memory maxima per CTA, one global atomicMax per (r, j) and CTA).

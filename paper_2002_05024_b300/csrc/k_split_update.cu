@@ -1,5 +1,5 @@
 // k_split_update.cu -- the tile update of one step of the tiled
-// backsubstitution (Sec. 3.4: Y_r <- 2^dy Y_r - T_rs (2^dx X_s) for every
+// backsubstitution (Sec. 3.3: Y_r <- 2^dy Y_r - T_rs (2^dx X_s) for every
 // tile row r above the diagonal tile s, with the column maxima of the new
 // segments) as split-precision products on the BF16 tensor cores.
 //

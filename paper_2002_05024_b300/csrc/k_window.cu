@@ -1,4 +1,4 @@
-// k_window.cu -- the off-diagonal updates of eigenvalue reordering (Sec. 3:
+// k_window.cu -- the off-diagonal updates of eigenvalue reordering (Sec. 3.2:
 // a window task gathers the local transformations of a diagonal window in
 // an accumulator matrix Z; the left and right update tasks then apply it to
 // the off-diagonal sections as level-3 products).  For a window of k rows

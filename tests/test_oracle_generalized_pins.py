@@ -1,5 +1,5 @@
 """Pins for the oracle's generalized path, (S - lambda T) y = 0 in
-homogeneous form (beta S - alpha T) y = 0 (Sec. 2, Eq. evec_solve; Sec. 3.4
+homogeneous form (beta S - alpha T) y = 0 (Sec. 2, Eq. evec_solve; Sec. 3.3
 for the robust scaling; the generalized solver is the subject of the
 paper's reference [ppam2019cckm])."""
 import numpy as np

@@ -1,6 +1,6 @@
 """Pins for the oracle's left eigenvectors: u^H S = lambda u^H, the
 eigenvector problem of Sec. 2 for S^T, by robust forward substitution
-(Sec. 3.4's protection applied in the other direction).  Closed forms,
+(Sec. 3.3's protection applied in the other direction).  Closed forms,
 LAPACK's left eigenvectors, biorthogonality with the right eigenvectors,
 arbitrary-precision brute force (the right-eigenvector reference on the
 flipped matrix J S^T J), an overflow witness and metamorphic relations.

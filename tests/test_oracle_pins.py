@@ -3,7 +3,7 @@ in arbitrary precision, a library special case, overflow witnesses and
 metamorphic relations.  None of these re-types the oracle's formulas: each
 compares it with something the mathematics fixes independently.
 
-Paper: Sec. 2 (Eq. evec_solve, Eq. evec_backtransform); Sec. 3.4 (robust
+Paper: Sec. 2 (Eq. evec_solve, Eq. evec_backtransform); Sec. 3.3 (robust
 computation of eigenvectors: augmented representation y = x / alpha,
 power-of-two scale factors, no overflow).
 """

@@ -1,6 +1,6 @@
 """Pins for the oracle's robust triangular solve (T x_j = b_j for every
 column of B, the xLATRS generalisation the eigenvector solve rests on,
-Sec. 3.4): library solvers on well-conditioned inputs, closed forms,
+Sec. 3.3): library solvers on well-conditioned inputs, closed forms,
 arbitrary-precision brute force on a matrix whose unscaled solve overflows,
 and exact power-of-two relations.  Output convention: x_j = X[:, j] *
 2**(-scale_exp[j]) with |X[:, j]|_inf in [1, 2)."""

@@ -1,7 +1,7 @@
 """Pins for the oracle's eigenvalue-reordering off-diagonal updates
 (oracle.window_update: each window's accumulated orthogonal transform Z
 applied as T <- Zhat^T T Zhat, Q <- Q Zhat; the left and right update
-tasks of the paper's reordering phase, Sec. 3).  Each pin is fixed by the
+tasks of the paper's reordering phase, Sec. 3.2).  Each pin is fixed by the
 mathematics, not by the oracle's own formula: the identity, exact
 permutations by index arithmetic, the invariant Q T Q^T of an orthogonal
 similarity, disjoint windows commuting, untouched regions, eigenvalues of a
