@@ -1,21 +1,31 @@
 #!/usr/bin/env python
 """Benchmark of the robust eigenvector path on one B300 (replicas across GPUs).
 
-Workload (one step = the whole path once): all eigenvectors of an n = 4096
-real Schur form drawn from the config-0 distribution (75% real 1x1 blocks,
-25% standardized 2x2 blocks, strictly upper part N(0, 1)), back-transformed
-by an orthogonal Q (product of 64 Householder reflectors), FP64 throughout.
-Inputs are seeded and synthetic; T, Q and X are 128 MiB each, larger than L2.
+Workload (one step = the whole path once): all 16384 eigenvectors of an
+n = 16384 real Schur form drawn from the config-0 distribution (75% real 1x1
+blocks, 25% standardized 2x2 blocks, strictly upper part N(0, 1)),
+back-transformed by an orthogonal Q (product of 64 Householder reflectors).
+The timed steps run the FP64 path (DFMA throughout); the same line carries,
+under "records", the split-precision path on the same input (8 BF16 digit
+slices on the tensor cores, FP32 exact accumulation, FP64 recombination,
+then one FP64 residual-correction sweep; also without the sweep) and the
+batched workload (2000 Schur forms of n in [32, 1024] in one persistent
+launch, FP64 and split), each with its rate, residuals and ratio to the
+plain FP64 path.  Inputs are seeded and synthetic; T, Q and X are 2 GiB
+each, larger than L2.
 
 Metric: eigenvector columns per second (and achieved FP64 TFLOPS with the
 algorithmic count F = sum_j [k_j^2 + 2 n (k_j + b_j)], k_j rows above the
-column's block, b_j its size).
+column's block, b_j its size); split and batched against the plain FP64
+path at normalised residual <= 10 n.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 --impl reference times the CPU oracle (the plain column-by-column robust
 substitution) on the machine's host cores, each step a bounded random sample of
-the same workload's columns.
+the same workload's columns, extrapolated to all columns by the flop count.
+Other workloads: --workload batched | generalized | trsolve |
+batched_generalized | hessenberg | window, --side left.
 """
 from __future__ import annotations
 
@@ -54,21 +64,32 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--n", type=int, default=4096)
+    ap.add_argument("--n", type=int, default=0,
+                    help="order (default: 16384 for the right eigenvectors, 8192 for the "
+                         "generalized workload, 4096 otherwise)")
     ap.add_argument("--tile", type=int, default=0)
-    ap.add_argument("--mode", choices=["fp64", "split"], default="split")
+    ap.add_argument("--mode", choices=["fp64", "split"], default="fp64")
     ap.add_argument("--slices", type=int, default=0)
     ap.add_argument("--refine", action="store_true",
                     help="split mode: one FP64 residual-correction sweep after the solve")
-    ap.add_argument("--cpu-sample", type=int, default=4096,
-                    help="columns of the CPU-oracle sample")
+    ap.add_argument("--cpu-sample", type=int, default=0,
+                    help="columns of the CPU-oracle sample (default 512 at n >= 8192, "
+                         "else 4096)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-records", dest="records", action="store_false",
+                    help="single workload, FP64: leave out the split and batched records")
+    ap.add_argument("--record-steps", type=int, default=3,
+                    help="timed steps of the split records")
+    ap.add_argument("--residual-cols", type=int, default=512,
+                    help="columns whose residual the line reports")
+    ap.add_argument("--profile-steps", type=int, default=0,
+                    help="extra steps timed kernel by kernel (default 1 at n >= 8192, else 3)")
     ap.add_argument("--workload", choices=["single", "batched", "generalized", "trsolve",
                                            "batched_generalized", "hessenberg", "window"],
                     default="single",
                     help="single: one n x n Schur form with Q (default); batched: the "
                          "2000-matrix batch of evec_batched; generalized: an n x n pencil "
-                         "(S, T) with Z (use --n 8192); trsolve: robust solve of an n x n "
+                         "(S, T) with Z; trsolve: robust solve of an n x n "
                          "quasi-triangular T with --nrhs right-hand sides; "
                          "batched_generalized: --batch pencils in one persistent launch")
     ap.add_argument("--nrhs", type=int, default=0, help="trsolve: right-hand sides (default n)")
@@ -79,7 +100,19 @@ def parse_args():
     ap.add_argument("--side", choices=["right", "left"], default="right",
                     help="single: right eigenvectors (default) or left ones (u^H T = lambda u^H)")
     ap.add_argument("--batch", type=int, default=2000)
-    return ap.parse_args()
+    args = ap.parse_args()
+    if not args.n:
+        args.n = (16384 if args.workload == "single" and args.side == "right" else
+                  8192 if args.workload == "generalized" else 4096)
+    if not args.cpu_sample:
+        args.cpu_sample = 512 if args.n >= 8192 else 4096
+    if not args.profile_steps:
+        args.profile_steps = 1 if args.n >= 8192 else 3
+    return args
+
+
+METRIC_SINGLE = ("eigvec columns/s (robust eigenvectors incl. back-transformation X = Q Y); "
+                 "TFLOPS vs the FP64 roofline; split/batched vs plain at residual <= 10 n")
 
 
 def workload(n):
@@ -287,12 +320,98 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(T, blocks, Q, sample_cols, seed=5, gpu=None, left=False):
+def block_columns(blocks):
+    """First output column of every block (all eigenvalues selected)."""
+    out, c = [], 0
+    for _, sz in blocks:
+        out.append(c)
+        c += sz
+    return out
+
+
+def pick_eigenvalues(blocks, k, seed):
+    """Seeded random blocks until they hold at least k columns."""
+    rng = np.random.default_rng(seed)
+    pick, cols = [], 0
+    for b in rng.permutation(len(blocks)):
+        if cols >= k:
+            break
+        pick.append(int(b))
+        cols += blocks[b][1]
+    return sorted(pick)
+
+
+def sample_flops(n, blocks, sel, with_q):
+    """The method's flops F = sum_j [k_j^2 + 2 n (k_j + b_j) [Q]] over the
+    selected columns."""
+    f = 0.0
+    for p, sz in blocks:
+        if sel is None or sel[p]:
+            f += sz * (float(p) * p + (2.0 * n * (p + sz) if with_q else 0.0))
+    return f
+
+
+def compare_columns(Xa, ea, Xb, eb, lam_im):
+    """Canonical columns a (reference) and b: per eigenvalue the exponent
+    difference and the normwise relative difference after bringing b to a's
+    exponent (a pair: row norms |re| + |im|).  Returns (max |exponent
+    difference|, max and median relative difference)."""
+    m = Xa.shape[1]
+    rels, max_de = [], 0
+    j = 0
+    step = 512
+    while j < m:
+        j1 = min(m, j + step)
+        if j1 < m and lam_im[j1 - 1] > 0:   # keep a pair together
+            j1 += 1
+        de = ea[j:j1].astype(np.int64) - eb[j:j1].astype(np.int64)
+        A = Xa[:, j:j1]
+        B = np.ldexp(Xb[:, j:j1], de.astype(np.int32))
+        D = np.abs(A - B)
+        N = np.abs(A)
+        c = 0
+        while c < j1 - j:
+            if lam_im[j + c] != 0.0:
+                rels.append((D[:, c] + D[:, c + 1]).max() / (N[:, c] + N[:, c + 1]).max())
+                max_de = max(max_de, abs(int(de[c])))
+                c += 2
+            else:
+                rels.append(D[:, c].max() / N[:, c].max())
+                max_de = max(max_de, abs(int(de[c])))
+                c += 1
+        j = j1
+    rels = np.asarray(rels) if rels else np.zeros(1)
+    return max_de, float(rels.max()), float(np.median(rels))
+
+
+def normalised_residuals(T, X, lr, li):
+    """||T x - lambda x||_1 / (||T||_1 ||x||_1 u) per eigenvalue (FP64)."""
+    T1 = np.abs(T).sum(axis=0).max()
+    R = T @ X
+    out = []
+    j = 0
+    while j < X.shape[1]:
+        if li[j] != 0.0:
+            x = X[:, j] + 1j * X[:, j + 1]
+            r = (R[:, j] + 1j * R[:, j + 1]) - (lr[j] + 1j * li[j]) * x
+            j += 2
+        else:
+            x = X[:, j]
+            r = R[:, j] - lr[j] * x
+            j += 1
+        out.append(np.abs(r).sum() / (T1 * np.abs(x).sum() * 2.0 ** -53))
+    return np.asarray(out)
+
+
+def cpu_baseline(T, blocks, Q, sample_cols, seed=5, gpu=None, left=False, flops=None):
     """The oracle, as it stands, on a seeded random sample of the workload's
-    columns, on all host cores.  With gpu = (X, scale_exp) of the timed run,
-    the sampled columns are also compared with the GPU's (largest exponent
-    difference and normwise relative difference after bringing both to one
-    exponent)."""
+    columns, on all host cores.  flops = (n, with_q): the rate is
+    extrapolated from the sample to the whole workload by the method's flop
+    count (sum over all columns / sum over the sampled ones), and the
+    oracle's result comes back with it: (record, (X, scale_exp, mask)).
+    With gpu = (X, scale_exp) of the timed run, the sampled columns are also
+    compared with the GPU's (largest exponent difference and normwise
+    relative difference after bringing both to one exponent)."""
     import oracle
     n = T.shape[0]
     rng = np.random.default_rng(seed)
@@ -316,60 +435,47 @@ def cpu_baseline(T, blocks, Q, sample_cols, seed=5, gpu=None, left=False):
            "sample": f"{X.shape[1]} randomly chosen columns (seed {seed}) of the n={n} "
                      f"workload incl. back-transformation"
                      + (" (left eigenvectors)" if left else "") + f", {dt:.2f} s"}
+    if flops is not None:
+        m = sum(sz for _, sz in blocks)
+        f_all = sample_flops(n, blocks, None, flops[1])
+        f_smp = sample_flops(n, blocks, sel, flops[1])
+        out["value"] = m / (dt * f_all / f_smp)
+        out["extrapolated"] = True
+        out["sample_columns_per_s"] = X.shape[1] / dt
+        out["sample"] += (f"; extrapolated to all {m} columns by the flop count "
+                          f"({f_all:.3e} / {f_smp:.3e})")
     if gpu is not None:
         Xg, eg = gpu
-        col, oc, max_de, max_rel = 0, 0, 0, 0.0
-        for p, sz in blocks:
-            if sel[p]:
-                de = int(e[oc]) - int(eg[col])
-                a = X[:, oc:oc + sz]
-                b = np.ldexp(Xg[:, col:col + sz], de)
-                rel = np.max(np.abs(a - b).sum(axis=1)) / np.max(np.abs(a).sum(axis=1))
-                max_de, max_rel = max(max_de, abs(de)), max(max_rel, float(rel))
-                oc += sz
-            col += sz
-        out["gpu_vs_oracle"] = {"columns": oc, "max_exponent_diff": max_de,
-                                "max_rel_diff": max_rel}
+        cidx = [c + k for c, (p, sz) in zip(block_columns(blocks), blocks) if sel[p]
+                for k in range(sz)]
+        de, rel, med = compare_columns(X, e, Xg[:, cidx], eg[cidx], li)
+        out["gpu_vs_oracle"] = {"columns": len(cidx), "max_exponent_diff": de,
+                                "max_rel_diff": rel, "median_rel_diff": med}
+    if flops is not None:
+        return out, (X, e, sel)
     return out
 
 
-def residual_sample(T, Q, X, lr, li, blocks, k=16, seed=7, left=False):
-    """Normalised residual ||T y - lambda y||_1 / (||T||_1 ||y||_1 u) of k
-    seeded random eigenvalues of the GPU result, y = Q^T x in long double
-    (the Schur-coordinate residual of x; no product with Q enters it).
-    left: the residual of T^T conj(y) = lambda conj(y) (u^H T = lambda u^H)
-    with ||T^T||_1."""
+def residual_sample(T, Q, X, lr, li, blocks, pick, left=False):
+    """Normalised residual ||T y - lambda y||_1 / (||T||_1 ||y||_1 u) of the
+    picked eigenvalues of a GPU result, y = Q^T x (the Schur-coordinate
+    residual of x), in FP64 on the host.  left: the residual of T^T conj(y)
+    = lambda conj(y) (u^H T = lambda u^H) with ||T^T||_1."""
+    starts = block_columns(blocks)
+    cols = [starts[b] + k for b in pick for k in range(blocks[b][1])]
+    Xs = np.array(X[:, cols], dtype=np.float64, order="F")
+    lrs, lis = np.asarray(lr)[cols], np.asarray(li)[cols]
     if left:
         T = np.ascontiguousarray(T.T)
-        X = np.array(X, copy=True)
-        for c in range(X.shape[1]):
-            if li[c] < 0:
-                X[:, c] = -X[:, c]
+        Xs[:, lis < 0] = -Xs[:, lis < 0]
+    Ys = Q.T @ Xs if Q is not None else Xs
+    res = normalised_residuals(T, Ys, lrs, lis)
     n = T.shape[0]
-    rng = np.random.default_rng(seed)
-    starts, col = [], 0
-    for p, sz in blocks:
-        starts.append((col, sz))
-        col += sz
-    pick = rng.choice(len(starts), size=min(k, len(starts)), replace=False)
-    Tl = T.astype(np.longdouble)
-    Ql = Q.astype(np.longdouble)
-    T1 = np.abs(Tl).sum(axis=0).max()
-    worst = 0.0
-    for b in pick:
-        c, sz = starts[b]
-        if sz == 2:
-            x = X[:, c].astype(np.longdouble) + 1j * X[:, c + 1].astype(np.longdouble)
-            lam = np.longdouble(lr[c]) + 1j * np.longdouble(li[c])
-            y = Ql.T @ x.real + 1j * (Ql.T @ x.imag)
-            r = (Tl @ y.real + 1j * (Tl @ y.imag)) - lam * y
-        else:
-            y = Ql.T @ X[:, c].astype(np.longdouble)
-            r = Tl @ y - np.longdouble(lr[c]) * y
-        res = np.abs(r).sum() / (T1 * np.abs(y).sum() * np.finfo(np.float64).eps / 2)
-        worst = max(worst, float(res))
-    return {"eigenvalues": int(len(pick)), "max_normalised_residual": worst,
-            "max_over_n": worst / n, "gate": "<= 10 n"}
+    return {"eigenvalues": int(len(pick)), "columns": len(cols),
+            "max_normalised_residual": float(res.max()),
+            "median_normalised_residual": float(np.median(res)),
+            "max_over_n": float(res.max()) / n, "gate": "<= 10 n",
+            "how": "Schur coordinates y = Q^T x, FP64 on the host"}
 
 
 def run_reference_trsolve(args):
@@ -514,29 +620,40 @@ def run_reference(args, rank, world):
         return run_reference_trsolve(args)
     if args.workload in ("batched", "batched_generalized", "generalized", "hessenberg", "window"):
         return run_reference_other(args)
-    T, blocks, Q = workload(args.n)
-    per_step = max(16, args.cpu_sample // 4)
+    n = args.n
+    T, blocks, Q = workload(n)
+    m = sum(sz for _, sz in blocks)
+    # a bounded sample per step (about 1.5 s of oracle work at n = 16384),
+    # extrapolated to the whole workload by the flop count
+    per_step = 64 if n >= 8192 else max(16, args.cpu_sample // 4)
     times, cols = [], []
     for i in range(args.warmup + args.steps):
-        r = cpu_baseline(T, blocks, Q, per_step, seed=1000 + i, left=args.side == "left")
+        r, _ = cpu_baseline(T, blocks, Q, per_step, seed=1000 + i, left=args.side == "left",
+                            flops=(n, True))
         if i >= args.warmup:
-            cols.append(r["columns"])
-            times.append(r["seconds"])
+            cols.append(m)
+            times.append(m / r["value"])
     value = sum(cols) / sum(times)
     cores = r["cores"]
     line = {
         "impl": "reference",
-        "metric": "eigvec columns/s (robust FP64 eigenvectors incl. back-transformation)",
+        "metric": METRIC_SINGLE,
         "value": value, "unit": "columns/s", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": f"config-0 Schur form n={args.n} + Q, all columns"
-                               + (", left eigenvectors" if args.side == "left" else "")
-                               + " (oracle samples)"},
+        "config": {"workload": f"single large Schur form: n={n} real Schur form (config-0 "
+                               "distribution) + Q (product of 64 Householder reflectors), all "
+                               f"{m} " + ("left eigenvectors" if args.side == "left" else
+                                          "eigenvectors")
+                               + "; the oracle on sampled columns, extrapolated",
+                   "n": n, "columns": m},
         "cpu_baseline": {"value": value, "unit": "columns/s", "cores": cores, "kind": "oracle",
-                         "sample": f"{per_step} random columns per step of the n={args.n} "
-                                   "workload, on the host cores"},
+                         "extrapolated": True,
+                         "sample": f"{per_step} random columns per step of the n={n} "
+                                   "workload, on the host cores; each step's time scaled to "
+                                   "all columns by the flop count (ms_per_step is that "
+                                   "extrapolated time of a whole step)"},
         "e2e": {"value": value, "unit": "columns/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -544,6 +661,12 @@ def run_reference(args, rank, world):
 
 
 def run_ours(args, rank, world, local_rank):
+    """The eigenvector workload: all eigenvectors of one n x n Schur form with
+    Q.  The timed steps run args.mode (FP64 by default); with --records (the
+    default for FP64 right eigenvectors on one GPU) the line also carries the
+    split-precision path on the same input, with and without the FP64
+    residual-correction sweep, and the batched workload in both modes, each
+    with its rate, its quality and its ratio to the plain FP64 path."""
     import ctypes
 
     import torch
@@ -567,7 +690,7 @@ def run_ours(args, rank, world, local_rank):
     F, F_upd, F_bt = flop_counts(n, blocks, tile_start, res=res)
     F_diag = max(F - F_upd - F_bt, 0.0)
     refine = bool(args.refine and args.mode == "split")
-    F_res = res[0] if refine else 0.0
+    F_res = res[0]
 
     dT = torch.from_numpy(T).to(dev)
     dQ = torch.from_numpy(Q).to(dev)
@@ -583,7 +706,8 @@ def run_ours(args, rank, world, local_rank):
     ev.handle(local_rank).lookahead(args.lookahead)
 
     def step():
-        solve(dT, dQ, tile=args.tile, out=out, mode=args.mode, slices=args.slices, refine=refine)
+        solve(dT, dQ, tile=args.tile, out=out, mode=args.mode, slices=args.slices,
+              refine=1 if refine else 0)
 
     for _ in range(args.warmup):
         step()
@@ -612,7 +736,7 @@ def run_ours(args, rank, world, local_rank):
     elapsed_ms = t0.elapsed_time(t1)
     clocks = sampler.stop() if sampler else None
     ev.sync(local_rank)
-    prof = profiled_steps(h, step, args.steps, dev)
+    prof = profiled_steps(h, step, args.steps, dev, k=args.profile_steps)
     elapsed_ms = reduce_over_ranks(elapsed_ms, dist, dev)
 
     ms_per_step = elapsed_ms / args.steps
@@ -624,13 +748,15 @@ def run_ours(args, rank, world, local_rank):
     slices = (args.slices or 8) if args.mode == "split" else 0
     tile = args.tile or 64
     roofs = rooflines(prof, args.steps, args.mode, slices, F_diag, F_upd, F_bt, peaks, n, tile,
-                      F_res=F_res, sweeps=2 if refine else 1, prefix="left:" if left else "")
+                      F_res=F_res if refine else 0.0, sweeps=2 if refine else 1,
+                      prefix="left:" if left else "")
     dominant = max(prof.items(), key=lambda kv: kv[1][0])[0]
     roofline = roofs.get(dominant)
     gpu_launches = sum(c for _, c in prof.values())
 
-    # end to end through the host-buffer entry point (pinned host memory)
+    # end to end through the public API with host buffers (pinned host memory)
     e2e = None
+    e2e_steps = args.steps if n <= 4096 else min(args.steps, 2)
     if left and not os.environ.get("EVEC_BENCH_NO_E2E"):
         # no host-buffer entry point for the left vectors: the public call on
         # device tensors with T and Q copied in from pinned memory and X,
@@ -652,22 +778,6 @@ def run_ours(args, rank, world, local_rank):
             hL[0].copy_(lr, non_blocking=True)
             hL[1].copy_(li, non_blocking=True)
             torch.cuda.synchronize(dev)
-
-        for _ in range(args.warmup):
-            host_step()
-        if dist:
-            dist.barrier()
-        w0 = time.perf_counter()
-        for _ in range(args.steps):
-            host_step()
-        w = time.perf_counter() - w0
-        if dist:
-            tt = torch.tensor([w], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            w = float(tt.item())
-        e2e = {"value": world * m * args.steps / w, "unit": "columns/s",
-               "h2d_bytes_per_step": 2 * n * n * 8,
-               "d2h_bytes_per_step": n * m * 8 + m * 4 + 2 * m * 8}
     elif not os.environ.get("EVEC_BENCH_NO_E2E"):
         pin = lambda shape, dt: torch.empty(shape, dtype=dt, pin_memory=True).numpy()  # noqa: E731
         hT = pin((n, n), torch.float64)
@@ -678,7 +788,7 @@ def run_ours(args, rank, world, local_rank):
         hE = pin((m,), torch.int32)
         hLr = pin((m,), torch.float64)
         hLi = pin((m,), torch.float64)
-        opts = ev._opts(args.tile, False, args.mode, args.slices, refine)
+        opts = ev._opts(args.tile, False, args.mode, args.slices, 1 if refine else 0)
         hh = ev.handle(local_rank)
         P = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
 
@@ -687,54 +797,84 @@ def run_ours(args, rank, world, local_rank):
                                              P(hLr), P(hLi), ctypes.byref(opts))
             if st:
                 raise ev.EvecError(st, "evec_standard_host")
-
-        for _ in range(args.warmup):
-            host_step()
+    if not os.environ.get("EVEC_BENCH_NO_E2E"):
+        host_step()
         if dist:
             dist.barrier()
         w0 = time.perf_counter()
-        for _ in range(args.steps):
+        for _ in range(e2e_steps):
             host_step()
         w = time.perf_counter() - w0
         if dist:
             tt = torch.tensor([w], device=dev)
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
             w = float(tt.item())
-        e2e = {"value": world * m * args.steps / w, "unit": "columns/s",
+        e2e = {"value": world * m * e2e_steps / w, "unit": "columns/s",
                "h2d_bytes_per_step": 2 * n * n * 8,
-               "d2h_bytes_per_step": n * m * 8 + m * 4 + 2 * m * 8}
+               "d2h_bytes_per_step": n * m * 8 + m * 4 + 2 * m * 8,
+               "steps": e2e_steps, "warmup": 1,
+               "entry": "evec_standard_left on device tensors with pinned-memory copies"
+                        if left else "evec_standard_host (C ABI, pinned host buffers)"}
 
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
     Xh, eh = X.cpu().numpy(), e.cpu().numpy()
-    quality = residual_sample(T, Q, Xh, lr.cpu().numpy(), li.cpu().numpy(), blocks, left=left)
+    lrh, lih = lr.cpu().numpy(), li.cpu().numpy()
+    pick = pick_eigenvalues(blocks, args.residual_cols, seed=7)
+    quality = residual_sample(T, Q, Xh, lrh, lih, blocks, pick, left=left)
     cpu = None
+    oracle_ref = None
     if world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(T, blocks, Q, args.cpu_sample, gpu=(Xh, eh), left=left)
+        cpu, oracle_ref = cpu_baseline(T, blocks, Q, args.cpu_sample, gpu=(Xh, eh), left=left,
+                                       flops=(n, True))
         cpu.pop("columns")
         cpu.pop("seconds")
+    records = None
+    if world == 1 and args.records and not left and args.mode == "fp64":
+        records = {}
+        rec_steps = max(1, min(args.steps, args.record_steps))
+        for name, ref in (("split", True), ("split_no_sweep", False)):
+            r = split_record(ev, dev, stream, dT, dQ, T, Q, blocks, m, F, F_upd, F_bt, F_res,
+                             args.tile, ref, rec_steps, max(1, min(args.warmup, 2)), peaks, pick,
+                             oracle_ref, (Xh, eh, lih), left=False)
+            r["vs_plain"] = r["value"] / value
+            records[name] = r
+        records["split_vs_plain"] = records["split"]["vs_plain"]
+        records["split_no_sweep_vs_plain"] = records["split_no_sweep"]["vs_plain"]
+        records["batched"] = batched_record(ev, dev, stream, local_rank, args.batch,
+                                            max(1, min(args.steps, 5)),
+                                            max(1, min(args.warmup, 2)), peaks)
+        records["batched_vs_plain"] = records["batched"]["batched_vs_plain"]
+    if args.mode == "fp64":
+        dtype, how = "f64", "FP64 (DFMA) throughout"
+    else:
+        dtype = "bf16 slice products + f64"
+        how = (f"split precision ({slices} BF16 slices, FP32 exact accumulation, FP64 "
+               "recombination)" + (", then one FP64 residual-correction sweep" if refine else ""))
     line = {
-        "metric": "eigvec columns/s (robust FP64 eigenvectors incl. back-transformation)",
+        "metric": METRIC_SINGLE,
         "value": value, "unit": "columns/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if args.mode == "fp64" else "bf16 slice products + f64",
+        "dtype": dtype,
         "data": "synthetic",
-        "config": {"workload": f"config-0 Schur form n={n} + Q (64 Householder reflectors), "
-                               f"all {m} " + ("left eigenvectors, " if left else "columns, ")
-                               + ("FP64" if args.mode == "fp64" else
-                                  f"split precision ({slices} BF16 slices, FP32 exact "
-                                  "accumulation, FP64 recombination)"
-                                  + (", then one FP64 residual-correction sweep"
-                                     if refine else "")),
+        "config": {"workload": f"single large Schur form: n={n} real Schur form (config-0 "
+                               "distribution: 75% 1x1 blocks, 25% standardized 2x2 blocks, "
+                               "strictly upper N(0, 1)) + Q (product of 64 Householder "
+                               f"reflectors), all {m} "
+                               + ("left eigenvectors; " if left else "eigenvectors; ")
+                               + "timed path: " + how
+                               + ("; the split-precision path with the FP64 residual-correction "
+                                  "sweep, and the 2000-matrix batch, in 'records'"
+                                  if records else ""),
                    "n": n, "columns": m, "tile": args.tile or 64, "mode": args.mode,
-                   "slices": (args.slices or 8) if args.mode == "split" else None,
+                   "slices": slices or None,
                    "refine": refine, "side": args.side,
                    "lookahead": args.lookahead,
                    "parallelism": "replicas",
-                   "l2": "inputs larger than L2 (T, Q, X 128 MiB each)"},
+                   "l2": f"inputs larger than L2 (T, Q, X {n * n * 8 / 2**20:.0f} MiB each)"},
         "tflops_fp64": tflops,
         "quality": quality,
         "flops_per_step": F,
@@ -745,10 +885,149 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clocks,
         "e2e": e2e,
         "cpu_baseline": cpu,
+        "records": records,
     }
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def split_record(ev, dev, stream, dT, dQ, T, Q, blocks, m, F, F_upd, F_bt, F_res, tile, refine,
+                 steps, warmup, peaks, pick, oracle_ref, fp64_out, left=False):
+    """The split-precision path (8 BF16 slices) on the timed workload's
+    input, with or without the FP64 residual-correction sweep: rate, the
+    split kernels' rooflines, the residual on the same sampled eigenvalues as
+    the main line, the difference to the oracle on its sampled columns and
+    to the FP64 GPU result on every column."""
+    import torch
+    n = T.shape[0]
+    X = torch.empty((m, n), dtype=torch.float64, device=dev).t()
+    e = torch.empty(m, dtype=torch.int32, device=dev)
+    lr = torch.empty(m, dtype=torch.float64, device=dev)
+    li = torch.empty(m, dtype=torch.float64, device=dev)
+    out = (X, e, lr, li)
+
+    def step():
+        ev.standard(dT, dQ, tile=tile, out=out, mode="split", slices=8,
+                    refine=1 if refine else 0)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(steps):
+        step()
+    t1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = t0.elapsed_time(t1)
+    ev.sync(dev.index)
+    h = ev.handle(dev.index)
+    prof = profiled_steps(h, step, steps, dev, k=1)
+    F_diag = max(F - F_upd - F_bt, 0.0)
+    roofs = rooflines(prof, steps, "split", 8, F_diag, F_upd, F_bt, peaks, n, tile or 64,
+                      F_res=F_res if refine else 0.0, sweeps=2 if refine else 1)
+    Xh, eh = X.cpu().numpy(), e.cpu().numpy()
+    lrh, lih = lr.cpu().numpy(), li.cpu().numpy()
+    rec = {"value": m * steps / (ms / 1e3), "unit": "columns/s", "steps": steps,
+           "warmup": warmup, "ms_per_step": ms / steps,
+           "tflops_fp64_equivalent": F * steps / (ms / 1e3) / 1e12,
+           "dtype": "bf16 slice products (FP32 exact accumulation) + f64",
+           "path": "split precision, 8 BF16 digit slices per operand, FP64 recombination"
+                   + (", then one FP64 residual-correction sweep" if refine else ""),
+           "quality": residual_sample(T, Q, Xh, lrh, lih, blocks, pick, left=left),
+           "rooflines": roofs,
+           "kernel_ms_per_step": {k: v[0] / steps for k, v in prof.items() if v[0] > 0}}
+    if oracle_ref is not None:
+        Xo, eo, sel = oracle_ref
+        cols = [c for c, (p, sz) in zip(block_columns(blocks), blocks) if sel[p]
+                for c in range(c, c + sz)]
+        de, rel, med = compare_columns(Xo, eo, Xh[:, cols], eh[cols], lih[cols])
+        rec["gpu_vs_oracle"] = {"columns": len(cols), "max_exponent_diff": de,
+                                "max_rel_diff": rel, "median_rel_diff": med}
+    X64, e64, li64 = fp64_out
+    de, rel, med = compare_columns(X64, e64, Xh, eh, li64)
+    rec["vs_fp64_gpu"] = {"columns": m, "max_exponent_diff": de, "max_rel_diff": rel,
+                          "median_rel_diff": med}
+    del X, e, lr, li, out
+    torch.cuda.empty_cache()
+    return rec
+
+
+def batched_record(ev, dev, stream, local_rank, count, steps, warmup, peaks):
+    """The batched workload (count Schur forms, n log-uniform in [32, 1024],
+    every 10th clustered-adversarial, 30% of the blocks selected) in one
+    persistent launch per step, FP64 and split, against the same batch one
+    evec_standard call per matrix (FP64, "plain").  Quality: the normalised
+    residual of every selected eigenvalue of 100 sampled matrices per mode."""
+    import torch
+    _, Ts, sels = workloads.batch_inputs(count)
+    Tp, ns, offs = ev.pack_batch(Ts, device=local_rank)
+    sel = np.concatenate(sels)
+    F = 0.0
+    for T, s_ in zip(Ts, sels):
+        nn = T.shape[0]
+        i = 0
+        while i < nn:
+            sz = 2 if i + 1 < nn and T[i + 1, i] != 0.0 else 1
+            if s_[i] or (sz == 2 and s_[i + 1]):
+                F += sz * float(i) * float(i)
+            i += sz
+    check = np.random.default_rng(11).choice(len(Ts), size=min(len(Ts), 100), replace=False)
+    out = {}
+    for mode in ("fp64", "split"):
+        o = ev.batched_packed(Tp, ns, offs, sel, mode=mode)
+        for _ in range(warmup):
+            ev.batched_packed(Tp, ns, offs, sel, mode=mode, out=o)
+        torch.cuda.synchronize(dev)
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(steps):
+            ev.batched_packed(Tp, ns, offs, sel, mode=mode, out=o)
+        t1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = t0.elapsed_time(t1)
+        ev.sync(local_rank)
+        cols = int(o[4].sum())
+        Xp, ep, lrp, lip = (t.cpu().numpy() for t in o[:4])
+        mm = o[4]
+        xo = np.concatenate([[0], np.cumsum(ns * mm)])
+        eo = np.concatenate([[0], np.cumsum(mm)])
+        worst = 0.0
+        for i in check:
+            nn, mi = int(ns[i]), int(mm[i])
+            if mi == 0:
+                continue
+            Xi = Xp[xo[i]:xo[i] + nn * mi].reshape(mi, nn).T
+            r = normalised_residuals(Ts[i], Xi, lrp[eo[i]:eo[i] + mi], lip[eo[i]:eo[i] + mi])
+            worst = max(worst, float((r / nn).max()))
+        out[mode] = {"value": cols * steps / (ms / 1e3), "unit": "columns/s", "steps": steps,
+                     "warmup": warmup, "ms_per_step": ms / steps,
+                     "tflops_fp64_equivalent": F * steps / (ms / 1e3) / 1e12,
+                     "tile_table": ev.tune_table(local_rank, mode),
+                     "quality": {"matrices": int(len(check)),
+                                 "max_normalised_residual_over_n": worst, "gate": "<= 10 n"}}
+        del o
+    dTs = [torch.from_numpy(np.asfortranarray(T)).to(dev) for T in Ts]
+    for T, s_ in zip(dTs, sels):
+        ev.standard(T, select=s_, tile=64)
+    torch.cuda.synchronize(dev)
+    w0 = time.perf_counter()
+    for T, s_ in zip(dTs, sels):
+        ev.standard(T, select=s_, tile=64)
+    torch.cuda.synchronize(dev)
+    plain = cols / (time.perf_counter() - w0)
+    del dTs, Tp
+    torch.cuda.empty_cache()
+    return {"workload": f"{count} Schur forms, n log-uniform in [32, 1024] (config-0 "
+                        "distribution, every 10th clustered adversarial), 30% of the blocks "
+                        "selected, no Q, one persistent launch per step (CUDA graph)",
+            "columns": cols, "flops_per_step": F, "fp64": out["fp64"], "split": out["split"],
+            "plain_fp64_one_call_per_matrix": {"value": plain, "unit": "columns/s"},
+            "batched_vs_plain": out["fp64"]["value"] / plain,
+            "batched_split_vs_plain": out["split"]["value"] / plain}
 
 
 def run_batched(args, rank, world, local_rank):

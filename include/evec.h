@@ -73,8 +73,8 @@ typedef enum {
     EVEC_ENOMEM = 4,     /* device or host allocation failed */
     EVEC_ECUDA = 5,      /* CUDA runtime error */
     EVEC_ETIMEOUT = 6,   /* a bounded device-side wait gave up (reported by evec_sync) */
-    EVEC_ERESIDUAL = 7,  /* reserved (the residual gate of refine = 2 repeats
-                            the solve in FP64 rather than failing) */
+    EVEC_ERESIDUAL = 7,  /* refine = 2: an eigenvalue failed the residual
+                            gate in every repeat, FP64 included (evec_sync) */
     EVEC_ECAPACITY = 8   /* problem larger than evec_standard_noalloc's fixed scratch */
 } evec_status;
 
@@ -89,16 +89,15 @@ typedef enum {
 typedef struct {
     int mode;    /* evec_mode */
     int tile;    /* tile size nb of the tiled solve, 16..128; 0 = default */
-    int check;   /* nonzero: synchronise at the end of the call and return
-                    the device status directly */
     int slices;  /* EVEC_SPLIT: digit slices per operand, 2..8; 0 = 8
                     (relative error of a product ~2^(-7 slices)) */
-    int refine;  /* EVEC_SPLIT, evec_standard: nonzero = one residual-
-                    correction sweep after the solve: the residual
-                    r = -(T - lambda I) y in FP64 on the rows above each
-                    column's block, formed on the solver's scaled segments
-                    (each tile row in its own power-of-two scale), the
-                    correction (T - lambda I) d = r solved by the same
+    int refine;  /* EVEC_SPLIT, evec_standard and evec_standard_left:
+                    1 (the default of evec_opts_default and of opt ==
+                    NULL) = one residual-correction sweep after the solve:
+                    the residual r = -(T - lambda I) y in FP64 on the rows
+                    above each column's block, formed on the solver's scaled
+                    segments (each tile row in its own power-of-two scale),
+                    the correction (T - lambda I) d = r solved by the same
                     robust tiled solver, y <- y + d exactly (power-of-two
                     scaling, one FP64 addition per entry).  A column whose
                     correction exceeds 2^(20 - 7 slices) of it keeps its
@@ -106,15 +105,24 @@ typedef struct {
                     rounding, amplified by an ill-conditioned column,
                     outweighs the split error.  Costs one FP64 product of
                     about n^3 / 3 flops for all columns, and an extra
-                    n x m FP64 workspace.  Ignored in EVEC_FP64 mode and
-                    for pencils.  2 = the sweep, then the residual gate of
-                    the refined vectors: ||(T - lambda I) y||_1 <=
-                    10 n ||T||_1 ||y||_1 u (u = 2^-53) per eigenvalue, from
-                    a second FP64 residual; if any eigenvalue fails, the
-                    matrix is solved again with 8 slices (and the gate), or
-                    in EVEC_FP64 mode when it already had 8
-                    (evec_gate_stats reports what happened). */
+                    n x m FP64 workspace.  0 = no sweep.  2 = the sweep,
+                    then the residual gate of the refined vectors:
+                    ||(T - lambda I) y||_1 <= 10 n ||T||_1 ||y||_1 u
+                    (u = 2^-53) per eigenvalue, from a second FP64
+                    residual; if any eigenvalue fails, the matrix is solved
+                    again with 8 slices (and the gate), then in EVEC_FP64
+                    mode, whose result is gated too: an eigenvalue that
+                    still fails makes evec_sync return EVEC_ERESIDUAL with
+                    the output column of the first one as its index
+                    (evec_gate_stats reports what happened).  Ignored in
+                    EVEC_FP64 mode and for pencils. */
+    int check;   /* nonzero: synchronise at the end of the call and return
+                    the device status directly */
 } evec_opts;
+
+/* The defaults that opt == NULL stands for: EVEC_FP64, tile 0 (64),
+ * slices 0 (8), refine 1, check 0. */
+void evec_opts_default(evec_opts *opt);
 
 /* Create a handle on CUDA device `device` that launches on `cuda_stream`
  * (a cudaStream_t; NULL = the legacy default stream).
@@ -302,6 +310,12 @@ enum {
  * repeated solves (more slices, then FP64). */
 evec_status evec_gate_stats(evec_handle h, int64_t *failed_units, int *retries);
 
+/* The bound of the residual gate (refine = 2) is factor * n (default 10,
+ * the bound ||(T - lambda I) y||_1 <= 10 n ||T||_1 ||y||_1 u).  A smaller
+ * factor asks for a tighter residual.  Errors: EVEC_EINVAL (factor not
+ * positive and finite). */
+evec_status evec_set_gate_factor(evec_handle h, double factor);
+
 /* Look-ahead schedule of the split-mode solve (default off): the diagonal
  * solve of step s leaves its protection decisions to a separate launch, and
  * the update of step s is cut at the 128-row block holding tile s - 1: that
@@ -344,6 +358,15 @@ evec_status evec_generalized(evec_handle h, int64_t n, const double *S, int64_t 
                              int32_t *scale_exp, double *alpha_re, double *alpha_im,
                              double *beta, const evec_opts *opt);
 
+/* Number of output columns m of evec_generalized for a selection: S's 1x1
+ * and 2x2 blocks (2 columns per selected 2x2 block), with the same checks
+ * of the pencil's form as evec_generalized (synchronises the handle's
+ * stream).  Errors: EVEC_EINVAL, EVEC_ENOTSCHUR, EVEC_ENONFINITE,
+ * EVEC_ECUDA. */
+evec_status evec_count_generalized(evec_handle h, int64_t n, const double *S, int64_t lds,
+                                   const double *T, int64_t ldt, const uint8_t *select_host,
+                                   int64_t *m);
+
 /*
  * Robust triangular solve with many right-hand sides (the LAPACK xLATRS
  * generalisation the eigenvector solve of Sec. 3.3 rests on): for every
@@ -383,28 +406,42 @@ evec_status evec_batched_count(evec_handle h, int64_t count, const int64_t *n_ho
                                const uint8_t *select_host, int64_t *m_host);
 
 /*
- * Right eigenvectors of every matrix (evec_standard without Q, per matrix) in
- * one persistent launch: a device work queue hands whole matrices to CTAs,
- * largest estimated work first; the device part of the call (plan upload,
- * queue reset, launch) is a CUDA graph, replayed while the batch layout and
- * buffers stay the same.  Outputs packed in matrix order: X_i (n_i x m_i,
- * leading dimension n_i) at X_packed + sum_{k<i} n_k m_k; scale_exp_i and
- * lam_re_i / lam_im_i (m_i each; lam may be NULL) at offset sum_{k<i} m_k.
+ * Right eigenvectors of every matrix (evec_standard per matrix, with or
+ * without its own Q) in one persistent launch: a device work queue hands
+ * whole matrices to CTAs, largest estimated work first; the device part of
+ * the call (plan upload, queue reset, launch) is a CUDA graph, replayed
+ * while the batch layout, buffers and offsets stay the same.
+ *   Q_packed (device, may be NULL) with q_off_host (host, count entries):
+ *     matrix i with q_off_host[i] >= 0 is back-transformed, X_i = Q_i Y_i
+ *     with Q_i (n_i x n_i, leading dimension n_i) at Q_packed +
+ *     q_off_host[i], and brought to canonical form; q_off_host[i] < 0 (or
+ *     Q_packed NULL) returns Y_i itself.  The CTA that solved the matrix
+ *     forms the product (FP64; K runs to the block end of each 64-column
+ *     block's last column), and the handle keeps Y_i in its workspace.
+ *   X_i (n_i x m_i, leading dimension n_i) at X_packed + x_off_host[i],
+ *     scale_exp_i and lam_re_i / lam_im_i (m_i each; lam may be NULL) at
+ *     offset e_off_host[i] of their arrays; x_off_host / e_off_host NULL
+ *     pack them in matrix order (X_i at sum_{k<i} n_k m_k, the others at
+ *     sum_{k<i} m_k).  Outputs must not overlap.
  * opt->mode: EVEC_FP64, or EVEC_SPLIT (opt->slices digit slices, 2..8;
  * 0 = 8): the updates of every matrix as BF16 slice products on the tensor
  * cores inside the same persistent kernel (each CTA holds 256 TMEM columns;
- * two CTAs per SM); the diagonal solves, decisions and canonical form stay
- * FP64.  opt->refine is ignored here.
+ * two CTAs per SM); the diagonal solves, decisions, back-transformation
+ * and canonical form stay FP64.  opt->refine is ignored here.
  * opt->tile: 16..64 for every matrix, or 0 = the tile of each matrix's size
  * class from the handle's table, tuned on first use of a class by timing
  * 16, 32 and 64 on up to eight of the batch's matrices of that class.
- * Device-side errors (evec_sync / opt->check): index = element offset in
- * T_packed.
+ * Errors: EVEC_EINVAL (a NULL q_off_host with Q_packed, a negative output
+ * offset, ...); device-side errors (evec_sync / opt->check): index =
+ * element offset in T_packed.
  */
 evec_status evec_batched(evec_handle h, int64_t count, const int64_t *n_host,
                          const double *T_packed, const int64_t *t_off_host,
-                         const uint8_t *select_host, double *X_packed, int32_t *scale_exp_packed,
-                         double *lam_re_packed, double *lam_im_packed, const evec_opts *opt);
+                         const double *Q_packed, const int64_t *q_off_host,
+                         const uint8_t *select_host, double *X_packed,
+                         const int64_t *x_off_host, int32_t *scale_exp_packed,
+                         const int64_t *e_off_host, double *lam_re_packed,
+                         double *lam_im_packed, const evec_opts *opt);
 
 /*
  * Generalized right eigenvectors of a batch of pencils (S_i, T_i) (the
@@ -417,8 +454,8 @@ evec_status evec_batched(evec_handle h, int64_t count, const int64_t *n_host,
  * n_i) at S_packed + s_off_host[i] and T_packed + t_off_host[i], with the
  * requirements of evec_generalized.  Output packing as evec_batched (X_i at
  * sum_{k<i} n_k m_k; scale_exp_i, alpha_re_i, alpha_im_i, beta_i at
- * sum_{k<i} m_k; the last three may be NULL); m_i from evec_batched_count
- * on S_packed.  opt->mode must be EVEC_FP64; opt->tile 16..64, 0 = 64 (the
+ * sum_{k<i} m_k; the last three may be NULL); m_i from
+ * evec_batched_generalized_count.  opt->mode must be EVEC_FP64; opt->tile 16..64, 0 = 64 (the
  * solver holds both matrices' diagonal tiles: one CTA per SM at 64).  Device-side errors
  * (evec_sync / opt->check): index = element offset in S_packed or T_packed
  * of the offending entry.
@@ -430,6 +467,13 @@ evec_status evec_batched_generalized(evec_handle h, int64_t count, const int64_t
                                      int32_t *scale_exp_packed, double *alpha_re_packed,
                                      double *alpha_im_packed, double *beta_packed,
                                      const evec_opts *opt);
+
+/* Output columns m_i of each pencil of a packed batch (m_host: count
+ * entries, host), with the checks of evec_batched_generalized. */
+evec_status evec_batched_generalized_count(evec_handle h, int64_t count, const int64_t *n_host,
+                                           const double *S_packed, const int64_t *s_off_host,
+                                           const double *T_packed, const int64_t *t_off_host,
+                                           const uint8_t *select_host, int64_t *m_host);
 
 /* Size classes of the tile table: n <= 64, <= 128, <= 256, <= 512, larger. */
 #define EVEC_SIZE_CLASSES 5
@@ -462,10 +506,12 @@ evec_status evec_tune_set(evec_handle h, int mode, int size_class, int tile);
  * that device current); make that first call before any stream capture.
  * Every call shares the array and reuses whatever the previous call left in
  * it (the status word is cleared at the start of each call; everything else
- * is written before it is read).  Calls are serialised inside the library
- * and each one synchronises its stream before returning, so calls through
- * this entry point never overlap on the GPU; two processes or any other
- * overlapping use would race on the array.
+ * is written before it is read).  Two calls that overlapped on the GPU
+ * would race on the array, so the library prevents overlap: the call is
+ * synchronous, calls are serialised inside the library, and each one
+ * synchronises its stream before it returns, on success and on every error
+ * after it queued work.  Each process that loads the library has its own
+ * copy of the array.
  * Returns, synchronously: EVEC_ECAPACITY when n > EVEC_NOALLOC_MAX_N or the
  * chosen tile needs more than the fixed scratch; EVEC_EINVAL,
  * EVEC_ENOTSCHUR, EVEC_ENONFINITE (with *bad_index, linear index into T) as

@@ -47,8 +47,9 @@ class EvecError(RuntimeError):
 
 
 class _Opts(ctypes.Structure):
-    _fields_ = [("mode", ctypes.c_int), ("tile", ctypes.c_int), ("check", ctypes.c_int),
-                ("slices", ctypes.c_int), ("refine", ctypes.c_int)]
+    """evec_opts, in the header's field order."""
+    _fields_ = [("mode", ctypes.c_int), ("tile", ctypes.c_int), ("slices", ctypes.c_int),
+                ("refine", ctypes.c_int), ("check", ctypes.c_int)]
 
 
 MODES = {"fp64": 0, "split": 1}
@@ -102,7 +103,10 @@ def lib() -> ctypes.CDLL:
         L.evec_generalized.argtypes = [p, i64, p, i64, p, i64, p, i64, p, p, i64, p, p, p, p,
                                        ctypes.POINTER(_Opts)]
         L.evec_batched_count.argtypes = [p, i64, p, p, p, p, p]
-        L.evec_batched.argtypes = [p, i64, p, p, p, p, p, p, p, p, ctypes.POINTER(_Opts)]
+        L.evec_count_generalized.argtypes = [p, i64, p, i64, p, i64, p, ctypes.POINTER(i64)]
+        L.evec_batched_generalized_count.argtypes = [p, i64, p, p, p, p, p, p, p]
+        L.evec_batched.argtypes = [p, i64, p, p, p, p, p, p, p, p, p, p, p, p,
+                                   ctypes.POINTER(_Opts)]
         L.evec_batched_generalized.argtypes = [p, i64, p, p, p, p, p, p, p, p, p, p, p,
                                                ctypes.POINTER(_Opts)]
         L.evec_tune_get.argtypes = [p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
@@ -114,7 +118,8 @@ def lib() -> ctypes.CDLL:
                   "evec_batched_generalized", "evec_set_lookahead", "evec_hessenberg",
                   "evec_set_hessenberg_panel", "evec_gate_stats", "evec_window_update",
                   "evec_window_update_set",
-                  "evec_generalized",
+                  "evec_generalized", "evec_count_generalized",
+                  "evec_batched_generalized_count",
                   "evec_tune_get", "evec_tune_set"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
@@ -145,8 +150,9 @@ def _mask(select, n):
     return s
 
 
-def _opts(tile, check, mode="fp64", slices=0, refine=False):
-    return _Opts(MODES[mode], int(tile), 1 if check else 0, int(slices), int(refine))
+def _opts(tile, check, mode="fp64", slices=0, refine=1):
+    return _Opts(mode=MODES[mode], tile=int(tile), slices=int(slices), refine=int(refine),
+                 check=1 if check else 0)
 
 
 # ---------------------------------------------------------------------------
@@ -282,10 +288,12 @@ def count(T, select=None) -> int:
 
 
 def standard(T, Q=None, select=None, tile: int = 0, check: bool = False, out=None,
-             mode: str = "fp64", slices: int = 0, refine: bool = False):
+             mode: str = "fp64", slices: int = 0, refine: int = 1):
     """Eigenvectors of the quasi-triangular T (optionally X = Q Y).
 
-    refine (split mode): one FP64 residual-correction sweep after the solve.
+    refine (split mode; evec_opts.refine): 1 (the library's default) one
+    FP64 residual-correction sweep after the solve, 0 none, 2 the sweep and
+    the residual gate.
     Returns (X, scale_exp, lam_re, lam_im) as CUDA tensors; X is (n, m)
     column-major.  The call is asynchronous on the current stream; device
     detected input errors surface at ``sync()`` (or immediately with
@@ -294,7 +302,7 @@ def standard(T, Q=None, select=None, tile: int = 0, check: bool = False, out=Non
 
 
 def left(T, Q=None, select=None, tile: int = 0, check: bool = False, out=None,
-         mode: str = "fp64", slices: int = 0, refine: bool = False):
+         mode: str = "fp64", slices: int = 0, refine: int = 1):
     """Left eigenvectors u^H T = lambda u^H (optionally X = Q U), same
     arguments, outputs and column order as ``standard``; a pair gives
     (Re u, Im u) for lambda = a + i w, w > 0."""
@@ -332,19 +340,17 @@ def _standard_call(fn, T, Q, select, tile, check, out, mode, slices, refine):
     return X, e, lr, li
 
 
-def _pencil_columns(S, sel):
-    """Output columns of a pencil: S's blocks from its first subdiagonal (a
-    pair counts 2 when either eigenvalue is selected)."""
-    import torch
-    sub = torch.diagonal(S, -1).cpu().numpy()
+def count_generalized(S, T, select=None) -> int:
+    """Output columns of evec_generalized for the pencil (S, T)."""
     n = S.shape[0]
-    m = i = 0
-    while i < n:
-        sz = 2 if i + 1 < n and sub[i] != 0.0 else 1
-        if sel is None or sel[i] or (sz == 2 and sel[i + 1]):
-            m += sz
-        i += sz
-    return m
+    lds = _check_colmajor(S, "S", n)
+    ldt = _check_colmajor(T, "T", n)
+    sel = _mask(select, n)
+    m = ctypes.c_int64(0)
+    h = handle(S.device.index)
+    _check(lib().evec_count_generalized(h.ptr, n, S.data_ptr(), lds, T.data_ptr(), ldt,
+                                        _np_ptr(sel), ctypes.byref(m)), "evec_count_generalized")
+    return int(m.value)
 
 
 def generalized(S, T, Z=None, select=None, tile: int = 0, check: bool = False,
@@ -361,7 +367,7 @@ def generalized(S, T, Z=None, select=None, tile: int = 0, check: bool = False,
     sel = _mask(select, n)
     dev = S.device
     h = handle(dev.index)
-    m = _pencil_columns(S, sel) if n else 0
+    m = count_generalized(S, T, sel) if n else 0
     X = torch.empty((m, n), dtype=torch.float64, device=dev).t()
     e = torch.empty(m, dtype=torch.int32, device=dev)
     ar = torch.empty(m, dtype=torch.float64, device=dev)
@@ -477,7 +483,7 @@ def hessenberg(A, calc_q: bool = True, check: bool = False, overwrite: bool = Fa
 
 
 def standard_host(T, Q=None, select=None, tile: int = 0, device: int = 0,
-                  mode: str = "fp64", slices: int = 0, refine: bool = False):
+                  mode: str = "fp64", slices: int = 0, refine: int = 1):
     """The same computation from host numpy arrays (column-major float64);
     copies in, computes, copies out.  Returns numpy arrays."""
     Tf = np.asfortranarray(T, dtype=np.float64)
@@ -544,30 +550,39 @@ def batched_count(T_packed, ns, t_offs, select=None):
 
 
 def batched_packed(T_packed, ns, t_offs, select=None, tile: int = 0, mode: str = "fp64",
-                   check: bool = False, out=None, slices: int = 0):
+                   check: bool = False, out=None, slices: int = 0, Q_packed=None, q_offs=None,
+                   x_offs=None, e_offs=None):
     """evec_batched on a packed device buffer.  select: concatenated n_i-byte
-    masks or None.  Returns (X_packed, scale_exp, lam_re, lam_im, m) with the
-    output packing of the C entry point (X_i at sum_{k<i} n_k m_k, leading
-    dimension n_i; the others at sum_{k<i} m_k).  out = (X, e, lr, li, m)
-    from an earlier call on the same batch layout skips the column count."""
+    masks or None.  Q_packed / q_offs: per-matrix back-transformations
+    (q_offs[i] < 0: none for matrix i).  Returns (X_packed, scale_exp,
+    lam_re, lam_im, m) with the output packing of the C entry point (X_i at
+    x_offs[i], default sum_{k<i} n_k m_k, leading dimension n_i; the others
+    at e_offs[i], default sum_{k<i} m_k).  out = (X, e, lr, li, m) from an
+    earlier call on the same batch layout skips the column count."""
     import torch
     h = handle(T_packed.device.index)
     ns = np.ascontiguousarray(ns, dtype=np.int64)
     t_offs = np.ascontiguousarray(t_offs, dtype=np.int64)
     sel = None if select is None else np.ascontiguousarray(select, dtype=np.uint8)
+    q_offs = None if q_offs is None else np.ascontiguousarray(q_offs, dtype=np.int64)
+    x_offs = None if x_offs is None else np.ascontiguousarray(x_offs, dtype=np.int64)
+    e_offs = None if e_offs is None else np.ascontiguousarray(e_offs, dtype=np.int64)
     if out is not None:
         X, e, lr, li, m = out
     else:
         m = batched_count(T_packed, ns, t_offs, sel)
         dev = T_packed.device
-        X = torch.empty(int((ns * m).sum()), dtype=torch.float64, device=dev)
-        e = torch.empty(int(m.sum()), dtype=torch.int32, device=dev)
-        lr = torch.empty(int(m.sum()), dtype=torch.float64, device=dev)
-        li = torch.empty(int(m.sum()), dtype=torch.float64, device=dev)
+        nx = int((ns * m).sum()) if x_offs is None else int((x_offs + ns * m).max(initial=0))
+        ne = int(m.sum()) if e_offs is None else int((e_offs + m).max(initial=0))
+        X = torch.empty(max(nx, 1), dtype=torch.float64, device=dev)
+        e = torch.empty(max(ne, 1), dtype=torch.int32, device=dev)
+        lr = torch.empty(max(ne, 1), dtype=torch.float64, device=dev)
+        li = torch.empty(max(ne, 1), dtype=torch.float64, device=dev)
     opts = _opts(tile, False, mode, slices)
     st = lib().evec_batched(h.ptr, len(ns), _np_ptr(ns), T_packed.data_ptr(), _np_ptr(t_offs),
-                            _np_ptr(sel), X.data_ptr(), e.data_ptr(), lr.data_ptr(),
-                            li.data_ptr(), ctypes.byref(opts))
+                            None if Q_packed is None else Q_packed.data_ptr(), _np_ptr(q_offs),
+                            _np_ptr(sel), X.data_ptr(), _np_ptr(x_offs), e.data_ptr(),
+                            _np_ptr(e_offs), lr.data_ptr(), li.data_ptr(), ctypes.byref(opts))
     _check(st, "evec_batched")
     if check:
         h.sync()
@@ -575,16 +590,28 @@ def batched_packed(T_packed, ns, t_offs, select=None, tile: int = 0, mode: str =
 
 
 def batched(Ts, selects=None, tile: int = 0, mode: str = "fp64", check: bool = True,
-            slices: int = 0):
+            slices: int = 0, Qs=None):
     """Eigenvectors of a list of quasi-triangular matrices in one persistent
-    launch.  Returns a list of (X_i (n_i, m_i), scale_exp_i, lam_re_i,
-    lam_im_i) CUDA tensors, X_i column-major."""
+    launch; Qs: a list of orthogonal factors (None entries: no
+    back-transformation for that matrix).  Returns a list of (X_i (n_i,
+    m_i), scale_exp_i, lam_re_i, lam_im_i) CUDA tensors, X_i column-major."""
     Tp, ns, offs = pack_batch(Ts)
     sel = None
     if selects is not None:
         sel = np.concatenate([np.ones(n, np.uint8) if s is None else
                               np.ascontiguousarray(s, dtype=np.uint8) for s, n in zip(selects, ns)])
-    X, e, lr, li, m = batched_packed(Tp, ns, offs, sel, tile, mode, check, slices=slices)
+    Qp = qoffs = None
+    if Qs is not None and any(q is not None for q in Qs):
+        have = [q for q in Qs if q is not None]
+        Qp, _, ho = pack_batch(have)
+        qoffs = np.full(len(Ts), -1, dtype=np.int64)
+        k = 0
+        for i, q in enumerate(Qs):
+            if q is not None:
+                qoffs[i] = ho[k]
+                k += 1
+    X, e, lr, li, m = batched_packed(Tp, ns, offs, sel, tile, mode, check, slices=slices,
+                                     Q_packed=Qp, q_offs=qoffs)
     out = []
     xo = eo = 0
     for n, mi in zip(ns, m):
@@ -611,7 +638,12 @@ def batched_generalized_packed(S_packed, T_packed, ns, s_offs, t_offs, select=No
     if out is not None:
         X, e, ar, ai, be, m = out
     else:
-        m = batched_count(S_packed, ns, s_offs, sel)
+        m = np.zeros(len(ns), dtype=np.int64)
+        _check(lib().evec_batched_generalized_count(h.ptr, len(ns), _np_ptr(ns),
+                                                    S_packed.data_ptr(), _np_ptr(s_offs),
+                                                    T_packed.data_ptr(), _np_ptr(t_offs),
+                                                    _np_ptr(sel), _np_ptr(m)),
+               "evec_batched_generalized_count")
         dev = S_packed.device
         X = torch.empty(int((ns * m).sum()), dtype=torch.float64, device=dev)
         e = torch.empty(int(m.sum()), dtype=torch.int32, device=dev)

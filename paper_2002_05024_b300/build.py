@@ -1,20 +1,26 @@
 """Build step: compile the CUDA sources of the library into
-paper_2002_05024_b300/_lib/libevec.so for sm_103a (B300), in-tree."""
+paper_2002_05024_b300/_lib/libevec.so for sm_103a (B300), in-tree.
+
+Each .cu file is compiled to its own object (in parallel; a file is
+recompiled when it, or any header, is newer than its object), then the
+objects are linked into the shared library."""
 from __future__ import annotations
 
 import glob
 import os
 import subprocess
 import sys
+from concurrent.futures import ThreadPoolExecutor
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB_DIR = os.path.join(HERE, "_lib")
+OBJ_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(LIB_DIR, "libevec.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
-         "-cudart", "shared", "-Xlinker", "-rpath,/usr/local/cuda/lib64"]
+CFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
+LFLAGS = ["-shared", "-cudart", "shared", "-Xlinker", "-rpath,/usr/local/cuda/lib64"]
 
 
 def sources():
@@ -24,6 +30,10 @@ def sources():
 def headers():
     return sorted(glob.glob(os.path.join(CSRC, "*.cuh")) +
                   glob.glob(os.path.join(HERE, "..", "include", "*.h")))
+
+
+def _obj(src):
+    return os.path.join(OBJ_DIR, os.path.basename(src)[:-3] + ".o")
 
 
 def up_to_date() -> bool:
@@ -37,12 +47,28 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and up_to_date():
         return LIB
     os.makedirs(LIB_DIR, exist_ok=True)
+    os.makedirs(OBJ_DIR, exist_ok=True)
+    hdr_t = max((os.path.getmtime(f) for f in headers()), default=0.0)
+    srcs = sources()
+    stale = [s for s in srcs if force or not os.path.exists(_obj(s)) or
+             os.path.getmtime(_obj(s)) < max(os.path.getmtime(s), hdr_t)]
+
+    def compile_one(src):
+        out = _obj(src)
+        tmp = out + f".tmp{os.getpid()}"
+        cmd = [NVCC, *ARCH, *CFLAGS, "-c", "-o", tmp, src]
+        if verbose:
+            cmd.insert(1, "-Xptxas=-v")
+            print(" ".join(cmd), file=sys.stderr)
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, out)
+
+    workers = max(1, min(len(stale), os.cpu_count() or 1))
+    with ThreadPoolExecutor(workers) as pool:
+        for f in [pool.submit(compile_one, s) for s in stale]:
+            f.result()
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [NVCC, *ARCH, *FLAGS, "-o", tmp, *sources()]
-    if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-        print(" ".join(cmd), file=sys.stderr)
-    subprocess.run(cmd, check=True)
+    subprocess.run([NVCC, *ARCH, *LFLAGS, "-o", tmp, *[_obj(s) for s in srcs]], check=True)
     os.replace(tmp, LIB)
     return LIB
 

@@ -205,6 +205,8 @@ struct BatchKey {
     bool valid = false;
     std::vector<int64_t> n, toff;
     const void *T = nullptr, *X = nullptr, *E = nullptr, *lr = nullptr, *li = nullptr;
+    const void *Q = nullptr;
+    std::vector<int64_t> qoff, xoff, eoff;   // empty: not given
     int tile = 0, mode = 0, slices = 0;
     std::vector<int> tune;
     bool has_sel = false;
@@ -578,6 +580,11 @@ struct evec_ctx {
     int gate_depth = 0;
     int64_t gate_failed = 0;
     int gate_retries = 0;
+    double gate_factor = 10.0;   // the gate's bound is gate_factor * n
+    // an error found on the host after the work that led to it finished
+    // (EVEC_ERESIDUAL), reported by the next evec_sync like a device one
+    int pend_code = 0;
+    int64_t pend_index = -1;
     bool hess_coop = true;   // panel as one cooperative launch (else six launches per column)
     std::vector<int32_t> lmap_h;
     std::vector<uint8_t> lsel;
@@ -976,6 +983,21 @@ evec_status evec_set_hessenberg_panel(evec_handle h, int cooperative) {
     return EVEC_OK;
 }
 
+void evec_opts_default(evec_opts *opt) {
+    if (!opt) return;
+    opt->mode = EVEC_FP64;
+    opt->tile = 0;
+    opt->slices = 0;
+    opt->refine = 1;
+    opt->check = 0;
+}
+
+evec_status evec_set_gate_factor(evec_handle h, double factor) {
+    if (!h || !(factor > 0.0) || !(factor <= 1e300)) return EVEC_EINVAL;
+    h->gate_factor = factor;
+    return EVEC_OK;
+}
+
 evec_status evec_gate_stats(evec_handle h, int64_t *failed_units, int *retries) {
     if (!h) return EVEC_EINVAL;
     if (failed_units) *failed_units = h->gate_failed;
@@ -1041,11 +1063,17 @@ evec_status evec_sync(evec_handle h, int64_t *bad_index) {
     EVEC_CUDA(cudaMemcpyAsync(h->status_h, h->status_d, sizeof(DevStatus),
                               cudaMemcpyDeviceToHost, h->stream));
     EVEC_CUDA(cudaStreamSynchronize(h->stream));
-    const DevStatus s = *h->status_h;
+    DevStatus s = *h->status_h;
     if (s.code != 0 || s.timeout != 0) {
         EVEC_CUDA(cudaMemsetAsync(h->status_d, 0, sizeof(DevStatus), h->stream));
         EVEC_CUDA(cudaStreamSynchronize(h->stream));
     }
+    if (s.code == 0 && h->pend_code != 0) {
+        s.code = h->pend_code;
+        s.index = h->pend_index;
+    }
+    h->pend_code = 0;
+    h->pend_index = -1;
     if (bad_index) *bad_index = s.code ? (int64_t)s.index : -1;
     if (s.code == 0 && s.timeout != 0) return EVEC_ETIMEOUT;
     return (evec_status)s.code;
@@ -1190,6 +1218,27 @@ static evec_status sweep_steps(evec_handle h, const HostPlan &HP, const Plan &dp
     return EVEC_OK;
 }
 
+// The residual gate on the solved segments (h->seg_ey holds their
+// exponents): the FP64 residual of y into D, then per eigenvalue
+// ||(T - lambda I) y||_1 <= gate_factor n ||T||_1 ||y||_1 u.  out[0]: the
+// eigenvalues that fail, out[1]: the output column of the first of them.
+static evec_status run_gate(evec_handle h, const Plan &dp, int N, int max_tile,
+                            const double *T, int64_t ldt, const double *Y, int64_t ldy,
+                            double *D, int64_t ldd, int out[2]) {
+    cudaStream_t st = h->stream;
+    if (!h->gate_d) EVEC_CUDA(cudaMalloc((void **)&h->gate_d, 2 * sizeof(uint64_t)));
+    timed(h, EVEC_K_REFINE, [&] {
+        launch_residual(T, ldt, dp, N, max_tile, Y, ldy, h->seg_ey, h->row_tile_d, D, ldd, st);
+        launch_gate(dp, Y, ldy, h->seg_ey, D, ldd, T, ldt, h->gate_factor * (double)dp.n,
+                    h->gate_d, nullptr, st);
+        return 4;
+    });
+    EVEC_CUDA(cudaGetLastError());
+    EVEC_CUDA(cudaMemcpyAsync(out, h->gate_d + 1, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    EVEC_CUDA(cudaStreamSynchronize(st));
+    return EVEC_OK;
+}
+
 evec_status evec_standard(evec_handle h, int64_t n, const double *T, int64_t ldt,
                           const double *Q, int64_t ldq, const uint8_t *select_host,
                           double *X, int64_t ldx, int32_t *scale_exp, double *lam_re,
@@ -1204,8 +1253,11 @@ evec_status evec_standard(evec_handle h, int64_t n, const double *T, int64_t ldt
     if (nb < 16 || nb > kMaxTile) return EVEC_EINVAL;
     if (n == 0) return EVEC_OK;
     if (!T || !X || !scale_exp) return EVEC_EINVAL;
-    const bool refine = mode == EVEC_SPLIT && opt && opt->refine;
-    const bool gate = refine && opt->refine >= 2;
+    const int refine_opt = opt ? opt->refine : 1;
+    const bool refine = mode == EVEC_SPLIT && refine_opt;
+    const bool gate = refine && refine_opt >= 2;
+    // the last repeat of a gated split solve: FP64, its result gated too
+    const bool fp64_gate = mode == EVEC_FP64 && h->gate_depth > 0 && refine_opt >= 2;
     DeviceGuard g(h->device);
     if (!g.ok) return EVEC_ECUDA;
     if (h->gate_depth == 0) {   // statistics of this top-level call
@@ -1253,7 +1305,7 @@ evec_status evec_standard(evec_handle h, int64_t n, const double *T, int64_t ldt
     EVEC_TRY(grow_device(&h->seg_nu, &h->segn_cap, segs));
     EVEC_TRY(grow_device(&h->tau, &h->tau_cap, (size_t)N * (size_t)N));
     EVEC_TRY(grow_device(&h->blk_tau, &h->blk_tau_cap, HP.blk_start.size()));
-    if (refine) {
+    if (refine || fp64_gate) {
         EVEC_TRY(grow_device(&h->Rd, &h->Rd_cap, (size_t)n * (size_t)m));
         EVEC_TRY(grow_device(&h->seg_ey, &h->seg_ey_cap, segs));
     }
@@ -1295,6 +1347,16 @@ evec_status evec_standard(evec_handle h, int64_t n, const double *T, int64_t ldt
         return sweep_steps(h, HP, dp, T, ldt, Yb, ldyb, rhs, mode, sctx, st);
     };
     EVEC_TRY(sweep(Y, ldy, false));
+    if (fp64_gate) {   // the FP64 repeat of a gated split solve
+        EVEC_CUDA(cudaMemcpyAsync(h->seg_ey, h->seg_e, segs * sizeof(int32_t),
+                                  cudaMemcpyDeviceToDevice, st));
+        int gres[2] = {0, 0};
+        EVEC_TRY(run_gate(h, dp, N, HP.max_tile, T, ldt, Y, ldy, h->Rd, n, gres));
+        if (gres[0] > 0 && h->pend_code == 0) {
+            h->pend_code = EVEC_ERESIDUAL;
+            h->pend_index = gres[1];
+        }
+    }
     if (refine) {   // residual-correction sweep on the solved segments
         double *D = h->Rd;
         const int64_t ldd = n;
@@ -1317,27 +1379,16 @@ evec_status evec_standard(evec_handle h, int64_t n, const double *T, int64_t ldt
             // the residual of the refined y on its segments, and the gate
             // ||(T - lambda I) y||_1 <= 10 n ||T||_1 ||y||_1 u per unit; a
             // failure re-runs the matrix with 8 slices, then in FP64
-            if (!h->gate_d) EVEC_CUDA(cudaMalloc((void **)&h->gate_d, 2 * sizeof(uint64_t)));
-            timed(h, EVEC_K_REFINE, [&] {
-                launch_residual(T, ldt, dp, N, HP.max_tile, Y, ldy, h->seg_ey, h->row_tile_d, D,
-                                ldd, st);
-                launch_gate(dp, Y, ldy, h->seg_ey, D, ldd, T, ldt, 10.0 * (double)n, h->gate_d,
-                            nullptr, st);
-                return 4;
-            });
-            EVEC_CUDA(cudaGetLastError());
-            int fails = 0;
-            EVEC_CUDA(cudaMemcpyAsync(&fails, h->gate_d + 1, sizeof(int), cudaMemcpyDeviceToHost,
-                                      st));
-            EVEC_CUDA(cudaStreamSynchronize(st));
+            int gres[2] = {0, 0};
+            EVEC_TRY(run_gate(h, dp, N, HP.max_tile, T, ldt, Y, ldy, D, ldd, gres));
+            const int fails = gres[0];
             if (h->gate_depth == 0) h->gate_failed = fails;
             if (fails > 0) {
                 evec_opts o = *opt;
                 if (slices < 8) {
                     o.slices = 8;
                 } else {
-                    o.mode = EVEC_FP64;
-                    o.refine = 0;
+                    o.mode = EVEC_FP64;   // refine stays 2: the FP64 result is gated too
                 }
                 h->gate_retries++;
                 h->gate_depth++;
@@ -1806,6 +1857,16 @@ namespace evec {
 // Pencils: T2_packed / t2_off_host hold the upper triangular T of each
 // pair (T_packed its S), beta_out receives beta per column, gen_tile is the
 // largest tile (no graph: use_graph must be false).
+// Standard problems: Q_packed (may be null) with q_off_host[i] >= 0 gives
+// matrix i a back-transformation X_i = Q_i Y_i (Q_i at Q_packed +
+// q_off_host[i], leading dimension n_i); x_off_host / e_off_host (may be
+// null: packed in matrix order) place X_i and scale_exp_i / lam_i; the
+// eigenvalues are written by the kernel.
+struct BatchOut {
+    const double *Q = nullptr;
+    const int64_t *q_off = nullptr, *x_off = nullptr, *e_off = nullptr;
+};
+
 static evec_status run_batch(evec_handle h, int64_t count, const int64_t *n_host,
                              const double *T_packed, const int64_t *t_off_host,
                              const std::vector<int> &idx, const std::vector<HostPlan> &plans,
@@ -1813,18 +1874,19 @@ static evec_status run_batch(evec_handle h, int64_t count, const int64_t *n_host
                              double *lam_im, bool use_graph, int slices,
                              const double *T2_packed = nullptr,
                              const int64_t *t2_off_host = nullptr, double *beta_out = nullptr,
-                             int gen_tile = 0) {
+                             int gen_tile = 0, const BatchOut &bo = BatchOut()) {
     const bool gen = T2_packed != nullptr;
     h->bcall.valid = false;   // the pinned plan buffer is rewritten below
     // output offsets (all matrices, matrix order)
     std::vector<int64_t> xo(count), eo(count);
     int64_t xacc = 0, eacc = 0;
     for (int64_t i = 0; i < count; i++) {
-        xo[i] = xacc;
-        eo[i] = eacc;
+        xo[i] = bo.x_off ? bo.x_off[i] : xacc;
+        eo[i] = bo.e_off ? bo.e_off[i] : eacc;
         xacc += n_host[i] * plans[i].m;
         eacc += plans[i].m;
     }
+    auto has_q = [&](int64_t i) { return !gen && bo.Q && bo.q_off && bo.q_off[i] >= 0; };
     std::vector<std::pair<double, int>> order;
     for (int i : idx) {
         const HostPlan &P = plans[i];
@@ -1832,7 +1894,9 @@ static evec_status run_batch(evec_handle h, int64_t count, const int64_t *n_host
         double w = (double)P.n;
         for (size_t u = 0; u < P.unit_col.size(); u++) {
             const double k = P.blk_start[P.unit_blk[u]];
-            w += k * k * (P.unit_lam[2 * u + 1] != 0.0 ? 2.0 : 1.0);
+            const double cols = P.unit_lam[2 * u + 1] != 0.0 ? 2.0 : 1.0;
+            w += k * k * cols;
+            if (has_q(i)) w += 2.0 * (double)P.n * (k + cols) * cols;
         }
         order.push_back({-w, i});
     }
@@ -1853,6 +1917,7 @@ static evec_status run_batch(evec_handle h, int64_t count, const int64_t *n_host
         const size_t N = P.tile_start.size() - 1, segs = N * (size_t)P.m;
         wsb += r16(8 * N * N) + r16(8 * P.blk_start.size()) + r16(8 * segs) + 3 * r16(4 * segs);
         if (gen) wsb += r16(8 * N * N) + r16(8 * P.blk_start.size());
+        if (has_q(o.second)) wsb += r16(8 * (size_t)P.n * (size_t)P.m);
     }
     EVEC_TRY(grow_host(&h->bplan_h, &h->bplan_h_cap, sz.off + 64));
     EVEC_TRY(grow_device(&h->bplan_d, &h->bplan_cap, sz.off + 64));
@@ -1889,9 +1954,15 @@ static evec_status run_batch(evec_handle h, int64_t count, const int64_t *n_host
         B.T = T_packed + t_off_host[i];
         B.ldt = n_host[i];
         B.t_base = t_off_host[i];
-        B.X = X_packed + xo[i];
+        B.Xout = X_packed + xo[i];
+        B.ldxo = n_host[i];
+        B.X = B.Xout;
         B.ldx = n_host[i];
         B.scale_exp = scale_exp_packed + eo[i];
+        B.Q = nullptr;
+        B.ldq = 0;
+        B.lam_re = (!gen && lam_re) ? lam_re + eo[i] : nullptr;
+        B.lam_im = (!gen && lam_im) ? lam_im + eo[i] : nullptr;
         const size_t N = P.tile_start.size() - 1, segs = N * (size_t)P.m;
         auto take = [&](size_t bytes) {   // the same rounding as wsb above
             unsigned char *p = h->bws + wo;
@@ -1914,6 +1985,11 @@ static evec_status run_batch(evec_handle h, int64_t count, const int64_t *n_host
             B.t2_base = t2_off_host[i];
             B.tau2 = (double *)take(8 * N * N);
             B.blk_tau2 = (double *)take(8 * P.blk_start.size());
+        }
+        if (has_q(i)) {   // the solve writes Y into a workspace
+            B.Q = bo.Q + bo.q_off[i];
+            B.ldq = n_host[i];
+            B.X = (double *)take(8 * (size_t)P.n * (size_t)P.m);
         }
     }
     memcpy(h->bplan_h + items_off, items.data(), (size_t)nb * sizeof(BatchItem));
@@ -1970,9 +2046,11 @@ static evec_status run_batch(evec_handle h, int64_t count, const int64_t *n_host
         EVEC_CUDA(le);
     }
     EVEC_CUDA(cudaGetLastError());
-    if (lam_re && eacc)
+    // pencils: (alpha, beta) per column from the plan buffer, matrix order
+    // (standard problems: the kernel writes the eigenvalues)
+    if (gen && lam_re && eacc)
         EVEC_CUDA(cudaMemcpyAsync(lam_re, h->bplan_h, eacc * 8, cudaMemcpyHostToDevice, st));
-    if (lam_im && eacc)
+    if (gen && lam_im && eacc)
         EVEC_CUDA(cudaMemcpyAsync(lam_im, h->bplan_h + eacc * 8, eacc * 8, cudaMemcpyHostToDevice,
                                   st));
     if (gen && beta_out && eacc)
@@ -1985,12 +2063,27 @@ static evec_status run_batch(evec_handle h, int64_t count, const int64_t *n_host
 
 extern "C" evec_status evec_batched(evec_handle h, int64_t count, const int64_t *n_host,
                                     const double *T_packed, const int64_t *t_off_host,
+                                    const double *Q_packed, const int64_t *q_off_host,
                                     const uint8_t *select_host, double *X_packed,
-                                    int32_t *scale_exp_packed, double *lam_re_packed,
+                                    const int64_t *x_off_host, int32_t *scale_exp_packed,
+                                    const int64_t *e_off_host, double *lam_re_packed,
                                     double *lam_im_packed, const evec_opts *opt) {
     if (!h || count < 0 || count > INT32_MAX ||
-        (count > 0 && (!n_host || !t_off_host || !T_packed)))
+        (count > 0 && (!n_host || !t_off_host || !T_packed)) || (Q_packed && !q_off_host))
         return EVEC_EINVAL;
+    for (int64_t i = 0; i < count; i++)
+        if ((x_off_host && x_off_host[i] < 0) || (e_off_host && e_off_host[i] < 0))
+            return EVEC_EINVAL;
+    BatchOut bo;
+    bo.Q = Q_packed;
+    bo.q_off = Q_packed ? q_off_host : nullptr;
+    bo.x_off = x_off_host;
+    bo.e_off = e_off_host;
+    auto same_offs = [&](const std::vector<int64_t> &v, const int64_t *a) {
+        return a ? (v.size() == (size_t)count &&
+                    memcmp(v.data(), a, count * sizeof(int64_t)) == 0)
+                 : v.empty();
+    };
     const int mode = opt ? opt->mode : EVEC_FP64;
     if (mode != EVEC_FP64 && mode != EVEC_SPLIT) return EVEC_EINVAL;
     const int slices = mode == EVEC_SPLIT ? ((opt && opt->slices) ? opt->slices : 8) : 0;
@@ -2014,7 +2107,9 @@ extern "C" evec_status evec_batched(evec_handle h, int64_t count, const int64_t 
                     K.T == (const void *)T_packed && K.X == (const void *)X_packed &&
                     K.E == (const void *)scale_exp_packed && K.lr == (const void *)lam_re_packed &&
                     K.li == (const void *)lam_im_packed && K.tile == tile && K.mode == mode &&
-                    K.slices == slices && K.has_sel == (select_host != nullptr);
+                    K.slices == slices && K.has_sel == (select_host != nullptr) &&
+                    K.Q == (const void *)Q_packed && same_offs(K.qoff, bo.q_off) &&
+                    same_offs(K.xoff, x_off_host) && same_offs(K.eoff, e_off_host);
         same = same && memcmp(K.n.data(), n_host, count * sizeof(int64_t)) == 0 &&
                memcmp(K.toff.data(), t_off_host, count * sizeof(int64_t)) == 0;
         if (same && tile == 0)
@@ -2029,13 +2124,6 @@ extern "C" evec_status evec_batched(evec_handle h, int64_t count, const int64_t 
                 return 1;
             });
             EVEC_CUDA(le);
-            const int64_t eacc = K.eacc;
-            if (lam_re_packed && eacc)
-                EVEC_CUDA(cudaMemcpyAsync(lam_re_packed, h->bplan_h, eacc * 8,
-                                          cudaMemcpyHostToDevice, h->stream));
-            if (lam_im_packed && eacc)
-                EVEC_CUDA(cudaMemcpyAsync(lam_im_packed, h->bplan_h + eacc * 8, eacc * 8,
-                                          cudaMemcpyHostToDevice, h->stream));
             if (opt && opt->check) return evec_sync(h, nullptr);
             return EVEC_OK;
         }
@@ -2099,9 +2187,18 @@ extern "C" evec_status evec_batched(evec_handle h, int64_t count, const int64_t 
                                    all, plans, &bad));
     }
     EVEC_TRY(run_batch(h, count, n_host, T_packed, t_off_host, all, plans, X_packed,
-                       scale_exp_packed, lam_re_packed, lam_im_packed, true, slices));
+                       scale_exp_packed, lam_re_packed, lam_im_packed, true, slices, nullptr,
+                       nullptr, nullptr, 0, bo));
     {   // remember this call for a replay
         BatchKey &K = h->bcall;
+        K.Q = Q_packed;
+        auto keep = [&](std::vector<int64_t> &v, const int64_t *a) {
+            if (a) v.assign(a, a + count);
+            else v.clear();
+        };
+        keep(K.qoff, bo.q_off);
+        keep(K.xoff, x_off_host);
+        keep(K.eoff, e_off_host);
         K.n.assign(n_host, n_host + count);
         K.toff.assign(t_off_host, t_off_host + count);
         K.T = T_packed;
@@ -2121,6 +2218,35 @@ extern "C" evec_status evec_batched(evec_handle h, int64_t count, const int64_t 
         K.valid = true;
     }
     if (opt && opt->check) return evec_sync(h, nullptr);
+    return EVEC_OK;
+}
+
+extern "C" evec_status evec_batched_generalized_count(
+    evec_handle h, int64_t count, const int64_t *n_host, const double *S_packed,
+    const int64_t *s_off_host, const double *T_packed, const int64_t *t_off_host,
+    const uint8_t *select_host, int64_t *m_host) {
+    if (!h || count < 0 || count > INT32_MAX ||
+        (count > 0 && (!n_host || !s_off_host || !t_off_host || !S_packed || !T_packed ||
+                       !m_host)))
+        return EVEC_EINVAL;
+    if (count == 0) return EVEC_OK;
+    DeviceGuard g(h->device);
+    if (!g.ok) return EVEC_ECUDA;
+    int64_t rows = 0;
+    for (int64_t i = 0; i < count; i++) {
+        if (n_host[i] < 0 || t_off_host[i] < 0) return EVEC_EINVAL;
+        rows += n_host[i];
+    }
+    h->bcall.valid = false;
+    const size_t ndiag = (size_t)std::max<int64_t>(3 * rows, 1);
+    EVEC_TRY(batched_gather(h, count, n_host, T_packed, t_off_host));
+    std::vector<double> diagT(h->diag_h, h->diag_h + ndiag);
+    EVEC_TRY(batched_gather(h, count, n_host, S_packed, s_off_host));
+    std::vector<int> tiles(count, 64), all(count);
+    for (int64_t i = 0; i < count; i++) all[i] = (int)i;
+    EVEC_TRY(batched_build(h, count, n_host, s_off_host, select_host, tiles, all, h->bplans,
+                           nullptr, diagT.data()));
+    for (int64_t i = 0; i < count; i++) m_host[i] = h->bplans[i].m;
     return EVEC_OK;
 }
 
@@ -2240,6 +2366,43 @@ extern "C" evec_status evec_tune_set(evec_handle h, int mode, int size_class, in
 // ---------------------------------------------------------------------------
 // generalized problem (pencil (S, T))
 // ---------------------------------------------------------------------------
+// The pencil plan in h->plan: S's three central diagonals and T's diagonal
+// and superdiagonal read back, then the host planner (blocks from S, (alpha,
+// beta) per block, tiles of nb rows).
+static evec_status plan_pencil(evec_handle h, int64_t n, const double *S, int64_t lds,
+                               const double *T, int64_t ldt, const uint8_t *select_host, int nb) {
+    const size_t cnt = (size_t)(3 * n > 2 ? 3 * n - 2 : 1);
+    EVEC_TRY(grow_device(&h->diag_d, &h->diag_cap, 2 * cnt));
+    EVEC_TRY(grow_host(&h->diag_h, &h->diag_h_cap, 2 * cnt));
+    timed(h, EVEC_K_GATHER, [&] {
+        launch_gather_diagonals(S, lds, n, h->diag_d, h->stream);
+        launch_gather_diagonals(T, ldt, n, h->diag_d + cnt, h->stream);
+        return 2;
+    });
+    EVEC_CUDA(cudaGetLastError());
+    EVEC_CUDA(cudaMemcpyAsync(h->diag_h, h->diag_d, 2 * cnt * sizeof(double),
+                              cudaMemcpyDeviceToHost, h->stream));
+    EVEC_CUDA(cudaStreamSynchronize(h->stream));
+    const double *d = h->diag_h, *dt = h->diag_h + cnt;
+    PencilDiags pd = {dt, dt + 2 * n - 1};
+    int64_t bad = -1;
+    h->pkey.valid = false;   // h->plan now holds a pencil plan
+    return build_plan(n, d, d + n, d + 2 * n - 1, select_host, nb, lds, h->plan, &bad, &pd);
+}
+
+extern "C" evec_status evec_count_generalized(evec_handle h, int64_t n, const double *S,
+                                              int64_t lds, const double *T, int64_t ldt,
+                                              const uint8_t *select_host, int64_t *m) {
+    if (!h || !m || n < 0 || !ld_ok(lds, n) || !ld_ok(ldt, n) || (n > 0 && (!S || !T)))
+        return EVEC_EINVAL;
+    if (n == 0) { *m = 0; return EVEC_OK; }
+    DeviceGuard g(h->device);
+    if (!g.ok) return EVEC_ECUDA;
+    EVEC_TRY(plan_pencil(h, n, S, lds, T, ldt, select_host, 64));
+    *m = h->plan.m;
+    return EVEC_OK;
+}
+
 extern "C" evec_status evec_generalized(evec_handle h, int64_t n, const double *S, int64_t lds,
                                         const double *T, int64_t ldt, const double *Z,
                                         int64_t ldz, const uint8_t *select_host, double *X,
@@ -2259,27 +2422,7 @@ extern "C" evec_status evec_generalized(evec_handle h, int64_t n, const double *
     DeviceGuard g(h->device);
     if (!g.ok) return EVEC_ECUDA;
 
-    // plan: S's three central diagonals, T's diagonal and superdiagonal
-    const size_t cnt = (size_t)(3 * n > 2 ? 3 * n - 2 : 1);
-    EVEC_TRY(grow_device(&h->diag_d, &h->diag_cap, 2 * cnt));
-    EVEC_TRY(grow_host(&h->diag_h, &h->diag_h_cap, 2 * cnt));
-    timed(h, EVEC_K_GATHER, [&] {
-        launch_gather_diagonals(S, lds, n, h->diag_d, h->stream);
-        launch_gather_diagonals(T, ldt, n, h->diag_d + cnt, h->stream);
-        return 2;
-    });
-    EVEC_CUDA(cudaGetLastError());
-    EVEC_CUDA(cudaMemcpyAsync(h->diag_h, h->diag_d, 2 * cnt * sizeof(double),
-                              cudaMemcpyDeviceToHost, h->stream));
-    EVEC_CUDA(cudaStreamSynchronize(h->stream));
-    {
-        const double *d = h->diag_h, *dt = h->diag_h + cnt;
-        PencilDiags pd = {dt, dt + 2 * n - 1};
-        int64_t bad = -1;
-        h->pkey.valid = false;   // h->plan now holds a pencil plan
-        EVEC_TRY(build_plan(n, d, d + n, d + 2 * n - 1, select_host, nb, lds, h->plan, &bad,
-                            &pd));
-    }
+    EVEC_TRY(plan_pencil(h, n, S, lds, T, ldt, select_host, nb));
     HostPlan &HP = h->plan;
     split_panel_layout(HP, mode == EVEC_SPLIT ? slices : 0);
     const int64_t m = HP.m;

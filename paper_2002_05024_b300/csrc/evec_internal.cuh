@@ -91,6 +91,15 @@ struct BatchItem {
     int64_t ldt2;
     int64_t t2_base;
     double *tau2, *blk_tau2;
+    // back-transformation (standard problem): with Q non-null the solve
+    // writes Y into X (a workspace, leading dimension n), then the CTA forms
+    // Xout = Q Y and its canonical form; without Q, Xout == X
+    const double *Q;
+    int64_t ldq;
+    double *Xout;
+    int64_t ldxo;
+    // eigenvalues per output column (may be null), written by the CTA
+    double *lam_re, *lam_im;
 };
 
 // ---------------------------------------------------------------------------

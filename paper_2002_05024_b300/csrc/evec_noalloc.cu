@@ -18,8 +18,8 @@
 // that device.  Every call shares the array and leaves its contents behind;
 // the status word is cleared at the start of each call and everything else
 // is written before it is read.  Calls are serialised on the host and each
-// call synchronises its stream before returning, so calls made through this
-// entry point do not overlap; work on the same device that is launched by
+// call synchronises its stream before returning (also when it fails after
+// queuing work), so calls made through this entry point do not overlap; work on the same device that is launched by
 // other means while such a call runs must not touch the array (only this
 // file can name it).
 #include <cuda_runtime.h>
@@ -180,6 +180,15 @@ struct Layout {
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// An error after work was queued on st: wait for that work (it may still
+// write the shared array) and clear the error, so the lock is released only
+// once nothing of this call runs any more.
+evec_status drain_and_fail(cudaStream_t st) {
+    cudaStreamSynchronize(st);
+    cudaGetLastError();
+    return EVEC_ECUDA;
+}
+
 Layout layout(int n, int ntiles, int nblk, int nunits, int m) {
     Layout L;
     size_t o = 0;
@@ -240,13 +249,11 @@ extern "C" evec_status evec_standard_noalloc(int64_t n, const double *T, int64_t
     // the diagonals: gathered into the scratch array, read back to the stack
     const size_t diag_off = layout((int)n, 1, 1, 1, 1).diag;
     launch_gather_diagonals(T, ldt, n, (double *)(base + diag_off), st);
-    if (cudaGetLastError() != cudaSuccess) return EVEC_ECUDA;
+    if (cudaGetLastError() != cudaSuccess) return drain_and_fail(st);
     if (cudaMemcpyAsync(P.diag, base + diag_off, sizeof(double) * (3 * (size_t)n - 2),
                         cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-        cudaStreamSynchronize(st) != cudaSuccess) {
-        cudaGetLastError();
-        return EVEC_ECUDA;
-    }
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return drain_and_fail(st);
     evec_status ps = plan_small(P, (int)n, select_host, nb, ldt, bad_index);
     if (ps != EVEC_OK) return ps;
     if (P.m == 0) return EVEC_OK;
@@ -259,7 +266,7 @@ extern "C" evec_status evec_standard_noalloc(int64_t n, const double *T, int64_t
                                     sizeof(int32_t) * (6 * (kMaxTiles + 1) + 6 * kMaxN) +
                                     kMaxN + 64];
     size_t off = 0;
-    Plan dp;
+    Plan dp{};
     auto put = [&](const void *src, size_t bytes, size_t align) -> const void * {
         off = align_up(off, align);
         memcpy(packed + off, src, bytes);
@@ -302,10 +309,8 @@ extern "C" evec_status evec_standard_noalloc(int64_t n, const double *T, int64_t
 
     // the status word is the only scratch that must start at zero
     if (cudaMemsetAsync(status, 0, sizeof(DevStatus), st) != cudaSuccess ||
-        cudaMemcpyAsync(base + L.plan, packed, off, cudaMemcpyHostToDevice, st) != cudaSuccess) {
-        cudaGetLastError();
-        return EVEC_ECUDA;
-    }
+        cudaMemcpyAsync(base + L.plan, packed, off, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return drain_and_fail(st);
     launch_tile_norms(T, ldt, dp, tau, blk_tau, status, st);
     for (int s = P.ntiles - 1; s >= 0; s--) {
         launch_diag_solve(s, T, ldt, dp, P.tile_start, P.tile_real, P.tile_cplx, tau, blk_tau, X,
@@ -316,13 +321,11 @@ extern "C" evec_status evec_standard_noalloc(int64_t n, const double *T, int64_t
                                seg_nu, st);
     }
     launch_finalize(dp, X, ldx, seg_e, scale_exp, st);
-    if (cudaGetLastError() != cudaSuccess) return EVEC_ECUDA;
+    if (cudaGetLastError() != cudaSuccess) return drain_and_fail(st);
     DevStatus hs;
     if (cudaMemcpyAsync(&hs, status, sizeof(DevStatus), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-        cudaStreamSynchronize(st) != cudaSuccess) {
-        cudaGetLastError();
-        return EVEC_ECUDA;
-    }
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return drain_and_fail(st);
     if (hs.code != 0 && bad_index) *bad_index = hs.index;
     return (evec_status)hs.code;
 }

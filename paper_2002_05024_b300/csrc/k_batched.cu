@@ -512,6 +512,104 @@ __device__ void cta_finalize_unit(const BatchItem &B, int u, int *sbest) {
     }
 }
 
+// Back-transformation Xout = Q Y of a solved matrix (Y canonical, zero
+// below each column's block), in 64 x 64 blocks of Xout with the thread
+// layout of cta_tile_update: K runs to the block end of the last column of
+// the column block (the rows below are zero in every column of it).  Then
+// the canonical form of every unit's columns (max_i |x_i|, a pair's
+// |re| + |im|, brought into [1, 2); the exponent adjusted by the same
+// power of two).  Y is canonical, so |Q Y|_inf <= 2 sqrt(n): no overflow.
+// smem: As [64][64], Bs [64][65] doubles; red [4] doubles.
+__device__ void cta_backtransform(const BatchItem &B, double *smem, double *red) {
+    const Plan &P = B.P;
+    const int64_t m = P.m, n = P.n;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int lane = tid & 31, warp = tid >> 5;
+    double *Bs = smem;                  // [k][65]
+    double *As = Bs + 64 * 65;          // [k][64]
+    for (int64_t j0 = 0; j0 < m; j0 += 64) {
+        const int nc = (int)min((int64_t)64, m - j0);
+        const int ul = P.col_unit[j0 + nc - 1];
+        const int kb = P.unit_blk[ul];
+        const int kend = P.blk_start[kb] + P.blk_size[kb];
+        for (int64_t i0 = 0; i0 < n; i0 += 64) {
+            const int rows = (int)min((int64_t)64, n - i0);
+            double acc[8][4];
+#pragma unroll
+            for (int i = 0; i < 8; i++)
+#pragma unroll
+                for (int j = 0; j < 4; j++) acc[i][j] = 0.0;
+            for (int k0 = 0; k0 < kend; k0 += 64) {
+                const int K = min(64, kend - k0);
+                __syncthreads();   // the previous chunk's readers are done
+                for (int e = tid; e < 64 * 64; e += kBThreads) {
+                    const int i = e % 64, k = e / 64;
+                    As[k * 64 + i] = (i < rows && k < K) ? B.Q[(i0 + i) + (int64_t)(k0 + k) * B.ldq]
+                                                         : 0.0;
+                }
+                for (int e = tid; e < 64 * 64; e += kBThreads) {
+                    const int k = e % 64, j = e / 64;
+                    Bs[k * 65 + j] = (k < K && j < nc) ? B.X[(k0 + k) + (j0 + j) * B.ldx] : 0.0;
+                }
+                __syncthreads();
+                for (int k = 0; k < K; k++) {
+                    double a[8], b[4];
+#pragma unroll
+                    for (int i = 0; i < 8; i++) a[i] = As[k * 64 + ty + 8 * i];
+#pragma unroll
+                    for (int j = 0; j < 4; j++) b[j] = Bs[k * 65 + tx + 16 * j];
+#pragma unroll
+                    for (int i = 0; i < 8; i++)
+#pragma unroll
+                        for (int j = 0; j < 4; j++) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const int jl = tx + 16 * j;
+                if (jl >= nc) continue;
+                double *c = B.Xout + (j0 + jl) * B.ldxo + i0;
+#pragma unroll
+                for (int i = 0; i < 8; i++) {
+                    const int row = ty + 8 * i;
+                    if (row < rows) c[row] = acc[i][j];
+                }
+            }
+        }
+    }
+    __syncthreads();   // every column of Xout is written
+    constexpr int kW = kBThreads / 32;
+    for (int u = 0; u < P.nunits; u++) {
+        const int col = P.unit_col[u];
+        const bool cplx = P.unit_lam[2 * u + 1] != 0.0;
+        double *xr = B.Xout + (int64_t)col * B.ldxo;
+        double *xi = B.Xout + (int64_t)(col + 1) * B.ldxo;
+        double mx = 0.0;
+        for (int64_t i = tid; i < n; i += kBThreads) {
+            double v = fabs(xr[i]);
+            if (cplx) v += fabs(xi[i]);
+            mx = fmax(mx, v);
+        }
+        mx = bwarp_max(mx);
+        if (lane == 0) red[warp] = mx;
+        __syncthreads();
+        mx = 0.0;
+#pragma unroll
+        for (int w = 0; w < kW; w++) mx = fmax(mx, red[w]);
+        __syncthreads();   // red is reused by the next unit
+        if (mx == 0.0) continue;
+        const int t2 = ilog2_abs(mx);
+        for (int64_t i = tid; i < n; i += kBThreads) {
+            xr[i] = scale2(xr[i], -t2);
+            if (cplx) xi[i] = scale2(xi[i], -t2);
+        }
+        if (tid == 0) {
+            B.scale_exp[col] -= t2;
+            if (cplx) B.scale_exp[col + 1] -= t2;
+        }
+    }
+}
+
 }  // namespace
 
 // GEN: every item is a pencil (beta S - alpha T), FP64 updates only.
@@ -522,6 +620,7 @@ __global__ void __launch_bounds__(kBThreads)
     extern __shared__ double smem[];
     __shared__ int next;
     __shared__ int sbest[kBThreads / 32];
+    __shared__ double sred[kBThreads / 32];
     __shared__ uint64_t mbar;
     __shared__ uint32_t tmem_holder;
     uint32_t tmem = 0, phase = 0;
@@ -589,6 +688,23 @@ __global__ void __launch_bounds__(kBThreads)
         if (!alive) break;
         for (int u = 0; u < P.nunits; u++) cta_finalize_unit(B, u, sbest);
         __syncthreads();
+        if constexpr (!GEN) {
+            if (B.lam_re || B.lam_im)
+                for (int u = threadIdx.x; u < P.nunits; u += kBThreads) {
+                    const int col = P.unit_col[u];
+                    const double re = P.unit_lam[2 * u], im = P.unit_lam[2 * u + 1];
+                    if (B.lam_re) B.lam_re[col] = re;
+                    if (B.lam_im) B.lam_im[col] = im;
+                    if (im != 0.0) {
+                        if (B.lam_re) B.lam_re[col + 1] = re;
+                        if (B.lam_im) B.lam_im[col + 1] = -im;
+                    }
+                }
+            if (B.Q) {
+                cta_backtransform(B, smem, sred);
+                __syncthreads();
+            }
+        }
     }
     if constexpr (SPLIT) {
         asm volatile("tcgen05.fence::before_thread_sync;");

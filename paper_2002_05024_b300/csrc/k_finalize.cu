@@ -263,7 +263,8 @@ __global__ void __launch_bounds__(kWarps * 32)
 __global__ void __launch_bounds__(kWarps * 32)
     k_gate(Plan P, const double *__restrict__ Y, int64_t ldy, const int32_t *__restrict__ ey,
            const double *__restrict__ R, int64_t ldr, const unsigned long long *__restrict__ tn,
-           double limit, int *__restrict__ fails, double *__restrict__ ratio) {
+           double limit, int *__restrict__ fails, double *__restrict__ ratio,
+           int *__restrict__ first_col) {
     const int u = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t m = P.m;
@@ -321,19 +322,25 @@ __global__ void __launch_bounds__(kWarps * 32)
         const double tnorm = __longlong_as_double((long long)*tn);
         const double q = r1 / (tnorm * y1 * 0x1p-53);
         if (ratio) ratio[u] = q;
-        if (!(q <= limit)) atomicAdd(fails, 1);
+        if (!(q <= limit)) {
+            atomicAdd(fails, 1);
+            atomicMin(first_col, col);
+        }
     }
 }
 
 void launch_gate(const Plan &p, const double *Y, int64_t ldy, const int32_t *ey, const double *R,
                  int64_t ldr, const double *T, int64_t ldt, double limit, void *buf,
                  double *ratio, cudaStream_t st) {
-    // buf: [0] ||T||_1 bits, [1] failure count (int)
+    // buf: [0] ||T||_1 bits, [1] the failure count (int) and the output
+    // column of the first failing eigenvalue (int, 0x7f7f7f7f when none)
     unsigned long long *tn = (unsigned long long *)buf;
     int *fails = (int *)(tn + 1);
     cudaMemsetAsync(buf, 0, 2 * sizeof(unsigned long long), st);
+    cudaMemsetAsync(fails + 1, 0x7f, sizeof(int), st);
     k_norm1<<<(unsigned)((p.n + kWarps - 1) / kWarps), kWarps * 32, 0, st>>>(T, ldt, p.n, tn);
-    k_gate<<<p.nunits, kWarps * 32, 0, st>>>(p, Y, ldy, ey, R, ldr, tn, limit, fails, ratio);
+    k_gate<<<p.nunits, kWarps * 32, 0, st>>>(p, Y, ldy, ey, R, ldr, tn, limit, fails, ratio,
+                                             fails + 1);
 }
 
 void launch_rhs_init(const Plan &p, const double *R, int64_t ldr, double *seg_nu,

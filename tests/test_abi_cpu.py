@@ -106,3 +106,20 @@ def test_no_cpu_fallback_without_gpu():
     # the device entry points refuse a NULL handle before touching anything
     assert ev.lib().evec_standard(None, 4, None, 4, None, 4, None, None, 4, None, None,
                                   None, None) == ev.EVEC_EINVAL
+
+
+def test_opts_defaults_in_the_documented_field_order():
+    # evec_opts as the header lays it out: {mode, tile, slices, refine,
+    # check}; the defaults (those of opt == NULL) set only refine
+    class Opts(ctypes.Structure):
+        _fields_ = [("mode", ctypes.c_int), ("tile", ctypes.c_int), ("slices", ctypes.c_int),
+                    ("refine", ctypes.c_int), ("check", ctypes.c_int)]
+
+    assert [f[0] for f in ev._Opts._fields_] == [f[0] for f in Opts._fields_]
+    o = Opts(7, 7, 7, 7, 7)
+    f = ev.lib().evec_opts_default
+    f.argtypes = [ctypes.POINTER(Opts)]
+    f.restype = None
+    f(ctypes.byref(o))
+    assert (o.mode, o.tile, o.slices, o.refine, o.check) == (0, 0, 0, 1, 0)
+    f(None)                                   # a NULL pointer is ignored

@@ -209,3 +209,67 @@ def test_batched_split_config3_full_size_sampled():
                           [adv[i] for i in pick], [res[i] for i in pick])
     for X, e, lr, li in res:
         assert bool(torch.isfinite(X).all())
+
+
+@pytest.mark.parametrize("mode", ["fp64", "split"])
+def test_batched_with_q_and_output_offsets(mode):
+    # a nullable Q per matrix (every other one back-transformed, X_i = Q_i Y_i)
+    # and outputs placed by x_off / e_off in reverse matrix order with gaps;
+    # each matrix against oracle.standard(T_i, Q=Q_i), and a second identical
+    # call (a replay of the captured graph) gives the same bits
+    sizes = [150, 33, 300, 64, 97, 1, 260, 40]
+    Ts, sels, adv = _members(sizes, seed=17, adversarial_every=4)
+    Qs = [workloads.householder_orthogonal(int(n), seed=300 + i) if i % 2 == 0 else None
+          for i, n in enumerate(sizes)]
+    Tp, ns, toffs = ev.pack_batch(Ts)
+    Qp, _, hoffs = ev.pack_batch([q for q in Qs if q is not None])
+    qoffs = np.full(len(Ts), -1, dtype=np.int64)
+    k = 0
+    for i, q in enumerate(Qs):
+        if q is not None:
+            qoffs[i] = hoffs[k]
+            k += 1
+    sel = np.concatenate([np.ones(n, np.uint8) if s is None else s for s, n in zip(sels, ns)])
+    m = ev.batched_count(Tp, ns, toffs, sel)
+    xoffs = np.zeros(len(Ts), dtype=np.int64)
+    eoffs = np.zeros(len(Ts), dtype=np.int64)
+    xa = ea = 0
+    for i in reversed(range(len(Ts))):          # reverse order, 7-element gaps
+        xoffs[i], eoffs[i] = xa, ea
+        xa += int(ns[i] * m[i]) + 7
+        ea += int(m[i]) + 7
+    X = torch.full((xa,), np.nan, dtype=torch.float64, device="cuda")
+    e = torch.zeros(ea, dtype=torch.int32, device="cuda")
+    lr = torch.zeros(ea, dtype=torch.float64, device="cuda")
+    li = torch.zeros(ea, dtype=torch.float64, device="cuda")
+    outs = []
+    for _ in range(2):
+        ev.batched_packed(Tp, ns, toffs, sel, tile=32, mode=mode, check=True,
+                          out=(X, e, lr, li, m), Q_packed=Qp, q_offs=qoffs, x_offs=xoffs,
+                          e_offs=eoffs)
+        outs.append((X.cpu().numpy().copy(), e.cpu().numpy().copy()))
+    np.testing.assert_array_equal(outs[0][0], outs[1][0])
+    np.testing.assert_array_equal(outs[0][1], outs[1][1])
+    Xh, eh, lrh, lih = X.cpu().numpy(), e.cpu().numpy(), lr.cpu().numpy(), li.cpu().numpy()
+    for i, (T, s, a, Q) in enumerate(zip(Ts, sels, adv, Qs)):
+        n, mi = int(ns[i]), int(m[i])
+        Xo, eo, lro, lio = oracle.standard(T, Q=Q, select=s)
+        assert Xo.shape == (n, mi)
+        if mi == 0:
+            continue
+        Xi = Xh[xoffs[i]:xoffs[i] + n * mi].reshape(mi, n).T
+        ei = eh[eoffs[i]:eoffs[i] + mi]
+        np.testing.assert_array_equal(lrh[eoffs[i]:eoffs[i] + mi], lro)
+        np.testing.assert_array_equal(lih[eoffs[i]:eoffs[i] + mi], lio)
+        assert np.isfinite(Xi).all()
+        de, rel = compare_canonical(Xo, eo, Xi, ei, lio)
+        assert de <= 1, (i, de)
+        assert rel <= (1e-3 if a else 1e-10), (i, n, rel)
+        A = T if Q is None else Q @ T @ Q.T
+        r = standard_residuals(A, Xi, lro, lio)
+        assert r.max() <= 10 * n, (i, r.max())
+    # the gaps between the outputs are untouched
+    gaps = np.ones(xa, bool)
+    for i in range(len(Ts)):
+        gaps[xoffs[i]:xoffs[i] + int(ns[i] * m[i])] = False
+    assert np.isnan(Xh[gaps]).all()

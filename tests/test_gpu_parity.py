@@ -27,11 +27,13 @@ pytestmark = pytest.mark.gpu
 REL_TOL = 1e-10
 
 
-def _gpu(T, Q=None, select=None, tile=0, mode="fp64", slices=0):
+def _gpu(T, Q=None, select=None, tile=0, mode="fp64", slices=0, refine=0):
+    # split mode here is the plain split solve (no residual-correction sweep;
+    # the sweep has its own tests)
     dT = torch.from_numpy(np.asfortranarray(T)).cuda()
     dQ = None if Q is None else torch.from_numpy(np.asfortranarray(Q)).cuda()
     X, e, lr, li = ev.standard(dT, dQ, select=select, tile=tile, check=True, mode=mode,
-                               slices=slices)
+                               slices=slices, refine=refine)
     torch.cuda.synchronize()
     return X.cpu().numpy(), e.cpu().numpy(), lr.cpu().numpy(), li.cpu().numpy()
 

@@ -12,6 +12,8 @@ eps ~ 1e-4 here: one sweep gains about four digits).  At 8 slices the split
 solve is already as close to the exact eigenvectors as the FP64 solve
 (checked against an extended-precision backsubstitution below), and the
 sweep takes only corrections below 2^(20 - 7 slices) of a column."""
+import ctypes
+
 import numpy as np
 import pytest
 import torch
@@ -282,3 +284,70 @@ def test_residual_gate_with_q_and_left():
     Xo, eo, _, lio = oracle.left(T)
     de, rel = compare_canonical(Xo, eo, X.cpu().numpy(), e.cpu().numpy(), lio)
     assert de <= 1 and rel <= REL_TOL, (de, rel)
+
+
+def test_residual_gate_reports_eresidual_after_every_repeat():
+    # a gate no result can pass (factor 1e-30 instead of 10): the split
+    # solve fails it, the 8-slice repeat fails it, the FP64 repeat fails it
+    # too, and evec_sync reports EVEC_ERESIDUAL with the output column of the
+    # first failing eigenvalue; the result is the FP64 one
+    n = 300
+    T, _ = workloads.config0_schur(n, seed=66)
+    dT = torch.from_numpy(np.asfortranarray(T)).cuda()
+    h = ev.handle(0)
+    L = ev.lib()
+    L.evec_set_gate_factor.argtypes = [ctypes.c_void_p, ctypes.c_double]
+    L.evec_set_gate_factor.restype = ctypes.c_int
+    assert L.evec_set_gate_factor(h.ptr, 0.0) == ev.EVEC_EINVAL
+    assert L.evec_set_gate_factor(h.ptr, 1e-30) == ev.EVEC_OK
+    try:
+        X, e, lr, li = ev.standard(dT, tile=32, mode="split", slices=4, refine=2)
+        with pytest.raises(ev.EvecError) as ei:
+            h.sync()
+        assert ei.value.status == ev.EVEC_ERESIDUAL
+        assert ei.value.bad == 0
+        assert ev.handle(0).gate_stats()[1] == 2       # 8 slices, then FP64
+        Xf, ef, _, lif = ev.standard(dT, tile=32, mode="fp64", check=True)
+        np.testing.assert_array_equal(X.cpu().numpy(), Xf.cpu().numpy())
+        np.testing.assert_array_equal(e.cpu().numpy(), ef.cpu().numpy())
+    finally:
+        assert L.evec_set_gate_factor(h.ptr, 10.0) == ev.EVEC_OK
+    # the default gate again: passes, and the status was cleared
+    out = _gpu(T, tile=32, slices=4, refine=2)
+    h.sync()
+    assert _against_oracle(T, None, out) <= REL_TOL
+
+
+def test_opts_struct_in_the_documented_field_order():
+    # evec_opts filled by a C caller in the header's order {mode, tile,
+    # slices, refine, check}: slices = 9 in the third field is refused, and
+    # check = 1 in the fifth makes the call return the device status
+    class Opts(ctypes.Structure):
+        _fields_ = [("mode", ctypes.c_int), ("tile", ctypes.c_int), ("slices", ctypes.c_int),
+                    ("refine", ctypes.c_int), ("check", ctypes.c_int)]
+
+    n = 120
+    T, _ = workloads.config0_schur(n, seed=67)
+    L = ev.lib()
+    f = L.evec_standard
+    p, i64 = ctypes.c_void_p, ctypes.c_int64
+    f.argtypes = [p, i64, p, i64, p, i64, p, p, i64, p, p, p, ctypes.POINTER(Opts)]
+    f.restype = ctypes.c_int
+    h = ev.handle(0)
+    X = torch.empty((n, n), dtype=torch.float64, device="cuda").t()
+    e = torch.empty(n, dtype=torch.int32, device="cuda")
+    bad_T = np.array(T, order="F", copy=True)
+    bad_T[5, 100] = np.inf
+    dT = torch.from_numpy(np.asfortranarray(bad_T)).cuda()
+
+    def call(o):
+        return f(h.ptr, n, dT.data_ptr(), n, None, n, None, X.data_ptr(), n, e.data_ptr(), None,
+                 None, ctypes.byref(o))
+
+    assert call(Opts(mode=1, tile=32, slices=9, refine=0, check=1)) == ev.EVEC_EINVAL
+    assert call(Opts(mode=1, tile=32, slices=6, refine=0, check=1)) == ev.EVEC_ENONFINITE
+    d = Opts()
+    L.evec_opts_default.argtypes = [ctypes.POINTER(Opts)]
+    L.evec_opts_default.restype = None
+    L.evec_opts_default(ctypes.byref(d))
+    assert (d.mode, d.tile, d.slices, d.refine, d.check) == (0, 0, 0, 1, 0)
