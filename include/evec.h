@@ -244,6 +244,14 @@ evec_status evec_window_update_set(evec_handle h, int64_t n, double *T, int64_t 
                                    const int32_t *size_host, const double *Z,
                                    const int64_t *zoff_host, const evec_opts *opt);
 
+/* Polls (about 64 ns each) that a CTA of evec_hessenberg's cooperative
+ * panel waits at a grid barrier before it gives up (0 = the built-in
+ * limit, 2^22 polls).  A wait that gives up makes the kernel's CTAs return
+ * and evec_sync report EVEC_ETIMEOUT; the matrix is then left partly
+ * reduced.  The handle stays usable.  A small limit makes the waits run
+ * out (a test of the failure path).  Errors: EVEC_EINVAL (polls < 0). */
+evec_status evec_set_wait_limit(evec_handle h, int64_t polls);
+
 /* How evec_hessenberg reduces a panel: 1 (default) one cooperative launch
  * per panel (every CTA co-resident, bounded grid barriers between the
  * column phases; falls back to 0 when the device refuses the launch), 0

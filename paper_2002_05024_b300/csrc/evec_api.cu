@@ -57,7 +57,7 @@ size_t hessenberg_workspace(int64_t n);
 int hess_panel_width();
 void hess_init_q(int64_t n, double *Q, int64_t ldq, cudaStream_t st);
 int hess_panel(int64_t n, double *A, int64_t lda, int64_t k, int b, double *ws, int *err,
-               int nsm, bool cooperative, cudaStream_t st);
+               int nsm, bool cooperative, cudaStream_t st, long wait_limit);
 int hess_update(int64_t n, double *A, int64_t lda, double *Q, int64_t ldq, int64_t k, int b,
                 double *ws, cudaStream_t st, cudaStream_t qst, cudaEvent_t fork,
                 cudaEvent_t join);
@@ -586,6 +586,7 @@ struct evec_ctx {
     int pend_code = 0;
     int64_t pend_index = -1;
     bool hess_coop = true;   // panel as one cooperative launch (else six launches per column)
+    long wait_limit = 0;     // polls of a bounded device-side wait; 0 = the built-in limit
     std::vector<int32_t> lmap_h;
     std::vector<uint8_t> lsel;
     // pinned host buffers
@@ -990,6 +991,12 @@ void evec_opts_default(evec_opts *opt) {
     opt->slices = 0;
     opt->refine = 1;
     opt->check = 0;
+}
+
+evec_status evec_set_wait_limit(evec_handle h, int64_t polls) {
+    if (!h || polls < 0) return EVEC_EINVAL;
+    h->wait_limit = (long)polls;
+    return EVEC_OK;
 }
 
 evec_status evec_set_gate_factor(evec_handle h, double factor) {
@@ -2335,7 +2342,7 @@ extern "C" evec_status evec_hessenberg(evec_handle h, int64_t n, double *A, int6
         const int b = (int)std::min<int64_t>(nbw, n - 2 - k);
         timed(h, EVEC_K_HESS_PANEL, [&] {
             return hess_panel(n, A, lda, k, b, h->hs_ws, &h->status_d->timeout, h->nsm,
-                              h->hess_coop, st);
+                              h->hess_coop, st, h->wait_limit);
         });
         timed(h, EVEC_K_HESS_UPDATE,
               [&] {

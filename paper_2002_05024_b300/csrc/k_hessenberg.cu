@@ -269,9 +269,12 @@ struct GridBar {
     unsigned count, gen;
 };
 
-// Sense-reversing grid barrier over gridDim.x co-resident CTAs.  Returns
-// false (and sets *err) when the wait gave up.
-__device__ bool grid_barrier(GridBar *bar, int *err) {
+// Sense-reversing grid barrier over gridDim.x co-resident CTAs; a CTA
+// waits at most `limit` polls (about 64 ns each).  Returns false (and sets
+// *err) when the wait gave up.  A CTA that gave up returns from the
+// kernel, so the others give up at their next barrier: every CTA ends
+// within a few limits.
+__device__ bool grid_barrier(GridBar *bar, int *err, long limit) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -287,7 +290,7 @@ __device__ bool grid_barrier(GridBar *bar, int *err) {
         } else {
             long it = 0;
             while (*vgen == my_gen) {
-                if (++it > kGridWaitLimit) {
+                if (++it > limit) {
                     ok = 0;
                     atomicExch(err, 1);
                     break;
@@ -378,7 +381,7 @@ __global__ void __launch_bounds__(kHRowThreads)
     k_hs_panel(int64_t n, double *__restrict__ A, int64_t lda, int64_t k, int b,
                double *__restrict__ V, double *__restrict__ Y, double *__restrict__ T,
                double *__restrict__ x, double *__restrict__ part, double *__restrict__ part2,
-               GridBar *bar, int *err) {
+               GridBar *bar, int *err, long wait_limit) {
     // part: the partials of phase 1 (read in phase 2), part2: those of
     // phase 3 (read in phase 4) -- a CTA done with phase 2 must not
     // overwrite the partials other CTAs are still reading
@@ -423,7 +426,7 @@ __global__ void __launch_bounds__(kHRowThreads)
             if ((int64_t)blockIdx.x < nparts)
                 block_sums_rs(acc, warp_rows, red, part + (int64_t)blockIdx.x * kHPartStride);
         }
-        if (!grid_barrier(bar, err)) return;
+        if (!grid_barrier(bar, err, wait_limit)) return;
         // 2. w = T^T (sum of partials), in every CTA
         sum_partials(part, nparts, 0, red, cs.s);
         if (tid < i) {
@@ -471,7 +474,7 @@ __global__ void __launch_bounds__(kHRowThreads)
                 }
             }
         }
-        if (!grid_barrier(bar, err)) return;
+        if (!grid_barrier(bar, err, wait_limit)) return;
         // 4. the reflector, in every CTA; the partials of V^T x below row
         //    c + 1 (and the sum of squares) into cs.w (w is done with)
         sum_partials(part2, nparts, 0, red, cs.w);
@@ -547,7 +550,7 @@ __global__ void __launch_bounds__(kHRowThreads)
             V[r + (int64_t)i * n] = v;
             if (r > c + 1) A[r + c * lda] = 0.0;
         }
-        if (!grid_barrier(bar, err)) return;
+        if (!grid_barrier(bar, err, wait_limit)) return;
         // 6. Y[:, i] = tau (A[:, c+1:n] v - Y s) for the CTA's own rows, in
         //    32-row chunks; the CTA's 8 warps split the columns.  No grid
         //    barrier follows: until the next column's first barrier a CTA
@@ -857,7 +860,8 @@ void hess_init_q(int64_t n, double *Q, int64_t ldq, cudaStream_t st) {
 // device grants it (co-resident CTAs, bounded grid barriers), else six
 // launches per column.  Returns the kernels launched.
 int hess_panel(int64_t n, double *A, int64_t lda, int64_t k, int b, double *ws, int *err,
-               int nsm, bool cooperative, cudaStream_t st) {
+               int nsm, bool cooperative, cudaStream_t st, long wait_limit) {
+    if (wait_limit <= 0) wait_limit = kGridWaitLimit;
     const HessWs w = hess_ws(n, ws);
     const int parts = hess_parts(n);
     cudaMemsetAsync(w.T, 0, sizeof(double) * kHb * kHb, st);
@@ -876,7 +880,8 @@ int hess_panel(int64_t n, double *A, int64_t lda, int64_t k, int b, double *ws, 
             int bb = b;
             double *V = w.V, *Y = w.Y, *T = w.T, *x = w.x, *pa = w.part, *pb = w.part2;
             GridBar *bar = w.bar;
-            void *args[] = {&nn, &A, &lda, &kk, &bb, &V, &Y, &T, &x, &pa, &pb, &bar, &err};
+            long wl = wait_limit;
+            void *args[] = {&nn, &A, &lda, &kk, &bb, &V, &Y, &T, &x, &pa, &pb, &bar, &err, &wl};
             if (cudaLaunchCooperativeKernel((const void *)k_hs_panel, dim3(grid),
                                             dim3(kHRowThreads), args, 0, st) == cudaSuccess)
                 return 1;

@@ -29,6 +29,9 @@
 // row r) and column j, Y_ij <- 2^dy[r, j] Y_ij - 2^(ea_i + eb_j + dx[r, j])
 // (A~ B~)_ij and merges |Y_ij| into the column maximum of segment (r, j)
 // (shared-memory maxima per CTA, one global atomicMax per (r, j) and CTA).
+#include <math.h>
+
+#include <algorithm>
 #include <mutex>
 
 #include "split_common.cuh"
@@ -146,7 +149,8 @@ __global__ void __launch_bounds__(kSplitThreads, 1)
     k_split_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                  int S, int M, int N, int aRow0, int aMpad, int Npad, const int *__restrict__ kend,
                  int kuni, const int *__restrict__ ea, const int *__restrict__ eb,
-                 double *__restrict__ C, int64_t ldc, SplitUpd upd, int *err) {
+                 double *__restrict__ C, int64_t ldc, SplitUpd upd, int *err, int ntiles_n,
+                 int gw) {
     extern __shared__ unsigned char smraw[];
     unsigned char *base = (unsigned char *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
     uint64_t *bars = (uint64_t *)(base + 2 * kStageBytes);
@@ -157,8 +161,17 @@ __global__ void __launch_bounds__(kSplitThreads, 1)
     int *sdy = sdx + kMaxSlots * kTN;                                 // [kMaxSlots][kTN]
     int *seb = sdy + kMaxSlots * kTN;                                 // [kTN]
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int nt = gridDim.x - 1 - blockIdx.x;   // heaviest column tiles first
-    const int mt = blockIdx.y;
+    // CTA order: groups of gw column tiles; within a group the row bands in
+    // turn, the group's column tiles fastest, so the CTAs resident at one
+    // time cover about (148 / gw) row bands x gw column tiles and share
+    // their operand slices through L2; heaviest column tiles first
+    const int mt_count = gridDim.x / ntiles_n;
+    const int per = gw * mt_count;
+    const int grp = blockIdx.x / per;
+    const int rem = blockIdx.x - grp * per;
+    const int w = min(gw, ntiles_n - grp * gw);
+    const int mt = rem / w;
+    const int nt = ntiles_n - 1 - (grp * gw + rem % w);
     const int n0 = nt * kTN, m0 = mt * kTM;
     const int K = kend ? kend[nt] : kuni;
     if (UPD)
@@ -472,8 +485,20 @@ cudaError_t split_gemm_cols(const double *B, int64_t ldb, int M, int N, int K, i
     cudaFuncSetAttribute(k_split_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
     SplitUpd none = {};
-    k_split_gemm<false><<<dim3(Npad / kTN, Mpad / kTM), kSplitThreads, smem, st>>>(
-        tmA, tmB, S, M, N, 0, Mpad, Npad, kend, 0, ea, eb, C, ldc, none, err);
+    // column tiles per group: gw about sqrt(CTAs in flight x (row band
+    // bytes / column tile bytes)), so one wave's row bands and column tiles
+    // cost about the same DRAM traffic (a band of Q's slices holds twice
+    // the rows of a column tile of Y's)
+    const int ntn = Npad / kTN, mtn = Mpad / kTM;
+    int nsm = 148, dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        nsm = 148;
+    }
+    const int gw = std::max(1, std::min(ntn, (int)lround(sqrt(2.0 * nsm))));
+    k_split_gemm<false><<<ntn * mtn, kSplitThreads, smem, st>>>(
+        tmA, tmB, S, M, N, 0, Mpad, Npad, kend, 0, ea, eb, C, ldc, none, err, ntn, gw);
     return cudaGetLastError();
 }
 
@@ -601,9 +626,10 @@ cudaError_t split_update_step(const SplitUpdateCtx &ctx, int t0, int ts, int pro
     upd.nu = (unsigned long long *)seg_nu;
     upd.m = m;
     upd.col0 = col0;
-    k_split_gemm<true><<<dim3(split_pad_n(N) / kTN, mpad / kTM), kSplitThreads, smem, st>>>(
+    const int ntn = split_pad_n(N) / kTN;
+    k_split_gemm<true><<<ntn * (mpad / kTM), kSplitThreads, smem, st>>>(
         ctx.tmA, ctx.tmB32, ctx.S, t0, N, prow0, mpad, ctx.Npad, nullptr, (K + kTK - 1) / kTK * kTK,
-        ea_panels + pea, eb, Y, ldy, upd, err);
+        ea_panels + pea, eb, Y, ldy, upd, err, ntn, ntn);
     return cudaGetLastError();
 }
 

@@ -154,3 +154,32 @@ def test_hessenberg_several_chunks_per_cta():
     assert np.abs(Q.T @ Q - np.eye(n)).max() <= 8 * n * U
     R = Q @ H @ Q.T - A
     assert np.abs(R).max() <= _bound(n) * np.abs(A).max(), np.abs(R).max()
+
+
+def test_panel_barrier_wait_runs_out_then_recovers():
+    # failure detection without a fault: a wait limit of one poll makes the
+    # cooperative panel's grid-barrier waits give up (the other CTAs are not
+    # there yet); every CTA returns, evec_sync reports EVEC_ETIMEOUT, and
+    # the next call with the built-in limit matches the oracle
+    import ctypes
+    n = 300
+    A = np.random.default_rng(31).standard_normal((n, n))
+    h = ev.handle(0)
+    L = ev.lib()
+    L.evec_set_wait_limit.argtypes = [ctypes.c_void_p, ctypes.c_int64]
+    L.evec_set_wait_limit.restype = ctypes.c_int
+    assert L.evec_set_wait_limit(h.ptr, -1) == ev.EVEC_EINVAL
+    assert L.evec_set_wait_limit(h.ptr, 1) == ev.EVEC_OK
+    try:
+        dA = torch.from_numpy(np.asfortranarray(A)).cuda()
+        ev.hessenberg(dA, calc_q=True, check=False, overwrite=True)
+        with pytest.raises(ev.EvecError) as ei:
+            h.sync()
+        assert ei.value.status == ev.EVEC_ETIMEOUT
+    finally:
+        assert L.evec_set_wait_limit(h.ptr, 0) == ev.EVEC_OK
+    h.sync()                                   # the status was cleared
+    H, Q = _gpu(A)
+    Ho, Qo, _ = oracle.hessenberg(A)
+    assert np.abs(H - Ho).max() <= _bound(n) * np.abs(A).max()
+    assert np.abs(Q - Qo).max() <= _bound(n)
