@@ -338,9 +338,23 @@ __device__ void diag_tile(int s, int list_pos0, const double *__restrict__ T, in
         for (int k = 0; k < nbt; k++) if (bsz[k] == 1) ford[f++] = k;
         for (int k = 0; k < nbt; k++) if (bsz[k] == 2) ford[f++] = k;
     }
-    // the tile, then the block factors below (they need only T and the
-    // shifts); the segments follow
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    // the segments, column by column (coalesced), in flight while the block
+    // factors are computed; own units start at zero
+    for (int idx = tid; idx < kUnits * ts; idx += kThreads) {
+        const int uu = idx / ts, i = idx % ts;
+        const int c = ucol[uu];
+        if (c >= 0 && (RHS || !uown[uu])) {
+            cp_async8(&yr[i * ys + uu], &Y[(t0 + i) + (int64_t)c * ldy]);
+            if (C) cp_async8(&yi[i * ys + uu], &Y[(t0 + i) + (int64_t)(c + 1) * ldy]);
+        } else {
+            yr[i * ys + uu] = 0.0;
+            if (C) yi[i * ys + uu] = 0.0;
+        }
+    }
+    asm volatile("cp.async.commit_group;");
+    // the tile (the older group), then the block factors below (they need
+    // only T and the shifts)
+    asm volatile("cp.async.wait_group 1;" ::: "memory");
     __syncthreads();
 
     // ---- one unit per G lanes --------------------------------------------
@@ -387,19 +401,6 @@ __device__ void diag_tile(int s, int list_pos0, const double *__restrict__ T, in
         }
     }
 
-    // the segments, column by column (coalesced); own units start at zero
-    for (int idx = tid; idx < kUnits * ts; idx += kThreads) {
-        const int uu = idx / ts, i = idx % ts;
-        const int c = ucol[uu];
-        if (c >= 0 && (RHS || !uown[uu])) {
-            cp_async8(&yr[i * ys + uu], &Y[(t0 + i) + (int64_t)c * ldy]);
-            if (C) cp_async8(&yi[i * ys + uu], &Y[(t0 + i) + (int64_t)(c + 1) * ldy]);
-        } else {
-            yr[i * ys + uu] = 0.0;
-            if (C) yi[i * ys + uu] = 0.0;
-        }
-    }
-    asm volatile("cp.async.commit_group;");
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();
 

@@ -1933,19 +1933,25 @@ static evec_status run_batch(evec_handle h, int64_t count, const int64_t *n_host
     Packer pk;
     pk.host = h->bplan_h;
     pk.dev = h->bplan_d;
-    {   // eigenvalues per column, matrix order
+    {   // eigenvalues per column, packed in matrix order (pencils: copied
+        // out after the launch; the pencil call has no output offsets)
         std::vector<double> re(eacc), im(eacc);
+        int64_t acc = 0;
         for (int64_t i = 0; i < count; i++) {
             const HostPlan &P = plans[i];
-            std::copy(P.col_lam_re.begin(), P.col_lam_re.end(), re.begin() + eo[i]);
-            std::copy(P.col_lam_im.begin(), P.col_lam_im.end(), im.begin() + eo[i]);
+            std::copy(P.col_lam_re.begin(), P.col_lam_re.end(), re.begin() + acc);
+            std::copy(P.col_lam_im.begin(), P.col_lam_im.end(), im.begin() + acc);
+            acc += P.m;
         }
         pk.put(re.data(), re.size() * 8, 8);
         pk.put(im.data(), im.size() * 8, 8);
         if (gen) {
             std::vector<double> be(eacc);
-            for (int64_t i = 0; i < count; i++)
-                std::copy(plans[i].col_beta.begin(), plans[i].col_beta.end(), be.begin() + eo[i]);
+            acc = 0;
+            for (int64_t i = 0; i < count; i++) {
+                std::copy(plans[i].col_beta.begin(), plans[i].col_beta.end(), be.begin() + acc);
+                acc += plans[i].m;
+            }
             pk.put(be.data(), be.size() * 8, 8);
         }
     }
