@@ -104,14 +104,14 @@ def test_generalized_errors():
 @pytest.mark.parametrize("mode", ["fp64", "split"])
 def test_generalized_config4_full_size_sampled(mode):
     # n = 8192 pencil with Z (every 50th diagonal entry of T = 1e-12: nearly
-    # infinite eigenvalues); 16 sampled eigenvalues against the oracle
+    # infinite eigenvalues); 256 sampled eigenvalues against the oracle
     n = 8192
     S, T, blocks = workloads.generalized_pair(n, seed=workloads.SEED_BASE + 4)
     Z = workloads.householder_orthogonal(n, seed=workloads.SEED_BASE + 104)
     X, e, ar, ai, be = _run(S, T, Z, tile=0, mode=mode)
     assert np.isfinite(X).all()
     rng = np.random.default_rng(6)
-    chosen = rng.choice(len(blocks), size=16, replace=False)
+    chosen = rng.choice(len(blocks), size=256, replace=False)
     sel = np.zeros(n, np.uint8)
     for b in chosen:
         p, sz = blocks[b]

@@ -292,7 +292,7 @@ def test_residual_gate_reports_eresidual_after_every_repeat():
     # too, and evec_sync reports EVEC_ERESIDUAL with the output column of the
     # first failing eigenvalue; the result is the FP64 one
     n = 300
-    T, _ = workloads.config0_schur(n, seed=66)
+    T, blocks = workloads.config0_schur(n, seed=66)
     dT = torch.from_numpy(np.asfortranarray(T)).cuda()
     h = ev.handle(0)
     L = ev.lib()
@@ -305,7 +305,9 @@ def test_residual_gate_reports_eresidual_after_every_repeat():
         with pytest.raises(ev.EvecError) as ei:
             h.sync()
         assert ei.value.status == ev.EVEC_ERESIDUAL
-        assert ei.value.bad == 0
+        # the first block's vector has no rows above it: its residual is 0
+        # and passes any gate; the first failure is the second block's
+        assert ei.value.bad == blocks[0][1]
         assert ev.handle(0).gate_stats()[1] == 2       # 8 slices, then FP64
         Xf, ef, _, lif = ev.standard(dT, tile=32, mode="fp64", check=True)
         np.testing.assert_array_equal(X.cpu().numpy(), Xf.cpu().numpy())
