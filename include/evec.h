@@ -88,7 +88,9 @@ typedef enum {
 
 typedef struct {
     int mode;    /* evec_mode */
-    int tile;    /* tile size nb of the tiled solve, 16..128; 0 = default */
+    int tile;    /* tile size nb of the tiled solve, 16..512; 0 = 64.  Tiles
+                    above 64 rows are solved in sub-blocks of at most 64
+                    rows with one scale exponent per tile segment */
     int slices;  /* EVEC_SPLIT: digit slices per operand, 2..8; 0 = 8
                     (relative error of a product ~2^(-7 slices)) */
     int refine;  /* EVEC_SPLIT, evec_standard and evec_standard_left:
@@ -275,7 +277,7 @@ evec_status evec_standard_host(evec_handle h, int64_t n, const double *T_host,
 /* Host-only planning query (no GPU needed).  From the diagonal, the first
  * subdiagonal and the first superdiagonal of T (host arrays of n, n-1 and
  * n-1 values) compute the number of output columns m of a selection and
- * the tile boundaries used for tile size nb (16..128): tiles of nb rows,
+ * the tile boundaries used for tile size nb (16..512): tiles of nb rows,
  * one row shorter where a boundary would split a 2x2 block.  tile_start
  * (may be NULL) receives ntiles + 1 entries and must hold n / (nb - 1) + 2.
  * Errors: EVEC_EINVAL (bad argument or an entry above 2^1000),

@@ -627,8 +627,6 @@ __device__ void diag_tile(int s, int list_pos0, const double *__restrict__ T, in
             const bool ownu = !RHS && uown[uu];   // fresh segments above the own block
             const int e_r = ownu ? es : er[j];
             const int a = min(e_r, es);
-            const double nup = ownu ? 0.0 : scale2(nur[j], a - e_r);
-            const double mup = scale2(umu[uu], a - es);
             double trs = tau[(int64_t)r * P.ntiles + s];
             if constexpr (GEN) {   // |beta| |S_rs| + |alpha|_1 |T_rs| for this unit
                 const int ui = uidx[uu];
@@ -636,7 +634,7 @@ __device__ void diag_tile(int s, int list_pos0, const double *__restrict__ T, in
                       (fabs(P.unit_lam[2 * ui]) + fabs(P.unit_lam[2 * ui + 1])) *
                           pen.tau[(int64_t)r * P.ntiles + s];
             }
-            const int g2 = protect_update(nup, trs, mup);
+            const int g2 = protect_update_scaled(ownu ? 0.0 : nur[j], a - e_r, trs, umu[uu], a - es);
             const int ne = a + g2;
             seg_e[at] = ne;
             seg_dx[at] = ne - es;

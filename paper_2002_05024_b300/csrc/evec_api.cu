@@ -108,6 +108,7 @@ cudaError_t launch_split_gemm(const double *A, int64_t lda, const double *B, int
 int split_pad_m(int M);
 int split_pad_n(int N);
 int split_pad_k(int K);
+int split_update_kp(int k);
 constexpr int kSplitColTile = 64;
 cudaError_t split_update_prepare(const double *T, int64_t ldt, const double *T2, int64_t ldt2,
                                  int n, int ntiles, int maxtile,
@@ -893,7 +894,7 @@ const char *evec_last_cuda_error(void) {
 evec_status evec_plan_query(int64_t n, const double *diag, const double *sub, const double *sup,
                             const uint8_t *select_host, int nb, int64_t *m, int32_t *ntiles,
                             int32_t *tile_start, int64_t *bad_index) {
-    if (n < 0 || (n > 0 && (!diag || (n > 1 && (!sub || !sup)))) || nb < 16 || nb > kMaxTile)
+    if (n < 0 || (n > 0 && (!diag || (n > 1 && (!sub || !sup)))) || nb < 16 || nb > kMaxTileBig)
         return EVEC_EINVAL;
     HostPlan P;
     if (n == 0) {
@@ -1257,7 +1258,7 @@ evec_status evec_standard(evec_handle h, int64_t n, const double *T, int64_t ldt
     const int slices = (opt && opt->slices) ? opt->slices : 8;
     if (slices < 2 || slices > 8) return EVEC_EINVAL;
     const int nb = resolve_tile(opt);
-    if (nb < 16 || nb > kMaxTile) return EVEC_EINVAL;
+    if (nb < 16 || nb > kMaxTileBig) return EVEC_EINVAL;
     if (n == 0) return EVEC_OK;
     if (!T || !X || !scale_exp) return EVEC_EINVAL;
     const int refine_opt = opt ? opt->refine : 1;
@@ -1331,7 +1332,7 @@ evec_status evec_standard(evec_handle h, int64_t n, const double *T, int64_t ldt
     });
     SplitUpdateCtx sctx;
     if (mode == EVEC_SPLIT) {
-        const int Kp = HP.max_tile <= 64 ? 64 : 128;
+        const int Kp = split_update_kp(HP.max_tile);
         const int Np = split_pad_n((int)m);
         EVEC_TRY(grow_device(&h->panels, &h->panels_cap,
                              (size_t)std::max(HP.panel_rows, 128) * Kp));
@@ -1516,7 +1517,7 @@ evec_status evec_trsolve(evec_handle h, int64_t n, const double *T, int64_t ldt,
     const int slices = (opt && opt->slices) ? opt->slices : 8;
     if (slices < 2 || slices > 8) return EVEC_EINVAL;
     const int nb = resolve_tile(opt);
-    if (nb < 16 || nb > kMaxTile) return EVEC_EINVAL;
+    if (nb < 16 || nb > kMaxTileBig) return EVEC_EINVAL;
     if (n == 0 || nrhs == 0) return EVEC_OK;
     if (!T || !B || !X || !scale_exp) return EVEC_EINVAL;
     DeviceGuard g(h->device);
@@ -1570,7 +1571,7 @@ evec_status evec_trsolve(evec_handle h, int64_t n, const double *T, int64_t ldt,
     });
     SplitUpdateCtx sctx;
     if (mode == EVEC_SPLIT) {
-        const int Kp = HP.max_tile <= 64 ? 64 : 128;
+        const int Kp = split_update_kp(HP.max_tile);
         const int Np = split_pad_n((int)m);
         EVEC_TRY(grow_device(&h->panels, &h->panels_cap,
                              (size_t)std::max(HP.panel_rows, 128) * Kp));
@@ -1611,7 +1612,7 @@ evec_status evec_standard_left(evec_handle h, int64_t n, const double *T, int64_
     if (n == 0) return EVEC_OK;
     if (!T || !X || !scale_exp) return EVEC_EINVAL;
     const int nb = resolve_tile(opt);
-    if (nb < 16 || nb > kMaxTile) return EVEC_EINVAL;
+    if (nb < 16 || nb > kMaxTileBig) return EVEC_EINVAL;
     DeviceGuard g(h->device);
     if (!g.ok) return EVEC_ECUDA;
     cudaStream_t st = h->stream;
@@ -2483,7 +2484,7 @@ extern "C" evec_status evec_generalized(evec_handle h, int64_t n, const double *
     pen.blk_tau = h->blk_tauT;
     SplitUpdateCtx sctx;
     if (mode == EVEC_SPLIT) {   // panels of [S T] (K = 2 |tile|)
-        const int Kp = 2 * HP.max_tile <= 64 ? 64 : 128;
+        const int Kp = split_update_kp(2 * HP.max_tile);
         const int Np = split_pad_n((int)m);
         EVEC_TRY(grow_device(&h->panels, &h->panels_cap,
                              (size_t)std::max(HP.panel_rows, 128) * Kp));

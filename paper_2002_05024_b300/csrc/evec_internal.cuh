@@ -27,7 +27,8 @@ constexpr double kSafeMin = 0x1p-1022;
 constexpr int kOmegaExp = 1020;
 // dy sentinel: the segment has never been written; treat it as zero.
 constexpr int32_t kFresh = INT32_MIN;
-constexpr int kMaxTile = 128;
+constexpr int kMaxTile = 128;      // tiles solved whole in shared memory (pencils: 64)
+constexpr int kMaxTileBig = 512;   // largest tile: solved in sub-blocks of 64 rows
 
 struct DevStatus {
     int code;          // evec_status of the first device-detected error
@@ -151,6 +152,24 @@ __device__ __forceinline__ int ilog2_abs(double x) {
 __device__ __forceinline__ int protect_update(double nu, double tau, double mu) {
     if (!(tau * mu > kOmega - nu)) return 0;
     return mu <= 1.0 ? -1 : -2 - ilog2_abs(mu);
+}
+
+// protect_update for the decisions of a tile update, with nu and mu given
+// as doubles times powers of two: q for (nu 2^kn, tau, mu 2^km).  The common
+// case is decided on exponent fields alone (integer pipe): nu 2^kn <
+// 2^(field(nu) - 1022 + kn) and likewise for tau and mu, so when the larger
+// of the two bounds is at most 2^1019 the sum stays below 2^1020 = Omega and
+// the FP64 test of protect_update would return 0 as well (its rounded
+// product is at most 2^1019, its rounded Omega - nu at least 2^1019).
+// Otherwise the scaled values are formed and the FP64 test decides.
+__device__ __forceinline__ int protect_update_scaled(double nu, int kn, double tau, double mu,
+                                                     int km) {
+    const int fn = (__double2hiint(nu) >> 20) & 0x7ff, ft = (__double2hiint(tau) >> 20) & 0x7ff;
+    const int fm = (__double2hiint(mu) >> 20) & 0x7ff;
+    const int en = nu == 0.0 ? INT32_MIN / 2 : fn - 1022 + kn;
+    const int ep = (tau == 0.0 || mu == 0.0) ? INT32_MIN / 2 : (ft - 1022) + (fm - 1022 + km);
+    if (max(en, ep) <= kOmegaExp - 1) return 0;
+    return protect_update(scale2(nu, kn), tau, scale2(mu, km));
 }
 
 // 1 / x for finite nonzero x without the IEEE division sequence: x = m 2^k

@@ -40,6 +40,7 @@
 // dy = a + q - e_r (scale of Y_r), dx = a + q - e_s (scale of X_s).
 #include <algorithm>
 
+#include "diag_big.cuh"
 #include "diag_tile.cuh"
 
 namespace evec {
@@ -61,6 +62,56 @@ __global__ void __launch_bounds__(32 * W)
         diag_tile<W, true, GEN, RHS, GR>(
             s, P.tile_cplx[s] + (blockIdx.x - nreal_ctas) * (Lanes<true, GR>::U * W), T, ldt, P,
             tau, blk_tau, Y, ldy, seg_e, seg_nu, seg_dx, seg_dy, smem, pen, decide != 0);
+}
+
+// Tiles of more than 64 rows: the sub-blocked solve (diag_big.cuh).
+template <int W, bool RHS, int GR>
+__global__ void __launch_bounds__(32 * W)
+    k_diag_solve_big(int s, int nreal_ctas, const double *__restrict__ T, int64_t ldt, Plan P,
+                     const double *__restrict__ tau, const double *__restrict__ blk_tau,
+                     double *__restrict__ Y, int64_t ldy, int32_t *__restrict__ seg_e,
+                     double *__restrict__ seg_nu, int32_t *__restrict__ seg_dx,
+                     int32_t *__restrict__ seg_dy, int decide) {
+    extern __shared__ double smem[];
+    if ((int)blockIdx.x < nreal_ctas)
+        diag_tile_big<W, false, RHS, GR>(
+            s, P.tile_real[s] + blockIdx.x * (Lanes<false, GR>::U * W), T, ldt, P, tau, blk_tau,
+            Y, ldy, seg_e, seg_nu, seg_dx, seg_dy, smem, decide != 0);
+    else
+        diag_tile_big<W, true, RHS, GR>(
+            s, P.tile_cplx[s] + (blockIdx.x - nreal_ctas) * (Lanes<true, GR>::U * W), T, ldt, P,
+            tau, blk_tau, Y, ldy, seg_e, seg_nu, seg_dx, seg_dy, smem, decide != 0);
+}
+
+template <int W, bool RHS, int GR = 8>
+static int launch_big(int s, int ts, int nr, int nc, const double *T, int64_t ldt, const Plan &p,
+                      const double *tau, const double *blk_tau, double *Y, int64_t ldy,
+                      int32_t *seg_e, double *seg_nu, int32_t *seg_dx, int32_t *seg_dy,
+                      cudaStream_t st, bool decide, int *sms) {
+    constexpr int ur = Lanes<false, GR>::U * W, uc = Lanes<true, GR>::U * W;
+    const int rct = (nr + ur - 1) / ur;
+    const int cct = (nc + uc - 1) / uc;
+    if (rct + cct == 0) return 0;
+    cudaFuncSetAttribute(k_diag_solve_big<W, RHS, GR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)diag_big_smem<W, GR>(kMaxTileBig));
+    cudaFuncSetAttribute(k_diag_solve_big<W, RHS, GR>,
+                         cudaFuncAttributePreferredSharedMemoryCarveout,
+                         cudaSharedmemCarveoutMaxShared);
+    const size_t smem = diag_big_smem<W, GR>(ts);
+    if (sms) {
+        int per = 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_diag_solve_big<W, RHS, GR>,
+                                                          32 * W, smem) != cudaSuccess ||
+            per < 1) {
+            cudaGetLastError();
+            per = 1;
+        }
+        *sms = (rct + cct + per - 1) / per;
+        return 0;
+    }
+    k_diag_solve_big<W, RHS, GR><<<rct + cct, 32 * W, smem, st>>>(
+        s, rct, T, ldt, p, tau, blk_tau, Y, ldy, seg_e, seg_nu, seg_dx, seg_dy, decide ? 1 : 0);
+    return 1;
 }
 
 // The decisions of step s for every active column and tile r < s (the
@@ -89,9 +140,8 @@ __global__ void __launch_bounds__(256)
         const int e_r = ownu ? es : seg_e[at];
         const double nur = ownu ? 0.0 : (cplx ? fmax(seg_nu[at], seg_nu[at + 1]) : seg_nu[at]);
         const int a = min(e_r, es);
-        const double nup = ownu ? 0.0 : scale2(nur, a - e_r);
-        const double mup = scale2(mus, a - es);
-        const int g2 = protect_update(nup, tau[(int64_t)r * P.ntiles + s], mup);
+        const int g2 = protect_update_scaled(nur, a - e_r, tau[(int64_t)r * P.ntiles + s], mus,
+                                             a - es);
         const int ne = a + g2;
         seg_e[at] = ne;
         seg_dx[at] = ne - es;
@@ -192,15 +242,22 @@ int launch_diag_solve(int s, const double *T, int64_t ldt, const Plan &p,
     if (pen)
         return launch_w<4, true, false>(s, ts, nr, nc, T, ldt, p, tau, blk_tau, Y, ldy, seg_e,
                                         seg_nu, seg_dx, seg_dy, *pen, st, decide, sms);
-    // four warps share a tile of up to 64 rows; two for larger tiles
-    if (ts > 64)
-        return rhs ? launch_w<2, false, true>(s, ts, nr, nc, T, ldt, p, tau, blk_tau, Y, ldy,
-                                              seg_e, seg_nu, seg_dx, seg_dy, Pencil(), st,
-                                              decide, sms)
-                   : launch_w<2, false, false>(s, ts, nr, nc, T, ldt, p, tau, blk_tau, Y, ldy,
-                                               seg_e, seg_nu, seg_dx, seg_dy, Pencil(), st,
-                                               decide, sms);
     const int gr = pick_lanes(nr, nc);
+    // tiles above 64 rows: the sub-blocked solve, four warps per CTA
+    if (ts > 64) {
+#define EVEC_BIG_LAUNCH(R, G_)                                                                   \
+    return launch_big<4, R, G_>(s, ts, nr, nc, T, ldt, p, tau, blk_tau, Y, ldy, seg_e, seg_nu,     \
+                                seg_dx, seg_dy, st, decide, sms)
+        if (rhs) {
+            if (gr == 32) EVEC_BIG_LAUNCH(true, 32);
+            if (gr == 16) EVEC_BIG_LAUNCH(true, 16);
+            EVEC_BIG_LAUNCH(true, 8);
+        }
+        if (gr == 32) EVEC_BIG_LAUNCH(false, 32);
+        if (gr == 16) EVEC_BIG_LAUNCH(false, 16);
+        EVEC_BIG_LAUNCH(false, 8);
+#undef EVEC_BIG_LAUNCH
+    }
 #define EVEC_DIAG_LAUNCH(R, G_)                                                                  \
     return launch_w<4, false, R, G_>(s, ts, nr, nc, T, ldt, p, tau, blk_tau, Y, ldy, seg_e,       \
                                      seg_nu, seg_dx, seg_dy, Pencil(), st, decide, sms)

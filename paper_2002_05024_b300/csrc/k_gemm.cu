@@ -129,9 +129,11 @@ __global__ void __launch_bounds__(kThreads)
     __shared__ double red[16][kBN + 1];
     constexpr int MI = BM / 16;
 
+    // tiles of more than BM rows: blockIdx.z picks the BM-row chunk
     const int r = blockIdx.y;
-    const int r0 = P.tile_start[r];
-    const int rows = P.tile_start[r + 1] - r0;
+    const int r0 = P.tile_start[r] + (int)blockIdx.z * BM;
+    const int rows = min(BM, P.tile_start[r + 1] - r0);
+    if (rows <= 0) return;
     const int k0 = P.tile_start[s];
     const int K = P.tile_start[s + 1] - k0;
     const int64_t m = P.m;
@@ -188,7 +190,11 @@ __global__ void __launch_bounds__(kThreads)
         double mx = 0.0;
 #pragma unroll
         for (int t = 0; t < 16; t++) mx = fmax(mx, red[t][tid]);
-        seg_nu[(int64_t)r * m + j0 + tid] = mx;
+        // the decisions zeroed seg_nu; the chunks of a tile merge their maxima
+        if (gridDim.z == 1) seg_nu[(int64_t)r * m + j0 + tid] = mx;
+        else if (mx > 0.0)
+            atomicMax((unsigned long long *)&seg_nu[(int64_t)r * m + j0 + tid],
+                      (unsigned long long)abs_bits(mx));
     }
 }
 
@@ -268,7 +274,9 @@ __global__ void __launch_bounds__(kThreads)
     const int ncols = (int)min((int64_t)kBN, m - j0);
     const int r = blockIdx.y;
     const int i0 = P.tile_start[r];
-    const int rows = P.tile_start[r + 1] - i0;
+    const int ic = (int)blockIdx.z * BM;   // this CTA's row chunk of tile r
+    const int rows = min(BM, P.tile_start[r + 1] - i0 - ic);
+    if (rows <= 0) return;
     const int tid = threadIdx.x;
     if (tid < kBN) {
         int be = 0, er = 0;
@@ -289,8 +297,8 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
         for (int j = 0; j < 4; j++) acc[i][j] = 0.0;
 
-    if (i0 < K) {
-        const double *A = T + i0 + (int64_t)i0 * ldt;
+    if (i0 + ic < K) {
+        const double *A = T + (i0 + ic) + (int64_t)i0 * ldt;
         const int KL = K - i0;
         double ra[A_PER], rb[B_PER];
         // A(i, k) = T(i0 + i, i0 + k) on and above the subdiagonal, diagonal
@@ -301,7 +309,7 @@ __global__ void __launch_bounds__(kThreads)
             for (int t = 0; t < A_PER; t++) {
                 const int e = tid + kThreads * t;
                 const int i = e % BM, k = kb + e / BM;
-                ra[t] = (i < rows && k < KL && k + 1 >= i && k != i)
+                ra[t] = (i < rows && k < KL && k + 1 >= ic + i && k != ic + i)
                             ? A[i + (int64_t)k * ldt]
                             : 0.0;
             }
@@ -375,7 +383,7 @@ __global__ void __launch_bounds__(kThreads)
         for (int i = 0; i < MI; i++) {
             const int row = ty + 16 * i;
             if (row >= rows) continue;
-            const int64_t gi = i0 + row;
+            const int64_t gi = i0 + ic + row;
             double v = 0.0;
             if (gi < pj) {   // same tile: Y_i is already in this scale
                 v = -fma(T[gi + gi * ldt] - lr, y[gi], acc[i][jj]);
@@ -388,11 +396,12 @@ __global__ void __launch_bounds__(kThreads)
 
 template <int BM>
 static void launch_residual_bm(const double *T, int64_t ldt, const Plan &p, int ntiles,
-                               const double *Y, int64_t ldy, const int32_t *seg_e,
+                               int max_tile, const double *Y, int64_t ldy, const int32_t *seg_e,
                                const int32_t *row_tile, double *R, int64_t ldr, cudaStream_t st) {
     cudaFuncSetAttribute(k_residual<BM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sizeof(GemmSmem<BM>));
-    dim3 grid((unsigned)((p.m + kBN - 1) / kBN), (unsigned)ntiles);
+    dim3 grid((unsigned)((p.m + kBN - 1) / kBN), (unsigned)ntiles,
+              (unsigned)((max_tile + BM - 1) / BM));
     k_residual<BM><<<grid, kThreads, sizeof(GemmSmem<BM>), st>>>(T, ldt, p, Y, ldy, seg_e,
                                                                  row_tile, R, ldr);
 }
@@ -402,9 +411,10 @@ void launch_residual(const double *T, int64_t ldt, const Plan &p, int ntiles, in
                      const int32_t *row_tile, double *R, int64_t ldr, cudaStream_t st) {
     if (p.m <= 0 || ntiles <= 0) return;
     if (max_tile <= 64)
-        launch_residual_bm<64>(T, ldt, p, ntiles, Y, ldy, seg_e, row_tile, R, ldr, st);
+        launch_residual_bm<64>(T, ldt, p, ntiles, max_tile, Y, ldy, seg_e, row_tile, R, ldr, st);
     else
-        launch_residual_bm<128>(T, ldt, p, ntiles, Y, ldy, seg_e, row_tile, R, ldr, st);
+        launch_residual_bm<128>(T, ldt, p, ntiles, max_tile, Y, ldy, seg_e, row_tile, R, ldr,
+                                st);
 }
 
 // W = [beta X_s; -(alpha X_s)] for the active columns of step s (pencils):
@@ -446,7 +456,8 @@ void launch_tile_update(int s, const double *T, int64_t ldt, const Plan &p, int 
     if (s <= 0) return;
     const int64_t cols = p.m - tile_col_h[s];
     if (cols <= 0) return;
-    dim3 grid((unsigned)((cols + kBN - 1) / kBN), (unsigned)s);
+    dim3 grid((unsigned)((cols + kBN - 1) / kBN), (unsigned)s,
+              (unsigned)(max_tile <= 64 ? 1 : (max_tile + 127) / 128));
     if (max_tile <= 64) {
         set_smem_attr<64>();
         k_tile_update<64, false><<<grid, kThreads, sizeof(GemmSmem<64>), st>>>(

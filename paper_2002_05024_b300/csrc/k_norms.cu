@@ -90,16 +90,17 @@ __global__ void __launch_bounds__(128) k_tile_norms(const double *__restrict__ T
     __shared__ double red[4];
 
     if (r < s) {
-        double sum = 0.0;
-        const int i = r0 + tid;
-        if (i < r1) {
+        double w = 0.0;
+        for (int i = r0 + tid; i < r1; i += 128) {   // tiles of up to 512 rows
+            double sum = 0.0;
             for (int j = c0; j < c1; j++) {
                 double v = T[i + (int64_t)j * ldt];
                 check_entry(v, (long long)i + (long long)j * ldt, status);
                 sum += fabs(v);
             }
+            w = fmax(w, sum);
         }
-        double w = warp_max(sum);
+        w = warp_max(w);
         if ((tid & 31) == 0) red[tid >> 5] = w;
         __syncthreads();
         if (tid == 0) {
@@ -109,11 +110,9 @@ __global__ void __launch_bounds__(128) k_tile_norms(const double *__restrict__ T
         return;
     }
     // diagonal tile: validate the upper part and the first subdiagonal
-    for (int j = c0; j < c1; j++) {
-        const int i = r0 + tid;
-        if (i < r1 && i <= j + lower)
+    for (int j = c0; j < c1; j++)
+        for (int i = r0 + tid; i < r1 && i <= j + lower; i += 128)
             check_entry(T[i + (int64_t)j * ldt], (long long)i + (long long)j * ldt, status);
-    }
     // in-tile block column norms: one warp per block
     const int lane = tid & 31, warp = tid >> 5;
     const int kb0 = P.tile_blk[s], kb1 = P.tile_blk[s + 1];

@@ -448,6 +448,9 @@ bool make_map(CUtensorMap *tm, void *ptr, int rows, int kpad, int box_rows) {
 int split_pad_m(int M) { return (M + kTM - 1) / kTM * kTM; }
 int split_pad_n(int N) { return (N + kTN - 1) / kTN * kTN; }
 int split_pad_k(int K) { return (K + 63) / 64 * 64; }
+// K columns of the panel slices of the split tile updates: 64 for the
+// panel-resident kernel (K <= 64), else the largest tile rounded up to 64
+int split_update_kp(int k) { return k <= 64 ? 64 : (k + 63) / 64 * 64; }
 
 // Slices of A (rows) and B (columns) into the caller's buffers, then the
 // GEMM.  Buffers: sa [S][Mpad][Kpad], sb [S][Npad][Kpad] BF16; rowmax
@@ -584,7 +587,7 @@ cudaError_t split_update_prepare(const double *T, int64_t ldt, const double *T2,
                                  SplitUpdateCtx *ctx, cudaStream_t st) {
     if (!get_encoder()) return cudaErrorInvalidValue;
     ctx->S = S;
-    ctx->Kp = (T2 ? 2 * maxtile : maxtile) <= 64 ? 64 : 128;
+    ctx->Kp = split_update_kp(T2 ? 2 * maxtile : maxtile);
     ctx->Npad = split_pad_n(m);
     if (ntiles > 1) {
         const int maxblocks = split_pad_m(n) / 32;   // >= roundup(t0_s, 128) / 32 for all s

@@ -50,7 +50,7 @@ def _diags(T):
             np.ascontiguousarray(np.diagonal(T, 1)))
 
 
-@pytest.mark.parametrize("nb", [16, 17, 32, 64, 100, 128])
+@pytest.mark.parametrize("nb", [16, 17, 32, 64, 100, 128, 256, 512])
 @pytest.mark.parametrize("n", [1, 2, 3, 63, 64, 65, 300, 1029])
 def test_plan_tiles_never_split_a_pair(n, nb):
     T, blocks = workloads.config0_schur(n, seed=n * 7 + nb)

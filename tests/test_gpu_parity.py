@@ -216,9 +216,9 @@ def test_plan_reuse_follows_the_diagonals_and_selection():
 # full size, in the benchmark's launch configuration (tile 64, with Q):
 # the GPU computes every column, the oracle a seeded sample of columns
 # ---------------------------------------------------------------------------
-def _sampled_parity(T, blocks, Q, k, seed, rel_tol, mode="fp64"):
+def _sampled_parity(T, blocks, Q, k, seed, rel_tol, mode="fp64", tile=0):
     n = T.shape[0]
-    X, e, lr, li = _gpu(T, Q, tile=0, mode=mode)
+    X, e, lr, li = _gpu(T, Q, tile=tile, mode=mode)
     assert np.isfinite(X).all()
     rng = np.random.default_rng(seed)
     chosen = rng.choice(len(blocks), size=k, replace=False)
@@ -244,18 +244,56 @@ def _sampled_parity(T, blocks, Q, k, seed, rel_tol, mode="fp64"):
     return rel
 
 
-def test_full_size_config1a_sampled():
+@pytest.mark.parametrize("tile", [0, 256, 512])
+def test_full_size_config1a_sampled(tile):
+    # n = 4096 with Q across the tile sweep (0 = the default 64; 256 and 512
+    # are solved in sub-blocks of at most 64 rows, one exponent per tile)
     n = 4096
     T, blocks = workloads.config0_schur(n, seed=workloads.SEED_BASE + 1)
     Q = workloads.householder_orthogonal(n, seed=workloads.SEED_BASE + 101)
-    _sampled_parity(T, blocks, Q, k=48, seed=1, rel_tol=REL_TOL)
+    _sampled_parity(T, blocks, Q, k=48, seed=1, rel_tol=REL_TOL, tile=tile)
 
 
-def test_full_size_config1b_sampled():
+@pytest.mark.parametrize("tile", [0, 256, 512])
+def test_full_size_config1b_sampled(tile):
     n = 4096
     T, blocks = workloads.adversarial_schur(n, seed=workloads.SEED_BASE + 11)
     Q = workloads.householder_orthogonal(n, seed=workloads.SEED_BASE + 111)
-    _sampled_parity(T, blocks, Q, k=32, seed=2, rel_tol=1e-3)
+    _sampled_parity(T, blocks, Q, k=32, seed=2, rel_tol=1e-3, tile=tile)
+
+
+@pytest.mark.parametrize("mode", ["fp64", "split"])
+@pytest.mark.parametrize("n,tile", [(1300, 200), (1300, 256), (1100, 512), (700, 512),
+                                    (600, 130)])
+def test_big_tiles(n, tile, mode):
+    # tiles above 64 rows: sub-blocks of at most 64 rows inside each tile
+    # (a boundary that would split a 2x2 block moves up a row), the rows
+    # above a sub-block updated in one protected pass; ragged last tiles,
+    # with Q, every column against the oracle
+    T, blocks = workloads.config0_schur(n, seed=n + tile)
+    Q = workloads.householder_orthogonal(n, seed=n + tile + 1)
+    X, e, lr, li = _gpu(T, Q, tile=tile, mode=mode)
+    _parity(T, Q, X, e, lr, li)
+    X, e, lr, li = _gpu(T, None, tile=tile, mode=mode)
+    _check_structure(T, blocks, X, li)
+    _parity(T, None, X, e, lr, li)
+
+
+@pytest.mark.parametrize("tile", [256, 512])
+def test_big_tiles_adversarial_and_selection(tile):
+    n = 1200
+    T, blocks = workloads.adversarial_schur(n, seed=88 + tile)
+    _, bad = oracle.naive_standard(T)
+    assert bad > 0
+    X, e, lr, li = _gpu(T, tile=tile)
+    _check_structure(T, blocks, X, li)
+    assert e.min() < -1074
+    _parity(T, None, X, e, lr, li, rel_tol=1e-3)
+    T, blocks = workloads.config0_schur(n, seed=89 + tile)
+    sel = workloads.random_eigen_selection(n, blocks, 0.35, seed=90)
+    X, e, lr, li = _gpu(T, select=sel, tile=tile, mode="split")
+    _check_structure(T, blocks, X, li, select=sel)
+    _parity(T, None, X, e, lr, li, select=sel)
 
 
 # ---------------------------------------------------------------------------

@@ -65,7 +65,7 @@ def _zeros_below_blocks(blocks, X, select=None):
         col += sz
 
 
-@pytest.mark.parametrize("tile", [16, 32, 64, 128])
+@pytest.mark.parametrize("tile", [16, 32, 64, 128, 256, 512])
 def test_refine_all_tiles(tile):
     # no Q: the refined Y itself (tiles <= 64: panel-resident update kernel
     # in both sweeps; 128: streamed panel)

@@ -55,7 +55,7 @@ def _compare(T, B, X, e, rel_tol=1e-10):
 
 
 @pytest.mark.parametrize("mode", ["fp64", "split"])
-@pytest.mark.parametrize("tile", [16, 32, 64, 128])
+@pytest.mark.parametrize("tile", [16, 32, 64, 128, 256, 512])
 def test_trsolve_tiles_and_modes(tile, mode):
     n = 613
     T, _ = _well_conditioned(n, seed=500 + tile)
