@@ -109,6 +109,12 @@ def lib() -> ctypes.CDLL:
                                    ctypes.POINTER(_Opts)]
         L.evec_batched_generalized.argtypes = [p, i64, p, p, p, p, p, p, p, p, p, p, p,
                                                ctypes.POINTER(_Opts)]
+        L.evec_set_wait_limit.argtypes = [p, i64]
+        L.evec_set_gate_factor.argtypes = [p, ctypes.c_double]
+        L.evec_opts_default.argtypes = [ctypes.POINTER(_Opts)]
+        L.evec_opts_default.restype = None
+        L.evec_standard_noalloc.argtypes = [i64, p, i64, p, p, i64, p, ctypes.c_int, p,
+                                            ctypes.POINTER(i64)]
         L.evec_tune_get.argtypes = [p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
         L.evec_tune_set.argtypes = [p, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         for f in ("evec_create", "evec_destroy", "evec_set_stream", "evec_count",
@@ -118,7 +124,8 @@ def lib() -> ctypes.CDLL:
                   "evec_batched_generalized", "evec_set_lookahead", "evec_hessenberg",
                   "evec_set_hessenberg_panel", "evec_gate_stats", "evec_window_update",
                   "evec_window_update_set",
-                  "evec_generalized", "evec_count_generalized",
+                  "evec_generalized", "evec_count_generalized", "evec_set_wait_limit",
+                  "evec_set_gate_factor", "evec_standard_noalloc",
                   "evec_batched_generalized_count",
                   "evec_tune_get", "evec_tune_set"):
             getattr(L, f).restype = ctypes.c_int
@@ -184,6 +191,15 @@ class Handle:
         r = ctypes.c_int(0)
         _check(lib().evec_gate_stats(self._h, ctypes.byref(f), ctypes.byref(r)), "evec_gate_stats")
         return int(f.value), int(r.value)
+
+    def wait_limit(self, polls: int):
+        """Polls of a bounded device-side wait before it gives up (0 = the
+        built-in limit)."""
+        _check(lib().evec_set_wait_limit(self._h, int(polls)), "evec_set_wait_limit")
+
+    def gate_factor(self, factor: float):
+        """Bound of the residual gate (refine = 2): factor * n (default 10)."""
+        _check(lib().evec_set_gate_factor(self._h, float(factor)), "evec_set_gate_factor")
 
     def hessenberg_panel(self, cooperative: bool):
         """Hessenberg panels as one cooperative launch (default) or six

@@ -117,7 +117,7 @@ def test_opts_defaults_in_the_documented_field_order():
 
     assert [f[0] for f in ev._Opts._fields_] == [f[0] for f in Opts._fields_]
     o = Opts(7, 7, 7, 7, 7)
-    f = ev.lib().evec_opts_default
+    f = ctypes.CDLL(ev.LIB_PATH).evec_opts_default   # a private prototype
     f.argtypes = [ctypes.POINTER(Opts)]
     f.restype = None
     f(ctypes.byref(o))

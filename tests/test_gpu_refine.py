@@ -330,7 +330,9 @@ def test_opts_struct_in_the_documented_field_order():
 
     n = 120
     T, _ = workloads.config0_schur(n, seed=67)
-    L = ev.lib()
+    # a private handle on the library: the prototype set here must not
+    # replace the one the binding uses
+    L = ctypes.CDLL(ev.LIB_PATH)
     f = L.evec_standard
     p, i64 = ctypes.c_void_p, ctypes.c_int64
     f.argtypes = [p, i64, p, i64, p, i64, p, p, i64, p, p, p, ctypes.POINTER(Opts)]
