@@ -20,6 +20,7 @@
 
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/evec.h"
 #include "split_common.cuh"
@@ -728,8 +729,22 @@ cudaEvent_t take_event(evec_handle h) {
 
 // Run one operation (launch() returns the number of kernels it launched),
 // bracketed by events when the handle is profiling.
+// NVTX range names of the kernel classes (a profiler shows each launch
+// group under its phase; without a tool attached a range costs a call that
+// returns at once)
+const char *const kPhaseNames[EVEC_K_COUNT] = {
+    "evec:gather", "evec:tile_norms", "evec:diag_solve", "evec:tile_update",
+    "evec:finalize", "evec:backtransform", "evec:canonicalize", "evec:batched",
+    "evec:refine", "evec:left", "evec:hess_panel", "evec:hess_update", "evec:window"};
+
+struct NvtxRange {
+    explicit NvtxRange(int kind) { nvtxRangePushA(kPhaseNames[kind]); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+
 template <class F>
 void timed_on(evec_handle h, int kind, cudaStream_t st, F &&launch) {
+    NvtxRange range(kind);
     if (!h->profiling) { launch(); return; }
     cudaEvent_t a = take_event(h), b = take_event(h);
     if (!a || !b) { h->prof_n[kind] += launch(); return; }

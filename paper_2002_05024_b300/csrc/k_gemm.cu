@@ -15,6 +15,10 @@
 // threads computes a BM x 64 tile, each thread (BM/16) x 4 outputs, with
 // operands staged through double-buffered shared memory (K step 16, the next
 // chunk prefetched into registers while the current one is consumed).
+#include <math.h>
+
+#include <algorithm>
+
 #include "evec_internal.cuh"
 
 namespace evec {
@@ -201,20 +205,30 @@ __global__ void __launch_bounds__(kThreads)
 // ---------------------------------------------------------------------------
 // back-transformation X = Q Y: grid (column blocks, heaviest first; row blocks)
 // ---------------------------------------------------------------------------
+// 1-D grid in groups of gw column blocks: within a group the row bands take
+// turns with the group's column blocks fastest, so the CTAs resident at one
+// time cover a few row bands x gw column blocks and share their Q rows and
+// Y columns through L2; heaviest column blocks first.
 template <int BM>
 __global__ void __launch_bounds__(kThreads)
     k_backtransform(const double *__restrict__ Q, int64_t ldq, Plan P,
                     const double *__restrict__ Y, int64_t ldy, double *__restrict__ X,
-                    int64_t ldx) {
+                    int64_t ldx, int gw) {
     extern __shared__ __align__(16) unsigned char smraw[];
     GemmSmem<BM> &sm = *reinterpret_cast<GemmSmem<BM> *>(smraw);
     constexpr int MI = BM / 16;
     const int64_t m = P.m, n = P.n;
-    const int64_t nblk_cols = (m + kBN - 1) / kBN;
-    const int64_t cb = nblk_cols - 1 - blockIdx.x;          // heaviest blocks first
+    const int nblk_cols = (int)((m + kBN - 1) / kBN);
+    const int nbands = (int)((n + BM - 1) / BM);
+    const int per = gw * nbands;
+    const int grp = (int)blockIdx.x / per;
+    const int rem = (int)blockIdx.x - grp * per;
+    const int w = min(gw, nblk_cols - grp * gw);
+    const int band = rem / w;
+    const int64_t cb = nblk_cols - 1 - (grp * gw + rem % w);   // heaviest blocks first
     const int64_t j0 = cb * kBN;
     const int ncols = (int)min((int64_t)kBN, m - j0);
-    const int64_t i0 = (int64_t)blockIdx.y * BM;
+    const int64_t i0 = (int64_t)band * BM;
     const int rows = (int)min((int64_t)BM, n - i0);
     // rows of Y beyond the last column's diagonal block are zero
     const int ul = P.col_unit[j0 + ncols - 1];
@@ -501,8 +515,26 @@ void launch_backtransform(const double *Q, int64_t ldq, const Plan &p, const dou
                           int64_t ldy, double *X, int64_t ldx, cudaStream_t st) {
     constexpr int BM = 128;
     set_smem_attr<BM>();
-    dim3 grid((unsigned)((p.m + kBN - 1) / kBN), (unsigned)((p.n + BM - 1) / BM));
-    k_backtransform<BM><<<grid, kThreads, sizeof(GemmSmem<BM>), st>>>(Q, ldq, p, Y, ldy, X, ldx);
+    const int ncb = (int)((p.m + kBN - 1) / kBN), nbands = (int)((p.n + BM - 1) / BM);
+    // column blocks per group: about sqrt(resident CTAs x 2) (a row band of
+    // Q is BM = 2 x kBN rows, a column block of Y kBN columns)
+    static int resident = 0;
+    if (resident == 0) {
+        int dev = 0, nsm = 148, per = 1;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_backtransform<BM>, kThreads,
+                                                          sizeof(GemmSmem<BM>)) != cudaSuccess ||
+            per < 1) {
+            cudaGetLastError();
+            nsm = 148;
+            per = 1;
+        }
+        resident = nsm * per;
+    }
+    const int gw = std::max(1, std::min(ncb, (int)lround(sqrt(2.0 * resident))));
+    k_backtransform<BM><<<(unsigned)(ncb * nbands), kThreads, sizeof(GemmSmem<BM>), st>>>(
+        Q, ldq, p, Y, ldy, X, ldx, gw);
 }
 
 }  // namespace evec

@@ -42,17 +42,22 @@ def complex_columns(X, lam_im):
 
 
 def standard_residuals(T, X, lam_re, lam_im):
-    """||T x - lambda x||_1 / (||T||_1 ||x||_1 u) per eigenvalue."""
+    """||T x - lambda x||_1 / (||T||_1 ||x||_1 u) per eigenvalue.  T X is
+    one real product (a pair's (Re, Im) columns give T x_re and T x_im),
+    so T is never copied to a complex array."""
     T1 = np.abs(T).sum(axis=0).max()
+    TX = T @ X
     res = []
     for j, pair in column_groups(lam_im):
         if pair:
             x = X[:, j] + 1j * X[:, j + 1]
             lam = lam_re[j] + 1j * lam_im[j]
+            tx = TX[:, j] + 1j * TX[:, j + 1]
         else:
             x = X[:, j]
             lam = lam_re[j]
-        r = T @ x - lam * x
+            tx = TX[:, j]
+        r = tx - lam * x
         res.append(np.abs(r).sum() / (T1 * np.abs(x).sum() * U))
     return np.array(res)
 
@@ -69,18 +74,24 @@ def left_residuals(T, X, lam_re, lam_im):
 
 
 def generalized_residuals(S, T, X, a_re, a_im, beta):
-    """||beta S x - alpha T x||_1 / ((|beta| ||S||_1 + |alpha| ||T||_1) ||x||_1 u)."""
+    """||beta S x - alpha T x||_1 / ((|beta| ||S||_1 + |alpha| ||T||_1) ||x||_1 u)
+    (S X and T X as real products, as in standard_residuals)."""
     S1 = np.abs(S).sum(axis=0).max()
     T1 = np.abs(T).sum(axis=0).max()
+    SX = S @ X
+    TX = T @ X
     res = []
     for j, pair in column_groups(a_im):
         if pair:
             x = X[:, j] + 1j * X[:, j + 1]
             al = a_re[j] + 1j * a_im[j]
+            sx = SX[:, j] + 1j * SX[:, j + 1]
+            tx = TX[:, j] + 1j * TX[:, j + 1]
         else:
             x = X[:, j]
             al = a_re[j]
-        r = beta[j] * (S @ x) - al * (T @ x)
+            sx, tx = SX[:, j], TX[:, j]
+        r = beta[j] * sx - al * tx
         den = (abs(beta[j]) * S1 + abs(al) * T1) * np.abs(x).sum() * U
         res.append(np.abs(r).sum() / den)
     return np.array(res)

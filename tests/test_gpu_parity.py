@@ -473,3 +473,37 @@ def test_lookahead_schedule_is_bit_identical(kind):
         outs.append((X.cpu().numpy(), e.cpu().numpy()))
     np.testing.assert_array_equal(outs[0][0], outs[1][0])
     np.testing.assert_array_equal(outs[0][1], outs[1][1])
+
+
+@pytest.mark.parametrize("mode", ["fp64", "split"])
+@pytest.mark.parametrize("with_q,tile", [(False, 64), (True, 64), (True, 256)])
+def test_outputs_stay_inside_their_buffers(mode, with_q, tile):
+    # canary-padded outputs (the race-detection substitute for a sanitizer):
+    # X with a leading dimension above n and spare columns, the exponent and
+    # eigenvalue vectors with spare entries, all filled with a sentinel; the
+    # call writes exactly the n x m block and the m entries
+    n, pad_rows, pad_cols = 333, 19, 5
+    T, _ = workloads.config0_schur(n, seed=42)
+    Q = workloads.householder_orthogonal(n, seed=43) if with_q else None
+    dT = torch.from_numpy(np.asfortranarray(T)).cuda()
+    dQ = None if Q is None else torch.from_numpy(np.asfortranarray(Q)).cuda()
+    m = ev.count(dT)
+    ld = n + pad_rows
+    sentinel = -1.2345e300
+    buf = torch.full((m + pad_cols, ld), sentinel, dtype=torch.float64, device="cuda")
+    X = buf.t()[:n, :m]
+    assert X.stride() == (1, ld)
+    ebuf = torch.full((m + pad_cols,), 7777777, dtype=torch.int32, device="cuda")
+    lbuf = torch.full((2, m + pad_cols), sentinel, dtype=torch.float64, device="cuda")
+    out = (X, ebuf[:m], lbuf[0, :m], lbuf[1, :m])
+    ev.standard(dT, dQ, tile=tile, check=True, out=out, mode=mode, refine=0)
+    torch.cuda.synchronize()
+    b = buf.t().cpu().numpy()
+    assert np.all(b[n:, :] == sentinel)                  # rows between n and ld
+    assert np.all(b[:, m:] == sentinel)                  # spare columns
+    assert np.isfinite(b[:n, :m]).all()
+    assert np.all(ebuf[m:].cpu().numpy() == 7777777)
+    assert np.all(lbuf[:, m:].cpu().numpy() == sentinel)
+    Xo, eo, _, lio = oracle.standard(T, Q=Q)
+    de, rel = compare_canonical(Xo, eo, b[:n, :m], ebuf[:m].cpu().numpy(), lio)
+    assert de <= 1 and rel <= REL_TOL, (de, rel)
