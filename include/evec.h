@@ -359,7 +359,8 @@ evec_status evec_profile_read(evec_handle h, double *ms, int64_t *launches, int 
  * two so that max(|alpha|, beta) is in [1, 2).  Outputs and canonical form
  * as evec_standard; alpha_re, alpha_im, beta (length m, device, may be NULL)
  * per column (a pair: alpha_im = +w, -w).  Every bound is
- * |beta| |S_rs| + |alpha|_1 |T_rs|.  opt->tile: 16..64 (0 = 64); opt->mode
+ * |beta| |S_rs| + |alpha|_1 |T_rs|.  opt->tile: 16..512 (0 = 64; above 64 in
+ * sub-blocks of at most 64 rows, as evec_standard); opt->mode
  * EVEC_SPLIT runs the back-transformation X = Z Y in split precision.
  */
 evec_status evec_generalized(evec_handle h, int64_t n, const double *S, int64_t lds,

@@ -22,6 +22,11 @@
 //      any order.
 // The maxima, write-back and the decisions for the tiles above are those
 // of the 64-row tiles.
+// GEN (a pencil beta S - alpha T, T upper triangular): S takes T's place
+// above, T's sub-block and panels are staged beside S's, the chain runs the
+// pencil updates, the pass over the rows above subtracts
+// S[0:a, a:b] (beta z) - T[0:a, a:b] (alpha z), and every bound is
+// |beta| |S ..| + |alpha|_1 |T ..|.
 #pragma once
 
 #include "diag_tile.cuh"
@@ -33,13 +38,14 @@ namespace {
 constexpr int kSub = 64;                                 // rows of a sub-block, at most
 constexpr int kMaxSubs = kMaxTileBig / (kSub - 1) + 2;   // sub-blocks of a tile, at most
 
-template <int W, bool C, bool RHS, int GR = 8>
+template <int W, bool C, bool GEN, bool RHS, int GR = 8>
 __device__ void diag_tile_big(int s, int list_pos0, const double *__restrict__ T, int64_t ldt,
                               const Plan &P, const double *__restrict__ tau,
                               const double *__restrict__ blk_tau, double *__restrict__ Y,
                               int64_t ldy, int32_t *__restrict__ seg_e,
                               double *__restrict__ seg_nu, int32_t *__restrict__ seg_dx,
-                              int32_t *__restrict__ seg_dy, double *smem, bool decide) {
+                              int32_t *__restrict__ seg_dy, double *smem, bool decide,
+                              const Pencil &pen = Pencil()) {
     constexpr int G = Lanes<C, GR>::G;
     constexpr int kThreads = 32 * W;
     constexpr int kUnits = Lanes<C, GR>::U * W;
@@ -74,12 +80,19 @@ __device__ void diag_tile_big(int s, int list_pos0, const double *__restrict__ T
     int *srow = facp + kUnits * kSub;                  // [kMaxSubs + 1] sub-block rows
     int *sblk = srow + kMaxSubs + 1;                   // [kMaxSubs + 1] sub-block first blocks
     int *snsub = sblk + kMaxSubs + 1;                  // [1]
+    // pencils: T's sub-block (and T panels), its block norms, the bounds of
+    // the sub-blocks' T panels, per-unit block bounds
+    double *Bsub = (double *)(((uintptr_t)(snsub + 1) + 15) & ~(uintptr_t)15);   // kSub x kSub
+    double *btauB = Bsub + (GEN ? kSub * kSub : 0);    // [ts]
+    double *stauB = btauB + (GEN ? ts : 0);            // [kMaxSubs]
+    double *utau = stauB + (GEN ? kMaxSubs : 0);       // [kUnits][kSub]
 
     for (int k = tid; k < nbt; k += kThreads) {
         bq[k] = P.blk_start[kb0 + k] - t0;
         bsz[k] = P.blk_size[kb0 + k];
         btau[k] = blk_tau[kb0 + k];
         btf[k] = efield(blk_tau[kb0 + k]);
+        if constexpr (GEN) btauB[k] = pen.blk_tau[kb0 + k];
     }
     if (tid < kUnits) {
         const int pos = list_pos0 + tid;
@@ -108,9 +121,14 @@ __device__ void diag_tile_big(int s, int list_pos0, const double *__restrict__ T
             }
             srow[ns] = a;
             sblk[ns] = k;
-            double tsum = 0.0;
-            while (k < nbt && bq[k] < b) tsum += btau[k++];
+            double tsum = 0.0, tsumB = 0.0;
+            while (k < nbt && bq[k] < b) {
+                tsum += btau[k];
+                if constexpr (GEN) tsumB += btauB[k];
+                k++;
+            }
             stau[ns] = tsum;
+            if constexpr (GEN) stauB[ns] = tsumB;
             ns++;
             a = b;
         }
@@ -144,7 +162,10 @@ __device__ void diag_tile_big(int s, int list_pos0, const double *__restrict__ T
     const bool own = valid && P.unit_tile[u] == s;
     const double lr = valid ? P.unit_lam[2 * u] : 0.0;
     const double li = (C && valid) ? P.unit_lam[2 * u + 1] : 0.0;
-    const double smin = fmax(kUlp * (fabs(lr) + fabs(li)), kSafeMin * ((double)P.n / kUlp));
+    const double be = (GEN && valid) ? P.unit_beta[u] : 1.0;
+    const double smin = GEN ? (valid ? P.unit_smin[u] : 1.0)
+                            : fmax(kUlp * (fabs(lr) + fabs(li)), kSafeMin * ((double)P.n / kUlp));
+    double *myutau = utau + (size_t)slot * kSub;
     double *myr = yr + slot;
     double *myi = yi + slot;
     double *myfac = fac + (size_t)slot * kSub * FW;
@@ -182,6 +203,12 @@ __device__ void diag_tile_big(int s, int list_pos0, const double *__restrict__ T
             if (i < sts && jj < sts && i <= jj + 1)
                 cp_async8(&Tsub[idx], T + (t0 + a + i) + (int64_t)(t0 + a + jj) * ldt);
             else Tsub[idx] = 0.0;
+            if constexpr (GEN) {
+                if (i < sts && jj < sts && i <= jj)
+                    cp_async8(&Bsub[idx],
+                              pen.T + (t0 + a + i) + (int64_t)(t0 + a + jj) * pen.ldt);
+                else Bsub[idx] = 0.0;
+            }
         }
         asm volatile("cp.async.commit_group;");
         if (tid == 0) {   // factor order: the 1x1 blocks, then the 2x2 blocks
@@ -195,7 +222,14 @@ __device__ void diag_tile_big(int s, int list_pos0, const double *__restrict__ T
             for (int f = g; f < nsb; f += G) {
                 const int kl = ford[f];
                 if (own && kb0 + sb0 + kl >= kown) continue;
-                const Fac F = factor<C>(bsz[sb0 + kl], Tsub, kSub, bq[sb0 + kl] - a, lr, li, smin);
+                Fac F;
+                if constexpr (GEN) {
+                    F = factor_pencil<C>(bsz[sb0 + kl], Tsub, Bsub, kSub, bq[sb0 + kl] - a, lr, li,
+                                         be, smin);
+                    myutau[kl] = fabs(be) * btau[sb0 + kl] + (fabs(lr) + fabs(li)) * btauB[sb0 + kl];
+                } else {
+                    F = factor<C>(bsz[sb0 + kl], Tsub, kSub, bq[sb0 + kl] - a, lr, li, smin);
+                }
                 double *fp = myfac + kl * FW;
                 if (C) {
                     fp[0] = F.ia.re; fp[1] = F.ia.im; fp[2] = F.l.re; fp[3] = F.l.im;
@@ -221,14 +255,26 @@ __device__ void diag_tile_big(int s, int list_pos0, const double *__restrict__ T
             const int k = kb0 + kt;                  // global block index
             const int q = bq[kt] - a;                // local row of the block
             const int bs = bsz[kt];
-            const double tauk = btau[kt];
-            const int ftq = btf[kt];
+            const double tauk = GEN ? myutau[kl] : btau[kt];
+            const int ftq = GEN ? efield(tauk) : btf[kt];
             const bool act = valid && (!own || k <= kown);
             const bool solving = act && !(own && k == kown);
             if (pq > 0) {   // local rows [0, pq) -= (block pq) pz
                 const double *c0 = Tsub + pq * kSub;
-                if (pbs == 1) update_rows<C, 1, G>(lyr, lyi, c0, c0, pq, g, pz0, pz1, ys);
-                else update_rows<C, 2, G>(lyr, lyi, c0, c0 + kSub, pq, g, pz0, pz1, ys);
+                if constexpr (GEN) {
+                    const double *d0 = Bsub + pq * kSub;
+                    const Cx zb0 = {be * pz0.re, be * pz0.im}, zb1 = {be * pz1.re, be * pz1.im};
+                    const Cx wz0 = cmul<C>(Cx{lr, li}, pz0), wz1 = cmul<C>(Cx{lr, li}, pz1);
+                    if (pbs == 1)
+                        update_rows_pencil<C, 1, G>(lyr, lyi, c0, c0, d0, d0, pq, g, zb0, zb1, wz0,
+                                                    wz1, ys);
+                    else
+                        update_rows_pencil<C, 2, G>(lyr, lyi, c0, c0 + kSub, d0, d0 + kSub, pq, g,
+                                                    zb0, zb1, wz0, wz1, ys);
+                } else {
+                    if (pbs == 1) update_rows<C, 1, G>(lyr, lyi, c0, c0, pq, g, pz0, pz1, ys);
+                    else update_rows<C, 2, G>(lyr, lyi, c0, c0 + kSub, pq, g, pz0, pz1, ys);
+                }
             }
             const int o0 = q % G, o1 = (q + 1) % G;
             double a0 = 0.0, b0 = 0.0, a1 = 0.0, b1 = 0.0;
@@ -334,7 +380,9 @@ __device__ void diag_tile_big(int s, int list_pos0, const double *__restrict__ T
         {   // protection: nu = max |rows [0, a)|, tau = stau[j], mu = max |z|
             const double nu = __longlong_as_double(rows_max(0, a));
             const double mu = __longlong_as_double(rows_max(a, b));
-            const int g2 = valid ? protect_update(nu, stau[j], mu) : 0;
+            const double tb = GEN ? fabs(be) * stau[j] + (fabs(lr) + fabs(li)) * stauB[j]
+                                  : stau[j];
+            const int g2 = valid ? protect_update(nu, tb, mu) : 0;
             if (g2 != 0) {
                 scale_rows(g2);
                 e += g2;
@@ -346,8 +394,12 @@ __device__ void diag_tile_big(int s, int list_pos0, const double *__restrict__ T
             __syncthreads();   // the chain's (or the previous chunk's) reads of Tsub are done
             for (int idx = tid; idx < kSub * sts; idx += kThreads) {
                 const int i = idx % kSub, c = idx / kSub;   // Tsub[c][i] = T[c0 + i, a + c]
-                if (i < rows)
+                if (i < rows) {
                     cp_async8(&Tsub[c * kSub + i], T + (t0 + c0 + i) + (int64_t)(t0 + a + c) * ldt);
+                    if constexpr (GEN)
+                        cp_async8(&Bsub[c * kSub + i],
+                                  pen.T + (t0 + c0 + i) + (int64_t)(t0 + a + c) * pen.ldt);
+                }
             }
             asm volatile("cp.async.commit_group;");
             asm volatile("cp.async.wait_group 0;" ::: "memory");
@@ -362,13 +414,30 @@ __device__ void diag_tile_big(int s, int list_pos0, const double *__restrict__ T
                 const double zr = myr[(a + c) * ys];
                 const double zi = C ? myi[(a + c) * ys] : 0.0;
                 const double *tc = Tsub + c * kSub;
+                if constexpr (GEN) {
+                    // rows -= S (beta z) - T (alpha z): accumulate
+                    // S zb - T wz with zb = beta z, wz = alpha z
+                    const Cx zb = {be * zr, be * zi};
+                    const Cx wz = cmul<C>(Cx{lr, li}, Cx{zr, zi});
+                    const double *dc = Bsub + c * kSub;
 #pragma unroll
-                for (int t = 0; t < R; t++) {
-                    const int i = g + G * t;
-                    if (i < rows) {
-                        const double tv = tc[i];
-                        accr[t] = fma(tv, zr, accr[t]);
-                        if (C) acci[t] = fma(tv, zi, acci[t]);
+                    for (int t = 0; t < R; t++) {
+                        const int i = g + G * t;
+                        if (i < rows) {
+                            const double sv = tc[i], tv = dc[i];
+                            accr[t] = fma(-tv, wz.re, fma(sv, zb.re, accr[t]));
+                            if (C) acci[t] = fma(-tv, wz.im, fma(sv, zb.im, acci[t]));
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int t = 0; t < R; t++) {
+                        const int i = g + G * t;
+                        if (i < rows) {
+                            const double tv = tc[i];
+                            accr[t] = fma(tv, zr, accr[t]);
+                            if (C) acci[t] = fma(tv, zi, acci[t]);
+                        }
                     }
                 }
             }
@@ -431,8 +500,14 @@ __device__ void diag_tile_big(int s, int list_pos0, const double *__restrict__ T
             if (C) nur = fmax(nur, seg_nu[at + 1]);
         }
         const int aa = min(e_r, es);
-        const int g2 = protect_update_scaled(nur, aa - e_r, tau[(int64_t)r * P.ntiles + s],
-                                             umu[uu], aa - es);
+        double trs = tau[(int64_t)r * P.ntiles + s];
+        if constexpr (GEN) {   // |beta| |S_rs| + |alpha|_1 |T_rs| for this unit
+            const int ui = ord[list_pos0 + uu];
+            trs = fabs(P.unit_beta[ui]) * trs +
+                  (fabs(P.unit_lam[2 * ui]) + fabs(P.unit_lam[2 * ui + 1])) *
+                      pen.tau[(int64_t)r * P.ntiles + s];
+        }
+        const int g2 = protect_update_scaled(nur, aa - e_r, trs, umu[uu], aa - es);
         const int ne = aa + g2;
         seg_e[at] = ne;
         seg_dx[at] = ne - es;
@@ -450,7 +525,7 @@ __device__ void diag_tile_big(int s, int list_pos0, const double *__restrict__ T
 }  // namespace
 
 // dynamic shared memory of diag_tile_big<W, C, *, GR> for a tile of t rows
-template <int W, bool C, int GR = 8>
+template <int W, bool C, bool GEN = false, int GR = 8>
 inline size_t diag_big_smem_bytes(int t) {
     constexpr int kUnits = Lanes<C, GR>::U * W;
     constexpr int FW = C ? 8 : 4;
@@ -458,12 +533,16 @@ inline size_t diag_big_smem_bytes(int t) {
                              (C ? 2 : 1) * (size_t)t * (kUnits + 1) +
                              (size_t)kUnits * kSub * FW) +
            sizeof(int) * (3 * (size_t)t + kSub + 3 * kUnits + (size_t)kUnits * kSub +
-                          2 * (kMaxSubs + 1) + 1);
+                          2 * (kMaxSubs + 1) + 1) + 16 +
+           (GEN ? sizeof(double) * ((size_t)kSub * kSub + (size_t)t + kMaxSubs +
+                                    (size_t)kUnits * kSub)
+                : 0);
 }
 
-template <int W, int GR = 8>
+template <int W, bool GEN = false, int GR = 8>
 inline size_t diag_big_smem(int t) {
-    return std::max(diag_big_smem_bytes<W, false, GR>(t), diag_big_smem_bytes<W, true, GR>(t));
+    return std::max(diag_big_smem_bytes<W, false, GEN, GR>(t),
+                    diag_big_smem_bytes<W, true, GEN, GR>(t));
 }
 
 }  // namespace evec

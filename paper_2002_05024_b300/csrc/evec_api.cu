@@ -124,7 +124,7 @@ int launch_tile_update_pencil(int s, const double *S, int64_t lds, const double 
                               int64_t ldt2, const Plan &p, const int32_t *tile_start_h,
                               const int32_t *tile_col_h, double *Y, int64_t ldy,
                               const int32_t *seg_dx, const int32_t *seg_dy, double *seg_nu,
-                              double *W, int64_t ldw, cudaStream_t st);
+                              double *W, int64_t ldw, int max_tile, cudaStream_t st);
 cudaError_t launch_batched(const BatchItem *items, int count, int *queue, DevStatus *status,
                            int nsm, cudaStream_t st, int S, int gen_tile);
 void launch_gather_batched(const double *T, const int64_t *t_off, const int64_t *row_off,
@@ -2445,7 +2445,7 @@ extern "C" evec_status evec_generalized(evec_handle h, int64_t n, const double *
     const int slices = (opt && opt->slices) ? opt->slices : 8;
     if (slices < 2 || slices > 8) return EVEC_EINVAL;
     const int nb = (opt && opt->tile) ? opt->tile : 64;
-    if (nb < 16 || nb > 64) return EVEC_EINVAL;
+    if (nb < 16 || nb > kMaxTileBig) return EVEC_EINVAL;
     if (n == 0) return EVEC_OK;
     if (!S || !T || !X || !scale_exp) return EVEC_EINVAL;
     DeviceGuard g(h->device);
@@ -2475,7 +2475,7 @@ extern "C" evec_status evec_generalized(evec_handle h, int64_t n, const double *
     EVEC_TRY(grow_device(&h->blk_tau, &h->blk_tau_cap, HP.blk_start.size()));
     EVEC_TRY(grow_device(&h->tauT, &h->tauT_cap, (size_t)N * (size_t)N));
     EVEC_TRY(grow_device(&h->blk_tauT, &h->blk_tauT_cap, HP.blk_start.size()));
-    const int64_t ldw = 2 * 64;
+    const int64_t ldw = 2 * (int64_t)HP.max_tile;
     EVEC_TRY(grow_device(&h->pW, &h->pW_cap, (size_t)ldw * (size_t)m));
     if (Z && mode == EVEC_SPLIT) {
         const int Mp = split_pad_m((int)n), Np = split_pad_n((int)m), Kp = split_pad_k((int)n);
@@ -2546,7 +2546,8 @@ extern "C" evec_status evec_generalized(evec_handle h, int64_t n, const double *
                 timed(h, EVEC_K_TILE_UPDATE, [&] {
                     return launch_tile_update_pencil(s, S, lds, T, ldt, dp, HP.tile_start.data(),
                                                      HP.tile_col.data(), Y, ldy, h->seg_dx,
-                                                     h->seg_dy, h->seg_nu, h->pW, ldw, st);
+                                                     h->seg_dy, h->seg_nu, h->pW, ldw,
+                                                     HP.max_tile, st);
                 });
             }
         }

@@ -65,42 +65,43 @@ __global__ void __launch_bounds__(32 * W)
 }
 
 // Tiles of more than 64 rows: the sub-blocked solve (diag_big.cuh).
-template <int W, bool RHS, int GR>
+template <int W, bool GEN, bool RHS, int GR>
 __global__ void __launch_bounds__(32 * W)
     k_diag_solve_big(int s, int nreal_ctas, const double *__restrict__ T, int64_t ldt, Plan P,
                      const double *__restrict__ tau, const double *__restrict__ blk_tau,
                      double *__restrict__ Y, int64_t ldy, int32_t *__restrict__ seg_e,
                      double *__restrict__ seg_nu, int32_t *__restrict__ seg_dx,
-                     int32_t *__restrict__ seg_dy, int decide) {
+                     int32_t *__restrict__ seg_dy, Pencil pen, int decide) {
     extern __shared__ double smem[];
     if ((int)blockIdx.x < nreal_ctas)
-        diag_tile_big<W, false, RHS, GR>(
+        diag_tile_big<W, false, GEN, RHS, GR>(
             s, P.tile_real[s] + blockIdx.x * (Lanes<false, GR>::U * W), T, ldt, P, tau, blk_tau,
-            Y, ldy, seg_e, seg_nu, seg_dx, seg_dy, smem, decide != 0);
+            Y, ldy, seg_e, seg_nu, seg_dx, seg_dy, smem, decide != 0, pen);
     else
-        diag_tile_big<W, true, RHS, GR>(
+        diag_tile_big<W, true, GEN, RHS, GR>(
             s, P.tile_cplx[s] + (blockIdx.x - nreal_ctas) * (Lanes<true, GR>::U * W), T, ldt, P,
-            tau, blk_tau, Y, ldy, seg_e, seg_nu, seg_dx, seg_dy, smem, decide != 0);
+            tau, blk_tau, Y, ldy, seg_e, seg_nu, seg_dx, seg_dy, smem, decide != 0, pen);
 }
 
-template <int W, bool RHS, int GR = 8>
+template <int W, bool RHS, int GR = 8, bool GEN = false>
 static int launch_big(int s, int ts, int nr, int nc, const double *T, int64_t ldt, const Plan &p,
                       const double *tau, const double *blk_tau, double *Y, int64_t ldy,
                       int32_t *seg_e, double *seg_nu, int32_t *seg_dx, int32_t *seg_dy,
-                      cudaStream_t st, bool decide, int *sms) {
+                      cudaStream_t st, bool decide, int *sms, const Pencil &pen = Pencil()) {
     constexpr int ur = Lanes<false, GR>::U * W, uc = Lanes<true, GR>::U * W;
     const int rct = (nr + ur - 1) / ur;
     const int cct = (nc + uc - 1) / uc;
     if (rct + cct == 0) return 0;
-    cudaFuncSetAttribute(k_diag_solve_big<W, RHS, GR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)diag_big_smem<W, GR>(kMaxTileBig));
-    cudaFuncSetAttribute(k_diag_solve_big<W, RHS, GR>,
+    cudaFuncSetAttribute(k_diag_solve_big<W, GEN, RHS, GR>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)diag_big_smem<W, GEN, GR>(kMaxTileBig));
+    cudaFuncSetAttribute(k_diag_solve_big<W, GEN, RHS, GR>,
                          cudaFuncAttributePreferredSharedMemoryCarveout,
                          cudaSharedmemCarveoutMaxShared);
-    const size_t smem = diag_big_smem<W, GR>(ts);
+    const size_t smem = diag_big_smem<W, GEN, GR>(ts);
     if (sms) {
         int per = 1;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_diag_solve_big<W, RHS, GR>,
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_diag_solve_big<W, GEN, RHS, GR>,
                                                           32 * W, smem) != cudaSuccess ||
             per < 1) {
             cudaGetLastError();
@@ -109,8 +110,9 @@ static int launch_big(int s, int ts, int nr, int nc, const double *T, int64_t ld
         *sms = (rct + cct + per - 1) / per;
         return 0;
     }
-    k_diag_solve_big<W, RHS, GR><<<rct + cct, 32 * W, smem, st>>>(
-        s, rct, T, ldt, p, tau, blk_tau, Y, ldy, seg_e, seg_nu, seg_dx, seg_dy, decide ? 1 : 0);
+    k_diag_solve_big<W, GEN, RHS, GR><<<rct + cct, 32 * W, smem, st>>>(
+        s, rct, T, ldt, p, tau, blk_tau, Y, ldy, seg_e, seg_nu, seg_dx, seg_dy, pen,
+        decide ? 1 : 0);
     return 1;
 }
 
@@ -239,6 +241,9 @@ int launch_diag_solve(int s, const double *T, int64_t ldt, const Plan &p,
     const int ts = tile_start_h[s + 1] - tile_start_h[s];
     const int nr = p.nreal - tile_real_h[s];
     const int nc = p.ncplx - tile_cplx_h[s];
+    if (pen && ts > 64)   // pencil tiles above 64 rows: the sub-blocked solve
+        return launch_big<4, false, 8, true>(s, ts, nr, nc, T, ldt, p, tau, blk_tau, Y, ldy,
+                                             seg_e, seg_nu, seg_dx, seg_dy, st, decide, sms, *pen);
     if (pen)
         return launch_w<4, true, false>(s, ts, nr, nc, T, ldt, p, tau, blk_tau, Y, ldy, seg_e,
                                         seg_nu, seg_dx, seg_dy, *pen, st, decide, sms);

@@ -438,19 +438,20 @@ __global__ void k_pencil_rhs(int s, Plan P, const double *__restrict__ Y, int64_
                              double *__restrict__ W, int64_t ldw) {
     const int t0 = P.tile_start[s], K = P.tile_start[s + 1] - t0;
     const int64_t c = P.tile_col[s] + blockIdx.x;
-    const int k = threadIdx.x;
-    if (k >= K || c >= P.m) return;
+    if (c >= P.m) return;
     const int u = P.col_unit[c];
     const int cu = P.unit_col[u];
     const double ar = P.unit_lam[2 * u], ai = P.unit_lam[2 * u + 1], be = P.unit_beta[u];
-    const double x = Y[(t0 + k) + c * ldy];
-    double ax;
-    if (ai == 0.0) ax = ar * x;
-    else if (c == cu) ax = fma(ar, x, -ai * Y[(t0 + k) + (c + 1) * ldy]);   // real part
-    else ax = fma(ar, x, ai * Y[(t0 + k) + (c - 1) * ldy]);                 // imaginary part
     double *w = W + (c - P.tile_col[s]) * ldw;
-    w[k] = be * x;
-    w[K + k] = -ax;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {   // tiles of up to 512 rows
+        const double x = Y[(t0 + k) + c * ldy];
+        double ax;
+        if (ai == 0.0) ax = ar * x;
+        else if (c == cu) ax = fma(ar, x, -ai * Y[(t0 + k) + (c + 1) * ldy]);   // real part
+        else ax = fma(ar, x, ai * Y[(t0 + k) + (c - 1) * ldy]);                 // imaginary part
+        w[k] = be * x;
+        w[K + k] = -ax;
+    }
 }
 
 template <int BM>
@@ -483,7 +484,7 @@ void launch_tile_update(int s, const double *T, int64_t ldt, const Plan &p, int 
     }
 }
 
-// W = [beta X_s; -(alpha X_s)] of step s (tiles of at most 64 rows).
+// W = [beta X_s; -(alpha X_s)] of step s (ld ldw >= 2 |tile s|).
 void launch_pencil_rhs(int s, const Plan &p, const int32_t *tile_col_h, const double *Y,
                        int64_t ldy, double *W, int64_t ldw, cudaStream_t st) {
     const int64_t cols = p.m - tile_col_h[s];
@@ -491,19 +492,20 @@ void launch_pencil_rhs(int s, const Plan &p, const int32_t *tile_col_h, const do
     k_pencil_rhs<<<(unsigned)cols, 64, 0, st>>>(s, p, Y, ldy, W, ldw);
 }
 
-// Pencils (tiles of at most 64 rows): W = [beta X_s; -(alpha X_s)], then
-// Y_r <- 2^dy Y_r - (S_rs W_top + T_rs W_bottom) 2^dx.  W: 2 * 64 x m
-// doubles, ld ldw >= 2 |tile s|.  Returns the number of kernels launched.
+// Pencils: W = [beta X_s; -(alpha X_s)], then
+// Y_r <- 2^dy Y_r - (S_rs W_top + T_rs W_bottom) 2^dx, one CTA per 64-row
+// chunk of a tile (max_tile: the largest tile).  W: ldw x m doubles, ld
+// ldw >= 2 |tile s|.  Returns the number of kernels launched.
 int launch_tile_update_pencil(int s, const double *S, int64_t lds, const double *T2,
                               int64_t ldt2, const Plan &p, const int32_t *tile_start_h,
                               const int32_t *tile_col_h, double *Y, int64_t ldy,
                               const int32_t *seg_dx, const int32_t *seg_dy, double *seg_nu,
-                              double *W, int64_t ldw, cudaStream_t st) {
+                              double *W, int64_t ldw, int max_tile, cudaStream_t st) {
     if (s <= 0) return 0;
     const int64_t cols = p.m - tile_col_h[s];
     if (cols <= 0) return 0;
     launch_pencil_rhs(s, p, tile_col_h, Y, ldy, W, ldw, st);
-    dim3 grid((unsigned)((cols + kBN - 1) / kBN), (unsigned)s);
+    dim3 grid((unsigned)((cols + kBN - 1) / kBN), (unsigned)s, (unsigned)((max_tile + 63) / 64));
     set_smem_attr<64>();
     k_tile_update<64, true><<<grid, kThreads, sizeof(GemmSmem<64>), st>>>(
         s, S, lds, p, Y, ldy, seg_dx, seg_dy, seg_nu, T2, ldt2, W, ldw);

@@ -123,3 +123,15 @@ def test_generalized_config4_full_size_sampled(mode):
         col += sz
     _parity(S, T, Z, (X[:, cols], e[cols], ar[cols], ai[cols], be[cols]), select=sel,
             rel_tol=1e-9)
+
+
+@pytest.mark.parametrize("mode", ["fp64", "split"])
+@pytest.mark.parametrize("n,tile", [(700, 128), (900, 256), (1100, 512), (600, 200)])
+def test_generalized_big_tiles(n, tile, mode):
+    # pencil tiles above 64 rows: S's and T's sub-blocks of at most 64 rows
+    # inside each tile, the rows above a sub-block updated in one protected
+    # pass with both matrices; with Z and without
+    S, T, blocks = workloads.generalized_pair(n, seed=n + tile)
+    Z = workloads.householder_orthogonal(n, seed=n + tile + 1)
+    _parity(S, T, Z, _run(S, T, Z, tile=tile, mode=mode))
+    _parity(S, T, None, _run(S, T, tile=tile, mode=mode))
