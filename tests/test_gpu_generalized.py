@@ -96,8 +96,8 @@ def test_generalized_errors():
     bad = T.copy()
     bad[90, 7] = np.nan                    # strictly lower part of T: never read
     _parity(S, T, None, _run(S, bad, tile=32))
-    with pytest.raises(ev.EvecError) as ei:   # tiles above 64 rows: not for pencils
-        _run(S, T, tile=128)
+    with pytest.raises(ev.EvecError) as ei:   # tiles above 512 rows are refused
+        _run(S, T, tile=513)
     assert ei.value.status == ev.EVEC_EINVAL
 
 
