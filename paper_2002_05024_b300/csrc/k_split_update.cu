@@ -237,37 +237,25 @@ __global__ void __launch_bounds__(kUThreads, 1)
             }
         }
         const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(cg * 8);
-        const int cl0 = cg * 8;   // first local column of this warp
-        // The old values of Y are loaded one tile ahead (software pipelined
-        // across the tile loop): tile j + 1's loads are issued as soon as
-        // tile j's accumulators are drained, so their latency hides behind
-        // tile j's recombination and stores and tile j + 1's waits.  Every
-        // loaded element lies in rows < M and columns < N; a fresh segment's
-        // value is loaded but not used.
-        double nxt[8];
-        auto load_old = [&](int jj) {
-            const int cj = ((int)blockIdx.x + jj * (int)gridDim.x) * kUN + cl0;
-            const double *yc = Y + row + ((int64_t)col0 + cj) * ldy;
-#pragma unroll
-            for (int q = 0; q < 8; q++) nxt[q] = (rv && cj + q < N) ? yc[q * ldy] : 0.0;
-        };
-        if (nmine > 0) load_old(0);
         for (int j = 0; j < nmine; j++) {
             const int ab = j & 1;
             const uint32_t ph = (uint32_t)(j >> 1) & 1;
+            const int cl0 = cg * 8;   // first local column of this warp
             const int c0 = ((int)blockIdx.x + j * (int)gridDim.x) * kUN + cl0;
-            double oldv[8];
-#pragma unroll
-            for (int q = 0; q < 8; q++) oldv[q] = nxt[q];
             if (!mbar_wait(saddr(&t_full[ab]), ph, err)) break;
             const int *t = tab + ab * kUTableInts;
             const int *tdx = t + slot * kUN + cl0;
             const int *tdy = t + (kUSlots + slot) * kUN + cl0;
             const int *teb = t + 2 * kUSlots * kUN + cl0;
+            // operands that do not wait for the accumulator
             double *ycol = Y + row + ((int64_t)col0 + c0) * ldy;
+            double oldv[8];
             int dyv[8];
 #pragma unroll
-            for (int q = 0; q < 8; q++) dyv[q] = tdy[q];
+            for (int q = 0; q < 8; q++) {
+                dyv[q] = tdy[q];
+                oldv[q] = (rv && c0 + q < N && dyv[q] != kFresh) ? ycol[q * ldy] : 0.0;
+            }
             if (!mbar_wait(saddr(&acc_full[ab]), ph, err)) break;
             asm volatile("tcgen05.fence::after_thread_sync;");
             const uint32_t ta = tl + (uint32_t)(ab * kUAccCols);
@@ -310,7 +298,6 @@ __global__ void __launch_bounds__(kUThreads, 1)
             asm volatile("tcgen05.fence::before_thread_sync;");
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_empty[ab]);
-            if (j + 1 < nmine) load_old(j + 1);
 #pragma unroll
             for (int q = 0; q < 8; q++) {
                 const int c = c0 + q;

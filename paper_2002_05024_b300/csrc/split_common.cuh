@@ -127,81 +127,10 @@ __device__ __forceinline__ double f2d_pow2(float f, int k, bool &ok) {
     return __longlong_as_double((long long)bits);
 }
 
-// (hi + lo) 2^k rounded once to the nearest double (ties to even) for a
-// renormalised double-float pair (|lo| <= ulp(hi)), built from the binary32
-// fields with 64-bit integer arithmetic, so the FP64 pipe (the scarce unit
-// of an epilogue) is not used: hi's 24-bit significand at bit 39 of M, lo's
-// aligned below it (bits shifted out kept as a sticky flag), normalised by a
-// count of leading zeros and rounded at bit 11.  The result equals the FP64
-// sum (double) hi + (double) lo scaled by 2^k.  ok is cleared for a zero hi
-// with a nonzero lo, a subnormal, Inf or NaN part, or a result that is not
-// a normal double.
-__device__ __forceinline__ double df_round_int(float hi, float lo, int k, bool &ok) {
-    const uint32_t uh = __float_as_uint(hi), ul = __float_as_uint(lo);
-    const uint32_t ah = uh & 0x7fffffffu, al = ul & 0x7fffffffu;
-    if (ah == 0u) {
-        ok = ok && al == 0u;
-        return 0.0;
-    }
-    const int eh = (int)(ah >> 23), el = (int)(al >> 23);
-    if (eh == 0 || eh == 255 || el == 255 || (el == 0 && al != 0u)) {
-        ok = false;
-        return 0.0;
-    }
-    uint64_t M = (uint64_t)((ah & 0x7fffffu) | 0x800000u) << 39;
-    bool sticky = false;
-    if (al != 0u) {
-        const uint64_t ml = (uint64_t)((al & 0x7fffffu) | 0x800000u);
-        const int d = eh - el;   // at least 23 for a renormalised pair
-        if (d < 16) {
-            ok = false;
-            return 0.0;
-        }
-        uint64_t L = 0;
-        if (d <= 39) {
-            L = ml << (39 - d);
-        } else if (d < 39 + 25) {
-            L = ml >> (d - 39);
-            sticky = (ml & ((1ull << (d - 39)) - 1)) != 0;
-        } else {
-            sticky = true;
-        }
-        if ((uh ^ ul) >> 31) {   // opposite signs: the value lies in (M - L - 1, M - L)
-            M -= L;
-            if (sticky) M -= 1;
-        } else {
-            M += L;
-        }
-    }
-    const int lz = __clzll((long long)M);
-    M <<= lz;
-    int E = eh - 126 - lz;   // value = (M / 2^63) 2^E
-    uint64_t m = M >> 11;
-    const uint64_t rem = M & 0x7ffull;
-    if (rem > 0x400ull || (rem == 0x400ull && (sticky || (m & 1ull)))) {
-        m += 1;
-        if (m >> 53) {
-            m >>= 1;
-            E += 1;
-        }
-    }
-    const int be = E + k + 1023;
-    if (be < 1 || be > 2046) {
-        ok = false;
-        return 0.0;
-    }
-    return __longlong_as_double((long long)(((uint64_t)(uh >> 31) << 63) | ((uint64_t)be << 52) |
-                                            (m & ((1ull << 52) - 1))));
-}
-
 // (hi + lo) 2^k in FP64 for a normalised double-float pair (|lo| <= ulp(hi)
-// / 2): by integer arithmetic (df_round_int), else both parts scaled and
-// one FP64 add
+// / 2): both parts scaled exactly, then one FP64 add, exact (48 bits)
 __device__ __forceinline__ double df_to_double(float hi, float lo, int k) {
     bool ok = true;
-    const double r = df_round_int(hi, lo, k, ok);
-    if (ok) return r;
-    ok = true;
     const double h = f2d_pow2(hi, k, ok), l = f2d_pow2(lo, k, ok);
     return ok ? h + l : scale2((double)hi + (double)lo, k);
 }
