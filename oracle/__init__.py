@@ -74,6 +74,8 @@ class Oracle:
         lib.evo_generalized.argtypes = [i64, p, i64, p, i64, p, i64, p, p, i64,
                                         p, p, p, p, ctypes.c_int, p]
         lib.evo_generalized.restype = ctypes.c_int
+        lib.evo_generalized_left.argtypes = lib.evo_generalized.argtypes
+        lib.evo_generalized_left.restype = ctypes.c_int
         lib.evo_trsolve.argtypes = [i64, p, i64, i64, p, i64, p, i64, p, ctypes.c_int, p]
         lib.evo_trsolve.restype = ctypes.c_int
         lib.evo_hessenberg.argtypes = [i64, p, i64, p, i64, p, p]
@@ -118,9 +120,11 @@ class Oracle:
             raise OracleError(st, int(bad[0]))
         return X, e, lr, li
 
-    def generalized(self, S, T, Z=None, select=None, threads: int = 0):
+    def generalized(self, S, T, Z=None, select=None, threads: int = 0, left: bool = False):
         """Generalized eigenvectors of (S, T) (optionally back-transformed by
-        Z).  Returns (X, scale_exp, alpha_re, alpha_im, beta)."""
+        Z).  Returns (X, scale_exp, alpha_re, alpha_im, beta).  left: the
+        left eigenvectors, u^H (beta S - alpha T) = 0 (pairs: columns Re u,
+        Im u for Im alpha > 0), zero above their block."""
         S = _fortran(S)
         T = _fortran(T)
         n = S.shape[0]
@@ -133,9 +137,10 @@ class Oracle:
         be = np.zeros(m)
         Zf = None if Z is None else _fortran(Z)
         bad = np.full(1, -1, dtype=np.int64)
-        st = self.lib.evo_generalized(n, _ptr(S), max(n, 1), _ptr(T), max(n, 1), _ptr(Zf),
-                                      max(n, 1), _ptr(sel), _ptr(X), max(n, 1), _ptr(e),
-                                      _ptr(ar), _ptr(ai), _ptr(be), int(threads), _ptr(bad))
+        fn = self.lib.evo_generalized_left if left else self.lib.evo_generalized
+        st = fn(n, _ptr(S), max(n, 1), _ptr(T), max(n, 1), _ptr(Zf), max(n, 1), _ptr(sel),
+                _ptr(X), max(n, 1), _ptr(e), _ptr(ar), _ptr(ai), _ptr(be), int(threads),
+                _ptr(bad))
         if st:
             raise OracleError(st, int(bad[0]))
         return X, e, ar, ai, be
@@ -248,6 +253,11 @@ def left(S, Q=None, select=None, threads: int = 0):
 
 def generalized(S, T, Z=None, select=None, threads: int = 0):
     return default().generalized(S, T, Z, select, threads)
+
+
+def generalized_left(S, T, Z=None, select=None, threads: int = 0):
+    """Left eigenvectors u^H (beta S - alpha T) = 0 (see Oracle.generalized)."""
+    return default().generalized(S, T, Z, select, threads, left=True)
 
 
 def naive_standard(S, select=None):

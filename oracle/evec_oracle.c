@@ -311,6 +311,7 @@ typedef struct {
     const double *tauS;               /* per block: |S[0:start, block]|_inf */
     const double *tauT;               /* per block: |T[0:start, block]|_inf */
     const double *tauL;               /* per block: |S[block, end:n]^T|_inf (left) */
+    const double *tauLT;              /* per block: |T[block, end:n]^T|_inf (left, pencil) */
     double smax, tmax;                /* max |S_ii|, max |T_ii| (generalized smin) */
 } problem_t;
 
@@ -431,7 +432,10 @@ static void solve_one(const problem_t *P, int generalized, int64_t k,
 }
 
 /*
- * Left eigenvector of block k of the standard problem, lambda = ar + i ai.
+ * Left eigenvector of block k of the standard problem, lambda = ar + i ai
+ * (generalized: of the pencil, eigenvalue alpha / beta with alpha = ar + i ai;
+ * the matrix S - lambda I below is then beta S - alpha T, and the bound of an
+ * update |beta| |S[..]| + |alpha|_1 |T[..]|).
  * A left eigenvector satisfies u^H S = lambda u^H; with w = conj(u) this is
  * w^T (S - lambda I) = 0, the transposed system, solved by forward
  * substitution over the blocks after k: w is zero above block k, fixed on
@@ -441,8 +445,8 @@ static void solve_one(const problem_t *P, int generalized, int64_t k,
  * an update from block q is |S[block q, after q]^T|_inf).  On return w (wr,
  * wi) holds w_true * 2^e; rows above the block are 0.
  */
-static void solve_one_left(const problem_t *P, int64_t k, double ar, double ai,
-                           const double *own_r, const double *own_i,
+static void solve_one_left(const problem_t *P, int generalized, int64_t k, double ar, double ai,
+                           double beta, const double *own_r, const double *own_i,
                            double *wr, double *wi, int64_t *e_out)
 {
     const int64_t n = P->n;
@@ -451,7 +455,11 @@ static void solve_one_left(const problem_t *P, int64_t k, double ar, double ai,
     const int64_t p = B[k].start;
     const int bs = B[k].size;
     int64_t e = 0;
-    double smin = ULP * cabs1(ar, ai);
+    double smin;
+    if (generalized)
+        smin = ULP * (fabs(beta) * P->smax + cabs1(ar, ai) * P->tmax);
+    else
+        smin = ULP * cabs1(ar, ai);
     double smlnum = SAFMIN * ((double)n / ULP);
     if (smin < smlnum) smin = smlnum;
 
@@ -479,7 +487,10 @@ static void solve_one_left(const problem_t *P, int64_t k, double ar, double ai,
                 if (cplx && fabs(wi[q + j]) > a) a = fabs(wi[q + j]);
                 if (a > mu) mu = a;
             }
-            int64_t s = protect_update(nu, P->tauL[cur], mu);
+            const double tau = generalized
+                                   ? fabs(beta) * P->tauL[cur] + cabs1(ar, ai) * P->tauLT[cur]
+                                   : P->tauL[cur];
+            int64_t s = protect_update(nu, tau, mu);
             if (s != 0) {
                 scale_vec(n, wr, s);
                 if (cplx) scale_vec(n, wi, s);
@@ -489,8 +500,15 @@ static void solve_one_left(const problem_t *P, int64_t k, double ar, double ai,
                 const double zr = wr[q + j], zi = cplx ? wi[q + j] : 0.0;
                 for (int64_t c = q1; c < n; c++) {
                     const double sv = AT(P->S, P->lds, q + j, c);
-                    wr[c] -= sv * zr;
-                    if (cplx) wi[c] -= sv * zi;
+                    if (!generalized) {
+                        wr[c] -= sv * zr;
+                        if (cplx) wi[c] -= sv * zi;
+                    } else {
+                        /* C^T z with C = beta S - alpha T, alpha complex */
+                        const double bsv = beta * sv, tv = AT(P->T, P->ldt, q + j, c);
+                        wr[c] -= bsv * zr - tv * (ar * zr - ai * zi);
+                        if (cplx) wi[c] -= bsv * zi - tv * (ar * zi + ai * zr);
+                    }
                 }
             }
         }
@@ -502,8 +520,16 @@ static void solve_one_left(const problem_t *P, int64_t k, double ar, double ai,
         double mr[4], mi[4], rr[2], ri[2], zr[2], zi[2];
         for (int a = 0; a < ib; a++) {
             for (int b = 0; b < ib; b++) {
-                mr[a * ib + b] = AT(P->S, P->lds, i0 + b, i0 + a) - (a == b ? ar : 0.0);
-                mi[a * ib + b] = (a == b ? -ai : 0.0);
+                /* the transposed block: entry (a, b) is C[i0 + b, i0 + a] */
+                const double sv = AT(P->S, P->lds, i0 + b, i0 + a);
+                if (!generalized) {
+                    mr[a * ib + b] = sv - (a == b ? ar : 0.0);
+                    mi[a * ib + b] = (a == b ? -ai : 0.0);
+                } else {
+                    const double tv = (a >= b) ? AT(P->T, P->ldt, i0 + b, i0 + a) : 0.0;
+                    mr[a * ib + b] = beta * sv - ar * tv;
+                    mi[a * ib + b] = -ai * tv;
+                }
             }
             rr[a] = wr[i0 + a];
             ri[a] = cplx ? wi[i0 + a] : 0.0;
@@ -591,7 +617,8 @@ static int run_jobs(const problem_t *P, int generalized, int left, const double 
             int64_t e = 0;
             if (left) {
                 /* w = conj(u): the stored columns are (Re u, Im u) */
-                solve_one_left(P, k, ar, ai, &own[4 * k], &own[4 * k + 2], yr, yi, &e);
+                solve_one_left(P, generalized, k, ar, ai, beta, &own[4 * k], &own[4 * k + 2], yr,
+                               yi, &e);
                 if (cplx)
                     for (int64_t r = 0; r < n; r++) yi[r] = -yi[r];
             } else {
@@ -700,7 +727,7 @@ static int standard_impl(int left, int64_t n, const double *S, int64_t lds, cons
     }
     {
         problem_t P = {n, S, lds, NULL, 0, blk, nblk, left ? NULL : tau, NULL,
-                       left ? tau : NULL, 0.0, 0.0};
+                       left ? tau : NULL, NULL, 0.0, 0.0};
         st = run_jobs(&P, 0, left, Q, ldq, jobs, njobs, lre, lim, NULL, own, X, ldx, scale_exp,
                       nthreads);
     }
@@ -746,11 +773,11 @@ int evo_standard_left(int64_t n, const double *S, int64_t lds, const double *Q, 
  * in [1, 2) (|alpha| = max(|re|, |im|)).  For a 2x2 block the column pair is
  * (Re, Im) of the eigenvector of the member with Im alpha > 0.  Optional Z.
  */
-int evo_generalized(int64_t n, const double *S, int64_t lds, const double *T, int64_t ldt,
-                    const double *Z, int64_t ldz, const uint8_t *select,
-                    double *X, int64_t ldx, int32_t *scale_exp,
-                    double *alpha_re, double *alpha_im, double *beta_out,
-                    int nthreads, int64_t *bad)
+static int generalized_impl(int left, int64_t n, const double *S, int64_t lds, const double *T,
+                            int64_t ldt, const double *Z, int64_t ldz, const uint8_t *select,
+                            double *X, int64_t ldx, int32_t *scale_exp,
+                            double *alpha_re, double *alpha_im, double *beta_out,
+                            int nthreads, int64_t *bad)
 {
     if (n < 0 || lds < (n > 0 ? n : 1) || ldt < (n > 0 ? n : 1) || ldx < (n > 0 ? n : 1))
         return EVO_EINVAL;
@@ -781,8 +808,11 @@ int evo_generalized(int64_t n, const double *S, int64_t lds, const double *T, in
     int64_t njobs = 0, col = 0;
     for (int64_t k = 0; k < nblk; k++) {
         const int64_t p = blk[k].start;
-        tauS[k] = block_col_norm(S, lds, p, p, blk[k].size);
-        tauT[k] = block_col_norm(T, ldt, p, p, blk[k].size);
+        const int64_t pe = p + blk[k].size;
+        tauS[k] = left ? block_row_norm(S, lds, n, p, blk[k].size, pe)
+                       : block_col_norm(S, lds, p, p, blk[k].size);
+        tauT[k] = left ? block_row_norm(T, ldt, n, p, blk[k].size, pe)
+                       : block_col_norm(T, ldt, p, p, blk[k].size);
         double ar, ai, be;
         double *o = &own[4 * k];
         if (blk[k].size == 1) {
@@ -798,6 +828,14 @@ int evo_generalized(int64_t n, const double *S, int64_t lds, const double *T, in
             double s11 = AT(S, lds, p, p), s12 = AT(S, lds, p, p + 1);
             double s21 = AT(S, lds, p + 1, p), s22 = AT(S, lds, p + 1, p + 1);
             double d1 = AT(T, ldt, p, p), d2 = AT(T, ldt, p + 1, p + 1);
+            if (left) {
+                /* the left eigenvalue pair is defined on the reversed
+                   transposed block J B^T J (entries (s22, s12; s21, s11)
+                   against diag(d2, d1)), the block a forward substitution
+                   meets first from its last row */
+                double t = s11; s11 = s22; s22 = t;
+                t = d1; d1 = d2; d2 = t;
+            }
             if (!(d1 > 0.0 && d2 > 0.0) || AT(T, ldt, p, p + 1) != 0.0) {
                 if (bad) *bad = p;
                 st = EVO_ENOTSCHUR;
@@ -833,10 +871,15 @@ int evo_generalized(int64_t n, const double *S, int64_t lds, const double *T, in
         }
         lre[k] = ar; lim[k] = ai; lbe[k] = be;
         if (blk[k].size == 2) {
-            /* null vector of M = beta S_b - alpha T_b (complex alpha) */
+            /* null vector of M = beta S_b - alpha T_b (complex alpha); left:
+               of the reversed transposed block, stored in reverse below */
             double s11 = AT(S, lds, p, p), s12 = AT(S, lds, p, p + 1);
             double s21 = AT(S, lds, p + 1, p), s22 = AT(S, lds, p + 1, p + 1);
             double d1 = AT(T, ldt, p, p), d2 = AT(T, ldt, p + 1, p + 1);
+            if (left) {
+                double t = s11; s11 = s22; s22 = t;
+                t = d1; d1 = d2; d2 = t;
+            }
             double m12 = be * s12, m21 = be * s21;
             if (fabs(m12) >= fabs(m21)) {
                 /* row 1: m11 v1 + m12 v2 = 0, v1 = 1, v2 = -m11 / m12 */
@@ -849,6 +892,10 @@ int evo_generalized(int64_t n, const double *S, int64_t lds, const double *T, in
                 /* -m22 * i = m22i - i m22r */
                 o[0] = m22i / m21; o[2] = -m22r / m21;
                 o[1] = 0.0; o[3] = 1.0;
+            }
+            if (left) {   /* w's block part is the reversed vector */
+                double t = o[0]; o[0] = o[1]; o[1] = t;
+                t = o[2]; o[2] = o[3]; o[3] = t;
             }
         }
         int sel = select == NULL || select[p] || (blk[k].size == 2 && select[p + 1]);
@@ -863,12 +910,45 @@ int evo_generalized(int64_t n, const double *S, int64_t lds, const double *T, in
         }
     }
     {
-        problem_t P = {n, S, lds, T, ldt, blk, nblk, tauS, tauT, NULL, smax, tmax};
-        st = run_jobs(&P, 1, 0, Z, ldz, jobs, njobs, lre, lim, lbe, own, X, ldx, scale_exp, nthreads);
+        problem_t P = {n, S, lds, T, ldt, blk, nblk, left ? NULL : tauS, left ? NULL : tauT,
+                       left ? tauS : NULL, left ? tauT : NULL, smax, tmax};
+        st = run_jobs(&P, 1, left, Z, ldz, jobs, njobs, lre, lim, lbe, own, X, ldx, scale_exp,
+                      nthreads);
     }
 done:
     free(blk); free(tauS); free(tauT); free(lre); free(lim); free(lbe); free(own); free(jobs);
     return st;
+}
+
+int evo_generalized(int64_t n, const double *S, int64_t lds, const double *T, int64_t ldt,
+                    const double *Z, int64_t ldz, const uint8_t *select,
+                    double *X, int64_t ldx, int32_t *scale_exp,
+                    double *alpha_re, double *alpha_im, double *beta_out,
+                    int nthreads, int64_t *bad)
+{
+    return generalized_impl(0, n, S, lds, T, ldt, Z, ldz, select, X, ldx, scale_exp, alpha_re,
+                            alpha_im, beta_out, nthreads, bad);
+}
+
+/*
+ * Left eigenvectors of the pencil (S, T): u_i^H (beta_i S - alpha_i T) = 0
+ * (the eigenvector problem of Sec. 2 for the transposed pencil), by robust
+ * forward substitution over the blocks after block i, optional Z (x_i =
+ * Z u_i).  Requirements, column order, canonical form and outputs as
+ * evo_generalized; u_i is zero above its block.  For a 2x2 block, (alpha,
+ * beta) and the block part of u are those of the reversed transposed block
+ * (entries (s22, s12; s21, s11) against diag(d2, d1)): the same eigenvalue
+ * alpha / beta, the pair normalised against d2; the column pair is (Re u,
+ * Im u) for the member with Im alpha > 0.
+ */
+int evo_generalized_left(int64_t n, const double *S, int64_t lds, const double *T, int64_t ldt,
+                         const double *Z, int64_t ldz, const uint8_t *select,
+                         double *X, int64_t ldx, int32_t *scale_exp,
+                         double *alpha_re, double *alpha_im, double *beta_out,
+                         int nthreads, int64_t *bad)
+{
+    return generalized_impl(1, n, S, lds, T, ldt, Z, ldz, select, X, ldx, scale_exp, alpha_re,
+                            alpha_im, beta_out, nthreads, bad);
 }
 
 /* ------------------------------------------------------------------ */
@@ -961,7 +1041,7 @@ int evo_trsolve(int64_t n, const double *S, int64_t lds, int64_t nrhs, const dou
     for (int64_t k = 0; k < nblk; k++)
         tau[k] = block_col_norm(S, lds, blk[k].start, blk[k].start, blk[k].size);
     {
-        problem_t P = {n, S, lds, NULL, 0, blk, nblk, tau, NULL, NULL, 0.0, 0.0};
+        problem_t P = {n, S, lds, NULL, 0, blk, nblk, tau, NULL, NULL, NULL, 0.0, 0.0};
 #ifdef _OPENMP
         if (nthreads > 0) omp_set_num_threads(nthreads);
 #else

@@ -97,6 +97,24 @@ def generalized_residuals(S, T, X, a_re, a_im, beta):
     return np.array(res)
 
 
+def generalized_left_residuals(S, T, X, a_re, a_im, beta):
+    """||u^H (beta S - alpha T)||_1 / ((|beta| ||S||_inf + |alpha| ||T||_inf)
+    ||u||_1 u) per eigenvalue, for left eigenvectors stored as (Re u, Im u):
+    the residual of (beta S^T - alpha T^T) conj(u) = 0."""
+    Xc = np.array(X, dtype=np.float64, copy=True)
+    for j, pair in column_groups(a_im):
+        if pair:
+            Xc[:, j + 1] = -Xc[:, j + 1]
+    return generalized_residuals(np.ascontiguousarray(S.T), np.ascontiguousarray(T.T), Xc,
+                                 a_re, a_im, beta)
+
+
+def flip_pencil(S, T):
+    """(J S^T J, J T^T J), J the reversal permutation: the pencil whose right
+    eigenvectors are the reversed conjugated left eigenvectors of (S, T)."""
+    return (np.asfortranarray(S.T[::-1, ::-1]), np.asfortranarray(T.T[::-1, ::-1]))
+
+
 def canonical_norms(X, lam_im):
     out = []
     for j, pair in column_groups(lam_im):
@@ -330,3 +348,15 @@ def mp_gen_eigvec(S, T, p, size, prec=256):
             y[q] = (rhs[0] * m22 - m12 * rhs[1]) / det
             y[q + 1] = (m11 * rhs[1] - m21 * rhs[0]) / det
     return y
+
+
+def mp_gen_left_eigvec(S, T, p, size, prec=256):
+    """Left eigenvector u of the pencil (S, T), u^H (beta S - alpha T) = 0,
+    for the block at p: from the right-eigenvector reference on the flipped
+    pencil (J S^T J, J T^T J) (upper quasi-triangular and upper triangular,
+    the same blocks in reverse order), u = conj(J y')."""
+    import mpmath as mp
+    n = S.shape[0]
+    Sf, Tf = flip_pencil(S, T)
+    y = mp_gen_eigvec(Sf, Tf, n - p - size, size, prec)
+    return [mp.conj(v) for v in reversed(y)]

@@ -16,9 +16,9 @@ import scipy.linalg as sl
 
 import oracle
 import workloads
-from evec_checks import (U, canonical_norms, column_groups, generalized_residuals,
-                         left_residuals, mp_canonical, mp_eigvec, mp_left_eigvec,
-                         standard_residuals)
+from evec_checks import (U, canonical_norms, column_groups, flip_pencil,
+                         generalized_left_residuals, generalized_residuals, left_residuals,
+                         mp_canonical, mp_eigvec, mp_left_eigvec, standard_residuals)
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "hand_examples.json")
 
@@ -50,12 +50,22 @@ MUTANTS = [
     ("eigenvalue_imag_sign", "lre[k] = a; lim[k] = w;", "lre[k] = a; lim[k] = -w;"),
     ("left_update_sign", "wr[c] -= sv * zr;", "wr[c] += sv * zr;"),
     ("left_small_system_not_transposed",
-     "mr[a * ib + b] = AT(P->S, P->lds, i0 + b, i0 + a) - (a == b ? ar : 0.0);",
-     "mr[a * ib + b] = AT(P->S, P->lds, i0 + a, i0 + b) - (a == b ? ar : 0.0);"),
+     "const double sv = AT(P->S, P->lds, i0 + b, i0 + a);",
+     "const double sv = AT(P->S, P->lds, i0 + a, i0 + b);"),
     ("left_own_block_sign", "o[2] = w / b;", "o[2] = -w / b;"),
     ("left_conjugation_dropped", "for (int64_t r = 0; r < n; r++) yi[r] = -yi[r];", "(void)0;"),
-    ("left_update_unprotected", "int64_t s = protect_update(nu, P->tauL[cur], mu);",
-     "int64_t s = 0;"),
+    ("left_update_unprotected",
+     ": P->tauL[cur];\n            int64_t s = protect_update(nu, tau, mu);",
+     ": P->tauL[cur];\n            int64_t s = 0;"),
+    ("generalized_left_T_update_dropped",
+     "tv = AT(P->T, P->ldt, q + j, c);", "tv = AT(P->T, P->ldt, c, q + j);"),
+    ("generalized_left_T_bound_dropped",
+     "cabs1(ar, ai) * P->tauLT[cur]", "0.0 * P->tauLT[cur]"),
+    ("generalized_left_own_block_not_reversed",
+     "double t = o[0]; o[0] = o[1]; o[1] = t;", "double t = o[0];"),
+    ("generalized_left_alpha_sign",
+     "wr[c] -= bsv * zr - tv * (ar * zr - ai * zi);",
+     "wr[c] -= bsv * zr + tv * (ar * zr - ai * zi);"),
     ("hessenberg_beta_sign", "if (alpha >= 0.0) beta = -beta;", "if (alpha < 0.0) beta = -beta;"),
     ("hessenberg_tau", "const double t = (beta - alpha) / beta;",
      "const double t = (beta - alpha) / alpha;"),
@@ -178,6 +188,36 @@ def detector_failures(orc):
             col += sz
         return True
 
+    def generalized_left():
+        S, T, _ = workloads.generalized_pair(80, seed=12)
+        Z = workloads.householder_orthogonal(80, seed=13)
+        X, e, ar, ai, be = orc.generalized(S, T, Z=Z, left=True)
+        A = Z @ S @ Z.T
+        B = Z @ T @ Z.T
+        if not (np.isfinite(X).all() and
+                generalized_left_residuals(A, B, X, ar, ai, be).max() <= 10 * 80):
+            return False
+        # the flipped pencil's right eigenvalues, in reverse block order
+        _, _, arf, aif, bef = orc.generalized(*flip_pencil(S, T))
+        lam = np.sort_complex((ar + 1j * ai) / be)
+        lamf = np.sort_complex((arf + 1j * aif) / bef)
+        return np.allclose(lam, lamf, rtol=1e-12, atol=0)
+
+    def generalized_left_adversarial():
+        # T-dominated growth: large upper part in T, clusters 1e-9 apart
+        rng = np.random.default_rng(14)
+        n = 64
+        S = np.triu(rng.standard_normal((n, n)), 1)
+        T = np.triu(rng.standard_normal((n, n)) * 1e3, 1)
+        d = rng.uniform(0.5, 2.0, n)
+        lam = np.concatenate([-0.5 + (rng.permutation(32) - 16) * 1e-9,
+                              0.5 + (rng.permutation(32) - 16) * 1e-9])
+        S[np.arange(n), np.arange(n)] = lam * d
+        T[np.arange(n), np.arange(n)] = d
+        X, e, ar, ai, be = orc.generalized(S, T, left=True)
+        return np.isfinite(X).all() and \
+            generalized_left_residuals(S, T, X, ar, ai, be).max() <= 10 * n
+
     def hessenberg():
         A = np.random.default_rng(3).standard_normal((40, 40))
         H, Q, _ = orc.hessenberg(A)
@@ -215,6 +255,8 @@ def detector_failures(orc):
     check("left_residual", left_residual)
     check("left_adversarial", left_adversarial)
     check("left_brute_force", left_brute_force)
+    check("generalized_left", generalized_left)
+    check("generalized_left_adversarial", generalized_left_adversarial)
     check("hessenberg", hessenberg)
     check("window", window)
     return fails
