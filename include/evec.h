@@ -369,6 +369,30 @@ evec_status evec_generalized(evec_handle h, int64_t n, const double *S, int64_t 
                              int32_t *scale_exp, double *alpha_re, double *alpha_im,
                              double *beta, const evec_opts *opt);
 
+/*
+ * Generalized left eigenvectors of the pencil (S, T): u_j^H (beta_j S -
+ * alpha_j T) = 0 (the eigenvector problem of Sec. 2 for the transposed
+ * pencil), optionally back-transformed by Z (NULL: X = U; else x_j = Z u_j).
+ * Same requirements on (S, T), arguments, selection, column order (S's
+ * block order), canonical form, options and errors as evec_generalized.
+ * u_j is zero above its block; for a 1x1 block u_p = 1.  For a 2x2 block
+ * the eigenvalue pair and the block part of u come from the reversed
+ * transposed block (entries (s22, s12; s21, s11) against diag(d2, d1)):
+ * alpha = lambda d2, beta = d2 before the power-of-two normalisation, and
+ * the columns are (Re u, Im u) for Im alpha > 0 (alpha_im = +w, -w).
+ * Computed as the right eigenvectors of the flipped pencil (J S^T J, J T^T
+ * J) (J the reversal permutation; the blocks in reverse order) with Z J
+ * for the back-transformation, so the handle holds three extra n x n and
+ * one n x m FP64 workspaces.  A non-finite or over-range entry of S or T
+ * strictly above the first superdiagonal is reported at evec_sync with its
+ * index i + j lds (or ldt).
+ */
+evec_status evec_generalized_left(evec_handle h, int64_t n, const double *S, int64_t lds,
+                                  const double *T, int64_t ldt, const double *Z, int64_t ldz,
+                                  const uint8_t *select_host, double *X, int64_t ldx,
+                                  int32_t *scale_exp, double *alpha_re, double *alpha_im,
+                                  double *beta, const evec_opts *opt);
+
 /* Number of output columns m of evec_generalized for a selection: S's 1x1
  * and 2x2 blocks (2 columns per selected 2x2 block), with the same checks
  * of the pencil's form as evec_generalized (synchronises the handle's

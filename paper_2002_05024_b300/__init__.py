@@ -102,6 +102,7 @@ def lib() -> ctypes.CDLL:
                                    ctypes.POINTER(_Opts)]
         L.evec_generalized.argtypes = [p, i64, p, i64, p, i64, p, i64, p, p, i64, p, p, p, p,
                                        ctypes.POINTER(_Opts)]
+        L.evec_generalized_left.argtypes = L.evec_generalized.argtypes
         L.evec_batched_count.argtypes = [p, i64, p, p, p, p, p]
         L.evec_count_generalized.argtypes = [p, i64, p, i64, p, i64, p, ctypes.POINTER(i64)]
         L.evec_batched_generalized_count.argtypes = [p, i64, p, p, p, p, p, p, p]
@@ -125,6 +126,7 @@ def lib() -> ctypes.CDLL:
                   "evec_set_hessenberg_panel", "evec_gate_stats", "evec_window_update",
                   "evec_window_update_set",
                   "evec_generalized", "evec_count_generalized", "evec_set_wait_limit",
+                  "evec_generalized_left",
                   "evec_set_gate_factor", "evec_standard_noalloc",
                   "evec_batched_generalized_count",
                   "evec_tune_get", "evec_tune_set"):
@@ -370,11 +372,12 @@ def count_generalized(S, T, select=None) -> int:
 
 
 def generalized(S, T, Z=None, select=None, tile: int = 0, check: bool = False,
-                mode: str = "fp64", slices: int = 0):
+                mode: str = "fp64", slices: int = 0, left: bool = False):
     """Generalized eigenvectors of the pencil (S, T) (optionally X = Z Y).
 
     Returns (X, scale_exp, alpha_re, alpha_im, beta) as CUDA tensors; X is
-    (n, m) column-major; column j is the eigenvector of alpha_j / beta_j."""
+    (n, m) column-major; column j is the eigenvector of alpha_j / beta_j.
+    left: the left eigenvectors u^H (beta S - alpha T) = 0 (evec_generalized_left)."""
     import torch
     n = S.shape[0]
     lds = _check_colmajor(S, "S", n)
@@ -393,14 +396,22 @@ def generalized(S, T, Z=None, select=None, tile: int = 0, check: bool = False,
         return X, e, ar, ai, be
     ldx = X.stride(1) if m > 1 else max(n, 1)
     opts = _opts(tile, False, mode, slices)
-    st = lib().evec_generalized(h.ptr, n, S.data_ptr(), lds, T.data_ptr(), ldt,
-                                Z.data_ptr() if Z is not None else None, ldz, _np_ptr(sel),
-                                X.data_ptr(), ldx, e.data_ptr(), ar.data_ptr(), ai.data_ptr(),
-                                be.data_ptr(), ctypes.byref(opts))
-    _check(st, "evec_generalized")
+    name = "evec_generalized_left" if left else "evec_generalized"
+    st = getattr(lib(), name)(h.ptr, n, S.data_ptr(), lds, T.data_ptr(), ldt,
+                              Z.data_ptr() if Z is not None else None, ldz, _np_ptr(sel),
+                              X.data_ptr(), ldx, e.data_ptr(), ar.data_ptr(), ai.data_ptr(),
+                              be.data_ptr(), ctypes.byref(opts))
+    _check(st, name)
     if check:
         h.sync()
     return X, e, ar, ai, be
+
+
+def generalized_left(S, T, Z=None, select=None, tile: int = 0, check: bool = False,
+                     mode: str = "fp64", slices: int = 0):
+    """Left eigenvectors of the pencil (S, T): u^H (beta S - alpha T) = 0
+    (optionally X = Z U); outputs as generalized()."""
+    return generalized(S, T, Z, select, tile, check, mode, slices, left=True)
 
 
 def trsolve(T, B, tile: int = 0, check: bool = False, mode: str = "fp64", slices: int = 0,

@@ -47,13 +47,13 @@ void launch_residual(const double *T, int64_t ldt, const Plan &p, int ntiles, in
 void launch_rhs_init(const Plan &p, const double *R, int64_t ldr, double *seg_nu,
                      cudaStream_t st);
 void launch_flip_transpose(const double *T, int64_t ldt, int64_t n, double *Tf, int64_t ldf,
-                           DevStatus *status, cudaStream_t st);
+                           DevStatus *status, cudaStream_t st, int sub = 1);
 void launch_reverse_cols(const double *Q, int64_t ldq, int64_t n, double *Qr, int64_t ldr,
                          cudaStream_t st);
 void launch_left_output(const double *Xw, int64_t ldw, int64_t n, int64_t m, const int32_t *dst,
                         int reverse, const int32_t *ew, const double *lrw, const double *liw,
                         double *X, int64_t ldx, int32_t *e, double *lr, double *li,
-                        cudaStream_t st);
+                        cudaStream_t st, const double *bw = nullptr, double *bo = nullptr);
 size_t hessenberg_workspace(int64_t n);
 int hess_panel_width();
 void hess_init_q(int64_t n, double *Q, int64_t ldq, cudaStream_t st);
@@ -570,7 +570,9 @@ struct evec_ctx {
     double *hL = nullptr; size_t hL_cap = 0;
     // left eigenvectors: the flipped T' = J T^T J, Q J, the result in T's
     // column order before the final scatter, and that scatter's column map
+    // (pencils: lT holds S', lT2 the flipped triangular factor)
     double *lT = nullptr, *lQ = nullptr, *lX = nullptr; size_t lT_cap = 0, lQ_cap = 0, lX_cap = 0;
+    double *lT2 = nullptr; size_t lT2_cap = 0;
     int32_t *lE = nullptr; size_t lE_cap = 0;
     double *lL = nullptr; size_t lL_cap = 0;
     int32_t *lmap_d = nullptr; size_t lmap_cap = 0;
@@ -971,7 +973,7 @@ evec_status evec_destroy(evec_handle h) {
                    h->slA, h->slB, h->rmax, h->cmax, h->ea, h->eb, h->panels,
                    h->ea_panels, h->boff_d, h->bws, h->bplan_d, h->queue_d, h->tauT,
                    h->blk_tauT, h->pW, h->Rd, h->seg_ey, h->lT, h->lQ, h->lX, h->lE, h->lL,
-                   h->lmap_d, h->hs_ws, h->gate_d, h->win_d};
+                   h->lmap_d, h->hs_ws, h->gate_d, h->win_d, h->lT2};
     for (void *p : dev)
         if (p) cudaFree(p);
     for (auto &t : h->live) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
@@ -2583,6 +2585,82 @@ extern "C" evec_status evec_generalized(evec_handle h, int64_t n, const double *
         EVEC_CUDA(cudaMemcpyAsync(alpha_im, h->plan_h + m * 8, m * 8, cudaMemcpyHostToDevice, st));
     if (beta)
         EVEC_CUDA(cudaMemcpyAsync(beta, h->plan_h + 2 * m * 8, m * 8, cudaMemcpyHostToDevice, st));
+    if (opt && opt->check) return evec_sync(h, nullptr);
+    return EVEC_OK;
+}
+
+// Left eigenvectors of the pencil: evec_generalized on (S', T') = (J S^T J,
+// J T^T J) (the blocks in reverse order; k_left.cu) with Z J, then the
+// scatter of evec_standard_left, carrying beta along.
+extern "C" evec_status evec_generalized_left(evec_handle h, int64_t n, const double *S,
+                                             int64_t lds, const double *T, int64_t ldt,
+                                             const double *Z, int64_t ldz,
+                                             const uint8_t *select_host, double *X, int64_t ldx,
+                                             int32_t *scale_exp, double *alpha_re,
+                                             double *alpha_im, double *beta,
+                                             const evec_opts *opt) {
+    if (!h || n < 0 || !ld_ok(lds, n) || !ld_ok(ldt, n) || !ld_ok(ldx, n) ||
+        (Z && !ld_ok(ldz, n)))
+        return EVEC_EINVAL;
+    const int mode = opt ? opt->mode : EVEC_FP64;
+    if (mode != EVEC_FP64 && mode != EVEC_SPLIT) return EVEC_EINVAL;
+    const int slices = (opt && opt->slices) ? opt->slices : 8;
+    if (slices < 2 || slices > 8) return EVEC_EINVAL;
+    const int nb = (opt && opt->tile) ? opt->tile : 64;
+    if (nb < 16 || nb > kMaxTileBig) return EVEC_EINVAL;
+    if (n == 0) return EVEC_OK;
+    if (!S || !T || !X || !scale_exp) return EVEC_EINVAL;
+    DeviceGuard g(h->device);
+    if (!g.ok) return EVEC_ECUDA;
+    cudaStream_t st = h->stream;
+    const size_t nn = (size_t)n * (size_t)n;
+    EVEC_TRY(grow_device(&h->lT, &h->lT_cap, nn));
+    EVEC_TRY(grow_device(&h->lT2, &h->lT2_cap, nn));
+    if (Z) EVEC_TRY(grow_device(&h->lQ, &h->lQ_cap, nn));
+    timed(h, EVEC_K_LEFT, [&] {
+        launch_flip_transpose(S, lds, n, h->lT, n, h->status_d, st, 1);
+        launch_flip_transpose(T, ldt, n, h->lT2, n, h->status_d, st, 0);
+        if (Z) launch_reverse_cols(Z, ldz, n, h->lQ, n, st);
+        return Z ? 3 : 2;
+    });
+    EVEC_CUDA(cudaGetLastError());
+    const uint8_t *sel = nullptr;
+    if (select_host) {
+        h->lsel.resize((size_t)n);
+        for (int64_t i = 0; i < n; i++) h->lsel[i] = select_host[n - 1 - i];
+        sel = h->lsel.data();
+    }
+    EVEC_TRY(plan_pencil(h, n, h->lT, n, h->lT2, n, sel, nb));
+    const int64_t m = h->plan.m;
+    if (m == 0) return (opt && opt->check) ? evec_sync(h, nullptr) : EVEC_OK;
+    EVEC_TRY(grow_device(&h->lX, &h->lX_cap, (size_t)n * (size_t)m));
+    EVEC_TRY(grow_device(&h->lE, &h->lE_cap, (size_t)m));
+    EVEC_TRY(grow_device(&h->lL, &h->lL_cap, 3 * (size_t)m));
+    EVEC_TRY(grow_device(&h->lmap_d, &h->lmap_cap, (size_t)m));
+    evec_opts o{};
+    if (opt) o = *opt;
+    o.check = 0;
+    EVEC_TRY(evec_generalized(h, n, h->lT, n, h->lT2, n, Z ? h->lQ : nullptr, n, sel, h->lX, n,
+                              h->lE, h->lL, h->lL + m, h->lL + 2 * m, &o));
+    // the column map of evec_standard_left (pairs keep their (Re, Im) order,
+    // ~d marks a negated imaginary column)
+    const HostPlan &HP = h->plan;
+    if ((int64_t)HP.col_lam_im.size() != m) return EVEC_EINVAL;
+    h->lmap_h.resize((size_t)m);
+    for (int64_t c = 0; c < m; c++) {
+        const double wi = HP.col_lam_im[c];
+        if (wi > 0.0) h->lmap_h[c] = (int32_t)(m - 2 - c);
+        else if (wi < 0.0) h->lmap_h[c] = ~(int32_t)(m - c);
+        else h->lmap_h[c] = (int32_t)(m - 1 - c);
+    }
+    EVEC_CUDA(cudaMemcpyAsync(h->lmap_d, h->lmap_h.data(), (size_t)m * sizeof(int32_t),
+                              cudaMemcpyHostToDevice, st));
+    timed(h, EVEC_K_LEFT, [&] {
+        launch_left_output(h->lX, n, n, m, h->lmap_d, Z ? 0 : 1, h->lE, h->lL, h->lL + m, X, ldx,
+                           scale_exp, alpha_re, alpha_im, st, h->lL + 2 * m, beta);
+        return 1;
+    });
+    EVEC_CUDA(cudaGetLastError());
     if (opt && opt->check) return evec_sync(h, nullptr);
     return EVEC_OK;
 }

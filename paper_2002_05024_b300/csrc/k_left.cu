@@ -11,6 +11,12 @@
 // scatter that restores T's column order, reverses the rows (without Q)
 // and negates the imaginary columns (u = conj(J y')).  All three are plain
 // copies: HBM-bound, one read and one write per element.
+//
+// Pencils: the left eigenvectors of (S, T), u^H (beta S - alpha T) = 0, are
+// the reversed conjugated right eigenvectors of (J S^T J, J T^T J), again an
+// upper quasi-triangular S' over an upper triangular T' with the same
+// blocks in reverse order (a diagonal 2x2 block of T stays diagonal), so
+// the same three copies serve there, with T' flipped without a subdiagonal.
 #include <algorithm>
 
 #include "evec_internal.cuh"
@@ -19,9 +25,10 @@ namespace evec {
 
 constexpr int kFlipTile = 32;
 
-// T'(i, j) = T(n-1-j, n-1-i) for j >= i - 1 (the part the solver reads:
-// upper triangle and first subdiagonal, T's own referenced part mirrored),
-// zero below.  One 32 x 32 tile of T' per CTA (32 x 8 threads) through
+// T'(i, j) = T(n-1-j, n-1-i) for j >= i - sub (sub = 1: the part the
+// solver reads, upper triangle and first subdiagonal, T's own referenced
+// part mirrored; sub = 0: the upper triangle of a pencil's triangular
+// factor), zero below.  One 32 x 32 tile of T' per CTA (32 x 8 threads) through
 // shared memory, so that both the reads of T (along its columns) and the
 // writes of T' are coalesced.  Entries of T strictly above its first
 // superdiagonal are validated here (finite, <= 2^1000) and reported in T's
@@ -29,13 +36,13 @@ constexpr int kFlipTile = 32;
 // central diagonals are validated by the planner.
 __global__ void __launch_bounds__(256)
     k_flip_transpose(const double *__restrict__ T, int64_t ldt, int64_t n,
-                     double *__restrict__ Tf, int64_t ldf, DevStatus *status) {
+                     double *__restrict__ Tf, int64_t ldf, int sub, DevStatus *status) {
     __shared__ double tile[kFlipTile][kFlipTile + 1];
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int64_t i0 = (int64_t)blockIdx.y * kFlipTile;   // rows of T'
     const int64_t j0 = (int64_t)blockIdx.x * kFlipTile;   // columns of T'
     // whole tile strictly below the first subdiagonal of T': zeros
-    const bool below = j0 + kFlipTile - 1 < i0 - 1;
+    const bool below = j0 + kFlipTile - 1 < i0 - sub;
     if (!below) {
         // load: lane tx reads T row r = n-1-(j0+31-tx) (consecutive r along
         // the lanes), column c = n-1-(i0+il)
@@ -43,7 +50,7 @@ __global__ void __launch_bounds__(256)
         for (int il = ty; il < kFlipTile; il += 8) {
             const int64_t ip = i0 + il;
             double v = 0.0;
-            if (ip < n && jp < n && jp >= ip - 1) {
+            if (ip < n && jp < n && jp >= ip - sub) {
                 const int64_t r = n - 1 - jp, c = n - 1 - ip;
                 v = T[r + c * ldt];
                 if (c >= r + 2) {
@@ -81,13 +88,14 @@ __global__ void __launch_bounds__(256)
 // X(:, d) = +-Xw(rows, c') for the source column c' = c0 + blockIdx.y,
 // d = dst[c'] (or ~dst[c'] for a negated, imaginary column); rows reversed
 // when `reverse` (no back-transformation), with the exponent and
-// eigenvalue of the column carried along.
+// eigenvalue (and a pencil's beta) of the column carried along.
 __global__ void __launch_bounds__(256)
     k_left_output(const double *__restrict__ Xw, int64_t ldw, int64_t n, int64_t c0,
                   const int32_t *__restrict__ dst, int reverse, const int32_t *__restrict__ ew,
                   const double *__restrict__ lrw, const double *__restrict__ liw,
                   double *__restrict__ X, int64_t ldx, int32_t *__restrict__ e,
-                  double *__restrict__ lr, double *__restrict__ li) {
+                  double *__restrict__ lr, double *__restrict__ li,
+                  const double *__restrict__ bw, double *__restrict__ bo) {
     const int64_t c = c0 + blockIdx.y;
     const int32_t code = dst[c];
     const bool neg = code < 0;
@@ -103,15 +111,16 @@ __global__ void __launch_bounds__(256)
         e[d] = ew[c];
         if (lr) lr[d] = lrw[c];
         if (li) li[d] = liw[c];
+        if (bo) bo[d] = bw[c];
     }
 }
 
 void launch_flip_transpose(const double *T, int64_t ldt, int64_t n, double *Tf, int64_t ldf,
-                           DevStatus *status, cudaStream_t st) {
+                           DevStatus *status, cudaStream_t st, int sub) {
     if (n <= 0) return;
     const int64_t nt = (n + kFlipTile - 1) / kFlipTile;   // <= 65535 for n < 2^21
     k_flip_transpose<<<dim3((unsigned)nt, (unsigned)nt), dim3(kFlipTile, 8), 0, st>>>(
-        T, ldt, n, Tf, ldf, status);
+        T, ldt, n, Tf, ldf, sub, status);
 }
 
 void launch_reverse_cols(const double *Q, int64_t ldq, int64_t n, double *Qr, int64_t ldr,
@@ -127,13 +136,13 @@ void launch_reverse_cols(const double *Q, int64_t ldq, int64_t n, double *Qr, in
 void launch_left_output(const double *Xw, int64_t ldw, int64_t n, int64_t m, const int32_t *dst,
                         int reverse, const int32_t *ew, const double *lrw, const double *liw,
                         double *X, int64_t ldx, int32_t *e, double *lr, double *li,
-                        cudaStream_t st) {
+                        cudaStream_t st, const double *bw, double *bo) {
     if (n <= 0 || m <= 0) return;
     const unsigned gx = (unsigned)std::min<int64_t>((n + 255) / 256, 16);
     for (int64_t c0 = 0; c0 < m; c0 += 65535) {
         const unsigned gy = (unsigned)std::min<int64_t>(m - c0, 65535);
         k_left_output<<<dim3(gx, gy), 256, 0, st>>>(Xw, ldw, n, c0, dst, reverse, ew, lrw, liw,
-                                                    X, ldx, e, lr, li);
+                                                    X, ldx, e, lr, li, bw, bo);
     }
 }
 
