@@ -87,6 +87,8 @@ __device__ void diag_tile_big(int s, int list_pos0, const double *__restrict__ T
     double *stauB = btauB + (GEN ? ts : 0);            // [kMaxSubs]
     double *utau = stauB + (GEN ? kMaxSubs : 0);       // [kUnits][kSub]
 
+    // the block norms and segments come from earlier kernels of the stream
+    grid_dependency_wait();
     for (int k = tid; k < nbt; k += kThreads) {
         bq[k] = P.blk_start[kb0 + k] - t0;
         bsz[k] = P.blk_size[kb0 + k];

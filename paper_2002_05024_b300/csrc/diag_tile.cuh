@@ -316,9 +316,6 @@ __device__ void diag_tile(int s, int list_pos0, const double *__restrict__ T, in
     for (int k = tid; k < nbt; k += kThreads) {
         bq[k] = P.blk_start[kb0 + k] - t0;
         bsz[k] = P.blk_size[kb0 + k];
-        btau[k] = blk_tau[kb0 + k];
-        btf[k] = efield(blk_tau[kb0 + k]);
-        if constexpr (GEN) btauB[k] = pen.blk_tau[kb0 + k];
     }
     if (tid < kUnits) {
         const int pos = list_pos0 + tid;
@@ -338,23 +335,10 @@ __device__ void diag_tile(int s, int list_pos0, const double *__restrict__ T, in
         for (int k = 0; k < nbt; k++) if (bsz[k] == 1) ford[f++] = k;
         for (int k = 0; k < nbt; k++) if (bsz[k] == 2) ford[f++] = k;
     }
-    // the segments, column by column (coalesced), in flight while the block
-    // factors are computed; own units start at zero
-    for (int idx = tid; idx < kUnits * ts; idx += kThreads) {
-        const int uu = idx / ts, i = idx % ts;
-        const int c = ucol[uu];
-        if (c >= 0 && (RHS || !uown[uu])) {
-            cp_async8(&yr[i * ys + uu], &Y[(t0 + i) + (int64_t)c * ldy]);
-            if (C) cp_async8(&yi[i * ys + uu], &Y[(t0 + i) + (int64_t)(c + 1) * ldy]);
-        } else {
-            yr[i * ys + uu] = 0.0;
-            if (C) yi[i * ys + uu] = 0.0;
-        }
-    }
-    asm volatile("cp.async.commit_group;");
-    // the tile (the older group), then the block factors below (they need
-    // only T and the shifts)
-    asm volatile("cp.async.wait_group 1;" ::: "memory");
+    // the tile, then the block factors below (they need only T and the
+    // shifts: with a programmatic launch this part overlaps the previous
+    // kernel of the stream)
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();
 
     // ---- one unit per G lanes --------------------------------------------
@@ -385,8 +369,6 @@ __device__ void diag_tile(int s, int list_pos0, const double *__restrict__ T, in
             Fac F;
             if constexpr (GEN) {
                 F = factor_pencil<C>(bsz[kk], Ts, Bt, ts, bq[kk], lr, li, be, smin);
-                // bound of the in-tile update from block kk for this unit
-                myutau[kk] = fabs(be) * btau[kk] + (fabs(lr) + fabs(li)) * btauB[kk];
             } else {
                 F = factor<C>(bsz[kk], Ts, ts, bq[kk], lr, li, smin);
             }
@@ -401,6 +383,36 @@ __device__ void diag_tile(int s, int list_pos0, const double *__restrict__ T, in
         }
     }
 
+    // everything below reads what earlier kernels of the stream wrote (the
+    // block norms, the segments and their exponents)
+    grid_dependency_wait();
+    for (int k = tid; k < nbt; k += kThreads) {
+        btau[k] = blk_tau[kb0 + k];
+        btf[k] = efield(blk_tau[kb0 + k]);
+        if constexpr (GEN) btauB[k] = pen.blk_tau[kb0 + k];
+    }
+    // the segments, column by column (coalesced); own units start at zero
+    for (int idx = tid; idx < kUnits * ts; idx += kThreads) {
+        const int uu = idx / ts, i = idx % ts;
+        const int c = ucol[uu];
+        if (c >= 0 && (RHS || !uown[uu])) {
+            cp_async8(&yr[i * ys + uu], &Y[(t0 + i) + (int64_t)c * ldy]);
+            if (C) cp_async8(&yi[i * ys + uu], &Y[(t0 + i) + (int64_t)(c + 1) * ldy]);
+        } else {
+            yr[i * ys + uu] = 0.0;
+            if (C) yi[i * ys + uu] = 0.0;
+        }
+    }
+    asm volatile("cp.async.commit_group;");
+    if constexpr (GEN) {   // bound of the in-tile update from each block, this unit
+        __syncthreads();
+        if (valid)
+            for (int f = g; f < nbt; f += G) {
+                const int kk = ford[f];
+                if (own && kb0 + kk >= kown) continue;
+                myutau[kk] = fabs(be) * btau[kk] + (fabs(lr) + fabs(li)) * btauB[kk];
+            }
+    }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();
 

@@ -45,6 +45,25 @@
 
 namespace evec {
 
+// A programmatic launch (see grid_dependency_wait): the launch of the
+// solve overlaps the end of the update kernel before it in the stream, and
+// its prologue (the diagonal tile, the unit map and the block factors)
+// reads only the input matrix and the plan.
+template <typename... KArgs, typename... Args>
+static void launch_programmatic(void (*kernel)(KArgs...), unsigned grid, unsigned block,
+                                size_t smem, cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, args...);
+}
 
 template <int W, bool GEN, bool RHS, int GR>
 __global__ void __launch_bounds__(32 * W)
@@ -110,9 +129,9 @@ static int launch_big(int s, int ts, int nr, int nc, const double *T, int64_t ld
         *sms = (rct + cct + per - 1) / per;
         return 0;
     }
-    k_diag_solve_big<W, GEN, RHS, GR><<<rct + cct, 32 * W, smem, st>>>(
-        s, rct, T, ldt, p, tau, blk_tau, Y, ldy, seg_e, seg_nu, seg_dx, seg_dy, pen,
-        decide ? 1 : 0);
+    launch_programmatic(k_diag_solve_big<W, GEN, RHS, GR>, (unsigned)(rct + cct), 32 * W, smem,
+                        st, s, rct, T, ldt, p, tau, blk_tau, Y, ldy, seg_e, seg_nu, seg_dx,
+                        seg_dy, pen, decide ? 1 : 0);
     return 1;
 }
 
@@ -198,9 +217,9 @@ static int launch_w(int s, int ts, int nr, int nc, const double *T, int64_t ldt,
         *sms = (rct + cct + per - 1) / per;
         return 0;
     }
-    k_diag_solve<W, GEN, RHS, GR><<<rct + cct, 32 * W, smem, st>>>(
-        s, rct, T, ldt, p, tau, blk_tau, Y, ldy, seg_e, seg_nu, seg_dx, seg_dy, pen,
-        decide ? 1 : 0);
+    launch_programmatic(k_diag_solve<W, GEN, RHS, GR>, (unsigned)(rct + cct), 32 * W, smem, st,
+                        s, rct, T, ldt, p, tau, blk_tau, Y, ldy, seg_e, seg_nu, seg_dx, seg_dy,
+                        pen, decide ? 1 : 0);
     return 1;
 }
 
