@@ -65,7 +65,9 @@ static void launch_programmatic(void (*kernel)(KArgs...), unsigned grid, unsigne
     cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
-template <int W, bool GEN, bool RHS, int GR>
+// GR: lanes per real unit; GRC: the lane parameter of the complex units
+// (Lanes<true, GRC>: 16 lanes per pair for GRC = 8, a whole warp for 16)
+template <int W, bool GEN, bool RHS, int GR, int GRC = GR>
 __global__ void __launch_bounds__(32 * W)
     k_diag_solve(int s, int nreal_ctas, const double *__restrict__ T, int64_t ldt, Plan P,
                  const double *__restrict__ tau, const double *__restrict__ blk_tau,
@@ -78,8 +80,8 @@ __global__ void __launch_bounds__(32 * W)
                                           T, ldt, P, tau, blk_tau, Y, ldy, seg_e, seg_nu, seg_dx,
                                           seg_dy, smem, pen, decide != 0);
     else
-        diag_tile<W, true, GEN, RHS, GR>(
-            s, P.tile_cplx[s] + (blockIdx.x - nreal_ctas) * (Lanes<true, GR>::U * W), T, ldt, P,
+        diag_tile<W, true, GEN, RHS, GRC>(
+            s, P.tile_cplx[s] + (blockIdx.x - nreal_ctas) * (Lanes<true, GRC>::U * W), T, ldt, P,
             tau, blk_tau, Y, ldy, seg_e, seg_nu, seg_dx, seg_dy, smem, pen, decide != 0);
 }
 
@@ -188,38 +190,53 @@ void launch_decide(int s, const Plan &p, int64_t c0, const double *tau, int32_t 
         k_decide<false><<<grid, 256, 0, st>>>(s, p, tau, seg_e, seg_nu, seg_dx, seg_dy, c0);
 }
 
-template <int W, bool GEN, bool RHS, int GR = 8>
+// dynamic shared memory of k_diag_solve<W, GEN, *, GR, GRC> for t rows
+template <int W, bool GEN, int GR, int GRC>
+static size_t diag_smem_mixed(int t) {
+    return std::max(diag_smem_bytes<W, false, GEN, GR>(t), diag_smem_bytes<W, true, GEN, GRC>(t));
+}
+
+// CTAs of k_diag_solve<W, GEN, RHS, GR, GRC> resident on one SM for t rows
+template <int W, bool GEN, bool RHS, int GR, int GRC>
+static int diag_ctas_per_sm(int t) {
+    int per = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_diag_solve<W, GEN, RHS, GR, GRC>,
+                                                      32 * W,
+                                                      diag_smem_mixed<W, GEN, GR, GRC>(t)) !=
+            cudaSuccess ||
+        per < 1) {
+        cudaGetLastError();
+        per = 1;
+    }
+    return per;
+}
+
+template <int W, bool GEN, bool RHS, int GR = 8, int GRC = GR>
 static int launch_w(int s, int ts, int nr, int nc, const double *T, int64_t ldt, const Plan &p,
                     const double *tau, const double *blk_tau, double *Y, int64_t ldy,
                     int32_t *seg_e, double *seg_nu, int32_t *seg_dx, int32_t *seg_dy,
                     const Pencil &pen, cudaStream_t st, bool decide, int *sms) {
-    constexpr int ur = Lanes<false, GR>::U * W, uc = Lanes<true, GR>::U * W;
+    constexpr int ur = Lanes<false, GR>::U * W, uc = Lanes<true, GRC>::U * W;
     const int rct = (nr + ur - 1) / ur;
     const int cct = (nc + uc - 1) / uc;
     if (rct + cct == 0) return 0;
-    cudaFuncSetAttribute(k_diag_solve<W, GEN, RHS, GR>,
+    cudaFuncSetAttribute(k_diag_solve<W, GEN, RHS, GR, GRC>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)diag_smem<W, GEN, GR>(W == 4 ? 64 : kMaxTile));
-    // two CTAs per SM at 8 lanes per unit (about 82 KB each for 64-row
+                         (int)diag_smem_mixed<W, GEN, GR, GRC>(W == 4 ? 64 : kMaxTile));
+    // two CTAs per SM at 8 lanes per real unit (about 82 KB each for 64-row
     // tiles; pencils: one), more with more lanes per unit
-    cudaFuncSetAttribute(k_diag_solve<W, GEN, RHS, GR>,
+    cudaFuncSetAttribute(k_diag_solve<W, GEN, RHS, GR, GRC>,
                          cudaFuncAttributePreferredSharedMemoryCarveout,
                          cudaSharedmemCarveoutMaxShared);
-    const size_t smem = diag_smem<W, GEN, GR>(ts);
+    const size_t smem = diag_smem_mixed<W, GEN, GR, GRC>(ts);
     if (sms) {   // SMs the launch occupies in one wave (planning only: no launch)
-        int per = 1;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_diag_solve<W, GEN, RHS, GR>,
-                                                          32 * W, smem) != cudaSuccess ||
-            per < 1) {
-            cudaGetLastError();
-            per = 1;
-        }
+        const int per = diag_ctas_per_sm<W, GEN, RHS, GR, GRC>(ts);
         *sms = (rct + cct + per - 1) / per;
         return 0;
     }
-    launch_programmatic(k_diag_solve<W, GEN, RHS, GR>, (unsigned)(rct + cct), 32 * W, smem, st,
-                        s, rct, T, ldt, p, tau, blk_tau, Y, ldy, seg_e, seg_nu, seg_dx, seg_dy,
-                        pen, decide ? 1 : 0);
+    launch_programmatic(k_diag_solve<W, GEN, RHS, GR, GRC>, (unsigned)(rct + cct), 32 * W, smem,
+                        st, s, rct, T, ldt, p, tau, blk_tau, Y, ldy, seg_e, seg_nu, seg_dx,
+                        seg_dy, pen, decide ? 1 : 0);
     return 1;
 }
 
@@ -230,7 +247,7 @@ static int launch_w(int s, int ts, int nr, int nc, const double *T, int64_t ldt,
 // spare; with many units the FP64 issue slots fill up and the solve work
 // that every lane of a unit repeats makes wide units the slower choice.
 // Largest GR with about 2.5 warps per SM sub-partition at most.
-static int pick_lanes(int nr, int nc) {
+static int sm_count() {
     static int nsm = 0;
     if (nsm == 0) {
         int dev = 0, v = 0;
@@ -240,6 +257,11 @@ static int pick_lanes(int nr, int nc) {
         else
             nsm = 148;
     }
+    return nsm;
+}
+
+static int pick_lanes(int nr, int nc) {
+    const int nsm = sm_count();
     const double cap = 2.5 * 4.0 * nsm;
     for (int gr : {32, 16}) {
         const double warps = nr * gr / 32.0 + nc * std::min(2 * gr, 32) / 32.0;
@@ -282,17 +304,36 @@ int launch_diag_solve(int s, const double *T, int64_t ldt, const Plan &p,
         EVEC_BIG_LAUNCH(false, 8);
 #undef EVEC_BIG_LAUNCH
     }
-#define EVEC_DIAG_LAUNCH(R, G_)                                                                  \
-    return launch_w<4, false, R, G_>(s, ts, nr, nc, T, ldt, p, tau, blk_tau, Y, ldy, seg_e,       \
-                                     seg_nu, seg_dx, seg_dy, Pencil(), st, decide, sms)
-    if (rhs) {
-        if (gr == 32) EVEC_DIAG_LAUNCH(true, 32);
-        if (gr == 16) EVEC_DIAG_LAUNCH(true, 16);
-        EVEC_DIAG_LAUNCH(true, 8);
+#define EVEC_DIAG_LAUNCH(R, G_, GC_)                                                             \
+    return launch_w<4, false, R, G_, GC_>(s, ts, nr, nc, T, ldt, p, tau, blk_tau, Y, ldy, seg_e,  \
+                                          seg_nu, seg_dx, seg_dy, Pencil(), st, decide, sms)
+    // With complex pairs in the step, a pair's chain (complex arithmetic,
+    // twice the FP64 instructions of a real column per block step) is the
+    // longest one of the launch, and the real units are given 8 lanes: their
+    // chain stays shorter, and their warps leave the sub-partitions' FP64
+    // issue slots to the pairs.  The pairs take a whole warp each when the
+    // launch still fits in one wave of resident CTAs, else 16 lanes.
+    if (nc > 0) {
+        const int nsm = sm_count();
+        const int wide = (nr + 15) / 16 + (nc + 3) / 4;   // CTAs with a warp per pair
+        const bool fits =
+            wide <= nsm * (rhs ? diag_ctas_per_sm<4, false, true, 8, 16>(ts)
+                               : diag_ctas_per_sm<4, false, false, 8, 16>(ts));
+        if (rhs) {
+            if (fits) EVEC_DIAG_LAUNCH(true, 8, 16);
+            EVEC_DIAG_LAUNCH(true, 8, 8);
+        }
+        if (fits) EVEC_DIAG_LAUNCH(false, 8, 16);
+        EVEC_DIAG_LAUNCH(false, 8, 8);
     }
-    if (gr == 32) EVEC_DIAG_LAUNCH(false, 32);
-    if (gr == 16) EVEC_DIAG_LAUNCH(false, 16);
-    EVEC_DIAG_LAUNCH(false, 8);
+    if (rhs) {
+        if (gr == 32) EVEC_DIAG_LAUNCH(true, 32, 32);
+        if (gr == 16) EVEC_DIAG_LAUNCH(true, 16, 16);
+        EVEC_DIAG_LAUNCH(true, 8, 8);
+    }
+    if (gr == 32) EVEC_DIAG_LAUNCH(false, 32, 32);
+    if (gr == 16) EVEC_DIAG_LAUNCH(false, 16, 16);
+    EVEC_DIAG_LAUNCH(false, 8, 8);
 #undef EVEC_DIAG_LAUNCH
 }
 
