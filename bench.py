@@ -165,6 +165,7 @@ KERNEL_SOURCES = {
     ("hess_panel", "fp64"): ["k_hessenberg.cu"],
     ("hess_update", "fp64"): ["k_hessenberg.cu"],
     ("window", "fp64"): ["k_window.cu"],
+    ("window", "split"): ["k_split.cu", "k_window.cu", "split_common.cuh"],
 }
 TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
 
@@ -587,7 +588,9 @@ def run_reference_other(args):
                 units += per
                 secs += dt
         unit = "windows/s"
-        metric = "reordering windows/s (off-diagonal updates with Q, FP64)"
+        metric = ("reordering windows/s (off-diagonal updates with Q, " +
+                  (f"split precision, {args.slices or 8} slices)" if args.mode == "split"
+                   else "FP64)"))
         what = window_what(n, k, len(wins))
         sample = f"{per} random windows of the chain per step, plain loops on one core"
         cores = 1
@@ -1572,7 +1575,9 @@ def run_window(args, rank, world, local_rank):
     dQ = torch.from_numpy(np.asfortranarray(Q)).to(dev)
     begin, size, zoff, Zp = ev.pack_windows(wins, dev)
     h = ev.handle(local_rank)
-    opts = ev._opts(0, False, "fp64", 0)
+    split = args.mode == "split"
+    slices = args.slices or 8
+    opts = ev._opts(0, False, args.mode, slices)
 
     def step():
         # each pass is one more orthogonal similarity of the same matrices
@@ -1648,7 +1653,21 @@ def run_window(args, rank, world, local_rank):
     fp64_peak = N_SMS * FP64_FLOP_PER_CLK_PER_SM * float(peaks.get("sm_max_mhz", 2032.0)) / 1e6
     roof = None
     wm, wn = prof.get("window", (0.0, 0))
-    if wm > 0:
+    if wm > 0 and split:
+        # BF16 slice products: S (S + 1) / 2 digit pairs per FP64 product
+        Fs = F * slices * (slices + 1) / 2
+        ach = Fs / (wm / args.steps / 1e3) / 1e12
+        bf16 = float(peaks.get("bf16_tflops_sustained") or 1400.0)
+        roof = {"kernel": "the split products of every window (k_split_gemm with its slicing "
+                          "kernels)",
+                "bound": "tensor",
+                "achieved": ach, "peak": bf16, "unit": "TFLOP/s", "frac": ach / bf16,
+                "traffic": stored_traffic("window", "split", n, k, "window:"),
+                "peak_source": "of measured sustained BF16 (MEASURED_PEAKS.json)",
+                "launches_per_step": wn / args.steps, "alg_flops_per_step": Fs,
+                "fp64_equivalent_tflops": F / (wm / args.steps / 1e3) / 1e12,
+                "ms_per_step": wm / args.steps}
+    elif wm > 0:
         ach = F / (wm / args.steps / 1e3) / 1e12
         roof = {"kernel": "left and right updates of the set (k_win_left_set, k_win_right_set)",
                 "bound": "alu",
@@ -1668,18 +1687,20 @@ def run_window(args, rank, world, local_rank):
         dt = time.perf_counter() - t
         dT.copy_(torch.from_numpy(np.asfortranarray(T)))
         dQ.copy_(torch.from_numpy(np.asfortranarray(Q)))
-        ev.window_update(dT, dQ, pick, check=True, disjoint=True)
+        ev.window_update(dT, dQ, pick, check=True, disjoint=True, mode=args.mode, slices=slices)
         quality["gpu_vs_oracle_two_windows"] = float(
             max(np.abs(dT.cpu().numpy() - To).max(), np.abs(dQ.cpu().numpy() - Qo).max()))
         cpu = {"value": len(pick) / dt, "unit": "windows/s", "cores": 1, "kind": "oracle",
                "sample": f"{len(pick)} windows of the pass (the first and the middle one), "
                          f"plain loops on one core, {dt:.2f} s"}
     line = {
-        "metric": "reordering windows/s (off-diagonal updates with Q, FP64)",
+        "metric": "reordering windows/s (off-diagonal updates with Q, "
+                  + (f"split precision, {slices} slices)" if split else "FP64)"),
         "value": world * len(wins) * args.steps / (elapsed / 1e3), "unit": "windows/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": elapsed / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "bf16 slice products + f64" if split else "f64",
+        "data": "synthetic",
         "config": {"workload": window_what(n, k, len(wins)), "n": n, "window": k,
                    "windows_per_step": len(wins), "parallelism": "replicas",
                    "l2": f"inputs larger than L2 (T and Q {8 * n * n >> 20} MiB each)"},

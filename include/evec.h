@@ -222,9 +222,19 @@ evec_status evec_hessenberg(evec_handle h, int64_t n, double *A, int64_t lda, do
  *   T [ldt x n], Q [ldq x n], Z: device pointers on the handle's device;
  *     Z holds sum_w size_host[w]^2 doubles at the given offsets.
  *   begin_host, size_host, zoff_host [nwin]: host arrays.
- *   FP64 throughout; opt: only check (synchronise) is read.
+ *   opt->mode: EVEC_FP64 (default): FP64 products, the Q updates on a
+ *     second stream of the handle beside the T updates.  EVEC_SPLIT: the
+ *     three products of each window through the split-precision GEMM of
+ *     the back-transformation (opt->slices BF16 digit slices of 7 bits per
+ *     operand, row and column power-of-two scales, FP64 results: each
+ *     entry within about k 2^-(7 slices) max|row of the left operand|
+ *     max|column of the right operand| of the exact product), one window
+ *     after another on the handle's stream, for n <= 65472; the handle
+ *     keeps the slice buffers (about 2 slices n pad(k) BF16 values).
+ *   opt->check: synchronise and return the device status.
  * Errors: EVEC_EINVAL (n < 0, a bad leading dimension, a window outside
- * [0, n), a size above 256, a negative offset).  Entries are not checked.
+ * [0, n), a size above 256, a negative offset, a bad mode or slice count,
+ * n > 65472 in EVEC_SPLIT mode).  Entries are not checked.
  */
 evec_status evec_window_update(evec_handle h, int64_t n, double *T, int64_t ldt, double *Q,
                                int64_t ldq, int nwin, const int64_t *begin_host,
@@ -239,7 +249,8 @@ evec_status evec_window_update(evec_handle h, int64_t n, double *T, int64_t ldt,
  * then all right updates, with all Q updates beside them.  The result
  * equals evec_window_update on the same windows in any order, up to
  * rounding.  Arguments and errors as evec_window_update; also EVEC_EINVAL
- * when two windows of nonzero size overlap.
+ * when two windows of nonzero size overlap.  In EVEC_SPLIT mode the
+ * windows are applied one after another in the order of their first rows.
  */
 evec_status evec_window_update_set(evec_handle h, int64_t n, double *T, int64_t ldt, double *Q,
                                    int64_t ldq, int nwin, const int64_t *begin_host,

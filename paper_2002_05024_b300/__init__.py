@@ -465,19 +465,22 @@ def pack_windows(windows, device):
     return begin, size, zoff, Zp
 
 
-def window_update(T, Q, windows, check: bool = False, packed=None, disjoint: bool = False):
+def window_update(T, Q, windows, check: bool = False, packed=None, disjoint: bool = False,
+                  mode: str = "fp64", slices: int = 0):
     """Eigenvalue reordering's off-diagonal updates, in place: for each
     (begin, Z) in windows, in order, T[a:b, a:] <- Z^T T[a:b, a:],
     T[:b, a:b] <- T[:b, a:b] Z and Q[:, a:b] <- Q[:, a:b] Z (T, Q float64
     CUDA, column-major; Q may be None).  disjoint: the windows are pairwise
     disjoint and are applied as one concurrent set (evec_window_update_set).
-    packed: the result of pack_windows, to skip packing.  Returns (T, Q)."""
+    packed: the result of pack_windows, to skip packing.  mode "split": the
+    products in split precision (BF16 digit slices, FP64 results).  Returns
+    (T, Q)."""
     n = T.shape[0]
     ldt = _check_colmajor(T, "T", n)
     ldq = _check_colmajor(Q, "Q", n) if Q is not None else 1
     begin, size, zoff, Zp = packed if packed is not None else pack_windows(windows, T.device)
     h = handle(T.device.index)
-    opts = _opts(0, False, "fp64", 0)
+    opts = _opts(0, False, mode, slices)
     fn = lib().evec_window_update_set if disjoint else lib().evec_window_update
     st = fn(h.ptr, n, T.data_ptr(), ldt, Q.data_ptr() if Q is not None else None, ldq, len(begin),
             _np_ptr(begin), _np_ptr(size), Zp.data_ptr(), _np_ptr(zoff), ctypes.byref(opts))

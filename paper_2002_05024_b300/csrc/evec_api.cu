@@ -63,6 +63,7 @@ int hess_update(int64_t n, double *A, int64_t lda, double *Q, int64_t ldq, int64
                 double *ws, cudaStream_t st, cudaStream_t qst, cudaEvent_t fork,
                 cudaEvent_t join);
 int window_max();
+void launch_transpose_acc(const double *Z, int k, double *Zt, cudaStream_t st);
 int window_update_t(int64_t n, double *T, int64_t ldt, int64_t a, int k, const double *Z,
                     cudaStream_t st);
 int window_update_q(int64_t n, double *Q, int64_t ldq, int64_t a, int k, const double *Z,
@@ -578,6 +579,7 @@ struct evec_ctx {
     int32_t *lmap_d = nullptr; size_t lmap_cap = 0;
     double *hs_ws = nullptr; size_t hs_ws_cap = 0;   // Hessenberg reduction
     WinDesc *win_d = nullptr; size_t win_cap = 0;    // reordering window tables
+    double *wZt = nullptr; size_t wZt_cap = 0;       // Z^T of a split left update
     // residual gate of the split solve (opts.refine >= 2): ||T||_1 and the
     // failure count on the device; the last top-level call's statistics
     unsigned long long *gate_d = nullptr;
@@ -973,7 +975,7 @@ evec_status evec_destroy(evec_handle h) {
                    h->slA, h->slB, h->rmax, h->cmax, h->ea, h->eb, h->panels,
                    h->ea_panels, h->boff_d, h->bws, h->bplan_d, h->queue_d, h->tauT,
                    h->blk_tauT, h->pW, h->Rd, h->seg_ey, h->lT, h->lQ, h->lX, h->lE, h->lL,
-                   h->lmap_d, h->hs_ws, h->gate_d, h->win_d, h->lT2};
+                   h->lmap_d, h->hs_ws, h->gate_d, h->win_d, h->lT2, h->wZt};
     for (void *p : dev)
         if (p) cudaFree(p);
     for (auto &t : h->live) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
@@ -2665,6 +2667,62 @@ extern "C" evec_status evec_generalized_left(evec_handle h, int64_t n, const dou
     return EVEC_OK;
 }
 
+// columns of a split product: split_pad_n(N) <= 65535, the grid rows of
+// the column-slicing kernel
+constexpr int64_t kSplitMaxN = 65472;
+
+// EVEC_SPLIT window updates: each window's left, right and Q products
+// through the split GEMM (row and column slices of the operands first, so
+// the products may overwrite their own inputs), in the order of `ws` on the
+// handle's stream.  Returns the kernels launched through *ng.
+static evec_status window_split(evec_handle h, int64_t n, double *T, int64_t ldt, double *Q,
+                                int64_t ldq, const std::vector<int> &ws,
+                                const int64_t *begin_host, const int32_t *size_host,
+                                const double *Z, const int64_t *zoff_host, int slices, int *ng) {
+    int kmax = 0;
+    for (int w : ws) kmax = std::max(kmax, (int)size_host[w]);
+    if (kmax == 0) return EVEC_OK;
+    if (n > kSplitMaxN) return EVEC_EINVAL;
+    const int Mp = split_pad_m((int)n), Np = split_pad_n((int)n), Kp = split_pad_k(kmax);
+    EVEC_TRY(grow_device(&h->slA, &h->slA_cap, (size_t)slices * Mp * Kp));
+    EVEC_TRY(grow_device(&h->slB, &h->slB_cap, (size_t)slices * Np * Kp));
+    EVEC_TRY(grow_device(&h->rmax, &h->rmax_cap, (size_t)Mp));
+    EVEC_TRY(grow_device(&h->ea, &h->ea_cap, (size_t)Mp));
+    EVEC_TRY(grow_device(&h->cmax, &h->cmax_cap, (size_t)Np));
+    EVEC_TRY(grow_device(&h->eb, &h->eb_cap, (size_t)Np));
+    EVEC_TRY(grow_device(&h->wZt, &h->wZt_cap, (size_t)kmax * kmax));
+    cudaStream_t st = h->stream;
+    int *err = &h->status_d->timeout;
+    cudaError_t ce = cudaSuccess;
+    for (int w : ws) {
+        const int64_t a = begin_host[w];
+        const int k = size_host[w];
+        if (k == 0) continue;
+        const double *Zw = Z + zoff_host[w];
+        // left: T[a:a+k, a:n] <- Z^T T[a:a+k, a:n]
+        launch_transpose_acc(Zw, k, h->wZt, st);
+        double *Tl = T + a + a * ldt;
+        ce = launch_split_gemm(h->wZt, k, Tl, ldt, k, (int)(n - a), k, slices, nullptr, Tl, ldt,
+                               h->slA, h->slB, h->rmax, h->cmax, h->ea, h->eb, err, st);
+        if (ce != cudaSuccess) break;
+        // right: T[0:a+k, a:a+k] <- T[0:a+k, a:a+k] Z
+        double *Tr = T + a * ldt;
+        ce = launch_split_gemm(Tr, ldt, Zw, k, (int)(a + k), k, k, slices, nullptr, Tr, ldt,
+                               h->slA, h->slB, h->rmax, h->cmax, h->ea, h->eb, err, st);
+        if (ce != cudaSuccess) break;
+        *ng += 11;
+        if (Q) {   // Q[:, a:a+k] <- Q[:, a:a+k] Z
+            double *Qw = Q + a * ldq;
+            ce = launch_split_gemm(Qw, ldq, Zw, k, (int)n, k, k, slices, nullptr, Qw, ldq, h->slA,
+                                   h->slB, h->rmax, h->cmax, h->ea, h->eb, err, st);
+            if (ce != cudaSuccess) break;
+            *ng += 5;
+        }
+    }
+    EVEC_CUDA(ce);
+    return EVEC_OK;
+}
+
 extern "C" evec_status evec_window_update(evec_handle h, int64_t n, double *T, int64_t ldt,
                                          double *Q, int64_t ldq, int nwin,
                                          const int64_t *begin_host, const int32_t *size_host,
@@ -2678,11 +2736,29 @@ extern "C" evec_status evec_window_update(evec_handle h, int64_t n, double *T, i
         if (a < 0 || k < 0 || k > window_max() || a + k > n || zoff_host[w] < 0)
             return EVEC_EINVAL;
     }
+    const int mode = opt ? opt->mode : EVEC_FP64;
+    const int slices = (opt && opt->slices) ? opt->slices : 8;
+    if ((mode != EVEC_FP64 && mode != EVEC_SPLIT) || slices < 2 || slices > 8) return EVEC_EINVAL;
     if (n == 0 || nwin == 0) return EVEC_OK;
     if (!T) return EVEC_EINVAL;
     DeviceGuard g(h->device);
     if (!g.ok) return EVEC_ECUDA;
     cudaStream_t st = h->stream;
+    if (mode == EVEC_SPLIT) {
+        std::vector<int> ws(nwin);
+        for (int w = 0; w < nwin; w++) ws[w] = w;
+        evec_status es = EVEC_OK;
+        timed(h, EVEC_K_WINDOW, [&] {
+            int ng = 0;
+            es = window_split(h, n, T, ldt, Q, ldq, ws, begin_host, size_host, Z, zoff_host,
+                              slices, &ng);
+            return ng;
+        });
+        if (es != EVEC_OK) return es;
+        EVEC_CUDA(cudaGetLastError());
+        if (opt && opt->check) return evec_sync(h, nullptr);
+        return EVEC_OK;
+    }
     if (Q) {   // the Q updates run on a second stream beside the T chain
         if (!h->la_stream)
             EVEC_CUDA(cudaStreamCreateWithFlags(&h->la_stream, cudaStreamNonBlocking));
@@ -2732,10 +2808,26 @@ extern "C" evec_status evec_window_update_set(evec_handle h, int64_t n, double *
     for (size_t i = 1; i < order.size(); i++)   // pairwise disjoint
         if (begin_host[order[i]] < begin_host[order[i - 1]] + size_host[order[i - 1]])
             return EVEC_EINVAL;
+    const int mode = opt ? opt->mode : EVEC_FP64;
+    const int slices = (opt && opt->slices) ? opt->slices : 8;
+    if ((mode != EVEC_FP64 && mode != EVEC_SPLIT) || slices < 2 || slices > 8) return EVEC_EINVAL;
     if (n == 0 || order.empty()) return EVEC_OK;
     if (!T) return EVEC_EINVAL;
     DeviceGuard g(h->device);
     if (!g.ok) return EVEC_ECUDA;
+    if (mode == EVEC_SPLIT) {   // disjoint windows commute: one after another
+        evec_status es = EVEC_OK;
+        timed(h, EVEC_K_WINDOW, [&] {
+            int ng = 0;
+            es = window_split(h, n, T, ldt, Q, ldq, order, begin_host, size_host, Z, zoff_host,
+                              slices, &ng);
+            return ng;
+        });
+        if (es != EVEC_OK) return es;
+        EVEC_CUDA(cudaGetLastError());
+        if (opt && opt->check) return evec_sync(h, nullptr);
+        return EVEC_OK;
+    }
     // one group of launches per kernel variant (window_class), so that no
     // window runs with columns past its own k
     struct Group {

@@ -455,7 +455,7 @@ int split_update_kp(int k) { return k <= 64 ? 64 : (k + 63) / 64 * 64; }
 // Slices of A (rows) and B (columns) into the caller's buffers, then the
 // GEMM.  Buffers: sa [S][Mpad][Kpad], sb [S][Npad][Kpad] BF16; rowmax
 // [Mpad], colmax [Npad] u64; ea [Mpad], eb [Npad] int; kend [N tiles]
-// (device, multiples of 32, <= Kpad).  Returns cudaErrorInvalidValue when
+// (device, multiples of 32, <= Kpad) or null for the whole K range.  Returns cudaErrorInvalidValue when
 // a tensor map cannot be encoded.
 // C = A B split in two parts, so that B's columns can be taken in chunks:
 // the row slices of A (once), then per chunk the column slices of B and
@@ -501,7 +501,8 @@ cudaError_t split_gemm_cols(const double *B, int64_t ldb, int M, int N, int K, i
     }
     const int gw = std::max(1, std::min(ntn, (int)lround(sqrt(2.0 * nsm))));
     k_split_gemm<false><<<ntn * mtn, kSplitThreads, smem, st>>>(
-        tmA, tmB, S, M, N, 0, Mpad, Npad, kend, 0, ea, eb, C, ldc, none, err, ntn, gw);
+        tmA, tmB, S, M, N, 0, Mpad, Npad, kend, kend ? 0 : Kpad, ea, eb, C, ldc, none, err, ntn,
+        gw);
     return cudaGetLastError();
 }
 

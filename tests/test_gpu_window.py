@@ -1,6 +1,7 @@
 """Eigenvalue reordering's off-diagonal updates on the GPU
 (evec_window_update: the left and right update tasks applying each
-window's accumulator as FP64 products) against the oracle's plain loops:
+window's accumulator as FP64 products, or through the split-precision
+GEMM) against the oracle's plain loops:
 element by element within a dot-product rounding bound for chains of
 overlapping windows of every kernel variant (k up to 256, ragged n), exact
 results for permutation windows, the invariant Q T Q^T for disjoint
@@ -170,3 +171,72 @@ def test_disjoint_set_rejects_overlap():
         ev.window_update(dT, None, [(0, np.eye(10)), (9, np.eye(5))], disjoint=True)
     assert ei.value.status == ev.EVEC_EINVAL
     np.testing.assert_array_equal(dT.cpu().numpy(), T)
+
+
+# --------------------------------------------------------------------------
+# split precision (EVEC_SPLIT): the products through the split GEMM
+# --------------------------------------------------------------------------
+
+def _gpu_split(T, Q, windows, disjoint=False):
+    dT = _dev(T)
+    dQ = _dev(Q) if Q is not None else None
+    ev.window_update(dT, dQ, windows, check=True, disjoint=disjoint, mode="split")
+    return dT.cpu().numpy(), (dQ.cpu().numpy() if dQ is not None else None)
+
+
+@pytest.mark.parametrize("k,stride", [(17, 9), (64, 40), (128, 64), (200, 100), (256, 128)])
+def test_window_chain_split_against_oracle(k, stride):
+    # 8 slices of 7 bits: each product within k 2^-55 max|row| max|column|
+    # of the exact one, inside the FP64 path's bound
+    n = 333 if k < 256 else 600
+    T, blocks = workloads.config0_schur(n, seed=k + 50)
+    Q = workloads.householder_orthogonal(n, seed=k + 51)
+    w = workloads.window_chain(n, k, stride, seed=k + 52, blocks=blocks)
+    Tg, Qg = _gpu_split(T, Q, w)
+    To, Qo = oracle.window_update(T, Q, w)
+    assert np.abs(Tg - To).max() <= _bound(To, w), np.abs(Tg - To).max()
+    assert np.abs(Qg - Qo).max() <= _bound(Qo, w)
+
+
+def test_window_split_edges_disjoint_set_and_errors():
+    n = 97
+    T, _ = workloads.config0_schur(n, seed=55)
+    rng = np.random.default_rng(56)
+    w = []
+    for a, k in ((0, 1), (96, 1), (0, 97), (60, 37), (0, 33)):
+        Z, _ = np.linalg.qr(rng.standard_normal((k, k)))
+        w.append((a, Z))
+    Tg, _ = _gpu_split(T, None, w)
+    To, _ = oracle.window_update(T, None, w)
+    assert np.abs(Tg - To).max() <= _bound(To, w)
+    # the disjoint set in split mode (applied in the order of first rows)
+    n = 777
+    T, _ = workloads.config0_schur(n, seed=57)
+    Q = workloads.householder_orthogonal(n, seed=58)
+    w = _mixed_disjoint(n, 59)
+    Tg, Qg = _gpu_split(T, Q, w, disjoint=True)
+    To, Qo = oracle.window_update(T, Q, w)
+    assert np.abs(Tg - To).max() <= _bound(To, w)
+    assert np.abs(Qg - Qo).max() <= _bound(Qo, w)
+    # a slice count outside 2..8 is refused and nothing is applied
+    dT = _dev(T)
+    with pytest.raises(ev.EvecError) as ei:
+        ev.window_update(dT, None, w, mode="split", slices=9)
+    assert ei.value.status == ev.EVEC_EINVAL
+    np.testing.assert_array_equal(dT.cpu().numpy(), T)
+
+
+def test_window_split_full_size_invariant_and_fp64_agreement():
+    # the benchmark's workload in split mode: Q T Q^T unchanged, Q
+    # orthogonal, and the result within the FP64 bound of the FP64 path's
+    n = 4096
+    T, blocks = workloads.config0_schur(n, seed=workloads.SEED_BASE)
+    Q = workloads.householder_orthogonal(n, seed=workloads.SEED_BASE + 100)
+    w = workloads.window_chain(n, 128, 128, seed=workloads.SEED_BASE + 9, blocks=blocks)
+    Tg, Qg = _gpu_split(T, Q, w)
+    A = Q @ T @ Q.T
+    assert np.abs(Qg @ Tg @ Qg.T - A).max() <= 64 * n * U * np.abs(A).max()
+    assert np.abs(Qg.T @ Qg - np.eye(n)).max() <= 64 * n * U
+    Tf, Qf = _gpu(T, Q, w)
+    assert np.abs(Tg - Tf).max() <= _bound(T, w[:2])
+    assert np.abs(Qg - Qf).max() <= _bound(Q, w[:2])
