@@ -63,7 +63,6 @@ int hess_update(int64_t n, double *A, int64_t lda, double *Q, int64_t ldq, int64
                 double *ws, cudaStream_t st, cudaStream_t qst, cudaEvent_t fork,
                 cudaEvent_t join);
 int window_max();
-void launch_transpose_acc(const double *Z, int k, double *Zt, cudaStream_t st);
 int window_update_t(int64_t n, double *T, int64_t ldt, int64_t a, int k, const double *Z,
                     cudaStream_t st);
 int window_update_q(int64_t n, double *Q, int64_t ldq, int64_t a, int k, const double *Z,
@@ -102,6 +101,13 @@ cudaError_t split_gemm_cols(const double *B, int64_t ldb, int M, int N, int K, i
                             int *eb, int *err, cudaStream_t st);
 void launch_canonicalize_range(const Plan &p, double *X, int64_t ldx, int32_t *scale_exp, int u0,
                                int u1, cudaStream_t st);
+cudaError_t split_slice_cols(const double *B, int64_t ldb, int K, int N, int S, int Npad,
+                             __nv_bfloat16 *sb, unsigned long long *colmax, int *eb,
+                             cudaStream_t st);
+cudaError_t split_gemm_sliced(const __nv_bfloat16 *sa, int Mpad, const __nv_bfloat16 *sb,
+                              int Npad, int M, int N, int K, int S, const int *kend,
+                              const int *ea, const int *eb, double *C, int64_t ldc, int *err,
+                              cudaStream_t st);
 cudaError_t launch_split_gemm(const double *A, int64_t lda, const double *B, int64_t ldb, int M,
                               int N, int K, int S, const int *kend, double *C, int64_t ldc,
                               __nv_bfloat16 *sa, __nv_bfloat16 *sb, unsigned long long *rowmax,
@@ -579,7 +585,15 @@ struct evec_ctx {
     int32_t *lmap_d = nullptr; size_t lmap_cap = 0;
     double *hs_ws = nullptr; size_t hs_ws_cap = 0;   // Hessenberg reduction
     WinDesc *win_d = nullptr; size_t win_cap = 0;    // reordering window tables
-    double *wZt = nullptr; size_t wZt_cap = 0;       // Z^T of a split left update
+    // split window updates: the column slices of an accumulator Z (also the
+    // row slices of Z^T), their maxima and exponents
+    __nv_bfloat16 *wZs = nullptr; size_t wZs_cap = 0;
+    unsigned long long *wZm = nullptr; size_t wZm_cap = 0;
+    int *wZe = nullptr; size_t wZe_cap = 0;
+    // and the Q products' own row slices (they run on la_stream)
+    __nv_bfloat16 *wQs = nullptr; size_t wQs_cap = 0;
+    unsigned long long *wQm = nullptr; size_t wQm_cap = 0;
+    int *wQe = nullptr; size_t wQe_cap = 0;
     // residual gate of the split solve (opts.refine >= 2): ||T||_1 and the
     // failure count on the device; the last top-level call's statistics
     unsigned long long *gate_d = nullptr;
@@ -975,7 +989,8 @@ evec_status evec_destroy(evec_handle h) {
                    h->slA, h->slB, h->rmax, h->cmax, h->ea, h->eb, h->panels,
                    h->ea_panels, h->boff_d, h->bws, h->bplan_d, h->queue_d, h->tauT,
                    h->blk_tauT, h->pW, h->Rd, h->seg_ey, h->lT, h->lQ, h->lX, h->lE, h->lL,
-                   h->lmap_d, h->hs_ws, h->gate_d, h->win_d, h->lT2, h->wZt};
+                   h->lmap_d, h->hs_ws, h->gate_d, h->win_d, h->lT2, h->wZs, h->wZm, h->wZe,
+                   h->wQs, h->wQm, h->wQe};
     for (void *p : dev)
         if (p) cudaFree(p);
     for (auto &t : h->live) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
@@ -2672,9 +2687,15 @@ extern "C" evec_status evec_generalized_left(evec_handle h, int64_t n, const dou
 constexpr int64_t kSplitMaxN = 65472;
 
 // EVEC_SPLIT window updates: each window's left, right and Q products
-// through the split GEMM (row and column slices of the operands first, so
-// the products may overwrite their own inputs), in the order of `ws` on the
-// handle's stream.  Returns the kernels launched through *ng.
+// through the split GEMM (the operands are sliced before each product, so
+// a product may overwrite its own input), in the order of `ws`.  The column
+// slices of every accumulator Z of a group of windows are taken first;
+// padded to a row band of the GEMM they serve as the left operand Z^T of
+// the left update (the rows of Z^T are the columns of Z, with the same
+// exponents) and as the right operand of the right and Q updates.  The T
+// products run in order on the handle's stream, the Q products (which read
+// no part of T) on its second stream beside them.  Returns the kernels
+// launched through *ng.
 static evec_status window_split(evec_handle h, int64_t n, double *T, int64_t ldt, double *Q,
                                 int64_t ldq, const std::vector<int> &ws,
                                 const int64_t *begin_host, const int32_t *size_host,
@@ -2683,40 +2704,88 @@ static evec_status window_split(evec_handle h, int64_t n, double *T, int64_t ldt
     for (int w : ws) kmax = std::max(kmax, (int)size_host[w]);
     if (kmax == 0) return EVEC_OK;
     if (n > kSplitMaxN) return EVEC_EINVAL;
+    constexpr int kGroup = 64;   // windows whose Z slices are held at once
     const int Mp = split_pad_m((int)n), Np = split_pad_n((int)n), Kp = split_pad_k(kmax);
+    const int Pz = split_pad_m(kmax);
+    const size_t zblk = (size_t)slices * Pz * Kp;   // one window's Z slices (at most)
+    const int group = std::min<int>(kGroup, (int)ws.size());
     EVEC_TRY(grow_device(&h->slA, &h->slA_cap, (size_t)slices * Mp * Kp));
     EVEC_TRY(grow_device(&h->slB, &h->slB_cap, (size_t)slices * Np * Kp));
     EVEC_TRY(grow_device(&h->rmax, &h->rmax_cap, (size_t)Mp));
     EVEC_TRY(grow_device(&h->ea, &h->ea_cap, (size_t)Mp));
     EVEC_TRY(grow_device(&h->cmax, &h->cmax_cap, (size_t)Np));
     EVEC_TRY(grow_device(&h->eb, &h->eb_cap, (size_t)Np));
-    EVEC_TRY(grow_device(&h->wZt, &h->wZt_cap, (size_t)kmax * kmax));
-    cudaStream_t st = h->stream;
+    EVEC_TRY(grow_device(&h->wZs, &h->wZs_cap, zblk * group));
+    EVEC_TRY(grow_device(&h->wZm, &h->wZm_cap, (size_t)Pz * group));
+    EVEC_TRY(grow_device(&h->wZe, &h->wZe_cap, (size_t)Pz * group));
+    cudaStream_t st = h->stream, sq = nullptr;
+    if (Q) {
+        EVEC_TRY(grow_device(&h->wQs, &h->wQs_cap, (size_t)slices * Mp * Kp));
+        EVEC_TRY(grow_device(&h->wQm, &h->wQm_cap, (size_t)Mp));
+        EVEC_TRY(grow_device(&h->wQe, &h->wQe_cap, (size_t)Mp));
+        if (!h->la_stream)
+            EVEC_CUDA(cudaStreamCreateWithFlags(&h->la_stream, cudaStreamNonBlocking));
+        if (!h->ev_slice) EVEC_CUDA(cudaEventCreateWithFlags(&h->ev_slice, cudaEventDisableTiming));
+        if (!h->ev_tail) EVEC_CUDA(cudaEventCreateWithFlags(&h->ev_tail, cudaEventDisableTiming));
+        sq = h->la_stream;
+    }
     int *err = &h->status_d->timeout;
     cudaError_t ce = cudaSuccess;
-    for (int w : ws) {
-        const int64_t a = begin_host[w];
-        const int k = size_host[w];
-        if (k == 0) continue;
-        const double *Zw = Z + zoff_host[w];
-        // left: T[a:a+k, a:n] <- Z^T T[a:a+k, a:n]
-        launch_transpose_acc(Zw, k, h->wZt, st);
-        double *Tl = T + a + a * ldt;
-        ce = launch_split_gemm(h->wZt, k, Tl, ldt, k, (int)(n - a), k, slices, nullptr, Tl, ldt,
-                               h->slA, h->slB, h->rmax, h->cmax, h->ea, h->eb, err, st);
-        if (ce != cudaSuccess) break;
-        // right: T[0:a+k, a:a+k] <- T[0:a+k, a:a+k] Z
-        double *Tr = T + a * ldt;
-        ce = launch_split_gemm(Tr, ldt, Zw, k, (int)(a + k), k, k, slices, nullptr, Tr, ldt,
-                               h->slA, h->slB, h->rmax, h->cmax, h->ea, h->eb, err, st);
-        if (ce != cudaSuccess) break;
-        *ng += 11;
-        if (Q) {   // Q[:, a:a+k] <- Q[:, a:a+k] Z
-            double *Qw = Q + a * ldq;
-            ce = launch_split_gemm(Qw, ldq, Zw, k, (int)n, k, k, slices, nullptr, Qw, ldq, h->slA,
-                                   h->slB, h->rmax, h->cmax, h->ea, h->eb, err, st);
-            if (ce != cudaSuccess) break;
-            *ng += 5;
+    for (size_t g0 = 0; g0 < ws.size() && ce == cudaSuccess; g0 += group) {
+        const size_t g1 = std::min(ws.size(), g0 + group);
+        // the group's Z slices (the previous group's Q products are done
+        // with the buffer: the main stream waited for them)
+        for (size_t i = g0; i < g1 && ce == cudaSuccess; i++) {
+            const int k = size_host[ws[i]];
+            if (k == 0) continue;
+            ce = split_slice_cols(Z + zoff_host[ws[i]], k, k, k, slices, split_pad_m(k),
+                                  h->wZs + (i - g0) * zblk, h->wZm + (i - g0) * Pz,
+                                  h->wZe + (i - g0) * Pz, st);
+            *ng += 2;
+        }
+        if (Q && ce == cudaSuccess) {   // Q[:, a:a+k] <- Q[:, a:a+k] Z
+            cudaEventRecord(h->ev_slice, st);
+            cudaStreamWaitEvent(sq, h->ev_slice, 0);
+            for (size_t i = g0; i < g1 && ce == cudaSuccess; i++) {
+                const int k = size_host[ws[i]];
+                if (k == 0) continue;
+                double *Qw = Q + begin_host[ws[i]] * ldq;
+                ce = split_gemm_rows(Qw, ldq, (int)n, k, slices, h->wQs, h->wQm, h->wQe, sq);
+                if (ce == cudaSuccess)
+                    ce = split_gemm_sliced(h->wQs, Mp, h->wZs + (i - g0) * zblk, split_pad_m(k),
+                                           (int)n, k, k, slices, nullptr, h->wQe,
+                                           h->wZe + (i - g0) * Pz, Qw, ldq, err, sq);
+                *ng += 3;
+            }
+        }
+        for (size_t i = g0; i < g1 && ce == cudaSuccess; i++) {
+            const int64_t a = begin_host[ws[i]];
+            const int k = size_host[ws[i]];
+            if (k == 0) continue;
+            const int P = split_pad_m(k);
+            const __nv_bfloat16 *zs = h->wZs + (i - g0) * zblk;
+            const int *ze = h->wZe + (i - g0) * Pz;
+            // left: T[a:a+k, a:n] <- Z^T T[a:a+k, a:n]
+            double *Tl = T + a + a * ldt;
+            const int nl = (int)(n - a);
+            ce = split_slice_cols(Tl, ldt, k, nl, slices, split_pad_n(nl), h->slB, h->cmax, h->eb,
+                                  st);
+            if (ce == cudaSuccess)
+                ce = split_gemm_sliced(zs, P, h->slB, split_pad_n(nl), k, nl, k, slices, nullptr,
+                                       ze, h->eb, Tl, ldt, err, st);
+            // right: T[0:a+k, a:a+k] <- T[0:a+k, a:a+k] Z
+            double *Tr = T + a * ldt;
+            const int mr = (int)(a + k);
+            if (ce == cudaSuccess)
+                ce = split_gemm_rows(Tr, ldt, mr, k, slices, h->slA, h->rmax, h->ea, st);
+            if (ce == cudaSuccess)
+                ce = split_gemm_sliced(h->slA, split_pad_m(mr), zs, P, mr, k, k, slices, nullptr,
+                                       h->ea, ze, Tr, ldt, err, st);
+            *ng += 6;
+        }
+        if (Q) {   // the next group's slices overwrite this group's
+            cudaEventRecord(h->ev_tail, sq);
+            cudaStreamWaitEvent(st, h->ev_tail, 0);
         }
     }
     EVEC_CUDA(ce);

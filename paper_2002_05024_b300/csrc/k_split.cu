@@ -471,18 +471,31 @@ cudaError_t split_gemm_rows(const double *A, int64_t lda, int M, int K, int S,
     return cudaGetLastError();
 }
 
-cudaError_t split_gemm_cols(const double *B, int64_t ldb, int M, int N, int K, int S,
-                            const int *kend, double *C, int64_t ldc, const __nv_bfloat16 *sa,
-                            __nv_bfloat16 *sb, unsigned long long *colmax, const int *ea,
-                            int *eb, int *err, cudaStream_t st) {
-    if (!get_encoder()) return cudaErrorInvalidValue;
-    const int Mpad = split_pad_m(M), Npad = split_pad_n(N), Kpad = split_pad_k(K);
+// Column slices of the K x N matrix B into sb [S][Npad][Kpad] (Npad >=
+// split_pad_n(N), a multiple of kTN: a larger Npad lets the same slices
+// serve as the row slices of B^T with Npad = split_pad_m(N)), exponents eb.
+cudaError_t split_slice_cols(const double *B, int64_t ldb, int K, int N, int S, int Npad,
+                             __nv_bfloat16 *sb, unsigned long long *colmax, int *eb,
+                             cudaStream_t st) {
+    const int Kpad = split_pad_k(K);
     k_col_max<<<(N + 7) / 8, 256, 0, st>>>(B, ldb, K, N, colmax);
     k_slice_cols<<<dim3((Kpad + 255) / 256, Npad), 256, 0, st>>>(B, ldb, K, N, S, colmax, sb,
                                                                   Npad, Kpad, eb);
+    return cudaGetLastError();
+}
+
+// C = A B from the slices of A (sa [S][Mpad][Kpad], exponents ea) and of B
+// (sb [S][Npad][Kpad], exponents eb), over K < kend[N tile] (or the whole
+// padded K when kend is null).
+cudaError_t split_gemm_sliced(const __nv_bfloat16 *sa, int Mpad, const __nv_bfloat16 *sb,
+                              int Npad, int M, int N, int K, int S, const int *kend,
+                              const int *ea, const int *eb, double *C, int64_t ldc, int *err,
+                              cudaStream_t st) {
+    if (!get_encoder()) return cudaErrorInvalidValue;
+    const int Kpad = split_pad_k(K);
     CUtensorMap tmA, tmB;
     if (!make_map(&tmA, (void *)sa, S * Mpad, Kpad, kTM) ||
-        !make_map(&tmB, sb, S * Npad, Kpad, 32))
+        !make_map(&tmB, (void *)sb, S * Npad, Kpad, 32))
         return cudaErrorInvalidValue;
     const size_t smem = split_smem_bytes();
     cudaFuncSetAttribute(k_split_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -492,7 +505,7 @@ cudaError_t split_gemm_cols(const double *B, int64_t ldb, int M, int N, int K, i
     // bytes / column tile bytes)), so one wave's row bands and column tiles
     // cost about the same DRAM traffic (a band of Q's slices holds twice
     // the rows of a column tile of Y's)
-    const int ntn = Npad / kTN, mtn = Mpad / kTM;
+    const int ntn = split_pad_n(N) / kTN, mtn = split_pad_m(M) / kTM;
     int nsm = 148, dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
@@ -504,6 +517,17 @@ cudaError_t split_gemm_cols(const double *B, int64_t ldb, int M, int N, int K, i
         tmA, tmB, S, M, N, 0, Mpad, Npad, kend, kend ? 0 : Kpad, ea, eb, C, ldc, none, err, ntn,
         gw);
     return cudaGetLastError();
+}
+
+cudaError_t split_gemm_cols(const double *B, int64_t ldb, int M, int N, int K, int S,
+                            const int *kend, double *C, int64_t ldc, const __nv_bfloat16 *sa,
+                            __nv_bfloat16 *sb, unsigned long long *colmax, const int *ea,
+                            int *eb, int *err, cudaStream_t st) {
+    if (!get_encoder()) return cudaErrorInvalidValue;
+    const int Mpad = split_pad_m(M), Npad = split_pad_n(N);
+    cudaError_t e = split_slice_cols(B, ldb, K, N, S, Npad, sb, colmax, eb, st);
+    if (e != cudaSuccess) return e;
+    return split_gemm_sliced(sa, Mpad, sb, Npad, M, N, K, S, kend, ea, eb, C, ldc, err, st);
 }
 
 cudaError_t launch_split_gemm(const double *A, int64_t lda, const double *B, int64_t ldb, int M,

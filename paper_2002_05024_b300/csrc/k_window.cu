@@ -275,21 +275,6 @@ int window_update_t(int64_t n, double *T, int64_t ldt, int64_t a, int k, const d
     return 2;
 }
 
-// Zt = Z^T of a k x k accumulator (column-major, ld k): the left operand of
-// the split-precision left update Z^T T[a:a+k, a:n].
-__global__ void __launch_bounds__(256)
-    k_transpose_acc(const double *__restrict__ Z, int k, double *__restrict__ Zt) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= k * k) return;
-    const int r = i % k, c = i / k;
-    Zt[c + (int64_t)r * k] = Z[i];
-}
-
-void launch_transpose_acc(const double *Z, int k, double *Zt, cudaStream_t st) {
-    if (k <= 0) return;
-    k_transpose_acc<<<(k * k + 255) / 256, 256, 0, st>>>(Z, k, Zt);
-}
-
 // The same window's Q[:, a:a+k] <- Q[:, a:a+k] Z.  It reads no part of T,
 // so the Q updates of a list of windows can run on their own stream.
 int window_update_q(int64_t n, double *Q, int64_t ldq, int64_t a, int k, const double *Z,
