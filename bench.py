@@ -121,6 +121,12 @@ def workload(n):
     return T, blocks, Q
 
 
+def default_tile(n, mode):
+    """The library's tile when opt->tile is 0: 64 rows, 256 in split mode
+    from n = 10240."""
+    return 256 if mode == "split" and n >= 10240 else 64
+
+
 def flop_counts(n, blocks, tile_start, with_q=True, res=None):
     """Algorithmic FP64 flops: total per the method's definition, and the
     parts done by the tile-update GEMMs and by the back-transformation (the
@@ -687,8 +693,9 @@ def run_ours(args, rank, world, local_rank):
     T, blocks, Q = workload(n)
     m = sum(sz for _, sz in blocks)
     d = np.ascontiguousarray(np.diagonal(T))
+    tile_used = args.tile or default_tile(n, args.mode)
     _, tile_start = ev.plan_query(d, np.ascontiguousarray(np.diagonal(T, -1)),
-                                  np.ascontiguousarray(np.diagonal(T, 1)), None, args.tile or 64)
+                                  np.ascontiguousarray(np.diagonal(T, 1)), None, tile_used)
     res = []
     F, F_upd, F_bt = flop_counts(n, blocks, tile_start, res=res)
     F_diag = max(F - F_upd - F_bt, 0.0)
@@ -749,8 +756,8 @@ def run_ours(args, rank, world, local_rank):
     # roofline of the dominant kernel (largest share of event-timed time)
     peaks = measured_peaks()
     slices = (args.slices or 8) if args.mode == "split" else 0
-    tile = args.tile or 64
-    roofs = rooflines(prof, args.steps, args.mode, slices, F_diag, F_upd, F_bt, peaks, n, tile,
+    roofs = rooflines(prof, args.steps, args.mode, slices, F_diag, F_upd, F_bt, peaks, n,
+                      tile_used,
                       F_res=F_res if refine else 0.0, sweeps=2 if refine else 1,
                       prefix="left:" if left else "")
     dominant = max(prof.items(), key=lambda kv: kv[1][0])[0]
@@ -838,10 +845,16 @@ def run_ours(args, rank, world, local_rank):
     if world == 1 and args.records and not left and args.mode == "fp64":
         records = {}
         rec_steps = max(1, min(args.steps, args.record_steps))
+        # the split path at its own tile (the library's default in split mode)
+        s_tile = args.tile or default_tile(n, "split")
+        _, s_start = ev.plan_query(d, np.ascontiguousarray(np.diagonal(T, -1)),
+                                   np.ascontiguousarray(np.diagonal(T, 1)), None, s_tile)
+        s_res = []
+        sF, sF_upd, sF_bt = flop_counts(n, blocks, s_start, res=s_res)
         for name, ref in (("split", True), ("split_no_sweep", False)):
-            r = split_record(ev, dev, stream, dT, dQ, T, Q, blocks, m, F, F_upd, F_bt, F_res,
-                             args.tile, ref, rec_steps, max(1, min(args.warmup, 2)), peaks, pick,
-                             oracle_ref, (Xh, eh, lih), left=False)
+            r = split_record(ev, dev, stream, dT, dQ, T, Q, blocks, m, sF, sF_upd, sF_bt,
+                             s_res[0], s_tile, ref, rec_steps, max(1, min(args.warmup, 2)),
+                             peaks, pick, oracle_ref, (Xh, eh, lih), left=False)
             r["vs_plain"] = r["value"] / value
             records[name] = r
         records["split_vs_plain"] = records["split"]["vs_plain"]
@@ -872,7 +885,7 @@ def run_ours(args, rank, world, local_rank):
                                + ("; the split-precision path with the FP64 residual-correction "
                                   "sweep, and the 2000-matrix batch, in 'records'"
                                   if records else ""),
-                   "n": n, "columns": m, "tile": args.tile or 64, "mode": args.mode,
+                   "n": n, "columns": m, "tile": tile_used, "mode": args.mode,
                    "slices": slices or None,
                    "refine": refine, "side": args.side,
                    "lookahead": args.lookahead,
@@ -929,7 +942,7 @@ def split_record(ev, dev, stream, dT, dQ, T, Q, blocks, m, F, F_upd, F_bt, F_res
     h = ev.handle(dev.index)
     prof = profiled_steps(h, step, steps, dev, k=1)
     F_diag = max(F - F_upd - F_bt, 0.0)
-    roofs = rooflines(prof, steps, "split", 8, F_diag, F_upd, F_bt, peaks, n, tile or 64,
+    roofs = rooflines(prof, steps, "split", 8, F_diag, F_upd, F_bt, peaks, n, tile,
                       F_res=F_res if refine else 0.0, sweeps=2 if refine else 1)
     Xh, eh = X.cpu().numpy(), e.cpu().numpy()
     lrh, lih = lr.cpu().numpy(), li.cpu().numpy()
@@ -939,6 +952,7 @@ def split_record(ev, dev, stream, dT, dQ, T, Q, blocks, m, F, F_upd, F_bt, F_res
            "dtype": "bf16 slice products (FP32 exact accumulation) + f64",
            "path": "split precision, 8 BF16 digit slices per operand, FP64 recombination"
                    + (", then one FP64 residual-correction sweep" if refine else ""),
+           "tile": tile,
            "quality": residual_sample(T, Q, Xh, lrh, lih, blocks, pick, left=left),
            "rooflines": roofs,
            "kernel_ms_per_step": {k: v[0] / steps for k, v in prof.items() if v[0] > 0}}

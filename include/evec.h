@@ -88,9 +88,11 @@ typedef enum {
 
 typedef struct {
     int mode;    /* evec_mode */
-    int tile;    /* tile size nb of the tiled solve, 16..512; 0 = 64.  Tiles
-                    above 64 rows are solved in sub-blocks of at most 64
-                    rows with one scale exponent per tile segment */
+    int tile;    /* tile size nb of the tiled solve, 16..512; 0 = 64, or
+                    256 in EVEC_SPLIT mode for n >= 10240 (the faster
+                    choice measured on B300).  Tiles above 64 rows are
+                    solved in sub-blocks of at most 64 rows with one scale
+                    exponent per tile segment */
     int slices;  /* EVEC_SPLIT: digit slices per operand, 2..8; 0 = 8
                     (relative error of a product ~2^(-7 slices)) */
     int refine;  /* EVEC_SPLIT, evec_standard and evec_standard_left:
@@ -122,8 +124,8 @@ typedef struct {
                     the device status directly */
 } evec_opts;
 
-/* The defaults that opt == NULL stands for: EVEC_FP64, tile 0 (64),
- * slices 0 (8), refine 1, check 0. */
+/* The defaults that opt == NULL stands for: EVEC_FP64, tile 0 (64 rows in
+ * FP64 mode), slices 0 (8), refine 1, check 0. */
 void evec_opts_default(evec_opts *opt);
 
 /* Create a handle on CUDA device `device` that launches on `cuda_stream`

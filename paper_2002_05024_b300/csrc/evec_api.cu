@@ -729,9 +729,15 @@ evec_status cuda_status(cudaError_t e) {
     } while (0)
 #define EVEC_CUDA(x) EVEC_TRY(cuda_status(x))
 
-int resolve_tile(const evec_opts *opt) {
-    int nb = (opt && opt->tile) ? opt->tile : 64;
-    return nb;
+// opt->tile, else the default: 64 rows, 256 in EVEC_SPLIT mode from
+// n = 10240 (measured on B300, all columns with Q: at n = 4096 and 8192 the
+// 64-row tiles are faster, 10.3 against 12.3 and 52.5 against 56.0 ms; at
+// n = 12288 and 16384 the 256-row tiles, 146 against 158 and 312 against
+// 360 ms, since the split updates then dominate and a 256-row tile makes
+// a quarter of the update epilogues).
+int resolve_tile(const evec_opts *opt, int64_t n) {
+    if (opt && opt->tile) return opt->tile;
+    return (opt && opt->mode == EVEC_SPLIT && n >= 10240) ? 256 : 64;
 }
 
 cudaEvent_t take_event(evec_handle h) {
@@ -1291,7 +1297,7 @@ evec_status evec_standard(evec_handle h, int64_t n, const double *T, int64_t ldt
     if (mode != EVEC_FP64 && mode != EVEC_SPLIT) return EVEC_EINVAL;
     const int slices = (opt && opt->slices) ? opt->slices : 8;
     if (slices < 2 || slices > 8) return EVEC_EINVAL;
-    const int nb = resolve_tile(opt);
+    const int nb = resolve_tile(opt, n);
     if (nb < 16 || nb > kMaxTileBig) return EVEC_EINVAL;
     if (n == 0) return EVEC_OK;
     if (!T || !X || !scale_exp) return EVEC_EINVAL;
@@ -1550,7 +1556,7 @@ evec_status evec_trsolve(evec_handle h, int64_t n, const double *T, int64_t ldt,
     if (mode != EVEC_FP64 && mode != EVEC_SPLIT) return EVEC_EINVAL;
     const int slices = (opt && opt->slices) ? opt->slices : 8;
     if (slices < 2 || slices > 8) return EVEC_EINVAL;
-    const int nb = resolve_tile(opt);
+    const int nb = resolve_tile(opt, n);
     if (nb < 16 || nb > kMaxTileBig) return EVEC_EINVAL;
     if (n == 0 || nrhs == 0) return EVEC_OK;
     if (!T || !B || !X || !scale_exp) return EVEC_EINVAL;
@@ -1645,7 +1651,7 @@ evec_status evec_standard_left(evec_handle h, int64_t n, const double *T, int64_
         return EVEC_EINVAL;
     if (n == 0) return EVEC_OK;
     if (!T || !X || !scale_exp) return EVEC_EINVAL;
-    const int nb = resolve_tile(opt);
+    const int nb = resolve_tile(opt, n);
     if (nb < 16 || nb > kMaxTileBig) return EVEC_EINVAL;
     DeviceGuard g(h->device);
     if (!g.ok) return EVEC_ECUDA;
@@ -1724,7 +1730,7 @@ evec_status evec_standard_host(evec_handle h, int64_t n, const double *T_host,
     }
     // the output size needs the plan; evec_standard plans again (cheap, host)
     int64_t bad = -1;
-    EVEC_TRY(plan_device_matrix(h, n, h->hT, n, select_host, resolve_tile(opt), &bad));
+    EVEC_TRY(plan_device_matrix(h, n, h->hT, n, select_host, resolve_tile(opt, n), &bad));
     const int64_t m = h->plan.m;
     if (m == 0) {
         h->q_src = nullptr;
