@@ -55,12 +55,13 @@ size_t split_smem_bytes() {
 // slicing kernels
 // ---------------------------------------------------------------------------
 
-// row maxima of the column-major M x K matrix A (bit patterns, atomicMax)
-__global__ void k_row_max(const double *__restrict__ A, int64_t lda, int M, int K,
+// row maxima of the column-major M x K matrix A (bit patterns, atomicMax),
+// kc columns per CTA row
+__global__ void k_row_max(const double *__restrict__ A, int64_t lda, int M, int K, int kc,
                           unsigned long long *__restrict__ rowmax) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= M) return;
-    const int k0 = blockIdx.y * 256, k1 = min(K, k0 + 256);
+    const int k0 = blockIdx.y * kc, k1 = min(K, k0 + kc);
     long long b = 0;
     for (int k = k0; k < k1; k++) b = max(b, abs_bits(A[i + (int64_t)k * lda]));
     if (b) atomicMax(&rowmax[i], (unsigned long long)b);
@@ -465,7 +466,11 @@ cudaError_t split_gemm_rows(const double *A, int64_t lda, int M, int K, int S,
                             cudaStream_t st) {
     const int Mpad = split_pad_m(M), Kpad = split_pad_k(K);
     cudaMemsetAsync(rowmax, 0, sizeof(unsigned long long) * Mpad, st);
-    k_row_max<<<dim3((M + 255) / 256, (K + 255) / 256), 256, 0, st>>>(A, lda, M, K, rowmax);
+    // short rows (the window products, K <= 256): chunks of 32 columns, so
+    // that a few hundred rows still fill the GPU; long rows: 256
+    const int kc = K <= 512 ? 32 : 256;
+    k_row_max<<<dim3((M + 255) / 256, (K + kc - 1) / kc), 256, 0, st>>>(A, lda, M, K, kc,
+                                                                        rowmax);
     k_slice_rows<<<dim3(Kpad / 64, Mpad / 32), 256, 0, st>>>(A, lda, M, K, S, rowmax, sa, Mpad,
                                                               Kpad, ea);
     return cudaGetLastError();
