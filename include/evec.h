@@ -503,10 +503,15 @@ evec_status evec_batched(evec_handle h, int64_t count, const int64_t *n_host,
  * requirements of evec_generalized.  Output packing as evec_batched (X_i at
  * sum_{k<i} n_k m_k; scale_exp_i, alpha_re_i, alpha_im_i, beta_i at
  * sum_{k<i} m_k; the last three may be NULL); m_i from
- * evec_batched_generalized_count.  opt->mode must be EVEC_FP64; opt->tile 16..64, 0 = 64 (the
- * solver holds both matrices' diagonal tiles: one CTA per SM at 64).  Device-side errors
- * (evec_sync / opt->check): index = element offset in S_packed or T_packed
- * of the offending entry.
+ * evec_batched_generalized_count.  opt->mode must be EVEC_FP64; opt->tile
+ * 16..64, 0 = 64 (the solver holds both matrices' diagonal tiles: one CTA
+ * per SM at 64).  As in evec_batched, the device part of the call is a
+ * CUDA graph, replayed while the call is the same (layout, buffers,
+ * selection, tile, and the three central diagonals of every S_i and T_i;
+ * the entries above them may change); a call of
+ * evec_batched_generalized_count in between ends the replay.  Device-side
+ * errors (evec_sync / opt->check): index = element offset in S_packed or
+ * T_packed of the offending entry.
  */
 evec_status evec_batched_generalized(evec_handle h, int64_t count, const int64_t *n_host,
                                      const double *S_packed, const int64_t *s_off_host,

@@ -222,6 +222,12 @@ struct BatchKey {
     std::vector<uint8_t> sel;
     std::vector<double> diag;
     int64_t eacc = 0;
+    // pencils (evec_batched_generalized): T_packed above is S; the
+    // triangular factors, their offsets and the beta output; diag holds
+    // S's diagonals, then T's
+    bool gen = false;
+    const void *T2 = nullptr, *beta = nullptr;
+    std::vector<int64_t> t2off;
 };
 
 // The second matrix of a pencil for the planner: its diagonal and first
@@ -1904,7 +1910,7 @@ namespace evec {
 // graph when use_graph.
 // Pencils: T2_packed / t2_off_host hold the upper triangular T of each
 // pair (T_packed its S), beta_out receives beta per column, gen_tile is the
-// largest tile (no graph: use_graph must be false).
+// largest tile.
 // Standard problems: Q_packed (may be null) with q_off_host[i] >= 0 gives
 // matrix i a back-transformation X_i = Q_i Y_i (Q_i at Q_packed +
 // q_off_host[i], leading dimension n_i); x_off_host / e_off_host (may be
@@ -2071,7 +2077,8 @@ static evec_status run_batch(evec_handle h, int64_t count, const int64_t *n_host
         std::vector<uint64_t> key = {(uint64_t)nb, (uint64_t)bytes, (uint64_t)items_off,
                                      (uint64_t)h->bplan_d, (uint64_t)h->bplan_h,
                                      (uint64_t)h->bws, (uint64_t)h->queue_d,
-                                     (uint64_t)h->status_d, (uint64_t)slices};
+                                     (uint64_t)h->status_d, (uint64_t)slices,
+                                     (uint64_t)gen_tile};
         if (!h->bexec || key != h->bkey) {
             if (h->bexec) {
                 cudaGraphExecDestroy(h->bexec);
@@ -2080,8 +2087,8 @@ static evec_status run_batch(evec_handle h, int64_t count, const int64_t *n_host
             if (!h->cap_stream)
                 EVEC_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
             // launch attributes are set outside the capture
-            EVEC_CUDA(
-                launch_batched(nullptr, 0, nullptr, nullptr, h->nsm, h->cap_stream, slices, 0));
+            EVEC_CUDA(launch_batched(nullptr, 0, nullptr, nullptr, h->nsm, h->cap_stream, slices,
+                                     gen_tile));
             EVEC_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
             cudaError_t e = enqueue(h->cap_stream);
             cudaGraph_t graph = nullptr;
@@ -2157,7 +2164,7 @@ extern "C" evec_status evec_batched(evec_handle h, int64_t count, const int64_t 
     const size_t ndiag = (size_t)std::max<int64_t>(3 * rows, 1);
     {   // the same call as the last completed one: replay its graph
         const BatchKey &K = h->bcall;
-        bool same = K.valid && h->bexec && (int64_t)K.n.size() == count &&
+        bool same = K.valid && !K.gen && h->bexec && (int64_t)K.n.size() == count &&
                     K.T == (const void *)T_packed && K.X == (const void *)X_packed &&
                     K.E == (const void *)scale_exp_packed && K.lr == (const void *)lam_re_packed &&
                     K.li == (const void *)lam_im_packed && K.tile == tile && K.mode == mode &&
@@ -2269,6 +2276,10 @@ extern "C" evec_status evec_batched(evec_handle h, int64_t count, const int64_t 
         else K.sel.clear();
         K.diag.swap(diag_now);
         K.eacc = mtot;
+        K.gen = false;
+        K.T2 = nullptr;
+        K.beta = nullptr;
+        K.t2off.clear();
         K.valid = true;
     }
     if (opt && opt->check) return evec_sync(h, nullptr);
@@ -2306,7 +2317,8 @@ extern "C" evec_status evec_batched_generalized_count(
 
 // Batched pencils: S's and T's diagonals gathered (T's first, kept aside),
 // the pencil plans built on the host threads, one persistent launch of the
-// pencil variant.  No graph cache and no tile tuning: one tile for all
+// pencil variant, captured as a graph and replayed while the call stays the
+// same (as evec_batched).  No tile tuning: one tile for all
 // (default 64: the batch is bound by its largest pencils' step chains,
 // which fewer, larger tiles shorten -- 2x faster than 32 on the 2000-pencil
 // benchmark batch, 4x faster than 16).
@@ -2331,11 +2343,50 @@ extern "C" evec_status evec_batched_generalized(
         if (n_host[i] < 0 || t_off_host[i] < 0) return EVEC_EINVAL;
         rows += n_host[i];
     }
-    h->bcall.valid = false;
     const size_t ndiag = (size_t)std::max<int64_t>(3 * rows, 1);
     EVEC_TRY(batched_gather(h, count, n_host, T_packed, t_off_host));
     std::vector<double> diagT(h->diag_h, h->diag_h + ndiag);
     EVEC_TRY(batched_gather(h, count, n_host, S_packed, s_off_host));
+    {   // the same call as the last completed one: replay its graph, then
+        // the (alpha, beta) copies from the pinned plan buffer (unchanged)
+        const BatchKey &K = h->bcall;
+        bool same = K.valid && K.gen && h->bexec && (int64_t)K.n.size() == count &&
+                    K.T == (const void *)S_packed && K.T2 == (const void *)T_packed &&
+                    K.X == (const void *)X_packed && K.E == (const void *)scale_exp_packed &&
+                    K.lr == (const void *)alpha_re_packed &&
+                    K.li == (const void *)alpha_im_packed && K.beta == (const void *)beta_packed &&
+                    K.tile == tile && K.has_sel == (select_host != nullptr);
+        same = same && memcmp(K.n.data(), n_host, count * sizeof(int64_t)) == 0 &&
+               memcmp(K.toff.data(), s_off_host, count * sizeof(int64_t)) == 0 &&
+               memcmp(K.t2off.data(), t_off_host, count * sizeof(int64_t)) == 0;
+        same = same && (!select_host || memcmp(K.sel.data(), select_host, (size_t)rows) == 0) &&
+               K.diag.size() == 2 * ndiag &&
+               memcmp(K.diag.data(), h->diag_h, ndiag * sizeof(double)) == 0 &&
+               memcmp(K.diag.data() + ndiag, diagT.data(), ndiag * sizeof(double)) == 0;
+        if (same) {
+            cudaStream_t st = h->stream;
+            const int64_t eacc = K.eacc;
+            cudaError_t le = cudaSuccess;
+            timed(h, EVEC_K_BATCHED, [&] {
+                le = cudaGraphLaunch(h->bexec, st);
+                return 1;
+            });
+            EVEC_CUDA(le);
+            if (alpha_re_packed && eacc)
+                EVEC_CUDA(cudaMemcpyAsync(alpha_re_packed, h->bplan_h, eacc * 8,
+                                          cudaMemcpyHostToDevice, st));
+            if (alpha_im_packed && eacc)
+                EVEC_CUDA(cudaMemcpyAsync(alpha_im_packed, h->bplan_h + eacc * 8, eacc * 8,
+                                          cudaMemcpyHostToDevice, st));
+            if (beta_packed && eacc)
+                EVEC_CUDA(cudaMemcpyAsync(beta_packed, h->bplan_h + 2 * eacc * 8, eacc * 8,
+                                          cudaMemcpyHostToDevice, st));
+            if (opt && opt->check) return evec_sync(h, nullptr);
+            return EVEC_OK;
+        }
+    }
+    h->bcall.valid = false;
+    std::vector<double> diagS(h->diag_h, h->diag_h + ndiag);
     std::vector<int> tiles(count, tile), all(count);
     for (int64_t i = 0; i < count; i++) all[i] = (int)i;
     std::vector<HostPlan> &plans = h->bplans;
@@ -2350,8 +2401,37 @@ extern "C" evec_status evec_batched_generalized(
     }
     if (mtot > 0 && (!X_packed || !scale_exp_packed)) return EVEC_EINVAL;
     EVEC_TRY(run_batch(h, count, n_host, S_packed, s_off_host, all, plans, X_packed,
-                       scale_exp_packed, alpha_re_packed, alpha_im_packed, false, 0, T_packed,
+                       scale_exp_packed, alpha_re_packed, alpha_im_packed, true, 0, T_packed,
                        t_off_host, beta_packed, max_tile));
+    {   // remember this call for a replay
+        BatchKey &K = h->bcall;
+        K.gen = true;
+        K.n.assign(n_host, n_host + count);
+        K.toff.assign(s_off_host, s_off_host + count);
+        K.t2off.assign(t_off_host, t_off_host + count);
+        K.T = S_packed;
+        K.T2 = T_packed;
+        K.X = X_packed;
+        K.E = scale_exp_packed;
+        K.lr = alpha_re_packed;
+        K.li = alpha_im_packed;
+        K.beta = beta_packed;
+        K.Q = nullptr;
+        K.qoff.clear();
+        K.xoff.clear();
+        K.eoff.clear();
+        K.tile = tile;
+        K.mode = mode;
+        K.slices = 0;
+        K.tune.clear();
+        K.has_sel = select_host != nullptr;
+        if (select_host) K.sel.assign(select_host, select_host + rows);
+        else K.sel.clear();
+        K.diag.assign(diagS.begin(), diagS.end());
+        K.diag.insert(K.diag.end(), diagT.begin(), diagT.end());
+        K.eacc = mtot;
+        K.valid = true;
+    }
     if (opt && opt->check) return evec_sync(h, nullptr);
     return EVEC_OK;
 }

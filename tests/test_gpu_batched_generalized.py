@@ -126,3 +126,54 @@ def test_batched_pencils_errors():
     assert st == ev.EVEC_EINVAL
     # the handle stays usable
     _check(pairs, [None] * 3, ev.batched_generalized(pairs))
+
+
+def _unpack(ns, out):
+    X, e, ar, ai, be, m = out
+    res, xo, eo = [], 0, 0
+    for n, mi in zip(ns, m):
+        n, mi = int(n), int(mi)
+        res.append((X[xo:xo + n * mi].view(mi, n).t(), e[eo:eo + mi], ar[eo:eo + mi],
+                    ai[eo:eo + mi], be[eo:eo + mi]))
+        xo += n * mi
+        eo += mi
+    return res
+
+
+def test_batched_pencils_graph_replay():
+    """The same call again replays the captured launch (bit-identical);
+    new values off the three central diagonals keep the plans and are read
+    by the replay; new diagonal values rebuild the plans."""
+    sizes = workloads.batch_sizes(40, seed=77, lo=8, hi=300)
+    pairs, sels = _batch(sizes, seed=7700, fraction=0.4)
+    Sp, ns, soffs = ev.pack_batch([S for S, _ in pairs])
+    Tp, _, toffs = ev.pack_batch([T for _, T in pairs])
+    sel = np.concatenate([np.ascontiguousarray(s, dtype=np.uint8) for s in sels])
+    out = ev.batched_generalized_packed(Sp, Tp, ns, soffs, toffs, sel, check=True)
+    first = [t.clone() for t in out[:5]]
+    _check(pairs, sels, _unpack(ns, out))
+    out2 = ev.batched_generalized_packed(Sp, Tp, ns, soffs, toffs, sel, check=True, out=out)
+    for a, b in zip(first, out2[:5]):
+        assert torch.equal(a, b)
+    # halve every entry above the superdiagonal of S and T in place
+    pairs2 = []
+    for (S, T), so, to, n in zip(pairs, soffs, toffs, ns):
+        n = int(n)
+        S2, T2 = np.array(S, copy=True), np.array(T, copy=True)
+        iu = np.triu_indices(n, 2)
+        S2[iu] *= 0.5
+        T2[iu] *= 0.5
+        Sp[int(so):int(so) + n * n] = torch.from_numpy(np.asfortranarray(S2).ravel(order="F"))
+        Tp[int(to):int(to) + n * n] = torch.from_numpy(np.asfortranarray(T2).ravel(order="F"))
+        pairs2.append((S2, T2))
+    out3 = ev.batched_generalized_packed(Sp, Tp, ns, soffs, toffs, sel, check=True, out=out)
+    _check(pairs2, sels, _unpack(ns, out3))
+    # a new diagonal of T in the first pencil: new plans (beta changes)
+    S3, T3 = pairs2[0]
+    T3 = np.array(T3, copy=True)
+    n0 = int(ns[0])
+    T3[np.arange(n0), np.arange(n0)] *= 2.0
+    Tp[int(toffs[0]):int(toffs[0]) + n0 * n0] = torch.from_numpy(np.asfortranarray(T3).ravel(order="F"))
+    pairs3 = [(S3, T3)] + pairs2[1:]
+    out4 = ev.batched_generalized_packed(Sp, Tp, ns, soffs, toffs, sel, check=True, out=out)
+    _check(pairs3, sels, _unpack(ns, out4))
