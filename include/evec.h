@@ -493,29 +493,37 @@ evec_status evec_batched(evec_handle h, int64_t count, const int64_t *n_host,
 
 /*
  * Generalized right eigenvectors of a batch of pencils (S_i, T_i) (the
- * single-pencil computation of evec_generalized, without Z) in one
- * persistent launch of the pencil variant of the batched kernel: each CTA
- * takes whole pencils from the work queue, computes the norms of both
- * matrices, runs the diagonal-tile solves of (beta S - alpha T) and the
- * updates Y_r <- 2^dy Y_r - [S_rs (beta X~) - T_rs (alpha X~)] in FP64,
- * and writes the canonical form.  S_i, T_i (n_i x n_i, leading dimension
- * n_i) at S_packed + s_off_host[i] and T_packed + t_off_host[i], with the
- * requirements of evec_generalized.  Output packing as evec_batched (X_i at
- * sum_{k<i} n_k m_k; scale_exp_i, alpha_re_i, alpha_im_i, beta_i at
- * sum_{k<i} m_k; the last three may be NULL); m_i from
- * evec_batched_generalized_count.  opt->mode must be EVEC_FP64; opt->tile
- * 16..64, 0 = 64 (the solver holds both matrices' diagonal tiles: one CTA
- * per SM at 64).  As in evec_batched, the device part of the call is a
- * CUDA graph, replayed while the call is the same (layout, buffers,
- * selection, tile, and the three central diagonals of every S_i and T_i;
- * the entries above them may change); a call of
- * evec_batched_generalized_count in between ends the replay.  Device-side
+ * single-pencil computation of evec_generalized) in one persistent launch
+ * of the pencil variant of the batched kernel: each CTA takes whole
+ * pencils from the work queue, computes the norms of both matrices, runs
+ * the diagonal-tile solves of (beta S - alpha T) and the updates
+ * Y_r <- 2^dy Y_r - [S_rs (beta X~) - T_rs (alpha X~)] in FP64, and writes
+ * the canonical form.  S_i, T_i (n_i x n_i, leading dimension n_i) at
+ * S_packed + s_off_host[i] and T_packed + t_off_host[i], with the
+ * requirements of evec_generalized.
+ *   Z_packed (device, may be NULL) with z_off_host (host, count entries):
+ *     pencil i with z_off_host[i] >= 0 is back-transformed, X_i = Z_i Y_i
+ *     with Z_i (n_i x n_i, leading dimension n_i) at Z_packed +
+ *     z_off_host[i], by the CTA that solved it (FP64), then brought to
+ *     canonical form; z_off_host[i] < 0 (or Z_packed NULL) returns Y_i.
+ *     The handle keeps Y_i in its workspace.
+ * Output packing as evec_batched (X_i at sum_{k<i} n_k m_k; scale_exp_i,
+ * alpha_re_i, alpha_im_i, beta_i at sum_{k<i} m_k; the last three may be
+ * NULL); m_i from evec_batched_generalized_count.  opt->mode must be
+ * EVEC_FP64; opt->tile 16..64, 0 = 64 (the solver holds both matrices'
+ * diagonal tiles: one CTA per SM at 64).  As in evec_batched, the device
+ * part of the call is a CUDA graph, replayed while the call is the same
+ * (layout, buffers, offsets, selection, tile, and the three central
+ * diagonals of every S_i and T_i; the entries above them may change); a
+ * call of evec_batched_generalized_count in between ends the replay.
+ * Errors: EVEC_EINVAL also for Z_packed without z_off_host.  Device-side
  * errors (evec_sync / opt->check): index = element offset in S_packed or
  * T_packed of the offending entry.
  */
 evec_status evec_batched_generalized(evec_handle h, int64_t count, const int64_t *n_host,
                                      const double *S_packed, const int64_t *s_off_host,
                                      const double *T_packed, const int64_t *t_off_host,
+                                     const double *Z_packed, const int64_t *z_off_host,
                                      const uint8_t *select_host, double *X_packed,
                                      int32_t *scale_exp_packed, double *alpha_re_packed,
                                      double *alpha_im_packed, double *beta_packed,

@@ -108,7 +108,7 @@ def lib() -> ctypes.CDLL:
         L.evec_batched_generalized_count.argtypes = [p, i64, p, p, p, p, p, p, p]
         L.evec_batched.argtypes = [p, i64, p, p, p, p, p, p, p, p, p, p, p, p,
                                    ctypes.POINTER(_Opts)]
-        L.evec_batched_generalized.argtypes = [p, i64, p, p, p, p, p, p, p, p, p, p, p,
+        L.evec_batched_generalized.argtypes = [p, i64, p, p, p, p, p, p, p, p, p, p, p, p, p,
                                                ctypes.POINTER(_Opts)]
         L.evec_set_wait_limit.argtypes = [p, i64]
         L.evec_set_gate_factor.argtypes = [p, ctypes.c_double]
@@ -654,11 +654,13 @@ def batched(Ts, selects=None, tile: int = 0, mode: str = "fp64", check: bool = T
 
 
 def batched_generalized_packed(S_packed, T_packed, ns, s_offs, t_offs, select=None,
-                               tile: int = 0, check: bool = False, out=None):
+                               tile: int = 0, check: bool = False, out=None, Z_packed=None,
+                               z_offs=None):
     """evec_batched_generalized on packed device buffers (FP64).  Returns
     (X_packed, scale_exp, alpha_re, alpha_im, beta, m) with the output
     packing of evec_batched; out = that tuple from an earlier call on the
-    same layout skips the column count."""
+    same layout skips the column count.  Z_packed / z_offs: pencil i with
+    z_offs[i] >= 0 gets X_i = Z_i Y_i."""
     import torch
     h = handle(S_packed.device.index)
     ns = np.ascontiguousarray(ns, dtype=np.int64)
@@ -681,27 +683,42 @@ def batched_generalized_packed(S_packed, T_packed, ns, s_offs, t_offs, select=No
         ai = torch.empty(int(m.sum()), dtype=torch.float64, device=dev)
         be = torch.empty(int(m.sum()), dtype=torch.float64, device=dev)
     opts = _opts(tile, False, "fp64", 0)
+    zo = None if Z_packed is None else np.ascontiguousarray(z_offs, dtype=np.int64)
     st = lib().evec_batched_generalized(h.ptr, len(ns), _np_ptr(ns), S_packed.data_ptr(),
                                         _np_ptr(s_offs), T_packed.data_ptr(), _np_ptr(t_offs),
-                                        _np_ptr(sel), X.data_ptr(), e.data_ptr(), ar.data_ptr(),
-                                        ai.data_ptr(), be.data_ptr(), ctypes.byref(opts))
+                                        None if Z_packed is None else Z_packed.data_ptr(),
+                                        _np_ptr(zo), _np_ptr(sel), X.data_ptr(), e.data_ptr(),
+                                        ar.data_ptr(), ai.data_ptr(), be.data_ptr(),
+                                        ctypes.byref(opts))
     _check(st, "evec_batched_generalized")
     if check:
         h.sync()
     return X, e, ar, ai, be, m
 
 
-def batched_generalized(pairs, selects=None, tile: int = 0, check: bool = True):
+def batched_generalized(pairs, selects=None, tile: int = 0, check: bool = True, Zs=None):
     """Generalized eigenvectors of a list of pencils [(S_i, T_i), ...] (numpy
-    or torch matrices, packed here) in one persistent launch (FP64).  Returns
-    a list of (X_i (n_i, m_i), scale_exp_i, alpha_re_i, alpha_im_i, beta_i)."""
+    or torch matrices, packed here) in one persistent launch (FP64); Zs (a
+    list with a matrix or None per pencil): X_i = Z_i Y_i.  Returns a list
+    of (X_i (n_i, m_i), scale_exp_i, alpha_re_i, alpha_im_i, beta_i)."""
     Sp, ns, soffs = pack_batch([S for S, _ in pairs])
     Tp, _, toffs = pack_batch([T for _, T in pairs])
+    Zp = zoffs = None
+    if Zs is not None and any(z is not None for z in Zs):
+        have = [z for z in Zs if z is not None]
+        Zp, _, zo = pack_batch(have)
+        zoffs = np.full(len(pairs), -1, dtype=np.int64)
+        j = 0
+        for i, z in enumerate(Zs):
+            if z is not None:
+                zoffs[i] = zo[j]
+                j += 1
     sel = None
     if selects is not None:
         sel = np.concatenate([np.ones(n, np.uint8) if s is None else
                               np.ascontiguousarray(s, dtype=np.uint8) for s, n in zip(selects, ns)])
-    X, e, ar, ai, be, m = batched_generalized_packed(Sp, Tp, ns, soffs, toffs, sel, tile, check)
+    X, e, ar, ai, be, m = batched_generalized_packed(Sp, Tp, ns, soffs, toffs, sel, tile, check,
+                                                     Z_packed=Zp, z_offs=zoffs)
     out = []
     xo = eo = 0
     for n, mi in zip(ns, m):

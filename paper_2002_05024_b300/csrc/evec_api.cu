@@ -1940,7 +1940,7 @@ static evec_status run_batch(evec_handle h, int64_t count, const int64_t *n_host
         xacc += n_host[i] * plans[i].m;
         eacc += plans[i].m;
     }
-    auto has_q = [&](int64_t i) { return !gen && bo.Q && bo.q_off && bo.q_off[i] >= 0; };
+    auto has_q = [&](int64_t i) { return bo.Q && bo.q_off && bo.q_off[i] >= 0; };
     std::vector<std::pair<double, int>> order;
     for (int i : idx) {
         const HostPlan &P = plans[i];
@@ -2122,6 +2122,12 @@ static evec_status run_batch(evec_handle h, int64_t count, const int64_t *n_host
 
 }  // namespace evec
 
+// a remembered offset array against this call's (null: none given)
+static bool same_offsets(const std::vector<int64_t> &v, const int64_t *a, int64_t count) {
+    return a ? (v.size() == (size_t)count && memcmp(v.data(), a, count * sizeof(int64_t)) == 0)
+             : v.empty();
+}
+
 extern "C" evec_status evec_batched(evec_handle h, int64_t count, const int64_t *n_host,
                                     const double *T_packed, const int64_t *t_off_host,
                                     const double *Q_packed, const int64_t *q_off_host,
@@ -2141,9 +2147,7 @@ extern "C" evec_status evec_batched(evec_handle h, int64_t count, const int64_t 
     bo.x_off = x_off_host;
     bo.e_off = e_off_host;
     auto same_offs = [&](const std::vector<int64_t> &v, const int64_t *a) {
-        return a ? (v.size() == (size_t)count &&
-                    memcmp(v.data(), a, count * sizeof(int64_t)) == 0)
-                 : v.empty();
+        return same_offsets(v, a, count);
     };
     const int mode = opt ? opt->mode : EVEC_FP64;
     if (mode != EVEC_FP64 && mode != EVEC_SPLIT) return EVEC_EINVAL;
@@ -2325,9 +2329,9 @@ extern "C" evec_status evec_batched_generalized_count(
 extern "C" evec_status evec_batched_generalized(
     evec_handle h, int64_t count, const int64_t *n_host, const double *S_packed,
     const int64_t *s_off_host, const double *T_packed, const int64_t *t_off_host,
-    const uint8_t *select_host, double *X_packed, int32_t *scale_exp_packed,
-    double *alpha_re_packed, double *alpha_im_packed, double *beta_packed,
-    const evec_opts *opt) {
+    const double *Z_packed, const int64_t *z_off_host, const uint8_t *select_host,
+    double *X_packed, int32_t *scale_exp_packed, double *alpha_re_packed,
+    double *alpha_im_packed, double *beta_packed, const evec_opts *opt) {
     if (!h || count < 0 || count > INT32_MAX ||
         (count > 0 && (!n_host || !s_off_host || !t_off_host || !S_packed || !T_packed)))
         return EVEC_EINVAL;
@@ -2335,6 +2339,7 @@ extern "C" evec_status evec_batched_generalized(
     if (mode != EVEC_FP64) return EVEC_EINVAL;
     const int tile = (opt && opt->tile) ? opt->tile : 64;
     if (tile < 16 || tile > 64) return EVEC_EINVAL;
+    if (Z_packed && !z_off_host) return EVEC_EINVAL;
     if (count == 0) return EVEC_OK;
     DeviceGuard g(h->device);
     if (!g.ok) return EVEC_ECUDA;
@@ -2342,6 +2347,11 @@ extern "C" evec_status evec_batched_generalized(
     for (int64_t i = 0; i < count; i++) {
         if (n_host[i] < 0 || t_off_host[i] < 0) return EVEC_EINVAL;
         rows += n_host[i];
+    }
+    BatchOut bo;
+    if (Z_packed) {
+        bo.Q = Z_packed;
+        bo.q_off = z_off_host;
     }
     const size_t ndiag = (size_t)std::max<int64_t>(3 * rows, 1);
     EVEC_TRY(batched_gather(h, count, n_host, T_packed, t_off_host));
@@ -2355,7 +2365,8 @@ extern "C" evec_status evec_batched_generalized(
                     K.X == (const void *)X_packed && K.E == (const void *)scale_exp_packed &&
                     K.lr == (const void *)alpha_re_packed &&
                     K.li == (const void *)alpha_im_packed && K.beta == (const void *)beta_packed &&
-                    K.tile == tile && K.has_sel == (select_host != nullptr);
+                    K.tile == tile && K.has_sel == (select_host != nullptr) &&
+                    K.Q == (const void *)Z_packed && same_offsets(K.qoff, bo.q_off, count);
         same = same && memcmp(K.n.data(), n_host, count * sizeof(int64_t)) == 0 &&
                memcmp(K.toff.data(), s_off_host, count * sizeof(int64_t)) == 0 &&
                memcmp(K.t2off.data(), t_off_host, count * sizeof(int64_t)) == 0;
@@ -2402,7 +2413,7 @@ extern "C" evec_status evec_batched_generalized(
     if (mtot > 0 && (!X_packed || !scale_exp_packed)) return EVEC_EINVAL;
     EVEC_TRY(run_batch(h, count, n_host, S_packed, s_off_host, all, plans, X_packed,
                        scale_exp_packed, alpha_re_packed, alpha_im_packed, true, 0, T_packed,
-                       t_off_host, beta_packed, max_tile));
+                       t_off_host, beta_packed, max_tile, bo));
     {   // remember this call for a replay
         BatchKey &K = h->bcall;
         K.gen = true;
@@ -2416,8 +2427,9 @@ extern "C" evec_status evec_batched_generalized(
         K.lr = alpha_re_packed;
         K.li = alpha_im_packed;
         K.beta = beta_packed;
-        K.Q = nullptr;
-        K.qoff.clear();
+        K.Q = Z_packed;
+        if (Z_packed) K.qoff.assign(z_off_host, z_off_host + count);
+        else K.qoff.clear();
         K.xoff.clear();
         K.eoff.clear();
         K.tile = tile;

@@ -700,10 +700,10 @@ __global__ void __launch_bounds__(kBThreads)
                         if (B.lam_im) B.lam_im[col + 1] = -im;
                     }
                 }
-            if (B.Q) {
-                cta_backtransform(B, smem, sred);
-                __syncthreads();
-            }
+        }
+        if (B.Q) {   // X = Q Y (pencils: Z Y) and the canonical form
+            cta_backtransform(B, smem, sred);
+            __syncthreads();
         }
     }
     if constexpr (SPLIT) {

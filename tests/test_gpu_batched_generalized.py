@@ -30,11 +30,12 @@ def _batch(sizes, seed, fraction=None):
     return pairs, sels
 
 
-def _check(pairs, sels, outs, rel_tol=1e-10):
+def _check(pairs, sels, outs, rel_tol=1e-10, Zs=None):
     worst = 0.0
-    for (S, T), sel, out in zip(pairs, sels, outs):
+    for i, ((S, T), sel, out) in enumerate(zip(pairs, sels, outs)):
         X, e, ar, ai, be = (t.cpu().numpy() for t in out)
-        Xo, eo, aro, aio, beo = oracle.generalized(S, T, select=sel)
+        Z = None if Zs is None else Zs[i]
+        Xo, eo, aro, aio, beo = oracle.generalized(S, T, Z, select=sel)
         assert X.shape == Xo.shape
         if Xo.shape[1] == 0:
             continue
@@ -47,7 +48,7 @@ def _check(pairs, sels, outs, rel_tol=1e-10):
         de, rel = compare_canonical(Xo, eo, X, e, aio)
         assert de <= 1, de
         worst = max(worst, rel)
-        r = generalized_residuals(S, T, X, ar, ai, be)
+        r = generalized_residuals(S, T, X if Z is None else Z.T @ X, ar, ai, be)
         assert r.max() <= 10 * S.shape[0], r.max()
     assert worst <= rel_tol, worst
     return worst
@@ -121,7 +122,7 @@ def test_batched_pencils_errors():
     opts = ev._opts(0, False, "split", 0)
     st = ev.lib().evec_batched_generalized(h.ptr, 3, ev._np_ptr(ns), Sp.data_ptr(),
                                            ev._np_ptr(offs), Tp.data_ptr(), ev._np_ptr(offs),
-                                           None, None, None, None, None, None,
+                                           None, None, None, None, None, None, None, None,
                                            ctypes.byref(opts))
     assert st == ev.EVEC_EINVAL
     # the handle stays usable
@@ -177,3 +178,24 @@ def test_batched_pencils_graph_replay():
     pairs3 = [(S3, T3)] + pairs2[1:]
     out4 = ev.batched_generalized_packed(Sp, Tp, ns, soffs, toffs, sel, check=True, out=out)
     _check(pairs3, sels, _unpack(ns, out4))
+
+
+def test_batched_pencils_with_z():
+    """X_i = Z_i Y_i for the pencils given a Z (every other one), Y_i for the
+    rest; against the oracle's back-transformed vectors."""
+    sizes = workloads.batch_sizes(30, seed=88, lo=8, hi=260)
+    pairs, sels = _batch(sizes, seed=8800, fraction=0.5)
+    Zs = [workloads.householder_orthogonal(int(n), seed=8900 + i) if i % 2 == 0 else None
+          for i, n in enumerate(sizes)]
+    outs = ev.batched_generalized(pairs, sels, Zs=Zs)
+    _check(pairs, sels, outs, Zs=Zs)
+    # Z_packed without offsets is refused
+    Sp, ns, offs = ev.pack_batch([S for S, _ in pairs])
+    Tp, _, _ = ev.pack_batch([T for _, T in pairs])
+    h = ev.handle(0)
+    opts = ev._opts(0, False, "fp64", 0)
+    st = ev.lib().evec_batched_generalized(h.ptr, len(ns), ev._np_ptr(ns), Sp.data_ptr(),
+                                           ev._np_ptr(offs), Tp.data_ptr(), ev._np_ptr(offs),
+                                           Sp.data_ptr(), None, None, None, None, None, None,
+                                           None, ctypes.byref(opts))
+    assert st == ev.EVEC_EINVAL
