@@ -1359,7 +1359,8 @@ def run_batched_generalized(args, rank, world, local_rank):
         "config": {"workload": f"batch of {args.batch} pencils, n log-uniform in [32, 1024] "
                                "(S config-0, T diag U[0.5, 2] with every 50th 1e-12), 30% of "
                                "blocks selected, no Z, one persistent launch per step",
-                   "matrices": args.batch, "columns": cols, "tile": args.tile or 64,
+                   "matrices": args.batch, "columns": cols, "tile": args.tile or "tuned",
+                   "tile_table": ev.tune_table(local_rank, "pencil"),
                    "mode": "fp64", "parallelism": "replicas",
                    "l2": f"inputs {(Sp.numel() + Tp.numel()) * 8 / 2**30:.1f} GiB, larger "
                          "than L2"},

@@ -510,8 +510,12 @@ evec_status evec_batched(evec_handle h, int64_t count, const int64_t *n_host,
  * Output packing as evec_batched (X_i at sum_{k<i} n_k m_k; scale_exp_i,
  * alpha_re_i, alpha_im_i, beta_i at sum_{k<i} m_k; the last three may be
  * NULL); m_i from evec_batched_generalized_count.  opt->mode must be
- * EVEC_FP64; opt->tile 16..64, 0 = 64 (the solver holds both matrices'
- * diagonal tiles: one CTA per SM at 64).  As in evec_batched, the device
+ * EVEC_FP64; opt->tile 16..64 for every pencil (the solver holds both
+ * matrices' diagonal tiles: one CTA per SM at 64), or 0 = the tile of
+ * each pencil's size class from the handle's pencil table
+ * (EVEC_TUNE_PENCIL), tuned on first use of a class by timing 16, 32 and
+ * 64 on up to eight of the batch's pencils of that class.  As in
+ * evec_batched, the device
  * part of the call is a CUDA graph, replayed while the call is the same
  * (layout, buffers, offsets, selection, tile, and the three central
  * diagonals of every S_i and T_i; the entries above them may change); a
@@ -539,8 +543,13 @@ evec_status evec_batched_generalized_count(evec_handle h, int64_t count, const i
 /* Size classes of the tile table: n <= 64, <= 128, <= 256, <= 512, larger. */
 #define EVEC_SIZE_CLASSES 5
 
-/* The handle's tile table (mode = evec_mode, size_class < EVEC_SIZE_CLASSES);
- * tile 0 = not tuned yet.  evec_tune_set accepts 0 (forget) or 16..64. */
+/* The table of batched pencils (evec_batched_generalized, FP64) in
+ * evec_tune_get / evec_tune_set. */
+#define EVEC_TUNE_PENCIL 2
+
+/* The handle's tile tables (mode = evec_mode for evec_batched, or
+ * EVEC_TUNE_PENCIL; size_class < EVEC_SIZE_CLASSES); tile 0 = not tuned
+ * yet.  evec_tune_set accepts 0 (forget) or 16..64. */
 evec_status evec_tune_get(evec_handle h, int mode, int size_class, int *tile);
 evec_status evec_tune_set(evec_handle h, int mode, int size_class, int tile);
 

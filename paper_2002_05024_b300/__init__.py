@@ -730,13 +730,18 @@ def batched_generalized(pairs, selects=None, tile: int = 0, check: bool = True, 
     return out
 
 
+TUNE_TABLES = {"fp64": 0, "split": 1, "pencil": 2}   # "pencil": EVEC_TUNE_PENCIL
+
+
 def tune_table(device: int = 0, mode: str = "fp64"):
-    """The handle's tile per size class (0 = not tuned yet)."""
+    """The handle's tile per size class (0 = not tuned yet); mode "fp64" or
+    "split" (evec_batched) or "pencil" (evec_batched_generalized)."""
     h = handle(device)
     out = []
     for c in range(SIZE_CLASSES):
         t = ctypes.c_int(0)
-        _check(lib().evec_tune_get(h.ptr, MODES[mode], c, ctypes.byref(t)), "evec_tune_get")
+        _check(lib().evec_tune_get(h.ptr, TUNE_TABLES[mode], c, ctypes.byref(t)),
+               "evec_tune_get")
         out.append(t.value)
     return out
 
@@ -745,4 +750,4 @@ def set_tune_table(table, device: int = 0, mode: str = "fp64"):
     """Load a tile table (e.g. one saved as JSON by an earlier run)."""
     h = handle(device)
     for c, t in enumerate(table):
-        _check(lib().evec_tune_set(h.ptr, MODES[mode], c, int(t)), "evec_tune_set")
+        _check(lib().evec_tune_set(h.ptr, TUNE_TABLES[mode], c, int(t)), "evec_tune_set")

@@ -631,7 +631,7 @@ struct evec_ctx {
     unsigned char *bplan_d = nullptr; size_t bplan_cap = 0;
     unsigned char *bplan_h = nullptr; size_t bplan_h_cap = 0;
     int *queue_d = nullptr;
-    int tune[2][EVEC_SIZE_CLASSES] = {{0}};
+    int tune[3][EVEC_SIZE_CLASSES] = {{0}};   // FP64, split, pencils (EVEC_TUNE_PENCIL)
     cudaStream_t cap_stream = nullptr;
     // evec_standard_host: Q's copy (q_src, q_bytes) is issued by
     // evec_standard on copy_stream once its own small copies are queued
@@ -2337,8 +2337,8 @@ extern "C" evec_status evec_batched_generalized(
         return EVEC_EINVAL;
     const int mode = opt ? opt->mode : EVEC_FP64;
     if (mode != EVEC_FP64) return EVEC_EINVAL;
-    const int tile = (opt && opt->tile) ? opt->tile : 64;
-    if (tile < 16 || tile > 64) return EVEC_EINVAL;
+    const int tile = opt ? opt->tile : 0;   // 0: the tuned tile of each size class
+    if (tile != 0 && (tile < 16 || tile > 64)) return EVEC_EINVAL;
     if (Z_packed && !z_off_host) return EVEC_EINVAL;
     if (count == 0) return EVEC_OK;
     DeviceGuard g(h->device);
@@ -2367,6 +2367,9 @@ extern "C" evec_status evec_batched_generalized(
                     K.li == (const void *)alpha_im_packed && K.beta == (const void *)beta_packed &&
                     K.tile == tile && K.has_sel == (select_host != nullptr) &&
                     K.Q == (const void *)Z_packed && same_offsets(K.qoff, bo.q_off, count);
+        if (same && tile == 0)
+            for (int c = 0; c < EVEC_SIZE_CLASSES; c++)
+                same = same && K.tune[c] == h->tune[EVEC_TUNE_PENCIL][c];
         same = same && memcmp(K.n.data(), n_host, count * sizeof(int64_t)) == 0 &&
                memcmp(K.toff.data(), s_off_host, count * sizeof(int64_t)) == 0 &&
                memcmp(K.t2off.data(), t_off_host, count * sizeof(int64_t)) == 0;
@@ -2398,19 +2401,74 @@ extern "C" evec_status evec_batched_generalized(
     }
     h->bcall.valid = false;
     std::vector<double> diagS(h->diag_h, h->diag_h + ndiag);
-    std::vector<int> tiles(count, tile), all(count);
+    std::vector<int> tiles(count, tile ? tile : 64), all(count);
     for (int64_t i = 0; i < count; i++) all[i] = (int)i;
     std::vector<HostPlan> &plans = h->bplans;
     int64_t bad = -1;
     EVEC_TRY(batched_build(h, count, n_host, s_off_host, select_host, tiles, all, plans, &bad,
                            diagT.data()));
     int64_t mtot = 0;
-    int max_tile = 16;
-    for (int64_t i = 0; i < count; i++) {
-        mtot += plans[i].m;
-        max_tile = std::max(max_tile, plans[i].max_tile);
-    }
+    for (int64_t i = 0; i < count; i++) mtot += plans[i].m;
     if (mtot > 0 && (!X_packed || !scale_exp_packed)) return EVEC_EINVAL;
+    auto largest_tile = [](const std::vector<HostPlan> &pl, const std::vector<int> &ids) {
+        int t = 16;
+        for (int i : ids) t = std::max(t, pl[i].max_tile);
+        return t;
+    };
+    if (tile == 0) {
+        // the tile of each size class: tuned on first use by timing the
+        // candidates on up to eight of the batch's pencils of the class
+        int *tab = h->tune[EVEC_TUNE_PENCIL];
+        for (int c = 0; c < EVEC_SIZE_CLASSES; c++) {
+            std::vector<int> members;
+            for (int64_t i = 0; i < count; i++)
+                if (size_class(n_host[i]) == c && plans[i].m > 0) members.push_back((int)i);
+            if (members.empty() || tab[c]) continue;
+            std::sort(members.begin(), members.end(),
+                      [&](int a, int b) { return n_host[a] > n_host[b]; });
+            if (members.size() > 8) members.resize(8);
+            double best_ms = 0.0;
+            int best = 64;
+            for (int cand : {16, 32, 64}) {
+                std::vector<int> tl(count, cand);
+                std::vector<HostPlan> tp;
+                EVEC_TRY(batched_build(h, count, n_host, s_off_host, select_host, tl, members, tp,
+                                       &bad, diagT.data()));
+                cudaEvent_t a = nullptr, b = nullptr;
+                EVEC_CUDA(cudaEventCreate(&a));
+                EVEC_CUDA(cudaEventCreate(&b));
+                cudaEventRecord(a, h->stream);
+                evec_status st = run_batch(h, count, n_host, S_packed, s_off_host, members, tp,
+                                           X_packed, scale_exp_packed, nullptr, nullptr, false,
+                                           0, T_packed, t_off_host, nullptr,
+                                           largest_tile(tp, members));
+                cudaEventRecord(b, h->stream);
+                cudaEventSynchronize(b);
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, a, b);
+                cudaEventDestroy(a);
+                cudaEventDestroy(b);
+                EVEC_TRY(st);
+                if (best_ms == 0.0 || ms < best_ms) {
+                    best_ms = ms;
+                    best = cand;
+                }
+            }
+            tab[c] = best;
+        }
+        bool rebuild = false;
+        for (int64_t i = 0; i < count; i++) {
+            const int t = tab[size_class(n_host[i])];
+            if (t && t != tiles[i]) {
+                tiles[i] = t;
+                rebuild = true;
+            }
+        }
+        if (rebuild)
+            EVEC_TRY(batched_build(h, count, n_host, s_off_host, select_host, tiles, all, plans,
+                                   &bad, diagT.data()));
+    }
+    const int max_tile = largest_tile(plans, all);
     EVEC_TRY(run_batch(h, count, n_host, S_packed, s_off_host, all, plans, X_packed,
                        scale_exp_packed, alpha_re_packed, alpha_im_packed, true, 0, T_packed,
                        t_off_host, beta_packed, max_tile, bo));
@@ -2435,7 +2493,7 @@ extern "C" evec_status evec_batched_generalized(
         K.tile = tile;
         K.mode = mode;
         K.slices = 0;
-        K.tune.clear();
+        K.tune.assign(h->tune[EVEC_TUNE_PENCIL], h->tune[EVEC_TUNE_PENCIL] + EVEC_SIZE_CLASSES);
         K.has_sel = select_host != nullptr;
         if (select_host) K.sel.assign(select_host, select_host + rows);
         else K.sel.clear();
@@ -2495,14 +2553,16 @@ extern "C" evec_status evec_hessenberg(evec_handle h, int64_t n, double *A, int6
 }
 
 extern "C" evec_status evec_tune_get(evec_handle h, int mode, int size_class, int *tile) {
-    if (!h || !tile || mode < 0 || mode > 1 || size_class < 0 || size_class >= EVEC_SIZE_CLASSES)
+    if (!h || !tile || mode < 0 || mode > EVEC_TUNE_PENCIL || size_class < 0 ||
+        size_class >= EVEC_SIZE_CLASSES)
         return EVEC_EINVAL;
     *tile = h->tune[mode][size_class];
     return EVEC_OK;
 }
 
 extern "C" evec_status evec_tune_set(evec_handle h, int mode, int size_class, int tile) {
-    if (!h || mode < 0 || mode > 1 || size_class < 0 || size_class >= EVEC_SIZE_CLASSES ||
+    if (!h || mode < 0 || mode > EVEC_TUNE_PENCIL || size_class < 0 ||
+        size_class >= EVEC_SIZE_CLASSES ||
         (tile != 0 && (tile < 16 || tile > 64)))
         return EVEC_EINVAL;
     h->tune[mode][size_class] = tile;

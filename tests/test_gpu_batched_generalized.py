@@ -199,3 +199,28 @@ def test_batched_pencils_with_z():
                                            Sp.data_ptr(), None, None, None, None, None, None,
                                            None, ctypes.byref(opts))
     assert st == ev.EVEC_EINVAL
+
+
+def test_batched_pencils_tile_tuning():
+    """tile 0: each size class gets the fastest of 16 / 32 / 64 on its first
+    use (timed on up to eight of its pencils); the tuned batch matches the
+    oracle; a table set by hand is used as given."""
+    h = ev.handle(0)
+    for c in range(ev.SIZE_CLASSES):
+        assert ev.lib().evec_tune_set(h.ptr, 2, c, 0) == ev.EVEC_OK
+    sizes = workloads.batch_sizes(40, seed=99, lo=16, hi=600)
+    pairs, sels = _batch(sizes, seed=9900, fraction=0.5)
+    outs = ev.batched_generalized(pairs, sels)
+    table = ev.tune_table(0, "pencil")
+    classes = {0 if n <= 64 else 1 if n <= 128 else 2 if n <= 256 else 3 if n <= 512 else 4
+               for n in sizes}
+    for c in range(ev.SIZE_CLASSES):
+        assert (table[c] in (16, 32, 64)) if c in classes else table[c] == 0, table
+    _check(pairs, sels, outs)
+    ev.set_tune_table([16] * ev.SIZE_CLASSES, 0, "pencil")
+    assert ev.tune_table(0, "pencil") == [16] * ev.SIZE_CLASSES
+    _check(pairs, sels, ev.batched_generalized(pairs, sels))
+    with pytest.raises(ev.EvecError):
+        ev.set_tune_table([100] * ev.SIZE_CLASSES, 0, "pencil")
+    for c in range(ev.SIZE_CLASSES):
+        assert ev.lib().evec_tune_set(h.ptr, 2, c, 0) == ev.EVEC_OK
