@@ -545,7 +545,9 @@ def run_reference_other(args):
             _, mats, sels = workloads.batch_pencils(args.batch)
             run = lambda i: oracle.generalized(mats[i][0], mats[i][1],  # noqa: E731
                                                select=sels[i])[0].shape[1]
-            metric = "eigvec columns/s, batched pencils (robust FP64 generalized eigenvectors)"
+            metric = ("eigvec columns/s, batched pencils (robust "
+                      + ("generalized eigenvectors, split-precision updates)"
+                         if args.mode == "split" else "FP64 generalized eigenvectors)"))
             what = f"batch of {args.batch} pencils, n log-uniform in [32, 1024]"
         per = max(8, min(len(mats), 50))
         for i in range(args.warmup + args.steps):
@@ -1259,7 +1261,8 @@ def run_batched_generalized(args, rank, world, local_rank):
     Sp, ns, soffs = ev.pack_batch([S for S, _ in pairs], device=local_rank)
     Tp, _, toffs = ev.pack_batch([T for _, T in pairs], device=local_rank)
     sel = np.concatenate(sels)
-    out = ev.batched_generalized_packed(Sp, Tp, ns, soffs, toffs, sel, tile=args.tile)
+    out = ev.batched_generalized_packed(Sp, Tp, ns, soffs, toffs, sel, tile=args.tile,
+                                        mode=args.mode, slices=args.slices)
     m = out[5]
     cols = int(m.sum())
     F = 0.0
@@ -1273,7 +1276,8 @@ def run_batched_generalized(args, rank, world, local_rank):
             i += sz
 
     def step():
-        ev.batched_generalized_packed(Sp, Tp, ns, soffs, toffs, sel, tile=args.tile, out=out)
+        ev.batched_generalized_packed(Sp, Tp, ns, soffs, toffs, sel, tile=args.tile, out=out,
+                                      mode=args.mode, slices=args.slices)
 
     for _ in range(args.warmup):
         step()
@@ -1352,16 +1356,21 @@ def run_batched_generalized(args, rank, world, local_rank):
                "sample": f"{len(pick)} randomly chosen pencils of the batch ({cc} columns), "
                          f"{dt:.2f} s"}
     line = {
-        "metric": "eigvec columns/s, batched pencils (robust FP64 generalized eigenvectors)",
+        "metric": "eigvec columns/s, batched pencils (robust "
+                  + ("generalized eigenvectors, split-precision updates)" if args.mode == "split"
+                     else "FP64 generalized eigenvectors)"),
         "value": value, "unit": "columns/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16 slice products + f64" if args.mode == "split" else "f64",
+        "data": "synthetic",
         "config": {"workload": f"batch of {args.batch} pencils, n log-uniform in [32, 1024] "
                                "(S config-0, T diag U[0.5, 2] with every 50th 1e-12), 30% of "
                                "blocks selected, no Z, one persistent launch per step",
-                   "matrices": args.batch, "columns": cols, "tile": args.tile or "tuned",
+                   "matrices": args.batch, "columns": cols,
+                   "tile": args.tile or ("tuned" if args.mode == "fp64" else 64),
                    "tile_table": ev.tune_table(local_rank, "pencil"),
-                   "mode": "fp64", "parallelism": "replicas",
+                   "mode": args.mode, "parallelism": "replicas",
                    "l2": f"inputs {(Sp.numel() + Tp.numel()) * 8 / 2**30:.1f} GiB, larger "
                          "than L2"},
         "tflops_fp64": F * args.steps / (elapsed / 1e3) / 1e12,

@@ -509,12 +509,17 @@ evec_status evec_batched(evec_handle h, int64_t count, const int64_t *n_host,
  *     The handle keeps Y_i in its workspace.
  * Output packing as evec_batched (X_i at sum_{k<i} n_k m_k; scale_exp_i,
  * alpha_re_i, alpha_im_i, beta_i at sum_{k<i} m_k; the last three may be
- * NULL); m_i from evec_batched_generalized_count.  opt->mode must be
- * EVEC_FP64; opt->tile 16..64 for every pencil (the solver holds both
- * matrices' diagonal tiles: one CTA per SM at 64), or 0 = the tile of
- * each pencil's size class from the handle's pencil table
- * (EVEC_TUNE_PENCIL), tuned on first use of a class by timing 16, 32 and
- * 64 on up to eight of the batch's pencils of that class.  As in
+ * NULL); m_i from evec_batched_generalized_count.  opt->mode: EVEC_FP64,
+ * or EVEC_SPLIT (opt->slices digit slices, 2..8; 0 = 8): each update as
+ * one split product of the rows [S_rs T_rs] against the 2K-row right-hand
+ * side [beta X~; -alpha X~] on the tensor cores inside the persistent
+ * kernel; the diagonal solves, decisions, back-transformation and
+ * canonical form stay FP64.  opt->tile 16..64 for every pencil (the solver
+ * holds both matrices' diagonal tiles: one CTA per SM at 64), or 0 = in
+ * EVEC_FP64 mode the tile of each pencil's size class from the handle's
+ * pencil table (EVEC_TUNE_PENCIL), tuned on first use of a class by timing
+ * 16, 32 and 64 on up to eight of the batch's pencils of that class; in
+ * EVEC_SPLIT mode 64.  As in
  * evec_batched, the device
  * part of the call is a CUDA graph, replayed while the call is the same
  * (layout, buffers, offsets, selection, tile, and the three central

@@ -655,12 +655,13 @@ def batched(Ts, selects=None, tile: int = 0, mode: str = "fp64", check: bool = T
 
 def batched_generalized_packed(S_packed, T_packed, ns, s_offs, t_offs, select=None,
                                tile: int = 0, check: bool = False, out=None, Z_packed=None,
-                               z_offs=None):
+                               z_offs=None, mode: str = "fp64", slices: int = 0):
     """evec_batched_generalized on packed device buffers (FP64).  Returns
     (X_packed, scale_exp, alpha_re, alpha_im, beta, m) with the output
     packing of evec_batched; out = that tuple from an earlier call on the
     same layout skips the column count.  Z_packed / z_offs: pencil i with
-    z_offs[i] >= 0 gets X_i = Z_i Y_i."""
+    z_offs[i] >= 0 gets X_i = Z_i Y_i.  mode "split": the updates as split
+    products on the tensor cores."""
     import torch
     h = handle(S_packed.device.index)
     ns = np.ascontiguousarray(ns, dtype=np.int64)
@@ -682,7 +683,7 @@ def batched_generalized_packed(S_packed, T_packed, ns, s_offs, t_offs, select=No
         ar = torch.empty(int(m.sum()), dtype=torch.float64, device=dev)
         ai = torch.empty(int(m.sum()), dtype=torch.float64, device=dev)
         be = torch.empty(int(m.sum()), dtype=torch.float64, device=dev)
-    opts = _opts(tile, False, "fp64", 0)
+    opts = _opts(tile, False, mode, slices)
     zo = None if Z_packed is None else np.ascontiguousarray(z_offs, dtype=np.int64)
     st = lib().evec_batched_generalized(h.ptr, len(ns), _np_ptr(ns), S_packed.data_ptr(),
                                         _np_ptr(s_offs), T_packed.data_ptr(), _np_ptr(t_offs),
@@ -696,7 +697,8 @@ def batched_generalized_packed(S_packed, T_packed, ns, s_offs, t_offs, select=No
     return X, e, ar, ai, be, m
 
 
-def batched_generalized(pairs, selects=None, tile: int = 0, check: bool = True, Zs=None):
+def batched_generalized(pairs, selects=None, tile: int = 0, check: bool = True, Zs=None,
+                        mode: str = "fp64", slices: int = 0):
     """Generalized eigenvectors of a list of pencils [(S_i, T_i), ...] (numpy
     or torch matrices, packed here) in one persistent launch (FP64); Zs (a
     list with a matrix or None per pencil): X_i = Z_i Y_i.  Returns a list
@@ -718,7 +720,8 @@ def batched_generalized(pairs, selects=None, tile: int = 0, check: bool = True, 
         sel = np.concatenate([np.ones(n, np.uint8) if s is None else
                               np.ascontiguousarray(s, dtype=np.uint8) for s, n in zip(selects, ns)])
     X, e, ar, ai, be, m = batched_generalized_packed(Sp, Tp, ns, soffs, toffs, sel, tile, check,
-                                                     Z_packed=Zp, z_offs=zoffs)
+                                                     Z_packed=Zp, z_offs=zoffs, mode=mode,
+                                                     slices=slices)
     out = []
     xo = eo = 0
     for n, mi in zip(ns, m):

@@ -2336,8 +2336,11 @@ extern "C" evec_status evec_batched_generalized(
         (count > 0 && (!n_host || !s_off_host || !t_off_host || !S_packed || !T_packed)))
         return EVEC_EINVAL;
     const int mode = opt ? opt->mode : EVEC_FP64;
-    if (mode != EVEC_FP64) return EVEC_EINVAL;
-    const int tile = opt ? opt->tile : 0;   // 0: the tuned tile of each size class
+    if (mode != EVEC_FP64 && mode != EVEC_SPLIT) return EVEC_EINVAL;
+    const int slices = mode == EVEC_SPLIT ? ((opt && opt->slices) ? opt->slices : 8) : 0;
+    if (mode == EVEC_SPLIT && (slices < 2 || slices > 8)) return EVEC_EINVAL;
+    // 0: the tuned tile of each size class (FP64), 64 rows (split)
+    const int tile = opt ? opt->tile : 0;
     if (tile != 0 && (tile < 16 || tile > 64)) return EVEC_EINVAL;
     if (Z_packed && !z_off_host) return EVEC_EINVAL;
     if (count == 0) return EVEC_OK;
@@ -2366,7 +2369,8 @@ extern "C" evec_status evec_batched_generalized(
                     K.lr == (const void *)alpha_re_packed &&
                     K.li == (const void *)alpha_im_packed && K.beta == (const void *)beta_packed &&
                     K.tile == tile && K.has_sel == (select_host != nullptr) &&
-                    K.Q == (const void *)Z_packed && same_offsets(K.qoff, bo.q_off, count);
+                    K.Q == (const void *)Z_packed && same_offsets(K.qoff, bo.q_off, count) &&
+                    K.mode == mode && K.slices == slices;
         if (same && tile == 0)
             for (int c = 0; c < EVEC_SIZE_CLASSES; c++)
                 same = same && K.tune[c] == h->tune[EVEC_TUNE_PENCIL][c];
@@ -2415,7 +2419,7 @@ extern "C" evec_status evec_batched_generalized(
         for (int i : ids) t = std::max(t, pl[i].max_tile);
         return t;
     };
-    if (tile == 0) {
+    if (tile == 0 && mode == EVEC_FP64) {
         // the tile of each size class: tuned on first use by timing the
         // candidates on up to eight of the batch's pencils of the class
         int *tab = h->tune[EVEC_TUNE_PENCIL];
@@ -2470,7 +2474,7 @@ extern "C" evec_status evec_batched_generalized(
     }
     const int max_tile = largest_tile(plans, all);
     EVEC_TRY(run_batch(h, count, n_host, S_packed, s_off_host, all, plans, X_packed,
-                       scale_exp_packed, alpha_re_packed, alpha_im_packed, true, 0, T_packed,
+                       scale_exp_packed, alpha_re_packed, alpha_im_packed, true, slices, T_packed,
                        t_off_host, beta_packed, max_tile, bo));
     {   // remember this call for a replay
         BatchKey &K = h->bcall;
@@ -2492,7 +2496,7 @@ extern "C" evec_status evec_batched_generalized(
         K.eoff.clear();
         K.tile = tile;
         K.mode = mode;
-        K.slices = 0;
+        K.slices = slices;
         K.tune.assign(h->tune[EVEC_TUNE_PENCIL], h->tune[EVEC_TUNE_PENCIL] + EVEC_SIZE_CLASSES);
         K.has_sel = select_host != nullptr;
         if (select_host) K.sel.assign(select_host, select_host + rows);

@@ -274,7 +274,12 @@ __device__ __forceinline__ void slice8_store(const double (&x)[8], int e, int S,
 }
 
 // Y_r <- 2^dy Y_r - T_rs (2^dx X_s) for all r < s, as split products.
+// Pencils (GEN): Y_r <- 2^dy Y_r - [S_rs T_rs] 2^dx W with the 2K x nc
+// right-hand side W = [beta X_s; -alpha X_s] (alpha mixes a pair's columns,
+// as in cta_tile_update<true>), so the product's K is twice the tile's;
+// the row exponents cover both matrices' rows, the column exponents W's.
 // Returns false if a bounded wait gave up (status->timeout is set).
+template <bool GEN>
 __device__ bool cta_split_update(const BatchItem &B, int s, int S, unsigned char *sm,
                                  uint32_t tmem, uint64_t *bar, uint32_t &phase, int *err) {
     const Plan &P = B.P;
@@ -289,10 +294,36 @@ __device__ bool cta_split_update(const BatchItem &B, int s, int S, unsigned char
     int *srt = sea + kTM;                                                // [128]
     int *seb = srt + kTM;                                                // [32]
     const int k0 = P.tile_start[s], K = P.tile_start[s + 1] - k0;
-    const int halves = (K + kTK - 1) / kTK;
+    const int K2 = GEN ? 2 * K : K;   // the product's K: [S T] against W
+    const int halves = (K2 + kTK - 1) / kTK;
     const int t0 = k0;   // rows above tile s
     double *Y = B.X;
     const int64_t ldy = B.ldx;
+    // A entry (row, kk): S (or T) for kk < K, the pencil's T for K <= kk < 2K
+    auto a_at = [&](int row, int kk) -> double {
+        if (GEN && kk >= K) return B.T2[row + (int64_t)(k0 + kk - K) * B.ldt2];
+        return B.T[row + (int64_t)(k0 + kk) * B.ldt];
+    };
+    // W entry (kk, column c): X_s for a standard problem; beta x, then
+    // -(alpha x) (a pair's partner column at the same scale) for a pencil
+    auto w_at = [&](int kk, int64_t c) -> double {
+        if constexpr (!GEN) {
+            return Y[(k0 + kk) + c * ldy];
+        } else {
+            const int u = P.col_unit[c];
+            const int k = kk < K ? kk : kk - K;
+            const double v = Y[(k0 + k) + c * ldy];
+            if (kk < K) return v * P.unit_beta[u];
+            const double ar = P.unit_lam[2 * u], ai = P.unit_lam[2 * u + 1];
+            double ax = ar * v;
+            if (ai != 0.0) {
+                const bool re = c == P.unit_col[u];
+                const double xp = Y[(k0 + k) + (re ? c + 1 : c - 1) * ldy];
+                ax = re ? fma(ar, v, -ai * xp) : fma(ar, v, ai * xp);
+            }
+            return -ax;
+        }
+    };
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTM >> 4) << 24);
     for (int rb0 = 0; rb0 < t0; rb0 += kTM) {
         const int rows = min(kTM, t0 - rb0);
@@ -312,8 +343,7 @@ __device__ bool cta_split_update(const BatchItem &B, int s, int S, unsigned char
             }
             long long mb = 0;
             if (rv)
-                for (int k = 0; k < K; k++)
-                    mb = max(mb, abs_bits(B.T[row + (int64_t)(k0 + k) * B.ldt]));
+                for (int kk = 0; kk < K2; kk++) mb = max(mb, abs_bits(a_at(row, kk)));
             srt[tid] = rv ? r : -1;
             sea[tid] = exp_from_max((unsigned long long)mb);
         }
@@ -328,8 +358,7 @@ __device__ bool cta_split_update(const BatchItem &B, int s, int S, unsigned char
             if (tid < kBSN) {
                 long long mb = 0;
                 if (tid < nc)
-                    for (int k = 0; k < K; k++)
-                        mb = max(mb, abs_bits(Y[(k0 + k) + (j0 + tid) * ldy]));
+                    for (int kk = 0; kk < K2; kk++) mb = max(mb, abs_bits(w_at(kk, j0 + tid)));
                 seb[tid] = exp_from_max((unsigned long long)mb);
             }
             for (int idx = tid; idx < nslots * kBSN; idx += kBThreads) {
@@ -346,8 +375,8 @@ __device__ bool cta_split_update(const BatchItem &B, int s, int S, unsigned char
                     double x[8];
 #pragma unroll
                     for (int t = 0; t < 8; t++) {
-                        const int k = h * kTK + c * 8 + t;
-                        x[t] = (rv && k < K) ? B.T[row + (int64_t)(k0 + k) * B.ldt] : 0.0;
+                        const int kk = h * kTK + c * 8 + t;
+                        x[t] = (rv && kk < K2) ? a_at(row, kk) : 0.0;
                     }
                     slice8_store(x, er, S, sA + sw64_off(tid, c), kBSBoxA);
                 }
@@ -356,8 +385,8 @@ __device__ bool cta_split_update(const BatchItem &B, int s, int S, unsigned char
                     double x[8];
 #pragma unroll
                     for (int t = 0; t < 8; t++) {
-                        const int k = h * kTK + c * 8 + t;
-                        x[t] = (j < nc && k < K) ? Y[(k0 + k) + (j0 + j) * ldy] : 0.0;
+                        const int kk = h * kTK + c * 8 + t;
+                        x[t] = (j < nc && kk < K2) ? w_at(kk, j0 + j) : 0.0;
                     }
                     slice8_store(x, seb[j], S, sB + sw64_off(j, c), kBSBoxB);
                 }
@@ -674,7 +703,7 @@ __global__ void __launch_bounds__(kBThreads)
             }
             if (s > 0 && P.tile_col[s] < P.m) {
                 if constexpr (SPLIT) {
-                    if (!cta_split_update(B, s, S, sbase, tmem, &mbar, phase,
+                    if (!cta_split_update<GEN>(B, s, S, sbase, tmem, &mbar, phase,
                                           &status->timeout)) {
                         alive = false;
                         break;
@@ -719,21 +748,21 @@ __global__ void __launch_bounds__(kBThreads)
 // (the diagonal-tile solver also holds T's tile)
 size_t batched_smem_bytes(bool split, int gen_tile) {
     const size_t upd = sizeof(double) * (64 * 65 + 64 * 64 + 8 * 64) + sizeof(int) * 128;
-    if (gen_tile > 0) return std::max(diag_smem<4, true>(gen_tile), upd);
     // the split variant aligns its operand tiles to 1024 bytes; its size
     // also keeps at most two CTAs (2 x 256 TMEM columns) on an SM
-    const size_t base = std::max(diag_smem<4>(64), upd);
+    const size_t base =
+        gen_tile > 0 ? std::max(diag_smem<4, true>(gen_tile), upd) : std::max(diag_smem<4>(64), upd);
     return split ? std::max(base + 1024, kBSBytes) : base;
 }
 
 // One persistent launch: grid = SMs x CTAs per SM (occupancy query); S > 0
-// runs the split-precision variant (S digit slices); gen_tile > 0 the
-// pencil variant (FP64, tiles of at most gen_tile rows).
+// runs the split-precision updates (S digit slices); gen_tile > 0 the
+// pencil variant (tiles of at most gen_tile rows).
 cudaError_t launch_batched(const BatchItem *items, int count, int *queue, DevStatus *status,
                            int nsm, cudaStream_t st, int S, int gen_tile) {
-    const bool split = S > 0 && gen_tile == 0;
+    const bool split = S > 0;
     const size_t smem = batched_smem_bytes(split, gen_tile);
-    auto kern = gen_tile > 0 ? k_batched<false, true>
+    auto kern = gen_tile > 0 ? (split ? k_batched<true, true> : k_batched<false, true>)
                              : (split ? k_batched<true, false> : k_batched<false, false>);
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,

@@ -115,11 +115,11 @@ def test_batched_pencils_errors():
         ev.batched_generalized(pairs_bad)
     assert ei.value.status == ev.EVEC_ENONFINITE
     assert ei.value.bad == 40 * 40 + 5 + 50 * 60      # offset in the packed T
-    # split mode is not offered for pencils in the batch
+    # a slice count outside 2..8 is refused
     Sp, ns, offs = ev.pack_batch([S for S, _ in pairs])
     Tp, _, _ = ev.pack_batch([T for _, T in pairs])
     h = ev.handle(0)
-    opts = ev._opts(0, False, "split", 0)
+    opts = ev._opts(0, False, "split", 9)
     st = ev.lib().evec_batched_generalized(h.ptr, 3, ev._np_ptr(ns), Sp.data_ptr(),
                                            ev._np_ptr(offs), Tp.data_ptr(), ev._np_ptr(offs),
                                            None, None, None, None, None, None, None, None,
@@ -224,3 +224,18 @@ def test_batched_pencils_tile_tuning():
         ev.set_tune_table([100] * ev.SIZE_CLASSES, 0, "pencil")
     for c in range(ev.SIZE_CLASSES):
         assert ev.lib().evec_tune_set(h.ptr, 2, c, 0) == ev.EVEC_OK
+
+
+@pytest.mark.parametrize("tile", [32, 64])
+def test_batched_pencils_split(tile):
+    """Split mode: the updates as one split product of [S_rs T_rs] against
+    [beta X; -alpha X] per step, in the persistent kernel; with and without
+    Z, against the oracle at the FP64 bar."""
+    sizes = workloads.batch_sizes(30, seed=111 + tile, lo=8, hi=400)
+    pairs, sels = _batch(sizes, seed=11100 + tile, fraction=0.5)
+    outs = ev.batched_generalized(pairs, sels, tile=tile, mode="split")
+    _check(pairs, sels, outs)
+    Zs = [workloads.householder_orthogonal(int(n), seed=11200 + i) if i % 3 == 0 else None
+          for i, n in enumerate(sizes)]
+    outs = ev.batched_generalized(pairs, sels, tile=tile, mode="split", Zs=Zs)
+    _check(pairs, sels, outs, Zs=Zs)
