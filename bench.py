@@ -614,7 +614,9 @@ def run_reference_other(args):
                 units += (ns / n) ** 3
                 secs += dt
         unit = "reductions/s"
-        metric = "Hessenberg reductions/s (A = Q H Q^T with Q, FP64)"
+        metric = ("Hessenberg reductions/s (A = Q H Q^T with Q, "
+                  + (f"split-precision updates, {args.slices or 8} slices)"
+                     if args.mode == "split" else "FP64)"))
         what = f"Hessenberg reduction of an n={n} N(0, 1) matrix with Q"
         sample = (f"one unblocked reduction with Q at n = {ns} per step on one core, counted as "
                   f"(n / {ns})^3 reductions of order {n}")
@@ -1422,7 +1424,9 @@ def run_hessenberg(args, rank, world, local_rank):
     dA = torch.empty((n, n), dtype=torch.float64, device=dev).t()
     dQ = torch.empty((n, n), dtype=torch.float64, device=dev).t()
     h = ev.handle(local_rank)
-    opts = ev._opts(0, False, "fp64", 0)
+    split = args.mode == "split"
+    slices = (args.slices or 8) if split else 0
+    opts = ev._opts(0, False, args.mode, slices)
 
     def step():
         dA.copy_(dA0)
@@ -1511,7 +1515,21 @@ def run_hessenberg(args, rank, world, local_rank):
                                "alg_flops_per_step": Fp, "alg_bytes_per_step": Bpan,
                                "ms_per_step": pm / args.steps}
     um, un = prof.get("hess_update", (0.0, 0))
-    if um > 0:
+    if um > 0 and split:
+        # BF16 slice products: S (S + 1) / 2 digit pairs per FP64 multiply-add
+        Fu = (F - 2.0 * Bpan / 8.0) * slices * (slices + 1) / 2
+        ach = Fu / (um / args.steps / 1e3) / 1e12
+        bf16 = float(peaks.get("bf16_tflops_sustained") or 1400.0)
+        roofs["hess_update"] = {"kernel": "trailing / top / Q updates through the split GEMM "
+                                          "(k_split_gemm with its slicing kernels)",
+                                "bound": "tensor", "achieved": ach, "peak": bf16,
+                                "unit": "TFLOP/s", "frac": ach / bf16, "traffic": None,
+                                "peak_source": "of measured sustained BF16 (MEASURED_PEAKS.json)",
+                                "launches_per_step": un / args.steps, "alg_flops_per_step": Fu,
+                                "fp64_equivalent_tflops":
+                                    (F - 2.0 * Bpan / 8.0) / (um / args.steps / 1e3) / 1e12,
+                                "ms_per_step": um / args.steps}
+    elif um > 0:
         Fu = F - 2.0 * Bpan / 8.0   # the products not done by the matrix-vector steps
         ach = Fu / (um / args.steps / 1e3) / 1e12
         roofs["hess_update"] = {"kernel": "trailing / top / Q updates (k_hs_gemm)", "bound": "alu",
@@ -1538,13 +1556,16 @@ def run_hessenberg(args, rank, world, local_rank):
                "sample": f"one unblocked reduction with Q at n = {ns} in {dt:.2f} s on one core, "
                          f"extrapolated to n = {n} by (n / {ns})^3"}
     line = {
-        "metric": "Hessenberg reductions/s (A = Q H Q^T with Q, FP64)",
+        "metric": "Hessenberg reductions/s (A = Q H Q^T with Q, "
+                  + (f"split-precision updates, {slices} slices)" if split else "FP64)"),
         "value": world * args.steps / (elapsed / 1e3), "unit": "reductions/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16 slice products + f64" if split else "f64",
         "data": "synthetic",
         "config": {"workload": f"Hessenberg reduction of an n={n} N(0, 1) matrix with Q, panels of "
-                               "32 columns", "n": n, "panel": 32, "parallelism": "replicas",
+                               "32 columns", "n": n, "panel": 32, "mode": args.mode,
+                   "parallelism": "replicas",
                    "l2": f"inputs larger than L2 (A, H, Q {8 * n * n >> 20} MiB each)"},
         "tflops_fp64": F * args.steps / (elapsed / 1e3) / 1e12,
         "flops_per_step": F,

@@ -490,9 +490,11 @@ def window_update(T, Q, windows, check: bool = False, packed=None, disjoint: boo
     return T, Q
 
 
-def hessenberg(A, calc_q: bool = True, check: bool = False, overwrite: bool = False):
+def hessenberg(A, calc_q: bool = True, check: bool = False, overwrite: bool = False,
+               mode: str = "fp64", slices: int = 0):
     """Hessenberg reduction A = Q H Q^T of a float64 CUDA matrix
-    (column-major).  Returns (H, Q or None); with overwrite, H is A itself."""
+    (column-major).  Returns (H, Q or None); with overwrite, H is A itself.
+    mode "split": the panels' large products through the split GEMM."""
     import torch
     n = A.shape[0]
     lda = _check_colmajor(A, "A", n)
@@ -501,7 +503,7 @@ def hessenberg(A, calc_q: bool = True, check: bool = False, overwrite: bool = Fa
     if n == 0:
         return H, Q
     h = handle(A.device.index)
-    opts = _opts(0, False, "fp64", 0)
+    opts = _opts(0, False, mode, slices)
     st = lib().evec_hessenberg(h.ptr, n, H.data_ptr(), H.stride(1) if n > 1 else lda,
                                Q.data_ptr() if Q is not None else None,
                                Q.stride(1) if (Q is not None and n > 1) else max(n, 1),

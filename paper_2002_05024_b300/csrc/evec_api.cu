@@ -54,6 +54,10 @@ void launch_left_output(const double *Xw, int64_t ldw, int64_t n, int64_t m, con
                         int reverse, const int32_t *ew, const double *lrw, const double *liw,
                         double *X, int64_t ldx, int32_t *e, double *lr, double *li,
                         cudaStream_t st, const double *bw = nullptr, double *bo = nullptr);
+int hess_update_split(int64_t n, double *A, int64_t lda, double *Q, int64_t ldq, int64_t k,
+                      int b, double *ws, const HessSplitWs &sw, int S, int *err, int nsm,
+                      cudaStream_t st, cudaStream_t qst, cudaEvent_t fork, cudaEvent_t join,
+                      cudaError_t *status);
 size_t hessenberg_workspace(int64_t n);
 int hess_panel_width();
 void hess_init_q(int64_t n, double *Q, int64_t ldq, cudaStream_t st);
@@ -107,7 +111,8 @@ cudaError_t split_slice_cols(const double *B, int64_t ldb, int K, int N, int S, 
 cudaError_t split_gemm_sliced(const __nv_bfloat16 *sa, int Mpad, const __nv_bfloat16 *sb,
                               int Npad, int M, int N, int K, int S, const int *kend,
                               const int *ea, const int *eb, double *C, int64_t ldc, int *err,
-                              cudaStream_t st);
+                              cudaStream_t st, int acc = 0, int ksplit = 1,
+                              double *part = nullptr);
 cudaError_t launch_split_gemm(const double *A, int64_t lda, const double *B, int64_t ldb, int M,
                               int N, int K, int S, const int *kend, double *C, int64_t ldc,
                               __nv_bfloat16 *sa, __nv_bfloat16 *sb, unsigned long long *rowmax,
@@ -205,6 +210,10 @@ struct PlanKey {
     bool has_sel = false;
     std::vector<uint8_t> sel;
 };
+
+// columns of a split product: split_pad_n(N) <= 65535, the grid rows of
+// the column-slicing kernel
+constexpr int64_t kSplitMaxN = 65472;
 
 // What the last completed evec_batched call was made of: the batch layout,
 // the buffers, the options and tile table, the selection and every
@@ -596,6 +605,15 @@ struct evec_ctx {
     __nv_bfloat16 *wZs = nullptr; size_t wZs_cap = 0;
     unsigned long long *wZm = nullptr; size_t wZm_cap = 0;
     int *wZe = nullptr; size_t wZe_cap = 0;
+    // split Hessenberg updates: the A chain's and the Q chain's slices
+    __nv_bfloat16 *hsA[4] = {nullptr, nullptr, nullptr, nullptr};
+    size_t hsA_cap[4] = {0, 0, 0, 0};
+    unsigned long long *hsM[4] = {nullptr, nullptr, nullptr, nullptr};
+    size_t hsM_cap[4] = {0, 0, 0, 0};
+    int *hsE[4] = {nullptr, nullptr, nullptr, nullptr};
+    size_t hsE_cap[4] = {0, 0, 0, 0};
+    double *hsP[2] = {nullptr, nullptr};   // partial products of a K split
+    size_t hsP_cap[2] = {0, 0};
     // and the Q products' own row slices (they run on la_stream)
     __nv_bfloat16 *wQs = nullptr; size_t wQs_cap = 0;
     unsigned long long *wQm = nullptr; size_t wQm_cap = 0;
@@ -1002,7 +1020,9 @@ evec_status evec_destroy(evec_handle h) {
                    h->ea_panels, h->boff_d, h->bws, h->bplan_d, h->queue_d, h->tauT,
                    h->blk_tauT, h->pW, h->Rd, h->seg_ey, h->lT, h->lQ, h->lX, h->lE, h->lL,
                    h->lmap_d, h->hs_ws, h->gate_d, h->win_d, h->lT2, h->wZs, h->wZm, h->wZe,
-                   h->wQs, h->wQm, h->wQe};
+                   h->wQs, h->wQm, h->wQe, h->hsA[0], h->hsA[1], h->hsA[2], h->hsA[3],
+                   h->hsM[0], h->hsM[1], h->hsM[2], h->hsM[3], h->hsE[0], h->hsE[1],
+                   h->hsE[2], h->hsE[3], h->hsP[0], h->hsP[1]};
     for (void *p : dev)
         if (p) cudaFree(p);
     for (auto &t : h->live) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
@@ -2517,12 +2537,34 @@ extern "C" evec_status evec_hessenberg(evec_handle h, int64_t n, double *A, int6
                                        double *Q, int64_t ldq, const evec_opts *opt) {
     if (!h || n < 0 || !ld_ok(lda, n) || (Q && !ld_ok(ldq, n)) || n > INT32_MAX)
         return EVEC_EINVAL;
+    const int mode = opt ? opt->mode : EVEC_FP64;
+    const int slices = mode == EVEC_SPLIT ? ((opt && opt->slices) ? opt->slices : 8) : 0;
+    if ((mode != EVEC_FP64 && mode != EVEC_SPLIT) || (mode == EVEC_SPLIT && (slices < 2 ||
+                                                                             slices > 8)))
+        return EVEC_EINVAL;
+    if (mode == EVEC_SPLIT && n > kSplitMaxN) return EVEC_EINVAL;
     if (n == 0) return EVEC_OK;
     if (!A) return EVEC_EINVAL;
     DeviceGuard g(h->device);
     if (!g.ok) return EVEC_ECUDA;
     cudaStream_t st = h->stream;
     EVEC_TRY(grow_device(&h->hs_ws, &h->hs_ws_cap, hessenberg_workspace(n)));
+    HessSplitWs sw{};
+    if (mode == EVEC_SPLIT) {   // slices of the A chain (0, 1) and of the Q chain (2, 3)
+        const size_t Mp = (size_t)split_pad_m((int)n), Kp = (size_t)split_pad_k((int)n);
+        const size_t big = (size_t)slices * Mp * Kp;
+        const size_t small = (size_t)slices * std::max(Mp * 64, 64 * Kp);
+        const size_t ext = std::max<size_t>(Mp, 64);
+        for (int i = 0; i < (Q ? 4 : 2); i++) {
+            EVEC_TRY(grow_device(&h->hsA[i], &h->hsA_cap[i], (i % 2 == 0) ? big : small));
+            EVEC_TRY(grow_device(&h->hsM[i], &h->hsM_cap[i], ext));
+            EVEC_TRY(grow_device(&h->hsE[i], &h->hsE_cap[i], ext));
+        }
+        for (int i = 0; i < (Q ? 2 : 1); i++)
+            EVEC_TRY(grow_device(&h->hsP[i], &h->hsP_cap[i], (size_t)kHSplitMax * Mp * 32));
+        sw = {h->hsA[0], h->hsA[1], h->hsA[2], h->hsA[3], h->hsM[0], h->hsM[1], h->hsM[2],
+              h->hsM[3], h->hsE[0], h->hsE[1], h->hsE[2], h->hsE[3], h->hsP[0], h->hsP[1]};
+    }
     timed(h, EVEC_K_NORMS, [&] {
         launch_check_rhs(A, lda, n, n, 0, h->status_d, st);
         return 1;
@@ -2545,11 +2587,16 @@ extern "C" evec_status evec_hessenberg(evec_handle h, int64_t n, double *A, int6
             return hess_panel(n, A, lda, k, b, h->hs_ws, &h->status_d->timeout, h->nsm,
                               h->hess_coop, st, h->wait_limit);
         });
-        timed(h, EVEC_K_HESS_UPDATE,
-              [&] {
-                  return hess_update(n, A, lda, Q, ldq, k, b, h->hs_ws, st, h->la_stream,
-                                     h->ev_slice, h->ev_tail);
-              });
+        cudaError_t ue = cudaSuccess;
+        timed(h, EVEC_K_HESS_UPDATE, [&] {
+            if (mode == EVEC_SPLIT)
+                return hess_update_split(n, A, lda, Q, ldq, k, b, h->hs_ws, sw, slices,
+                                         &h->status_d->timeout, h->nsm, st, h->la_stream,
+                                         h->ev_slice, h->ev_tail, &ue);
+            return hess_update(n, A, lda, Q, ldq, k, b, h->hs_ws, st, h->la_stream, h->ev_slice,
+                               h->ev_tail);
+        });
+        EVEC_CUDA(ue);
     }
     EVEC_CUDA(cudaGetLastError());
     if (opt && opt->check) return evec_sync(h, nullptr);
@@ -2843,10 +2890,6 @@ extern "C" evec_status evec_generalized_left(evec_handle h, int64_t n, const dou
     if (opt && opt->check) return evec_sync(h, nullptr);
     return EVEC_OK;
 }
-
-// columns of a split product: split_pad_n(N) <= 65535, the grid rows of
-// the column-slicing kernel
-constexpr int64_t kSplitMaxN = 65472;
 
 // EVEC_SPLIT window updates: each window's left, right and Q products
 // through the split GEMM (the operands are sliced before each product, so

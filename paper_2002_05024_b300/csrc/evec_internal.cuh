@@ -13,6 +13,7 @@
 // Units: one unit per selected real eigenvalue (one column) or selected
 // complex pair (two columns, Re then Im), in block order.
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -224,6 +225,20 @@ __device__ __forceinline__ void report(DevStatus *st, int code, long long index)
 __device__ __forceinline__ void grid_dependency_wait() {
     asm volatile("griddepcontrol.wait;" ::: "memory");
 }
+
+// Slice buffers of the split-precision Hessenberg updates: the A chain (t*)
+// and the Q chain (q*); *a: left-operand slices, S x split_pad_m(n) x
+// split_pad_k(n) BF16; *b: right-operand slices, S x max(split_pad_m(n) x
+// 64, 64 x split_pad_k(n)); *am / *ae and *bm / *be: maxima and exponents,
+// split_pad_m(n) (at least 64) entries; tp / qp: partial products of a K
+// split, kHSplitMax x split_pad_m(n) x 32 doubles.
+constexpr int kHSplitMax = 16;
+struct HessSplitWs {
+    __nv_bfloat16 *ta, *tb, *qa, *qb;
+    unsigned long long *tam, *tbm, *qam, *qbm;
+    int *tae, *tbe, *qae, *qbe;
+    double *tp, *qp;
+};
 
 // One window of a disjoint set for the reordering updates: rows and
 // columns [a, a + k), accumulator at Z + zoff, first CTA of its tiles cta0.

@@ -16,6 +16,8 @@
 // atomics), so the result does not depend on scheduling.
 #include <algorithm>
 
+#include <cuda_bf16.h>
+
 #include "evec_internal.cuh"
 
 namespace evec {
@@ -945,6 +947,112 @@ int hess_update(int64_t n, double *A, int64_t lda, double *Q, int64_t ldq, int64
         ng += 4;
     }
     if (side) cudaStreamWaitEvent(st, join, 0);
+    return ng;
+}
+
+// ---------------------------------------------------------------------------
+// split-precision updates (evec_hessenberg with EVEC_SPLIT)
+// ---------------------------------------------------------------------------
+
+cudaError_t split_gemm_rows(const double *A, int64_t lda, int M, int K, int S,
+                            __nv_bfloat16 *sa, unsigned long long *rowmax, int *ea,
+                            cudaStream_t st);
+cudaError_t split_slice_cols(const double *B, int64_t ldb, int K, int N, int S, int Npad,
+                             __nv_bfloat16 *sb, unsigned long long *colmax, int *eb,
+                             cudaStream_t st);
+cudaError_t split_gemm_sliced(const __nv_bfloat16 *sa, int Mpad, const __nv_bfloat16 *sb,
+                              int Npad, int M, int N, int K, int S, const int *kend,
+                              const int *ea, const int *eb, double *C, int64_t ldc, int *err,
+                              cudaStream_t st, int acc, int ksplit, double *part);
+int split_pad_m(int M);
+int split_pad_n(int N);
+int split_pad_k(int K);
+
+// The same updates as hess_update with the five large products through the
+// split GEMM (BF16 digit slices with row / column power-of-two scales, FP64
+// results; the operands are sliced before each product, so a product may
+// update its own input): the two long products with the panel's columns
+// (W = Q V and Z = A^T V, K = the rows below the panel) and the three
+// rank-b updates (Q -= (W T) V^T, A -= Y V^T, A -= (V T^T) Z^T).  A
+// transposed operand is sliced from the stored matrix directly: the row
+// slices of M^T are the column slices of M and the other way round.  The
+// two b x b products with T stay FP64.  sw: the slice buffers of both
+// chains (HessSplitWs).  *status receives the first launch error.
+int hess_update_split(int64_t n, double *A, int64_t lda, double *Q, int64_t ldq, int64_t k,
+                      int b, double *ws, const HessSplitWs &sw, int S, int *err, int nsm,
+                      cudaStream_t st, cudaStream_t qst, cudaEvent_t fork, cudaEvent_t join,
+                      cudaError_t *status) {
+    const HessWs w = hess_ws(n, ws);
+    int ng = 0;
+    const int64_t j0 = k + b;            // first trailing column
+    const int nt = (int)(n - j0);
+    const int rows = (int)(n - k - 1);   // rows k+1 .. n-1 (V is zero above)
+    const int ni = (int)n;
+    const bool side = Q && qst && fork && join;
+    cudaError_t ce = cudaSuccess;
+    auto ok = [&](cudaError_t e) {
+        if (ce == cudaSuccess) ce = e;
+        return ce == cudaSuccess;
+    };
+    // the long products (b output columns, K = rows) have one 128-row band
+    // per CTA: their K steps are shared by up to kHSplitMax CTAs per band
+    // so that the GPU fills, at least four 32-deep K steps each
+    auto ksplit = [&](int M, int K) {
+        const int bands = split_pad_m(M) / 128;
+        int ks = std::min(kHSplitMax, std::max(1, (nsm + bands - 1) / bands));
+        return std::max(1, std::min(ks, split_pad_k(K) / 128));
+    };
+    if (Q) {
+        cudaStream_t s = st;
+        if (side) {
+            cudaEventRecord(fork, st);
+            cudaStreamWaitEvent(qst, fork, 0);
+            s = qst;
+        }
+        double *Qc = Q + (k + 1) * ldq;
+        const double *V1 = w.V + (k + 1);
+        // W = Q[:, k+1:n] V (n x b, K = rows)
+        if (ok(split_gemm_rows(Qc, ldq, ni, rows, S, sw.qa, sw.qam, sw.qae, s)) &&
+            ok(split_slice_cols(V1, n, rows, b, S, split_pad_n(b), sw.qb, sw.qbm, sw.qbe, s)))
+            ok(split_gemm_sliced(sw.qa, split_pad_m(ni), sw.qb, split_pad_n(b), ni, b, rows, S,
+                                 nullptr, sw.qae, sw.qbe, w.W, n, err, s, 0, ksplit(ni, rows),
+                                 sw.qp));
+        gemm(false, false, ni, b, b, 1.0, w.W, n, w.T, kHb, 0.0, w.VTq, n, s);
+        // Q[:, k+1:n] -= VTq V^T: V^T's columns are V's rows
+        if (ok(split_gemm_rows(w.VTq, n, ni, b, S, sw.qa, sw.qam, sw.qae, s)) &&
+            ok(split_gemm_rows(V1, n, rows, b, S, sw.qb, sw.qbm, sw.qbe, s)))
+            ok(split_gemm_sliced(sw.qa, split_pad_m(ni), sw.qb, split_pad_m(rows), ni, rows, b, S,
+                                 nullptr, sw.qae, sw.qbe, Qc, ldq, err, s, -1, 1, nullptr));
+        if (side) cudaEventRecord(join, qst);
+        ng += 11;
+    }
+    if (nt > 0 && ce == cudaSuccess) {
+        double *Aj = A + j0 * lda;
+        double *As = A + (k + 1) + j0 * lda;
+        // A[:, j0:n] -= Y V[j0:n, :]^T (every row)
+        if (ok(split_gemm_rows(w.Y, n, ni, b, S, sw.ta, sw.tam, sw.tae, st)) &&
+            ok(split_gemm_rows(w.V + j0, n, nt, b, S, sw.tb, sw.tbm, sw.tbe, st)))
+            ok(split_gemm_sliced(sw.ta, split_pad_m(ni), sw.tb, split_pad_m(nt), ni, nt, b, S,
+                                 nullptr, sw.tae, sw.tbe, Aj, lda, err, st, -1, 1, nullptr));
+        // Z = A[k+1:n, j0:n]^T V[k+1:n, :] (nt x b, K = rows): A^T's rows are
+        // the columns of A
+        if (ok(split_slice_cols(As, lda, rows, nt, S, split_pad_m(nt), sw.ta, sw.tam, sw.tae,
+                                st)) &&
+            ok(split_slice_cols(w.V + (k + 1), n, rows, b, S, split_pad_n(b), sw.tb, sw.tbm,
+                                sw.tbe, st)))
+            ok(split_gemm_sliced(sw.ta, split_pad_m(nt), sw.tb, split_pad_n(b), nt, b, rows, S,
+                                 nullptr, sw.tae, sw.tbe, w.Z, n, err, st, 0, ksplit(nt, rows),
+                                 sw.tp));
+        gemm(false, true, rows, b, b, 1.0, w.V + (k + 1), n, w.T, kHb, 0.0, w.VT, n, st);
+        // A[k+1:n, j0:n] -= VT Z^T: Z^T's columns are Z's rows
+        if (ok(split_gemm_rows(w.VT, n, rows, b, S, sw.ta, sw.tam, sw.tae, st)) &&
+            ok(split_gemm_rows(w.Z, n, nt, b, S, sw.tb, sw.tbm, sw.tbe, st)))
+            ok(split_gemm_sliced(sw.ta, split_pad_m(rows), sw.tb, split_pad_m(nt), rows, nt, b, S,
+                                 nullptr, sw.tae, sw.tbe, As, lda, err, st, -1, 1, nullptr));
+        ng += 16;
+    }
+    if (side) cudaStreamWaitEvent(st, join, 0);
+    if (status) *status = ce;
     return ng;
 }
 

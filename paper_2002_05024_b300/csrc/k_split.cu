@@ -138,6 +138,9 @@ struct SplitUpd {
     unsigned long long *nu;      // [ntiles][m] column maxima (bit patterns)
     int64_t m;                   // row length of the segment arrays
     int col0;                    // global column of local column 0
+    int acc;                     // plain product: 0 C = P, +1 C += P, -1 C -= P
+    int64_t zstride;             // plain product split over K (gridDim.z > 1):
+                                 // CTA z writes its partial product at C + z zstride
 };
 constexpr int kMaxSlots = 12;    // tile rows met by one 128-row CTA tile (tiles >= 15 rows)
 
@@ -177,7 +180,13 @@ __global__ void __launch_bounds__(kSplitThreads, 1)
     const int K = kend ? kend[nt] : kuni;
     if (UPD)
         for (int i = tid; i < kMaxSlots * kTN; i += kSplitThreads) red[i] = 0ull;
-    const int nst = K / kTK;
+    // the K steps of this CTA: all of them, or its share of a K split
+    const int nst_all = K / kTK;
+    const int zper = ((int)gridDim.z > 1) ? (nst_all + (int)gridDim.z - 1) / (int)gridDim.z
+                                         : nst_all;
+    const int s0 = (int)blockIdx.z * zper;
+    const int nst = max(0, min(nst_all, s0 + zper) - s0);
+    if (!UPD && gridDim.z > 1) C += (int64_t)blockIdx.z * upd.zstride;
     const int chunks = (nst + kChunkStages - 1) / kChunkStages;
 
     if (warp == 8) {
@@ -212,13 +221,14 @@ __global__ void __launch_bounds__(kSplitThreads, 1)
                 unsigned char *sa = base + st * kStageBytes;
                 unsigned char *sb = sa + kSplitMaxS * kStageA;
                 for (int p = 0; p < S; p++)
-                    tma2d(saddr(sa + p * kStageA), &tmA, it * kTK, aRow0 + p * aMpad + m0,
+                    tma2d(saddr(sa + p * kStageA), &tmA, (s0 + it) * kTK, aRow0 + p * aMpad + m0,
                           saddr(&bars[st]));
                 // B as [column half c][slice q] boxes of 32 rows, so the
                 // slices of one half lie one after another
                 for (int c = 0; c < 2; c++)
                     for (int q = 0; q < S; q++)
-                        tma2d(saddr(sb + (c * kSplitMaxS + q) * (kStageB / 2)), &tmB, it * kTK,
+                        tma2d(saddr(sb + (c * kSplitMaxS + q) * (kStageB / 2)), &tmB,
+                              (s0 + it) * kTK,
                               q * Npad + n0 + c * 32, saddr(&bars[st]));
                 issued = it + 1;
             }
@@ -337,11 +347,30 @@ __global__ void __launch_bounds__(kSplitThreads, 1)
         }
         if (!UPD && row < M) {
             const int er = ea[row];
+            if (upd.acc == 0) {
 #pragma unroll
-            for (int j = 0; j < 32; j++) {
-                const int col = n0 + cb0 + j;
-                if (col < N)
-                    C[row + (int64_t)col * ldc] = df_to_double(hi[j], lo[j], er + eb[col]);
+                for (int j = 0; j < 32; j++) {
+                    const int col = n0 + cb0 + j;
+                    if (col < N)
+                        C[row + (int64_t)col * ldc] = df_to_double(hi[j], lo[j], er + eb[col]);
+                }
+            } else {   // C +- P: eight old values loaded, then eight updates
+#pragma unroll
+                for (int g = 0; g < 4; g++) {
+                    double oldv[8];
+#pragma unroll
+                    for (int q = 0; q < 8; q++) {
+                        const int col = n0 + cb0 + g * 8 + q;
+                        oldv[q] = col < N ? C[row + (int64_t)col * ldc] : 0.0;
+                    }
+#pragma unroll
+                    for (int q = 0; q < 8; q++) {
+                        const int j = g * 8 + q, col = n0 + cb0 + j;
+                        if (col >= N) break;
+                        const double p = df_to_double(hi[j], lo[j], er + eb[col]);
+                        C[row + (int64_t)col * ldc] = upd.acc > 0 ? oldv[q] + p : oldv[q] - p;
+                    }
+                }
             }
         }
         if (UPD) {
@@ -489,13 +518,31 @@ cudaError_t split_slice_cols(const double *B, int64_t ldb, int K, int N, int S, 
     return cudaGetLastError();
 }
 
-// C = A B from the slices of A (sa [S][Mpad][Kpad], exponents ea) and of B
-// (sb [S][Npad][Kpad], exponents eb), over K < kend[N tile] (or the whole
-// padded K when kend is null).
+// C (+ or -)= sum over z of the ksplit partial products at part + z M N
+// (leading dimension M), summed in FP64 in the order of z.
+__global__ void __launch_bounds__(256)
+    k_sum_partials(const double *__restrict__ part, int ksplit, int M, int N,
+                   double *__restrict__ C, int64_t ldc, int acc) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t MN = (int64_t)M * N;
+    if (e >= MN) return;
+    double v = part[e];
+    for (int z = 1; z < ksplit; z++) v += part[(int64_t)z * MN + e];
+    const int64_t i = e % M, j = e / M;
+    double *c = C + i + j * ldc;
+    *c = acc == 0 ? v : (acc > 0 ? *c + v : *c - v);
+}
+
+// C = A B (acc 0), C += A B (+1) or C -= A B (-1) from the slices of A (sa
+// [S][Mpad][Kpad], exponents ea) and of B (sb [S][Npad][Kpad], exponents
+// eb), over K < kend[N tile] (or the whole padded K when kend is null).
+// ksplit > 1 (kend null): the K steps are shared by ksplit CTAs per output
+// tile, each writing its partial product to part (ksplit M N doubles),
+// then summed into C -- for products with few output tiles and a long K.
 cudaError_t split_gemm_sliced(const __nv_bfloat16 *sa, int Mpad, const __nv_bfloat16 *sb,
                               int Npad, int M, int N, int K, int S, const int *kend,
                               const int *ea, const int *eb, double *C, int64_t ldc, int *err,
-                              cudaStream_t st) {
+                              cudaStream_t st, int acc, int ksplit, double *part) {
     if (!get_encoder()) return cudaErrorInvalidValue;
     const int Kpad = split_pad_k(K);
     CUtensorMap tmA, tmB;
@@ -505,7 +552,10 @@ cudaError_t split_gemm_sliced(const __nv_bfloat16 *sa, int Mpad, const __nv_bflo
     const size_t smem = split_smem_bytes();
     cudaFuncSetAttribute(k_split_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
+    if (ksplit > 1 && (kend || !part)) return cudaErrorInvalidValue;
     SplitUpd none = {};
+    none.acc = ksplit > 1 ? 0 : acc;
+    none.zstride = (int64_t)M * N;
     // column tiles per group: gw about sqrt(CTAs in flight x (row band
     // bytes / column tile bytes)), so one wave's row bands and column tiles
     // cost about the same DRAM traffic (a band of Q's slices holds twice
@@ -518,6 +568,14 @@ cudaError_t split_gemm_sliced(const __nv_bfloat16 *sa, int Mpad, const __nv_bflo
         nsm = 148;
     }
     const int gw = std::max(1, std::min(ntn, (int)lround(sqrt(2.0 * nsm))));
+    if (ksplit > 1) {
+        k_split_gemm<false><<<dim3(ntn * mtn, 1, ksplit), kSplitThreads, smem, st>>>(
+            tmA, tmB, S, M, N, 0, Mpad, Npad, nullptr, Kpad, ea, eb, part, M, none, err, ntn, gw);
+        const int64_t MN = (int64_t)M * N;
+        k_sum_partials<<<(unsigned)((MN + 255) / 256), 256, 0, st>>>(part, ksplit, M, N, C, ldc,
+                                                                     acc);
+        return cudaGetLastError();
+    }
     k_split_gemm<false><<<ntn * mtn, kSplitThreads, smem, st>>>(
         tmA, tmB, S, M, N, 0, Mpad, Npad, kend, kend ? 0 : Kpad, ea, eb, C, ldc, none, err, ntn,
         gw);
@@ -532,7 +590,8 @@ cudaError_t split_gemm_cols(const double *B, int64_t ldb, int M, int N, int K, i
     const int Mpad = split_pad_m(M), Npad = split_pad_n(N);
     cudaError_t e = split_slice_cols(B, ldb, K, N, S, Npad, sb, colmax, eb, st);
     if (e != cudaSuccess) return e;
-    return split_gemm_sliced(sa, Mpad, sb, Npad, M, N, K, S, kend, ea, eb, C, ldc, err, st);
+    return split_gemm_sliced(sa, Mpad, sb, Npad, M, N, K, S, kend, ea, eb, C, ldc, err, st, 0, 1,
+                             nullptr);
 }
 
 cudaError_t launch_split_gemm(const double *A, int64_t lda, const double *B, int64_t ldb, int M,
@@ -652,7 +711,7 @@ cudaError_t split_update_step(const SplitUpdateCtx &ctx, int t0, int ts, int pro
     const size_t smem = split_smem_bytes();
     cudaFuncSetAttribute(k_split_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
-    SplitUpd upd;
+    SplitUpd upd = {};
     upd.row_tile = row_tile;
     upd.dx = dx;
     upd.dy = dy;

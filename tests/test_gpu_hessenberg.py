@@ -16,9 +16,9 @@ pytestmark = pytest.mark.gpu
 U = 2.0 ** -53
 
 
-def _gpu(A, calc_q=True):
+def _gpu(A, calc_q=True, mode="fp64"):
     dA = torch.from_numpy(np.asfortranarray(A)).cuda()
-    H, Q = ev.hessenberg(dA, calc_q=calc_q, check=True)
+    H, Q = ev.hessenberg(dA, calc_q=calc_q, check=True, mode=mode)
     torch.cuda.synchronize()
     return H.cpu().numpy(), (Q.cpu().numpy() if Q is not None else None)
 
@@ -183,3 +183,50 @@ def test_panel_barrier_wait_runs_out_then_recovers():
     Ho, Qo, _ = oracle.hessenberg(A)
     assert np.abs(H - Ho).max() <= _bound(n) * np.abs(A).max()
     assert np.abs(Q - Qo).max() <= _bound(n)
+
+
+# --------------------------------------------------------------------------
+# split precision (EVEC_SPLIT): the five large products of every panel's
+# update through the split GEMM, at the FP64 path's bounds
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [3, 33, 100, 257, 600])
+def test_hessenberg_split_against_oracle(n):
+    A = np.random.default_rng(n + 1000).standard_normal((n, n))
+    H, Q = _gpu(A, mode="split")
+    Ho, Qo, _ = oracle.hessenberg(A)
+    nrm = np.abs(A).max()
+    assert np.all(np.tril(H, -2) == 0.0)
+    assert np.abs(H - Ho).max() <= _bound(n) * nrm, np.abs(H - Ho).max()
+    assert np.abs(Q - Qo).max() <= _bound(n), np.abs(Q - Qo).max()
+    assert np.abs(Q.T @ Q - np.eye(n)).max() <= 8 * n * U
+    assert np.abs(Q @ H @ Q.T - A).max() <= _bound(n) * nrm
+    # without Q
+    H2, Q2 = _gpu(A, calc_q=False, mode="split")
+    assert Q2 is None and np.abs(H2 - Ho).max() <= _bound(n) * nrm
+
+
+@pytest.mark.parametrize("e2", [-900, 900])
+def test_hessenberg_split_extreme_scales(e2):
+    n = 200
+    A = np.random.default_rng(78).standard_normal((n, n))
+    H, Q = _gpu(np.ldexp(A, e2), mode="split")
+    H = np.ldexp(H, -e2)
+    Ho, Qo, _ = oracle.hessenberg(A)
+    nrm = np.abs(A).max()
+    assert np.abs(H - Ho).max() <= _bound(n) * nrm, np.abs(H - Ho).max()
+    assert np.abs(Q - Qo).max() <= _bound(n)
+
+
+def test_hessenberg_split_full_size_invariants():
+    n = 4096
+    A = np.random.default_rng(2021).standard_normal((n, n))
+    H, Q = _gpu(A, mode="split")
+    assert np.all(np.tril(H, -2) == 0.0)
+    assert np.abs(Q.T @ Q - np.eye(n)).max() <= 8 * n * U
+    R = Q @ H @ Q.T - A
+    assert np.abs(R).max() <= _bound(n) * np.abs(A).max(), np.abs(R).max()
+    with pytest.raises(ev.EvecError) as ei:   # a slice count outside 2..8
+        ev.hessenberg(torch.from_numpy(np.asfortranarray(A[:64, :64])).cuda(), mode="split",
+                      slices=9)
+    assert ei.value.status == ev.EVEC_EINVAL
