@@ -192,12 +192,18 @@ evec_status evec_standard_left(evec_handle h, int64_t n, const double *T, int64_
  * accumulated in the compact WY form I - V T V^T with Y = A V T, whose
  * columns need the matrix-vector product of the trailing matrix with w_j;
  * then the trailing matrix gets (I - V T V^T)^T (A - Y V^T) and the rows
- * above the panel A - Y V^T.  All FP64 on the device.
+ * above the panel A - Y V^T.  All FP64 on the device, or with opt->mode
+ * EVEC_SPLIT (opt->slices digit slices, 2..8; 0 = 8; n <= 65472) the five
+ * large products of each panel's update (Q V, A^T V and the three rank-32
+ * updates) through the split-precision GEMM: BF16 digit slices with row /
+ * column power-of-two scales on the tensor cores, FP64 results; the panel
+ * reductions stay FP64.  The split updates need slice buffers of about
+ * 4 slices n^2 BF16 values (with Q; half without).
  *   A [lda x n] (device): overwritten with H, exact zeros below the first
  *     subdiagonal.  Entries must be finite and at most 2^1000 (else
  *     EVEC_ENONFINITE / EVEC_EINVAL at evec_sync, index i + j lda).
  *   Q [ldq x n] (device) or NULL: receives the orthogonal factor.
- *   opt: only check is read.
+ *   opt: mode, slices and check are read.
  * The handle keeps a workspace of about 5 * 32 n + n doubles.
  */
 evec_status evec_hessenberg(evec_handle h, int64_t n, double *A, int64_t lda, double *Q,
