@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(kSplitThreads, 1)
                  int S, int M, int N, int aRow0, int aMpad, int Npad, const int *__restrict__ kend,
                  int kuni, const int *__restrict__ ea, const int *__restrict__ eb,
                  double *__restrict__ C, int64_t ldc, SplitUpd upd, int *err, int ntiles_n,
-                 int gw) {
+                 int gw, int mtiles) {
     extern __shared__ unsigned char smraw[];
     unsigned char *base = (unsigned char *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
     uint64_t *bars = (uint64_t *)(base + 2 * kStageBytes);
@@ -165,29 +165,38 @@ __global__ void __launch_bounds__(kSplitThreads, 1)
     int *sdy = sdx + kMaxSlots * kTN;                                 // [kMaxSlots][kTN]
     int *seb = sdy + kMaxSlots * kTN;                                 // [kTN]
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // CTA order: groups of gw column tiles; within a group the row bands in
-    // turn, the group's column tiles fastest, so the CTAs resident at one
-    // time cover about (148 / gw) row bands x gw column tiles and share
-    // their operand slices through L2; heaviest column tiles first
-    const int mt_count = gridDim.x / ntiles_n;
-    const int per = gw * mt_count;
-    const int grp = blockIdx.x / per;
-    const int rem = blockIdx.x - grp * per;
-    const int w = min(gw, ntiles_n - grp * gw);
-    const int mt = rem / w;
-    const int nt = ntiles_n - 1 - (grp * gw + rem % w);
-    const int n0 = nt * kTN, m0 = mt * kTM;
-    const int K = kend ? kend[nt] : kuni;
+    // Tile order: groups of gw column tiles; within a group the row bands
+    // in turn, the group's column tiles fastest, so the tiles in flight at
+    // one time cover about (148 / gw) row bands x gw column tiles and share
+    // their operand slices through L2; heaviest column tiles first.  A CTA
+    // takes tiles blockIdx.x, blockIdx.x + gridDim.x, ... (persistent: the
+    // next tile's loads and MMAs run while the epilogue writes the last
+    // one's results); the tile-update epilogue (UPD) is launched with one
+    // CTA per tile.
+    const int ntiles_total = mtiles * ntiles_n;
+    auto tile_of = [&](int t, int &m0_, int &n0_, int &nt_) {
+        const int per = gw * mtiles;
+        const int grp = t / per;
+        const int rem = t - grp * per;
+        const int w = min(gw, ntiles_n - grp * gw);
+        nt_ = ntiles_n - 1 - (grp * gw + rem % w);
+        n0_ = nt_ * kTN;
+        m0_ = (rem / w) * kTM;
+    };
+    // the K steps of a tile for this CTA: all of them, or its share of a K
+    // split over gridDim.z
+    auto ksteps = [&](int nt_, int &s0_) {
+        const int nst_all = (kend ? kend[nt_] : kuni) / kTK;
+        const int zper = ((int)gridDim.z > 1) ? (nst_all + (int)gridDim.z - 1) / (int)gridDim.z
+                                             : nst_all;
+        s0_ = (int)blockIdx.z * zper;
+        return max(0, min(nst_all, s0_ + zper) - s0_);
+    };
+    if (!UPD && gridDim.z > 1) C += (int64_t)blockIdx.z * upd.zstride;
+    int m0, n0, nt;   // the first tile (UPD: the only one)
+    tile_of((int)blockIdx.x, m0, n0, nt);
     if (UPD)
         for (int i = tid; i < kMaxSlots * kTN; i += kSplitThreads) red[i] = 0ull;
-    // the K steps of this CTA: all of them, or its share of a K split
-    const int nst_all = K / kTK;
-    const int zper = ((int)gridDim.z > 1) ? (nst_all + (int)gridDim.z - 1) / (int)gridDim.z
-                                         : nst_all;
-    const int s0 = (int)blockIdx.z * zper;
-    const int nst = max(0, min(nst_all, s0 + zper) - s0);
-    if (!UPD && gridDim.z > 1) C += (int64_t)blockIdx.z * upd.zstride;
-    const int chunks = (nst + kChunkStages - 1) / kChunkStages;
 
     if (warp == 8) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -210,11 +219,19 @@ __global__ void __launch_bounds__(kSplitThreads, 1)
 
     if (warp == 9) {
         if (lane == 0) {   // TMA producer
-            int issued = 0;
-            for (int it = 0; it < nst; it++) {
-                const int st = it & 1;
-                const uint32_t ph = (uint32_t)(it >> 1) & 1;
-                if (!mbar_wait(saddr(&bars[2 + st]), ph ^ 1, err)) break;
+            int gi = 0;   // K steps issued over all of this CTA's tiles
+            bool run = true;
+            for (int t = (int)blockIdx.x; run && t < ntiles_total; t += (int)gridDim.x) {
+                int m0, n0, nt, s0;
+                tile_of(t, m0, n0, nt);
+                const int nst = ksteps(nt, s0);
+            for (int it = 0; it < nst; it++, gi++) {
+                const int st = gi & 1;
+                const uint32_t ph = (uint32_t)(gi >> 1) & 1;
+                if (!mbar_wait(saddr(&bars[2 + st]), ph ^ 1, err)) {
+                    run = false;
+                    break;
+                }
                 asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
                                  saddr(&bars[st])),
                              "r"(S * (kStageA + kStageB)));
@@ -230,21 +247,35 @@ __global__ void __launch_bounds__(kSplitThreads, 1)
                         tma2d(saddr(sb + (c * kSplitMaxS + q) * (kStageB / 2)), &tmB,
                               (s0 + it) * kTK,
                               q * Npad + n0 + c * 32, saddr(&bars[st]));
-                issued = it + 1;
+            }
             }
             // the copies of the last stages have landed before the CTA ends
-            for (int it = max(0, issued - 2); it < issued; it++)
+            for (int it = max(0, gi - 2); it < gi; it++)
                 mbar_wait(saddr(&bars[it & 1]), (uint32_t)(it >> 1) & 1, err);
         }
     } else if (warp == 8) {
         if (lane == 0) {   // MMA issue
             const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTM >> 4) << 24);
-            for (int it = 0; it < nst; it++) {
-                const int st = it & 1;
-                const int c = it / kChunkStages, sic = it % kChunkStages;
-                if (sic == 0 && c > 0 && !mbar_wait(saddr(&bars[5]), (uint32_t)(c - 1) & 1, err))
+            int gi = 0, gc = 0;   // K steps and accumulator chunks over all tiles
+            bool run = true;
+            for (int t = (int)blockIdx.x; run && t < ntiles_total; t += (int)gridDim.x) {
+                int m0, n0, nt, s0;
+                tile_of(t, m0, n0, nt);
+                const int nst = ksteps(nt, s0);
+            for (int it = 0; it < nst; it++, gi++) {
+                const int st = gi & 1;
+                const int sic = it % kChunkStages;
+                // before a chunk overwrites TMEM, the epilogue has drained
+                // the previous one (of this tile or the last)
+                if (sic == 0 && gc > 0 &&
+                    !mbar_wait(saddr(&bars[5]), (uint32_t)(gc - 1) & 1, err)) {
+                    run = false;
                     break;
-                if (!mbar_wait(saddr(&bars[st]), (uint32_t)(it >> 1) & 1, err)) break;
+                }
+                if (!mbar_wait(saddr(&bars[st]), (uint32_t)(gi >> 1) & 1, err)) {
+                    run = false;
+                    break;
+                }
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 const uint32_t sa = saddr(base + st * kStageBytes);
                 const uint32_t sb = sa + kSplitMaxS * kStageA;
@@ -273,16 +304,25 @@ __global__ void __launch_bounds__(kSplitThreads, 1)
                 asm volatile(
                     "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                         saddr(&bars[2 + st])));
-                if (sic == kChunkStages - 1 || it == nst - 1)
+                if (sic == kChunkStages - 1 || it == nst - 1) {
                     asm volatile(
                         "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 "
                         "[%0];" ::"r"(saddr(&bars[4])));
+                    gc++;
+                }
+            }
             }
         }
     } else {   // epilogue warps 0-7
         const int quarter = warp & 3, half = warp >> 2;
-        const int row = m0 + quarter * 32 + lane;
         const int cb0 = half * 32;
+        int gc = 0;   // accumulator chunks drained over all tiles
+        bool ok = true;
+        for (int t = (int)blockIdx.x; ok && t < ntiles_total; t += (int)gridDim.x) {
+        int m0, n0, nt, s0;
+        tile_of(t, m0, n0, nt);
+        const int chunks = (ksteps(nt, s0) + kChunkStages - 1) / kChunkStages;
+        const int row = m0 + quarter * 32 + lane;
         if (UPD) {   // exponent tables of this CTA's (tile row, column) pairs
             const int rlo = upd.row_tile[m0], rhi = upd.row_tile[min(m0 + kTM, M) - 1];
             const int cnt = (rhi - rlo + 1) * kTN;
@@ -303,9 +343,8 @@ __global__ void __launch_bounds__(kSplitThreads, 1)
         float hi[32], lo[32];
 #pragma unroll
         for (int j = 0; j < 32; j++) { hi[j] = 0.0f; lo[j] = 0.0f; }
-        bool ok = true;
-        for (int c = 0; c < chunks && ok; c++) {
-            ok = mbar_wait(saddr(&bars[4]), (uint32_t)c & 1, err);
+        for (int c = 0; c < chunks && ok; c++, gc++) {
+            ok = mbar_wait(saddr(&bars[4]), (uint32_t)gc & 1, err);
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;");
 #pragma unroll
@@ -426,6 +465,7 @@ __global__ void __launch_bounds__(kSplitThreads, 1)
                 }
             }
         }
+        }   // tiles
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
@@ -570,15 +610,26 @@ cudaError_t split_gemm_sliced(const __nv_bfloat16 *sa, int Mpad, const __nv_bflo
     const int gw = std::max(1, std::min(ntn, (int)lround(sqrt(2.0 * nsm))));
     if (ksplit > 1) {
         k_split_gemm<false><<<dim3(ntn * mtn, 1, ksplit), kSplitThreads, smem, st>>>(
-            tmA, tmB, S, M, N, 0, Mpad, Npad, nullptr, Kpad, ea, eb, part, M, none, err, ntn, gw);
+            tmA, tmB, S, M, N, 0, Mpad, Npad, nullptr, Kpad, ea, eb, part, M, none, err, ntn, gw,
+            mtn);
         const int64_t MN = (int64_t)M * N;
         k_sum_partials<<<(unsigned)((MN + 255) / 256), 256, 0, st>>>(part, ksplit, M, N, C, ldc,
                                                                      acc);
         return cudaGetLastError();
     }
-    k_split_gemm<false><<<ntn * mtn, kSplitThreads, smem, st>>>(
+    // Products with one or two K steps (the rank-32 updates) run persistent,
+    // one CTA per SM taking every gridDim.x-th tile, so that a CTA's fixed
+    // cost (TMEM allocation, barrier set-up, the first loads) is paid once
+    // and the next tile's MMAs run under the last one's epilogue: the
+    // Hessenberg updates 108 -> 98 ms at n = 4096.  Longer products keep one
+    // CTA per tile: there the scheduler hands each free SM the next tile, so
+    // the tiles in flight stay a contiguous window that shares its operand
+    // slices through L2 (persistent CTAs drift apart; the n = 16384
+    // back-transformation went from 110 to 119 ms).
+    const int grid = Kpad <= 64 ? std::min(ntn * mtn, nsm) : ntn * mtn;
+    k_split_gemm<false><<<grid, kSplitThreads, smem, st>>>(
         tmA, tmB, S, M, N, 0, Mpad, Npad, kend, kend ? 0 : Kpad, ea, eb, C, ldc, none, err, ntn,
-        gw);
+        gw, mtn);
     return cudaGetLastError();
 }
 
@@ -721,7 +772,7 @@ cudaError_t split_update_step(const SplitUpdateCtx &ctx, int t0, int ts, int pro
     const int ntn = split_pad_n(N) / kTN;
     k_split_gemm<true><<<ntn * (mpad / kTM), kSplitThreads, smem, st>>>(
         ctx.tmA, ctx.tmB32, ctx.S, t0, N, prow0, mpad, ctx.Npad, nullptr, (K + kTK - 1) / kTK * kTK,
-        ea_panels + pea, eb, Y, ldy, upd, err, ntn, ntn);
+        ea_panels + pea, eb, Y, ldy, upd, err, ntn, ntn, mpad / kTM);
     return cudaGetLastError();
 }
 
