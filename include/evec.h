@@ -584,7 +584,7 @@ evec_status evec_tune_set(evec_handle h, int mode, int size_class, int tile);
  *   evec_plan_query); tile: 16..128, 0 = 64; cuda_stream: stream of the
  *   current device (NULL = legacy default stream).
  * The first call on a device looks up the array's device address (with
- * that device current); make that first call before any stream capture.
+ * that device current).
  * Every call shares the array and reuses whatever the previous call left in
  * it (the status word is cleared at the start of each call; everything else
  * is written before it is read).  Two calls that overlapped on the GPU
