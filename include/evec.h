@@ -75,7 +75,9 @@ typedef enum {
     EVEC_ETIMEOUT = 6,   /* a bounded device-side wait gave up (reported by evec_sync) */
     EVEC_ERESIDUAL = 7,  /* refine = 2: an eigenvalue failed the residual
                             gate in every repeat, FP64 included (evec_sync) */
-    EVEC_ECAPACITY = 8   /* problem larger than evec_standard_noalloc's fixed scratch */
+    EVEC_ECAPACITY = 8,  /* problem larger than evec_standard_noalloc's fixed scratch */
+    EVEC_EBOUNDS = 9     /* checked build only: a device access outside the range
+                            the plan allows was skipped; index = the site */
 } evec_status;
 
 typedef enum {
@@ -609,6 +611,13 @@ const char *evec_last_cuda_error(void);
 
 /* Static, human-readable name of a status code. */
 const char *evec_strerror(evec_status s);
+
+/* 1 when this library is the checked build (compiled with -DEVEC_CHECK:
+ * the kernels test the row, column, tile and segment indices of their main
+ * device accesses against the plan, skip an access that fails and report
+ * EVEC_EBOUNDS at evec_sync with the site's number as the index), else 0.
+ * Results are otherwise identical to the normal build's. */
+int evec_checked_build(void);
 
 #ifdef __cplusplus
 }

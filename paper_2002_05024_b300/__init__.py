@@ -22,10 +22,13 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libevec.so")
+# the checked build (bounds checks of the kernels' main device accesses,
+# reported as EVEC_EBOUNDS); use_checked_build() selects it
+CHECK_LIB_PATH = os.path.join(_HERE, "_lib", "libevec_check.so")
 
 STATUS = {0: "EVEC_OK", 1: "EVEC_EINVAL", 2: "EVEC_ENOTSCHUR", 3: "EVEC_ENONFINITE",
           4: "EVEC_ENOMEM", 5: "EVEC_ECUDA", 6: "EVEC_ETIMEOUT", 7: "EVEC_ERESIDUAL",
-          8: "EVEC_ECAPACITY"}
+          8: "EVEC_ECAPACITY", 9: "EVEC_EBOUNDS"}
 EVEC_OK, EVEC_EINVAL, EVEC_ENOTSCHUR, EVEC_ENONFINITE = 0, 1, 2, 3
 EVEC_ENOMEM, EVEC_ECUDA, EVEC_ETIMEOUT, EVEC_ERESIDUAL = 4, 5, 6, 7
 EVEC_ECAPACITY = 8
@@ -57,6 +60,15 @@ MODES = {"fp64": 0, "split": 1}
 
 _lib = None
 _lock = threading.Lock()
+
+
+def use_checked_build() -> None:
+    """Load the checked build instead of the normal one; call before the
+    first use of the library in the process."""
+    global LIB_PATH
+    if _lib is not None:
+        raise RuntimeError("the library is already loaded")
+    LIB_PATH = CHECK_LIB_PATH
 
 
 def lib() -> ctypes.CDLL:

@@ -142,7 +142,8 @@ __device__ void diag_tile_big(int s, int list_pos0, const double *__restrict__ T
     for (int idx = tid; idx < kUnits * ts; idx += kThreads) {
         const int uu = idx / ts, i = idx % ts;
         const int c = ucol[uu];
-        if (c >= 0 && (RHS || !uown[uu])) {
+        if (c >= 0 && (RHS || !uown[uu]) &&
+            evec_in(P, t0 + i < P.n && c + (C ? 1 : 0) < P.m, 111)) {
             cp_async8(&yr[i * ys + uu], &Y[(t0 + i) + (int64_t)c * ldy]);
             if (C) cp_async8(&yi[i * ys + uu], &Y[(t0 + i) + (int64_t)(c + 1) * ldy]);
         } else {
@@ -482,7 +483,7 @@ __device__ void diag_tile_big(int s, int list_pos0, const double *__restrict__ T
     for (int idx = tid; idx < kUnits * ts; idx += kThreads) {
         const int uu = idx / ts, i = idx % ts;
         const int c = ucol[uu];
-        if (c >= 0) {
+        if (c >= 0 && evec_in(P, t0 + i < P.n && c + (C ? 1 : 0) < P.m, 112)) {
             Y[(t0 + i) + (int64_t)c * ldy] = yr[i * ys + uu];
             if (C) Y[(t0 + i) + (int64_t)(c + 1) * ldy] = yi[i * ys + uu];
         }
@@ -491,7 +492,7 @@ __device__ void diag_tile_big(int s, int list_pos0, const double *__restrict__ T
     for (int idx = tid; idx < items; idx += kThreads) {
         const int uu = idx % kUnits, r = idx / kUnits;
         const int c = ucol[uu];
-        if (c < 0) continue;
+        if (c < 0 || !evec_in(P, r < P.ntiles && c + (C ? 1 : 0) < m, 113)) continue;
         const int64_t at = (int64_t)r * m + c;
         const int es = ue[uu];
         const bool ownu = !RHS && uown[uu];   // fresh segments above the own block

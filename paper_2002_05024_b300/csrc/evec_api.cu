@@ -894,6 +894,7 @@ void pack_plan(Packer &pk, const HostPlan &P, Plan &dp) {
                        ? nullptr
                        : (const double *)pk.put(P.unit_smin.data(), P.unit_smin.size() * 8, 8);
     dp.blk_size = (const int8_t *)pk.put(P.blk_size.data(), P.blk_size.size(), 1);
+    dp.status = nullptr;
 }
 
 static size_t plan_bytes(const HostPlan &P) {
@@ -918,6 +919,7 @@ evec_status upload_plan(evec_handle h, Plan &dp) {
     pk.put(P.col_lam_im.data(), P.col_lam_im.size() * 8, 8);
     pk.put(P.col_beta.data(), P.col_beta.size() * 8, 8);
     pack_plan(pk, P, dp);
+    dp.status = h->status_d;
     h->bt_kend_d = (const int32_t *)pk.put(P.bt_kend.data(), P.bt_kend.size() * 4, 4);
     h->row_tile_d = (const int32_t *)pk.put(P.row_tile.data(), P.row_tile.size() * 4, 4);
     h->prow0_d = (const int32_t *)pk.put(P.prow0.data(), P.prow0.size() * 4, 4);
@@ -946,8 +948,17 @@ const char *evec_strerror(evec_status s) {
         case EVEC_ETIMEOUT: return "EVEC_ETIMEOUT: bounded device wait gave up";
         case EVEC_ERESIDUAL: return "EVEC_ERESIDUAL: residual gate failed";
         case EVEC_ECAPACITY: return "EVEC_ECAPACITY: larger than the fixed no-allocation scratch";
+        case EVEC_EBOUNDS: return "EVEC_EBOUNDS: checked build: an out-of-range access was skipped";
     }
     return "unknown evec_status";
+}
+
+int evec_checked_build(void) {
+#ifdef EVEC_CHECK
+    return 1;
+#else
+    return 0;
+#endif
 }
 
 const char *evec_last_cuda_error(void) {
@@ -2031,6 +2042,7 @@ static evec_status run_batch(evec_handle h, int64_t count, const int64_t *n_host
         const HostPlan &P = plans[i];
         BatchItem &B = items[q];
         pack_plan(pk, P, B.P);
+        B.P.status = h->status_d;
         B.T = T_packed + t_off_host[i];
         B.ldt = n_host[i];
         B.t_base = t_off_host[i];

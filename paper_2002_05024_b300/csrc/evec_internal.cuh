@@ -65,7 +65,22 @@ struct Plan {
     // pencils (beta S - alpha T) only, else null: unit_lam holds alpha
     const double *unit_beta;    // [nunits]
     const double *unit_smin;    // [nunits] perturbation threshold of the small solves
+    DevStatus *status;          // the handle's status word (bounds reports of a checked build)
 };
+
+// Bounds checks of the checked build (compiled with -DEVEC_CHECK): a
+// guarded access runs only when evec_in(P, ok, site) holds; a failed check
+// records EVEC_EBOUNDS (9) with the site's number as the index in the
+// plan's status word, so evec_sync reports it, and the access is skipped.
+// In the normal build evec_in is `true` and the compiler drops the test.
+#ifdef EVEC_CHECK
+__device__ __forceinline__ bool evec_in(const Plan &P, bool ok, int site) {
+    if (!ok && P.status && atomicCAS(&P.status->code, 0, 9) == 0) P.status->index = site;
+    return ok;
+}
+#else
+__device__ __forceinline__ bool evec_in(const Plan &, bool, int) { return true; }
+#endif
 
 // The second matrix T of a pencil (upper triangular) with its tile norms
 // (tau[r * N + s] = |T_rs|_inf) and in-tile block column norms.

@@ -300,6 +300,7 @@ extern "C" evec_status evec_standard_noalloc(int64_t n, const double *T, int64_t
     dp.blk_size = (const int8_t *)put(P.blk_size, (size_t)P.nblk, 1);
 
     DevStatus *status = (DevStatus *)(base + L.status);
+    dp.status = status;
     double *tau = (double *)(base + L.tau);
     double *blk_tau = (double *)(base + L.blk_tau);
     int32_t *seg_e = (int32_t *)(base + L.seg_e);

@@ -40,6 +40,9 @@ __global__ void __launch_bounds__(kWarps * 32)
     const int c = P.unit_tile[u];
     const int kb = P.unit_blk[u];
     const int row_end = P.blk_start[kb] + P.blk_size[kb];
+    if (!evec_in(P, u < P.nunits && col + (cplx ? 1 : 0) < m && row_end <= n && c < P.ntiles,
+                 131))
+        return;
     double *yr = Y + (int64_t)col * ldy;
     double *yi = Y + (int64_t)(col + 1) * ldy;
     __shared__ int sbest[kWarps];
@@ -96,8 +99,10 @@ __global__ void __launch_bounds__(kWarps * 32)
     const int u = u0 + blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t n = P.n;
+    if (!evec_in(P, u < P.nunits, 132)) return;
     const int col = P.unit_col[u];
     const bool cplx = P.unit_lam[2 * u + 1] != 0.0;
+    if (!evec_in(P, col + (cplx ? 1 : 0) < P.m, 133)) return;
     double *xr = X + (int64_t)col * ldx;
     double *xi = X + (int64_t)(col + 1) * ldx;
     __shared__ double smax[kWarps];

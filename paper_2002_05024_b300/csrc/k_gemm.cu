@@ -143,6 +143,7 @@ __global__ void __launch_bounds__(kThreads)
     const int64_t m = P.m;
     const int64_t j0 = (int64_t)P.tile_col[s] + (int64_t)blockIdx.x * kBN;
     const int ncols = (int)min((int64_t)kBN, m - j0);
+    if (!evec_in(P, r < s && r0 + rows <= P.n && k0 + K <= P.n && ncols > 0, 121)) return;
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
 
@@ -231,9 +232,11 @@ __global__ void __launch_bounds__(kThreads)
     const int64_t i0 = (int64_t)band * BM;
     const int rows = (int)min((int64_t)BM, n - i0);
     // rows of Y beyond the last column's diagonal block are zero
+    if (!evec_in(P, rows > 0 && ncols > 0, 141)) return;
     const int ul = P.col_unit[j0 + ncols - 1];
     const int kb = P.unit_blk[ul];
     const int K = P.blk_start[kb] + P.blk_size[kb];
+    if (!evec_in(P, K <= n, 142)) return;
 
     double acc[MI][4];
     dfma_mainloop<BM>(Q + i0, ldq, rows, Y + j0 * ldy, ldy, K, ncols, sm, false, acc);

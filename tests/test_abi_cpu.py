@@ -40,8 +40,22 @@ def test_library_exports_every_declared_symbol():
         assert hasattr(ev.lib(), n)
 
 
+def test_checked_build_exports_the_same_symbols():
+    from paper_2002_05024_b300 import build as b
+    b.build(checked=True)
+    names = _declared_functions()
+    out = subprocess.run(["nm", "-D", "--defined-only", ev.CHECK_LIB_PATH],
+                         capture_output=True, text=True, check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    assert not [n for n in names if n not in exported]
+    # the flag itself, without a GPU
+    Lc = ctypes.CDLL(ev.CHECK_LIB_PATH)
+    assert Lc.evec_checked_build() == 1
+    assert ev.lib().evec_checked_build() == 0
+
+
 def test_strerror_names_every_status():
-    for s in range(9):
+    for s in range(10):
         assert ev.strerror(s).startswith(ev.STATUS[s])
 
 
