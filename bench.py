@@ -906,6 +906,10 @@ def run_ours(args, rank, world, local_rank):
         "e2e": e2e,
         "cpu_baseline": cpu,
         "records": records,
+        # the metric's comparisons, from the records (same input, same GPU)
+        "split_vs_plain": records.get("split_vs_plain") if records else None,
+        "split_no_sweep_vs_plain": records.get("split_no_sweep_vs_plain") if records else None,
+        "batched_vs_plain": records.get("batched_vs_plain") if records else None,
     }
     print(json.dumps(line), flush=True)
     if dist:
