@@ -100,6 +100,11 @@ def parse_args():
     ap.add_argument("--side", choices=["right", "left"], default="right",
                     help="single: right eigenvectors (default) or left ones (u^H T = lambda u^H)")
     ap.add_argument("--batch", type=int, default=2000)
+    ap.add_argument("--input", choices=["config0", "adversarial"], default="config0",
+                    help="single workload: config-0 Schur form (default) or the clustered "
+                         "adversarial one (4 clusters 1e-9 apart, upper part N(0, 1) x 1e3)")
+    ap.add_argument("--no-other", dest="other", action="store_false",
+                    help="default line: leave out the short runs of the other workloads")
     args = ap.parse_args()
     if not args.n:
         args.n = (16384 if args.workload == "single" and args.side == "right" else
@@ -115,10 +120,73 @@ METRIC_SINGLE = ("eigvec columns/s (robust eigenvectors incl. back-transformatio
                  "TFLOPS vs the FP64 roofline; split/batched vs plain at residual <= 10 n")
 
 
-def workload(n):
-    T, blocks = workloads.config0_schur(n, seed=workloads.SEED_BASE + 1)
+def workload(n, kind="config0"):
+    if kind == "adversarial":
+        T, blocks = workloads.adversarial_schur(n, seed=workloads.SEED_BASE + 11)
+    else:
+        T, blocks = workloads.config0_schur(n, seed=workloads.SEED_BASE + 1)
     Q = workloads.householder_orthogonal(n, seed=workloads.SEED_BASE + 101)
     return T, blocks, Q
+
+
+# Short runs of the other workloads that the default line carries under
+# "other_workloads" (each a child process of this script, so its device
+# memory and its own timing are separate): name, arguments, what it is.
+OTHER_WORKLOADS = [
+    ("config1a_fp64", ["--n", "4096", "--no-records"],
+     "n = 4096 config-0 Schur form + Q, FP64, tile 64"),
+    ("config1a_split_sweep", ["--n", "4096", "--no-records", "--mode", "split", "--refine"],
+     "n = 4096 config-0 Schur form + Q, split (8 slices) + FP64 residual-correction sweep"),
+    ("config1b_fp64", ["--n", "4096", "--no-records", "--input", "adversarial"],
+     "n = 4096 clustered adversarial Schur form + Q, FP64, tile 64"),
+    ("config4_fp64", ["--workload", "generalized"],
+     "n = 8192 pencil (S, T) + Z, FP64"),
+    ("config4_split", ["--workload", "generalized", "--mode", "split"],
+     "n = 8192 pencil (S, T) + Z, split (8 slices)"),
+    ("next1_trsolve_split", ["--workload", "trsolve", "--mode", "split"],
+     "robust triangular solve, n = 4096, 4096 right-hand sides, split"),
+    ("next2_left_split", ["--n", "4096", "--no-records", "--side", "left", "--mode", "split"],
+     "left eigenvectors, n = 4096 + Q, split"),
+    ("next2_batched_pencils", ["--workload", "batched_generalized"],
+     "2000 pencils, n in [32, 1024], 30% selected, FP64, one persistent launch"),
+    ("next3_window_split", ["--workload", "window", "--mode", "split"],
+     "reordering off-diagonal updates, n = 4096 + Q, 32 windows of 128, split"),
+    ("next4_hessenberg_split", ["--workload", "hessenberg", "--mode", "split"],
+     "Hessenberg reduction with Q, n = 4096, split updates"),
+]
+OTHER_KEYS = ("metric", "value", "unit", "ms_per_step", "steps", "warmup", "dtype",
+              "tflops_fp64", "tflops_fp64_equivalent", "quality", "e2e")
+
+
+def other_workloads_record(steps=3, warmup=2, timeout=600):
+    """Each entry of OTHER_WORKLOADS as a child run of this script (no CPU
+    baseline), reduced to its rate, quality and dominant kernel's roofline;
+    a child that fails is recorded with its exit status, not raised."""
+    out = {}
+    for name, extra, what in OTHER_WORKLOADS:
+        cmd = [sys.executable, os.path.abspath(__file__), "--steps", str(steps), "--warmup",
+               str(warmup), "--no-cpu-baseline", *extra]
+        t = time.time()
+        try:
+            r = subprocess.run(cmd, capture_output=True, text=True, timeout=timeout, cwd=ROOT)
+            lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+            if r.returncode != 0 or not lines:
+                out[name] = {"what": what, "error": f"exit {r.returncode}",
+                             "tail": (r.stderr or r.stdout)[-300:]}
+                continue
+            line = json.loads(lines[-1])
+        except Exception as exc:   # timeout, bad JSON: record it
+            out[name] = {"what": what, "error": repr(exc)[:300]}
+            continue
+        rec = {"what": what, "args": " ".join(extra), "wall_s": round(time.time() - t, 1)}
+        rec.update({k: line[k] for k in OTHER_KEYS if k in line})
+        rec["workload"] = (line.get("config") or {}).get("workload")
+        roof = line.get("roofline")
+        if isinstance(roof, dict):
+            rec["roofline"] = {k: roof.get(k) for k in ("kernel", "bound", "achieved", "peak",
+                                                         "unit", "frac")}
+        out[name] = rec
+    return out
 
 
 def default_tile(n, mode):
@@ -634,7 +702,7 @@ def run_reference(args, rank, world):
     if args.workload in ("batched", "batched_generalized", "generalized", "hessenberg", "window"):
         return run_reference_other(args)
     n = args.n
-    T, blocks, Q = workload(n)
+    T, blocks, Q = workload(n, args.input)
     m = sum(sz for _, sz in blocks)
     # a bounded sample per step (about 1.5 s of oracle work at n = 16384),
     # extrapolated to the whole workload by the flop count
@@ -655,8 +723,10 @@ def run_reference(args, rank, world):
         "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": f"single large Schur form: n={n} real Schur form (config-0 "
-                               "distribution) + Q (product of 64 Householder reflectors), all "
+        "config": {"workload": f"single large Schur form: n={n} real Schur form ("
+                               + ("clustered adversarial" if args.input == "adversarial" else
+                                  "config-0 distribution")
+                               + ") + Q (product of 64 Householder reflectors), all "
                                f"{m} " + ("left eigenvectors" if args.side == "left" else
                                           "eigenvectors")
                                + "; the oracle on sampled columns, extrapolated",
@@ -694,7 +764,7 @@ def run_ours(args, rank, world, local_rank):
         dist.init_process_group("nccl", device_id=dev)
 
     n = args.n
-    T, blocks, Q = workload(n)
+    T, blocks, Q = workload(n, args.input)
     m = sum(sz for _, sz in blocks)
     d = np.ascontiguousarray(np.diagonal(T))
     tile_used = args.tile or default_tile(n, args.mode)
@@ -867,6 +937,10 @@ def run_ours(args, rank, world, local_rank):
                                             max(1, min(args.steps, 5)),
                                             max(1, min(args.warmup, 2)), peaks)
         records["batched_vs_plain"] = records["batched"]["batched_vs_plain"]
+        if args.other:
+            del dT, dQ, X, e, lr, li, out
+            torch.cuda.empty_cache()
+            records["other_workloads"] = other_workloads_record()
     if args.mode == "fp64":
         dtype, how = "f64", "FP64 (DFMA) throughout"
     else:
@@ -880,9 +954,13 @@ def run_ours(args, rank, world, local_rank):
         "scaling": "weak", "vs_baseline": None,
         "dtype": dtype,
         "data": "synthetic",
-        "config": {"workload": f"single large Schur form: n={n} real Schur form (config-0 "
-                               "distribution: 75% 1x1 blocks, 25% standardized 2x2 blocks, "
-                               "strictly upper N(0, 1)) + Q (product of 64 Householder "
+        "config": {"workload": f"single large Schur form: n={n} real Schur form "
+                               + ("(clustered adversarial: 4 clusters of real eigenvalues "
+                                  "1e-9 apart, strictly upper N(0, 1) x 1e3)"
+                                  if args.input == "adversarial" else
+                                  "(config-0 distribution: 75% 1x1 blocks, 25% standardized "
+                                  "2x2 blocks, strictly upper N(0, 1))")
+                               + " + Q (product of 64 Householder "
                                f"reflectors), all {m} "
                                + ("left eigenvectors; " if left else "eigenvectors; ")
                                + "timed path: " + how
