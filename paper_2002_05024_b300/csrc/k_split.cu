@@ -144,6 +144,19 @@ struct SplitUpd {
 };
 constexpr int kMaxSlots = 12;    // tile rows met by one 128-row CTA tile (tiles >= 15 rows)
 
+// barrier 1 over the 256 threads of the epilogue warps, returning the AND of
+// their predicates
+__device__ __forceinline__ bool epi_bar_and(bool p) {
+    int r;
+    asm volatile(
+        "{\n.reg .pred pi, po;\nsetp.ne.b32 pi, %1, 0;\n"
+        "bar.red.and.pred po, 1, 256, pi;\nselp.b32 %0, 1, 0, po;\n}\n"
+        : "=r"(r)
+        : "r"((int)p)
+        : "memory");
+    return r != 0;
+}
+
 // C[i, j] (FP64, column-major, rows < M, cols < N) = 2^(ea_i + eb_j) *
 // sum_k A~_ik B~_kj over k < K (kend[N tile], or kuni when kend is null);
 // with UPD the tile-update epilogue instead.  A slice p of this product
@@ -171,8 +184,8 @@ __global__ void __launch_bounds__(kSplitThreads, 1)
     // their operand slices through L2; heaviest column tiles first.  A CTA
     // takes tiles blockIdx.x, blockIdx.x + gridDim.x, ... (persistent: the
     // next tile's loads and MMAs run while the epilogue writes the last
-    // one's results); the tile-update epilogue (UPD) is launched with one
-    // CTA per tile.
+    // one's results); the tile-update epilogue (UPD) merges each tile's
+    // column maxima before it takes the next tile.
     const int ntiles_total = mtiles * ntiles_n;
     auto tile_of = [&](int t, int &m0_, int &n0_, int &nt_) {
         const int per = gw * mtiles;
@@ -193,8 +206,6 @@ __global__ void __launch_bounds__(kSplitThreads, 1)
         return max(0, min(nst_all, s0_ + zper) - s0_);
     };
     if (!UPD && gridDim.z > 1) C += (int64_t)blockIdx.z * upd.zstride;
-    int m0, n0, nt;   // the first tile (UPD: the only one)
-    tile_of((int)blockIdx.x, m0, n0, nt);
     if (UPD)
         for (int i = tid; i < kMaxSlots * kTN; i += kSplitThreads) red[i] = 0ull;
 
@@ -464,20 +475,24 @@ __global__ void __launch_bounds__(kSplitThreads, 1)
                     if (head && b) atomicMax(&red[slot * kTN + c], b);
                 }
             }
+            // the tile's column maxima into the segment maxima, red[] cleared
+            // for the next tile of this CTA; the eight warps agree on ok, so
+            // a warp whose wait gave up never leaves the others at a barrier
+            ok = epi_bar_and(ok);
+            const int r0 = upd.row_tile[m0];
+            for (int i = tid; i < kMaxSlots * kTN; i += 256) {
+                const unsigned long long v = red[i];
+                const int col = n0 + i % kTN;
+                if (v != 0ull && col < N)
+                    atomicMax(&upd.nu[(int64_t)(r0 + i / kTN) * upd.m + upd.col0 + col], v);
+                red[i] = 0ull;
+            }
+            ok = epi_bar_and(ok);
         }
         }   // tiles
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-    if (UPD) {
-        const int r0 = upd.row_tile[m0];
-        for (int i = tid; i < kMaxSlots * kTN; i += kSplitThreads) {
-            const unsigned long long v = red[i];
-            const int col = n0 + i % kTN;
-            if (v != 0ull && col < N)
-                atomicMax(&upd.nu[(int64_t)(r0 + i / kTN) * upd.m + upd.col0 + col], v);
-        }
-    }
     if (warp == 8)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                      "r"(kTmemCols));
@@ -770,7 +785,18 @@ cudaError_t split_update_step(const SplitUpdateCtx &ctx, int t0, int ts, int pro
     upd.m = m;
     upd.col0 = col0;
     const int ntn = split_pad_n(N) / kTN;
-    k_split_gemm<true><<<ntn * (mpad / kTM), kSplitThreads, smem, st>>>(
+    // persistent, one CTA per SM over every gridDim.x-th tile: once a tile's
+    // accumulators are drained, the next tile's loads and MMAs run under the
+    // rest of its epilogue (the FP64 read-modify-write of Y and the column
+    // maxima), which with one CTA per tile left the tensor pipe idle
+    int nsm = 148, dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        nsm = 148;
+    }
+    const int tiles = ntn * (mpad / kTM);
+    k_split_gemm<true><<<std::min(tiles, nsm), kSplitThreads, smem, st>>>(
         ctx.tmA, ctx.tmB32, ctx.S, t0, N, prow0, mpad, ctx.Npad, nullptr, (K + kTK - 1) / kTK * kTK,
         ea_panels + pea, eb, Y, ldy, upd, err, ntn, ntn, mpad / kTM);
     return cudaGetLastError();
