@@ -191,8 +191,8 @@ def other_workloads_record(steps=3, warmup=2, timeout=600):
 
 def default_tile(n, mode):
     """The library's tile when opt->tile is 0: 64 rows, 256 in split mode
-    from n = 10240."""
-    return 256 if mode == "split" and n >= 10240 else 64
+    from n = 8192."""
+    return 256 if mode == "split" and n >= 8192 else 64
 
 
 def flop_counts(n, blocks, tile_start, with_q=True, res=None):

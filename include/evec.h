@@ -91,7 +91,7 @@ typedef enum {
 typedef struct {
     int mode;    /* evec_mode */
     int tile;    /* tile size nb of the tiled solve, 16..512; 0 = 64, or
-                    256 in EVEC_SPLIT mode for n >= 10240 (the faster
+                    256 in EVEC_SPLIT mode for n >= 8192 (the faster
                     choice measured on B300).  Tiles above 64 rows are
                     solved in sub-blocks of at most 64 rows with one scale
                     exponent per tile segment */

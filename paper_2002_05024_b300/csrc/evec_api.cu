@@ -754,14 +754,15 @@ evec_status cuda_status(cudaError_t e) {
 #define EVEC_CUDA(x) EVEC_TRY(cuda_status(x))
 
 // opt->tile, else the default: 64 rows, 256 in EVEC_SPLIT mode from
-// n = 10240 (measured on B300, all columns with Q: at n = 4096 and 8192 the
-// 64-row tiles are faster, 10.3 against 12.3 and 52.5 against 56.0 ms; at
-// n = 12288 and 16384 the 256-row tiles, 146 against 158 and 312 against
-// 360 ms, since the split updates then dominate and a 256-row tile makes
-// a quarter of the update epilogues).
+// n = 8192 (measured on B300, all columns with Q, with the persistent split
+// update of the larger tiles: at n = 4096 the 64-row tiles are faster,
+// 10.3 against 11.9 ms; at n = 8192, 12288 and 16384 the 256-row tiles,
+// 50.6 against 52.6, 133.5 against 158.3 and 281.5 against 360 ms, since
+// the split updates then dominate and a 256-row tile makes a quarter of
+// the update epilogues).
 int resolve_tile(const evec_opts *opt, int64_t n) {
     if (opt && opt->tile) return opt->tile;
-    return (opt && opt->mode == EVEC_SPLIT && n >= 10240) ? 256 : 64;
+    return (opt && opt->mode == EVEC_SPLIT && n >= 8192) ? 256 : 64;
 }
 
 cudaEvent_t take_event(evec_handle h) {
