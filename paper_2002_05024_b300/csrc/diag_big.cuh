@@ -326,7 +326,7 @@ __device__ void diag_tile_big(int s, int list_pos0, const double *__restrict__ T
                         z1 = {o[1], C ? o[3] : 0.0};
                     }
                 } else {
-                    sc = solve<C>(F, bs, r0, r1, z0, z1);
+                    sc = solve<C>(F, bs, r0, r1, z0, z1, (g & 1) != 0, unit_mask<G>());
                 }
                 if (sc != 0) {
                     scale_all(sc);

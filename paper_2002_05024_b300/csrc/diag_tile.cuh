@@ -124,6 +124,59 @@ __device__ Fac factor_pencil(int bs, const double *Ss, const double *Tt, int ts,
     return factor_matrix<C>(bs, M, smin);
 }
 
+// The lanes of one unit: the lane group's mask (G lanes from a multiple of G)
+template <int G>
+__device__ __forceinline__ unsigned unit_mask() {
+    if constexpr (G >= 32) return 0xffffffffu;
+    else return ((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1));
+}
+
+// A complex value whose real part is formed on the even lanes of a unit and
+// its imaginary part on the odd ones: each lane holds its own part in `mine`;
+// the pair of lanes (g, g ^ 1) swaps them.
+__device__ __forceinline__ Cx cx_join(double mine, bool odd, unsigned mask) {
+    const double other = __shfl_xor_sync(mask, mine, 1);
+    return odd ? Cx{other, mine} : Cx{mine, other};
+}
+
+// Complex case of apply: the same FP64 expressions, component by component,
+// as the form below, but each lane evaluates only its own component (even
+// lanes the real parts, odd lanes the imaginary ones) and the partner lane
+// supplies the other.  On B300 an FP64 warp instruction costs its
+// sub-partition 64 cycles whatever its active lanes, so this halves the
+// FP64 instructions of a complex pair's small solves (1x1: 2 instead of 4,
+// 2x2: 8 instead of 16) on the critical chain; the results are
+// bit-identical (the operand selections and negations are exact).
+__device__ __forceinline__ void apply_split(const Fac &F, int bs, Cx r0, Cx r1, Cx &z0, Cx &z1,
+                                            bool odd, unsigned mask) {
+    if (bs == 1) {
+        // z0 = r0 ia: re = fma(r.re, ia.re, -r.im ia.im), im = fma(r.re, ia.im, r.im ia.re)
+        const double p = r0.im * (odd ? F.ia.re : F.ia.im);
+        const double v = fma(r0.re, odd ? F.ia.im : F.ia.re, odd ? p : -p);
+        z0 = cx_join(v, odd, mask);
+        z1 = {0.0, 0.0};
+        return;
+    }
+    const Cx d1 = F.pr == 0 ? r0 : r1, d2 = F.pr == 0 ? r1 : r0;
+    // t = d2 - l d1:
+    //   re = fma(-l.re, d1.re, fma(l.im, d1.im, d2.re))
+    //   im = fma(-l.re, d1.im, fma(-l.im, d1.re, d2.im))
+    const double ti = fma(odd ? -F.l.im : F.l.im, odd ? d1.re : d1.im, odd ? d2.im : d2.re);
+    const Cx t = cx_join(fma(-F.l.re, odd ? d1.im : d1.re, ti), odd, mask);
+    // w2 = t iu, as cmul
+    const double q = t.im * (odd ? F.iu.re : F.iu.im);
+    const Cx w2 = cx_join(fma(t.re, odd ? F.iu.im : F.iu.re, odd ? q : -q), odd, mask);
+    // w1 = d1 ia - g w2:
+    //   re = fma(d1.re, ia.re, fma(-d1.im, ia.im, fma(-g.re, w2.re, g.im w2.im)))
+    //   im = fma(d1.re, ia.im, fma(d1.im, ia.re, fma(-g.re, w2.im, -g.im w2.re)))
+    const double m = (odd ? -F.g.im : F.g.im) * (odd ? w2.re : w2.im);
+    const double a1 = fma(-F.g.re, odd ? w2.im : w2.re, m);
+    const double a2 = fma(odd ? d1.im : -d1.im, odd ? F.ia.re : F.ia.im, a1);
+    const Cx w1 = cx_join(fma(d1.re, odd ? F.ia.im : F.ia.re, a2), odd, mask);
+    z0 = F.pc == 0 ? w1 : w2;
+    z1 = F.pc == 0 ? w2 : w1;
+}
+
 template <bool C>
 __device__ __forceinline__ void apply(const Fac &F, int bs, Cx r0, Cx r1, Cx &z0, Cx &z1) {
     if (bs == 1) {
@@ -155,9 +208,19 @@ __device__ __forceinline__ void apply(const Fac &F, int bs, Cx r0, Cx r1, Cx &z0
 // exact up to rounding whenever its result is finite and <= Omega (an
 // intermediate overflow always leaves an Inf or NaN in the result);
 // otherwise normalise the right-hand side, apply again and fit sc <= 0.
+// Complex units (C): every lane of the unit's group (mask) calls this
+// together, with odd = its lane parity within the group.
 template <bool C>
-__device__ __forceinline__ int solve(const Fac &F, int bs, Cx r0, Cx r1, Cx &z0, Cx &z1) {
-    apply<C>(F, bs, r0, r1, z0, z1);
+__device__ __forceinline__ void apply_any(const Fac &F, int bs, Cx r0, Cx r1, Cx &z0, Cx &z1,
+                                         bool odd, unsigned mask) {
+    if (C) apply_split(F, bs, r0, r1, z0, z1, odd, mask);
+    else apply<C>(F, bs, r0, r1, z0, z1);
+}
+
+template <bool C>
+__device__ __forceinline__ int solve(const Fac &F, int bs, Cx r0, Cx r1, Cx &z0, Cx &z1,
+                                     bool odd, unsigned mask) {
+    apply_any<C>(F, bs, r0, r1, z0, z1, odd, mask);
     // |z| < 2^1020 (and finite) on the exponent fields alone
     const int fz = max(max(efield(z0.re), efield(z0.im)), max(efield(z1.re), efield(z1.im)));
     if (fz <= 2042) return 0;
@@ -165,7 +228,7 @@ __device__ __forceinline__ int solve(const Fac &F, int bs, Cx r0, Cx r1, Cx &z0,
     if (rb == 0) { z0 = {0.0, 0.0}; z1 = {0.0, 0.0}; return 0; }
     const int kr = ilog2_abs(__longlong_as_double(rb)) + 1;
     Cx h0, h1;
-    apply<C>(F, bs, cscale(r0, -kr), cscale(r1, -kr), h0, h1);
+    apply_any<C>(F, bs, cscale(r0, -kr), cscale(r1, -kr), h0, h1, odd, mask);
     const long long hb = max(cbits(h0), cbits(h1));
     if (hb == 0) { z0 = {0.0, 0.0}; z1 = {0.0, 0.0}; return 0; }
     int sc = kOmegaExp - ilog2_abs(__longlong_as_double(hb)) - 1 - kr;
@@ -517,7 +580,7 @@ __device__ void diag_tile(int s, int list_pos0, const double *__restrict__ T, in
                     z1 = {o[1], C ? o[3] : 0.0};
                 }
             } else {
-                sc = solve<C>(F, bs, r0, r1, z0, z1);
+                sc = solve<C>(F, bs, r0, r1, z0, z1, (g & 1) != 0, unit_mask<G>());
             }
             if (sc != 0) {
                 scale_rows(sc);
