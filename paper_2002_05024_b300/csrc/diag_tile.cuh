@@ -92,8 +92,21 @@ __device__ Fac factor_matrix(int bs, Cx (&M)[2][2], double smin) {
     return F;
 }
 
+// The diagonal tile of diag_tile is kept in shared memory packed by
+// columns: column j holds rows 0 .. j + 1 (the upper part and the first
+// subdiagonal, all a quasi-triangular tile has) from pk_col(j) on, about
+// half of a square ts x ts array.
+__host__ __device__ constexpr int pk_col(int j) { return j * (j + 3) / 2; }
+__host__ __device__ constexpr int pk_size(int t) { return t * (t + 3) / 2; }
+
+// entry (i, j) of a tile: packed (PK, i <= j + 1) or square with ld
+template <bool PK>
+__device__ __forceinline__ double tile_at(const double *A, int ld, int i, int j) {
+    return PK ? A[pk_col(j) + i] : A[i + j * ld];
+}
+
 // factors of T_qq - lambda I
-template <bool C>
+template <bool C, bool PK = false>
 __device__ Fac factor(int bs, const double *Ts, int ts, int q, double lr, double li, double smin) {
     Cx M[2][2];
 #pragma unroll
@@ -101,14 +114,14 @@ __device__ Fac factor(int bs, const double *Ts, int ts, int q, double lr, double
 #pragma unroll
         for (int b = 0; b < 2; b++) {
             if (a >= bs || b >= bs) { M[a][b] = {0.0, 0.0}; continue; }
-            const double t = Ts[(q + a) + (q + b) * ts];
+            const double t = tile_at<PK>(Ts, ts, q + a, q + b);
             M[a][b] = (a == b) ? Cx{t - lr, C ? -li : 0.0} : Cx{t, 0.0};
         }
     return factor_matrix<C>(bs, M, smin);
 }
 
 // factors of beta S_qq - alpha T_qq (pencil; T upper triangular)
-template <bool C>
+template <bool C, bool PK = false>
 __device__ Fac factor_pencil(int bs, const double *Ss, const double *Tt, int ts, int q, double ar,
                              double ai, double be, double smin) {
     Cx M[2][2];
@@ -117,8 +130,8 @@ __device__ Fac factor_pencil(int bs, const double *Ss, const double *Tt, int ts,
 #pragma unroll
         for (int b = 0; b < 2; b++) {
             if (a >= bs || b >= bs) { M[a][b] = {0.0, 0.0}; continue; }
-            const double sv = Ss[(q + a) + (q + b) * ts];
-            const double tv = b >= a ? Tt[(q + a) + (q + b) * ts] : 0.0;
+            const double sv = tile_at<PK>(Ss, ts, q + a, q + b);
+            const double tv = b >= a ? tile_at<PK>(Tt, ts, q + a, q + b) : 0.0;
             M[a][b] = {be * sv - ar * tv, C ? -ai * tv : 0.0};
         }
     return factor_matrix<C>(bs, M, smin);
@@ -343,8 +356,8 @@ __device__ void diag_tile(int s, int list_pos0, const double *__restrict__ T, in
     const int tid = threadIdx.x;
 
     // shared layout
-    double *Ts = smem;                                 // ts x ts, ld ts
-    double *btau = Ts + ts * ts;                       // [kMaxTile]
+    double *Ts = smem;                                 // packed tile, pk_size(ts)
+    double *btau = Ts + pk_size(ts);                   // [kMaxTile]
     double *umu = btau + kMaxTile;                     // [kUnits]
     double *yr = umu + kUnits;                         // [ts][ys]
     double *yi = yr + ts * ys;                         // [ts][ys], complex units only
@@ -359,21 +372,19 @@ __device__ void diag_tile(int s, int list_pos0, const double *__restrict__ T, in
     int *facp = ue + kUnits;                           // [kUnits][ts] pivot positions
     int *uidx = facp + kUnits * ts;                    // [kUnits] unit index
     // pencils: T's tile, its in-tile block norms, per-unit block bounds
-    double *Bt = (double *)(((uintptr_t)(uidx + kUnits) + 15) & ~(uintptr_t)15);   // ts x ts
-    double *btauB = Bt + (GEN ? ts * ts : 0);          // [kMaxTile]
+    double *Bt = (double *)(((uintptr_t)(uidx + kUnits) + 15) & ~(uintptr_t)15);   // packed
+    double *btauB = Bt + (GEN ? pk_size(ts) : 0);      // [kMaxTile]
     double *utau = btauB + (GEN ? kMaxTile : 0);       // [kUnits][ts]
 
     // diagonal tile (upper part and first subdiagonal only), asynchronously
     for (int idx = tid; idx < ts * ts; idx += kThreads) {
         const int i = idx % ts, j = idx / ts;
-        if (i <= j + 1) cp_async8(&Ts[idx], T + (t0 + i) + (int64_t)(t0 + j) * ldt);
-        else Ts[idx] = 0.0;
+        if (i <= j + 1) cp_async8(&Ts[pk_col(j) + i], T + (t0 + i) + (int64_t)(t0 + j) * ldt);
     }
     if constexpr (GEN)
         for (int idx = tid; idx < ts * ts; idx += kThreads) {
             const int i = idx % ts, j = idx / ts;
-            if (i <= j) cp_async8(&Bt[idx], pen.T + (t0 + i) + (int64_t)(t0 + j) * pen.ldt);
-            else Bt[idx] = 0.0;
+            if (i <= j) cp_async8(&Bt[pk_col(j) + i], pen.T + (t0 + i) + (int64_t)(t0 + j) * pen.ldt);
         }
     asm volatile("cp.async.commit_group;");
     for (int k = tid; k < nbt; k += kThreads) {
@@ -431,9 +442,9 @@ __device__ void diag_tile(int s, int list_pos0, const double *__restrict__ T, in
             if (own && kb0 + kk >= kown) continue;
             Fac F;
             if constexpr (GEN) {
-                F = factor_pencil<C>(bsz[kk], Ts, Bt, ts, bq[kk], lr, li, be, smin);
+                F = factor_pencil<C, true>(bsz[kk], Ts, Bt, ts, bq[kk], lr, li, be, smin);
             } else {
-                F = factor<C>(bsz[kk], Ts, ts, bq[kk], lr, li, smin);
+                F = factor<C, true>(bsz[kk], Ts, ts, bq[kk], lr, li, smin);
             }
             double *fp = myfac + kk * FW;
             if (C) {
@@ -517,20 +528,21 @@ __device__ void diag_tile(int s, int list_pos0, const double *__restrict__ T, in
         const bool act = valid && (!own || k <= kown);
         const bool solving = act && !(own && k == kown);
         if (pq > 0) {   // rows [0, pq) -= (block pq) pz; pq = q + bs
-            const double *c0 = Ts + pq * ts;
+            const double *c0 = Ts + pk_col(pq);             // column pq, rows [0, pq)
             if constexpr (GEN) {
-                const double *d0 = Bt + pq * ts;
+                const double *d0 = Bt + pk_col(pq);
                 const Cx zb0 = {be * pz0.re, be * pz0.im}, zb1 = {be * pz1.re, be * pz1.im};
                 const Cx wz0 = cmul<C>(Cx{lr, li}, pz0), wz1 = cmul<C>(Cx{lr, li}, pz1);
                 if (pbs == 1)
                     update_rows_pencil<C, 1, G>(myr, myi, c0, c0, d0, d0, pq, g, zb0, zb1, wz0,
                                                 wz1, ys);
                 else
-                    update_rows_pencil<C, 2, G>(myr, myi, c0, c0 + ts, d0, d0 + ts, pq, g, zb0,
-                                                zb1, wz0, wz1, ys);
+                    update_rows_pencil<C, 2, G>(myr, myi, c0, Ts + pk_col(pq + 1), d0,
+                                                Bt + pk_col(pq + 1), pq, g, zb0, zb1, wz0, wz1,
+                                                ys);
             } else {
                 if (pbs == 1) update_rows<C, 1, G>(myr, myi, c0, c0, pq, g, pz0, pz1, ys);
-                else update_rows<C, 2, G>(myr, myi, c0, c0 + ts, pq, g, pz0, pz1, ys);
+                else update_rows<C, 2, G>(myr, myi, c0, Ts + pk_col(pq + 1), pq, g, pz0, pz1, ys);
             }
         }
         // the block's right-hand side from its owner lanes
@@ -734,10 +746,10 @@ template <int W, bool C, bool GEN = false, int GR = 8>
 inline size_t diag_smem_bytes(int t) {
     constexpr int kUnits = Lanes<C, GR>::U * W;
     constexpr int FW = C ? 8 : 4;
-    return sizeof(double) * ((size_t)t * t + kMaxTile + kUnits +
+    return sizeof(double) * ((size_t)pk_size(t) + kMaxTile + kUnits +
                              (C ? 2 : 1) * (size_t)t * (kUnits + 1) + (size_t)kUnits * t * FW) +
            sizeof(int) * (4 * (size_t)kMaxTile + 4 * kUnits + (size_t)kUnits * t) + 16 +
-           (GEN ? sizeof(double) * ((size_t)t * t + kMaxTile + (size_t)kUnits * t) : 0);
+           (GEN ? sizeof(double) * ((size_t)pk_size(t) + kMaxTile + (size_t)kUnits * t) : 0);
 }
 
 template <int W, bool GEN = false, int GR = 8>

@@ -775,6 +775,12 @@ cudaError_t launch_batched(const BatchItem *items, int count, int *queue, DevSta
         per_sm = 1;
     }
     if (split) per_sm = std::min(per_sm, kTmemCols / kBSTmemCols);
+    // Standard batches: at most two CTAs per SM.  Their time is the chain of
+    // the largest matrices, each on one CTA, and a third CTA on its SM slows
+    // that CTA more than it adds (B300, the 2000-matrix batch: 61.7 ms at two
+    // CTAs per SM, 79.4 at three).  Pencil batches, whose steps carry twice
+    // the update work, gain from the third (142.7 -> 113.3 ms).
+    if (gen_tile <= 0) per_sm = std::min(per_sm, 2);
     const int grid = std::min(count, nsm * per_sm);
     if (grid <= 0) return cudaSuccess;
     kern<<<grid, kBThreads, smem, st>>>(items, count, queue, status, S);
