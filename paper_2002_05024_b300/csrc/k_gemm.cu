@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(kThreads)
     extern __shared__ __align__(16) unsigned char smraw[];
     GemmSmem<BM> &sm = *reinterpret_cast<GemmSmem<BM> *>(smraw);
     __shared__ int sdy[kBN];
-    __shared__ double red[16][kBN + 1];
+    __shared__ long long red[16][kBN + 1];
     constexpr int MI = BM / 16;
 
     // tiles of more than BM rows: blockIdx.z picks the BM-row chunk
@@ -170,7 +170,10 @@ __global__ void __launch_bounds__(kThreads)
                           acc, false);
     }
 
-    double cmax[4] = {0.0, 0.0, 0.0, 0.0};
+    // one FP64 operation per entry on the DFMA pipe: the power-of-two
+    // scaling only when dy != 0 (2^0 Y is Y), the column maxima on the bit
+    // patterns of |v| (the order of non-negative doubles) in integer code
+    long long cmax[4] = {0, 0, 0, 0};
 #pragma unroll
     for (int jj = 0; jj < 4; jj++) {
         const int jl = tx + 16 * jj;
@@ -181,10 +184,10 @@ __global__ void __launch_bounds__(kThreads)
         for (int i = 0; i < MI; i++) {
             const int row = ty + 16 * i;
             if (row < rows) {
-                const double old = (dy == kFresh) ? 0.0 : scale2(c[row], dy);
+                const double old = (dy == kFresh) ? 0.0 : (dy == 0 ? c[row] : scale2(c[row], dy));
                 const double v = old - acc[i][jj];
                 c[row] = v;
-                cmax[jj] = fmax(cmax[jj], fabs(v));
+                cmax[jj] = max(cmax[jj], abs_bits(v));
             }
         }
     }
@@ -192,14 +195,14 @@ __global__ void __launch_bounds__(kThreads)
     for (int jj = 0; jj < 4; jj++) red[ty][tx + 16 * jj] = cmax[jj];
     __syncthreads();
     if (tid < ncols) {
-        double mx = 0.0;
+        long long mx = 0;
 #pragma unroll
-        for (int t = 0; t < 16; t++) mx = fmax(mx, red[t][tid]);
+        for (int t = 0; t < 16; t++) mx = max(mx, red[t][tid]);
         // the decisions zeroed seg_nu; the chunks of a tile merge their maxima
-        if (gridDim.z == 1) seg_nu[(int64_t)r * m + j0 + tid] = mx;
-        else if (mx > 0.0)
+        if (gridDim.z == 1) seg_nu[(int64_t)r * m + j0 + tid] = __longlong_as_double(mx);
+        else if (mx > 0)
             atomicMax((unsigned long long *)&seg_nu[(int64_t)r * m + j0 + tid],
-                      (unsigned long long)abs_bits(mx));
+                      (unsigned long long)mx);
     }
 }
 
