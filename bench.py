@@ -133,25 +133,25 @@ def workload(n, kind="config0"):
 # "other_workloads" (each a child process of this script, so its device
 # memory and its own timing are separate): name, arguments, what it is.
 OTHER_WORKLOADS = [
-    ("config1a_fp64", ["--n", "4096", "--no-records"],
+    ("n4096_fp64", ["--n", "4096", "--no-records"],
      "n = 4096 config-0 Schur form + Q, FP64, tile 64"),
-    ("config1a_split_sweep", ["--n", "4096", "--no-records", "--mode", "split", "--refine"],
+    ("n4096_split_sweep", ["--n", "4096", "--no-records", "--mode", "split", "--refine"],
      "n = 4096 config-0 Schur form + Q, split (8 slices) + FP64 residual-correction sweep"),
-    ("config1b_fp64", ["--n", "4096", "--no-records", "--input", "adversarial"],
+    ("n4096_clustered_fp64", ["--n", "4096", "--no-records", "--input", "adversarial"],
      "n = 4096 clustered adversarial Schur form + Q, FP64, tile 64"),
-    ("config4_fp64", ["--workload", "generalized"],
+    ("pencil_n8192_fp64", ["--workload", "generalized"],
      "n = 8192 pencil (S, T) + Z, FP64"),
-    ("config4_split", ["--workload", "generalized", "--mode", "split"],
+    ("pencil_n8192_split", ["--workload", "generalized", "--mode", "split"],
      "n = 8192 pencil (S, T) + Z, split (8 slices)"),
-    ("next1_trsolve_split", ["--workload", "trsolve", "--mode", "split"],
+    ("trsolve_n4096_split", ["--workload", "trsolve", "--mode", "split"],
      "robust triangular solve, n = 4096, 4096 right-hand sides, split"),
-    ("next2_left_split", ["--n", "4096", "--no-records", "--side", "left", "--mode", "split"],
+    ("left_n4096_split", ["--n", "4096", "--no-records", "--side", "left", "--mode", "split"],
      "left eigenvectors, n = 4096 + Q, split"),
-    ("next2_batched_pencils", ["--workload", "batched_generalized"],
+    ("batched_pencils_fp64", ["--workload", "batched_generalized"],
      "2000 pencils, n in [32, 1024], 30% selected, FP64, one persistent launch"),
-    ("next3_window_split", ["--workload", "window", "--mode", "split"],
+    ("window_n4096_split", ["--workload", "window", "--mode", "split"],
      "reordering off-diagonal updates, n = 4096 + Q, 32 windows of 128, split"),
-    ("next4_hessenberg_split", ["--workload", "hessenberg", "--mode", "split"],
+    ("hessenberg_n4096_split", ["--workload", "hessenberg", "--mode", "split"],
      "Hessenberg reduction with Q, n = 4096, split updates"),
 ]
 OTHER_KEYS = ("metric", "value", "unit", "ms_per_step", "steps", "warmup", "dtype",

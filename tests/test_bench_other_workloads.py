@@ -42,7 +42,12 @@ def test_other_workloads_record_parses_and_records_failures(monkeypatch):
     assert rec["c"]["error"] == "exit 0"
 
 
-def test_other_workloads_cover_every_config_and_next_row():
+def test_other_workloads_cover_every_workload_kind():
+    # the n = 4096 forms (config-0 and clustered), the pencil, and the
+    # triangular-solve, left, batched-pencil, reordering and Hessenberg runs
     names = [n for n, _, _ in bench.OTHER_WORKLOADS]
-    for prefix in ("config1a", "config1b", "config4", "next1", "next2", "next3", "next4"):
+    for prefix in ("n4096_fp64", "n4096_split", "n4096_clustered", "pencil_n8192", "trsolve",
+                   "left", "batched_pencils", "window", "hessenberg"):
         assert any(n.startswith(prefix) for n in names), prefix
+    args = {n: a for n, a, _ in bench.OTHER_WORKLOADS}
+    assert "adversarial" in args["n4096_clustered_fp64"]
