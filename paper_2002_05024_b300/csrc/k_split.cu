@@ -28,7 +28,8 @@
 // tile update of step s (Sec. 3.3, Z <- Y - T X) applies, per row i (tile
 // row r) and column j, Y_ij <- 2^dy[r, j] Y_ij - 2^(ea_i + eb_j + dx[r, j])
 // (A~ B~)_ij and merges |Y_ij| into the column maximum of segment (r, j)
-// (shared-memory maxima per CTA, one global atomicMax per (r, j) and CTA).
+// (shared-memory maxima per output tile, one global atomicMax per (r, j)
+// and tile, before the CTA takes its next tile).
 #include <math.h>
 
 #include <algorithm>
